@@ -1,0 +1,1357 @@
+/*
+ * gks_oracle.c -- plain, slow, FP64 CPU oracle of one two-stage fourth-order
+ * (S2O4) step of the high-order gas-kinetic scheme (GKS) for 3D weakly
+ * compressible isothermal flow on a structured grid, with actuator-line (ALM)
+ * and immersed-boundary (IBM) body forcing.
+ *
+ * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library. It shares no code, header,
+ * table or constant generator with the CUDA path, and it never calls it.
+ *
+ * Every step is written the way the paper states it (Sec. 2, Sec. 3 and the
+ * Appendix), in FP64, with every intermediate stored, and with the readings of
+ * silent or garbled passages that the repository's design notes list:
+ *   - BGK model and isothermal Maxwellian: Sec. 2, Eq. (bgk-3d) and the
+ *     equilibrium state below it; lambda = Ma^2 / (2 U_inf^2).
+ *   - Finite volume operator: Sec. 2, Eq. (semi), Eq. (finite).
+ *   - 2x2 Gauss quadrature on every face: Sec. 2, Eq. (x_example).
+ *   - Interface distribution f = g0 (1 - tau (a1 u + a2 v + a3 w + A) + A t):
+ *     Sec. 2, Eq. (flux); tau = mu / p.
+ *   - Micro-coefficients a1, a2, a3 and A: Sec. 2 and the Appendix (moment
+ *     recursion, 4x4 system and its closed-form solution, compatibility).
+ *   - WENO5 (Jiang-Shu) normal reconstruction, dimension by dimension, down to
+ *     the Gauss points: Sec. 2, last paragraph.
+ *   - Two-stage fourth-order time stepping and the CFL time step: Sec. 2.
+ *   - ALM sampling, loads and Gaussian projection: Sec. 3.1, Eq. (axial-
+ *     tangential), Eq. (Gaussian); truncation at 3 eps: Sec. 4.3.1.
+ *   - IBM spreading, direct forcing iteration: Sec. 3.2, Eq. (ibm-1),
+ *     Eq. (force-ibm); forcing after the S2O4 update: Sec. 3.3.
+ *   - Power and thrust coefficients: Sec. 4.4.1.
+ *   - Boundary conditions: Sec. 4.1 (periodic, no-slip wall), Sec. 4.3
+ *     (Riemann-invariant inflow, extrapolation outflow, slip wall), Sec. 4.4
+ *     (symmetry).
+ */
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "gks_oracle.h"
+
+#define G OG_GHOST
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Small dense linear algebra (used once, to derive reconstruction stencils). */
+/* ------------------------------------------------------------------------- */
+
+/* Solve A x = b in place (A n x n row-major, b length n) by Gaussian
+ * elimination with partial pivoting. Returns 0 on success. */
+static int solve_dense(int n, double *A, double *b)
+{
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) {
+                double t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+            }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
+        b[r] = s / A[r * n + r];
+    }
+    return 0;
+}
+
+/* Mean of x^p over [a, b]. */
+static double mean_pow(int p, double a, double b)
+{
+    return (pow(b, p + 1) - pow(a, p + 1)) / ((double)(p + 1) * (b - a));
+}
+
+/* Given the n x n matrix M that maps polynomial coefficients to the stencil
+ * data, and a linear functional ell on the coefficients, return the stencil
+ * weights w with ell(M^{-1} q) = sum_m w[m] q[m]. */
+static int stencil_weights(int n, const double *M, const double *ell, double *w)
+{
+    double A[36], e[6];
+    for (int m = 0; m < n; ++m) {
+        memcpy(A, M, sizeof(double) * n * n);
+        for (int r = 0; r < n; ++r) e[r] = (r == m) ? 1.0 : 0.0;
+        if (solve_dense(n, A, e)) return -1;
+        double s = 0.0;
+        for (int p = 0; p < n; ++p) s += ell[p] * e[p];
+        w[m] = s;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reconstruction stencils, all in index space (unit cells).                  */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int ready;
+    /* WENO5 candidates k = 0,1,2 over cells (k-2 .. k) relative to cell 0 =
+     * [-1/2, 1/2]: coefficient maps q -> quadratic coefficients (c0,c1,c2). */
+    double weno_cinv[3][3][3];
+    /* Linear (optimal) weights of the three candidates, Jiang-Shu. */
+    double weno_d[3];
+    /* Normal derivative at a face x = 0 from the face value Q0 and the cell
+     * averages of [-2,-1], [-1,0], [0,1], [1,2]: weights on (Q0, c0..c3). */
+    double dn_w[5];
+    /* Tangential quartic through 5 cell averages (offsets -2..2), evaluated at
+     * the Gauss points x = -g, +g with g = 1/(2 sqrt 3): value and derivative. */
+    double tv_w[2][5], td_w[2][5];
+    /* Reference quartic value at x = 1/2 from 5 cells (-2..2) (for pins). */
+    double q5_face_w[5];
+} og_stencils;
+
+static og_stencils ST;
+
+static int init_stencils(void)
+{
+    if (ST.ready) return 0;
+    /* WENO candidate quadratics. */
+    for (int k = 0; k < 3; ++k) {
+        double M[9];
+        for (int r = 0; r < 3; ++r) {
+            int o = k - 2 + r;
+            for (int p = 0; p < 3; ++p) M[r * 3 + p] = mean_pow(p, o - 0.5, o + 0.5);
+        }
+        /* column m of M^{-1}: coefficients produced by unit data e_m */
+        for (int m = 0; m < 3; ++m) {
+            double A[9], e[3] = {0, 0, 0};
+            memcpy(A, M, sizeof(A));
+            e[m] = 1.0;
+            if (solve_dense(3, A, e)) return -1;
+            for (int p = 0; p < 3; ++p) ST.weno_cinv[k][p][m] = e[p];
+        }
+    }
+    ST.weno_d[0] = 0.1; ST.weno_d[1] = 0.6; ST.weno_d[2] = 0.3;
+
+    /* Normal derivative: quartic with a point value at 0 and 4 cell averages. */
+    {
+        double M[25], ell[5] = {0, 1, 0, 0, 0};
+        for (int p = 0; p < 5; ++p) M[0 * 5 + p] = (p == 0) ? 1.0 : 0.0;
+        for (int r = 0; r < 4; ++r) {
+            double a = -2.0 + r, b = a + 1.0;
+            for (int p = 0; p < 5; ++p) M[(r + 1) * 5 + p] = mean_pow(p, a, b);
+        }
+        if (stencil_weights(5, M, ell, ST.dn_w)) return -1;
+    }
+    /* Tangential quartic through 5 cell averages. */
+    {
+        double M[25];
+        for (int r = 0; r < 5; ++r) {
+            double o = -2.0 + r;
+            for (int p = 0; p < 5; ++p) M[r * 5 + p] = mean_pow(p, o - 0.5, o + 0.5);
+        }
+        double gp = 1.0 / (2.0 * sqrt(3.0));
+        for (int m = 0; m < 2; ++m) {
+            double x = (m == 0) ? -gp : gp;
+            double ev[5], ed[5];
+            for (int p = 0; p < 5; ++p) {
+                ev[p] = pow(x, p);
+                ed[p] = (p == 0) ? 0.0 : p * pow(x, p - 1);
+            }
+            if (stencil_weights(5, M, ev, ST.tv_w[m])) return -1;
+            if (stencil_weights(5, M, ed, ST.td_w[m])) return -1;
+        }
+        double ef[5];
+        for (int p = 0; p < 5; ++p) ef[p] = pow(0.5, p);
+        if (stencil_weights(5, M, ef, ST.q5_face_w)) return -1;
+    }
+    ST.ready = 1;
+    return 0;
+}
+
+/* Smoothness indicator of Jiang and Shu for a quadratic p(x) = c0 + c1 x +
+ * c2 x^2 over the unit cell [-1/2, 1/2]: integral of (p')^2 + (p'')^2
+ * (the h^(2l-1) factors are 1 in index space). Integrated with 3-point
+ * Gauss-Legendre, exact for these polynomial degrees. */
+static double smoothness(const double c[3])
+{
+    static const double xg[3] = {-0.38729833462074168852, 0.0, 0.38729833462074168852};
+    static const double wg[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        double d1 = c[1] + 2.0 * c[2] * xg[q];
+        double d2 = 2.0 * c[2];
+        s += wg[q] * (d1 * d1 + d2 * d2);
+    }
+    return s;
+}
+
+/* WENO5-JS value at the right face (x = +1/2) of the centre cell of q[0..4]
+ * (cell averages of cells -2..2). eps_w = 1e-6, power 2 (reading R2). */
+double og_weno5(const double q[5])
+{
+    init_stencils();
+    double p[3], beta[3], alpha[3], asum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double c[3];
+        for (int r = 0; r < 3; ++r) {
+            c[r] = 0.0;
+            for (int m = 0; m < 3; ++m) c[r] += ST.weno_cinv[k][r][m] * q[k + m];
+        }
+        p[k] = c[0] + 0.5 * c[1] + 0.25 * c[2];
+        beta[k] = smoothness(c);
+        double e = 1e-6 + beta[k];
+        alpha[k] = ST.weno_d[k] / (e * e);
+        asum += alpha[k];
+    }
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) v += (alpha[k] / asum) * p[k];
+    return v;
+}
+
+/* Candidate values, smoothness indicators and nonlinear weights (for pins). */
+void og_weno5_parts(const double q[5], double p_out[3], double beta_out[3], double w_out[3])
+{
+    init_stencils();
+    double alpha[3], asum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double c[3];
+        for (int r = 0; r < 3; ++r) {
+            c[r] = 0.0;
+            for (int m = 0; m < 3; ++m) c[r] += ST.weno_cinv[k][r][m] * q[k + m];
+        }
+        p_out[k] = c[0] + 0.5 * c[1] + 0.25 * c[2];
+        beta_out[k] = smoothness(c);
+        double e = 1e-6 + beta_out[k];
+        alpha[k] = ST.weno_d[k] / (e * e);
+        asum += alpha[k];
+    }
+    for (int k = 0; k < 3; ++k) w_out[k] = alpha[k] / asum;
+}
+
+/* Normal derivative at the face between cells c[1] and c[2] of c[0..3]
+ * (cell averages of the cells i-1, i, i+1, i+2 around face i+1/2), from the
+ * quartic that takes the value Q0 at the face and those four averages
+ * (reading R4). Index-space derivative. */
+double og_normal_derivative(double q0, const double c[4])
+{
+    init_stencils();
+    /* The weights of a derivative sum to zero, so the value is written in
+     * difference form: uniform data give exactly zero. */
+    double s = 0.0;
+    for (int r = 0; r < 4; ++r) s += ST.dn_w[r + 1] * (c[r] - q0);
+    return s;
+}
+
+/* Tangential quartic reconstruction from 5 face averages (offsets -2..2) to
+ * the two Gauss points -g, +g: values val[2] and index-space derivatives
+ * der[2] (reading R5: linear, no WENO). */
+void og_tangential(const double q[5], double val[2], double der[2])
+{
+    init_stencils();
+    for (int m = 0; m < 2; ++m) {
+        double v = 0.0, d = 0.0;
+        for (int r = 0; r < 5; ++r) {
+            v += ST.tv_w[m][r] * q[r];
+            d += ST.td_w[m][r] * (q[r] - q[2]); /* derivative weights sum to zero */
+        }
+        val[m] = v;
+        der[m] = d;
+    }
+}
+
+/* Fifth-order linear reconstruction at x = +1/2 from 5 cell averages. */
+double og_linear5_face(const double q[5])
+{
+    init_stencils();
+    double v = 0.0;
+    for (int r = 0; r < 5; ++r) v += ST.q5_face_w[r] * q[r];
+    return v;
+}
+
+void og_stencil_table(double dn_w[5], double tv_w[10], double td_w[10], double weno_d[3])
+{
+    init_stencils();
+    memcpy(dn_w, ST.dn_w, sizeof(ST.dn_w));
+    memcpy(tv_w, ST.tv_w, sizeof(ST.tv_w));
+    memcpy(td_w, ST.td_w, sizeof(ST.td_w));
+    memcpy(weno_d, ST.weno_d, sizeof(ST.weno_d));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Maxwellian moments (Appendix).                                             */
+/* ------------------------------------------------------------------------- */
+
+/* Full-space normalised moments <u^k>, k = 0..kmax, of the isothermal
+ * Maxwellian with mean U: <u^0> = 1, <u^1> = U,
+ * <u^{k+2}> = (k+1)/(2 lambda) <u^k> + U <u^{k+1}>. */
+void og_moments(double U, double lambda, int kmax, double *M)
+{
+    M[0] = 1.0;
+    if (kmax >= 1) M[1] = U;
+    for (int k = 0; k + 2 <= kmax; ++k)
+        M[k + 2] = (k + 1) / (2.0 * lambda) * M[k] + U * M[k + 1];
+}
+
+/* Half-space moments <u^0>_{u>0}, <u^1>_{u>0} (sign = +1) or over u<0
+ * (sign = -1), normalised by rho. */
+void og_half_moments(double U, double lambda, int sign, double out[2])
+{
+    double sl = sqrt(lambda);
+    double e = exp(-lambda * U * U) / (2.0 * sqrt(PI * lambda));
+    if (sign > 0) {
+        out[0] = 0.5 * erfc(-sl * U);
+        out[1] = U * out[0] + e;
+    } else {
+        out[0] = 0.5 * erfc(sl * U);
+        out[1] = U * out[0] - e;
+    }
+}
+
+/* Appendix: solve M a = d with M = <psi psi^T> for the isothermal Maxwellian
+ * of mean (U,V,W), using the closed form printed there (reading R7 for the
+ * garbled superscripts of the last line). */
+void og_coeff_solve(double U, double V, double W, double lambda, const double d[4], double a[4])
+{
+    a[1] = 2.0 * lambda * (d[1] - U * d[0]);
+    a[2] = 2.0 * lambda * (d[2] - V * d[0]);
+    a[3] = 2.0 * lambda * (d[3] - W * d[0]);
+    a[0] = d[0] - U * a[1] - V * a[2] - W * a[3];
+}
+
+/* moment <u^p v^q w^r> from the per-axis moment tables */
+#define MOM(p, q, r) (Mu[(p)] * Mv[(q)] * Mw[(r)])
+
+/* <(c0 + c1 u + c2 v + c3 w) u^p v^q w^r> */
+static double mom_lin(const double *Mu, const double *Mv, const double *Mw, const double c[4], int p,
+                      int q, int r)
+{
+    return c[0] * MOM(p, q, r) + c[1] * MOM(p + 1, q, r) + c[2] * MOM(p, q + 1, r) +
+           c[3] * MOM(p, q, r + 1);
+}
+
+/* Gas-kinetic flux at one Gauss point, in the local frame of the face (u is
+ * the normal particle velocity, v and w the two tangential ones), Sec. 2
+ * Eq. (flux) and the Appendix:
+ *   f = g0 (1 - tau (a1 u + a2 v + a3 w + A) + A t)
+ *   F0 = rho0 [ <u psi> - tau <(a1 u + a2 v + a3 w + A) u psi> ],
+ *   F1 = d F / d t = rho0 <A u psi>.
+ * Q: conserved (rho, m_n, m_t1, m_t2); Dn, Dt1, Dt2: their derivatives along
+ * the normal and the two tangents. tau = mu / p with p = rho0 / (2 lambda)
+ * (reading R8); the right-hand sides are d = D / rho0 (reading R6). */
+void og_flux_local(double lambda, double mu, const double Q[4], const double Dn[4],
+                   const double Dt1[4], const double Dt2[4], double F0[4], double F1[4])
+{
+    double rho = Q[0];
+    double U = Q[1] / rho, V = Q[2] / rho, W = Q[3] / rho;
+    double Mu[8], Mv[8], Mw[8];
+    og_moments(U, lambda, 7, Mu);
+    og_moments(V, lambda, 7, Mv);
+    og_moments(W, lambda, 7, Mw);
+
+    double dn[4], dt1[4], dt2[4], an[4], at1[4], at2[4];
+    for (int k = 0; k < 4; ++k) {
+        dn[k] = Dn[k] / rho;
+        dt1[k] = Dt1[k] / rho;
+        dt2[k] = Dt2[k] / rho;
+    }
+    og_coeff_solve(U, V, W, lambda, dn, an);
+    og_coeff_solve(U, V, W, lambda, dt1, at1);
+    og_coeff_solve(U, V, W, lambda, dt2, at2);
+
+    /* psi_k = 1, u, v, w as exponents (p, q, r) */
+    static const int E[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+    /* compatibility: <A psi> = -<(a1 u + a2 v + a3 w) psi> */
+    double b[4], A[4];
+    for (int k = 0; k < 4; ++k) {
+        int p = E[k][0], q = E[k][1], r = E[k][2];
+        b[k] = -(mom_lin(Mu, Mv, Mw, an, p + 1, q, r) + mom_lin(Mu, Mv, Mw, at1, p, q + 1, r) +
+                 mom_lin(Mu, Mv, Mw, at2, p, q, r + 1));
+    }
+    og_coeff_solve(U, V, W, lambda, b, A);
+
+    double tau = 2.0 * lambda * mu / rho;
+    for (int k = 0; k < 4; ++k) {
+        int p = E[k][0] + 1, q = E[k][1], r = E[k][2]; /* u psi_k */
+        double neq = mom_lin(Mu, Mv, Mw, an, p + 1, q, r) + mom_lin(Mu, Mv, Mw, at1, p, q + 1, r) +
+                     mom_lin(Mu, Mv, Mw, at2, p, q, r + 1) + mom_lin(Mu, Mv, Mw, A, p, q, r);
+        F0[k] = rho * (MOM(p, q, r) - tau * neq);
+        F1[k] = rho * mom_lin(Mu, Mv, Mw, A, p, q, r);
+    }
+}
+
+/* Equilibrium state at the face from the left and right reconstructed
+ * states (local frame), by taking the u>0 half of the left Maxwellian and
+ * the u<0 half of the right one (reading R3). */
+void og_equilibrium_local(double lambda, const double Ql[4], const double Qr[4], double Q0[4])
+{
+    double rl = Ql[0], Ul = Ql[1] / rl, Vl = Ql[2] / rl, Wl = Ql[3] / rl;
+    double rr = Qr[0], Ur = Qr[1] / rr, Vr = Qr[2] / rr, Wr = Qr[3] / rr;
+    double hl[2], hr[2];
+    og_half_moments(Ul, lambda, +1, hl);
+    og_half_moments(Ur, lambda, -1, hr);
+    Q0[0] = rl * hl[0] + rr * hr[0];
+    Q0[1] = rl * hl[1] + rr * hr[1];
+    Q0[2] = rl * Vl * hl[0] + rr * Vr * hr[0];
+    Q0[3] = rl * Wl * hl[0] + rr * Wr * hr[0];
+}
+
+/* Truncated Gaussian projection kernel of Sec. 3.1 Eq. (Gaussian), cut at
+ * r = 3 eps (Sec. 4.3.1) and not renormalised (reading R23). */
+double og_gauss_kernel(double r, double eps)
+{
+    if (r > 3.0 * eps) return 0.0;
+    return exp(-(r / eps) * (r / eps)) / (eps * eps * eps * pow(PI, 1.5));
+}
+
+/* Two-stage fourth-order combination (reading R1), elementwise on n values:
+ *   stage 1: W* = W + dt/2 L(W) + dt^2/8 Lt(W)
+ *   stage 2: W^{n+1} = W + dt L(W) + dt^2/6 (Lt(W) + 2 Lt(W*)). */
+void og_s2o4_stage1(long n, double dt, const double *W, const double *L, const double *Lt,
+                    double *Ws)
+{
+    for (long i = 0; i < n; ++i) Ws[i] = W[i] + 0.5 * dt * L[i] + 0.125 * dt * dt * Lt[i];
+}
+
+void og_s2o4_stage2(long n, double dt, const double *W, const double *L, const double *Lt,
+                    const double *Lts, double *Wn)
+{
+    for (long i = 0; i < n; ++i)
+        Wn[i] = W[i] + dt * L[i] + dt * dt / 6.0 * (Lt[i] + 2.0 * Lts[i]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grid, state, boundary conditions.                                          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int kind; /* 0 = rotor, 1 = body */
+    /* rotor */
+    int nb, np;
+    double hub[3], omega, azimuth0, eps, rho_inf, radius, u_inf_ref;
+    double *r, *chord, *twist, *width, *scale;
+    int correction;
+    double *Fx, *Ft, *alpha, *phi, *X; /* per point: loads, angles, positions */
+    double thrust[OG_MAX_BLADES], torque[OG_MAX_BLADES], power, cp, ct;
+    /* body */
+    int n;
+    double *xyz, *dS, *vel;
+    int niter;
+    double tol;
+    long bb[3][2]; /* interior cell box touched by the kernel support */
+    double *Vbar, *vbar, *phi_c; /* per box cell */
+    double *fsum;                /* per box cell, 3 */
+    double force[3];
+    double *resid;               /* per iteration residual of the last step */
+    int iters_done;
+} og_object;
+
+struct og_grid {
+    int n[3], P[3];
+    long np;
+    double *xf[3];
+    double *h[3];  /* padded widths, index i + G */
+    double mach, u_ref, mu, lambda, theta, csound;
+    int bc[3][2];
+    double rho_in, u_in[3];
+    double fbody[3];
+    double cfl, dt_fixed;
+    int uniform[3];
+    double *W, *Ws, *L1, *Lt1, *L2, *Lt2;
+    double t, dt_last;
+    long nstep;
+    int nobj;
+    og_object *obj[OG_MAX_OBJECTS];
+    char err[256];
+};
+
+static long IDX(const og_grid *g, int i, int j, int k)
+{
+    return (long)(i + G) + (long)g->P[0] * ((long)(j + G) + (long)g->P[1] * (long)(k + G));
+}
+
+static int pmod(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+static void set_err(og_grid *g, const char *msg)
+{
+    snprintf(g->err, sizeof(g->err), "%s", msg);
+}
+
+const char *og_last_error(og_grid *g) { return g ? g->err : "null grid"; }
+
+og_grid *og_create(const int n[3], const double *xf0, const double *xf1, const double *xf2,
+                   double mach, double u_ref, double mu, const int bc[6], double cfl,
+                   double dt_fixed)
+{
+    if (init_stencils()) return NULL;
+    const double *xf[3] = {xf0, xf1, xf2};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 1) return NULL;
+        if (bc[2 * d] != OG_BC_PERIODIC || bc[2 * d + 1] != OG_BC_PERIODIC) {
+            if (n[d] < 3) return NULL;
+        }
+        if ((bc[2 * d] == OG_BC_PERIODIC) != (bc[2 * d + 1] == OG_BC_PERIODIC)) return NULL;
+        for (int i = 0; i < n[d]; ++i)
+            if (!(xf[d][i + 1] > xf[d][i])) return NULL;
+    }
+    if (!(mach > 0 && u_ref > 0 && mu >= 0)) return NULL;
+    og_grid *g = (og_grid *)calloc(1, sizeof(og_grid));
+    for (int d = 0; d < 3; ++d) {
+        g->n[d] = n[d];
+        g->P[d] = n[d] + 2 * G;
+        g->bc[d][0] = bc[2 * d];
+        g->bc[d][1] = bc[2 * d + 1];
+        g->xf[d] = (double *)malloc(sizeof(double) * (n[d] + 1));
+        memcpy(g->xf[d], xf[d], sizeof(double) * (n[d] + 1));
+        g->h[d] = (double *)malloc(sizeof(double) * g->P[d]);
+        for (int i = 0; i < n[d]; ++i) g->h[d][i + G] = xf[d][i + 1] - xf[d][i];
+        for (int l = 1; l <= G; ++l) {
+            if (g->bc[d][0] == OG_BC_PERIODIC) {
+                g->h[d][G - l] = g->h[d][G + pmod(-l, n[d])];
+                g->h[d][G + n[d] - 1 + l] = g->h[d][G + pmod(n[d] - 1 + l, n[d])];
+            } else {
+                g->h[d][G - l] = g->h[d][G + l - 1];
+                g->h[d][G + n[d] - 1 + l] = g->h[d][G + n[d] - l];
+            }
+        }
+        double h0 = g->h[d][G];
+        g->uniform[d] = 1;
+        for (int i = 0; i < n[d]; ++i)
+            if (fabs(g->h[d][G + i] - h0) > 1e-12 * fabs(h0)) g->uniform[d] = 0;
+    }
+    g->np = (long)g->P[0] * g->P[1] * g->P[2];
+    g->mach = mach;
+    g->u_ref = u_ref;
+    g->mu = mu;
+    g->lambda = mach * mach / (2.0 * u_ref * u_ref);
+    g->theta = 1.0 / (2.0 * g->lambda);
+    g->csound = sqrt(g->theta);
+    g->cfl = cfl;
+    g->dt_fixed = dt_fixed;
+    g->rho_in = 1.0;
+    g->W = (double *)calloc(4 * g->np, sizeof(double));
+    g->Ws = (double *)calloc(4 * g->np, sizeof(double));
+    g->L1 = (double *)calloc(4 * g->np, sizeof(double));
+    g->Lt1 = (double *)calloc(4 * g->np, sizeof(double));
+    g->L2 = (double *)calloc(4 * g->np, sizeof(double));
+    g->Lt2 = (double *)calloc(4 * g->np, sizeof(double));
+    return g;
+}
+
+static void free_object(og_object *o)
+{
+    if (!o) return;
+    free(o->r); free(o->chord); free(o->twist); free(o->width); free(o->scale);
+    free(o->Fx); free(o->Ft); free(o->alpha); free(o->phi); free(o->X);
+    free(o->xyz); free(o->dS); free(o->vel);
+    free(o->Vbar); free(o->vbar); free(o->phi_c); free(o->fsum); free(o->resid);
+    free(o);
+}
+
+void og_destroy(og_grid *g)
+{
+    if (!g) return;
+    for (int d = 0; d < 3; ++d) { free(g->xf[d]); free(g->h[d]); }
+    free(g->W); free(g->Ws); free(g->L1); free(g->Lt1); free(g->L2); free(g->Lt2);
+    for (int o = 0; o < g->nobj; ++o) free_object(g->obj[o]);
+    free(g);
+}
+
+long og_num_cells(const og_grid *g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
+
+void og_set_inflow(og_grid *g, double rho, double u, double v, double w)
+{
+    g->rho_in = rho;
+    g->u_in[0] = u; g->u_in[1] = v; g->u_in[2] = w;
+}
+
+void og_set_body_force(og_grid *g, double fx, double fy, double fz)
+{
+    g->fbody[0] = fx; g->fbody[1] = fy; g->fbody[2] = fz;
+}
+
+/* State exchange: Q is 4 x N, component-major, x fastest over the interior. */
+void og_set_state(og_grid *g, const double *Q)
+{
+    long N = og_num_cells(g);
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i)
+                    g->W[v * g->np + IDX(g, i, j, k)] =
+                        Q[v * N + i + (long)g->n[0] * (j + (long)g->n[1] * k)];
+}
+
+void og_get_state(const og_grid *g, double *Q)
+{
+    long N = og_num_cells(g);
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i)
+                    Q[v * N + i + (long)g->n[0] * (j + (long)g->n[1] * k)] =
+                        g->W[v * g->np + IDX(g, i, j, k)];
+}
+
+double og_time(const og_grid *g) { return g->t; }
+double og_last_dt(const og_grid *g) { return g->dt_last; }
+void og_set_time(og_grid *g, double t) { g->t = t; }
+
+/* Ghost cells, 3 layers (reading of the boundary conditions of Sec. 4). The
+ * axes are swept x, y, z; each sweep covers the ghost layers already filled
+ * on the earlier axes, so edges and corners are defined. */
+static void ghost_fill(og_grid *g, double *A)
+{
+    long np = g->np;
+    for (int d = 0; d < 3; ++d) {
+        int lo[3], hi[3];
+        for (int e = 0; e < 3; ++e) {
+            if (e < d) { lo[e] = -G; hi[e] = g->n[e] + G; }
+            else { lo[e] = 0; hi[e] = g->n[e]; }
+        }
+        int e1 = (d == 0) ? 1 : 0, e2 = (d == 2) ? 1 : 2;
+        int nd = g->n[d];
+        for (int s = 0; s < 2; ++s) {
+            int bc = g->bc[d][s];
+            for (int l = 1; l <= G; ++l) {
+                int gi = (s == 0) ? -l : nd - 1 + l;
+                int src;
+                switch (bc) {
+                case OG_BC_PERIODIC: src = pmod(gi, nd); break;
+                case OG_BC_NOSLIP:
+                case OG_BC_SLIP: src = (s == 0) ? l - 1 : nd - l; break;
+                default: src = (s == 0) ? 0 : nd - 1; break;
+                }
+                for (int b = lo[e2]; b < hi[e2]; ++b)
+                    for (int a = lo[e1]; a < hi[e1]; ++a) {
+                        int cg[3], cs[3];
+                        cg[d] = gi; cg[e1] = a; cg[e2] = b;
+                        cs[d] = src; cs[e1] = a; cs[e2] = b;
+                        long ig = IDX(g, cg[0], cg[1], cg[2]);
+                        long is = IDX(g, cs[0], cs[1], cs[2]);
+                        double q[4];
+                        for (int v = 0; v < 4; ++v) q[v] = A[v * np + is];
+                        if (bc == OG_BC_NOSLIP) {
+                            q[1] = -q[1]; q[2] = -q[2]; q[3] = -q[3];
+                        } else if (bc == OG_BC_SLIP) {
+                            q[1 + d] = -q[1 + d];
+                        } else if (bc == OG_BC_INFLOW) {
+                            /* outgoing isothermal Riemann invariant U -/+ C ln rho
+                             * carried from the first interior cell */
+                            double r1 = q[0], un1 = q[1 + d] / r1;
+                            double sg = (s == 0) ? 1.0 : -1.0;
+                            double rg = r1 * exp(sg * (g->u_in[d] - un1) / g->csound);
+                            q[0] = rg;
+                            q[1] = rg * g->u_in[0];
+                            q[2] = rg * g->u_in[1];
+                            q[3] = rg * g->u_in[2];
+                        }
+                        for (int v = 0; v < 4; ++v) A[v * np + ig] = q[v];
+                    }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spatial operator L and its time derivative (Sec. 2, Eq. (finite)).          */
+/* ------------------------------------------------------------------------- */
+
+static void spatial_operator(og_grid *g, const double *A, double *L, double *Lt)
+{
+    long np = g->np;
+    /* S accumulates sum over faces of (+-) area * flux, per cell. */
+    memset(L, 0, sizeof(double) * 4 * np);
+    memset(Lt, 0, sizeof(double) * 4 * np);
+
+    for (int d = 0; d < 3; ++d) {
+        int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        int nd = g->n[d], n1 = g->n[t1], n2 = g->n[t2];
+        long nf = nd + 1, e1 = n1 + 4, e2 = n2 + 4;
+        long nprep = nf * e1 * e2;
+        double *Q0 = (double *)malloc(sizeof(double) * 4 * nprep);
+        double *DN = (double *)malloc(sizeof(double) * 4 * nprep);
+        int vn = 1 + d, v1 = 1 + t1, v2 = 1 + t2; /* global component of local n, t1, t2 */
+
+        /* (1) normal WENO5, equilibrium state, normal derivative, on every face
+         *     of the tangentially extended face box */
+#pragma omp parallel for schedule(static)
+        for (long b = -2; b < n2 + 2; ++b) {
+            for (long a = -2; a < n1 + 2; ++a) {
+                for (long f = 0; f < nf; ++f) {
+                    double cell[6][4]; /* cells f-3 .. f+2 along d, local frame */
+                    for (int m = 0; m < 6; ++m) {
+                        int c[3];
+                        c[d] = (int)f - 3 + m; c[t1] = (int)a; c[t2] = (int)b;
+                        long ic = IDX(g, c[0], c[1], c[2]);
+                        cell[m][0] = A[0 * np + ic];
+                        cell[m][1] = A[vn * np + ic];
+                        cell[m][2] = A[v1 * np + ic];
+                        cell[m][3] = A[v2 * np + ic];
+                    }
+                    double Ql[4], Qr[4], Qe[4];
+                    for (int v = 0; v < 4; ++v) {
+                        double ql[5], qr[5];
+                        for (int m = 0; m < 5; ++m) {
+                            ql[m] = cell[m][v];     /* cells f-3 .. f+1 */
+                            qr[m] = cell[5 - m][v]; /* cells f+2 .. f-2 (mirrored) */
+                        }
+                        Ql[v] = og_weno5(ql);
+                        Qr[v] = og_weno5(qr);
+                    }
+                    og_equilibrium_local(g->lambda, Ql, Qr, Qe);
+                    double hfc = 0.5 * (g->h[d][G + f - 1] + g->h[d][G + f]);
+                    long ip = f + nf * ((a + 2) + e1 * (b + 2));
+                    for (int v = 0; v < 4; ++v) {
+                        double c4[4] = {cell[1][v], cell[2][v], cell[3][v], cell[4][v]};
+                        Q0[v * nprep + ip] = Qe[v];
+                        DN[v * nprep + ip] = og_normal_derivative(Qe[v], c4) / hfc;
+                    }
+                }
+            }
+        }
+
+        /* (2) tangential reconstruction to the 2x2 Gauss points, flux there,
+         *     quadrature, and accumulation into both neighbour cells */
+        long nff = nf * n1 * n2;
+        double *FF = (double *)malloc(sizeof(double) * 8 * nff);
+#pragma omp parallel for schedule(static)
+        for (long b = 0; b < n2; ++b) {
+            for (long a = 0; a < n1; ++a) {
+                for (long f = 0; f < nf; ++f) {
+                    /* t1 pass on the 5 rows b-2 .. b+2 */
+                    double rq[2][5][4], rd[2][5][4], rn[2][5][4];
+                    for (int s = 0; s < 5; ++s) {
+                        long bb = b - 2 + s;
+                        for (int v = 0; v < 4; ++v) {
+                            double q5[5], n5[5];
+                            for (int r = 0; r < 5; ++r) {
+                                long ip = f + nf * ((a - 2 + r + 2) + e1 * (bb + 2));
+                                q5[r] = Q0[v * nprep + ip];
+                                n5[r] = DN[v * nprep + ip];
+                            }
+                            double val[2], der[2], nval[2], nder[2];
+                            og_tangential(q5, val, der);
+                            og_tangential(n5, nval, nder);
+                            for (int m = 0; m < 2; ++m) {
+                                rq[m][s][v] = val[m];
+                                rd[m][s][v] = der[m];
+                                rn[m][s][v] = nval[m];
+                            }
+                        }
+                    }
+                    double ih1 = 1.0 / g->h[t1][G + a], ih2 = 1.0 / g->h[t2][G + b];
+                    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    for (int m = 0; m < 2; ++m) {
+                        for (int nn = 0; nn < 2; ++nn) {
+                            double Qg[4], Dn[4], D1[4], D2[4];
+                            for (int v = 0; v < 4; ++v) {
+                                double c5[5], d5[5], n5[5], val[2], der[2], dv[2], dd[2], nv[2],
+                                    nd2[2];
+                                for (int s = 0; s < 5; ++s) {
+                                    c5[s] = rq[m][s][v];
+                                    d5[s] = rd[m][s][v];
+                                    n5[s] = rn[m][s][v];
+                                }
+                                og_tangential(c5, val, der);
+                                og_tangential(d5, dv, dd);
+                                og_tangential(n5, nv, nd2);
+                                Qg[v] = val[nn];
+                                D2[v] = der[nn] * ih2;
+                                D1[v] = dv[nn] * ih1;
+                                Dn[v] = nv[nn];
+                            }
+                            double F0[4], F1[4];
+                            og_flux_local(g->lambda, g->mu, Qg, Dn, D1, D2, F0, F1);
+                            for (int v = 0; v < 4; ++v) {
+                                acc[v] += 0.25 * F0[v];
+                                acc[4 + v] += 0.25 * F1[v];
+                            }
+                        }
+                    }
+                    long iff = f + nf * (a + n1 * b);
+                    /* back to global component order */
+                    int gv[4] = {0, vn, v1, v2};
+                    for (int v = 0; v < 4; ++v) {
+                        FF[gv[v] * nff + iff] = acc[v];
+                        FF[(4 + gv[v]) * nff + iff] = acc[4 + v];
+                    }
+                }
+            }
+        }
+
+        /* (3) accumulate sum over faces of (+-) area * flux into S, in the order
+         *     low face then high face, direction by direction */
+#pragma omp parallel for schedule(static)
+        for (long b = 0; b < n2; ++b) {
+            for (long a = 0; a < n1; ++a) {
+                for (long c = 0; c < nd; ++c) {
+                    int cc[3];
+                    cc[d] = (int)c; cc[t1] = (int)a; cc[t2] = (int)b;
+                    long ic = IDX(g, cc[0], cc[1], cc[2]);
+                    double area = g->h[t1][G + a] * g->h[t2][G + b];
+                    long ilo = c + nf * (a + n1 * b), ihi = ilo + 1;
+                    for (int v = 0; v < 4; ++v) {
+                        L[v * np + ic] += -area * FF[v * nff + ilo];
+                        L[v * np + ic] += area * FF[v * nff + ihi];
+                        Lt[v * np + ic] += -area * FF[(4 + v) * nff + ilo];
+                        Lt[v * np + ic] += area * FF[(4 + v) * nff + ihi];
+                    }
+                }
+            }
+        }
+        free(Q0);
+        free(DN);
+        free(FF);
+    }
+    /* L = -(1/|Omega|) S */
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < g->n[2]; ++k)
+        for (long j = 0; j < g->n[1]; ++j)
+            for (long i = 0; i < g->n[0]; ++i) {
+                long ic = IDX(g, (int)i, (int)j, (int)k);
+                double vol = g->h[0][G + i] * g->h[1][G + j] * g->h[2][G + k];
+                for (int v = 0; v < 4; ++v) {
+                    L[v * np + ic] = -L[v * np + ic] / vol;
+                    Lt[v * np + ic] = -Lt[v * np + ic] / vol;
+                }
+            }
+}
+
+/* L and dL/dt of a given interior state (4 x N, same layout as og_set_state).
+ * The state is ghost-filled by the grid's boundary conditions first. */
+void og_rhs(og_grid *g, const double *Q, double *Lout, double *Ltout)
+{
+    long N = og_num_cells(g), np = g->np;
+    double *A = (double *)calloc(4 * np, sizeof(double));
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i)
+                    A[v * np + IDX(g, i, j, k)] = Q[v * N + i + (long)g->n[0] * (j + (long)g->n[1] * k)];
+    ghost_fill(g, A);
+    double *L = (double *)malloc(sizeof(double) * 4 * np);
+    double *Lt = (double *)malloc(sizeof(double) * 4 * np);
+    spatial_operator(g, A, L, Lt);
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    long o = v * N + i + (long)g->n[0] * (j + (long)g->n[1] * k);
+                    Lout[o] = L[v * np + IDX(g, i, j, k)];
+                    Ltout[o] = Lt[v * np + IDX(g, i, j, k)];
+                }
+    free(A); free(L); free(Lt);
+}
+
+/* Ghost-filled padded copy of an interior state (for pins of the boundary
+ * conditions): out has 4 x P0 x P1 x P2 values. */
+void og_ghost_filled(og_grid *g, const double *Q, double *out)
+{
+    long N = og_num_cells(g), np = g->np;
+    memset(out, 0, sizeof(double) * 4 * np);
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i)
+                    out[v * np + IDX(g, i, j, k)] = Q[v * N + i + (long)g->n[0] * (j + (long)g->n[1] * k)];
+    ghost_fill(g, out);
+}
+
+/* Largest velocity magnitude over the interior cells. */
+static double max_speed(const og_grid *g, const double *A)
+{
+    double mx = 0.0;
+    long np = g->np;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                long ic = IDX(g, i, j, k);
+                double r = A[ic];
+                double u = A[np + ic] / r, v = A[2 * np + ic] / r, w = A[3 * np + ic] / r;
+                double s = sqrt(u * u + v * v + w * w);
+                if (s > mx) mx = s;
+            }
+    return mx;
+}
+
+/* CFL time step of Sec. 2: dt = CFL min(dx,dy,dz) / (|U|max + C). */
+double og_cfl_dt(const og_grid *g)
+{
+    double hmin = INFINITY;
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < g->n[d]; ++i)
+            if (g->h[d][G + i] < hmin) hmin = g->h[d][G + i];
+    return g->cfl * hmin / (max_speed(g, g->W) + g->csound);
+}
+
+/* ------------------------------------------------------------------------- */
+/* ALM (Sec. 3.1) and IBM (Sec. 3.2).                                         */
+/* ------------------------------------------------------------------------- */
+
+static double cell_centre(const og_grid *g, int d, int i)
+{
+    return g->xf[d][0] + (i + 0.5) * g->h[d][G];
+}
+
+/* Trilinear interpolation of the cell-centre velocity m/rho at X (uniform
+ * axes). Returns -1 when X is outside the hull of interior cell centres. */
+static int trilinear_velocity(const og_grid *g, const double *A, const double X[3], double U[3])
+{
+    int i0[3];
+    double fr[3];
+    for (int d = 0; d < 3; ++d) {
+        double s = (X[d] - g->xf[d][0]) / g->h[d][G] - 0.5;
+        double fl = floor(s);
+        i0[d] = (int)fl;
+        fr[d] = s - fl;
+        if (i0[d] < 0 || i0[d] + 1 > g->n[d] - 1) {
+            if (g->n[d] == 1 && s >= -0.5 && s <= 0.5) { i0[d] = 0; fr[d] = 0.0; continue; }
+            return -1;
+        }
+    }
+    long np = g->np;
+    U[0] = U[1] = U[2] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        double w = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1]) * (dk ? fr[2] : 1.0 - fr[2]);
+        if (w == 0.0) continue;
+        int ii = i0[0] + di, jj = i0[1] + dj, kk = i0[2] + dk;
+        if (g->n[0] == 1) ii = 0;
+        if (g->n[1] == 1) jj = 0;
+        if (g->n[2] == 1) kk = 0;
+        long ic = IDX(g, ii, jj, kk);
+        double r = A[ic];
+        U[0] += w * A[np + ic] / r;
+        U[1] += w * A[2 * np + ic] / r;
+        U[2] += w * A[3 * np + ic] / r;
+    }
+    return 0;
+}
+
+static int axes_uniform(const og_grid *g)
+{
+    return g->uniform[0] && g->uniform[1] && g->uniform[2];
+}
+
+/* Interior cell index box whose centres may lie within rad of the points. */
+static void support_box(const og_grid *g, const double *X, long npts, double rad, long bb[3][2])
+{
+    for (int d = 0; d < 3; ++d) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (long p = 0; p < npts; ++p) {
+            if (X[3 * p + d] < lo) lo = X[3 * p + d];
+            if (X[3 * p + d] > hi) hi = X[3 * p + d];
+        }
+        double h = g->h[d][G];
+        long a = (long)floor((lo - rad - g->xf[d][0]) / h - 0.5) - 1;
+        long b = (long)ceil((hi + rad - g->xf[d][0]) / h - 0.5) + 1;
+        if (a < 0) a = 0;
+        if (b > g->n[d] - 1) b = g->n[d] - 1;
+        bb[d][0] = a;
+        bb[d][1] = b;
+    }
+}
+
+int og_add_rotor(og_grid *g, int nb, int np, const double hub[3], double omega, double azimuth0,
+                 double radius, double eps, double rho_inf, double u_inf_ref, const double *r,
+                 const double *chord, const double *twist, const double *width, int correction)
+{
+    if (!axes_uniform(g)) { set_err(g, "ALM needs uniform axes"); return -1; }
+    if (nb < 1 || nb > OG_MAX_BLADES || np < 1 || eps <= 0 || g->nobj >= OG_MAX_OBJECTS) {
+        set_err(g, "bad rotor");
+        return -1;
+    }
+    og_object *o = (og_object *)calloc(1, sizeof(og_object));
+    o->kind = 0;
+    o->nb = nb; o->np = np;
+    memcpy(o->hub, hub, sizeof(o->hub));
+    o->omega = omega; o->azimuth0 = azimuth0; o->eps = eps; o->rho_inf = rho_inf;
+    o->radius = radius; o->u_inf_ref = u_inf_ref; o->correction = correction;
+    o->r = (double *)malloc(sizeof(double) * np); memcpy(o->r, r, sizeof(double) * np);
+    o->chord = (double *)malloc(sizeof(double) * np); memcpy(o->chord, chord, sizeof(double) * np);
+    o->twist = (double *)malloc(sizeof(double) * np); memcpy(o->twist, twist, sizeof(double) * np);
+    o->width = (double *)malloc(sizeof(double) * np); memcpy(o->width, width, sizeof(double) * np);
+    o->scale = (double *)malloc(sizeof(double) * nb * np);
+    for (int i = 0; i < nb * np; ++i) o->scale[i] = 1.0;
+    o->Fx = (double *)calloc(nb * np, sizeof(double));
+    o->Ft = (double *)calloc(nb * np, sizeof(double));
+    o->alpha = (double *)calloc(nb * np, sizeof(double));
+    o->phi = (double *)calloc(nb * np, sizeof(double));
+    o->X = (double *)calloc(3 * nb * np, sizeof(double));
+    g->obj[g->nobj] = o;
+    return g->nobj++;
+}
+
+int og_set_force_scales(og_grid *g, int id, const double *s)
+{
+    if (id < 0 || id >= g->nobj || g->obj[id]->kind != 0) return -1;
+    og_object *o = g->obj[id];
+    memcpy(o->scale, s, sizeof(double) * o->nb * o->np);
+    return 0;
+}
+
+/* Synthetic polar of the rotor workloads: C_L = clip(2 pi sin a, +-1.4),
+ * C_D = 0.01 + 0.02 a^2 (a in radians). */
+static double polar_cl(double a)
+{
+    double c = 2.0 * PI * sin(a);
+    if (c > 1.4) c = 1.4;
+    if (c < -1.4) c = -1.4;
+    return c;
+}
+static double polar_cd(double a) { return 0.01 + 0.02 * a * a; }
+
+static int alm_apply(og_grid *g, og_object *o, double t, double dt)
+{
+    long np_ = g->np;
+    int nb = o->nb, npt = o->np;
+    /* (1) positions at t, sampling, loads */
+    for (int b = 0; b < nb; ++b) {
+        double th = o->azimuth0 + o->omega * t + 2.0 * PI * b / nb;
+        double cth = cos(th), sth = sin(th);
+        for (int p = 0; p < npt; ++p) {
+            int q = b * npt + p;
+            double rr = o->r[p];
+            double X[3] = {o->hub[0], o->hub[1] + rr * cth, o->hub[2] + rr * sth};
+            o->X[3 * q] = X[0]; o->X[3 * q + 1] = X[1]; o->X[3 * q + 2] = X[2];
+            double U[3];
+            if (trilinear_velocity(g, g->W, X, U)) { set_err(g, "actuator point outside"); return -1; }
+            double ux = U[0];
+            double ut = -sth * U[1] + cth * U[2];
+            double wr = o->omega * rr;
+            if (o->correction) {
+                double phi0 = atan2(ux, wr - ut);
+                double cd0 = polar_cd(phi0 - o->twist[p]);
+                double fac = 1.0 / (1.0 - cd0 * o->chord[p] / (4.0 * sqrt(PI) * o->eps));
+                ux *= fac;
+                ut *= fac;
+            }
+            double phi = atan2(ux, wr - ut);
+            double al = phi - o->twist[p];
+            double urel2 = ux * ux + (wr - ut) * (wr - ut);
+            double qd = 0.5 * o->rho_inf * o->chord[p] * o->width[p] * urel2;
+            double Lf = qd * polar_cl(al), Df = qd * polar_cd(al);
+            o->Fx[q] = (Lf * cos(phi) + Df * sin(phi)) * o->scale[q];
+            o->Ft[q] = (Lf * sin(phi) - Df * cos(phi)) * o->scale[q];
+            o->alpha[q] = al;
+            o->phi[q] = phi;
+        }
+    }
+    double ptot = 0.0, ttot = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        double T = 0.0, Q = 0.0;
+        for (int p = 0; p < npt; ++p) {
+            T += o->Fx[b * npt + p];
+            Q += o->r[p] * o->Ft[b * npt + p];
+        }
+        o->thrust[b] = T;
+        o->torque[b] = Q;
+        ttot += T;
+        ptot += Q;
+    }
+    o->power = o->omega * ptot;
+    double A = PI * o->radius * o->radius;
+    double U = o->u_inf_ref;
+    o->cp = o->power / (0.5 * o->rho_inf * A * U * U * U);
+    o->ct = ttot / (0.5 * o->rho_inf * A * U * U);
+
+    /* (2) projection: every cell within 3 eps of a point receives -F eta */
+    long bb[3][2];
+    support_box(g, o->X, (long)nb * npt, 3.0 * o->eps, bb);
+#pragma omp parallel for schedule(static)
+    for (long k = bb[2][0]; k <= bb[2][1]; ++k)
+        for (long j = bb[1][0]; j <= bb[1][1]; ++j)
+            for (long i = bb[0][0]; i <= bb[0][1]; ++i) {
+                double xc[3] = {cell_centre(g, 0, (int)i), cell_centre(g, 1, (int)j),
+                                cell_centre(g, 2, (int)k)};
+                double f[3] = {0, 0, 0};
+                for (int b = 0; b < nb; ++b) {
+                    double th = o->azimuth0 + o->omega * t + 2.0 * PI * b / nb;
+                    double cth = cos(th), sth = sin(th);
+                    double fb[3] = {0, 0, 0};
+                    for (int p = 0; p < npt; ++p) {
+                        int q = b * npt + p;
+                        double dx = xc[0] - o->X[3 * q], dy = xc[1] - o->X[3 * q + 1],
+                               dz = xc[2] - o->X[3 * q + 2];
+                        double rr = sqrt(dx * dx + dy * dy + dz * dz);
+                        double eta = og_gauss_kernel(rr, o->eps);
+                        if (eta == 0.0) continue;
+                        fb[0] += -o->Fx[q] * eta;
+                        fb[1] += -o->Ft[q] * (-sth) * eta;
+                        fb[2] += -o->Ft[q] * cth * eta;
+                    }
+                    f[0] += fb[0]; f[1] += fb[1]; f[2] += fb[2];
+                }
+                long ic = IDX(g, (int)i, (int)j, (int)k);
+                g->W[np_ + ic] += dt * f[0];
+                g->W[2 * np_ + ic] += dt * f[1];
+                g->W[3 * np_ + ic] += dt * f[2];
+            }
+    return 0;
+}
+
+int og_add_body(og_grid *g, int n, const double *xyz, const double *dS, const double *vel,
+                double eps, int niter, double tol)
+{
+    if (!axes_uniform(g)) { set_err(g, "IBM needs uniform axes"); return -1; }
+    if (n < 1 || eps <= 0 || niter < 1 || g->nobj >= OG_MAX_OBJECTS) { set_err(g, "bad body"); return -1; }
+    og_object *o = (og_object *)calloc(1, sizeof(og_object));
+    o->kind = 1;
+    o->n = n; o->eps = eps; o->niter = niter; o->tol = tol;
+    o->xyz = (double *)malloc(sizeof(double) * 3 * n); memcpy(o->xyz, xyz, sizeof(double) * 3 * n);
+    o->dS = (double *)malloc(sizeof(double) * n); memcpy(o->dS, dS, sizeof(double) * n);
+    o->vel = (double *)calloc(3 * n, sizeof(double));
+    if (vel) memcpy(o->vel, vel, sizeof(double) * 3 * n);
+    o->resid = (double *)calloc(niter, sizeof(double));
+    support_box(g, o->xyz, n, 3.0 * eps, o->bb);
+    long nbx = (o->bb[0][1] - o->bb[0][0] + 1) * (o->bb[1][1] - o->bb[1][0] + 1) *
+               (o->bb[2][1] - o->bb[2][0] + 1);
+    o->Vbar = (double *)calloc(nbx, sizeof(double));
+    o->vbar = (double *)calloc(3 * nbx, sizeof(double));
+    o->phi_c = (double *)calloc(nbx, sizeof(double));
+    o->fsum = (double *)calloc(3 * nbx, sizeof(double));
+    double vol = g->h[0][G] * g->h[1][G] * g->h[2][G];
+    double Delta = cbrt(vol);
+    long lx = o->bb[0][1] - o->bb[0][0] + 1, ly = o->bb[1][1] - o->bb[1][0] + 1;
+    /* Sec. 3.2: Vbar = sum_p W V_p, vbar from sum_p W V_p v_p, V_p = Delta dS */
+#pragma omp parallel for schedule(static)
+    for (long k = o->bb[2][0]; k <= o->bb[2][1]; ++k)
+        for (long j = o->bb[1][0]; j <= o->bb[1][1]; ++j)
+            for (long i = o->bb[0][0]; i <= o->bb[0][1]; ++i) {
+                long c = (i - o->bb[0][0]) + lx * ((j - o->bb[1][0]) + ly * (k - o->bb[2][0]));
+                double xc[3] = {cell_centre(g, 0, (int)i), cell_centre(g, 1, (int)j),
+                                cell_centre(g, 2, (int)k)};
+                double Vb = 0.0, vs[3] = {0, 0, 0};
+                for (long p = 0; p < n; ++p) {
+                    double dx = xc[0] - o->xyz[3 * p], dy = xc[1] - o->xyz[3 * p + 1],
+                           dz = xc[2] - o->xyz[3 * p + 2];
+                    double W = og_gauss_kernel(sqrt(dx * dx + dy * dy + dz * dz), eps) * vol;
+                    if (W == 0.0) continue;
+                    double Vp = Delta * o->dS[p];
+                    Vb += W * Vp;
+                    vs[0] += W * Vp * o->vel[3 * p];
+                    vs[1] += W * Vp * o->vel[3 * p + 1];
+                    vs[2] += W * Vp * o->vel[3 * p + 2];
+                }
+                o->Vbar[c] = Vb;
+                for (int d = 0; d < 3; ++d) o->vbar[3 * c + d] = (Vb > 0.0) ? vs[d] / Vb : 0.0;
+                double ph = Vb / vol;
+                o->phi_c[c] = ph > 1.0 ? 1.0 : ph;
+            }
+    g->obj[g->nobj] = o;
+    return g->nobj++;
+}
+
+/* Per-cell IBM fields of a body over its cell box (for pins). Returns the
+ * number of box cells; fills bb[6] and, if not NULL, Vbar and phi. */
+long og_body_fields(og_grid *g, int id, long bb[6], double *Vbar, double *phi)
+{
+    if (id < 0 || id >= g->nobj || g->obj[id]->kind != 1) return -1;
+    og_object *o = g->obj[id];
+    for (int d = 0; d < 3; ++d) { bb[2 * d] = o->bb[d][0]; bb[2 * d + 1] = o->bb[d][1]; }
+    long nbx = (o->bb[0][1] - o->bb[0][0] + 1) * (o->bb[1][1] - o->bb[1][0] + 1) *
+               (o->bb[2][1] - o->bb[2][0] + 1);
+    if (Vbar) memcpy(Vbar, o->Vbar, sizeof(double) * nbx);
+    if (phi) memcpy(phi, o->phi_c, sizeof(double) * nbx);
+    return nbx;
+}
+
+static double ibm_residual(og_grid *g, og_object *o)
+{
+    long np_ = g->np;
+    double vol = g->h[0][G] * g->h[1][G] * g->h[2][G];
+    double rmax = 0.0;
+    for (long p = 0; p < o->n; ++p) {
+        double Up[3] = {0, 0, 0};
+        for (long k = o->bb[2][0]; k <= o->bb[2][1]; ++k)
+            for (long j = o->bb[1][0]; j <= o->bb[1][1]; ++j)
+                for (long i = o->bb[0][0]; i <= o->bb[0][1]; ++i) {
+                    double dx = cell_centre(g, 0, (int)i) - o->xyz[3 * p];
+                    double dy = cell_centre(g, 1, (int)j) - o->xyz[3 * p + 1];
+                    double dz = cell_centre(g, 2, (int)k) - o->xyz[3 * p + 2];
+                    double W = og_gauss_kernel(sqrt(dx * dx + dy * dy + dz * dz), o->eps) * vol;
+                    if (W == 0.0) continue;
+                    long ic = IDX(g, (int)i, (int)j, (int)k);
+                    double r = g->W[ic];
+                    Up[0] += W * g->W[np_ + ic] / r;
+                    Up[1] += W * g->W[2 * np_ + ic] / r;
+                    Up[2] += W * g->W[3 * np_ + ic] / r;
+                }
+        double e0 = o->vel[3 * p] - Up[0], e1 = o->vel[3 * p + 1] - Up[1], e2 = o->vel[3 * p + 2] - Up[2];
+        double e = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        if (e > rmax) rmax = e;
+    }
+    return rmax;
+}
+
+static void ibm_apply(og_grid *g, og_object *o, double dt)
+{
+    long np_ = g->np;
+    double vol = g->h[0][G] * g->h[1][G] * g->h[2][G];
+    long lx = o->bb[0][1] - o->bb[0][0] + 1, ly = o->bb[1][1] - o->bb[1][0] + 1;
+    long nbx = lx * ly * (o->bb[2][1] - o->bb[2][0] + 1);
+    memset(o->fsum, 0, sizeof(double) * 3 * nbx);
+    o->iters_done = 0;
+    for (int s = 0; s < o->niter; ++s) {
+        /* Eq. (ibm-1) and the momentum update, with the volume reading R15 */
+        for (long k = o->bb[2][0]; k <= o->bb[2][1]; ++k)
+            for (long j = o->bb[1][0]; j <= o->bb[1][1]; ++j)
+                for (long i = o->bb[0][0]; i <= o->bb[0][1]; ++i) {
+                    long c = (i - o->bb[0][0]) + lx * ((j - o->bb[1][0]) + ly * (k - o->bb[2][0]));
+                    if (!(o->Vbar[c] > 0.0)) continue;
+                    long ic = IDX(g, (int)i, (int)j, (int)k);
+                    double rho = g->W[ic];
+                    for (int d = 0; d < 3; ++d) {
+                        double U = g->W[(1 + d) * np_ + ic] / rho;
+                        double F = rho * o->phi_c[c] * vol * (o->vbar[3 * c + d] - U) / dt;
+                        g->W[(1 + d) * np_ + ic] += dt * F / vol;
+                        o->fsum[3 * c + d] += F;
+                    }
+                }
+        o->iters_done = s + 1;
+        if (o->tol > 0.0 || s == o->niter - 1) {
+            o->resid[s] = ibm_residual(g, o);
+            if (o->tol > 0.0 && o->resid[s] < o->tol) break;
+        }
+    }
+    /* Eq. (force-ibm): force on the structure is minus the summed cell force */
+    double fb[3] = {0, 0, 0};
+    for (long c = 0; c < nbx; ++c)
+        for (int d = 0; d < 3; ++d) fb[d] += o->fsum[3 * c + d];
+    for (int d = 0; d < 3; ++d) o->force[d] = -fb[d];
+}
+
+/* ------------------------------------------------------------------------- */
+/* One S2O4 step and the public driver.                                       */
+/* ------------------------------------------------------------------------- */
+
+static int one_step(og_grid *g)
+{
+    long np = g->np;
+    ghost_fill(g, g->W);
+    double dt = (g->dt_fixed > 0.0) ? g->dt_fixed : og_cfl_dt(g);
+    g->dt_last = dt;
+    spatial_operator(g, g->W, g->L1, g->Lt1);
+    og_s2o4_stage1(4 * np, dt, g->W, g->L1, g->Lt1, g->Ws);
+    ghost_fill(g, g->Ws);
+    spatial_operator(g, g->Ws, g->L2, g->Lt2);
+    /* W^{n+1} on the interior (ghost values of W are refilled next step) */
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    long o = v * np + IDX(g, i, j, k);
+                    double w = g->W[o];
+                    og_s2o4_stage2(1, dt, &w, &g->L1[o], &g->Lt1[o], &g->Lt2[o], &g->W[o]);
+                }
+    /* constant body force (channel driving force), after the update */
+    for (int d = 0; d < 3; ++d) {
+        if (g->fbody[d] == 0.0) continue;
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) g->W[(1 + d) * np + IDX(g, i, j, k)] += dt * g->fbody[d];
+    }
+    g->t += dt;
+    /* Sec. 3.3: external forcing after the S2O4 update; rotors, then bodies */
+    for (int o = 0; o < g->nobj; ++o)
+        if (g->obj[o]->kind == 0)
+            if (alm_apply(g, g->obj[o], g->t, dt)) return -1;
+    for (int o = 0; o < g->nobj; ++o)
+        if (g->obj[o]->kind == 1) ibm_apply(g, g->obj[o], dt);
+    g->nstep++;
+    return 0;
+}
+
+int og_step(og_grid *g, int nsteps)
+{
+    for (int s = 0; s < nsteps; ++s)
+        if (one_step(g)) return -1;
+    return 0;
+}
+
+/* Rotor: out = [thrust[nb], torque[nb], power, cp, ct]; point data =
+ * [Fx, Ft, alpha, phi] x (nb*np). Body: out = [fx, fy, fz, iters, resid_last]. */
+int og_forces(og_grid *g, int id, double *out, double *points)
+{
+    if (id < 0 || id >= g->nobj) return -1;
+    og_object *o = g->obj[id];
+    if (o->kind == 0) {
+        for (int b = 0; b < o->nb; ++b) { out[b] = o->thrust[b]; out[o->nb + b] = o->torque[b]; }
+        out[2 * o->nb] = o->power;
+        out[2 * o->nb + 1] = o->cp;
+        out[2 * o->nb + 2] = o->ct;
+        if (points) {
+            int n = o->nb * o->np;
+            memcpy(points, o->Fx, sizeof(double) * n);
+            memcpy(points + n, o->Ft, sizeof(double) * n);
+            memcpy(points + 2 * n, o->alpha, sizeof(double) * n);
+            memcpy(points + 3 * n, o->phi, sizeof(double) * n);
+        }
+    } else {
+        out[0] = o->force[0]; out[1] = o->force[1]; out[2] = o->force[2];
+        out[3] = o->iters_done;
+        out[4] = o->iters_done > 0 ? o->resid[o->iters_done - 1] : 0.0;
+        if (points) memcpy(points, o->resid, sizeof(double) * o->niter);
+    }
+    return 0;
+}
+
+/* Mass, momentum (3) and kinetic energy, summed over interior cells with
+ * the cell volumes, in FP64, in x-fastest cell order. */
+void og_diagnostics(const og_grid *g, double out[5])
+{
+    long np = g->np;
+    /* compensated (Neumaier) summation: s holds the sums, c the lost parts */
+    double s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                long ic = IDX(g, i, j, k);
+                double vol = g->h[0][G + i] * g->h[1][G + j] * g->h[2][G + k];
+                double r = g->W[ic], mx = g->W[np + ic], my = g->W[2 * np + ic], mz = g->W[3 * np + ic];
+                double x[5] = {r * vol, mx * vol, my * vol, mz * vol,
+                               0.5 * (mx * mx + my * my + mz * mz) / r * vol};
+                for (int q = 0; q < 5; ++q) {
+                    double t = s[q] + x[q];
+                    if (fabs(s[q]) >= fabs(x[q])) c[q] += (s[q] - t) + x[q];
+                    else c[q] += (x[q] - t) + s[q];
+                    s[q] = t;
+                }
+            }
+    for (int q = 0; q < 5; ++q) out[q] = s[q] + c[q];
+}
+
+void og_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int og_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Throughput of the S2O4 gas-kinetic step with ALM + IBM forcing on GB300.
+
+One step = one full two-stage fourth-order step of the high-order GKS on the
+whole grid (ghost fill, reconstruction, flux and update of both stages, the
+CFL time step) followed by the actuator-line and immersed-boundary forcing.
+The default workload is the rotor plus IBM tower and nacelle on a
+384 x 256 x 256 grid in FP32 with compensated state; FP64 is timed on the
+same grid for a few steps. Metric: MLUPS = cells x steps / seconds.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+For N > 1 launch one process per GPU with torch.distributed.run; each rank
+runs an independent replica (the method is not sharded here), value is the
+sum over ranks (weak scaling). ``--impl reference`` times the CPU oracle on
+a bounded window of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_11102_gb300 import workloads as WL  # noqa: E402
+
+# FP32 operations per face in the source of the two face kernels (adds,
+# multiplies, FMA = 2, one per division/transcendental call), counted per
+# face of the face box each launch processes.
+FLOPS = {
+    # WENO5 on 4 variables x 2 sides (40 each), half-space equilibrium (~40
+    # plus 2 erf, 2 exp, 2 expm1), normal slope (4 x 5)
+    "face_eq": 4 * 2 * 40 + 46 + 20,
+    # t1 pass (4 x (25 + 17) per row), t2 pass (2 x 4 x 63), 4 fluxes, average
+    "face_flux_stage1": 168 + 504 + 4 * 118 + 8,
+    "face_flux_stage2": 168 + 504 + 4 * 100 + 4,
+}
+SM_COUNT, FP32_LANES = 152, 128
+BYTES_PER_CELL_STEP = {"fp32c": 160, "fp64": 192}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-i",
+                 str(gpu_index), "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(name):
+    if name == "alm-ibm":
+        return WL.alm_ibm_rotor((384, 256, 256))
+    if name == "alm":
+        return WL.alm_rotor((512, 192, 192))
+    if name == "channel":
+        return WL.channel((128, 128, 128))
+    if name == "tgv":
+        return WL.taylor_green_3d(32)
+    if name == "tgv192":
+        return WL.taylor_green_3d(192)
+    raise ValueError(name)
+
+
+def window(w, lo, size):
+    """Sub-grid of a workload at the same spacing (cells lo..lo+size per axis),
+    same boundary kinds, rotor and bodies, initial state cut from state0."""
+    faces = [w.faces[a][lo[a]:lo[a] + size[a] + 1].copy() for a in range(3)]
+    Q = w.state0[:, lo[2]:lo[2] + size[2], lo[1]:lo[1] + size[1], lo[0]:lo[0] + size[0]].copy()
+    sub = WL.Workload(w.name + "-window", tuple(size), faces, w.mach, w.u_ref, w.mu, list(w.bc), cfl=w.cfl,
+                      dt_fixed=w.dt_fixed, inflow=w.inflow, body_force=w.body_force, rho_ref=w.rho_ref,
+                      state0=Q, rotors=list(w.rotors), bodies=list(w.bodies), steps=w.steps)
+    return sub
+
+
+def oracle_sample(w):
+    """Bounded sample of the workload for the CPU oracle: a window of the grid
+    around the rotor at the full resolution."""
+    n = w.n
+    size = (min(16, n[0]), min(80, n[1]), min(80, n[2]))
+    if w.rotors:
+        hub = w.rotors[0].hub
+        lo = [int((hub[a] - w.faces[a][0]) / (w.faces[a][1] - w.faces[a][0])) - size[a] // 2 for a in range(3)]
+    else:
+        lo = [(n[a] - size[a]) // 2 for a in range(3)]
+    lo = [max(0, min(lo[a], n[a] - size[a])) for a in range(3)]
+    return window(w, lo, size), lo
+
+
+def oracle_grid(w):
+    import oracle
+    o = oracle.OracleGrid(w.n, w.faces, w.mach, w.u_ref, w.mu, w.bc, cfl=w.cfl, dt_fixed=w.dt_fixed)
+    o.set_inflow(*w.inflow)
+    o.set_body_force(*w.body_force)
+    for r in w.rotors:
+        o.add_rotor(r.n_blades, r.r, r.chord, r.twist, r.width, r.hub, r.omega, r.azimuth0, r.radius, r.eps,
+                    r.rho_inf, r.u_inf_ref, r.correction)
+    for b in w.bodies:
+        o.add_body(b.xyz, b.dS, b.eps, vel=b.vel, niter=b.niter, tol=b.tol)
+    o.set_state(w.state0)
+    return o
+
+
+def time_oracle(w, steps, warmup):
+    import oracle
+    sample, lo = oracle_sample(w)
+    o = oracle_grid(sample)
+    for _ in range(warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = sample.cells * steps / dt / 1e6
+    desc = ("window of %dx%dx%d cells (origin cell %s) of the %s grid at the same spacing, same "
+            "boundary kinds, rotor and bodies; %d step(s) after %d warm-up, FP64 oracle"
+            % (sample.n + (tuple(lo), w.name, steps, warmup)))
+    return mlups, dt, oracle.get_threads(), desc
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("gks_stencil.cu", "gks_forcing.cu", "gks_api.cu", "gks_internal.h"):
+        with open(os.path.join(ROOT, "paper_2603_11102_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel, precision):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == precision and parts[3] == cur:
+            return float(parts[2])
+    return None
+
+
+def face_counts(n):
+    out = []
+    for d in range(3):
+        t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+        out.append({"eq": (n[d] + 1) * (n[t1] + 4) * (n[t2] + 4), "flux": (n[d] + 1) * n[t1] * n[t2]})
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2603_11102_gb300 import build, gks
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload)
+    peaks, peak_kind = load_peaks()
+    g = gks.Grid.from_workload(w, precision=args.precision, device=dev)
+    for _ in range(args.warmup):
+        g.step(1)
+    stream = g.stream
+    sampler = ClockSampler(local) if rank == 0 else None
+    g.profile_enable(timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    ms = max_over_ranks(ms, world, dev)
+    cells = w.cells
+    value = world * cells * args.steps / (ms / 1e3) / 1e6
+    ms_step = ms / args.steps
+
+    # roofline of the dominant kernel group
+    kms = prof["ms"]
+    top = max(kms, key=kms.get)
+    fc = face_counts(w.n)
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12 if args.precision == "fp32c" else 1.25
+    if top == "face_flux":
+        flops = args.steps * sum(fc[d]["flux"] * (FLOPS["face_flux_stage1"] + FLOPS["face_flux_stage2"])
+                                 for d in range(3))
+    elif top == "face_eq":
+        flops = args.steps * 2 * sum(fc[d]["eq"] * FLOPS["face_eq"] for d in range(3))
+    else:
+        flops = None
+    achieved = flops / (kms[top] / 1e3) / 1e12 if flops else None
+    traffic = read_traffic(top, args.precision)
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
+                "peak_source": ("FP32 lanes 152 x 128 x 2 x %.0f MHz (max SM clock of %s peaks)"
+                                % (clock_mhz, peak_kind)) if args.precision == "fp32c"
+                else "nominal GB300 FP64 1.25 TFLOP/s",
+                "launches": prof["launches"][top], "avg_launch_ms": kms[top] / max(1, prof["launches"][top])}
+    hbm_ach = cells * BYTES_PER_CELL_STEP[args.precision] * args.steps / (ms / 1e3) / 1e9
+    hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": hbm_ach / peaks["hbm_gbs"], "bytes_per_cell_step": BYTES_PER_CELL_STEP[args.precision],
+           "peak_source": peak_kind}
+    share = {k: round(v / sum(kms.values()), 4) for k, v in kms.items() if v > 0}
+
+    # end to end through the C ABI with host buffers: per step, upload the
+    # state from page-locked memory, step, read the rotor loads back
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(np.ascontiguousarray(w.state0.reshape(-1))).pin_memory()
+        ke = max(1, min(args.steps, args.e2e_steps))
+        out_bytes = 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            g.set_state_pinned(host)
+            g.step(1)
+            f = g.forces(0) if g.objects else None
+            out_bytes = 224 + (8 * 4 * f["Fx"].size if f else 0)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": world * cells * ke / te / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(host.numel() * 8),
+               "d2h_bytes_per_step": int(out_bytes), "steps": ke}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
+    fp64 = None
+    if args.precision == "fp32c" and not args.no_fp64:
+        g64 = gks.Grid.from_workload(w, precision="fp64", device=dev)
+        g64.step(1)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g64.stream)
+        g64.step(args.fp64_steps)
+        b.record(g64.stream)
+        torch.cuda.synchronize(dev)
+        ms64 = max_over_ranks(a.elapsed_time(b), world, dev)
+        fp64 = {"value": world * cells * args.fp64_steps / (ms64 / 1e3) / 1e6, "unit": "MLUPS",
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+        g64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        mlups, secs, cores, desc = time_oracle(w, args.cpu_steps, 0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    line = {"metric": "GKS MLUPS (S2O4 step with ALM+IBM forcing)", "value": value, "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": cells,
+                       "precision": "fp32-compensated" if args.precision == "fp32c" else "fp64",
+                       "rotor_points": sum(r.n_blades * len(r.r) for r in w.rotors),
+                       "ib_points": sum(len(b.dS) for b in w.bodies),
+                       "l2": "inputs larger than L2 (state %.0f MB per replica)" % (
+                           cells * (32 if args.precision == "fp32c" else 32) / 1e6),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline, "hbm_step": hbm, "kernel_share": share, "cpu_baseline": cpu,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle as it stands, on a bounded window of the workload; each
+    timed step is one oracle step of the window."""
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    mlups, secs, cores, desc = time_oracle(w, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": "GKS MLUPS (S2O4 step with ALM+IBM forcing)", "value": mlups,
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.cells, "precision": "fp64 (oracle)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="alm-ibm", choices=["alm-ibm", "alm", "channel", "tgv", "tgv192"])
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * gks_api.h -- C ABI of the GB300 (sm_103a) library libgks.so: one two-stage
+ * fourth-order (S2O4) step of the high-order gas-kinetic scheme (GKS) for 3D
+ * weakly compressible isothermal flow on a structured grid, with actuator-line
+ * (ALM) and immersed-boundary (IBM) body forcing.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: GKS_OK (0) or a negative error
+ *     code below. gks_last_error(g) returns a message for the last failure on
+ *     a grid (a static string for calls without a grid).
+ *   - Host arrays passed in are copied during the call; the library keeps no
+ *     pointer to them.
+ *   - Device memory for the state and the work space is owned by the caller
+ *     (for example torch tensors): the library never frees it, and it must
+ *     outlive the grid. The library owns only the small device buffers it
+ *     allocates for actuator lines and immersed bodies (freed by
+ *     gks_destroy_grid); a time step allocates nothing.
+ *   - Work is enqueued on the CUDA stream given in the grid description (NULL
+ *     = the legacy default stream). Calls that return results to the host
+ *     synchronise that stream.
+ *   - Calls on one grid are not thread safe.
+ *
+ * Citations name the paper (Huo, Pan, Cao et al., "High-order gas-kinetic
+ * scheme for numerical simulations of wind turbine with nacelle and tower
+ * using ALM and IBM") by section, equation or appendix.
+ */
+#ifndef GKS_API_H
+#define GKS_API_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GKS_OK 0
+#define GKS_ERR_ARG (-1)       /* invalid argument or handle                        */
+#define GKS_ERR_CUDA (-2)      /* a CUDA runtime call failed                        */
+#define GKS_ERR_NONFINITE (-3) /* a non-finite value appeared in the updated state  */
+#define GKS_ERR_CFL (-4)       /* fixed time step above the CFL limit given        */
+#define GKS_ERR_STATE (-5)     /* call not allowed in the current state             */
+#define GKS_ERR_RANGE (-6)     /* actuator point outside the sampled interior       */
+
+#define GKS_MAX_BLADES 8
+
+/* Arithmetic of the step. GKS_FP64: everything in FP64. GKS_FP32C:
+ * reconstruction and flux in FP32 on density perturbations rho - rho_ref,
+ * the conserved state carried as compensated FP32 pairs (hi + lo) updated
+ * with an error-free two-sum; global reductions and rotor loads summed in
+ * FP64. */
+typedef enum { GKS_FP64 = 0, GKS_FP32C = 1 } gks_precision;
+
+/* Boundary kinds (Sec. 4): periodic; no-slip isothermal wall (mirror, all
+ * momenta negated); slip / symmetry wall (mirror, normal momentum negated);
+ * inflow with prescribed velocity and density from the outgoing isothermal
+ * Riemann invariant U -/+ C ln rho; extrapolation (zero-gradient) outflow. */
+typedef enum {
+    GKS_BC_PERIODIC = 0,
+    GKS_BC_NOSLIP = 1,
+    GKS_BC_SLIP = 2,
+    GKS_BC_INFLOW = 3,
+    GKS_BC_OUTFLOW = 4
+} gks_bc;
+
+typedef struct gks_grid gks_grid;
+
+/* Grid description (Sec. 2; Sec. 4 for the boundary kinds).
+ *   n[d]       cells along axis d (x, y, z). >= 3 for non-periodic axes, >= 1
+ *              for periodic ones (n = 1 collapses an axis).
+ *   faces[d]   host array of n[d]+1 strictly increasing face coordinates
+ *              (uniform or stretched; reconstruction is done in index space
+ *              and derivatives use the local cell widths).
+ *   mach,u_ref lambda = mach^2 / (2 u_ref^2) of the isothermal Maxwellian
+ *              (Sec. 2); sound speed C = sqrt(1 / (2 lambda)).
+ *   mu         dynamic viscosity; collision time tau = mu / p, p = rho/(2 lambda).
+ *   bc[d][s]   boundary kind at the low (s=0) and high (s=1) end of axis d;
+ *              periodic must be set on both ends or neither.
+ *   precision  gks_precision.
+ *   cfl        CFL number of Sec. 2: dt = cfl min(dx,dy,dz) / (|U|max + C).
+ *   dt_fixed   > 0: use this time step instead; cfl then is the largest CFL
+ *              number allowed (GKS_ERR_CFL above it; cfl <= 0 disables).
+ *   rho_ref    reference density of the FP32C perturbation form (> 0); not
+ *              used by GKS_FP64.
+ *   stream     cudaStream_t (as void*) on which every call enqueues work. */
+typedef struct {
+    int n[3];
+    const double *faces[3];
+    double mach, u_ref, mu;
+    int bc[3][2];
+    int precision;
+    double cfl, dt_fixed;
+    double rho_ref;
+    void *stream;
+} gks_grid_desc;
+
+/* Bytes of device memory the caller must provide for the state and for the
+ * work space of a grid with this description. Both buffers must be 256-byte
+ * aligned. Returns GKS_ERR_ARG for an invalid description. */
+int gks_workspace_bytes(const gks_grid_desc *desc, size_t *state_bytes, size_t *work_bytes);
+
+/* Create a grid over caller-owned device buffers d_state and d_work of the
+ * sizes returned by gks_workspace_bytes. The state is set to rest
+ * (rho = 1, momentum 0), the time to 0. *out receives the handle. */
+int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_grid **out);
+
+/* Release the handle and the library-owned device buffers (not d_state or
+ * d_work). Synchronises the grid's stream first. */
+int gks_destroy_grid(gks_grid *g);
+
+/* Message for the last failure on g (or for a failure without a grid). */
+const char *gks_last_error(const gks_grid *g);
+
+/* Change the stream used by subsequent calls. */
+int gks_set_stream(gks_grid *g, void *stream);
+
+/* Set / get the conserved state (rho, rho U, rho V, rho W) of the interior
+ * cells from / to a host FP64 array of 4 * N values, component-major, x
+ * fastest then y then z (N = n0 n1 n2). Page-locked host memory makes the
+ * copy asynchronous for gks_set_state; gks_get_state synchronises. For
+ * GKS_FP32C the value is split into hi = fl32(q), lo = fl32(q - hi). */
+int gks_set_state(gks_grid *g, const double *h_state);
+int gks_get_state(gks_grid *g, double *h_state);
+
+/* Inflow state used by GKS_BC_INFLOW faces: density (the ghost density is
+ * set from the Riemann invariant; this value is the reference of the
+ * boundary) and the prescribed velocity. Sec. 4.3. */
+int gks_set_inflow(gks_grid *g, double rho, double u, double v, double w);
+
+/* Constant body force per unit volume added to the momentum after each S2O4
+ * update (channel driving force of Sec. 4.1: rho U += dt f). */
+int gks_set_body_force(gks_grid *g, double fx, double fy, double fz);
+
+/* Actuator-line rotor (Sec. 3.1). The rotor axis is +x; blade b's azimuth at
+ * time t is azimuth0 + omega t + 2 pi b / n_blades, its points sit at
+ * hub + r (0, cos th, sin th) and move along e_th = (0, -sin th, cos th).
+ * Per point (host arrays of n_pts, copied): radius r, chord, twist (rad) and
+ * element width. Loads use the synthetic polar C_L = clip(2 pi sin a, +-1.4),
+ * C_D = 0.01 + 0.02 a^2, L and D = 1/2 rho_inf c w C |U_rel|^2 (Eq.
+ * (axial-tangential)), F_x = L cos phi + D sin phi, F_th = L sin phi -
+ * D cos phi, and are projected with the Gaussian of Eq. (Gaussian) cut at
+ * 3 eps. correction != 0 applies the free-stream velocity correction of
+ * Sec. 3.1 once, with C_D of the uncorrected angle. radius and u_inf_ref
+ * normalise C_P and C_T (Sec. 4.4.1). All axes must be uniform. */
+typedef struct {
+    int n_blades, n_pts;
+    double hub[3];
+    double omega, azimuth0, radius, eps;
+    double rho_inf, u_inf_ref;
+    const double *r, *chord, *twist, *width;
+    int correction;
+} gks_rotor_desc;
+
+/* Add a rotor; *id receives its object id. Not allowed after the first step
+ * (GKS_ERR_STATE). Allocates small library-owned device buffers. */
+int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *desc, int *id);
+
+/* Per-point force scales s (host array of n_blades * n_pts, blade-major)
+ * multiplying every point force of rotor id; 1 by default. */
+int gks_set_force_scales(gks_grid *g, int id, const double *h_scales);
+
+/* Add a stationary or moving immersed body (Sec. 3.2) of n Lagrangian
+ * points: xyz (3n host values, point-major), surface element areas dS (n),
+ * point velocities vel (3n, or NULL for a stationary body), the kernel width
+ * eps of the truncated Gaussian used both ways, the number of direct-forcing
+ * iterations niter (>= 1) and a residual tolerance tol (0 = always niter
+ * iterations). V_p = Delta dS with Delta = (dx dy dz)^(1/3). The cell fields
+ * Vbar, vbar and phi = min(Vbar/|Omega|, 1) are computed once here. Kernel
+ * supports are truncated to interior cells. All axes must be uniform. */
+int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, const double *vel,
+                      double eps, int niter, double tol, int *id);
+
+/* Advance nsteps S2O4 steps (Sec. 2; forcing after each update, Sec. 3.3:
+ * body force, rotors in the order added, then bodies in the order added).
+ * Synchronises the stream at the end and reports GKS_ERR_NONFINITE,
+ * GKS_ERR_CFL or GKS_ERR_RANGE raised on the device. t_out (may be NULL)
+ * receives the time after the last step. */
+int gks_step(gks_grid *g, int nsteps, double *t_out);
+
+/* Current time and the last time step (synchronises). */
+int gks_get_time(gks_grid *g, double *t, double *dt_last);
+int gks_set_time(gks_grid *g, double t);
+
+/* Loads of object id from the last step (synchronises).
+ * Rotor: thrust and torque per blade, power = omega sum(torque),
+ *   C_P = 2 omega T' / (rho pi R^2 U^3), C_T = 2 D' / (rho pi R^2 U^2)
+ *   (Sec. 4.4.1), summed in FP64. h_points (may be NULL) receives 4 arrays of
+ *   n_blades * n_pts: F_x, F_th, angle of attack, flow angle.
+ * Body: the force on the structure (minus the summed cell forces of Eq.
+ *   (force-ibm)), the iterations done and the last residual
+ *   max_p |v_p - sum W U|. h_points (may be NULL) receives the residual of
+ *   each iteration (niter values; zero where not evaluated). */
+typedef struct {
+    int kind; /* 0 rotor, 1 body */
+    int n_blades;
+    double thrust[GKS_MAX_BLADES], torque[GKS_MAX_BLADES];
+    double power, cp, ct;
+    double body_force[3];
+    int iters;
+    double residual;
+} gks_forces_out;
+int gks_forces(gks_grid *g, int id, gks_forces_out *out, double *h_points);
+
+/* Mass, momentum (3) and kinetic energy summed over interior cells with
+ * their volumes, in FP64 (synchronises). */
+int gks_diagnostics(gks_grid *g, double out[5]);
+
+/* Checkpoint: the interior state in its stored precision, the time and the
+ * step count. gks_checkpoint_bytes gives the blob size. */
+int gks_checkpoint_bytes(gks_grid *g, size_t *bytes);
+int gks_save_state(gks_grid *g, void *h_blob, size_t bytes);
+int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes);
+
+/* Layout of the caller-owned state buffer: out[0..2] padded extents (n + 6),
+ * out[3] element bytes (8 for FP64, 4 for FP32C), out[4] number of arrays
+ * (4 for FP64: rho, rho U, rho V, rho W; 8 for FP32C: the 4 hi arrays then
+ * the 4 lo arrays), out[5] element stride between arrays, out[6] ghost width
+ * (3). Interior cell (i,j,k) of array a is element
+ * a*out[5] + (i+3) + out[0]*((j+3) + out[1]*(k+3)). */
+int gks_state_layout(const gks_grid *g, long out[7]);
+
+/* Kernel accounting of the library's own kernels. Every kernel launch is
+ * counted per group (0 prep, 1 ghost, 2 cfl, 3 face_eq, 4 face_flux,
+ * 5 update, 6 alm, 7 ibm, 8 misc); with timing enabled each launch is also
+ * bracketed by CUDA events on the grid's stream and its duration summed.
+ * gks_profile_enable sets timing on or off and clears the counters;
+ * gks_profile_read synchronises, fills out and clears the counters. */
+#define GKS_NUM_KERNEL_GROUPS 9
+typedef struct {
+    long launches[GKS_NUM_KERNEL_GROUPS];
+    double ms[GKS_NUM_KERNEL_GROUPS];
+    long total_launches;
+} gks_profile_out;
+int gks_profile_enable(gks_grid *g, int timing_on);
+int gks_profile_read(gks_grid *g, gks_profile_out *out);
+const char *gks_kernel_group_name(int group);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKS_API_H */

@@ -14,6 +14,6 @@ __all__ = ["workloads", "gks"]
 
 def __getattr__(name):
     if name == "gks":
-        from . import gks
-        return gks
+        import importlib
+        return importlib.import_module(__name__ + ".gks")
     raise AttributeError(name)

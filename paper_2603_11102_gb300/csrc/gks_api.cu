@@ -1,0 +1,746 @@
+// gks_api.cu -- host side of the C ABI declared in include/gks_api.h: grid
+// validation, carving of the caller-owned buffers, geometry tables, object
+// set-up, and the launch sequence of one S2O4 step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gks_internal.h"
+
+using namespace gks;
+
+struct Profiler {
+    bool timing = false;
+    std::vector<cudaEvent_t> pool;
+    size_t next = 0;
+    struct Rec {
+        int group;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t open_ev = nullptr;
+    long launches[K_NGROUPS] = {0};
+};
+
+struct gks_grid {
+    Ctx c;
+    Profiler prof;
+    std::string err;
+    std::vector<RotorDev> rotors;
+    std::vector<BodyDev> bodies;
+    std::vector<int> obj_kind, obj_index;
+    std::vector<void *> owned;
+    double *d_diag = nullptr;
+    long nstep = 0;
+    bool stepped = false;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(gks_grid *g, int code, const std::string &msg)
+{
+    if (g)
+        g->err = msg;
+    else
+        g_err = msg;
+    return code;
+}
+
+int cuda_check(gks_grid *g, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GKS_OK;
+    return fail(g, GKS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Layout {
+    size_t state = 0, work = 0;
+    size_t o_wk0 = 0, o_wk1 = 0, o_p = 0, o_fq = 0, o_ff[3] = {0, 0, 0};
+    size_t o_ih[3], o_ihf[3], o_h64[3], o_part = 0, o_scal = 0, o_diag = 0;
+    long np = 0, nfq = 0, nff[3] = {0, 0, 0};
+    int P[3];
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int validate(const gks_grid_desc *d, std::string *msg)
+{
+    if (!d) { *msg = "null grid description"; return GKS_ERR_ARG; }
+    if (d->precision != GKS_FP64 && d->precision != GKS_FP32C) { *msg = "bad precision"; return GKS_ERR_ARG; }
+    for (int a = 0; a < 3; ++a) {
+        const bool p0 = d->bc[a][0] == GKS_BC_PERIODIC, p1 = d->bc[a][1] == GKS_BC_PERIODIC;
+        for (int s = 0; s < 2; ++s)
+            if (d->bc[a][s] < GKS_BC_PERIODIC || d->bc[a][s] > GKS_BC_OUTFLOW) { *msg = "bad boundary kind"; return GKS_ERR_ARG; }
+        if (p0 != p1) { *msg = "periodic must be set on both ends of an axis"; return GKS_ERR_ARG; }
+        if (d->n[a] < (p0 ? 1 : 3)) { *msg = "too few cells on an axis"; return GKS_ERR_ARG; }
+        if (d->n[a] > (1 << 24)) { *msg = "too many cells on an axis"; return GKS_ERR_ARG; }
+        if (!d->faces[a]) { *msg = "null face array"; return GKS_ERR_ARG; }
+        for (int i = 0; i < d->n[a]; ++i)
+            if (!(d->faces[a][i + 1] > d->faces[a][i])) { *msg = "faces must increase"; return GKS_ERR_ARG; }
+    }
+    if (!(d->mach > 0.0) || !(d->u_ref > 0.0) || !(d->mu >= 0.0)) { *msg = "bad mach, u_ref or mu"; return GKS_ERR_ARG; }
+    if (!(d->dt_fixed > 0.0) && !(d->cfl > 0.0)) { *msg = "need cfl > 0 or dt_fixed > 0"; return GKS_ERR_ARG; }
+    if (d->precision == GKS_FP32C && !(d->rho_ref > 0.0)) { *msg = "rho_ref must be > 0"; return GKS_ERR_ARG; }
+    return GKS_OK;
+}
+
+void plan(const gks_grid_desc *d, Layout *L)
+{
+    const size_t R = d->precision == GKS_FP64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) L->P[a] = d->n[a] + 2 * G;
+    const long pn = (long)L->P[0] * L->P[1] * L->P[2];
+    L->np = (pn + 63) / 64 * 64;
+    L->state = (d->precision == GKS_FP64 ? 4 : 8) * (size_t)L->np * R;
+    L->nfq = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+        const long nfq = (long)(d->n[a] + 1) * (d->n[t1] + 4) * (d->n[t2] + 4);
+        if (nfq > L->nfq) L->nfq = nfq;
+        L->nff[a] = (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
+    }
+    size_t o = 0;
+    L->o_wk0 = o;
+    if (d->precision == GKS_FP32C) o = align256(o + 4 * (size_t)L->np * 4);
+    L->o_wk1 = o; o = align256(o + 4 * (size_t)L->np * R);
+    L->o_p = o; o = align256(o + (d->precision == GKS_FP64 ? 4 : 8) * (size_t)L->np * R);
+    L->o_fq = o; o = align256(o + 8 * (size_t)L->nfq * R);
+    for (int a = 0; a < 3; ++a) { L->o_ff[a] = o; o = align256(o + 8 * (size_t)L->nff[a] * R); }
+    for (int a = 0; a < 3; ++a) { L->o_ih[a] = o; o = align256(o + (size_t)L->P[a] * R); }
+    for (int a = 0; a < 3; ++a) { L->o_ihf[a] = o; o = align256(o + (size_t)(d->n[a] + 1) * R); }
+    for (int a = 0; a < 3; ++a) { L->o_h64[a] = o; o = align256(o + (size_t)L->P[a] * 8); }
+    L->o_part = o; o = align256(o + (size_t)kMaxPartials * 8 * 8);
+    L->o_scal = o; o = align256(o + sizeof(Scalars));
+    L->o_diag = o; o = align256(o + 8 * 8);
+    L->work = o;
+}
+
+// Padded cell widths of one axis (ghosts wrap or mirror like the state).
+std::vector<double> padded_widths(const gks_grid_desc *d, int a)
+{
+    const int n = d->n[a];
+    std::vector<double> h(n + 2 * G);
+    for (int i = 0; i < n; ++i) h[i + G] = d->faces[a][i + 1] - d->faces[a][i];
+    for (int l = 1; l <= G; ++l) {
+        if (d->bc[a][0] == GKS_BC_PERIODIC) {
+            h[G - l] = h[G + (((-l) % n) + n) % n];
+            h[G + n - 1 + l] = h[G + (n - 1 + l) % n];
+        } else {
+            h[G - l] = h[G + l - 1];
+            h[G + n - 1 + l] = h[G + n - l];
+        }
+    }
+    return h;
+}
+
+template <typename R>
+int upload(gks_grid *g, void *dst, const std::vector<double> &v)
+{
+    std::vector<R> t(v.size());
+    for (size_t i = 0; i < v.size(); ++i) t[i] = (R)v[i];
+    return cuda_check(g, cudaMemcpyAsync(dst, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice, g->c.stream),
+                      "copy geometry");
+}
+
+int check_launch(gks_grid *g, const char *what)
+{
+    return cuda_check(g, cudaGetLastError(), what);
+}
+
+int sync(gks_grid *g) { return cuda_check(g, cudaStreamSynchronize(g->c.stream), "stream synchronize"); }
+
+int read_scalars(gks_grid *g, Scalars *s)
+{
+    int rc = cuda_check(g, cudaMemcpyAsync(s, g->c.scal, sizeof(Scalars), cudaMemcpyDeviceToHost, g->c.stream),
+                        "read scalars");
+    if (rc) return rc;
+    return sync(g);
+}
+
+int device_alloc(gks_grid *g, void **p, size_t bytes)
+{
+    int rc = cuda_check(g, cudaMalloc(p, bytes), "allocate object buffers");
+    if (rc == GKS_OK) g->owned.push_back(*p);
+    return rc;
+}
+
+cudaEvent_t prof_event(Profiler &p)
+{
+    if (p.next == p.pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        p.pool.push_back(e);
+    }
+    return p.pool[p.next++];
+}
+
+void prof_mark(void *ctx, int group, int begin)
+{
+    gks_grid *g = (gks_grid *)ctx;
+    Profiler &p = g->prof;
+    if (begin) {
+        p.launches[group]++;
+        if (p.timing) {
+            p.open_ev = prof_event(p);
+            cudaEventRecord(p.open_ev, g->c.stream);
+        }
+    } else if (p.timing) {
+        cudaEvent_t e = prof_event(p);
+        cudaEventRecord(e, g->c.stream);
+        p.recs.push_back({group, p.open_ev, e});
+    }
+}
+
+int cell_range(const Ctx &c, int a, double lo, double hi, int out[2])
+{
+    long i0 = (long)floor((lo - c.x0[a]) / c.hu[a] - 0.5) - 1;
+    long i1 = (long)ceil((hi - c.x0[a]) / c.hu[a] - 0.5) + 1;
+    if (i0 < 0) i0 = 0;
+    if (i1 > c.n[a] - 1) i1 = c.n[a] - 1;
+    if (i1 < i0) return -1;
+    out[0] = (int)i0;
+    out[1] = (int)i1;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gks_last_error(const gks_grid *g) { return g ? g->err.c_str() : g_err.c_str(); }
+
+int gks_workspace_bytes(const gks_grid_desc *desc, size_t *state_bytes, size_t *work_bytes)
+{
+    std::string msg;
+    int rc = validate(desc, &msg);
+    if (rc) return fail(nullptr, rc, msg);
+    if (!state_bytes || !work_bytes) return fail(nullptr, GKS_ERR_ARG, "null output");
+    Layout L;
+    plan(desc, &L);
+    *state_bytes = L.state;
+    *work_bytes = L.work;
+    return GKS_OK;
+}
+
+int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_grid **out)
+{
+    std::string msg;
+    int rc = validate(desc, &msg);
+    if (rc) return fail(nullptr, rc, msg);
+    if (!out || !d_state || !d_work) return fail(nullptr, GKS_ERR_ARG, "null buffer or output");
+    if (((uintptr_t)d_state & 255) || ((uintptr_t)d_work & 255))
+        return fail(nullptr, GKS_ERR_ARG, "buffers must be 256-byte aligned");
+    Layout L;
+    plan(desc, &L);
+    gks_grid *g = new gks_grid();
+    Ctx &c = g->c;
+    c.prec = desc->precision;
+    for (int a = 0; a < 3; ++a) {
+        c.n[a] = desc->n[a];
+        c.P[a] = L.P[a];
+        c.bc[a][0] = desc->bc[a][0];
+        c.bc[a][1] = desc->bc[a][1];
+    }
+    c.np = L.np;
+    c.ncell = (long)c.n[0] * c.n[1] * c.n[2];
+    c.lambda = desc->mach * desc->mach / (2.0 * desc->u_ref * desc->u_ref);
+    c.theta = 1.0 / (2.0 * c.lambda);
+    c.csound = sqrt(c.theta);
+    c.mu = desc->mu;
+    c.rho_ref = desc->precision == GKS_FP32C ? desc->rho_ref : 0.0;
+    c.off = c.rho_ref;
+    c.cfl = desc->cfl;
+    c.dt_fixed = desc->dt_fixed;
+    c.inflow[0] = 1.0;
+    c.inflow[1] = c.inflow[2] = c.inflow[3] = 0.0;
+    c.fbody[0] = c.fbody[1] = c.fbody[2] = 0.0;
+    c.stream = (cudaStream_t)desc->stream;
+    char *w = (char *)d_work;
+    c.state = d_state;
+    c.wk0 = c.prec == GKS_FP32C ? (void *)(w + L.o_wk0) : d_state;
+    c.wk1 = w + L.o_wk1;
+    c.pbuf = w + L.o_p;
+    c.fq = w + L.o_fq;
+    c.nfq = L.nfq;
+    for (int a = 0; a < 3; ++a) {
+        c.ff[a] = w + L.o_ff[a];
+        c.nff[a] = L.nff[a];
+        c.ih[a] = w + L.o_ih[a];
+        c.ihf[a] = w + L.o_ihf[a];
+        c.h64[a] = (double *)(w + L.o_h64[a]);
+    }
+    c.partials = (double *)(w + L.o_part);
+    c.scal = (Scalars *)(w + L.o_scal);
+    g->d_diag = (double *)(w + L.o_diag);
+    c.staging = (double *)c.ff[0];   // the face-flux buffers hold >= 4 N doubles
+    c.mark = prof_mark;
+    c.mark_ctx = g;
+
+    // geometry tables
+    c.hmin = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<double> h = padded_widths(desc, a);
+        std::vector<double> ih(h.size()), ihf(c.n[a] + 1);
+        for (size_t i = 0; i < h.size(); ++i) ih[i] = 1.0 / h[i];
+        for (int f = 0; f <= c.n[a]; ++f) ihf[f] = 1.0 / (0.5 * (h[G + f - 1] + h[G + f]));
+        for (int i = 0; i < c.n[a]; ++i) c.hmin = fmin(c.hmin, h[G + i]);
+        c.x0[a] = desc->faces[a][0];
+        c.hu[a] = h[G];
+        c.uniform[a] = 1;
+        for (int i = 0; i < c.n[a]; ++i)
+            if (fabs(h[G + i] - h[G]) > 1e-12 * fabs(h[G])) c.uniform[a] = 0;
+        if (c.prec == GKS_FP64) {
+            rc = upload<double>(g, c.ih[a], ih);
+            if (!rc) rc = upload<double>(g, c.ihf[a], ihf);
+        } else {
+            rc = upload<float>(g, c.ih[a], ih);
+            if (!rc) rc = upload<float>(g, c.ihf[a], ihf);
+        }
+        if (!rc) rc = upload<double>(g, c.h64[a], h);
+        if (rc) { msg = g->err; delete g; return fail(nullptr, rc, msg); }
+    }
+    rc = cuda_check(g, cudaMemsetAsync(c.scal, 0, sizeof(Scalars), c.stream), "clear scalars");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(c.state, 0, L.state, c.stream), "clear state");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w, 0, L.o_fq, c.stream), "clear work");
+    if (!rc) {
+        launch_fill_rest(c);
+        rc = check_launch(g, "fill state");
+    }
+    if (!rc) rc = sync(g);
+    if (rc) { msg = g->err; delete g; return fail(nullptr, rc, msg); }
+    *out = g;
+    return GKS_OK;
+}
+
+int gks_destroy_grid(gks_grid *g)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    cudaStreamSynchronize(g->c.stream);
+    for (void *p : g->owned) cudaFree(p);
+    for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+    delete g;
+    return GKS_OK;
+}
+
+int gks_set_stream(gks_grid *g, void *stream)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    g->c.stream = (cudaStream_t)stream;
+    return GKS_OK;
+}
+
+int gks_set_state(gks_grid *g, const double *h_state)
+{
+    if (!g || !h_state) return fail(g, GKS_ERR_ARG, "null argument");
+    int rc = cuda_check(g, cudaMemcpyAsync(g->c.staging, h_state, sizeof(double) * 4 * g->c.ncell,
+                                           cudaMemcpyHostToDevice, g->c.stream),
+                        "copy state to device");
+    if (rc) return rc;
+    launch_scatter_state(g->c, g->c.staging);
+    return check_launch(g, "scatter state");
+}
+
+int gks_get_state(gks_grid *g, double *h_state)
+{
+    if (!g || !h_state) return fail(g, GKS_ERR_ARG, "null argument");
+    launch_gather_state(g->c, g->c.staging);
+    int rc = check_launch(g, "gather state");
+    if (!rc)
+        rc = cuda_check(g, cudaMemcpyAsync(h_state, g->c.staging, sizeof(double) * 4 * g->c.ncell,
+                                           cudaMemcpyDeviceToHost, g->c.stream),
+                        "copy state to host");
+    if (!rc) rc = sync(g);
+    return rc;
+}
+
+int gks_set_inflow(gks_grid *g, double rho, double u, double v, double w)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    if (!(rho > 0.0)) return fail(g, GKS_ERR_ARG, "inflow density must be > 0");
+    g->c.inflow[0] = rho;
+    g->c.inflow[1] = u;
+    g->c.inflow[2] = v;
+    g->c.inflow[3] = w;
+    return GKS_OK;
+}
+
+int gks_set_body_force(gks_grid *g, double fx, double fy, double fz)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    g->c.fbody[0] = fx;
+    g->c.fbody[1] = fy;
+    g->c.fbody[2] = fz;
+    return GKS_OK;
+}
+
+int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
+{
+    if (!g || !d || !id) return fail(g, GKS_ERR_ARG, "null argument");
+    Ctx &c = g->c;
+    if (g->stepped) return fail(g, GKS_ERR_STATE, "objects must be added before the first step");
+    if (!(c.uniform[0] && c.uniform[1] && c.uniform[2])) return fail(g, GKS_ERR_ARG, "actuator lines need uniform axes");
+    if (d->n_blades < 1 || d->n_blades > GKS_MAX_BLADES || d->n_pts < 1 || !(d->eps > 0.0) || !d->r ||
+        !d->chord || !d->twist || !d->width || !(d->radius > 0.0) || !(d->u_inf_ref > 0.0) || !(d->rho_inf > 0.0))
+        return fail(g, GKS_ERR_ARG, "bad rotor description");
+    const int nb = d->n_blades, np = d->n_pts, npts = nb * np;
+    RotorDev r;
+    memset(&r, 0, sizeof(r));
+    r.nb = nb;
+    r.np = np;
+    r.correction = d->correction ? 1 : 0;
+    for (int a = 0; a < 3; ++a) r.hub[a] = d->hub[a];
+    r.omega = d->omega;
+    r.az0 = d->azimuth0;
+    r.radius = d->radius;
+    r.eps = d->eps;
+    r.rho_inf = d->rho_inf;
+    r.uref = d->u_inf_ref;
+    double rmax = 0.0;
+    for (int p = 0; p < np; ++p) rmax = fmax(rmax, fabs(d->r[p]));
+    const double cut = 3.0 * d->eps;
+    if (cell_range(c, 0, d->hub[0] - cut, d->hub[0] + cut, r.box[0]) ||
+        cell_range(c, 1, d->hub[1] - rmax - cut, d->hub[1] + rmax + cut, r.box[1]) ||
+        cell_range(c, 2, d->hub[2] - rmax - cut, d->hub[2] + rmax + cut, r.box[2]))
+        return fail(g, GKS_ERR_RANGE, "rotor outside the grid");
+    const size_t nd = 4 * (size_t)np + (size_t)npts + 3 * (size_t)npts + 4 * (size_t)npts + 2 * nb + 2 * nb + 3;
+    double *buf = nullptr;
+    int rc = device_alloc(g, (void **)&buf, nd * sizeof(double));
+    if (rc) return rc;
+    std::vector<double> host(nd, 0.0);
+    size_t o = 0;
+    r.r = buf + o; memcpy(&host[o], d->r, np * sizeof(double)); o += np;
+    r.chord = buf + o; memcpy(&host[o], d->chord, np * sizeof(double)); o += np;
+    r.twist = buf + o; memcpy(&host[o], d->twist, np * sizeof(double)); o += np;
+    r.width = buf + o; memcpy(&host[o], d->width, np * sizeof(double)); o += np;
+    r.scale = buf + o; for (int q = 0; q < npts; ++q) host[o + q] = 1.0; o += npts;
+    r.X = buf + o; o += 3 * (size_t)npts;
+    r.F = buf + o; o += 4 * (size_t)npts;
+    r.et = buf + o; o += 2 * nb;
+    r.out = buf + o;
+    rc = cuda_check(g, cudaMemcpyAsync(buf, host.data(), nd * sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                    "copy rotor");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    g->rotors.push_back(r);
+    g->obj_kind.push_back(0);
+    g->obj_index.push_back((int)g->rotors.size() - 1);
+    *id = (int)g->obj_kind.size() - 1;
+    return GKS_OK;
+}
+
+int gks_set_force_scales(gks_grid *g, int id, const double *h_scales)
+{
+    if (!g || !h_scales || id < 0 || id >= (int)g->obj_kind.size() || g->obj_kind[id] != 0)
+        return fail(g, GKS_ERR_ARG, "bad rotor id or scales");
+    const RotorDev &r = g->rotors[g->obj_index[id]];
+    return cuda_check(g, cudaMemcpyAsync(r.scale, h_scales, sizeof(double) * r.nb * r.np, cudaMemcpyHostToDevice,
+                                         g->c.stream),
+                      "copy force scales");
+}
+
+int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, const double *vel, double eps,
+                      int niter, double tol, int *id)
+{
+    if (!g || !xyz || !dS || !id) return fail(g, GKS_ERR_ARG, "null argument");
+    Ctx &c = g->c;
+    if (g->stepped) return fail(g, GKS_ERR_STATE, "objects must be added before the first step");
+    if (!(c.uniform[0] && c.uniform[1] && c.uniform[2])) return fail(g, GKS_ERR_ARG, "immersed bodies need uniform axes");
+    if (n < 1 || !(eps > 0.0) || niter < 1 || niter > 1000 || !(tol >= 0.0)) return fail(g, GKS_ERR_ARG, "bad body description");
+    BodyDev b;
+    memset(&b, 0, sizeof(b));
+    b.n = n;
+    b.niter = niter;
+    b.eps = eps;
+    b.tol = tol;
+    if (body_box(c, xyz, n, eps, b.box)) return fail(g, GKS_ERR_RANGE, "body outside the grid");
+    b.nbox = (long)(b.box[0][1] - b.box[0][0] + 1) * (b.box[1][1] - b.box[1][0] + 1) * (b.box[2][1] - b.box[2][0] + 1);
+    const size_t nd = 7 * (size_t)n + 8 * (size_t)b.nbox + 7 + niter;
+    double *buf = nullptr;
+    int rc = device_alloc(g, (void **)&buf, nd * sizeof(double));
+    if (rc) return rc;
+    std::vector<double> host(7 * (size_t)n, 0.0);
+    memcpy(&host[0], xyz, 3 * n * sizeof(double));
+    if (vel) memcpy(&host[3 * (size_t)n], vel, 3 * n * sizeof(double));
+    memcpy(&host[6 * (size_t)n], dS, n * sizeof(double));
+    b.xyz = buf;
+    b.vel = buf + 3 * (size_t)n;
+    b.dS = buf + 6 * (size_t)n;
+    b.Vbar = buf + 7 * (size_t)n;
+    b.vbar = b.Vbar + b.nbox;
+    b.phi = b.vbar + 3 * b.nbox;
+    b.fsum = b.phi + b.nbox;
+    b.out = b.fsum + 3 * b.nbox;
+    rc = cuda_check(g, cudaMemcpyAsync(buf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                    "copy body");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(b.Vbar, 0, (8 * (size_t)b.nbox + 7 + niter) * sizeof(double), c.stream),
+                             "clear body");
+    if (rc) return rc;
+    launch_body_precompute(c, b);
+    rc = check_launch(g, "body fields");
+    if (rc) return rc;
+    // CSR of the back-interpolation weights: count, scan on the host, fill
+    long *d_cnt = nullptr;
+    rc = device_alloc(g, (void **)&d_cnt, sizeof(long) * (n + 1));
+    if (rc) return rc;
+    launch_body_csr_count(c, b, d_cnt);
+    std::vector<long> cnt(n), off(n + 1, 0);
+    rc = check_launch(g, "count weights");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(long) * n, cudaMemcpyDeviceToHost, c.stream),
+                             "read counts");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    for (int p = 0; p < n; ++p) off[p + 1] = off[p] + cnt[p];
+    b.nnz = off[n];
+    b.csr_off = d_cnt;
+    char *cbuf = nullptr;
+    rc = device_alloc(g, (void **)&cbuf, (size_t)b.nnz * (sizeof(double) + sizeof(int)) + 3 * sizeof(double) * b.nbox + 64);
+    if (rc) return rc;
+    b.csr_w = (double *)cbuf;
+    b.Ubox = b.csr_w + b.nnz;
+    b.csr_cell = (int *)(b.Ubox + 3 * b.nbox);
+    rc = cuda_check(g, cudaMemcpyAsync(d_cnt, off.data(), sizeof(long) * (n + 1), cudaMemcpyHostToDevice, c.stream),
+                    "copy offsets");
+    if (rc) return rc;
+    launch_body_csr_fill(c, b);
+    rc = check_launch(g, "fill weights");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    g->bodies.push_back(b);
+    g->obj_kind.push_back(1);
+    g->obj_index.push_back((int)g->bodies.size() - 1);
+    *id = (int)g->obj_kind.size() - 1;
+    return GKS_OK;
+}
+
+int gks_step(gks_grid *g, int nsteps, double *t_out)
+{
+    if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
+    Ctx &c = g->c;
+    g->stepped = true;
+    for (int s = 0; s < nsteps; ++s) {
+        launch_prep(c);
+        launch_ghost(c, c.wk0);
+        launch_cfl(c);
+        launch_stage(c, 1);
+        launch_ghost(c, c.wk1);
+        launch_stage(c, 2);
+        for (size_t k = 0; k < g->obj_kind.size(); ++k)
+            if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
+        for (size_t k = 0; k < g->obj_kind.size(); ++k)
+            if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
+        launch_advance(c);
+        int rc = check_launch(g, "step");
+        if (rc) return rc;
+        g->nstep++;
+    }
+    Scalars sc;
+    int rc = read_scalars(g, &sc);
+    if (rc) return rc;
+    if (t_out) *t_out = sc.t;
+    if (sc.flags) {
+        int flags = 0;
+        cudaMemcpyAsync(&c.scal->flags, &flags, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+        sync(g);
+        if (sc.flags & FLAG_NONFINITE) return fail(g, GKS_ERR_NONFINITE, "non-finite value in the state");
+        if (sc.flags & FLAG_RANGE) return fail(g, GKS_ERR_RANGE, "actuator point outside the sampled interior");
+        if (sc.flags & FLAG_CFL) return fail(g, GKS_ERR_CFL, "fixed time step above the CFL limit");
+    }
+    return GKS_OK;
+}
+
+int gks_get_time(gks_grid *g, double *t, double *dt_last)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    Scalars sc;
+    int rc = read_scalars(g, &sc);
+    if (rc) return rc;
+    if (t) *t = sc.t;
+    if (dt_last) *dt_last = sc.dt;
+    return GKS_OK;
+}
+
+int gks_set_time(gks_grid *g, double t)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    int rc = cuda_check(g, cudaMemcpyAsync(&g->c.scal->t, &t, sizeof(double), cudaMemcpyHostToDevice, g->c.stream),
+                        "set time");
+    if (!rc) rc = sync(g);
+    return rc;
+}
+
+int gks_forces(gks_grid *g, int id, gks_forces_out *out, double *h_points)
+{
+    if (!g || !out || id < 0 || id >= (int)g->obj_kind.size()) return fail(g, GKS_ERR_ARG, "bad object id");
+    memset(out, 0, sizeof(*out));
+    int rc = sync(g);
+    if (rc) return rc;
+    if (g->obj_kind[id] == 0) {
+        const RotorDev &r = g->rotors[g->obj_index[id]];
+        std::vector<double> o(2 * r.nb + 3);
+        rc = cuda_check(g, cudaMemcpy(o.data(), r.out, o.size() * sizeof(double), cudaMemcpyDeviceToHost), "read loads");
+        if (rc) return rc;
+        out->kind = 0;
+        out->n_blades = r.nb;
+        for (int b = 0; b < r.nb; ++b) {
+            out->thrust[b] = o[b];
+            out->torque[b] = o[r.nb + b];
+        }
+        out->power = o[2 * r.nb];
+        out->cp = o[2 * r.nb + 1];
+        out->ct = o[2 * r.nb + 2];
+        if (h_points)
+            rc = cuda_check(g, cudaMemcpy(h_points, r.F, 4 * sizeof(double) * r.nb * r.np, cudaMemcpyDeviceToHost),
+                            "read point loads");
+        return rc;
+    }
+    const BodyDev &b = g->bodies[g->obj_index[id]];
+    std::vector<double> o(7 + b.niter);
+    rc = cuda_check(g, cudaMemcpy(o.data(), b.out, o.size() * sizeof(double), cudaMemcpyDeviceToHost), "read body force");
+    if (rc) return rc;
+    out->kind = 1;
+    for (int d = 0; d < 3; ++d) out->body_force[d] = o[d];
+    out->iters = (int)o[3];
+    out->residual = o[4];
+    if (h_points) memcpy(h_points, &o[7], sizeof(double) * b.niter);
+    return GKS_OK;
+}
+
+int gks_diagnostics(gks_grid *g, double out[5])
+{
+    if (!g || !out) return fail(g, GKS_ERR_ARG, "null argument");
+    launch_diagnostics(g->c, g->d_diag);
+    int rc = check_launch(g, "diagnostics");
+    if (!rc)
+        rc = cuda_check(g, cudaMemcpyAsync(out, g->d_diag, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->c.stream),
+                        "read diagnostics");
+    if (!rc) rc = sync(g);
+    return rc;
+}
+
+namespace {
+struct BlobHeader {
+    char magic[8];
+    int prec, n[3];
+    double t;
+    long nstep;
+    size_t payload;
+};
+size_t payload_bytes(const Ctx &c) { return (size_t)c.ncell * (c.prec == GKS_FP64 ? 4 * 8 : 8 * 4); }
+}  // namespace
+
+int gks_checkpoint_bytes(gks_grid *g, size_t *bytes)
+{
+    if (!g || !bytes) return fail(g, GKS_ERR_ARG, "null argument");
+    *bytes = sizeof(BlobHeader) + payload_bytes(g->c);
+    return GKS_OK;
+}
+
+int gks_save_state(gks_grid *g, void *h_blob, size_t bytes)
+{
+    if (!g || !h_blob) return fail(g, GKS_ERR_ARG, "null argument");
+    const size_t pb = payload_bytes(g->c);
+    if (bytes < sizeof(BlobHeader) + pb) return fail(g, GKS_ERR_ARG, "blob too small");
+    Scalars sc;
+    int rc = read_scalars(g, &sc);
+    if (rc) return rc;
+    BlobHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "GKSCKPT1", 8);
+    h.prec = g->c.prec;
+    for (int a = 0; a < 3; ++a) h.n[a] = g->c.n[a];
+    h.t = sc.t;
+    h.nstep = g->nstep;
+    h.payload = pb;
+    memcpy(h_blob, &h, sizeof(h));
+    launch_raw_copy(g->c, g->c.staging, 1);
+    rc = check_launch(g, "gather checkpoint");
+    if (!rc)
+        rc = cuda_check(g, cudaMemcpyAsync((char *)h_blob + sizeof(h), g->c.staging, pb, cudaMemcpyDeviceToHost, g->c.stream),
+                        "copy checkpoint");
+    if (!rc) rc = sync(g);
+    return rc;
+}
+
+int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes)
+{
+    if (!g || !h_blob || bytes < sizeof(BlobHeader)) return fail(g, GKS_ERR_ARG, "bad blob");
+    BlobHeader h;
+    memcpy(&h, h_blob, sizeof(h));
+    if (memcmp(h.magic, "GKSCKPT1", 8) != 0 || h.prec != g->c.prec || h.n[0] != g->c.n[0] || h.n[1] != g->c.n[1] ||
+        h.n[2] != g->c.n[2] || h.payload != payload_bytes(g->c) || bytes < sizeof(h) + h.payload)
+        return fail(g, GKS_ERR_ARG, "checkpoint does not match this grid");
+    int rc = cuda_check(g, cudaMemcpyAsync(g->c.staging, (const char *)h_blob + sizeof(h), h.payload,
+                                           cudaMemcpyHostToDevice, g->c.stream),
+                        "copy checkpoint");
+    if (rc) return rc;
+    launch_raw_copy(g->c, g->c.staging, 0);
+    rc = check_launch(g, "scatter checkpoint");
+    if (rc) return rc;
+    rc = cuda_check(g, cudaMemcpyAsync(&g->c.scal->t, &h.t, sizeof(double), cudaMemcpyHostToDevice, g->c.stream),
+                    "set time");
+    if (!rc) rc = sync(g);
+    g->nstep = h.nstep;
+    return rc;
+}
+
+int gks_profile_enable(gks_grid *g, int timing_on)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    int rc = sync(g);
+    if (rc) return rc;
+    Profiler &p = g->prof;
+    p.timing = timing_on != 0;
+    p.next = 0;
+    p.recs.clear();
+    for (int k = 0; k < K_NGROUPS; ++k) p.launches[k] = 0;
+    return GKS_OK;
+}
+
+int gks_profile_read(gks_grid *g, gks_profile_out *out)
+{
+    if (!g || !out) return fail(g, GKS_ERR_ARG, "null argument");
+    int rc = sync(g);
+    if (rc) return rc;
+    Profiler &p = g->prof;
+    memset(out, 0, sizeof(*out));
+    for (const Profiler::Rec &r : p.recs) {
+        float ms = 0.0f;
+        rc = cuda_check(g, cudaEventElapsedTime(&ms, r.a, r.b), "event time");
+        if (rc) return rc;
+        out->ms[r.group] += ms;
+    }
+    for (int k = 0; k < K_NGROUPS; ++k) {
+        out->launches[k] = p.launches[k];
+        out->total_launches += p.launches[k];
+        p.launches[k] = 0;
+    }
+    p.next = 0;
+    p.recs.clear();
+    return GKS_OK;
+}
+
+const char *gks_kernel_group_name(int group)
+{
+    static const char *names[K_NGROUPS] = {"prep", "ghost", "cfl", "face_eq", "face_flux",
+                                           "update", "alm", "ibm", "misc"};
+    return (group >= 0 && group < K_NGROUPS) ? names[group] : "";
+}
+
+int gks_state_layout(const gks_grid *g, long out[7])
+{
+    if (!g || !out) return fail(nullptr, GKS_ERR_ARG, "null argument");
+    out[0] = g->c.P[0];
+    out[1] = g->c.P[1];
+    out[2] = g->c.P[2];
+    out[3] = g->c.prec == GKS_FP64 ? 8 : 4;
+    out[4] = g->c.prec == GKS_FP64 ? 4 : 8;
+    out[5] = g->c.np;
+    out[6] = G;
+    return GKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// gks_internal.h -- declarations shared by the translation units of libgks.so
+// (host context, device-resident scalars, kernel launchers). Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "gks_api.h"
+
+namespace gks {
+
+constexpr int G = 3;              // ghost layers (WENO5 needs 3)
+constexpr int kMaxPartials = 1024;
+
+enum : int { FLAG_NONFINITE = 1, FLAG_CFL = 2, FLAG_RANGE = 4 };
+
+// Kernel groups for the optional per-launch event timing (gks_profile_*).
+enum : int {
+    K_PREP = 0, K_GHOST, K_CFL, K_FACE_EQ, K_FACE_FLUX, K_UPDATE, K_ALM, K_IBM, K_MISC, K_NGROUPS
+};
+
+// Scalars that live in device memory so that a step needs no host round trip.
+struct Scalars {
+    double t;                       // time at the start of the current step
+    double dt;                      // time step of the current step
+    double cfl_number;              // CFL number of the last step
+    unsigned long long maxu2_bits;  // max |U|^2 over interior cells (bits of a double >= 0)
+    int flags;                      // FLAG_* raised by kernels
+    int pad0;
+    unsigned long long resid_bits;  // IBM residual max (bits of a double >= 0)
+    int ibm_converged;
+    int ibm_iters;
+    double reserve[8];
+};
+
+// Host-side description of every device buffer and constant of one grid.
+struct Ctx {
+    int prec;                 // GKS_FP64 or GKS_FP32C
+    int n[3], P[3];
+    long np;                  // element stride between component arrays (>= P0 P1 P2)
+    long ncell;               // interior cells
+    int bc[3][2];
+    double lambda, theta, csound, mu, rho_ref, off;  // off = rho_ref (FP32C) or 0 (FP64)
+    double cfl, dt_fixed, hmin;
+    double inflow[4];         // rho, u, v, w
+    double fbody[3];
+    double x0[3], hu[3];      // origin and width of uniform axes (forcing)
+    int uniform[3];
+    cudaStream_t stream;
+
+    void *state;              // FP64: double[4][np]; FP32C: float hi[4][np], lo[4][np]
+    void *wk0;                // reconstruction input of stage 1 (FP64: == state)
+    void *wk1;                // W* (reconstruction input of stage 2), R[4][np]
+    void *pbuf;               // P = W + dt L + dt^2/6 Lt (FP64 double[4][np]; FP32C hi/lo)
+    void *fq;                 // face equilibrium state + normal slope, R[8][nfq]
+    long nfq;
+    void *ff[3];              // face-averaged F0 and F1 per direction, R[8][nff]
+    long nff[3];
+    void *ih[3];              // R: inverse cell widths, padded index i + 3
+    void *ihf[3];             // R: inverse centre distance at faces, f = 0..n
+    double *h64[3];           // double: cell widths, padded index i + 3
+    double *partials;         // double[kMaxPartials * 8]
+    Scalars *scal;            // device scalars
+    double *staging;          // >= 4 * ncell doubles, aliases the face-flux buffers
+
+    // optional launch hook: called before (begin = 1) and after (begin = 0)
+    // every kernel launch with the kernel group
+    void (*mark)(void *ctx, int group, int begin) = nullptr;
+    void *mark_ctx = nullptr;
+};
+
+inline void mark(const Ctx &c, int group, int begin)
+{
+    if (c.mark) c.mark(c.mark_ctx, group, begin);
+}
+
+// Launchers of the stencil path (gks_stencil.cu).
+void launch_prep(const Ctx &c);                        // FP32C: state -> wk0
+void launch_ghost(const Ctx &c, void *w);              // 3 ghost layers of w (working type)
+void launch_stage(const Ctx &c, int stage);            // face kernels + update
+void launch_cfl(const Ctx &c);                          // max|U| and dt into scal
+void launch_advance(const Ctx &c);                      // t += dt
+void launch_scatter_state(const Ctx &c, const double *d_src);  // compact FP64 -> state
+void launch_gather_state(const Ctx &c, double *d_dst);         // state -> compact FP64
+void launch_diagnostics(const Ctx &c, double *d_out5);
+void launch_fill_rest(const Ctx &c);                            // rho = 1, momentum 0
+void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored arrays <-> compact
+
+// Actuator line (gks_forcing.cu).
+struct RotorDev {
+    int nb, np, correction;
+    double hub[3], omega, az0, radius, eps, rho_inf, uref;
+    double *r, *chord, *twist, *width, *scale;  // device arrays
+    double *X;          // 3 nb np positions of the last step
+    double *F;          // 4 nb np: F_x, F_th, alpha, phi
+    double *et;         // 2 nb: -sin th_b, cos th_b
+    double *out;        // thrust[nb], torque[nb], power, cp, ct
+    int box[3][2];      // interior cell box swept by the 3 eps supports
+};
+void launch_alm(const Ctx &c, const RotorDev &r);
+
+// Immersed body (gks_forcing.cu).
+struct BodyDev {
+    int n, niter;
+    double eps, tol;
+    double *xyz, *vel;  // device, 3n each
+    double *dS;         // device, n
+    int box[3][2];
+    long nbox;
+    double *Vbar, *vbar, *phi;  // per box cell (vbar: 3 per cell)
+    double *fsum;               // 3 per box cell
+    double *out;                // force[3], iters, residual, residual history[niter]
+    // back-interpolation weights W_{ijk->p} (static): CSR over points, columns
+    // are box-local cell indices in (k, j, i) order
+    long *csr_off;              // n + 1
+    int *csr_cell;              // nnz
+    double *csr_w;              // nnz
+    long nnz;
+    double *Ubox;               // 3 per box cell: cell velocity of the residual
+};
+void launch_body_csr_count(const Ctx &c, const BodyDev &b, long *d_counts);
+void launch_body_csr_fill(const Ctx &c, const BodyDev &b);
+int body_box(const Ctx &c, const double *xyz, int n, double eps, int box[3][2]);
+void launch_body_precompute(const Ctx &c, const BodyDev &b);
+void launch_ibm(const Ctx &c, const BodyDev &b);
+
+}  // namespace gks

@@ -1,0 +1,883 @@
+// gks_stencil.cu -- the gas-kinetic stencil of one S2O4 stage on sm_103a.
+//
+// Per stage and per direction d (x, y, z) two kernels run:
+//   face_eq    one thread per face of the tangentially extended face box:
+//              WENO5-JS left/right states along d (Sec. 2, Jiang-Shu), the
+//              equilibrium state Q0 from the half Maxwellians (u>0 from the
+//              left, u<0 from the right), and the quartic normal slope of Q0.
+//   face_flux  32x8 face tiles: linear quartic reconstruction of Q0 and its
+//              normal slope to the 2x2 Gauss points (Sec. 2, Eq. (x_example))
+//              with the tangential pass staged in shared memory, and the
+//              gas-kinetic flux F0 and its time derivative F1 at each point
+//              (Sec. 2, Eq. (flux); Appendix), averaged with weights 1/4.
+// then the update kernel forms L and dL/dt (Eq. (finite)) and applies the
+// two-stage fourth-order combination.
+//
+// All arithmetic runs in the working type R: double for GKS_FP64, float for
+// GKS_FP32C. The reconstruction works on rho - off (off = rho_ref in FP32C,
+// 0 in FP64), so the large constant pressure theta * rho_ref never enters an
+// FP32 difference; it cancels exactly between the two faces of a cell.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+template <typename R>
+struct Phys {
+    R lambda, theta, mu, off, sqlam, kE;
+};
+
+template <typename R>
+Phys<R> make_phys(const Ctx &c)
+{
+    Phys<R> p;
+    p.lambda = (R)c.lambda;
+    p.theta = (R)c.theta;
+    p.mu = (R)c.mu;
+    p.off = (R)c.off;
+    p.sqlam = (R)sqrt(c.lambda);
+    p.kE = (R)(1.0 / (2.0 * sqrt(3.14159265358979323846 * c.lambda)));
+    return p;
+}
+
+// Direction d: normal axis d, tangential axes t1, t2.
+__host__ __device__ inline int tan1(int d) { return d == 0 ? 1 : 0; }
+__host__ __device__ inline int tan2(int d) { return d == 2 ? 1 : 2; }
+
+// ---------------------------------------------------------------- ghosts --
+
+template <typename R>
+struct GhostArgs {
+    R *w;
+    long np;
+    int n[3], P[3];
+    int d, e1, e2, lo1, lo2, len1, len2;
+    int bc0, bc1;
+    R off, csound;
+    R uin[3];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) ghost_kernel(GhostArgs<R> A)
+{
+    const int a = A.lo1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int b = A.lo2 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (a >= A.lo1 + A.len1 || b >= A.lo2 + A.len2) return;
+    const int s = blockIdx.z / G, l = blockIdx.z % G + 1;
+    const int d = A.d, nd = A.n[d];
+    const int bc = s == 0 ? A.bc0 : A.bc1;
+    const int gi = s == 0 ? -l : nd - 1 + l;
+    int src;
+    if (bc == GKS_BC_PERIODIC) {
+        src = gi % nd;
+        if (src < 0) src += nd;
+    } else if (bc == GKS_BC_NOSLIP || bc == GKS_BC_SLIP) {
+        src = s == 0 ? l - 1 : nd - l;
+    } else {
+        src = s == 0 ? 0 : nd - 1;
+    }
+    int cg[3], cs[3];
+    cg[d] = gi; cg[A.e1] = a; cg[A.e2] = b;
+    cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
+    const long ig = (long)(cg[0] + G) + (long)A.P[0] * ((long)(cg[1] + G) + (long)A.P[1] * (cg[2] + G));
+    const long is = (long)(cs[0] + G) + (long)A.P[0] * ((long)(cs[1] + G) + (long)A.P[1] * (cs[2] + G));
+    R q[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = A.w[v * A.np + is];
+    if (bc == GKS_BC_NOSLIP) {
+        q[1] = -q[1]; q[2] = -q[2]; q[3] = -q[3];
+    } else if (bc == GKS_BC_SLIP) {
+        q[1 + d] = -q[1 + d];
+    } else if (bc == GKS_BC_INFLOW) {
+        // density from the outgoing isothermal Riemann invariant of cell 1
+        const R r1 = A.off + q[0];
+        const R un1 = q[1 + d] / r1;
+        const R x = (s == 0 ? R(1) : R(-1)) * (A.uin[d] - un1) / A.csound;
+        const R ex = exp(x);
+        const R rg = r1 * ex;
+        q[0] = q[0] * ex + A.off * expm1(x);   // rg - off
+        q[1] = rg * A.uin[0];
+        q[2] = rg * A.uin[1];
+        q[3] = rg * A.uin[2];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.w[v * A.np + ig] = q[v];
+}
+
+template <typename R>
+void ghost_impl(const Ctx &c, R *w)
+{
+    for (int d = 0; d < 3; ++d) {
+        GhostArgs<R> A;
+        A.w = w;
+        A.np = c.np;
+        for (int e = 0; e < 3; ++e) { A.n[e] = c.n[e]; A.P[e] = c.P[e]; }
+        A.d = d;
+        A.e1 = tan1(d);
+        A.e2 = tan2(d);
+        // axes swept before d include their ghosts (edges and corners)
+        A.lo1 = A.e1 < d ? -G : 0;
+        A.len1 = A.e1 < d ? c.n[A.e1] + 2 * G : c.n[A.e1];
+        A.lo2 = A.e2 < d ? -G : 0;
+        A.len2 = A.e2 < d ? c.n[A.e2] + 2 * G : c.n[A.e2];
+        A.bc0 = c.bc[d][0];
+        A.bc1 = c.bc[d][1];
+        A.off = (R)c.off;
+        A.csound = (R)c.csound;
+        for (int e = 0; e < 3; ++e) A.uin[e] = (R)c.inflow[1 + e];
+        dim3 blk(32, 8), grd((A.len1 + 31) / 32, (A.len2 + 7) / 8, 2 * G);
+        mark(c, K_GHOST, 1);
+        ghost_kernel<R><<<grd, blk, 0, c.stream>>>(A);
+        mark(c, K_GHOST, 0);
+    }
+}
+
+// ------------------------------------------------------------ face state --
+
+// WENO5-JS value at the right face of the centre cell of (a,b,c,d,e), with
+// eps_w = 1e-6 and power 2. The three nonlinear weights d_k/(eps+beta_k)^2
+// are scaled by (eps+beta_0)^2 (eps+beta_1)^2 (eps+beta_2)^2 so that one
+// division remains.
+template <typename R>
+__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
+{
+    const R r6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0), q = R(0.25);
+    const R p0 = (R(2) * a - R(7) * b + R(11) * c) * r6;
+    const R p1 = (-b + R(5) * c + R(2) * d) * r6;
+    const R p2 = (R(2) * c + R(5) * d - e) * r6;
+    R t = a - R(2) * b + c, u = a - R(4) * b + R(3) * c;
+    R s0 = R(1e-6) + (c13 * t * t + q * u * u);
+    t = b - R(2) * c + d; u = b - d;
+    R s1 = R(1e-6) + (c13 * t * t + q * u * u);
+    t = c - R(2) * d + e; u = R(3) * c - R(4) * d + e;
+    R s2 = R(1e-6) + (c13 * t * t + q * u * u);
+    s0 *= s0; s1 *= s1; s2 *= s2;
+    const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
+    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+}
+
+template <typename R>
+struct FaceEqArgs {
+    const R *w;      // working state, 4 arrays of np
+    long np;
+    R *fq;           // 8 arrays of nfq
+    long nfq;
+    const R *ihf;    // inverse centre distance at faces of axis d
+    int n1, n2;      // interior cells along t1, t2
+    long sd, s1, s2; // element strides along d, t1, t2
+    int cn, c1, c2;  // state component of the normal / t1 / t2 momentum
+    Phys<R> ph;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
+    const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f = blockIdx.z;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
+    // cell f-1 (left neighbour of face f)
+    const long base = (long)(f - 1 + G) * A.sd + (long)(a + G) * A.s1 + (long)(b + G) * A.s2;
+    const int comp[4] = {0, A.cn, A.c1, A.c2};
+    R c[4][6];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const R *p = A.w + comp[v] * A.np + base;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) c[v][m] = __ldg(p + (long)(m - 2) * A.sd);
+    }
+    R Ql[4], Qr[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        Ql[v] = weno5(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4]);
+        Qr[v] = weno5(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1]);
+    }
+    // equilibrium state: u>0 half of the left Maxwellian, u<0 half of the
+    // right one; written on rho - off
+    const Phys<R> &ph = A.ph;
+    const R rl = ph.off + Ql[0], rr = ph.off + Qr[0];
+    const R Ul = Ql[1] / rl, Ur = Qr[1] / rr;
+    const R el = erf(ph.sqlam * Ul), er = erf(ph.sqlam * Ur);
+    const R Pl = R(0.5) + R(0.5) * el;   // <u^0>_{u>0} of the left state
+    const R Pr = R(0.5) - R(0.5) * er;   // <u^0>_{u<0} of the right state
+    const R xl = -ph.lambda * Ul * Ul, xr = -ph.lambda * Ur * Ur;
+    const R El = ph.kE * exp(xl), Er = ph.kE * exp(xr);
+    R Q0[4];
+    Q0[0] = Ql[0] * Pl + Qr[0] * Pr + ph.off * (R(0.5) * (el - er));
+    Q0[1] = Ql[1] * Pl + Qr[1] * Pr + (Ql[0] * El - Qr[0] * Er) +
+            ph.off * (ph.kE * (expm1(xl) - expm1(xr)));
+    Q0[2] = Ql[2] * Pl + Qr[2] * Pr;
+    Q0[3] = Ql[3] * Pl + Qr[3] * Pr;
+    // normal slope at the face: derivative of the quartic through Q0 and the
+    // cell averages f-2..f+1 (the face value drops out)
+    const R s = A.ihf[f] * R(1.0 / 12.0);
+    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * (A.n1 + 4) + (a + 2);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        A.fq[v * A.nfq + o] = Q0[v];
+        A.fq[(4 + v) * A.nfq + o] = (R(15) * (c[v][3] - c[v][2]) - (c[v][4] - c[v][1])) * s;
+    }
+}
+
+// ------------------------------------------------------------- face flux --
+
+// Quartic through 5 face averages q[-2..2], at the Gauss points -g, +g of
+// the centre cell, g = 1/(2 sqrt 3) (index space):
+//   value(+-g) = E +- O, derivative(+-g) = Do +- De with s_k = q_k + q_-k,
+//   a_k = q_k - q_-k and
+//   E  = q0 + (s1 - 2 q0)/1080 - (s2 - 2 q0)/4320,
+//   O  = (25 sqrt3 / 216) a1 - (7 sqrt3 / 432) a2,
+//   Do = (2/3) a1 - (1/12) a2,
+//   De = (13 sqrt3 / 54)(s1 - 2 q0) - (sqrt3 / 54)(s2 - 2 q0).
+template <typename R>
+__device__ __forceinline__ void tan_val(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp)
+{
+    const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
+    const R a1 = qp1 - qm1, a2 = qp2 - qm2;
+    const R E = q0 + (d1 * R(1.0 / 1080.0) - d2 * R(1.0 / 4320.0));
+    const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
+    vm = E - O;
+    vp = E + O;
+}
+
+template <typename R>
+__device__ __forceinline__ void tan_val_der(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp, R &dm,
+                                            R &dp)
+{
+    const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
+    const R a1 = qp1 - qm1, a2 = qp2 - qm2;
+    const R E = q0 + (d1 * R(1.0 / 1080.0) - d2 * R(1.0 / 4320.0));
+    const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
+    const R Do = R(2.0 / 3.0) * a1 - R(1.0 / 12.0) * a2;
+    const R De = R(0.41697519441472974) * d1 - R(0.032075014954979206) * d2;
+    vm = E - O;
+    vp = E + O;
+    dm = Do - De;
+    dp = Do + De;
+}
+
+// Gas-kinetic flux at one Gauss point (local frame: index 0 normal, 1 and 2
+// tangential). The moments of f = g0 (1 - tau (a1 u + a2 v + a3 w + A) + A t)
+// with the coefficients solved from the slopes and compatibility (Appendix)
+// reduce to the closed form below (Chapman-Enskog structure, tau p = mu):
+//   a.u + A = (1/theta) d_i U_j (c_i c_j - theta delta_ij),   c = u - U,
+//   A = A0 + A_j c_j, A0 = -U.grad ln rho - div U,
+//   A_k = -d_k ln rho - 2 lambda U_i d_i U_k,
+//   F0 = (m_n, m_n U_k + p' delta_nk - mu (d_n U_k + d_k U_n)),
+//   F1 = rho (A0 U_n + theta A_n, A0 (U_n U_k + theta delta_nk) + theta (A_k U_n + A_n U_k)),
+// with p' = theta (rho - off): the constant theta off cancels in L.
+template <typename R, bool NEED_F0>
+__device__ __forceinline__ void gk_flux(const Phys<R> &ph, const R q[4], const R Dn[4],
+                                        const R D1[4], const R D2[4], R F0[4], R F1[4])
+{
+    const R rho = ph.off + q[0];
+    const R inv = R(1) / rho;
+    const R U0 = q[1] * inv, U1 = q[2] * inv, U2 = q[3] * inv;
+    const R g0 = Dn[0] * inv, g1 = D1[0] * inv, g2 = D2[0] * inv;
+    const R G00 = (Dn[1] - U0 * Dn[0]) * inv, G01 = (Dn[2] - U1 * Dn[0]) * inv,
+            G02 = (Dn[3] - U2 * Dn[0]) * inv;
+    const R G10 = (D1[1] - U0 * D1[0]) * inv, G11 = (D1[2] - U1 * D1[0]) * inv,
+            G12 = (D1[3] - U2 * D1[0]) * inv;
+    const R G20 = (D2[1] - U0 * D2[0]) * inv, G21 = (D2[2] - U1 * D2[0]) * inv,
+            G22 = (D2[3] - U2 * D2[0]) * inv;
+    const R th = ph.theta, tl = R(2) * ph.lambda;
+    const R A0 = -(U0 * g0 + U1 * g1 + U2 * g2) - (G00 + G11 + G22);
+    const R An = -g0 - tl * (U0 * G00 + U1 * G10 + U2 * G20);
+    const R A1 = -g1 - tl * (U0 * G01 + U1 * G11 + U2 * G21);
+    const R A2 = -g2 - tl * (U0 * G02 + U1 * G12 + U2 * G22);
+    if (NEED_F0) {
+        F0[0] = q[1];
+        F0[1] = q[1] * U0 + th * q[0] - ph.mu * (G00 + G00);
+        F0[2] = q[1] * U1 - ph.mu * (G01 + G10);
+        F0[3] = q[1] * U2 - ph.mu * (G02 + G20);
+    }
+    F1[0] = rho * (A0 * U0 + th * An);
+    F1[1] = rho * (A0 * (U0 * U0 + th) + th * (An * U0 + An * U0));
+    F1[2] = rho * (A0 * (U0 * U1) + th * (A1 * U0 + An * U1));
+    F1[3] = rho * (A0 * (U0 * U2) + th * (A2 * U0 + An * U2));
+}
+
+constexpr int TX = 32, TY = 8;              // face tile
+constexpr int SQ_W = TX + 4, SQ_H = TY + 4; // tile with the tangential halo
+constexpr int SQ_N = 8 * SQ_H * SQ_W;
+constexpr int ST_ROWS = SQ_H * TX;          // rows of the t1 pass
+constexpr int ST_N = 24 * ST_ROWS;
+
+template <typename R>
+struct FluxArgs {
+    const R *fq;
+    long nfq;
+    R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
+    long nff;
+    const R *ih1, *ih2;  // inverse cell widths along t1, t2 (padded index)
+    int n1, n2;
+    int gcomp[4];        // global component of local component 0..3
+    Phys<R> ph;
+};
+
+template <typename R, bool NEED_F0>
+__global__ void __launch_bounds__(256) face_flux_kernel(FluxArgs<R> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sq = reinterpret_cast<R *>(smem_raw);
+    R *st = sq + SQ_N;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY, f = blockIdx.z;
+    const int e1 = A.n1 + 4, e2 = A.n2 + 4;
+
+    // (1) Q0 and its normal slope on the (TX+4) x (TY+4) tile of faces
+    for (int idx = tid; idx < SQ_N; idx += TX * TY) {
+        const int cc = idx / (SQ_H * SQ_W);
+        const int rem = idx - cc * (SQ_H * SQ_W);
+        const int r = rem / SQ_W, col = rem - r * SQ_W;
+        const int sa = a0 + col, sb = b0 + r;
+        R v = R(0);
+        if (sa < e1 && sb < e2) v = __ldg(A.fq + cc * A.nfq + ((long)f * e2 + sb) * e1 + sa);
+        sq[idx] = v;
+    }
+    __syncthreads();
+
+    // (2) t1 pass: values and t1-derivatives of Q0, values of the normal
+    //     slope, at the two t1 Gauss points, for every row of the tile
+    for (int idx = tid; idx < ST_ROWS; idx += TX * TY) {
+        const int r = idx / TX, col = idx - r * TX;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const R *p = sq + (v * SQ_H + r) * SQ_W + col;
+            R vm, vp, dm, dp;
+            tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
+            st[(v * 4 + 0) * ST_ROWS + idx] = vm;
+            st[(v * 4 + 1) * ST_ROWS + idx] = vp;
+            st[(v * 4 + 2) * ST_ROWS + idx] = dm;
+            st[(v * 4 + 3) * ST_ROWS + idx] = dp;
+            const R *pn = sq + ((4 + v) * SQ_H + r) * SQ_W + col;
+            tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
+            st[(16 + v * 2 + 0) * ST_ROWS + idx] = vm;
+            st[(16 + v * 2 + 1) * ST_ROWS + idx] = vp;
+        }
+    }
+    __syncthreads();
+
+    const int a = a0 + tx, b = b0 + ty;
+    if (a >= A.n1 || b >= A.n2) return;
+    const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
+    R acc0[4] = {R(0), R(0), R(0), R(0)}, acc1[4] = {R(0), R(0), R(0), R(0)};
+
+    // (3) t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g)
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        R Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const R *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+            const R *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+            const R *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+            R vm, vp, dm, dp;
+            tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
+            Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm * ih2; D2[1][v] = dp * ih2;
+            tan_val(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+            D1[0][v] = vm * ih1; D1[1][v] = vp * ih1;
+            tan_val(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+            Dn[0][v] = vm; Dn[1][v] = vp;
+        }
+#pragma unroll
+        for (int nn = 0; nn < 2; ++nn) {
+            R F0[4], F1[4];
+            gk_flux<R, NEED_F0>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], F0, F1);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (NEED_F0) acc0[v] += F0[v];
+                acc1[v] += F1[v];
+            }
+        }
+    }
+    const long o = ((long)f * A.n2 + b) * A.n1 + a;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
+        A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * acc1[v];
+    }
+}
+
+// ---------------------------------------------------------------- update --
+
+template <typename R>
+struct UpdArgs {
+    const R *ff[3];
+    long nff[3];
+    const R *ih[3];
+    int n[3], P[3];
+    long np;
+    const void *w0;   // stage 1: state (FP64 W / FP32C hi,lo)
+    void *wk1;        // stage 1 output W* (R)
+    void *pbuf;       // P
+    void *state;      // stage 2 output
+    R off;
+    R fb[3];
+    Scalars *scal;
+};
+
+__device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
+{
+    // error-free two-sum of hi + d, then renormalise (hi, lo + err)
+    const float s = hi + d;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (d - bp);
+    const float l = lo + e;
+    const float h2 = s + l;
+    lo = l - (h2 - s);
+    hi = h2;
+}
+
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const long lin = (long)(i + G) + (long)A.P[0] * ((long)(j + G) + (long)A.P[1] * (k + G));
+    const R ihx = __ldg(A.ih[0] + i + G), ihy = __ldg(A.ih[1] + j + G), ihz = __ldg(A.ih[2] + k + G);
+    const long ix = ((long)i * nz + k) * ny + j, sx = (long)nz * ny;
+    const long iy = ((long)j * nz + k) * nx + i, sy = (long)nz * nx;
+    const long iz = ((long)k * ny + j) * nx + i, sz = (long)ny * nx;
+    const double dt = A.scal->dt;
+    const R dtr = (R)dt;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const R *fx = A.ff[0] + (4 + v) * A.nff[0];
+        const R *fy = A.ff[1] + (4 + v) * A.nff[1];
+        const R *fz = A.ff[2] + (4 + v) * A.nff[2];
+        const R Lt = -((__ldg(fx + ix + sx) - __ldg(fx + ix)) * ihx +
+                       (__ldg(fy + iy + sy) - __ldg(fy + iy)) * ihy +
+                       (__ldg(fz + iz + sz) - __ldg(fz + iz)) * ihz);
+        if (STAGE == 1) {
+            const R *gx = A.ff[0] + v * A.nff[0];
+            const R *gy = A.ff[1] + v * A.nff[1];
+            const R *gz = A.ff[2] + v * A.nff[2];
+            const R L = -((__ldg(gx + ix + sx) - __ldg(gx + ix)) * ihx +
+                          (__ldg(gy + iy + sy) - __ldg(gy + iy)) * ihy +
+                          (__ldg(gz + iz + sz) - __ldg(gz + iz)) * ihz);
+            if constexpr (std::is_same<R, double>::value) {
+                const double *W = (const double *)A.w0;
+                const double w = W[v * A.np + lin];
+                ((double *)A.wk1)[v * A.np + lin] = w + 0.5 * dt * L + 0.125 * dt * dt * Lt;
+                ((double *)A.pbuf)[v * A.np + lin] = w + dt * L + dt * dt / 6.0 * Lt;
+            } else {
+                const float *S = (const float *)A.w0;
+                float hi = S[v * A.np + lin], lo = S[(4 + v) * A.np + lin];
+                const float offv = v == 0 ? A.off : 0.0f;
+                ((float *)A.wk1)[v * A.np + lin] =
+                    ((hi - offv) + lo) + (0.5f * dtr * L + 0.125f * dtr * dtr * Lt);
+                add_comp(hi, lo, dtr * L + dtr * dtr * (1.0f / 6.0f) * Lt);
+                ((float *)A.pbuf)[v * A.np + lin] = hi;
+                ((float *)A.pbuf)[(4 + v) * A.np + lin] = lo;
+            }
+        } else {
+            if constexpr (std::is_same<R, double>::value) {
+                double w = ((const double *)A.pbuf)[v * A.np + lin] + dt * dt / 3.0 * Lt;
+                if (v > 0) w += dt * (double)A.fb[v - 1];
+                ((double *)A.state)[v * A.np + lin] = w;
+                bad |= !isfinite(w);
+            } else {
+                float hi = ((const float *)A.pbuf)[v * A.np + lin];
+                float lo = ((const float *)A.pbuf)[(4 + v) * A.np + lin];
+                float inc = dtr * dtr * (1.0f / 3.0f) * Lt;
+                if (v > 0) inc += dtr * A.fb[v - 1];
+                add_comp(hi, lo, inc);
+                ((float *)A.state)[v * A.np + lin] = hi;
+                ((float *)A.state)[(4 + v) * A.np + lin] = lo;
+                bad |= !isfinite(hi) || !isfinite(lo);
+            }
+        }
+    }
+    if (STAGE == 2 && bad) atomicOr(&A.scal->flags, FLAG_NONFINITE);
+}
+
+template <typename R>
+void stage_impl(const Ctx &c, int stage)
+{
+    const Phys<R> ph = make_phys<R>(c);
+    const R *w = (const R *)(stage == 1 ? c.wk0 : c.wk1);
+    const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
+    const size_t smem = (size_t)(SQ_N + ST_N) * sizeof(R);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(face_flux_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaFuncSetAttribute(face_flux_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr_done = true;
+    }
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = tan1(d), t2 = tan2(d);
+        FaceEqArgs<R> E;
+        E.w = w;
+        E.np = c.np;
+        E.fq = (R *)c.fq;
+        E.nfq = c.nfq;
+        E.ihf = (const R *)c.ihf[d];
+        E.n1 = c.n[t1];
+        E.n2 = c.n[t2];
+        E.sd = stride[d];
+        E.s1 = stride[t1];
+        E.s2 = stride[t2];
+        E.cn = 1 + d;
+        E.c1 = 1 + t1;
+        E.c2 = 1 + t2;
+        E.ph = ph;
+        dim3 blk(32, 8);
+        dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, c.n[d] + 1);
+        mark(c, K_FACE_EQ, 1);
+        face_eq_kernel<R><<<ge, blk, 0, c.stream>>>(E);
+        mark(c, K_FACE_EQ, 0);
+
+        FluxArgs<R> F;
+        F.fq = (const R *)c.fq;
+        F.nfq = c.nfq;
+        F.ff = (R *)c.ff[d];
+        F.nff = c.nff[d];
+        F.ih1 = (const R *)c.ih[t1];
+        F.ih2 = (const R *)c.ih[t2];
+        F.n1 = c.n[t1];
+        F.n2 = c.n[t2];
+        F.gcomp[0] = 0;
+        F.gcomp[1] = 1 + d;
+        F.gcomp[2] = 1 + t1;
+        F.gcomp[3] = 1 + t2;
+        F.ph = ph;
+        dim3 gf((F.n1 + TX - 1) / TX, (F.n2 + TY - 1) / TY, c.n[d] + 1);
+        mark(c, K_FACE_FLUX, 1);
+        if (stage == 1)
+            face_flux_kernel<R, true><<<gf, blk, smem, c.stream>>>(F);
+        else
+            face_flux_kernel<R, false><<<gf, blk, smem, c.stream>>>(F);
+        mark(c, K_FACE_FLUX, 0);
+    }
+    UpdArgs<R> U;
+    for (int d = 0; d < 3; ++d) {
+        U.ff[d] = (const R *)c.ff[d];
+        U.nff[d] = c.nff[d];
+        U.ih[d] = (const R *)c.ih[d];
+        U.n[d] = c.n[d];
+        U.P[d] = c.P[d];
+        U.fb[d] = (R)c.fbody[d];
+    }
+    U.np = c.np;
+    U.w0 = c.state;
+    U.wk1 = c.wk1;
+    U.pbuf = c.pbuf;
+    U.state = c.state;
+    U.off = (R)c.off;
+    U.scal = c.scal;
+    dim3 blk(32, 8), gu((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    mark(c, K_UPDATE, 1);
+    if (stage == 1)
+        update_kernel<R, 1><<<gu, blk, 0, c.stream>>>(U);
+    else
+        update_kernel<R, 2><<<gu, blk, 0, c.stream>>>(U);
+    mark(c, K_UPDATE, 0);
+}
+
+// ----------------------------------------------------- prep, CFL, misc --
+
+__global__ void __launch_bounds__(256) prep_kernel(const float *S, float *wk, long np, int nx, int ny,
+                                                   int nz, int P0, int P1, float off)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        wk[v * np + lin] = (S[v * np + lin] - (v == 0 ? off : 0.0f)) + S[(4 + v) * np + lin];
+}
+
+__device__ __forceinline__ void load_cell(int prec, const void *S, long np, long lin, double q[4])
+{
+    if (prec == GKS_FP64) {
+        const double *W = (const double *)S;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[v] = W[v * np + lin];
+    } else {
+        const float *W = (const float *)S;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[v] = (double)W[v * np + lin] + (double)W[(4 + v) * np + lin];
+    }
+}
+
+__global__ void __launch_bounds__(256) cfl_kernel(int prec, const void *S, long np, int nx, int ny,
+                                                  int nz, int P0, int P1, Scalars *scal)
+{
+    const long ncell = (long)nx * ny * nz;
+    double mx = 0.0;
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const long r = c / nx;
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+        double u2;
+        if (prec == GKS_FP64) {
+            const double *W = (const double *)S;
+            const double r = W[lin], a = W[np + lin], b = W[2 * np + lin], c2 = W[3 * np + lin];
+            u2 = (a * a + b * b + c2 * c2) / (r * r);
+        } else {
+            // FP32C: hi + lo in FP32 (the time step needs no more)
+            const float *W = (const float *)S;
+            const float r = W[lin] + W[4 * np + lin], a = W[np + lin] + W[5 * np + lin];
+            const float b = W[2 * np + lin] + W[6 * np + lin], c2 = W[3 * np + lin] + W[7 * np + lin];
+            u2 = (double)((a * a + b * b + c2 * c2) / (r * r));
+        }
+        mx = (u2 > mx || u2 != u2) ? u2 : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = (y > mx || y != y) ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&scal->maxu2_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmin, double csound)
+{
+    const double umax = sqrt(__longlong_as_double((long long)scal->maxu2_bits));
+    double dt;
+    if (dt_fixed > 0.0) {
+        dt = dt_fixed;
+        const double num = dt * (umax + csound) / hmin;
+        scal->cfl_number = num;
+        if (cfl > 0.0 && !(num <= cfl)) atomicOr(&scal->flags, FLAG_CFL);
+    } else {
+        dt = cfl * hmin / (umax + csound);
+        scal->cfl_number = cfl;
+        if (!isfinite(dt)) atomicOr(&scal->flags, FLAG_NONFINITE);
+    }
+    scal->dt = dt;
+    scal->maxu2_bits = 0ull;
+}
+
+__global__ void advance_kernel(Scalars *scal) { scal->t = scal->t + scal->dt; }
+
+__global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *src, void *S, long np,
+                                                      int nx, int ny, int nz, int P0, int P1)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long N = (long)nx * ny * nz;
+    const long ci = i + (long)nx * (j + (long)ny * k);
+    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double q = src[v * N + ci];
+        if (prec == GKS_FP64) {
+            ((double *)S)[v * np + lin] = q;
+        } else {
+            const float hi = (float)q;
+            ((float *)S)[v * np + lin] = hi;
+            ((float *)S)[(4 + v) * np + lin] = (float)(q - (double)hi);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(int prec, const void *S, double *dst, long np,
+                                                     int nx, int ny, int nz, int P0, int P1)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long N = (long)nx * ny * nz;
+    const long ci = i + (long)nx * (j + (long)ny * k);
+    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+    double q[4];
+    load_cell(prec, S, np, lin, q);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dst[v * N + ci] = q[v];
+}
+
+// FP64 sums of mass, momentum and kinetic energy: per-block partial sums in
+// a fixed order, then one block adds the partials in order (deterministic).
+__global__ void __launch_bounds__(256) diag_partial_kernel(int prec, const void *S, long np, int nx,
+                                                           int ny, int nz, int P0, int P1,
+                                                           const double *hx, const double *hy,
+                                                           const double *hz, double *partials)
+{
+    __shared__ double sh[5][256];
+    const long ncell = (long)nx * ny * nz;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const long r = c / nx;
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+        double q[4];
+        load_cell(prec, S, np, lin, q);
+        const double vol = hx[i + G] * hy[j + G] * hz[k + G];
+        s[0] += q[0] * vol;
+        s[1] += q[1] * vol;
+        s[2] += q[2] * vol;
+        s[3] += q[3] * vol;
+        s[4] += 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0] * vol;
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) partials[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) diag_final_kernel(const double *partials, int nparts, double *out)
+{
+    __shared__ double sh[5][256];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s[q] += partials[b * 8 + q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) fill_rest_kernel(int prec, void *S, long np, int nx, int ny,
+                                                        int nz, int P0, int P1)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+    if (prec == GKS_FP64)
+        ((double *)S)[lin] = 1.0;
+    else
+        ((float *)S)[lin] = 1.0f;
+}
+
+// Copy the stored component arrays (4 doubles or 8 floats per cell) between
+// the padded state and a compact interior array (x fastest).
+template <typename T>
+__global__ void __launch_bounds__(256) raw_copy_kernel(T *S, T *cpt, int narr, long np, int nx, int ny,
+                                                       int nz, int P0, int P1, int to_compact)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long N = (long)nx * ny * nz;
+    const long ci = i + (long)nx * (j + (long)ny * k);
+    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+    for (int a = 0; a < narr; ++a) {
+        if (to_compact)
+            cpt[a * N + ci] = S[a * np + lin];
+        else
+            S[a * np + lin] = cpt[a * N + ci];
+    }
+}
+
+int reduce_blocks(long ncell)
+{
+    long b = (ncell + 255) / 256;
+    if (b > kMaxPartials) b = kMaxPartials;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+void launch_prep(const Ctx &c)
+{
+    if (c.prec != GKS_FP32C) return;
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    mark(c, K_PREP, 1);
+    prep_kernel<<<g, blk, 0, c.stream>>>((const float *)c.state, (float *)c.wk0, c.np, c.n[0], c.n[1],
+                                         c.n[2], c.P[0], c.P[1], (float)c.off);
+    mark(c, K_PREP, 0);
+}
+
+void launch_ghost(const Ctx &c, void *w)
+{
+    if (c.prec == GKS_FP64)
+        ghost_impl<double>(c, (double *)w);
+    else
+        ghost_impl<float>(c, (float *)w);
+}
+
+void launch_stage(const Ctx &c, int stage)
+{
+    if (c.prec == GKS_FP64)
+        stage_impl<double>(c, stage);
+    else
+        stage_impl<float>(c, stage);
+}
+
+void launch_cfl(const Ctx &c)
+{
+    mark(c, K_CFL, 1);
+    cfl_kernel<<<reduce_blocks(c.ncell), 256, 0, c.stream>>>(c.prec, c.state, c.np, c.n[0], c.n[1],
+                                                             c.n[2], c.P[0], c.P[1], c.scal);
+    mark(c, K_CFL, 0);
+    mark(c, K_MISC, 1);
+    dt_kernel<<<1, 1, 0, c.stream>>>(c.scal, c.cfl, c.dt_fixed, c.hmin, c.csound);
+    mark(c, K_MISC, 0);
+}
+
+void launch_advance(const Ctx &c)
+{
+    mark(c, K_MISC, 1);
+    advance_kernel<<<1, 1, 0, c.stream>>>(c.scal);
+    mark(c, K_MISC, 0);
+}
+
+void launch_scatter_state(const Ctx &c, const double *d_src)
+{
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    scatter_kernel<<<g, blk, 0, c.stream>>>(c.prec, d_src, c.state, c.np, c.n[0], c.n[1], c.n[2],
+                                            c.P[0], c.P[1]);
+}
+
+void launch_gather_state(const Ctx &c, double *d_dst)
+{
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    gather_kernel<<<g, blk, 0, c.stream>>>(c.prec, c.state, d_dst, c.np, c.n[0], c.n[1], c.n[2],
+                                           c.P[0], c.P[1]);
+}
+
+void launch_fill_rest(const Ctx &c)
+{
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    fill_rest_kernel<<<g, blk, 0, c.stream>>>(c.prec, c.state, c.np, c.n[0], c.n[1], c.n[2], c.P[0],
+                                              c.P[1]);
+}
+
+void launch_raw_copy(const Ctx &c, void *compact, int to_compact)
+{
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    if (c.prec == GKS_FP64)
+        raw_copy_kernel<double><<<g, blk, 0, c.stream>>>((double *)c.state, (double *)compact, 4, c.np,
+                                                         c.n[0], c.n[1], c.n[2], c.P[0], c.P[1],
+                                                         to_compact);
+    else
+        raw_copy_kernel<float><<<g, blk, 0, c.stream>>>((float *)c.state, (float *)compact, 8, c.np,
+                                                        c.n[0], c.n[1], c.n[2], c.P[0], c.P[1],
+                                                        to_compact);
+}
+
+void launch_diagnostics(const Ctx &c, double *d_out5)
+{
+    const int nb = reduce_blocks(c.ncell);
+    diag_partial_kernel<<<nb, 256, 0, c.stream>>>(c.prec, c.state, c.np, c.n[0], c.n[1], c.n[2],
+                                                  c.P[0], c.P[1], c.h64[0], c.h64[1], c.h64[2],
+                                                  c.partials);
+    diag_final_kernel<<<1, 256, 0, c.stream>>>(c.partials, nb, d_out5);
+}
+
+}  // namespace gks

@@ -1,0 +1,318 @@
+"""Thin ctypes binding of libgks.so (the C ABI of include/gks_api.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library. torch provides the device memory (the state and work
+buffers are torch uint8 tensors owned by :class:`Grid`) and the stream. The
+functions of the C ABI are available under their own names as attributes of
+:data:`lib` after :func:`load`. There is no CPU fallback: loading raises if
+the library has not been built or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GKS_OK = 0
+ERRORS = {-1: "GKS_ERR_ARG", -2: "GKS_ERR_CUDA", -3: "GKS_ERR_NONFINITE", -4: "GKS_ERR_CFL",
+          -5: "GKS_ERR_STATE", -6: "GKS_ERR_RANGE"}
+FP64, FP32C = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32c": FP32C}
+MAX_BLADES = 8
+
+_dp = C.POINTER(C.c_double)
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("faces", _dp * 3), ("mach", C.c_double), ("u_ref", C.c_double),
+                ("mu", C.c_double), ("bc", (C.c_int * 2) * 3), ("precision", C.c_int), ("cfl", C.c_double),
+                ("dt_fixed", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p)]
+
+
+class RotorDesc(C.Structure):
+    _fields_ = [("n_blades", C.c_int), ("n_pts", C.c_int), ("hub", C.c_double * 3), ("omega", C.c_double),
+                ("azimuth0", C.c_double), ("radius", C.c_double), ("eps", C.c_double),
+                ("rho_inf", C.c_double), ("u_inf_ref", C.c_double), ("r", _dp), ("chord", _dp),
+                ("twist", _dp), ("width", _dp), ("correction", C.c_int)]
+
+
+class ForcesOut(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_blades", C.c_int), ("thrust", C.c_double * MAX_BLADES),
+                ("torque", C.c_double * MAX_BLADES), ("power", C.c_double), ("cp", C.c_double),
+                ("ct", C.c_double), ("body_force", C.c_double * 3), ("iters", C.c_int),
+                ("residual", C.c_double)]
+
+
+NUM_KERNEL_GROUPS = 9
+
+
+class ProfileOut(C.Structure):
+    _fields_ = [("launches", C.c_long * NUM_KERNEL_GROUPS), ("ms", C.c_double * NUM_KERNEL_GROUPS),
+                ("total_launches", C.c_long)]
+
+
+# name -> (restype, argtypes); every entry point that include/gks_api.h declares
+SIGNATURES = {
+    "gks_workspace_bytes": (C.c_int, [C.POINTER(GridDesc), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "gks_create_grid": (C.c_int, [C.POINTER(GridDesc), C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gks_destroy_grid": (C.c_int, [C.c_void_p]),
+    "gks_last_error": (C.c_char_p, [C.c_void_p]),
+    "gks_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gks_set_state": (C.c_int, [C.c_void_p, _dp]),
+    "gks_get_state": (C.c_int, [C.c_void_p, _dp]),
+    "gks_set_inflow": (C.c_int, [C.c_void_p] + [C.c_double] * 4),
+    "gks_set_body_force": (C.c_int, [C.c_void_p] + [C.c_double] * 3),
+    "gks_add_actuator_lines": (C.c_int, [C.c_void_p, C.POINTER(RotorDesc), C.POINTER(C.c_int)]),
+    "gks_set_force_scales": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "gks_add_ib_points": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int, C.c_double,
+                                    C.POINTER(C.c_int)]),
+    "gks_step": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "gks_get_time": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "gks_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "gks_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ForcesOut), _dp]),
+    "gks_diagnostics": (C.c_int, [C.c_void_p, _dp]),
+    "gks_checkpoint_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "gks_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "gks_state_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_long)]),
+    "gks_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "gks_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ProfileOut)]),
+    "gks_kernel_group_name": (C.c_char_p, [C.c_int]),
+}
+
+lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libgks.so (built in-tree by ``build.build()``) and declare the
+    signatures. Raises when the library is missing."""
+    global lib
+    if lib is not None:
+        return lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libgks.so is not built (%s); run paper_2603_11102_gb300.build.build()" % path)
+    L = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    lib = L
+    return L
+
+
+class GKSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _check(rc, handle=None):
+    if rc != GKS_OK:
+        msg = lib.gks_last_error(handle)
+        raise GKSError(rc, msg.decode() if msg else "")
+
+
+def _arr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+class Grid:
+    """One grid on the current CUDA device; device buffers are torch tensors.
+
+    Parameters mirror ``gks_grid_desc``; ``bc`` is [(lo, hi)] per axis with the
+    integer kinds of the C ABI (0 periodic, 1 no-slip, 2 slip, 3 inflow,
+    4 outflow)."""
+
+    def __init__(self, n, faces, mach, u_ref, mu, bc, precision="fp64", cfl=0.5, dt_fixed=0.0,
+                 rho_ref=1.0, device=None, stream=None):
+        import torch
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.n = tuple(int(x) for x in n)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._faces = [np.ascontiguousarray(f, dtype=np.float64) for f in faces]
+        d = GridDesc()
+        for a in range(3):
+            d.n[a] = self.n[a]
+            d.faces[a] = self._faces[a].ctypes.data_as(_dp)
+            d.bc[a][0] = int(bc[a][0])
+            d.bc[a][1] = int(bc[a][1])
+        d.mach, d.u_ref, d.mu = float(mach), float(u_ref), float(mu)
+        d.precision = self.precision
+        d.cfl, d.dt_fixed, d.rho_ref = float(cfl), float(dt_fixed), float(rho_ref)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        d.stream = C.c_void_p(stream.cuda_stream)
+        self._desc = d
+        sb, wb = C.c_size_t(), C.c_size_t()
+        _check(lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)))
+        self.state_bytes, self.work_bytes = sb.value, wb.value
+        self.state_buf = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+        self.work_buf = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        _check(lib.gks_create_grid(C.byref(d), C.c_void_p(self.state_buf.data_ptr()),
+                                   C.c_void_p(self.work_buf.data_ptr()), C.byref(h)))
+        self.h = h
+        self.objects = []
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", **kw):
+        g = cls(w.n, w.faces, w.mach, w.u_ref, w.mu, w.bc, precision=precision, cfl=w.cfl,
+                dt_fixed=w.dt_fixed, rho_ref=w.rho_ref, **kw)
+        g.set_inflow(*w.inflow)
+        g.set_body_force(*w.body_force)
+        for r in w.rotors:
+            g.add_rotor(r)
+        for b in w.bodies:
+            g.add_body(b)
+        if w.state0 is not None:
+            g.set_state(w.state0)
+        return g
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.gks_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (4, self.n[2], self.n[1], self.n[0])
+
+    def set_state(self, Q):
+        Q, p = _arr(np.asarray(Q).reshape(self.shape))
+        _check(lib.gks_set_state(self.h, p), self.h)
+        self.stream.synchronize()
+
+    def set_state_pinned(self, host_tensor):
+        """Asynchronous upload from a page-locked float64 torch tensor."""
+        _check(lib.gks_set_state(self.h, C.cast(host_tensor.data_ptr(), _dp)), self.h)
+
+    def get_state(self):
+        Q = np.zeros(self.shape)
+        _check(lib.gks_get_state(self.h, Q.ctypes.data_as(_dp)), self.h)
+        return Q
+
+    def set_inflow(self, rho, u, v=0.0, w=0.0):
+        _check(lib.gks_set_inflow(self.h, float(rho), float(u), float(v), float(w)), self.h)
+
+    def set_body_force(self, fx, fy=0.0, fz=0.0):
+        _check(lib.gks_set_body_force(self.h, float(fx), float(fy), float(fz)), self.h)
+
+    def add_rotor(self, rot):
+        arrs = [_arr(x) for x in (rot.r, rot.chord, rot.twist, rot.width)]
+        d = RotorDesc()
+        d.n_blades, d.n_pts = int(rot.n_blades), int(arrs[0][0].size)
+        for a in range(3):
+            d.hub[a] = float(rot.hub[a])
+        d.omega, d.azimuth0, d.radius, d.eps = float(rot.omega), float(rot.azimuth0), float(rot.radius), float(rot.eps)
+        d.rho_inf, d.u_inf_ref = float(rot.rho_inf), float(rot.u_inf_ref)
+        d.r, d.chord, d.twist, d.width = (p for _, p in arrs)
+        d.correction = int(bool(rot.correction))
+        rid = C.c_int()
+        _check(lib.gks_add_actuator_lines(self.h, C.byref(d), C.byref(rid)), self.h)
+        self.objects.append(("rotor", d.n_blades, d.n_pts))
+        return rid.value
+
+    def set_force_scales(self, rid, s):
+        s, p = _arr(s)
+        _check(lib.gks_set_force_scales(self.h, int(rid), p), self.h)
+
+    def add_body(self, body):
+        xyz, px = _arr(body.xyz)
+        dS, pd = _arr(body.dS)
+        if body.vel is None:
+            pv = None
+        else:
+            vel, pv = _arr(body.vel)
+        bid = C.c_int()
+        _check(lib.gks_add_ib_points(self.h, int(dS.size), px, pd, pv, float(body.eps), int(body.niter),
+                                     float(body.tol), C.byref(bid)), self.h)
+        self.objects.append(("body", int(dS.size), int(body.niter)))
+        return bid.value
+
+    def step(self, nsteps=1):
+        t = C.c_double()
+        _check(lib.gks_step(self.h, int(nsteps), C.byref(t)), self.h)
+        return t.value
+
+    @property
+    def time(self):
+        t, dt = C.c_double(), C.c_double()
+        _check(lib.gks_get_time(self.h, C.byref(t), C.byref(dt)), self.h)
+        return t.value
+
+    @property
+    def last_dt(self):
+        t, dt = C.c_double(), C.c_double()
+        _check(lib.gks_get_time(self.h, C.byref(t), C.byref(dt)), self.h)
+        return dt.value
+
+    def set_time(self, t):
+        _check(lib.gks_set_time(self.h, float(t)), self.h)
+
+    def forces(self, oid):
+        kind, a, b = self.objects[oid]
+        out = ForcesOut()
+        if kind == "rotor":
+            pts = np.zeros(4 * a * b)
+            _check(lib.gks_forces(self.h, int(oid), C.byref(out), pts.ctypes.data_as(_dp)), self.h)
+            nb, npt = a, b
+            return {"thrust": np.array(out.thrust[:nb]), "torque": np.array(out.torque[:nb]),
+                    "power": out.power, "cp": out.cp, "ct": out.ct,
+                    "Fx": pts[:nb * npt].reshape(nb, npt), "Ft": pts[nb * npt:2 * nb * npt].reshape(nb, npt),
+                    "alpha": pts[2 * nb * npt:3 * nb * npt].reshape(nb, npt),
+                    "phi": pts[3 * nb * npt:].reshape(nb, npt)}
+        res = np.zeros(b)
+        _check(lib.gks_forces(self.h, int(oid), C.byref(out), res.ctypes.data_as(_dp)), self.h)
+        return {"force": np.array(out.body_force[:]), "iters": out.iters, "residual": out.residual,
+                "residual_history": res[:out.iters].copy()}
+
+    def diagnostics(self):
+        out = np.zeros(5)
+        _check(lib.gks_diagnostics(self.h, out.ctypes.data_as(_dp)), self.h)
+        return out
+
+    def save_state(self) -> bytes:
+        nb = C.c_size_t()
+        _check(lib.gks_checkpoint_bytes(self.h, C.byref(nb)), self.h)
+        buf = C.create_string_buffer(nb.value)
+        _check(lib.gks_save_state(self.h, buf, nb.value), self.h)
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib.gks_load_state(self.h, buf, len(blob)), self.h)
+
+    def profile_enable(self, timing=True):
+        _check(lib.gks_profile_enable(self.h, int(bool(timing))), self.h)
+
+    def profile_read(self):
+        out = ProfileOut()
+        _check(lib.gks_profile_read(self.h, C.byref(out)), self.h)
+        return {"launches": {lib.gks_kernel_group_name(k).decode(): out.launches[k]
+                             for k in range(NUM_KERNEL_GROUPS)},
+                "ms": {lib.gks_kernel_group_name(k).decode(): out.ms[k] for k in range(NUM_KERNEL_GROUPS)},
+                "total_launches": out.total_launches}
+
+    def layout(self):
+        out = (C.c_long * 7)()
+        _check(lib.gks_state_layout(self.h, out), self.h)
+        return list(out)

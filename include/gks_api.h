@@ -234,6 +234,32 @@ int gks_profile_enable(gks_grid *g, int timing_on);
 int gks_profile_read(gks_grid *g, gks_profile_out *out);
 const char *gks_kernel_group_name(int group);
 
+/* gks_diagnostics_noalloc: the same FP64 sums as gks_diagnostics (mass,
+ * momentum, kinetic energy, with cell volumes), for callers that cannot
+ * allocate device memory -- for example an application that owns all device
+ * memory through its own pool and does not let libraries allocate, or a
+ * process whose device-memory budget is already fully committed. The paper
+ * has no counterpart to this call. It allocates nothing: its scratch (one
+ * partial sum per block of 4096 cells) lives in a static device array of
+ * 512 KiB inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   d_state    device, 4 * N FP64 values (rho, rho U, rho V, rho W),
+ *              component-major, x fastest, N = nx ny nz (the layout of
+ *              gks_set_state, in device memory).
+ *   d_hx/hy/hz device, nx / ny / nz cell widths.
+ *   d_out      device, 5 doubles written by the call.
+ *   stream     cudaStream_t (as void*), NULL = legacy default stream.
+ * Returns GKS_ERR_ARG for null pointers, empty extents or more than
+ * 33,554,432 cells (the scratch limit), GKS_ERR_CUDA if a launch fails; the
+ * message is in gks_last_error(NULL). The work is asynchronous on stream.
+ * The first call on a device looks up the device address of the static
+ * scratch (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the one scratch array:
+ * calls that overlap on the GPU (in flight on different streams at once)
+ * race and must be serialised by the caller. */
+int gks_diagnostics_noalloc(const double *d_state, int nx, int ny, int nz, const double *d_hx,
+                            const double *d_hy, const double *d_hz, double *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgks.so")
-SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu"]
+SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu"]
 HEADERS = ["gks_internal.h", os.path.join(ROOT, "include", "gks_api.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

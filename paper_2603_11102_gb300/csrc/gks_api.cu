@@ -209,6 +209,8 @@ int cell_range(const Ctx &c, int a, double lo, double hi, int out[2])
 
 }  // namespace
 
+void gks::record_error(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 const char *gks_last_error(const gks_grid *g) { return g ? g->err.c_str() : g_err.c_str(); }

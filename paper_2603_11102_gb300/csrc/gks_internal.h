@@ -76,6 +76,9 @@ inline void mark(const Ctx &c, int group, int begin)
     if (c.mark) c.mark(c.mark_ctx, group, begin);
 }
 
+// Message returned by gks_last_error(NULL) on this thread (gks_api.cu).
+void record_error(const char *msg);
+
 // Launchers of the stencil path (gks_stencil.cu).
 void launch_prep(const Ctx &c);                        // FP32C: state -> wk0
 void launch_ghost(const Ctx &c, void *w);              // 3 ghost layers of w (working type)

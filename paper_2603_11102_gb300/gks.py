@@ -81,6 +81,8 @@ SIGNATURES = {
     "gks_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ProfileOut)]),
     "gks_kernel_group_name": (C.c_char_p, [C.c_int]),
+    "gks_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 lib = None

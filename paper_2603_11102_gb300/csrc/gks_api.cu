@@ -1,6 +1,8 @@
 // gks_api.cu -- host side of the C ABI declared in include/gks_api.h: grid
 // validation, carving of the caller-owned buffers, geometry tables, object
 // set-up, and the launch sequence of one S2O4 step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -63,7 +65,7 @@ struct Layout {
     size_t o_wk0 = 0, o_wk1 = 0, o_p = 0, o_fq = 0, o_ff[3] = {0, 0, 0};
     size_t o_ih[3], o_ihf[3], o_h64[3], o_part = 0, o_scal = 0, o_diag = 0;
     long np = 0, nfq = 0, nff[3] = {0, 0, 0};
-    int P[3];
+    int P[3], e1p[3];
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -99,10 +101,13 @@ void plan(const gks_grid_desc *d, Layout *L)
     L->nfq = 0;
     for (int a = 0; a < 3; ++a) {
         const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
-        const long nfq = (long)(d->n[a] + 1) * (d->n[t1] + 4) * (d->n[t2] + 4);
+        // rows of the face box padded to 16 bytes (tensor-map stride rule)
+        L->e1p[a] = (d->n[t1] + 4 + 3) / 4 * 4;
+        const long nfq = (long)(d->n[a] + 1) * (d->n[t2] + 4) * L->e1p[a];
         if (nfq > L->nfq) L->nfq = nfq;
         L->nff[a] = (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
     }
+    L->nfq = (L->nfq + 63) / 64 * 64;
     size_t o = 0;
     L->o_wk0 = o;
     if (d->precision == GKS_FP32C) o = align256(o + 4 * (size_t)L->np * 4);
@@ -305,9 +310,40 @@ int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_
         if (!rc) rc = upload<double>(g, c.h64[a], h);
         if (rc) { msg = g->err; delete g; return fail(nullptr, rc, msg); }
     }
+    // TMA descriptors of the face box, one per direction: dims (t1 padded,
+    // t2, face, component), box (36, 12, 1, 8)
+    {
+        PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&encode, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || !encode || q != cudaDriverEntryPointSuccess) {
+            msg = "cuTensorMapEncodeTiled not available";
+            delete g;
+            return fail(nullptr, GKS_ERR_CUDA, msg);
+        }
+        const cuuint64_t es = c.prec == GKS_FP64 ? 8 : 4;
+        for (int a = 0; a < 3; ++a) {
+            const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+            (void)t1;
+            c.e1p[a] = L.e1p[a];
+            const cuuint64_t dims[4] = {(cuuint64_t)L.e1p[a], (cuuint64_t)(c.n[t2] + 4), (cuuint64_t)(c.n[a] + 1), 8};
+            const cuuint64_t strides[3] = {dims[0] * es, dims[0] * dims[1] * es, (cuuint64_t)L.nfq * es};
+            const cuuint32_t box[4] = {36, 12, 1, 8};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUresult r = encode(&c.tmap[a], c.prec == GKS_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                4, c.fq, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                msg = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+                delete g;
+                return fail(nullptr, GKS_ERR_CUDA, msg);
+            }
+        }
+    }
     rc = cuda_check(g, cudaMemsetAsync(c.scal, 0, sizeof(Scalars), c.stream), "clear scalars");
     if (!rc) rc = cuda_check(g, cudaMemsetAsync(c.state, 0, L.state, c.stream), "clear state");
-    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w, 0, L.o_fq, c.stream), "clear work");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w, 0, L.o_ff[0], c.stream), "clear work");
     if (!rc) {
         launch_fill_rest(c);
         rc = check_launch(g, "fill state");
@@ -401,8 +437,14 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
     r.eps = d->eps;
     r.rho_inf = d->rho_inf;
     r.uref = d->u_inf_ref;
-    double rmax = 0.0;
-    for (int p = 0; p < np; ++p) rmax = fmax(rmax, fabs(d->r[p]));
+    double rmax = 0.0, rmin = INFINITY;
+    for (int p = 0; p < np; ++p) {
+        rmax = fmax(rmax, d->r[p]);
+        rmin = fmin(rmin, d->r[p]);
+    }
+    r.rmin = rmin;
+    r.rmax = rmax;
+    rmax = fmax(fabs(rmax), fabs(rmin));
     const double cut = 3.0 * d->eps;
     if (cell_range(c, 0, d->hub[0] - cut, d->hub[0] + cut, r.box[0]) ||
         cell_range(c, 1, d->hub[1] - rmax - cut, d->hub[1] + rmax + cut, r.box[1]) ||
@@ -550,6 +592,7 @@ int gks_step(gks_grid *g, int nsteps, double *t_out)
         if (sc.flags & FLAG_NONFINITE) return fail(g, GKS_ERR_NONFINITE, "non-finite value in the state");
         if (sc.flags & FLAG_RANGE) return fail(g, GKS_ERR_RANGE, "actuator point outside the sampled interior");
         if (sc.flags & FLAG_CFL) return fail(g, GKS_ERR_CFL, "fixed time step above the CFL limit");
+        if (sc.flags & FLAG_TIMEOUT) return fail(g, GKS_ERR_CUDA, "a device-side wait timed out");
     }
     return GKS_OK;
 }

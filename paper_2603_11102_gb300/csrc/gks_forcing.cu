@@ -232,12 +232,26 @@ __global__ void __launch_bounds__(256) alm_spread_kernel(Lattice L, void *S, Rot
     const R norm = (R)(1.0 / (r.eps * r.eps * r.eps * pow(kPi, 1.5)));
     R f[3] = {R(0), R(0), R(0)};
     bool any = false;
+    const float cut2f = (float)(cut * cut) * 1.0001f;
     for (int b = 0; b < r.nb; ++b) {
         const R e1 = (R)r.et[2 * b], e2 = (R)r.et[2 * b + 1];
+        // every point of blade b lies on the segment hub + s e_r, s in
+        // [rmin, rmax]; a cell farther than 3 eps from it gets nothing
+        {
+            const double ery = r.et[2 * b + 1], erz = -r.et[2 * b];
+            const double px = xc[0] - r.hub[0], py = xc[1] - r.hub[1], pz = xc[2] - r.hub[2];
+            double sp = py * ery + pz * erz;
+            sp = sp < r.rmin ? r.rmin : (sp > r.rmax ? r.rmax : sp);
+            const double qy = py - sp * ery, qz = pz - sp * erz;
+            if (px * px + qy * qy + qz * qz > cut * cut * (1.0 + 1e-6) + 1e-300) continue;
+        }
         R fb[3] = {R(0), R(0), R(0)};
         for (int p = 0; p < r.np; ++p) {
             const int q = b * r.np + p;
             const double dx = xc[0] - r.X[3 * q], dy = xc[1] - r.X[3 * q + 1], dz = xc[2] - r.X[3 * q + 2];
+            // FP32 screen, then the exact FP64 test near the cut
+            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+            if (fx * fx + fy * fy + fz * fz > cut2f) continue;
             const double rr = dist(dx, dy, dz);
             if (rr > cut) continue;
             any = true;
@@ -462,15 +476,15 @@ __global__ void ibm_check_kernel(BodyDev b, int s, double tol)
 }
 
 // force on the structure = - sum over box cells (fixed order), FP64
-__global__ void __launch_bounds__(256) ibm_force_kernel(BodyDev b)
+__global__ void __launch_bounds__(1024) ibm_force_kernel(BodyDev b)
 {
-    __shared__ double sh[3][256];
+    __shared__ double sh[3][1024];
     double s[3] = {0.0, 0.0, 0.0};
     for (long c = threadIdx.x; c < b.nbox; c += blockDim.x)
         for (int d = 0; d < 3; ++d) s[d] += b.fsum[3 * c + d];
     for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = s[d];
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = 512; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
             for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
         __syncthreads();
@@ -564,7 +578,7 @@ void launch_ibm(const Ctx &c, const BodyDev &b)
         mark(c, K_IBM, 0);
     }
     mark(c, K_IBM, 1);
-    ibm_force_kernel<<<1, 256, 0, c.stream>>>(b);
+    ibm_force_kernel<<<1, 1024, 0, c.stream>>>(b);
     mark(c, K_IBM, 0);
 }
 

@@ -2,6 +2,7 @@
 // (host context, device-resident scalars, kernel launchers). Not installed.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -14,7 +15,7 @@ namespace gks {
 constexpr int G = 3;              // ghost layers (WENO5 needs 3)
 constexpr int kMaxPartials = 1024;
 
-enum : int { FLAG_NONFINITE = 1, FLAG_CFL = 2, FLAG_RANGE = 4 };
+enum : int { FLAG_NONFINITE = 1, FLAG_CFL = 2, FLAG_RANGE = 4, FLAG_TIMEOUT = 8 };
 
 // Kernel groups for the optional per-launch event timing (gks_profile_*).
 enum : int {
@@ -56,6 +57,8 @@ struct Ctx {
     void *pbuf;               // P = W + dt L + dt^2/6 Lt (FP64 double[4][np]; FP32C hi/lo)
     void *fq;                 // face equilibrium state + normal slope, R[8][nfq]
     long nfq;
+    int e1p[3];               // padded t1 extent of the face box per direction (multiple of 4)
+    CUtensorMap tmap[3];      // TMA descriptors of the face box per direction
     void *ff[3];              // face-averaged F0 and F1 per direction, R[8][nff]
     long nff[3];
     void *ih[3];              // R: inverse cell widths, padded index i + 3
@@ -95,6 +98,7 @@ void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored ar
 struct RotorDev {
     int nb, np, correction;
     double hub[3], omega, az0, radius, eps, rho_inf, uref;
+    double rmin, rmax;  // smallest and largest point radius
     double *r, *chord, *twist, *width, *scale;  // device arrays
     double *X;          // 3 nb np positions of the last step
     double *F;          // 4 nb np: F_x, F_th, alpha, phi

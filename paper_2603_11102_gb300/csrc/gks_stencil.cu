@@ -44,6 +44,12 @@ Phys<R> make_phys(const Ctx &c)
     return p;
 }
 
+// Division in the working type: IEEE division in FP64; the two-instruction
+// approximate division (2 ulp) in FP32, whose error is far below the FP32
+// rounding of the stencil itself.
+__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
+
 // Direction d: normal axis d, tangential axes t1, t2.
 __host__ __device__ inline int tan1(int d) { return d == 0 ? 1 : 0; }
 __host__ __device__ inline int tan2(int d) { return d == 2 ? 1 : 2; }
@@ -157,7 +163,7 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
     R s2 = R(1e-6) + (c13 * t * t + q * u * u);
     s0 *= s0; s1 *= s1; s2 *= s2;
     const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
-    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+    return wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
 }
 
 template <typename R>
@@ -168,6 +174,7 @@ struct FaceEqArgs {
     long nfq;
     const R *ihf;    // inverse centre distance at faces of axis d
     int n1, n2;      // interior cells along t1, t2
+    int e1p;         // row stride of the face box (n1 + 4 rounded up to 4)
     long sd, s1, s2; // element strides along d, t1, t2
     int cn, c1, c2;  // state component of the normal / t1 / t2 momentum
     Phys<R> ph;
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
     // right one; written on rho - off
     const Phys<R> &ph = A.ph;
     const R rl = ph.off + Ql[0], rr = ph.off + Qr[0];
-    const R Ul = Ql[1] / rl, Ur = Qr[1] / rr;
+    const R Ul = wdiv(Ql[1], rl), Ur = wdiv(Qr[1], rr);
     const R el = erf(ph.sqlam * Ul), er = erf(ph.sqlam * Ur);
     const R Pl = R(0.5) + R(0.5) * el;   // <u^0>_{u>0} of the left state
     const R Pr = R(0.5) - R(0.5) * er;   // <u^0>_{u<0} of the right state
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
     // normal slope at the face: derivative of the quartic through Q0 and the
     // cell averages f-2..f+1 (the face value drops out)
     const R s = A.ihf[f] * R(1.0 / 12.0);
-    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * (A.n1 + 4) + (a + 2);
+    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         A.fq[v * A.nfq + o] = Q0[v];
@@ -238,7 +245,7 @@ __device__ __forceinline__ void tan_val(R qm2, R qm1, R q0, R qp1, R qp2, R &vm,
 {
     const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
     const R a1 = qp1 - qm1, a2 = qp2 - qm2;
-    const R E = q0 + (d1 * R(1.0 / 1080.0) - d2 * R(1.0 / 4320.0));
+    const R E = fma(d1, R(1.0 / 1080.0), fma(d2, R(-1.0 / 4320.0), q0));
     const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
     vm = E - O;
     vp = E + O;
@@ -250,7 +257,7 @@ __device__ __forceinline__ void tan_val_der(R qm2, R qm1, R q0, R qp1, R qp2, R 
 {
     const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
     const R a1 = qp1 - qm1, a2 = qp2 - qm2;
-    const R E = q0 + (d1 * R(1.0 / 1080.0) - d2 * R(1.0 / 4320.0));
+    const R E = fma(d1, R(1.0 / 1080.0), fma(d2, R(-1.0 / 4320.0), q0));
     const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
     const R Do = R(2.0 / 3.0) * a1 - R(1.0 / 12.0) * a2;
     const R De = R(0.41697519441472974) * d1 - R(0.032075014954979206) * d2;
@@ -270,20 +277,23 @@ __device__ __forceinline__ void tan_val_der(R qm2, R qm1, R q0, R qp1, R qp2, R 
 //   F0 = (m_n, m_n U_k + p' delta_nk - mu (d_n U_k + d_k U_n)),
 //   F1 = rho (A0 U_n + theta A_n, A0 (U_n U_k + theta delta_nk) + theta (A_k U_n + A_n U_k)),
 // with p' = theta (rho - off): the constant theta off cancels in L.
+// D1 and D2 are index-space tangential slopes; ih1, ih2 turn them into
+// physical ones.
 template <typename R, bool NEED_F0>
-__device__ __forceinline__ void gk_flux(const Phys<R> &ph, const R q[4], const R Dn[4],
-                                        const R D1[4], const R D2[4], R F0[4], R F1[4])
+__device__ __forceinline__ void gk_flux(const Phys<R> &ph, const R q[4], const R Dn[4], const R D1[4],
+                                        const R D2[4], R ih1, R ih2, R F0[4], R F1[4])
 {
     const R rho = ph.off + q[0];
-    const R inv = R(1) / rho;
+    const R inv = wdiv(R(1), rho);
+    const R inv1 = inv * ih1, inv2 = inv * ih2;
     const R U0 = q[1] * inv, U1 = q[2] * inv, U2 = q[3] * inv;
-    const R g0 = Dn[0] * inv, g1 = D1[0] * inv, g2 = D2[0] * inv;
+    const R g0 = Dn[0] * inv, g1 = D1[0] * inv1, g2 = D2[0] * inv2;
     const R G00 = (Dn[1] - U0 * Dn[0]) * inv, G01 = (Dn[2] - U1 * Dn[0]) * inv,
             G02 = (Dn[3] - U2 * Dn[0]) * inv;
-    const R G10 = (D1[1] - U0 * D1[0]) * inv, G11 = (D1[2] - U1 * D1[0]) * inv,
-            G12 = (D1[3] - U2 * D1[0]) * inv;
-    const R G20 = (D2[1] - U0 * D2[0]) * inv, G21 = (D2[2] - U1 * D2[0]) * inv,
-            G22 = (D2[3] - U2 * D2[0]) * inv;
+    const R G10 = (D1[1] - U0 * D1[0]) * inv1, G11 = (D1[2] - U1 * D1[0]) * inv1,
+            G12 = (D1[3] - U2 * D1[0]) * inv1;
+    const R G20 = (D2[1] - U0 * D2[0]) * inv2, G21 = (D2[2] - U1 * D2[0]) * inv2,
+            G22 = (D2[3] - U2 * D2[0]) * inv2;
     const R th = ph.theta, tl = R(2) * ph.lambda;
     const R A0 = -(U0 * g0 + U1 * g1 + U2 * g2) - (G00 + G11 + G22);
     const R An = -g0 - tl * (U0 * G00 + U1 * G10 + U2 * G20);
@@ -308,98 +318,184 @@ constexpr int ST_ROWS = SQ_H * TX;          // rows of the t1 pass
 constexpr int ST_N = 24 * ST_ROWS;
 
 template <typename R>
+constexpr size_t flux_smem_bytes()
+{
+    return (size_t)(2 * SQ_N + ST_N) * sizeof(R) + 2 * sizeof(unsigned long long);
+}
+
+template <typename R>
 struct FluxArgs {
-    const R *fq;
-    long nfq;
     R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
     long nff;
     const R *ih1, *ih2;  // inverse cell widths along t1, t2 (padded index)
-    int n1, n2;
+    int n1, n2, nf;
     int gcomp[4];        // global component of local component 0..3
     Phys<R> ph;
+    Scalars *scal;
 };
 
-template <typename R, bool NEED_F0>
-__global__ void __launch_bounds__(256) face_flux_kernel(FluxArgs<R> A)
+// ---- TMA and mbarrier helpers (sm_90+ PTX) ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sq = reinterpret_cast<R *>(smem_raw);
-    R *st = sq + SQ_N;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One bulk tensor copy of the (TX+4) x (TY+4) x 1 x 8 face box starting at
+// (c0, c1, c2, 0) into dst; completion is signalled on bar with the byte
+// count.
+__device__ __forceinline__ void tma_load_tile(const CUtensorMap *map, void *dst, uint64_t *bar, int c0, int c1,
+                                              int c2, uint32_t bytes)
+{
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(b)
+        : "memory");
+}
+
+// Wait for phase `parity` of bar; gives up after ~1 s of SM clock and
+// returns false (the caller raises FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t b = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
+
+// Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
+// box of the next tile is fetched by TMA into the other buffer while the
+// current one is computed.
+template <typename R, bool NEED_F0>
+__global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
+    R *st = sqb + 2 * SQ_N;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY, f = blockIdx.z;
-    const int e1 = A.n1 + 4, e2 = A.n2 + 4;
-
-    // (1) Q0 and its normal slope on the (TX+4) x (TY+4) tile of faces
-    for (int idx = tid; idx < SQ_N; idx += TX * TY) {
-        const int cc = idx / (SQ_H * SQ_W);
-        const int rem = idx - cc * (SQ_H * SQ_W);
-        const int r = rem / SQ_W, col = rem - r * SQ_W;
-        const int sa = a0 + col, sb = b0 + r;
-        R v = R(0);
-        if (sa < e1 && sb < e2) v = __ldg(A.fq + cc * A.nfq + ((long)f * e2 + sb) * e1 + sa);
-        sq[idx] = v;
+    const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
+    const long ntiles = (long)NA * NB * A.nf;
+    const uint32_t bytes = (uint32_t)(SQ_N * sizeof(R));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
-
-    // (2) t1 pass: values and t1-derivatives of Q0, values of the normal
-    //     slope, at the two t1 Gauss points, for every row of the tile
-    for (int idx = tid; idx < ST_ROWS; idx += TX * TY) {
-        const int r = idx / TX, col = idx - r * TX;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const R *p = sq + (v * SQ_H + r) * SQ_W + col;
-            R vm, vp, dm, dp;
-            tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
-            st[(v * 4 + 0) * ST_ROWS + idx] = vm;
-            st[(v * 4 + 1) * ST_ROWS + idx] = vp;
-            st[(v * 4 + 2) * ST_ROWS + idx] = dm;
-            st[(v * 4 + 3) * ST_ROWS + idx] = dp;
-            const R *pn = sq + ((4 + v) * SQ_H + r) * SQ_W + col;
-            tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
-            st[(16 + v * 2 + 0) * ST_ROWS + idx] = vm;
-            st[(16 + v * 2 + 1) * ST_ROWS + idx] = vp;
-        }
+    long t = blockIdx.x;
+    if (tid == 0 && t < ntiles) {
+        const int ta = (int)(t % NA), tb = (int)((t / NA) % NB), f = (int)(t / ((long)NA * NB));
+        tma_load_tile(&tmap, sqb, &bar[0], ta * TX, tb * TY, f, bytes);
     }
-    __syncthreads();
-
-    const int a = a0 + tx, b = b0 + ty;
-    if (a >= A.n1 || b >= A.n2) return;
-    const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
-    R acc0[4] = {R(0), R(0), R(0), R(0)}, acc1[4] = {R(0), R(0), R(0), R(0)};
-
-    // (3) t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g)
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        R Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const R *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
-            const R *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
-            const R *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
-            R vm, vp, dm, dp;
-            tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
-            Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm * ih2; D2[1][v] = dp * ih2;
-            tan_val(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
-            D1[0][v] = vm * ih1; D1[1][v] = vp * ih1;
-            tan_val(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
-            Dn[0][v] = vm; Dn[1][v] = vp;
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const long tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            const int ta = (int)(tn % NA), tb = (int)((tn / NA) % NB), f = (int)(tn / ((long)NA * NB));
+            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], ta * TX, tb * TY, f, bytes);
         }
-#pragma unroll
-        for (int nn = 0; nn < 2; ++nn) {
-            R F0[4], F1[4];
-            gk_flux<R, NEED_F0>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], F0, F1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&A.scal->flags, FLAG_TIMEOUT);
+                if (tn < ntiles) mbar_wait(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        const R *sq = sqb + buf * SQ_N;
+        const int ta = (int)(t % NA), tb = (int)((t / NA) % NB), f = (int)(t / ((long)NA * NB));
+        const int a0 = ta * TX, b0 = tb * TY;
+
+        // t1 pass: values and t1-derivatives of Q0, values of the normal
+        // slope, at the two t1 Gauss points, for every row of the tile
+        for (int idx = tid; idx < ST_ROWS; idx += TX * TY) {
+            const int r = idx / TX, col = idx - r * TX;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                if (NEED_F0) acc0[v] += F0[v];
-                acc1[v] += F1[v];
+                const R *p = sq + (v * SQ_H + r) * SQ_W + col;
+                R vm, vp, dm, dp;
+                tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
+                st[(v * 4 + 0) * ST_ROWS + idx] = vm;
+                st[(v * 4 + 1) * ST_ROWS + idx] = vp;
+                st[(v * 4 + 2) * ST_ROWS + idx] = dm;
+                st[(v * 4 + 3) * ST_ROWS + idx] = dp;
+                const R *pn = sq + ((4 + v) * SQ_H + r) * SQ_W + col;
+                tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
+                st[(16 + v * 2 + 0) * ST_ROWS + idx] = vm;
+                st[(16 + v * 2 + 1) * ST_ROWS + idx] = vp;
             }
         }
-    }
-    const long o = ((long)f * A.n2 + b) * A.n1 + a;
+        __syncthreads();
+
+        const int a = a0 + tx, b = b0 + ty;
+        if (a < A.n1 && b < A.n2) {
+            const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
+            R acc0[4] = {R(0), R(0), R(0), R(0)}, acc1[4] = {R(0), R(0), R(0), R(0)};
+            // t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
-        A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * acc1[v];
+            for (int m = 0; m < 2; ++m) {
+                R Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const R *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+                    const R *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+                    const R *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+                    R vm, vp, dm, dp;
+                    tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
+                    Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
+                    tan_val(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+                    D1[0][v] = vm; D1[1][v] = vp;
+                    tan_val(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+                    Dn[0][v] = vm; Dn[1][v] = vp;
+                }
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    R F0[4], F1[4];
+                    gk_flux<R, NEED_F0>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, F0, F1);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        if (NEED_F0) acc0[v] += F0[v];
+                        acc1[v] += F1[v];
+                    }
+                }
+            }
+            const long o = ((long)f * A.n2 + b) * A.n1 + a;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
+                A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * acc1[v];
+            }
+        }
+        __syncthreads();   // st and this buffer are free again
     }
 }
 
@@ -436,12 +532,27 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
 template <typename R, int STAGE>
 __global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
 {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-    if (i >= A.n[0] || j >= A.n[1]) return;
+    // x-face fluxes are stored y-fastest ([x][z][y]); the block's 33 x-faces
+    // by 8 y rows are staged through shared memory so that every global read
+    // of the kernel is a full sector.
+    constexpr int NC = STAGE == 1 ? 8 : 4;
+    __shared__ R sx[NC][33][9];
     const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8, k = blockIdx.z;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int e = tid; e < NC * 33 * 8; e += 256) {
+        const int cc = e / (33 * 8), rem = e - cc * 33 * 8, f = rem >> 3, jj = rem & 7;
+        const int comp = STAGE == 1 ? cc : 4 + cc;
+        R v = R(0);
+        if (i0 + f <= nx && j0 + jj < ny)
+            v = __ldg(A.ff[0] + comp * A.nff[0] + ((long)(i0 + f) * nz + k) * ny + j0 + jj);
+        sx[cc][f][jj] = v;
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i >= nx || j >= ny) return;
     const long lin = (long)(i + G) + (long)A.P[0] * ((long)(j + G) + (long)A.P[1] * (k + G));
     const R ihx = __ldg(A.ih[0] + i + G), ihy = __ldg(A.ih[1] + j + G), ihz = __ldg(A.ih[2] + k + G);
-    const long ix = ((long)i * nz + k) * ny + j, sx = (long)nz * ny;
     const long iy = ((long)j * nz + k) * nx + i, sy = (long)nz * nx;
     const long iz = ((long)k * ny + j) * nx + i, sz = (long)ny * nx;
     const double dt = A.scal->dt;
@@ -449,17 +560,16 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        const R *fx = A.ff[0] + (4 + v) * A.nff[0];
+        const int cx = STAGE == 1 ? 4 + v : v;
         const R *fy = A.ff[1] + (4 + v) * A.nff[1];
         const R *fz = A.ff[2] + (4 + v) * A.nff[2];
-        const R Lt = -((__ldg(fx + ix + sx) - __ldg(fx + ix)) * ihx +
+        const R Lt = -((sx[cx][threadIdx.x + 1][threadIdx.y] - sx[cx][threadIdx.x][threadIdx.y]) * ihx +
                        (__ldg(fy + iy + sy) - __ldg(fy + iy)) * ihy +
                        (__ldg(fz + iz + sz) - __ldg(fz + iz)) * ihz);
         if (STAGE == 1) {
-            const R *gx = A.ff[0] + v * A.nff[0];
             const R *gy = A.ff[1] + v * A.nff[1];
             const R *gz = A.ff[2] + v * A.nff[2];
-            const R L = -((__ldg(gx + ix + sx) - __ldg(gx + ix)) * ihx +
+            const R L = -((sx[v][threadIdx.x + 1][threadIdx.y] - sx[v][threadIdx.x][threadIdx.y]) * ihx +
                           (__ldg(gy + iy + sy) - __ldg(gy + iy)) * ihy +
                           (__ldg(gz + iz + sz) - __ldg(gz + iz)) * ihz);
             if constexpr (std::is_same<R, double>::value) {
@@ -499,20 +609,36 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
 }
 
 template <typename R>
+int flux_grid(int stage)
+{
+    // persistent grid: resident blocks per SM x SMs (computed once per type)
+    static int blocks[2] = {0, 0};
+    const int s = stage == 1 ? 0 : 1;
+    if (!blocks[s]) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t smem = flux_smem_bytes<R>();
+        if (stage == 1) {
+            cudaFuncSetAttribute(face_flux_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, face_flux_kernel<R, true>, TX * TY, smem);
+        } else {
+            cudaFuncSetAttribute(face_flux_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, face_flux_kernel<R, false>, TX * TY, smem);
+        }
+        blocks[s] = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks[s];
+}
+
+template <typename R>
 void stage_impl(const Ctx &c, int stage)
 {
     const Phys<R> ph = make_phys<R>(c);
     const R *w = (const R *)(stage == 1 ? c.wk0 : c.wk1);
     const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
-    const size_t smem = (size_t)(SQ_N + ST_N) * sizeof(R);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(face_flux_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaFuncSetAttribute(face_flux_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr_done = true;
-    }
+    const size_t smem = flux_smem_bytes<R>();
+    const int gmax = flux_grid<R>(stage);
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
         FaceEqArgs<R> E;
@@ -523,6 +649,7 @@ void stage_impl(const Ctx &c, int stage)
         E.ihf = (const R *)c.ihf[d];
         E.n1 = c.n[t1];
         E.n2 = c.n[t2];
+        E.e1p = c.e1p[d];
         E.sd = stride[d];
         E.s1 = stride[t1];
         E.s2 = stride[t2];
@@ -537,25 +664,26 @@ void stage_impl(const Ctx &c, int stage)
         mark(c, K_FACE_EQ, 0);
 
         FluxArgs<R> F;
-        F.fq = (const R *)c.fq;
-        F.nfq = c.nfq;
         F.ff = (R *)c.ff[d];
         F.nff = c.nff[d];
         F.ih1 = (const R *)c.ih[t1];
         F.ih2 = (const R *)c.ih[t2];
         F.n1 = c.n[t1];
         F.n2 = c.n[t2];
+        F.nf = c.n[d] + 1;
         F.gcomp[0] = 0;
         F.gcomp[1] = 1 + d;
         F.gcomp[2] = 1 + t1;
         F.gcomp[3] = 1 + t2;
         F.ph = ph;
-        dim3 gf((F.n1 + TX - 1) / TX, (F.n2 + TY - 1) / TY, c.n[d] + 1);
+        F.scal = c.scal;
+        const long ntiles = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY) * F.nf;
+        const int grid = (int)(ntiles < gmax ? ntiles : gmax);
         mark(c, K_FACE_FLUX, 1);
         if (stage == 1)
-            face_flux_kernel<R, true><<<gf, blk, smem, c.stream>>>(F);
+            face_flux_kernel<R, true><<<grid, blk, smem, c.stream>>>(c.tmap[d], F);
         else
-            face_flux_kernel<R, false><<<gf, blk, smem, c.stream>>>(F);
+            face_flux_kernel<R, false><<<grid, blk, smem, c.stream>>>(c.tmap[d], F);
         mark(c, K_FACE_FLUX, 0);
     }
     UpdArgs<R> U;

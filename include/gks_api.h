@@ -218,6 +218,38 @@ int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes);
  * a*out[5] + (i+3) + out[0]*((j+3) + out[1]*(k+3)). */
 int gks_state_layout(const gks_grid *g, long out[7]);
 
+/* Device-side state exchange: the same compact FP64 layout as
+ * gks_set_state / gks_get_state (4 * N values, component-major, x fastest),
+ * in device memory. Asynchronous on the grid's stream. */
+int gks_set_state_device(gks_grid *g, const double *d_state);
+int gks_get_state_device(gks_grid *g, double *d_state);
+
+/* Adjoint of one step (reverse mode, FP64): for a functional J of the state
+ * after the step, given lambda^{n+1} = dJ/dW^{n+1}, computes
+ * lambda^n = dJ/dW^n (through the ghost fill, both S2O4 stages with their
+ * WENO5 reconstruction, equilibrium state, tangential Gauss-point
+ * reconstruction and gas-kinetic flux (Sec. 2, Appendix), and the ALM
+ * sampling, loads and Gaussian projection (Sec. 3.1)), and adds to
+ * *h_grad_scales (n_blades * n_pts, rotor 0) the gradient with respect to
+ * the per-point force scales and to *h_grad_uinf the gradient with respect
+ * to the inflow speed u (the x velocity of gks_set_inflow), both through
+ * this step only. power_seed is dJ/dP for the rotor power P of this step.
+ *   d_adj_work  device workspace of gks_adjoint_workspace_bytes bytes
+ *               (256-byte aligned, caller-owned);
+ *   t_n         time at the start of the step;
+ *   d_state_n   device, W^n (compact FP64 layout);
+ *   d_adj_np1   device, lambda^{n+1} (compact FP64);
+ *   d_adj_n     device, receives lambda^n (compact FP64; may not alias the
+ *               inputs).
+ * The forward step is recomputed from d_state_n inside the call; the grid's
+ * own state is not changed. Requires a GKS_FP64 grid with a fixed time step,
+ * at most one rotor without the velocity correction and no immersed body
+ * (GKS_ERR_STATE otherwise). Synchronises the stream. */
+int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes);
+int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n,
+                     const double *d_adj_np1, double *d_adj_n, double power_seed,
+                     double *h_grad_scales, double *h_grad_uinf);
+
 /* Kernel accounting of the library's own kernels. Every kernel launch is
  * counted per group (0 prep, 1 ghost, 2 cfl, 3 face_eq, 4 face_flux,
  * 5 update, 6 alm, 7 ibm, 8 misc); with timing enabled each launch is also

@@ -1,0 +1,108 @@
+"""Gradients of a wake and power objective through the hand-written adjoint.
+
+The objective of a rotor run of N fixed-dt steps from a uniform stream U_inf:
+
+    J(s, U_inf) = mean over the cells of the plane x-index `iplane` of
+                  (U_inf - rho U / rho) after the last step  +  beta * P_N,
+
+with s the per-actuator-point force scales and P_N the rotor power of the
+last step. :class:`RotorObjective` is a ``torch.autograd.Function``: the
+forward pass runs the CUDA steps and keeps the state every K steps; the
+backward pass recomputes each segment from its checkpoint and runs
+``gks_step_adjoint`` backwards through it (checkpointed recomputation). The
+state and adjoint stay on the device; the objective's own seed
+(dJ/dW after the last step) is formed with torch.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+
+def uniform_state(grid, uinf, rho=1.0):
+    Q = torch.zeros(grid.shape, dtype=torch.float64, device=grid.device)
+    Q[0] = rho
+    Q[1] = rho * uinf
+    return Q
+
+
+def plane_deficit(state, iplane, uinf):
+    u = state[1, :, :, iplane] / state[0, :, :, iplane]
+    return float((uinf - u).mean().item())
+
+
+def plane_deficit_seed(state, iplane):
+    """dJ/dW of the plane-mean deficit term."""
+    lam = torch.zeros_like(state)
+    rho = state[0, :, :, iplane]
+    mx = state[1, :, :, iplane]
+    n = rho.numel()
+    lam[1, :, :, iplane] = -1.0 / (n * rho)
+    lam[0, :, :, iplane] = mx / (n * rho * rho)
+    return lam
+
+
+class RotorObjective(torch.autograd.Function):
+    """J(scales, uinf) for a configured FP64 grid with one rotor and a fixed
+    time step. Arguments after uinf are not differentiated: grid, nsteps,
+    checkpoint interval K, plane index, power weight beta."""
+
+    @staticmethod
+    def forward(ctx, scales, uinf, grid, nsteps, K, iplane, beta):
+        u = float(uinf.item())
+        grid.set_force_scales(0, scales.detach().cpu().numpy())
+        grid.set_inflow(1.0, u, 0.0, 0.0)
+        grid.set_state_tensor(uniform_state(grid, u))
+        grid.set_time(0.0)
+        dt = grid.dt_fixed
+        ckpts = {0: uniform_state(grid, u)}
+        for n in range(nsteps):
+            grid.step(1)
+            if (n + 1) % K == 0 and n + 1 < nsteps:
+                ckpts[n + 1] = grid.state_tensor()
+        WN = grid.state_tensor()
+        P = grid.forces(0)["power"]
+        J = plane_deficit(WN, iplane, u) + beta * P
+        ctx.grid, ctx.nsteps, ctx.K, ctx.iplane, ctx.beta, ctx.u, ctx.dt = grid, nsteps, K, iplane, beta, u, dt
+        ctx.ckpts, ctx.WN = ckpts, WN
+        ctx.nscales = scales.numel()
+        return torch.tensor(J, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        g, N, K, dt = ctx.grid, ctx.nsteps, ctx.K, ctx.dt
+        work = g.adjoint_workspace()
+        lam = plane_deficit_seed(ctx.WN, ctx.iplane)
+        gs = np.zeros(ctx.nscales)
+        gu = 0.0
+        starts = sorted(ctx.ckpts)
+        for si in range(len(starts) - 1, -1, -1):
+            k0 = starts[si]
+            k1 = starts[si + 1] if si + 1 < len(starts) else N
+            # recompute the segment's states from its checkpoint
+            g.set_state_tensor(ctx.ckpts[k0])
+            g.set_time(k0 * dt)
+            states = [ctx.ckpts[k0]]
+            for _ in range(k0, k1 - 1):
+                g.step(1)
+                states.append(g.state_tensor())
+            for n in range(k1 - 1, k0 - 1, -1):
+                seed = ctx.beta if n == N - 1 else 0.0
+                lam, gun = g.step_adjoint(work, n * dt, states[n - k0], lam, seed, gs)
+                gu += gun
+        # the initial state (rho, rho U_inf, 0, 0) and the explicit U_inf of J
+        gu += float(lam[1].sum().item()) + 1.0
+        gJ = float(gJ)
+        return (torch.from_numpy(gs * gJ), torch.tensor(gu * gJ, dtype=torch.float64),
+                None, None, None, None, None)
+
+
+def rotor_objective(grid, scales, uinf, nsteps, K=20, iplane=None, beta=1.0):
+    """J as a differentiable function of (scales, uinf) (float64 CPU tensors
+    with requires_grad); the grid must be an FP64 grid with one rotor and
+    dt_fixed > 0."""
+    if iplane is None:
+        raise ValueError("iplane (x index of the sampling plane) is required")
+    if scales.dtype != torch.float64 or uinf.dtype != torch.float64:
+        raise TypeError("scales and uinf must be float64 tensors (FP64 adjoint)")
+    return RotorObjective.apply(scales, uinf, grid, int(nsteps), int(K), int(iplane), float(beta))

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgks.so")
-SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu"]
-HEADERS = ["gks_internal.h", os.path.join(ROOT, "include", "gks_api.h")]
+SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu", "gks_adjoint.cu"]
+HEADERS = ["gks_internal.h", "gks_device.cuh", os.path.join(ROOT, "include", "gks_api.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

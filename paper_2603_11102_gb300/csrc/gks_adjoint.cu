@@ -1,0 +1,941 @@
+// gks_adjoint.cu -- hand-written reverse mode (adjoint) of one S2O4 step in
+// FP64, for gradients of a functional of the state with respect to the
+// per-point actuator force scales and the inflow speed.
+//
+// The forward step (Sec. 2 and Sec. 3.3) is a composition of
+//   ghost fill G, spatial operator (L, Lt) = S(A) per direction d
+//   [face state: WENO5 + half-space equilibrium + normal slope;
+//    face flux: tangential quartic to the Gauss points + closed-form flux;
+//    divergence], the two stage combinations, and the ALM forcing
+//   [trilinear sample, loads, truncated-Gaussian projection].
+// Its adjoint runs the pieces backwards. Every transposed stencil is written
+// as a gather (each output sums its inputs in a fixed order), so the adjoint
+// is deterministic and uses no atomics on the state:
+//   RA  per interior face: recompute the Gauss-point inputs, reverse the
+//       flux, write the 64 Gauss-input adjoints;
+//   RB  t2 transpose: Gauss adjoints -> adjoints of the t1-pass rows;
+//   RC  t1 transpose: rows -> adjoints of Q0 and its normal slope per face;
+//   RD  per face: recompute WENO5 and the equilibrium, reverse them and the
+//       normal slope -> adjoints of the 6 cells of the face's stencil;
+//   RE  per cell: gather the 6 faces whose stencil holds the cell;
+//   ghost adjoint: axes z, y, x, one launch per side and layer, each ghost
+//       adjoint added to its source cell (Riemann inflow through its
+//       Jacobian; its U_inf sensitivity stored per ghost and reduced in a
+//       fixed order).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "gks_device.cuh"
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+using namespace dev;
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kS3 = 1.7320508075688772935;
+
+// Explicit 5-point weights (offsets -2..2) of the tangential quartic at the
+// Gauss points -g (index 0) and +g (index 1): values WV and derivatives WD.
+__device__ __constant__ double cWV[2][5] = {
+    {-1.0 / 4320.0 - 7.0 * kS3 / 432.0, 1.0 / 1080.0 + 25.0 * kS3 / 216.0, 719.0 / 720.0,
+     1.0 / 1080.0 - 25.0 * kS3 / 216.0, -1.0 / 4320.0 + 7.0 * kS3 / 432.0},
+    {-1.0 / 4320.0 + 7.0 * kS3 / 432.0, 1.0 / 1080.0 - 25.0 * kS3 / 216.0, 719.0 / 720.0,
+     1.0 / 1080.0 + 25.0 * kS3 / 216.0, -1.0 / 4320.0 - 7.0 * kS3 / 432.0}};
+__device__ __constant__ double cWD[2][5] = {
+    {1.0 / 12.0 + kS3 / 54.0, -2.0 / 3.0 - 13.0 * kS3 / 54.0, 4.0 * kS3 / 9.0, 2.0 / 3.0 - 13.0 * kS3 / 54.0,
+     -1.0 / 12.0 + kS3 / 54.0},
+    {1.0 / 12.0 - kS3 / 54.0, -2.0 / 3.0 + 13.0 * kS3 / 54.0, -4.0 * kS3 / 9.0, 2.0 / 3.0 + 13.0 * kS3 / 54.0,
+     -1.0 / 12.0 - kS3 / 54.0}};
+
+__device__ __forceinline__ long lin(const int P0, const int P1, int i, int j, int k)
+{
+    return (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+}
+
+// ------------------------------------------------------ reverse building blocks
+
+// Adjoint of dev::gk_flux: given the adjoints of F0 (if needF0) and F1,
+// accumulate the adjoints of its inputs (index-space tangential slopes).
+__device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const double Dn[4], const double D1[4],
+                            const double D2[4], double ih1, double ih2, const double lF0[4], const double lF1[4],
+                            bool needF0, double qb[4], double Dnb[4], double D1b[4], double D2b[4])
+{
+    const double rho = ph.off + q[0];
+    const double inv = 1.0 / rho;
+    const double invi[3] = {inv, inv * ih1, inv * ih2};
+    const double *D[3] = {Dn, D1, D2};
+    const double U[3] = {q[1] * inv, q[2] * inv, q[3] * inv};
+    double g[3], Gm[3][3];
+    for (int i = 0; i < 3; ++i) {
+        g[i] = D[i][0] * invi[i];
+        for (int j = 0; j < 3; ++j) Gm[i][j] = (D[i][j + 1] - U[j] * D[i][0]) * invi[i];
+    }
+    const double th = ph.theta, tl = 2.0 * ph.lambda, mu = ph.mu;
+    const double A0 = -(U[0] * g[0] + U[1] * g[1] + U[2] * g[2]) - (Gm[0][0] + Gm[1][1] + Gm[2][2]);
+    double A[3];
+    for (int k = 0; k < 3; ++k) A[k] = -g[k] - tl * (U[0] * Gm[0][k] + U[1] * Gm[1][k] + U[2] * Gm[2][k]);
+
+    double rhob = 0.0, Ub[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, Gb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double A0b = 0.0, Ab[3] = {0, 0, 0}, qd[4] = {0, 0, 0, 0};
+    // F1[0] = rho (A0 U0 + th A_0)
+    {
+        const double T0 = A0 * U[0] + th * A[0];
+        rhob += lF1[0] * T0;
+        const double T0b = lF1[0] * rho;
+        A0b += T0b * U[0];
+        Ub[0] += T0b * A0;
+        Ab[0] += T0b * th;
+    }
+    // F1[1+k] = rho (A0 (U0 U_k + th d_k0) + th (A_k U0 + A_0 U_k))
+    for (int k = 0; k < 3; ++k) {
+        const double c = U[0] * U[k] + (k == 0 ? th : 0.0);
+        const double Tk = A0 * c + th * (A[k] * U[0] + A[0] * U[k]);
+        rhob += lF1[1 + k] * Tk;
+        const double Tb = lF1[1 + k] * rho;
+        A0b += Tb * c;
+        Ub[0] += Tb * A0 * U[k];
+        Ub[k] += Tb * A0 * U[0];
+        Ab[k] += Tb * th * U[0];
+        Ub[0] += Tb * th * A[k];
+        Ab[0] += Tb * th * U[k];
+        Ub[k] += Tb * th * A[0];
+    }
+    if (needF0) {
+        qd[1] += lF0[0];
+        qd[1] += lF0[1] * U[0];
+        Ub[0] += lF0[1] * q[1];
+        qd[0] += lF0[1] * th;
+        Gb[0][0] += -2.0 * mu * lF0[1];
+        for (int k = 1; k < 3; ++k) {
+            qd[1] += lF0[1 + k] * U[k];
+            Ub[k] += lF0[1 + k] * q[1];
+            Gb[0][k] -= mu * lF0[1 + k];
+            Gb[k][0] -= mu * lF0[1 + k];
+        }
+    }
+    // A_k = -g_k - tl sum_i U_i G_ik
+    for (int k = 0; k < 3; ++k) {
+        gb[k] -= Ab[k];
+        for (int i = 0; i < 3; ++i) {
+            Ub[i] -= tl * Ab[k] * Gm[i][k];
+            Gb[i][k] -= tl * Ab[k] * U[i];
+        }
+    }
+    // A0 = -sum U_i g_i - sum G_ii
+    for (int i = 0; i < 3; ++i) {
+        Ub[i] -= A0b * g[i];
+        gb[i] -= A0b * U[i];
+        Gb[i][i] -= A0b;
+    }
+    double Db[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    double invb[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            Db[i][j + 1] += Gb[i][j] * invi[i];
+            Ub[j] -= Gb[i][j] * D[i][0] * invi[i];
+            Db[i][0] -= Gb[i][j] * U[j] * invi[i];
+            invb[i] += Gb[i][j] * (D[i][j + 1] - U[j] * D[i][0]);
+        }
+        Db[i][0] += gb[i] * invi[i];
+        invb[i] += gb[i] * D[i][0];
+    }
+    double inv_b = invb[0] + invb[1] * ih1 + invb[2] * ih2;
+    for (int j = 0; j < 3; ++j) {
+        qd[j + 1] += Ub[j] * inv;
+        inv_b += Ub[j] * q[j + 1];
+    }
+    rhob += -inv_b * inv * inv;
+    qd[0] += rhob;
+    for (int v = 0; v < 4; ++v) {
+        qb[v] = qd[v];
+        Dnb[v] = Db[0][v];
+        D1b[v] = Db[1][v];
+        D2b[v] = Db[2][v];
+    }
+}
+
+// Adjoint of dev::weno5 (same arithmetic for the forward values).
+__device__ void weno5_rev(double a, double b, double c, double d, double e, double vb, double out[5])
+{
+    const double r6 = 1.0 / 6.0, c13 = 13.0 / 12.0;
+    const double p0 = (2.0 * a - 7.0 * b + 11.0 * c) * r6;
+    const double p1 = (-b + 5.0 * c + 2.0 * d) * r6;
+    const double p2 = (2.0 * c + 5.0 * d - e) * r6;
+    const double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+    const double t1 = b - 2.0 * c + d, u1 = b - d;
+    const double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+    const double s0 = 1e-6 + (c13 * t0 * t0 + 0.25 * u0 * u0);
+    const double s1 = 1e-6 + (c13 * t1 * t1 + 0.25 * u1 * u1);
+    const double s2 = 1e-6 + (c13 * t2 * t2 + 0.25 * u2 * u2);
+    const double S0 = s0 * s0, S1 = s1 * s1, S2 = s2 * s2;
+    const double w0 = 0.1 * (S1 * S2), w1 = 0.6 * (S0 * S2), w2 = 0.3 * (S0 * S1);
+    const double W = w0 + w1 + w2, N = w0 * p0 + w1 * p1 + w2 * p2, v = N / W;
+    const double Nb = vb / W, Wb = -vb * v / W;
+    const double p0b = Nb * w0, p1b = Nb * w1, p2b = Nb * w2;
+    const double w0b = Nb * p0 + Wb, w1b = Nb * p1 + Wb, w2b = Nb * p2 + Wb;
+    const double S0b = w1b * 0.6 * S2 + w2b * 0.3 * S1;
+    const double S1b = w0b * 0.1 * S2 + w2b * 0.3 * S0;
+    const double S2b = w0b * 0.1 * S1 + w1b * 0.6 * S0;
+    const double s0b = 2.0 * s0 * S0b, s1b = 2.0 * s1 * S1b, s2b = 2.0 * s2 * S2b;
+    const double t0b = s0b * (13.0 / 6.0) * t0, u0b = s0b * 0.5 * u0;
+    const double t1b = s1b * (13.0 / 6.0) * t1, u1b = s1b * 0.5 * u1;
+    const double t2b = s2b * (13.0 / 6.0) * t2, u2b = s2b * 0.5 * u2;
+    out[0] = 2.0 * r6 * p0b + t0b + u0b;
+    out[1] = -7.0 * r6 * p0b - r6 * p1b - 2.0 * t0b - 4.0 * u0b + t1b + u1b;
+    out[2] = 11.0 * r6 * p0b + 5.0 * r6 * p1b + 2.0 * r6 * p2b + t0b + 3.0 * u0b - 2.0 * t1b + t2b + 3.0 * u2b;
+    out[3] = 2.0 * r6 * p1b + 5.0 * r6 * p2b + t1b - u1b - 2.0 * t2b - 4.0 * u2b;
+    out[4] = -r6 * p2b + t2b + u2b;
+}
+
+// Adjoint of the half-space equilibrium state (local frame).
+__device__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], const double Qr[4], const double Q0b[4],
+                                double Qlb[4], double Qrb[4])
+{
+    const double off = ph.off;
+    const double rl = off + Ql[0], rr = off + Qr[0];
+    const double Ul = Ql[1] / rl, Ur = Qr[1] / rr;
+    const double zl = ph.sqlam * Ul, zr = ph.sqlam * Ur;
+    const double el = erf(zl), er = erf(zr);
+    const double Pl = 0.5 + 0.5 * el, Pr = 0.5 - 0.5 * er;
+    const double xl = -ph.lambda * Ul * Ul, xr = -ph.lambda * Ur * Ur;
+    const double exl = exp(xl), exr = exp(xr);
+    const double El = ph.kE * exl, Er = ph.kE * exr;
+    double Plb = 0.0, Prb = 0.0;
+    for (int v = 0; v < 4; ++v) {
+        Plb += Q0b[v] * Ql[v];
+        Prb += Q0b[v] * Qr[v];
+        Qlb[v] = Q0b[v] * Pl;
+        Qrb[v] = Q0b[v] * Pr;
+    }
+    double elb = 0.5 * Q0b[0] * off + 0.5 * Plb;
+    double erb = -0.5 * Q0b[0] * off - 0.5 * Prb;
+    Qlb[0] += Q0b[1] * El;
+    Qrb[0] -= Q0b[1] * Er;
+    const double Elb = Q0b[1] * Ql[0], Erb = -Q0b[1] * Qr[0];
+    double xlb = Q0b[1] * off * ph.kE * exl + Elb * El;
+    double xrb = -Q0b[1] * off * ph.kE * exr + Erb * Er;
+    const double dz = 2.0 / sqrt(kPi);
+    double Ulb = elb * ph.sqlam * dz * exp(-zl * zl) + xlb * (-2.0 * ph.lambda * Ul);
+    double Urb = erb * ph.sqlam * dz * exp(-zr * zr) + xrb * (-2.0 * ph.lambda * Ur);
+    Qlb[1] += Ulb / rl;
+    Qlb[0] += -Ulb * Ul / rl;
+    Qrb[1] += Urb / rr;
+    Qrb[0] += -Urb * Ur / rr;
+}
+
+// ------------------------------------------------------------------ kernels
+
+struct RevArgs {
+    const double *A;          // forward working array (ghost-filled, padded)
+    const double *fq;         // forward face states of direction d
+    long nfq;
+    int e1p;
+    const double *lamL, *lamLt;   // padded indexing; lamL may be null (stage 2)
+    double *lamG;
+    long nG;
+    double *lamR;
+    long nR;
+    double *lamFQ, *lamC;
+    double *lamA;
+    const double *ihd, *ih1, *ih2, *ihf;
+    int n[3], P[3];
+    int d, t1, t2, nd, n1, n2;
+    long np;
+    Phys<double> ph;
+};
+
+// RA: reverse of the face flux at every interior face.
+__global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
+{
+    extern __shared__ __align__(16) double rev_smem[];
+    double(*sq)[SQ_H][SQ_W] = reinterpret_cast<double(*)[SQ_H][SQ_W]>(rev_smem);
+    double(*st)[SQ_H][TX] = reinterpret_cast<double(*)[SQ_H][TX]>(rev_smem + 8 * SQ_H * SQ_W);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY, f = blockIdx.z;
+    const int e2 = A.n2 + 4;
+    for (int cc = 0; cc < 8; ++cc)
+        for (int r = ty; r < SQ_H; r += TY)
+            for (int col = tx; col < SQ_W; col += TX) {
+                const int sa = a0 + col, sb = b0 + r;
+                double v = 0.0;
+                if (sa < A.n1 + 4 && sb < e2) v = A.fq[cc * A.nfq + ((long)f * e2 + sb) * A.e1p + sa];
+                sq[cc][r][col] = v;
+            }
+    __syncthreads();
+    for (int idx = tid; idx < SQ_H * TX; idx += TX * TY) {
+        const int r = idx / TX, col = idx - r * TX;
+        for (int v = 0; v < 4; ++v) {
+            const double *p = &sq[v][r][col];
+            double vm, vp, dm, dp;
+            tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
+            st[v * 4 + 0][r][col] = vm;
+            st[v * 4 + 1][r][col] = vp;
+            st[v * 4 + 2][r][col] = dm;
+            st[v * 4 + 3][r][col] = dp;
+            const double *pn = &sq[4 + v][r][col];
+            tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
+            st[16 + v * 2 + 0][r][col] = vm;
+            st[16 + v * 2 + 1][r][col] = vp;
+        }
+    }
+    __syncthreads();
+    const int a = a0 + tx, b = b0 + ty;
+    if (a >= A.n1 || b >= A.n2) return;
+    // adjoint of the face-averaged fluxes from the two neighbour cells
+    const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    double lF0[4] = {0, 0, 0, 0}, lF1[4] = {0, 0, 0, 0};
+    int cl[3], cr[3];
+    cl[A.d] = f - 1; cl[A.t1] = a; cl[A.t2] = b;
+    cr[A.d] = f; cr[A.t1] = a; cr[A.t2] = b;
+    const bool hasl = f - 1 >= 0, hasr = f < A.nd;
+    const long il = lin(A.P[0], A.P[1], cl[0], cl[1], cl[2]), ir = lin(A.P[0], A.P[1], cr[0], cr[1], cr[2]);
+    const double ihl = hasl ? A.ihd[f - 1 + G] : 0.0, ihr = hasr ? A.ihd[f + G] : 0.0;
+    for (int v = 0; v < 4; ++v) {
+        const long o = gc[v] * A.np;
+        const double ll = hasl ? A.lamLt[o + il] : 0.0, lr = hasr ? A.lamLt[o + ir] : 0.0;
+        lF1[v] = 0.25 * (-ll * ihl + lr * ihr);
+        if (A.lamL) {
+            const double ml = hasl ? A.lamL[o + il] : 0.0, mr = hasr ? A.lamL[o + ir] : 0.0;
+            lF0[v] = 0.25 * (-ml * ihl + mr * ihr);
+        }
+    }
+    const double ih1 = A.ih1[a + G], ih2 = A.ih2[b + G];
+    const long face = ((long)f * A.n2 + b) * A.n1 + a;
+    for (int m = 0; m < 2; ++m) {
+        double Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+        for (int v = 0; v < 4; ++v) {
+            double vm, vp, dm, dp;
+            tan_val_der(st[v * 4 + m][ty][tx], st[v * 4 + m][ty + 1][tx], st[v * 4 + m][ty + 2][tx],
+                        st[v * 4 + m][ty + 3][tx], st[v * 4 + m][ty + 4][tx], vm, vp, dm, dp);
+            Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
+            tan_val(st[v * 4 + 2 + m][ty][tx], st[v * 4 + 2 + m][ty + 1][tx], st[v * 4 + 2 + m][ty + 2][tx],
+                    st[v * 4 + 2 + m][ty + 3][tx], st[v * 4 + 2 + m][ty + 4][tx], vm, vp);
+            D1[0][v] = vm; D1[1][v] = vp;
+            tan_val(st[16 + v * 2 + m][ty][tx], st[16 + v * 2 + m][ty + 1][tx], st[16 + v * 2 + m][ty + 2][tx],
+                    st[16 + v * 2 + m][ty + 3][tx], st[16 + v * 2 + m][ty + 4][tx], vm, vp);
+            Dn[0][v] = vm; Dn[1][v] = vp;
+        }
+        for (int nn = 0; nn < 2; ++nn) {
+            double qb[4], Dnb[4], D1b[4], D2b[4];
+            gk_flux_rev(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, lF0, lF1, A.lamL != nullptr, qb, Dnb, D1b,
+                        D2b);
+            const int g = m * 2 + nn;
+            for (int v = 0; v < 4; ++v) {
+                A.lamG[(g * 16 + 0 + v) * A.nG + face] = qb[v];
+                A.lamG[(g * 16 + 4 + v) * A.nG + face] = Dnb[v];
+                A.lamG[(g * 16 + 8 + v) * A.nG + face] = D1b[v];
+                A.lamG[(g * 16 + 12 + v) * A.nG + face] = D2b[v];
+            }
+        }
+    }
+}
+
+// RB: transpose of the t2 pass, per t1-pass row (f, a, b'), b' in [-2, n2+2).
+__global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
+{
+    const int a = blockIdx.x * 32 + threadIdx.x, bp = (int)(blockIdx.y * 8 + threadIdx.y) - 2, f = blockIdx.z;
+    if (a >= A.n1 || bp >= A.n2 + 2) return;
+    double X[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}}, Y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    double Z[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    const int blo = bp - 2 < 0 ? 0 : bp - 2, bhi = bp + 2 > A.n2 - 1 ? A.n2 - 1 : bp + 2;
+    for (int b = blo; b <= bhi; ++b) {
+        const int s = bp - b + 2;
+        const long face = ((long)f * A.n2 + b) * A.n1 + a;
+        for (int m = 0; m < 2; ++m)
+            for (int nn = 0; nn < 2; ++nn) {
+                const int g = m * 2 + nn;
+                const double wv = cWV[nn][s], wd = cWD[nn][s];
+                for (int v = 0; v < 4; ++v) {
+                    X[m][v] += wv * A.lamG[(g * 16 + 0 + v) * A.nG + face] + wd * A.lamG[(g * 16 + 12 + v) * A.nG + face];
+                    Y[m][v] += wv * A.lamG[(g * 16 + 8 + v) * A.nG + face];
+                    Z[m][v] += wv * A.lamG[(g * 16 + 4 + v) * A.nG + face];
+                }
+            }
+    }
+    const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
+    for (int m = 0; m < 2; ++m)
+        for (int v = 0; v < 4; ++v) {
+            A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = X[m][v];
+            A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = Y[m][v];
+            A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = Z[m][v];
+        }
+}
+
+// RC: transpose of the t1 pass, per face of the extended box.
+__global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
+{
+    const int ap = (int)(blockIdx.x * 32 + threadIdx.x) - 2, bp = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f = blockIdx.z;
+    if (ap >= A.n1 + 2 || bp >= A.n2 + 2) return;
+    double lq[4] = {0, 0, 0, 0}, ln[4] = {0, 0, 0, 0};
+    const int alo = ap - 2 < 0 ? 0 : ap - 2, ahi = ap + 2 > A.n1 - 1 ? A.n1 - 1 : ap + 2;
+    for (int a = alo; a <= ahi; ++a) {
+        const int r = ap - a + 2;
+        const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
+        for (int m = 0; m < 2; ++m) {
+            const double wv = cWV[m][r], wd = cWD[m][r];
+            for (int v = 0; v < 4; ++v) {
+                lq[v] += wv * A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] + wd * A.lamR[(1 * 8 + m * 4 + v) * A.nR + row];
+                ln[v] += wv * A.lamR[(2 * 8 + m * 4 + v) * A.nR + row];
+            }
+        }
+    }
+    const long o = ((long)f * (A.n2 + 4) + (bp + 2)) * A.e1p + (ap + 2);
+    for (int v = 0; v < 4; ++v) {
+        A.lamFQ[v * A.nfq + o] = lq[v];
+        A.lamFQ[(4 + v) * A.nfq + o] = ln[v];
+    }
+}
+
+// RD: reverse of WENO5, the equilibrium state and the normal slope, per
+// face of the extended box -> adjoints of the 6 stencil cells.
+__global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f = blockIdx.z;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
+    const long stride[3] = {1, (long)A.P[0], (long)A.P[0] * A.P[1]};
+    const long sd = stride[A.d];
+    int cc[3];
+    cc[A.d] = f - 1; cc[A.t1] = a; cc[A.t2] = b;
+    const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    double c[4][6];
+    for (int v = 0; v < 4; ++v)
+        for (int m = 0; m < 6; ++m) c[v][m] = A.A[comp[v] * A.np + base + (long)(m - 2) * sd];
+    double Ql[4], Qr[4];
+    for (int v = 0; v < 4; ++v) {
+        Ql[v] = weno5(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4]);
+        Qr[v] = weno5(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1]);
+    }
+    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+    double Q0b[4], DNb[4];
+    for (int v = 0; v < 4; ++v) {
+        Q0b[v] = A.lamFQ[v * A.nfq + o];
+        DNb[v] = A.lamFQ[(4 + v) * A.nfq + o];
+    }
+    double Qlb[4], Qrb[4];
+    equilibrium_rev(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
+    const double s = A.ihf[f] * (1.0 / 12.0);
+    for (int v = 0; v < 4; ++v) {
+        double cb[6] = {0, 0, 0, 0, 0, 0}, t[5];
+        weno5_rev(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4], Qlb[v], t);
+        for (int m = 0; m < 5; ++m) cb[m] += t[m];
+        weno5_rev(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1], Qrb[v], t);
+        for (int m = 0; m < 5; ++m) cb[5 - m] += t[m];
+        cb[1] += DNb[v] * s;
+        cb[2] -= 15.0 * DNb[v] * s;
+        cb[3] += 15.0 * DNb[v] * s;
+        cb[4] -= DNb[v] * s;
+        for (int m = 0; m < 6; ++m) A.lamC[(m * 4 + v) * A.nfq + o] = cb[m];
+    }
+}
+
+// RE: gather, per cell of the padded box along d and the extended
+// tangential box, the contributions of the 6 faces whose stencil holds it.
+__global__ void __launch_bounds__(256) rev_gather_cells_kernel(RevArgs A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int c = (int)blockIdx.z - G;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
+    const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    double acc[4] = {0, 0, 0, 0};
+    const int flo = c - 2 < 0 ? 0 : c - 2, fhi = c + 3 > A.nd ? A.nd : c + 3;
+    for (int f = flo; f <= fhi; ++f) {
+        const int m = c - f + 3;
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+        for (int v = 0; v < 4; ++v) acc[v] += A.lamC[(m * 4 + v) * A.nfq + o];
+    }
+    int cc[3];
+    cc[A.d] = c; cc[A.t1] = a; cc[A.t2] = b;
+    const long l = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + l] += acc[v];
+}
+
+// Ghost adjoint of one (axis, side, layer): the ghost's adjoint goes to its
+// source cell and is cleared.
+struct GhostRevArgs {
+    const double *A;  // forward working array
+    double *lamA;
+    double *uinf_part;
+    int n[3], P[3];
+    long np;
+    int d, e1, e2, lo1, lo2, len1, len2, s, l, bc;
+    double csound, uin[3];
+};
+
+__global__ void __launch_bounds__(256) ghost_rev_kernel(GhostRevArgs A)
+{
+    const int a = A.lo1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int b = A.lo2 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (a >= A.lo1 + A.len1 || b >= A.lo2 + A.len2) return;
+    const int d = A.d, nd = A.n[d], s = A.s, l = A.l, bc = A.bc;
+    const int gi = s == 0 ? -l : nd - 1 + l;
+    int src;
+    if (bc == GKS_BC_PERIODIC) {
+        src = gi % nd;
+        if (src < 0) src += nd;
+    } else if (bc == GKS_BC_NOSLIP || bc == GKS_BC_SLIP) {
+        src = s == 0 ? l - 1 : nd - l;
+    } else {
+        src = s == 0 ? 0 : nd - 1;
+    }
+    int cg[3], cs[3];
+    cg[d] = gi; cg[A.e1] = a; cg[A.e2] = b;
+    cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
+    const long ig = lin(A.P[0], A.P[1], cg[0], cg[1], cg[2]), is = lin(A.P[0], A.P[1], cs[0], cs[1], cs[2]);
+    double lg[4];
+    for (int v = 0; v < 4; ++v) {
+        lg[v] = A.lamA[v * A.np + ig];
+        A.lamA[v * A.np + ig] = 0.0;
+    }
+    double add[4] = {lg[0], lg[1], lg[2], lg[3]};
+    double gu = 0.0;
+    if (bc == GKS_BC_NOSLIP) {
+        add[1] = -lg[1]; add[2] = -lg[2]; add[3] = -lg[3];
+    } else if (bc == GKS_BC_SLIP) {
+        add[1 + d] = -lg[1 + d];
+    } else if (bc == GKS_BC_INFLOW) {
+        const double r1 = A.A[is], un1 = A.A[(1 + d) * A.np + is] / r1;
+        const double sg = s == 0 ? 1.0 : -1.0;
+        const double x = sg * (A.uin[d] - un1) / A.csound;
+        const double ex = exp(x);
+        const double rg = r1 * ex;
+        const double rgb = lg[0] + lg[1] * A.uin[0] + lg[2] * A.uin[1] + lg[3] * A.uin[2];
+        add[0] = rgb * ex * (1.0 + sg * un1 / A.csound);
+        add[1] = add[2] = add[3] = 0.0;
+        add[1 + d] = -rgb * sg * ex / A.csound;
+        // sensitivity to the inflow speed U_inf = u_in[0]
+        gu = lg[1] * rg + (d == 0 ? rgb * r1 * ex * sg / A.csound : 0.0);
+    }
+    for (int v = 0; v < 4; ++v) A.lamA[v * A.np + is] += add[v];
+    if (bc == GKS_BC_INFLOW)
+        A.uinf_part[(long)(b - A.lo2) * A.len1 + (a - A.lo1)] = gu;
+}
+
+__global__ void __launch_bounds__(1024) reduce_add_kernel(const double *x, long n, double *acc)
+{
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (long i = threadIdx.x; i < n; i += 1024) s += x[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += sh[0];
+}
+
+// Stage combinations, reversed (interior cells, padded indexing).
+//   stage 2: W' = P + dt^2/3 Lt(W*):     lamLt = dt^2/3 lamP
+//   stage 1: W* = W + dt/2 L + dt^2/8 Lt, P = W + dt L + dt^2/6 Lt:
+//            lamW = lamWs + lamP, lamL = dt/2 lamWs + dt lamP,
+//            lamLt = dt^2/8 lamWs + dt^2/6 lamP
+__global__ void __launch_bounds__(256) rev_update_kernel(int stage, const double *lamWs, const double *lamP,
+                                                         double *lamW, double *lamL, double *lamLt, double dt,
+                                                         long np, int nx, int ny, int P0, int P1)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long l = lin(P0, P1, i, j, k);
+    for (int v = 0; v < 4; ++v) {
+        const long o = v * np + l;
+        if (stage == 2) {
+            lamLt[o] = dt * dt / 3.0 * lamP[o];
+        } else {
+            const double ws = lamWs[o], p = lamP[o];
+            lamW[o] = ws + p;
+            lamL[o] = 0.5 * dt * ws + dt * p;
+            lamLt[o] = 0.125 * dt * dt * ws + dt * dt / 6.0 * p;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- ALM adjoint
+
+struct AlmAdjArgs {
+    int P[3], n[3];
+    long np;
+    double x0[3], h[3];
+    const double *Wp;    // state the loads were sampled from
+    double *lam;         // adjoint of the state after forcing (in: lambda'', out: lambda')
+    RotorDev r;
+    double *pts;         // 8 per point
+    double dt, power_seed, t;
+};
+
+__device__ __forceinline__ double centre_d(const AlmAdjArgs &A, int d, int i)
+{
+    return __dadd_rn(A.x0[d], __dmul_rn((double)i + 0.5, A.h[d]));
+}
+
+__device__ __forceinline__ double dist3(double dx, double dy, double dz)
+{
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+// mu_p = d J / d (F_x, F_th)_p from the projection: -dt sum_cells lambda_m . e eta
+__global__ void __launch_bounds__(256) alm_interp_adj_kernel(AlmAdjArgs A)
+{
+    __shared__ double sx[256], stt[256];
+    const int q = blockIdx.x;
+    const RotorDev &r = A.r;
+    const int b = q / r.np;
+    const double X[3] = {r.X[3 * q], r.X[3 * q + 1], r.X[3 * q + 2]};
+    const double e1 = r.et[2 * b], e2 = r.et[2 * b + 1];
+    const double cut = 3.0 * r.eps, norm = 1.0 / (r.eps * r.eps * r.eps * pow(kPi, 1.5));
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = (int)floor((X[d] - cut - A.x0[d]) / A.h[d] - 0.5) - 1;
+        hi[d] = (int)ceil((X[d] + cut - A.x0[d]) / A.h[d] - 0.5) + 1;
+        if (lo[d] < r.box[d][0]) lo[d] = r.box[d][0];
+        if (hi[d] > r.box[d][1]) hi[d] = r.box[d][1];
+    }
+    const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
+    double ax = 0.0, at = 0.0;
+    const long nc = (bx > 0 && by > 0 && bz > 0) ? (long)bx * by * bz : 0;
+    for (long c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int i = lo[0] + (int)(c % bx), j = lo[1] + (int)((c / bx) % by), k = lo[2] + (int)(c / ((long)bx * by));
+        const double rr = dist3(centre_d(A, 0, i) - X[0], centre_d(A, 1, j) - X[1], centre_d(A, 2, k) - X[2]);
+        if (rr > cut) continue;
+        const double eta = exp(-(rr / r.eps) * (rr / r.eps)) * norm;
+        const long l = lin(A.P[0], A.P[1], i, j, k);
+        ax += A.lam[A.np + l] * eta;
+        at += (A.lam[2 * A.np + l] * e1 + A.lam[3 * A.np + l] * e2) * eta;
+    }
+    sx[threadIdx.x] = ax;
+    stt[threadIdx.x] = at;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sx[threadIdx.x] += sx[threadIdx.x + w];
+            stt[threadIdx.x] += stt[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.pts[8 * q + 0] = -A.dt * sx[0];
+        A.pts[8 * q + 1] = -A.dt * stt[0];
+    }
+}
+
+__device__ bool trilinear_w(const AlmAdjArgs &A, const double X[3], int i0[3], double fr[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        const double s = (X[d] - A.x0[d]) / A.h[d] - 0.5;
+        const double fl = floor(s);
+        i0[d] = (int)fl;
+        fr[d] = s - fl;
+        if (i0[d] < 0 || i0[d] + 1 > A.n[d] - 1) {
+            if (A.n[d] == 1 && s >= -0.5 && s <= 0.5) {
+                i0[d] = 0;
+                fr[d] = 0.0;
+                continue;
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ double cd_of(double a) { return 0.01 + 0.02 * a * a; }
+
+// Reverse of the point loads: gradient of the force scales (this step), the
+// power seed, and the adjoint of the sampled velocity.
+__global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
+{
+    const RotorDev &r = A.r;
+    const int npts = r.nb * r.np;
+    for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+        const int b = q / r.np, p = q - b * r.np;
+        const double th = r.az0 + r.omega * A.t + 2.0 * kPi * b / r.nb;
+        const double cth = cos(th), sth = sin(th);
+        const double rr = r.r[p];
+        const double X[3] = {r.hub[0], r.hub[1] + rr * cth, r.hub[2] + rr * sth};
+        int i0[3];
+        double fr[3];
+        double Ub[3] = {0, 0, 0}, gs = 0.0;
+        if (trilinear_w(A, X, i0, fr)) {
+            double U[3] = {0, 0, 0};
+            for (int c = 0; c < 8; ++c) {
+                const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+                const double w = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1]) * (dk ? fr[2] : 1.0 - fr[2]);
+                if (w == 0.0) continue;
+                const int ii = A.n[0] == 1 ? 0 : i0[0] + di, jj = A.n[1] == 1 ? 0 : i0[1] + dj;
+                const int kk = A.n[2] == 1 ? 0 : i0[2] + dk;
+                const long l = lin(A.P[0], A.P[1], ii, jj, kk);
+                const double rho = A.Wp[l];
+                U[0] += w * A.Wp[A.np + l] / rho;
+                U[1] += w * A.Wp[2 * A.np + l] / rho;
+                U[2] += w * A.Wp[3 * A.np + l] / rho;
+            }
+            const double ux = U[0], ut = -sth * U[1] + cth * U[2];
+            const double wr = r.omega * rr;
+            const double av = ux, bv = wr - ut;
+            const double phi = atan2(av, bv), al = phi - r.twist[p];
+            const double urel2 = av * av + bv * bv;
+            const double qk = 0.5 * r.rho_inf * r.chord[p] * r.width[p];
+            const double qd = qk * urel2;
+            const double clr = 2.0 * kPi * sin(al);
+            const double cl = clr > 1.4 ? 1.4 : (clr < -1.4 ? -1.4 : clr);
+            const double dcl = (clr > 1.4 || clr < -1.4) ? 0.0 : 2.0 * kPi * cos(al);
+            const double cd = cd_of(al);
+            const double Lf = qd * cl, Df = qd * cd;
+            const double cp = cos(phi), sp = sin(phi);
+            const double fx = Lf * cp + Df * sp, ft = Lf * sp - Df * cp;
+            const double s = r.scale[q];
+            const double mux = A.pts[8 * q + 0];
+            const double mut = A.pts[8 * q + 1] + A.power_seed * r.omega * rr;
+            gs = mux * fx + mut * ft;
+            const double fxb = s * mux, ftb = s * mut;
+            const double Lb = fxb * cp + ftb * sp, Db = fxb * sp - ftb * cp;
+            double phib = fxb * (-Lf * sp + Df * cp) + ftb * (Lf * cp + Df * sp);
+            const double qdb = Lb * cl + Db * cd;
+            const double alb = Lb * qd * dcl + Db * qd * 0.04 * al;
+            phib += alb;
+            const double u2b = qdb * qk;
+            const double den = urel2 > 0.0 ? urel2 : 1.0;
+            const double ab = phib * bv / den + u2b * 2.0 * av;
+            const double bb = -phib * av / den + u2b * 2.0 * bv;
+            const double uxb = ab, utb = -bb;
+            Ub[0] = uxb;
+            Ub[1] = -sth * utb;
+            Ub[2] = cth * utb;
+        }
+        A.pts[8 * q + 2] = gs;
+        A.pts[8 * q + 3] = Ub[0];
+        A.pts[8 * q + 4] = Ub[1];
+        A.pts[8 * q + 5] = Ub[2];
+    }
+}
+
+// Reverse of the trilinear sampling, points in order (one thread: a few
+// hundred points x 8 corners; deterministic accumulation).
+__global__ void alm_sample_adj_kernel(AlmAdjArgs A)
+{
+    const RotorDev &r = A.r;
+    const int npts = r.nb * r.np;
+    for (int q = 0; q < npts; ++q) {
+        const int b = q / r.np, p = q - b * r.np;
+        const double th = r.az0 + r.omega * A.t + 2.0 * kPi * b / r.nb;
+        const double rr = r.r[p];
+        const double X[3] = {r.hub[0], r.hub[1] + rr * cos(th), r.hub[2] + rr * sin(th)};
+        int i0[3];
+        double fr[3];
+        if (!trilinear_w(A, X, i0, fr)) continue;
+        const double Ub[3] = {A.pts[8 * q + 3], A.pts[8 * q + 4], A.pts[8 * q + 5]};
+        for (int c = 0; c < 8; ++c) {
+            const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+            const double w = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1]) * (dk ? fr[2] : 1.0 - fr[2]);
+            if (w == 0.0) continue;
+            const int ii = A.n[0] == 1 ? 0 : i0[0] + di, jj = A.n[1] == 1 ? 0 : i0[1] + dj;
+            const int kk = A.n[2] == 1 ? 0 : i0[2] + dk;
+            const long l = lin(A.P[0], A.P[1], ii, jj, kk);
+            const double rho = A.Wp[l];
+            double dot = 0.0;
+            for (int v = 0; v < 3; ++v) {
+                A.lam[(1 + v) * A.np + l] += w * Ub[v] / rho;
+                dot += Ub[v] * A.Wp[(1 + v) * A.np + l];
+            }
+            A.lam[l] -= w * dot / (rho * rho);
+        }
+    }
+}
+
+// S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
+// for lamL (may be null) and lamLt; result accumulated into w.lamA.
+void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, const double *lamL, const double *lamLt)
+{
+    const Phys<double> ph = make_phys<double>(c);
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = tan1(d), t2 = tan2(d);
+        launch_face_eq_fp64(c, Aw, d);
+        RevArgs R;
+        R.A = Aw;
+        R.fq = (const double *)c.fq;
+        R.nfq = c.nfq;
+        R.e1p = c.e1p[d];
+        R.lamL = lamL;
+        R.lamLt = lamLt;
+        R.lamG = w.lamG;
+        R.nG = w.nG;
+        R.lamR = w.lamR;
+        R.nR = w.nR;
+        R.lamFQ = w.lamFQ;
+        R.lamC = w.lamC;
+        R.lamA = w.lamA;
+        R.ihd = (const double *)c.ih[d];
+        R.ih1 = (const double *)c.ih[t1];
+        R.ih2 = (const double *)c.ih[t2];
+        R.ihf = (const double *)c.ihf[d];
+        for (int e = 0; e < 3; ++e) {
+            R.n[e] = c.n[e];
+            R.P[e] = c.P[e];
+        }
+        R.d = d;
+        R.t1 = t1;
+        R.t2 = t2;
+        R.nd = c.n[d];
+        R.n1 = c.n[t1];
+        R.n2 = c.n[t2];
+        R.np = c.np;
+        R.ph = ph;
+        const dim3 blk(32, 8);
+        const int nf = c.n[d] + 1;
+        const size_t smem = sizeof(double) * (8 * SQ_H * SQ_W + 24 * SQ_H * TX);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(rev_flux_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, smem, c.stream>>>(R);
+        rev_t2_kernel<<<dim3((R.n1 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_t1_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_gather_cells_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
+                                  c.stream>>>(R);
+    }
+}
+
+// Adjoint of the ghost fill of working array Aw: axes z, y, x (reverse of
+// the forward sweep), each side and layer in turn.
+void ghost_adjoint(const Ctx &c, const AdjWork &w, const double *Aw)
+{
+    cudaMemsetAsync(w.uinf_part, 0, sizeof(double) * w.nuinf, c.stream);
+    for (int d = 2; d >= 0; --d) {
+        GhostRevArgs A;
+        A.A = Aw;
+        A.lamA = w.lamA;
+        for (int e = 0; e < 3; ++e) {
+            A.n[e] = c.n[e];
+            A.P[e] = c.P[e];
+        }
+        A.np = c.np;
+        A.d = d;
+        A.e1 = tan1(d);
+        A.e2 = tan2(d);
+        A.lo1 = A.e1 < d ? -G : 0;
+        A.len1 = A.e1 < d ? c.n[A.e1] + 2 * G : c.n[A.e1];
+        A.lo2 = A.e2 < d ? -G : 0;
+        A.len2 = A.e2 < d ? c.n[A.e2] + 2 * G : c.n[A.e2];
+        A.csound = c.csound;
+        for (int e = 0; e < 3; ++e) A.uin[e] = c.inflow[1 + e];
+        for (int s = 0; s < 2; ++s)
+            for (int l = G; l >= 1; --l) {
+                A.s = s;
+                A.l = l;
+                A.bc = c.bc[d][s];
+                A.uinf_part = w.uinf_part + ((long)((d * 2 + s) * G + (l - 1))) * (w.nuinf / (6 * G));
+                ghost_rev_kernel<<<dim3((A.len1 + 31) / 32, (A.len2 + 7) / 8, 1), dim3(32, 8), 0, c.stream>>>(A);
+            }
+    }
+    reduce_add_kernel<<<1, 1024, 0, c.stream>>>(w.uinf_part, w.nuinf, w.scal);
+}
+
+__global__ void __launch_bounds__(256) add_interior_kernel(double *dst, const double *src, long np, int nx, int ny,
+                                                           int P0, int P1)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long l = lin(P0, P1, i, j, k);
+    for (int v = 0; v < 4; ++v) dst[v * np + l] += src[v * np + l];
+}
+
+}  // namespace
+
+// Offsets of the adjoint buffers from `base` (base may be 0 to size them);
+// returns the total bytes.
+size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
+{
+    size_t o = 0;
+    const uintptr_t b0 = (uintptr_t)base;
+    auto take = [&](size_t n) {
+        double *p = (double *)(b0 + o);
+        o += (n * sizeof(double) + 255) & ~(size_t)255;
+        return p;
+    };
+    const long np4 = 4 * c.np;
+    w->A0 = take(np4);
+    w->Wp = take(np4);
+    w->lamA = take(np4);
+    w->lamW = take(np4);
+    w->lamP = take(np4);
+    w->lamL = take(np4);
+    w->lamLt = take(np4);
+    long nG = 0, nR = 0, maxsurf = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = tan1(d), t2 = tan2(d);
+        nG = std::max(nG, (long)(c.n[d] + 1) * c.n[t1] * c.n[t2]);
+        nR = std::max(nR, (long)(c.n[d] + 1) * (c.n[t2] + 4) * c.n[t1]);
+        const long l1 = t1 < d ? c.n[t1] + 2 * G : c.n[t1];
+        const long l2 = t2 < d ? c.n[t2] + 2 * G : c.n[t2];
+        maxsurf = std::max(maxsurf, l1 * l2);
+    }
+    w->nG = nG;
+    w->nR = nR;
+    w->lamG = take(64 * nG);
+    w->lamR = take(24 * nR);
+    w->lamFQ = take(8 * c.nfq);
+    w->lamC = take(24 * c.nfq);
+    w->nuinf = 3 * 2 * G * maxsurf;
+    w->uinf_part = take(w->nuinf);
+    w->pts = take(8 * (npts_total > 0 ? npts_total : 1));
+    w->scal = take(8);
+    return o;
+}
+
+size_t adjoint_bytes(const Ctx &c, long npts_total)
+{
+    AdjWork w;
+    return adjoint_carve(c, npts_total, nullptr, &w);
+}
+
+void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double power_seed, double dt,
+                     double t_np1)
+{
+    const dim3 blk(32, 8), gcell((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
+    const size_t bytes4 = sizeof(double) * 4 * c.np;
+    // ALM reverse: lamP holds lambda'' (state after the step) and becomes
+    // lambda' (state before the forcing); per-point scale gradients in pts
+    if (rot) {
+        AlmAdjArgs A;
+        for (int d = 0; d < 3; ++d) {
+            A.P[d] = c.P[d];
+            A.n[d] = c.n[d];
+            A.x0[d] = c.x0[d];
+            A.h[d] = c.hu[d];
+        }
+        A.np = c.np;
+        A.Wp = w.Wp;
+        A.lam = w.lamP;
+        A.r = *rot;
+        A.pts = w.pts;
+        A.dt = dt;
+        A.power_seed = power_seed;
+        A.t = t_np1;
+        const int npts = rot->nb * rot->np;
+        alm_interp_adj_kernel<<<npts, 256, 0, c.stream>>>(A);
+        alm_loads_adj_kernel<<<1, 256, 0, c.stream>>>(A);
+        alm_sample_adj_kernel<<<1, 1, 0, c.stream>>>(A);
+    }
+    // stage 2: W' = P + dt^2/3 Lt(W*)
+    rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
+                                                   c.n[0], c.n[1], c.P[0], c.P[1]);
+    cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
+    spatial_adjoint(c, w, (const double *)c.wk1, nullptr, w.lamLt);
+    ghost_adjoint(c, w, (const double *)c.wk1);
+    // stage 1: lamA (interior) is lambda of W*
+    rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
+                                                   c.n[1], c.P[0], c.P[1]);
+    cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
+    spatial_adjoint(c, w, w.A0, w.lamL, w.lamLt);
+    ghost_adjoint(c, w, w.A0);
+    add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
+}
+
+}  // namespace gks

@@ -732,6 +732,111 @@ int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes)
     return rc;
 }
 
+int gks_set_state_device(gks_grid *g, const double *d_state)
+{
+    if (!g || !d_state) return fail(g, GKS_ERR_ARG, "null argument");
+    launch_scatter_state(g->c, d_state);
+    return check_launch(g, "scatter state");
+}
+
+int gks_get_state_device(gks_grid *g, double *d_state)
+{
+    if (!g || !d_state) return fail(g, GKS_ERR_ARG, "null argument");
+    launch_gather_state(g->c, d_state);
+    return check_launch(g, "gather state");
+}
+
+namespace {
+long total_points(const gks_grid *g)
+{
+    long n = 0;
+    for (const RotorDev &r : g->rotors) n += (long)r.nb * r.np;
+    return n;
+}
+
+int adjoint_check(gks_grid *g)
+{
+    const Ctx &c = g->c;
+    if (c.prec != GKS_FP64) return fail(g, GKS_ERR_STATE, "the adjoint needs a GKS_FP64 grid");
+    if (!(c.dt_fixed > 0.0)) return fail(g, GKS_ERR_STATE, "the adjoint needs a fixed time step (dt_fixed > 0)");
+    if (!g->bodies.empty()) return fail(g, GKS_ERR_STATE, "the adjoint does not cover immersed bodies");
+    if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
+    if (!g->rotors.empty() && g->rotors[0].correction)
+        return fail(g, GKS_ERR_STATE, "the adjoint does not cover the ALM velocity correction");
+    return GKS_OK;
+}
+}  // namespace
+
+int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes)
+{
+    if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
+    *bytes = adjoint_bytes(g->c, total_points(g));
+    return GKS_OK;
+}
+
+int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n, const double *d_adj_np1,
+                     double *d_adj_n, double power_seed, double *h_grad_scales, double *h_grad_uinf)
+{
+    if (!g || !d_adj_work || !d_state_n || !d_adj_np1 || !d_adj_n) return fail(g, GKS_ERR_ARG, "null argument");
+    if ((uintptr_t)d_adj_work & 255) return fail(g, GKS_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+    int rc = adjoint_check(g);
+    if (rc) return rc;
+    const Ctx &c = g->c;
+    AdjWork w;
+    adjoint_carve(c, total_points(g), d_adj_work, &w);
+    const double dt = c.dt_fixed;
+    Ctx cc = c;
+    cc.mark = nullptr;
+    // forward recompute of the step from W^n: A0 = G(W^n), W* (c.wk1), P,
+    // W' (before forcing) and the rotor loads at t_{n+1}
+    double sv[2] = {t_n, dt};
+    rc = cuda_check(g, cudaMemcpyAsync(&c.scal->t, sv, 2 * sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                    "set time");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.scal, 0, 8 * sizeof(double), c.stream), "clear adjoint scalars");
+    if (rc) return rc;
+    cc.state = w.A0;
+    cc.wk0 = w.A0;
+    launch_scatter_state(cc, d_state_n);
+    launch_ghost(cc, w.A0);
+    launch_stage(cc, 1);
+    launch_ghost(cc, cc.wk1);
+    cc.state = w.Wp;
+    launch_stage(cc, 2);
+    const RotorDev *rot = g->rotors.empty() ? nullptr : &g->rotors[0];
+    if (rot) launch_alm_loads(cc, *rot);
+    // reverse
+    cc.state = w.lamP;
+    launch_scatter_state(cc, d_adj_np1);
+    adjoint_reverse(cc, w, rot, power_seed, dt, t_n + dt);
+    cc.state = w.lamW;
+    launch_gather_state(cc, d_adj_n);
+    rc = check_launch(g, "adjoint step");
+    if (rc) return rc;
+    const long npts = total_points(g);
+    std::vector<double> pts(8 * (npts > 0 ? npts : 1));
+    double gu = 0.0;
+    if (npts > 0)
+        rc = cuda_check(g, cudaMemcpyAsync(pts.data(), w.pts, sizeof(double) * 8 * npts, cudaMemcpyDeviceToHost, c.stream),
+                        "read scale gradients");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&gu, w.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream),
+                             "read inflow gradient");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    if (h_grad_scales)
+        for (long q = 0; q < npts; ++q) h_grad_scales[q] += pts[8 * q + 2];
+    if (h_grad_uinf) *h_grad_uinf += gu;
+    Scalars sc;
+    rc = read_scalars(g, &sc);
+    if (rc) return rc;
+    if (sc.flags) {
+        int flags = 0;
+        cudaMemcpyAsync(&c.scal->flags, &flags, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+        sync(g);
+        return fail(g, GKS_ERR_NONFINITE, "device flag raised during the adjoint step");
+    }
+    return GKS_OK;
+}
+
 int gks_profile_enable(gks_grid *g, int timing_on)
 {
     if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");

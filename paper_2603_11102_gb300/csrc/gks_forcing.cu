@@ -494,6 +494,12 @@ __global__ void __launch_bounds__(1024) ibm_force_kernel(BodyDev b)
 
 }  // namespace
 
+void launch_alm_loads(const Ctx &c, const RotorDev &r)
+{
+    const Lattice L = make_lattice(c);
+    alm_loads_kernel<<<1, 256, 0, c.stream>>>(L, c.state, r, c.scal);
+}
+
 void launch_alm(const Ctx &c, const RotorDev &r)
 {
     const Lattice L = make_lattice(c);

@@ -107,6 +107,26 @@ struct RotorDev {
     int box[3][2];      // interior cell box swept by the 3 eps supports
 };
 void launch_alm(const Ctx &c, const RotorDev &r);
+void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no projection
+void launch_face_eq_fp64(const Ctx &c, const double *w, int d);
+
+// Adjoint of one step (gks_adjoint.cu). Buffers of the adjoint workspace.
+struct AdjWork {
+    double *A0, *Wp, *lamA, *lamW, *lamP, *lamL, *lamLt;   // 4 * np each (padded indexing)
+    double *lamG, *lamR, *lamFQ, *lamC;                   // per face / row buffers
+    long nG, nR;                                          // component strides of lamG, lamR
+    double *uinf_part;                                    // per inflow ghost contribution
+    long nuinf;
+    double *pts;                                          // per actuator point scratch (8 per point)
+    double *scal;                                         // [0] grad U_inf (device accumulator)
+};
+size_t adjoint_bytes(const Ctx &c, long npts_total);
+size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
+// Runs the reverse of one step whose forward quantities were recomputed into
+// w (A0, W* in c.wk1, Wp, rotor loads); accumulates into grad (per point) and
+// w.scal[0].
+void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double power_seed, double dt,
+                     double t_np1);
 
 // Immersed body (gks_forcing.cu).
 struct BodyDev {

@@ -21,38 +21,13 @@
 
 #include <type_traits>
 
+#include "gks_device.cuh"
 #include "gks_internal.h"
 
 namespace gks {
 namespace {
 
-template <typename R>
-struct Phys {
-    R lambda, theta, mu, off, sqlam, kE;
-};
-
-template <typename R>
-Phys<R> make_phys(const Ctx &c)
-{
-    Phys<R> p;
-    p.lambda = (R)c.lambda;
-    p.theta = (R)c.theta;
-    p.mu = (R)c.mu;
-    p.off = (R)c.off;
-    p.sqlam = (R)sqrt(c.lambda);
-    p.kE = (R)(1.0 / (2.0 * sqrt(3.14159265358979323846 * c.lambda)));
-    return p;
-}
-
-// Division in the working type: IEEE division in FP64; the two-instruction
-// approximate division (2 ulp) in FP32, whose error is far below the FP32
-// rounding of the stencil itself.
-__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
-
-// Direction d: normal axis d, tangential axes t1, t2.
-__host__ __device__ inline int tan1(int d) { return d == 0 ? 1 : 0; }
-__host__ __device__ inline int tan2(int d) { return d == 2 ? 1 : 2; }
+using namespace dev;
 
 // ---------------------------------------------------------------- ghosts --
 
@@ -144,28 +119,6 @@ void ghost_impl(const Ctx &c, R *w)
 
 // ------------------------------------------------------------ face state --
 
-// WENO5-JS value at the right face of the centre cell of (a,b,c,d,e), with
-// eps_w = 1e-6 and power 2. The three nonlinear weights d_k/(eps+beta_k)^2
-// are scaled by (eps+beta_0)^2 (eps+beta_1)^2 (eps+beta_2)^2 so that one
-// division remains.
-template <typename R>
-__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
-{
-    const R r6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0), q = R(0.25);
-    const R p0 = (R(2) * a - R(7) * b + R(11) * c) * r6;
-    const R p1 = (-b + R(5) * c + R(2) * d) * r6;
-    const R p2 = (R(2) * c + R(5) * d - e) * r6;
-    R t = a - R(2) * b + c, u = a - R(4) * b + R(3) * c;
-    R s0 = R(1e-6) + (c13 * t * t + q * u * u);
-    t = b - R(2) * c + d; u = b - d;
-    R s1 = R(1e-6) + (c13 * t * t + q * u * u);
-    t = c - R(2) * d + e; u = R(3) * c - R(4) * d + e;
-    R s2 = R(1e-6) + (c13 * t * t + q * u * u);
-    s0 *= s0; s1 *= s1; s2 *= s2;
-    const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
-    return wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
-}
-
 template <typename R>
 struct FaceEqArgs {
     const R *w;      // working state, 4 arrays of np
@@ -232,97 +185,6 @@ __global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
 
 // ------------------------------------------------------------- face flux --
 
-// Quartic through 5 face averages q[-2..2], at the Gauss points -g, +g of
-// the centre cell, g = 1/(2 sqrt 3) (index space):
-//   value(+-g) = E +- O, derivative(+-g) = Do +- De with s_k = q_k + q_-k,
-//   a_k = q_k - q_-k and
-//   E  = q0 + (s1 - 2 q0)/1080 - (s2 - 2 q0)/4320,
-//   O  = (25 sqrt3 / 216) a1 - (7 sqrt3 / 432) a2,
-//   Do = (2/3) a1 - (1/12) a2,
-//   De = (13 sqrt3 / 54)(s1 - 2 q0) - (sqrt3 / 54)(s2 - 2 q0).
-template <typename R>
-__device__ __forceinline__ void tan_val(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp)
-{
-    const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
-    const R a1 = qp1 - qm1, a2 = qp2 - qm2;
-    const R E = fma(d1, R(1.0 / 1080.0), fma(d2, R(-1.0 / 4320.0), q0));
-    const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
-    vm = E - O;
-    vp = E + O;
-}
-
-template <typename R>
-__device__ __forceinline__ void tan_val_der(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp, R &dm,
-                                            R &dp)
-{
-    const R d1 = qp1 + qm1 - R(2) * q0, d2 = qp2 + qm2 - R(2) * q0;
-    const R a1 = qp1 - qm1, a2 = qp2 - qm2;
-    const R E = fma(d1, R(1.0 / 1080.0), fma(d2, R(-1.0 / 4320.0), q0));
-    const R O = R(0.20046884346862007) * a1 - R(0.028065638085606807) * a2;
-    const R Do = R(2.0 / 3.0) * a1 - R(1.0 / 12.0) * a2;
-    const R De = R(0.41697519441472974) * d1 - R(0.032075014954979206) * d2;
-    vm = E - O;
-    vp = E + O;
-    dm = Do - De;
-    dp = Do + De;
-}
-
-// Gas-kinetic flux at one Gauss point (local frame: index 0 normal, 1 and 2
-// tangential). The moments of f = g0 (1 - tau (a1 u + a2 v + a3 w + A) + A t)
-// with the coefficients solved from the slopes and compatibility (Appendix)
-// reduce to the closed form below (Chapman-Enskog structure, tau p = mu):
-//   a.u + A = (1/theta) d_i U_j (c_i c_j - theta delta_ij),   c = u - U,
-//   A = A0 + A_j c_j, A0 = -U.grad ln rho - div U,
-//   A_k = -d_k ln rho - 2 lambda U_i d_i U_k,
-//   F0 = (m_n, m_n U_k + p' delta_nk - mu (d_n U_k + d_k U_n)),
-//   F1 = rho (A0 U_n + theta A_n, A0 (U_n U_k + theta delta_nk) + theta (A_k U_n + A_n U_k)),
-// with p' = theta (rho - off): the constant theta off cancels in L.
-// D1 and D2 are index-space tangential slopes; ih1, ih2 turn them into
-// physical ones.
-template <typename R, bool NEED_F0>
-__device__ __forceinline__ void gk_flux(const Phys<R> &ph, const R q[4], const R Dn[4], const R D1[4],
-                                        const R D2[4], R ih1, R ih2, R F0[4], R F1[4])
-{
-    const R rho = ph.off + q[0];
-    const R inv = wdiv(R(1), rho);
-    const R inv1 = inv * ih1, inv2 = inv * ih2;
-    const R U0 = q[1] * inv, U1 = q[2] * inv, U2 = q[3] * inv;
-    const R g0 = Dn[0] * inv, g1 = D1[0] * inv1, g2 = D2[0] * inv2;
-    const R G00 = (Dn[1] - U0 * Dn[0]) * inv, G01 = (Dn[2] - U1 * Dn[0]) * inv,
-            G02 = (Dn[3] - U2 * Dn[0]) * inv;
-    const R G10 = (D1[1] - U0 * D1[0]) * inv1, G11 = (D1[2] - U1 * D1[0]) * inv1,
-            G12 = (D1[3] - U2 * D1[0]) * inv1;
-    const R G20 = (D2[1] - U0 * D2[0]) * inv2, G21 = (D2[2] - U1 * D2[0]) * inv2,
-            G22 = (D2[3] - U2 * D2[0]) * inv2;
-    const R th = ph.theta, tl = R(2) * ph.lambda;
-    const R A0 = -(U0 * g0 + U1 * g1 + U2 * g2) - (G00 + G11 + G22);
-    const R An = -g0 - tl * (U0 * G00 + U1 * G10 + U2 * G20);
-    const R A1 = -g1 - tl * (U0 * G01 + U1 * G11 + U2 * G21);
-    const R A2 = -g2 - tl * (U0 * G02 + U1 * G12 + U2 * G22);
-    if (NEED_F0) {
-        F0[0] = q[1];
-        F0[1] = q[1] * U0 + th * q[0] - ph.mu * (G00 + G00);
-        F0[2] = q[1] * U1 - ph.mu * (G01 + G10);
-        F0[3] = q[1] * U2 - ph.mu * (G02 + G20);
-    }
-    F1[0] = rho * (A0 * U0 + th * An);
-    F1[1] = rho * (A0 * (U0 * U0 + th) + th * (An * U0 + An * U0));
-    F1[2] = rho * (A0 * (U0 * U1) + th * (A1 * U0 + An * U1));
-    F1[3] = rho * (A0 * (U0 * U2) + th * (A2 * U0 + An * U2));
-}
-
-constexpr int TX = 32, TY = 8;              // face tile
-constexpr int SQ_W = TX + 4, SQ_H = TY + 4; // tile with the tangential halo
-constexpr int SQ_N = 8 * SQ_H * SQ_W;
-constexpr int ST_ROWS = SQ_H * TX;          // rows of the t1 pass
-constexpr int ST_N = 24 * ST_ROWS;
-
-template <typename R>
-constexpr size_t flux_smem_bytes()
-{
-    return (size_t)(2 * SQ_N + ST_N) * sizeof(R) + 2 * sizeof(unsigned long long);
-}
-
 template <typename R>
 struct FluxArgs {
     R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
@@ -333,61 +195,6 @@ struct FluxArgs {
     Phys<R> ph;
     Scalars *scal;
 };
-
-// ---- TMA and mbarrier helpers (sm_90+ PTX) ----
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One bulk tensor copy of the (TX+4) x (TY+4) x 1 x 8 face box starting at
-// (c0, c1, c2, 0) into dst; completion is signalled on bar with the byte
-// count.
-__device__ __forceinline__ void tma_load_tile(const CUtensorMap *map, void *dst, uint64_t *bar, int c0, int c1,
-                                              int c2, uint32_t bytes)
-{
-    const uint32_t b = smem_u32(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(b)
-        : "memory");
-}
-
-// Wait for phase `parity` of bar; gives up after ~1 s of SM clock and
-// returns false (the caller raises FLAG_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t b = smem_u32(bar);
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(b), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
-    }
-}
 
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of the next tile is fetched by TMA into the other buffer while the
@@ -920,6 +727,31 @@ int reduce_blocks(long ncell)
 }
 
 }  // namespace
+
+void launch_face_eq_fp64(const Ctx &c, const double *w, int d)
+{
+    const Phys<double> ph = make_phys<double>(c);
+    const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
+    const int t1 = tan1(d), t2 = tan2(d);
+    FaceEqArgs<double> E;
+    E.w = w;
+    E.np = c.np;
+    E.fq = (double *)c.fq;
+    E.nfq = c.nfq;
+    E.ihf = (const double *)c.ihf[d];
+    E.n1 = c.n[t1];
+    E.n2 = c.n[t2];
+    E.e1p = c.e1p[d];
+    E.sd = stride[d];
+    E.s1 = stride[t1];
+    E.s2 = stride[t2];
+    E.cn = 1 + d;
+    E.c1 = 1 + t1;
+    E.c2 = 1 + t2;
+    E.ph = ph;
+    dim3 blk(32, 8), ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, c.n[d] + 1);
+    face_eq_kernel<double><<<ge, blk, 0, c.stream>>>(E);
+}
 
 void launch_prep(const Ctx &c)
 {

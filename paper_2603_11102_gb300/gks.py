@@ -81,6 +81,11 @@ SIGNATURES = {
     "gks_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ProfileOut)]),
     "gks_kernel_group_name": (C.c_char_p, [C.c_int]),
+    "gks_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gks_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gks_adjoint_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_step_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_double, _dp, _dp]),
     "gks_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -158,6 +163,7 @@ class Grid:
         self.stream = stream
         d.stream = C.c_void_p(stream.cuda_stream)
         self._desc = d
+        self.dt_fixed = float(dt_fixed)
         sb, wb = C.c_size_t(), C.c_size_t()
         _check(lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)))
         self.state_bytes, self.work_bytes = sb.value, wb.value
@@ -302,6 +308,39 @@ class Grid:
     def load_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib.gks_load_state(self.h, buf, len(blob)), self.h)
+
+    def state_tensor(self):
+        """The conserved state as a (4, nz, ny, nx) float64 tensor on the device."""
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        _check(lib.gks_get_state_device(self.h, C.c_void_p(out.data_ptr())), self.h)
+        return out
+
+    def set_state_tensor(self, t):
+        import torch
+        t = t.to(device=self.device, dtype=torch.float64).contiguous()
+        _check(lib.gks_set_state_device(self.h, C.c_void_p(t.data_ptr())), self.h)
+        self.stream.synchronize()
+
+    def adjoint_workspace(self):
+        import torch
+        nb = C.c_size_t()
+        _check(lib.gks_adjoint_workspace_bytes(self.h, C.byref(nb)))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+
+    def step_adjoint(self, work, t_n, state_n, adj_np1, power_seed=0.0, grad_scales=None):
+        """One reverse step: returns (lambda^n, grad_uinf of this step); adds
+        the force-scale gradient of this step into grad_scales (numpy)."""
+        import torch
+        state_n = state_n.to(self.device, torch.float64).contiguous()
+        adj_np1 = adj_np1.to(self.device, torch.float64).contiguous()
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        gu = C.c_double(0.0)
+        gs = None if grad_scales is None else grad_scales.ctypes.data_as(_dp)
+        _check(lib.gks_step_adjoint(self.h, C.c_void_p(work.data_ptr()), float(t_n), C.c_void_p(state_n.data_ptr()),
+                                    C.c_void_p(adj_np1.data_ptr()), C.c_void_p(out.data_ptr()), float(power_seed),
+                                    gs, C.byref(gu)), self.h)
+        return out, gu.value
 
     def profile_enable(self, timing=True):
         _check(lib.gks_profile_enable(self.h, int(bool(timing))), self.h)

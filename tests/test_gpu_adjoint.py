@@ -1,0 +1,188 @@
+"""The hand-written adjoint (reverse mode) of the FP64 step, through the C ABI.
+
+One step: <lambda^{n+1}, dW^{n+1}> from central differences of the CUDA
+forward step equals <lambda^n, dW^n> (+ the force-scale, inflow-speed and
+power-seed terms) from gks_step_adjoint. Rollout: the checkpointed
+torch.autograd.Function gives the gradient of the wake-deficit plus power
+objective that central differences (h = 1e-6, FP64) of the CUDA forward and
+of the CPU oracle give."""
+import numpy as np
+import pytest
+
+from paper_2603_11102_gb300 import workloads as WL
+
+from _setup import oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+
+    from paper_2603_11102_gb300 import adjoint, build, gks
+    build.build()
+    gks.load()
+    return gks, adjoint, torch
+
+
+def rotor_box_workload(n=(24, 16, 16), n_pts=6, uinf=1.0):
+    nx, ny, nz = n
+    faces = [np.linspace(-1.5, 1.5, nx + 1), np.linspace(-1.0, 1.0, ny + 1), np.linspace(-1.0, 1.0, nz + 1)]
+    dx = 3.0 / nx
+    hmin = min(3.0 / nx, 2.0 / ny, 2.0 / nz)
+    dt = 0.5 * hmin / (uinf + 10.0)
+    rot = WL.rotor_3x50(D=1.0, hub=(0.0, 0.0, 0.0), dx=dx, n_pts=n_pts, u_inf=uinf)
+    Q = np.zeros((4, nz, ny, nx))
+    Q[0], Q[1] = 1.0, uinf
+    return WL.Workload("adjoint-rotor", n, faces, 0.1, 1.0, 2e-3, [(3, 4), (0, 0), (2, 2)], cfl=0.9, dt_fixed=dt,
+                       inflow=(1.0, uinf, 0.0, 0.0), state0=Q, rotors=[rot])
+
+
+def walls_workload(n=(20, 12, 10)):
+    faces = [np.linspace(0, 2.0, n[0] + 1), WL.tanh_faces(n[1]), np.linspace(0, 1.0, n[2] + 1)]
+    Q = np.zeros((4, n[2], n[1], n[0]))
+    Q[0], Q[1] = 1.0, 0.6
+    return WL.Workload("adjoint-walls", n, faces, 0.1, 1.0, 3e-3, [(3, 4), (1, 2), (0, 0)], cfl=0.9, dt_fixed=1.5e-3,
+                       inflow=(1.0, 0.6, 0.0, 0.0), state0=Q)
+
+
+def perturbed_state(w, seed, amp=0.03):
+    rng = np.random.default_rng(seed)
+    Q = w.state0.copy()
+    xc = [0.5 * (f[1:] + f[:-1]) for f in w.faces]
+    Z, Y, X = np.meshgrid(xc[2], xc[1], xc[0], indexing="ij")
+    Q[0] += 0.01 * np.sin(2 * X + 0.3) * np.cos(3 * Y)
+    Q[1] += amp * np.cos(X) * np.sin(2 * Z + 0.1)
+    Q[2] += amp * np.sin(Y + Z)
+    Q[3] += amp * np.cos(2 * X - Y)
+    Q += 1e-3 * rng.standard_normal(Q.shape) * np.array([0.1, 1, 1, 1])[:, None, None, None]
+    return Q
+
+
+def forward_step(g, torch, W, t_n, scales=None, uinf=None):
+    if scales is not None:
+        g.set_force_scales(0, scales)
+    if uinf is not None:
+        g.set_inflow(1.0, uinf, 0.0, 0.0)
+    g.set_state_tensor(W)
+    g.set_time(t_n)
+    g.step(1)
+    out = g.state_tensor()
+    P = g.forces(0)["power"] if g.objects else 0.0
+    return out, P
+
+
+@pytest.mark.parametrize("case", ["rotor", "walls"])
+def test_one_step_adjoint_matches_central_differences(mods, case):
+    gks, adjoint, torch = mods
+    w = rotor_box_workload() if case == "rotor" else walls_workload()
+    g = gks.Grid.from_workload(w, precision="fp64")
+    W = torch.tensor(perturbed_state(w, 3), dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(5)
+    lam1 = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
+    beta = 0.7 if case == "rotor" else 0.0
+    t_n = 0.37
+    npts = 3 * 6 if case == "rotor" else 0
+    s0 = np.ones(max(npts, 1))
+    u0 = w.inflow[1]
+
+    def J(Wx, s=None, u=None):
+        out, P = forward_step(g, torch, Wx, t_n, s if npts else None, u)
+        return float((lam1 * out).sum().item()) + beta * P
+
+    work = g.adjoint_workspace()
+    if npts:
+        g.set_force_scales(0, s0)
+    g.set_inflow(1.0, u0, 0.0, 0.0)
+    gs = np.zeros(max(npts, 1))
+    lam0, gu = g.step_adjoint(work, t_n, W, lam1, beta, gs if npts else None)
+
+    # state direction. The WENO weights of this noisy state sit in the
+    # beta ~ eps_w regime, where they bend on a 1e-3 scale: the central
+    # differences need h ~ 1e-7 for their O(h^2) error to drop below 1e-6.
+    dW = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
+    dW[0] *= 0.1
+    h = 1e-7
+    fd = (J(W + h * dW, s0, u0) - J(W - h * dW, s0, u0)) / (2 * h)
+    ad = float((lam0 * dW).sum().item())
+    assert abs(fd - ad) <= 1e-5 * max(abs(ad), 1e-12), (fd, ad)
+    # inflow speed
+    fdu = (J(W, s0, u0 + h) - J(W, s0, u0 - h)) / (2 * h)
+    assert abs(fdu - gu) <= 1e-5 * max(abs(fdu), 1e-3), (fdu, gu)
+    # force scales
+    if npts:
+        h = 1e-6
+        ds = rng.standard_normal(npts)
+        fds = (J(W, s0 + h * ds, u0) - J(W, s0 - h * ds, u0)) / (2 * h)
+        assert abs(fds - float(np.dot(gs, ds))) <= 1e-5 * max(abs(fds), 1e-12), (fds, np.dot(gs, ds))
+    g.close()
+
+
+def oracle_objective(w, s, u, nsteps, iplane, beta):
+    w = WL.Workload(w.name, w.n, w.faces, w.mach, w.u_ref, w.mu, w.bc, cfl=w.cfl, dt_fixed=w.dt_fixed,
+                    inflow=(1.0, u, 0.0, 0.0), state0=None, rotors=w.rotors)
+    Q = np.zeros((4,) + w.n[::-1])
+    Q[0], Q[1] = 1.0, u
+    o = oracle_from_workload(w, Q)
+    o.set_force_scales(0, s)
+    o.step(nsteps)
+    A = o.get_state()
+    return float(np.mean(u - A[1, :, :, iplane] / A[0, :, :, iplane])) + beta * o.forces(0)["power"]
+
+
+def test_rollout_gradient_vs_finite_differences_and_oracle(mods):
+    gks, adjoint, torch = mods
+    w = rotor_box_workload()
+    g = gks.Grid.from_workload(w, precision="fp64")
+    N, K, beta = 6, 2, 1.0
+    iplane = 20          # x index downstream of the rotor
+    npts = 18
+    s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+    u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    J = adjoint.rotor_objective(g, s, u, N, K=K, iplane=iplane, beta=beta)
+    J.backward()
+    gs, gu = s.grad.numpy().copy(), float(u.grad)
+
+    def Jgpu(sv, uv):
+        return float(adjoint.rotor_objective(g, torch.tensor(sv, dtype=torch.float64),
+                                             torch.tensor(uv, dtype=torch.float64), N, K=K, iplane=iplane,
+                                             beta=beta))
+
+    h = 1e-6
+    s0 = np.ones(npts)
+    scale = np.max(np.abs(gs))
+    for p in (0, 7, 17):
+        e = np.zeros(npts)
+        e[p] = h
+        fd = (Jgpu(s0 + e, 1.0) - Jgpu(s0 - e, 1.0)) / (2 * h)
+        assert abs(fd - gs[p]) <= 1e-4 * scale, (p, fd, gs[p])
+    fdu = (Jgpu(s0, 1.0 + h) - Jgpu(s0, 1.0 - h)) / (2 * h)
+    assert abs(fdu - gu) <= 1e-4 * abs(gu), (fdu, gu)
+    # reference gradient from the CPU oracle (central differences of its J)
+    for p in (0, 17):
+        e = np.zeros(npts)
+        e[p] = h
+        fo = (oracle_objective(w, s0 + e, 1.0, N, iplane, beta) -
+              oracle_objective(w, s0 - e, 1.0, N, iplane, beta)) / (2 * h)
+        assert abs(fo - gs[p]) <= 1e-4 * scale, (p, fo, gs[p])
+    fou = (oracle_objective(w, s0, 1.0 + h, N, iplane, beta) -
+           oracle_objective(w, s0, 1.0 - h, N, iplane, beta)) / (2 * h)
+    assert abs(fou - gu) <= 1e-4 * abs(gu), (fou, gu)
+    g.close()
+
+
+def test_adjoint_rejects_unsupported_grids(mods):
+    gks, adjoint, torch = mods
+    w = rotor_box_workload()
+    w.dt_fixed = 0.0
+    g = gks.Grid.from_workload(w, precision="fp64")
+    work = g.adjoint_workspace()
+    W = g.state_tensor()
+    with pytest.raises(gks.GKSError) as e:
+        g.step_adjoint(work, 0.0, W, W)
+    assert e.value.code == -5
+    g2 = gks.Grid.from_workload(rotor_box_workload(), precision="fp32c")
+    with pytest.raises(gks.GKSError) as e:
+        g2.step_adjoint(g2.adjoint_workspace(), 0.0, W, W)
+    assert e.value.code == -5

@@ -204,7 +204,7 @@ def time_oracle(w, steps, warmup):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("gks_stencil.cu", "gks_forcing.cu", "gks_api.cu", "gks_internal.h"):
+    for f in ("gks_stencil.cu", "gks_device.cuh", "gks_internal.h"):
         with open(os.path.join(ROOT, "paper_2603_11102_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -230,6 +230,46 @@ def face_counts(n):
         t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
         out.append({"eq": (n[d] + 1) * (n[t1] + 4) * (n[t2] + 4), "flux": (n[d] + 1) * n[t1] * n[t2]})
     return out
+
+
+def adjoint_workload(n=(256, 128, 128)):
+    """Rotor as the ALM workload on a 256x128x128 grid, FP64, fixed dt equal
+    to the CFL-0.5 step of the initial uniform stream."""
+    w = WL.alm_rotor(n=n)
+    h = min((w.faces[a][-1] - w.faces[a][0]) / w.n[a] for a in range(3))
+    w.dt_fixed = 0.5 * h / (1.0 + 1.0 / w.mach)
+    w.cfl = 0.9
+    return w
+
+
+def time_adjoint(args, dev):
+    """Forward and checkpointed adjoint of the wake-deficit plus power
+    objective; ratio = backward time (segment recomputation included) over
+    the forward time of the same steps."""
+    import torch
+
+    from paper_2603_11102_gb300 import adjoint, gks
+    w = adjoint_workload()
+    g = gks.Grid.from_workload(w, precision="fp64", device=dev)
+    iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
+    npts = w.rotors[0].n_blades * len(w.rotors[0].r)
+    s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+    u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    J = adjoint.rotor_objective(g, s, u, args.adjoint_steps, K=args.adjoint_k, iplane=iplane, beta=1.0)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    g.close()
+    fwd, bwd = t1 - t0, t2 - t1
+    return {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
+            "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
+            "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
+            "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
+                         % npts, "grad_uinf": float(u.grad)}
 
 
 def run_ours(args, world, rank, local):
@@ -328,6 +368,11 @@ def run_ours(args, world, rank, local):
                 "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
         g64.close()
 
+    adj = None
+    if args.adjoint_steps > 0 and rank == 0:
+        adj = time_adjoint(args, dev)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         mlups, secs, cores, desc = time_oracle(w, args.cpu_steps, 0)
@@ -346,7 +391,8 @@ def run_ours(args, world, rank, local):
                            cells * (32 if args.precision == "fp32c" else 32) / 1e6),
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "hbm_step": hbm, "kernel_share": share, "cpu_baseline": cpu,
-            "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64}
+            "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64,
+            "adjoint": adj}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -380,6 +426,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--adjoint-k", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -64,6 +64,60 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
     return wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
 }
 
+// Both face values of the centre cell of q[0..4] (cells -2..2) from one set
+// of Jiang-Shu smoothness indicators: the value at the right face (+1/2) and,
+// with the stencils mirrored, at the left face (-1/2). The mirrored
+// indicators are the same numbers in reverse order, so they are computed
+// once. Weights scaled by (eps+b0)^2 (eps+b1)^2 (eps+b2)^2, one division each.
+template <typename R>
+__device__ __forceinline__ void weno5_pair(const R q[5], R &right, R &left)
+{
+    const R r6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0), qq = R(0.25);
+    const R a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
+    R t = a - R(2) * b + c, u = a - R(4) * b + R(3) * c;
+    R s0 = R(1e-6) + (c13 * t * t + qq * u * u);
+    t = b - R(2) * c + d; u = b - d;
+    R s1 = R(1e-6) + (c13 * t * t + qq * u * u);
+    t = c - R(2) * d + e; u = R(3) * c - R(4) * d + e;
+    R s2 = R(1e-6) + (c13 * t * t + qq * u * u);
+    s0 *= s0; s1 *= s1; s2 *= s2;
+    const R s01 = s0 * s1, s02 = s0 * s2, s12 = s1 * s2;
+    // right face
+    {
+        const R p0 = (R(2) * a - R(7) * b + R(11) * c) * r6;
+        const R p1 = (-b + R(5) * c + R(2) * d) * r6;
+        const R p2 = (R(2) * c + R(5) * d - e) * r6;
+        const R w0 = R(0.1) * s12, w1 = R(0.6) * s02, w2 = R(0.3) * s01;
+        right = wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
+    }
+    // left face: candidates on (e,d,c), (d,c,b), (c,b,a) with indicators s2, s1, s0
+    {
+        const R p0 = (R(2) * e - R(7) * d + R(11) * c) * r6;
+        const R p1 = (-d + R(5) * c + R(2) * b) * r6;
+        const R p2 = (R(2) * c + R(5) * b - a) * r6;
+        const R w0 = R(0.1) * s01, w1 = R(0.6) * s02, w2 = R(0.3) * s12;
+        left = wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
+    }
+}
+
+// Equilibrium state at a face (local frame, rho written as rho - off): the
+// u>0 half of the left Maxwellian plus the u<0 half of the right one.
+template <typename R>
+__device__ __forceinline__ void face_equilibrium(const Phys<R> &ph, const R Ql[4], const R Qr[4], R Q0[4])
+{
+    const R rl = ph.off + Ql[0], rr = ph.off + Qr[0];
+    const R Ul = wdiv(Ql[1], rl), Ur = wdiv(Qr[1], rr);
+    const R el = erf(ph.sqlam * Ul), er = erf(ph.sqlam * Ur);
+    const R Pl = R(0.5) + R(0.5) * el;   // <u^0>_{u>0} of the left state
+    const R Pr = R(0.5) - R(0.5) * er;   // <u^0>_{u<0} of the right state
+    const R xl = -ph.lambda * Ul * Ul, xr = -ph.lambda * Ur * Ur;
+    const R El = ph.kE * exp(xl), Er = ph.kE * exp(xr);
+    Q0[0] = Ql[0] * Pl + Qr[0] * Pr + ph.off * (R(0.5) * (el - er));
+    Q0[1] = Ql[1] * Pl + Qr[1] * Pr + (Ql[0] * El - Qr[0] * Er) + ph.off * (ph.kE * (expm1(xl) - expm1(xr)));
+    Q0[2] = Ql[2] * Pl + Qr[2] * Pr;
+    Q0[3] = Ql[3] * Pl + Qr[3] * Pr;
+}
+
 // Quartic through 5 face averages q[-2..2], at the Gauss points -g, +g of
 // the centre cell, g = 1/(2 sqrt 3) (index space):
 //   value(+-g) = E +- O, derivative(+-g) = Do +- De with s_k = q_k + q_-k,

@@ -130,6 +130,7 @@ struct FaceEqArgs {
     int e1p;         // row stride of the face box (n1 + 4 rounded up to 4)
     long sd, s1, s2; // element strides along d, t1, t2
     int cn, c1, c2;  // state component of the normal / t1 / t2 momentum
+    int nf, K;       // faces along d, faces per thread of the marching kernel
     Phys<R> ph;
 };
 
@@ -180,6 +181,61 @@ __global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
     for (int v = 0; v < 4; ++v) {
         A.fq[v * A.nfq + o] = Q0[v];
         A.fq[(4 + v) * A.nfq + o] = (R(15) * (c[v][3] - c[v][2]) - (c[v][4] - c[v][1])) * s;
+    }
+}
+
+constexpr int kMarch = 16;   // faces per thread of the marching face-state kernel
+
+// Marching variant: each thread walks K consecutive faces along d at one
+// tangential position of the extended face box, with the 5 cells around the
+// current cell in registers. Per cell it forms both face values of WENO5
+// from one set of smoothness indicators; face f takes the right-face value
+// of cell f-1 and the left-face value of cell f.
+template <typename R>
+__global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
+    const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f0 = blockIdx.z * A.K;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= A.nf) return;
+    const int f1 = min(f0 + A.K, A.nf);
+    const long base = (long)(a + G) * A.s1 + (long)(b + G) * A.s2;   // cell index along d = -G
+    const int comp[4] = {0, A.cn, A.c1, A.c2};
+    const Phys<R> &ph = A.ph;
+    // window w[v][k] = cell (c - 2 + k); start with c = f0 - 1
+    R w[4][5];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const R *p = A.w + comp[v] * A.np + base;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[v][k] = __ldg(p + (long)(f0 - 3 + k + G) * A.sd);
+    }
+    R Qprev[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        R l;
+        weno5_pair(w[v], Qprev[v], l);
+    }
+    for (int f = f0; f < f1; ++f) {
+        R Ql[4], Qr[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[v][k] = w[v][k + 1];
+            w[v][4] = __ldg(A.w + comp[v] * A.np + base + (long)(f + 2 + G) * A.sd);
+            Ql[v] = Qprev[v];
+            weno5_pair(w[v], Qprev[v], Qr[v]);
+        }
+        R Q0[4];
+        face_equilibrium(ph, Ql, Qr, Q0);
+        const R s = A.ihf[f] * R(1.0 / 12.0);
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            A.fq[v * A.nfq + o] = Q0[v];
+            // cells f-2 .. f+1 are w[v][0..3]
+            A.fq[(4 + v) * A.nfq + o] = (R(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s;
+        }
     }
 }
 
@@ -465,9 +521,11 @@ void stage_impl(const Ctx &c, int stage)
         E.c2 = 1 + t2;
         E.ph = ph;
         dim3 blk(32, 8);
-        dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, c.n[d] + 1);
+        E.nf = c.n[d] + 1;
+        E.K = kMarch;
+        dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
         mark(c, K_FACE_EQ, 1);
-        face_eq_kernel<R><<<ge, blk, 0, c.stream>>>(E);
+        face_eq_march_kernel<R><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);
 
         FluxArgs<R> F;
@@ -749,8 +807,10 @@ void launch_face_eq_fp64(const Ctx &c, const double *w, int d)
     E.c1 = 1 + t1;
     E.c2 = 1 + t2;
     E.ph = ph;
-    dim3 blk(32, 8), ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, c.n[d] + 1);
-    face_eq_kernel<double><<<ge, blk, 0, c.stream>>>(E);
+    E.nf = c.n[d] + 1;
+    E.K = kMarch;
+    dim3 blk(32, 8), ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
+    face_eq_march_kernel<double><<<ge, blk, 0, c.stream>>>(E);
 }
 
 void launch_prep(const Ctx &c)

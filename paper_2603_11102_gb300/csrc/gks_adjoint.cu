@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
             st[v * 4 + 2][r][col] = dm;
             st[v * 4 + 3][r][col] = dp;
             const double *pn = &sq[4 + v][r][col];
-            tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
+            tan_val_direct(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
             st[16 + v * 2 + 0][r][col] = vm;
             st[16 + v * 2 + 1][r][col] = vp;
         }
@@ -312,10 +312,10 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
             tan_val_der(st[v * 4 + m][ty][tx], st[v * 4 + m][ty + 1][tx], st[v * 4 + m][ty + 2][tx],
                         st[v * 4 + m][ty + 3][tx], st[v * 4 + m][ty + 4][tx], vm, vp, dm, dp);
             Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
-            tan_val(st[v * 4 + 2 + m][ty][tx], st[v * 4 + 2 + m][ty + 1][tx], st[v * 4 + 2 + m][ty + 2][tx],
+            tan_val_direct(st[v * 4 + 2 + m][ty][tx], st[v * 4 + 2 + m][ty + 1][tx], st[v * 4 + 2 + m][ty + 2][tx],
                     st[v * 4 + 2 + m][ty + 3][tx], st[v * 4 + 2 + m][ty + 4][tx], vm, vp);
             D1[0][v] = vm; D1[1][v] = vp;
-            tan_val(st[16 + v * 2 + m][ty][tx], st[16 + v * 2 + m][ty + 1][tx], st[16 + v * 2 + m][ty + 2][tx],
+            tan_val_direct(st[16 + v * 2 + m][ty][tx], st[16 + v * 2 + m][ty + 1][tx], st[16 + v * 2 + m][ty + 2][tx],
                     st[16 + v * 2 + m][ty + 3][tx], st[16 + v * 2 + m][ty + 4][tx], vm, vp);
             Dn[0][v] = vm; Dn[1][v] = vp;
         }

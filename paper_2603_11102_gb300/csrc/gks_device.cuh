@@ -137,6 +137,20 @@ __device__ __forceinline__ void tan_val(R qm2, R qm1, R q0, R qp1, R qp2, R &vm,
     vp = E + O;
 }
 
+// The same values as tan_val as two 5-weight dot products (all on the FMA
+// pipe). Used for rows that vanish identically in a uniform state (normal
+// slopes, tangential derivatives), where the weights not summing exactly to
+// one in floating point is harmless.
+template <typename R>
+__device__ __forceinline__ void tan_val_direct(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp)
+{
+    const R w0 = R(-1.0 / 4320.0 + 0.028065638085606807), w1 = R(1.0 / 1080.0 - 0.20046884346862007);
+    const R w2 = R(719.0 / 720.0);
+    const R w3 = R(1.0 / 1080.0 + 0.20046884346862007), w4 = R(-1.0 / 4320.0 - 0.028065638085606807);
+    vp = fma(w4, qp2, fma(w3, qp1, fma(w2, q0, fma(w1, qm1, w0 * qm2))));
+    vm = fma(w0, qp2, fma(w1, qp1, fma(w2, q0, fma(w3, qm1, w4 * qm2))));
+}
+
 template <typename R>
 __device__ __forceinline__ void tan_val_der(R qm2, R qm1, R q0, R qp1, R qp2, R &vm, R &vp, R &dm,
                                             R &dp)

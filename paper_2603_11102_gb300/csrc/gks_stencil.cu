@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
                 st[(v * 4 + 2) * ST_ROWS + idx] = dm;
                 st[(v * 4 + 3) * ST_ROWS + idx] = dp;
                 const R *pn = sq + ((4 + v) * SQ_H + r) * SQ_W + col;
-                tan_val(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
+                tan_val_direct(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
                 st[(16 + v * 2 + 0) * ST_ROWS + idx] = vm;
                 st[(16 + v * 2 + 1) * ST_ROWS + idx] = vp;
             }
@@ -335,9 +335,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
                     R vm, vp, dm, dp;
                     tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
                     Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
-                    tan_val(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+                    tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
                     D1[0][v] = vm; D1[1][v] = vp;
-                    tan_val(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+                    tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
                     Dn[0][v] = vm; Dn[1][v] = vp;
                 }
 #pragma unroll

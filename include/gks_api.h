@@ -66,7 +66,8 @@ typedef struct gks_grid gks_grid;
 
 /* Grid description (Sec. 2; Sec. 4 for the boundary kinds).
  *   n[d]       cells along axis d (x, y, z). >= 3 for non-periodic axes, >= 1
- *              for periodic ones (n = 1 collapses an axis).
+ *              for periodic ones (n = 1 collapses an axis); at most 2^24
+ *              per axis and (n[0]+1)(n[1]+1)(n[2]+1) <= 2e9.
  *   faces[d]   host array of n[d]+1 strictly increasing face coordinates
  *              (uniform or stretched; reconstruction is done in index space
  *              and derivatives use the local cell widths).

@@ -88,6 +88,8 @@ int validate(const gks_grid_desc *d, std::string *msg)
     if (!(d->mach > 0.0) || !(d->u_ref > 0.0) || !(d->mu >= 0.0)) { *msg = "bad mach, u_ref or mu"; return GKS_ERR_ARG; }
     if (!(d->dt_fixed > 0.0) && !(d->cfl > 0.0)) { *msg = "need cfl > 0 or dt_fixed > 0"; return GKS_ERR_ARG; }
     if (d->precision == GKS_FP32C && !(d->rho_ref > 0.0)) { *msg = "rho_ref must be > 0"; return GKS_ERR_ARG; }
+    // face-tile indices of the flux kernels are 32-bit
+    if ((double)(d->n[0] + 1) * (d->n[1] + 1) * (d->n[2] + 1) > 2.0e9) { *msg = "too many cells"; return GKS_ERR_ARG; }
     return GKS_OK;
 }
 

@@ -252,6 +252,51 @@ struct FluxArgs {
     Scalars *scal;
 };
 
+// 8 consecutive values of a shared-memory row from a 16-byte aligned address,
+// and 4 consecutive values to one.
+__device__ __forceinline__ void lds8(const float *p, float q[8])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+    q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double *p, double q[8])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[i];
+        q[2 * i] = a.x;
+        q[2 * i + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void sts4(float *p, const float q[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(q[0], q[1], q[2], q[3]);
+}
+__device__ __forceinline__ void sts4(double *p, const double q[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(q[0], q[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(q[2], q[3]);
+}
+
+// Tile t of the face box as (t1 tile, t2 tile, face): t = ta + NA (tb + NB f).
+struct TileIdx {
+    int ta, tb, f;
+};
+
+// t + g for a step g given in the same mixed radix (ga < NA, gb < NB).
+__device__ __forceinline__ TileIdx tile_add(TileIdx t, const TileIdx &g, int NA, int NB)
+{
+    t.ta += g.ta;
+    t.tb += g.tb;
+    t.f += g.f;
+    if (t.ta >= NA) { t.ta -= NA; t.tb += 1; }
+    if (t.tb >= NB) { t.tb -= NB; t.f += 1; }
+    return t;
+}
+
+static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assumes 32 x 8 tiles");
+
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of the next tile is fetched by TMA into the other buffer while the
 // current one is computed.
@@ -264,26 +309,26 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
-    const long ntiles = (long)NA * NB * A.nf;
+    const int ntiles = NA * NB * A.nf;
     const uint32_t bytes = (uint32_t)(SQ_N * sizeof(R));
+    // the block's first tile and its stride, in (ta, tb, f)
+    const TileIdx g = {(int)(gridDim.x % NA), (int)((gridDim.x / NA) % NB), (int)(gridDim.x / (NA * NB))};
+    TileIdx cur = {(int)(blockIdx.x % NA), (int)((blockIdx.x / NA) % NB), (int)(blockIdx.x / (NA * NB))};
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    long t = blockIdx.x;
-    if (tid == 0 && t < ntiles) {
-        const int ta = (int)(t % NA), tb = (int)((t / NA) % NB), f = (int)(t / ((long)NA * NB));
-        tma_load_tile(&tmap, sqb, &bar[0], ta * TX, tb * TY, f, bytes);
-    }
+    int t = blockIdx.x;
+    if (tid == 0 && t < ntiles) tma_load_tile(&tmap, sqb, &bar[0], cur.ta * TX, cur.tb * TY, cur.f, bytes);
     for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
         const int buf = k & 1;
-        const long tn = t + gridDim.x;
+        const int tn = t + gridDim.x;
+        const TileIdx nxt = tile_add(cur, g, NA, NB);
         if (tid == 0 && tn < ntiles) {
             fence_proxy_async();
-            const int ta = (int)(tn % NA), tb = (int)((tn / NA) % NB), f = (int)(tn / ((long)NA * NB));
-            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], ta * TX, tb * TY, f, bytes);
+            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], nxt.ta * TX, nxt.tb * TY, nxt.f, bytes);
         }
         const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
@@ -295,26 +340,36 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             return;
         }
         const R *sq = sqb + buf * SQ_N;
-        const int ta = (int)(t % NA), tb = (int)((t / NA) % NB), f = (int)(t / ((long)NA * NB));
-        const int a0 = ta * TX, b0 = tb * TY;
+        const int a0 = cur.ta * TX, b0 = cur.tb * TY, f = cur.f;
+        cur = nxt;
 
         // t1 pass: values and t1-derivatives of Q0, values of the normal
-        // slope, at the two t1 Gauss points, for every row of the tile
-        for (int idx = tid; idx < ST_ROWS; idx += TX * TY) {
-            const int r = idx / TX, col = idx - r * TX;
+        // slope, at the two t1 Gauss points, for every row of the tile. 768
+        // equal tasks (Q0 or slope, component, row, group of 4 columns): a
+        // task reads 8 consecutive values of its row and writes 4 columns;
+        // the lanes of a warp share the kind and the component.
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const R *p = sq + (v * SQ_H + r) * SQ_W + col;
-                R vm, vp, dm, dp;
-                tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
-                st[(v * 4 + 0) * ST_ROWS + idx] = vm;
-                st[(v * 4 + 1) * ST_ROWS + idx] = vp;
-                st[(v * 4 + 2) * ST_ROWS + idx] = dm;
-                st[(v * 4 + 3) * ST_ROWS + idx] = dp;
-                const R *pn = sq + ((4 + v) * SQ_H + r) * SQ_W + col;
-                tan_val_direct(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
-                st[(16 + v * 2 + 0) * ST_ROWS + idx] = vm;
-                st[(16 + v * 2 + 1) * ST_ROWS + idx] = vp;
+        for (int j = 0; j < 3; ++j) {
+            const int task = tid + j * 256;
+            const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
+            const int r = rc >> 3, cg = rc & 7;
+            R q[8];
+            lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
+            R *o = st + r * TX + 4 * cg;
+            if (kind == 0) {
+                R vm[4], vp[4], dm[4], dp[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
+                sts4(o + (v * 4 + 0) * ST_ROWS, vm);
+                sts4(o + (v * 4 + 1) * ST_ROWS, vp);
+                sts4(o + (v * 4 + 2) * ST_ROWS, dm);
+                sts4(o + (v * 4 + 3) * ST_ROWS, dp);
+            } else {
+                R vm[4], vp[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
+                sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
+                sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
             }
         }
         __syncthreads();

@@ -83,10 +83,10 @@ inline void mark(const Ctx &c, int group, int begin)
 void record_error(const char *msg);
 
 // Launchers of the stencil path (gks_stencil.cu).
-void launch_prep(const Ctx &c);                        // FP32C: state -> wk0
+void launch_prep(const Ctx &c);                        // max |U|^2 into scal; FP32C: state -> wk0
 void launch_ghost(const Ctx &c, void *w);              // 3 ghost layers of w (working type)
 void launch_stage(const Ctx &c, int stage);            // face kernels + update
-void launch_cfl(const Ctx &c);                          // max|U| and dt into scal
+void launch_cfl(const Ctx &c);                          // dt from max |U| (after launch_prep)
 void launch_advance(const Ctx &c);                      // t += dt
 void launch_scatter_state(const Ctx &c, const double *d_src);  // compact FP64 -> state
 void launch_gather_state(const Ctx &c, double *d_dst);         // state -> compact FP64

@@ -475,46 +475,60 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
     const long iz = ((long)k * ny + j) * nx + i, sz = (long)ny * nx;
     const double dt = A.scal->dt;
     const R dtr = (R)dt;
-    bool bad = false;
+    // Every load is issued before the first store: the outputs are distinct
+    // buffers, but through untyped pointers the compiler would otherwise
+    // keep each component's loads behind the previous component's stores.
+    R L[4], Lt[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const int cx = STAGE == 1 ? 4 + v : v;
         const R *fy = A.ff[1] + (4 + v) * A.nff[1];
         const R *fz = A.ff[2] + (4 + v) * A.nff[2];
-        const R Lt = -((sx[cx][threadIdx.x + 1][threadIdx.y] - sx[cx][threadIdx.x][threadIdx.y]) * ihx +
-                       (__ldg(fy + iy + sy) - __ldg(fy + iy)) * ihy +
-                       (__ldg(fz + iz + sz) - __ldg(fz + iz)) * ihz);
+        Lt[v] = -((sx[cx][threadIdx.x + 1][threadIdx.y] - sx[cx][threadIdx.x][threadIdx.y]) * ihx +
+                  (__ldg(fy + iy + sy) - __ldg(fy + iy)) * ihy + (__ldg(fz + iz + sz) - __ldg(fz + iz)) * ihz);
         if (STAGE == 1) {
             const R *gy = A.ff[1] + v * A.nff[1];
             const R *gz = A.ff[2] + v * A.nff[2];
-            const R L = -((sx[v][threadIdx.x + 1][threadIdx.y] - sx[v][threadIdx.x][threadIdx.y]) * ihx +
-                          (__ldg(gy + iy + sy) - __ldg(gy + iy)) * ihy +
-                          (__ldg(gz + iz + sz) - __ldg(gz + iz)) * ihz);
+            L[v] = -((sx[v][threadIdx.x + 1][threadIdx.y] - sx[v][threadIdx.x][threadIdx.y]) * ihx +
+                     (__ldg(gy + iy + sy) - __ldg(gy + iy)) * ihy + (__ldg(gz + iz + sz) - __ldg(gz + iz)) * ihz);
+        }
+    }
+    // state: stage 1 reads W^n, stage 2 reads P
+    R s0[4], s1[4];
+    {
+        const R *src = (const R *)(STAGE == 1 ? A.w0 : A.pbuf);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            s0[v] = __ldg(src + v * A.np + lin);
+            s1[v] = std::is_same<R, double>::value ? R(0) : __ldg(src + (4 + v) * A.np + lin);
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (STAGE == 1) {
             if constexpr (std::is_same<R, double>::value) {
-                const double *W = (const double *)A.w0;
-                const double w = W[v * A.np + lin];
-                ((double *)A.wk1)[v * A.np + lin] = w + 0.5 * dt * L + 0.125 * dt * dt * Lt;
-                ((double *)A.pbuf)[v * A.np + lin] = w + dt * L + dt * dt / 6.0 * Lt;
+                const double w = s0[v];
+                ((double *)A.wk1)[v * A.np + lin] = w + 0.5 * dt * L[v] + 0.125 * dt * dt * Lt[v];
+                ((double *)A.pbuf)[v * A.np + lin] = w + dt * L[v] + dt * dt / 6.0 * Lt[v];
             } else {
-                const float *S = (const float *)A.w0;
-                float hi = S[v * A.np + lin], lo = S[(4 + v) * A.np + lin];
+                float hi = s0[v], lo = s1[v];
                 const float offv = v == 0 ? A.off : 0.0f;
                 ((float *)A.wk1)[v * A.np + lin] =
-                    ((hi - offv) + lo) + (0.5f * dtr * L + 0.125f * dtr * dtr * Lt);
-                add_comp(hi, lo, dtr * L + dtr * dtr * (1.0f / 6.0f) * Lt);
+                    ((hi - offv) + lo) + (0.5f * dtr * L[v] + 0.125f * dtr * dtr * Lt[v]);
+                add_comp(hi, lo, dtr * L[v] + dtr * dtr * (1.0f / 6.0f) * Lt[v]);
                 ((float *)A.pbuf)[v * A.np + lin] = hi;
                 ((float *)A.pbuf)[(4 + v) * A.np + lin] = lo;
             }
         } else {
             if constexpr (std::is_same<R, double>::value) {
-                double w = ((const double *)A.pbuf)[v * A.np + lin] + dt * dt / 3.0 * Lt;
+                double w = s0[v] + dt * dt / 3.0 * Lt[v];
                 if (v > 0) w += dt * (double)A.fb[v - 1];
                 ((double *)A.state)[v * A.np + lin] = w;
                 bad |= !isfinite(w);
             } else {
-                float hi = ((const float *)A.pbuf)[v * A.np + lin];
-                float lo = ((const float *)A.pbuf)[(4 + v) * A.np + lin];
-                float inc = dtr * dtr * (1.0f / 3.0f) * Lt;
+                float hi = s0[v], lo = s1[v];
+                float inc = dtr * dtr * (1.0f / 3.0f) * Lt[v];
                 if (v > 0) inc += dtr * A.fb[v - 1];
                 add_comp(hi, lo, inc);
                 ((float *)A.state)[v * A.np + lin] = hi;
@@ -633,15 +647,54 @@ void stage_impl(const Ctx &c, int stage)
 
 // ----------------------------------------------------- prep, CFL, misc --
 
-__global__ void __launch_bounds__(256) prep_kernel(const float *S, float *wk, long np, int nx, int ny,
-                                                   int nz, int P0, int P1, float off)
+constexpr int kPrepZ = 8;   // z planes per block of the prep / CFL kernel
+
+// max(a, b) that keeps a NaN (so that a non-finite state reaches dt).
+__device__ __forceinline__ double max_nan(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Start of a step: the largest |U|^2 over the interior cells (for the CFL
+// time step), and for FP32C the FP32 reconstruction input hi + lo (density
+// as rho - off). One atomicMax per block.
+template <int PREC>
+__global__ void __launch_bounds__(256) prep_cfl_kernel(const void *S, float *wk, long np, int nx, int ny,
+                                                       int nz, int P0, int P1, float off, Scalars *scal)
 {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-    if (i >= nx || j >= ny) return;
-    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+    __shared__ double red[8];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * kPrepZ, k1 = min(k0 + kPrepZ, nz);
+    double mx = 0.0;
+    if (i < nx && j < ny) {
+        for (int k = k0; k < k1; ++k) {
+            const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+            double u2;
+            if (PREC == GKS_FP64) {
+                const double *W = (const double *)S;
+                const double r = W[lin], a = W[np + lin], b = W[2 * np + lin], c = W[3 * np + lin];
+                u2 = (a * a + b * b + c * c) / (r * r);
+            } else {
+                const float *W = (const float *)S;
+                float h[4], l[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-        wk[v * np + lin] = (S[v * np + lin] - (v == 0 ? off : 0.0f)) + S[(4 + v) * np + lin];
+                for (int v = 0; v < 4; ++v) {
+                    h[v] = W[v * np + lin];
+                    l[v] = W[(4 + v) * np + lin];
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) wk[v * np + lin] = (h[v] - (v == 0 ? off : 0.0f)) + l[v];
+                // the time step needs no more than FP32 hi + lo
+                const float r = h[0] + l[0], a = h[1] + l[1], b = h[2] + l[2], c = h[3] + l[3];
+                u2 = (double)((a * a + b * b + c * c) / (r * r));
+            }
+            mx = max_nan(mx, u2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max_nan(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) red[threadIdx.y] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = max_nan(mx, red[w]);
+        atomicMax(&scal->maxu2_bits, (unsigned long long)__double_as_longlong(mx));
+    }
 }
 
 __device__ __forceinline__ void load_cell(int prec, const void *S, long np, long lin, double q[4])
@@ -655,38 +708,6 @@ __device__ __forceinline__ void load_cell(int prec, const void *S, long np, long
 #pragma unroll
         for (int v = 0; v < 4; ++v) q[v] = (double)W[v * np + lin] + (double)W[(4 + v) * np + lin];
     }
-}
-
-__global__ void __launch_bounds__(256) cfl_kernel(int prec, const void *S, long np, int nx, int ny,
-                                                  int nz, int P0, int P1, Scalars *scal)
-{
-    const long ncell = (long)nx * ny * nz;
-    double mx = 0.0;
-    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell;
-         c += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx);
-        const long r = c / nx;
-        const int j = (int)(r % ny), k = (int)(r / ny);
-        const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
-        double u2;
-        if (prec == GKS_FP64) {
-            const double *W = (const double *)S;
-            const double r = W[lin], a = W[np + lin], b = W[2 * np + lin], c2 = W[3 * np + lin];
-            u2 = (a * a + b * b + c2 * c2) / (r * r);
-        } else {
-            // FP32C: hi + lo in FP32 (the time step needs no more)
-            const float *W = (const float *)S;
-            const float r = W[lin] + W[4 * np + lin], a = W[np + lin] + W[5 * np + lin];
-            const float b = W[2 * np + lin] + W[6 * np + lin], c2 = W[3 * np + lin] + W[7 * np + lin];
-            u2 = (double)((a * a + b * b + c2 * c2) / (r * r));
-        }
-        mx = (u2 > mx || u2 != u2) ? u2 : mx;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = (y > mx || y != y) ? y : mx;
-    }
-    if ((threadIdx.x & 31) == 0) atomicMax(&scal->maxu2_bits, (unsigned long long)__double_as_longlong(mx));
 }
 
 __global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmin, double csound)
@@ -870,12 +891,16 @@ void launch_face_eq_fp64(const Ctx &c, const double *w, int d)
 
 void launch_prep(const Ctx &c)
 {
-    if (c.prec != GKS_FP32C) return;
-    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
-    mark(c, K_PREP, 1);
-    prep_kernel<<<g, blk, 0, c.stream>>>((const float *)c.state, (float *)c.wk0, c.np, c.n[0], c.n[1],
-                                         c.n[2], c.P[0], c.P[1], (float)c.off);
-    mark(c, K_PREP, 0);
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, (c.n[2] + kPrepZ - 1) / kPrepZ);
+    const int grp = c.prec == GKS_FP32C ? K_PREP : K_CFL;
+    mark(c, grp, 1);
+    if (c.prec == GKS_FP32C)
+        prep_cfl_kernel<GKS_FP32C><<<g, blk, 0, c.stream>>>(c.state, (float *)c.wk0, c.np, c.n[0], c.n[1], c.n[2],
+                                                           c.P[0], c.P[1], (float)c.off, c.scal);
+    else
+        prep_cfl_kernel<GKS_FP64><<<g, blk, 0, c.stream>>>(c.state, nullptr, c.np, c.n[0], c.n[1], c.n[2], c.P[0],
+                                                          c.P[1], 0.0f, c.scal);
+    mark(c, grp, 0);
 }
 
 void launch_ghost(const Ctx &c, void *w)
@@ -896,10 +921,6 @@ void launch_stage(const Ctx &c, int stage)
 
 void launch_cfl(const Ctx &c)
 {
-    mark(c, K_CFL, 1);
-    cfl_kernel<<<reduce_blocks(c.ncell), 256, 0, c.stream>>>(c.prec, c.state, c.np, c.n[0], c.n[1],
-                                                             c.n[2], c.P[0], c.P[1], c.scal);
-    mark(c, K_CFL, 0);
     mark(c, K_MISC, 1);
     dt_kernel<<<1, 1, 0, c.stream>>>(c.scal, c.cfl, c.dt_fixed, c.hmin, c.csound);
     mark(c, K_MISC, 0);

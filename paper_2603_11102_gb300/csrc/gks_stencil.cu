@@ -216,13 +216,25 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
         R l;
         weno5_pair(w[v], Qprev[v], l);
     }
+    // the cell entering the window, loaded one face ahead
+    R nxt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) nxt[v] = __ldg(A.w + comp[v] * A.np + base + (long)(f0 + 2 + G) * A.sd);
     for (int f = f0; f < f1; ++f) {
         R Ql[4], Qr[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) w[v][k] = w[v][k + 1];
-            w[v][4] = __ldg(A.w + comp[v] * A.np + base + (long)(f + 2 + G) * A.sd);
+            w[v][4] = nxt[v];
+        }
+        if (f + 1 < f1) {
+            // cell f + 3 <= nf + 1 = n + 2: inside the ghost layers
+#pragma unroll
+            for (int v = 0; v < 4; ++v) nxt[v] = __ldg(A.w + comp[v] * A.np + base + (long)(f + 3 + G) * A.sd);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
             Ql[v] = Qprev[v];
             weno5_pair(w[v], Qprev[v], Qr[v]);
         }

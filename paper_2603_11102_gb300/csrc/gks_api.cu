@@ -107,7 +107,9 @@ void plan(const gks_grid_desc *d, Layout *L)
         L->e1p[a] = (d->n[t1] + 4 + 3) / 4 * 4;
         const long nfq = (long)(d->n[a] + 1) * (d->n[t2] + 4) * L->e1p[a];
         if (nfq > L->nfq) L->nfq = nfq;
-        L->nff[a] = (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
+        // face fluxes are kept for x and y only: the z-face kernel applies
+        // the stage update itself
+        L->nff[a] = a == 2 ? 0 : (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
     }
     L->nfq = (L->nfq + 63) / 64 * 64;
     size_t o = 0;

@@ -305,6 +305,23 @@ __device__ __forceinline__ void tma_load_tile(const CUtensorMap *map, void *dst,
         : "memory");
 }
 
+// 4- or 8-byte asynchronous copy global -> shared (completion through
+// cp.async groups), and the group fences.
+__device__ __forceinline__ void cp_async(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)),
+                 "l"((unsigned long long)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async(double *dst, const double *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)),
+                 "l"((unsigned long long)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Wait for phase `parity` of bar; gives up after ~1 s of SM clock and
 // returns false (the caller raises FLAG_TIMEOUT).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)

@@ -59,7 +59,7 @@ struct Ctx {
     long nfq;
     int e1p[3];               // padded t1 extent of the face box per direction (multiple of 4)
     CUtensorMap tmap[3];      // TMA descriptors of the face box per direction
-    void *ff[3];              // face-averaged F0 and F1 per direction, R[8][nff]
+    void *ff[3];              // face-averaged F0 and F1 of x and y faces, R[8][nff] (none for z)
     long nff[3];
     void *ih[3];              // R: inverse cell widths, padded index i + 3
     void *ihf[3];             // R: inverse centre distance at faces, f = 0..n

@@ -309,6 +309,77 @@ __device__ __forceinline__ TileIdx tile_add(TileIdx t, const TileIdx &g, int NA,
 
 static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assumes 32 x 8 tiles");
 
+// t1 pass of one tile: values and t1-derivatives of Q0, values of the normal
+// slope, at the two t1 Gauss points, for every row of the tile. 768 equal
+// tasks (Q0 or slope, component, row, group of 4 columns): a task reads 8
+// consecutive values of its row and writes 4 columns; the lanes of a warp
+// share the kind and the component.
+template <typename R>
+__device__ __forceinline__ void tile_t1_pass(const R *sq, R *st, int tid)
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int task = tid + j * 256;
+        const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
+        const int r = rc >> 3, cg = rc & 7;
+        R q[8];
+        lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
+        R *o = st + r * TX + 4 * cg;
+        if (kind == 0) {
+            R vm[4], vp[4], dm[4], dp[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
+            sts4(o + (v * 4 + 0) * ST_ROWS, vm);
+            sts4(o + (v * 4 + 1) * ST_ROWS, vp);
+            sts4(o + (v * 4 + 2) * ST_ROWS, dm);
+            sts4(o + (v * 4 + 3) * ST_ROWS, dp);
+        } else {
+            R vm[4], vp[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
+            sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
+            sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
+        }
+    }
+}
+
+// t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g): the
+// sums of F0 and F1 over the 4 Gauss points of face (tx, ty) of the tile.
+template <typename R, bool NEED_F0>
+__device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, int tx, int ty, R ih1, R ih2,
+                                                R acc0[4], R acc1[4])
+{
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc0[v] = acc1[v] = R(0);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        R Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const R *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+            const R *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+            const R *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+            R vm, vp, dm, dp;
+            tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
+            Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
+            tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+            D1[0][v] = vm; D1[1][v] = vp;
+            tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+            Dn[0][v] = vm; Dn[1][v] = vp;
+        }
+#pragma unroll
+        for (int nn = 0; nn < 2; ++nn) {
+            R F0[4], F1[4];
+            gk_flux<R, NEED_F0>(ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, F0, F1);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (NEED_F0) acc0[v] += F0[v];
+                acc1[v] += F1[v];
+            }
+        }
+    }
+}
+
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of the next tile is fetched by TMA into the other buffer while the
 // current one is computed.
@@ -355,69 +426,14 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
         const int a0 = cur.ta * TX, b0 = cur.tb * TY, f = cur.f;
         cur = nxt;
 
-        // t1 pass: values and t1-derivatives of Q0, values of the normal
-        // slope, at the two t1 Gauss points, for every row of the tile. 768
-        // equal tasks (Q0 or slope, component, row, group of 4 columns): a
-        // task reads 8 consecutive values of its row and writes 4 columns;
-        // the lanes of a warp share the kind and the component.
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int task = tid + j * 256;
-            const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
-            const int r = rc >> 3, cg = rc & 7;
-            R q[8];
-            lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
-            R *o = st + r * TX + 4 * cg;
-            if (kind == 0) {
-                R vm[4], vp[4], dm[4], dp[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
-                sts4(o + (v * 4 + 0) * ST_ROWS, vm);
-                sts4(o + (v * 4 + 1) * ST_ROWS, vp);
-                sts4(o + (v * 4 + 2) * ST_ROWS, dm);
-                sts4(o + (v * 4 + 3) * ST_ROWS, dp);
-            } else {
-                R vm[4], vp[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
-                sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
-                sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
-            }
-        }
+        tile_t1_pass(sq, st, tid);
         __syncthreads();
 
         const int a = a0 + tx, b = b0 + ty;
         if (a < A.n1 && b < A.n2) {
             const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
-            R acc0[4] = {R(0), R(0), R(0), R(0)}, acc1[4] = {R(0), R(0), R(0), R(0)};
-            // t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g)
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                R Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const R *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
-                    const R *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
-                    const R *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
-                    R vm, vp, dm, dp;
-                    tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
-                    Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
-                    tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
-                    D1[0][v] = vm; D1[1][v] = vp;
-                    tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
-                    Dn[0][v] = vm; Dn[1][v] = vp;
-                }
-#pragma unroll
-                for (int nn = 0; nn < 2; ++nn) {
-                    R F0[4], F1[4];
-                    gk_flux<R, NEED_F0>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, F0, F1);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        if (NEED_F0) acc0[v] += F0[v];
-                        acc1[v] += F1[v];
-                    }
-                }
-            }
+            R acc0[4], acc1[4];
+            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1);
             const long o = ((long)f * A.n2 + b) * A.n1 + a;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -429,14 +445,14 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
     }
 }
 
-// ---------------------------------------------------------------- update --
+// ------------------------------------------------- z flux + stage update --
 
 template <typename R>
 struct UpdArgs {
-    const R *ff[3];
-    long nff[3];
-    const R *ih[3];
-    int n[3], P[3];
+    const R *ffx, *ffy;   // face fluxes of the x and y directions (8 arrays each)
+    long nffx, nffy;
+    const R *ihz;         // inverse cell widths along z (padded index)
+    int nx, ny, nz, P0, P1;
     long np;
     const void *w0;   // stage 1: state (FP64 W / FP32C hi,lo)
     void *wk1;        // stage 1 output W* (R)
@@ -444,7 +460,7 @@ struct UpdArgs {
     void *state;      // stage 2 output
     R off;
     R fb[3];
-    Scalars *scal;
+    int seg;          // z-faces per segment of the fused z kernel
 };
 
 __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
@@ -459,88 +475,45 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
     hi = h2;
 }
 
+// Stage update of one cell from the differences of its face fluxes along x,
+// y, z (high minus low face, global components; entries 0..3 hold F0, used
+// in stage 1 only, entries 4..7 hold F1):
+//   L = -sum_d dF0_d / h_d, Lt = -sum_d dF1_d / h_d,
+//   stage 1: W* = W + dt/2 L + dt^2/8 Lt, P = W + dt L + dt^2/6 Lt,
+//   stage 2: W = P + dt^2/3 Lt(W*) + dt f_body.
+// Returns false when a written value is not finite (stage 2).
 template <typename R, int STAGE>
-__global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
+__device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, double dt, const R dx[], const R dy[],
+                                            const R dz[], R ihx, R ihy, R ihz, const R s0[4], const R s1[4])
 {
-    // x-face fluxes are stored y-fastest ([x][z][y]); the block's 33 x-faces
-    // by 8 y rows are staged through shared memory so that every global read
-    // of the kernel is a full sector.
-    constexpr int NC = STAGE == 1 ? 8 : 4;
-    __shared__ R sx[NC][33][9];
-    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8, k = blockIdx.z;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int e = tid; e < NC * 33 * 8; e += 256) {
-        const int cc = e / (33 * 8), rem = e - cc * 33 * 8, f = rem >> 3, jj = rem & 7;
-        const int comp = STAGE == 1 ? cc : 4 + cc;
-        R v = R(0);
-        if (i0 + f <= nx && j0 + jj < ny)
-            v = __ldg(A.ff[0] + comp * A.nff[0] + ((long)(i0 + f) * nz + k) * ny + j0 + jj);
-        sx[cc][f][jj] = v;
-    }
-    __syncthreads();
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (i >= nx || j >= ny) return;
-    const long lin = (long)(i + G) + (long)A.P[0] * ((long)(j + G) + (long)A.P[1] * (k + G));
-    const R ihx = __ldg(A.ih[0] + i + G), ihy = __ldg(A.ih[1] + j + G), ihz = __ldg(A.ih[2] + k + G);
-    const long iy = ((long)j * nz + k) * nx + i, sy = (long)nz * nx;
-    const long iz = ((long)k * ny + j) * nx + i, sz = (long)ny * nx;
-    const double dt = A.scal->dt;
     const R dtr = (R)dt;
-    // Every load is issued before the first store: the outputs are distinct
-    // buffers, but through untyped pointers the compiler would otherwise
-    // keep each component's loads behind the previous component's stores.
-    R L[4], Lt[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int cx = STAGE == 1 ? 4 + v : v;
-        const R *fy = A.ff[1] + (4 + v) * A.nff[1];
-        const R *fz = A.ff[2] + (4 + v) * A.nff[2];
-        Lt[v] = -((sx[cx][threadIdx.x + 1][threadIdx.y] - sx[cx][threadIdx.x][threadIdx.y]) * ihx +
-                  (__ldg(fy + iy + sy) - __ldg(fy + iy)) * ihy + (__ldg(fz + iz + sz) - __ldg(fz + iz)) * ihz);
-        if (STAGE == 1) {
-            const R *gy = A.ff[1] + v * A.nff[1];
-            const R *gz = A.ff[2] + v * A.nff[2];
-            L[v] = -((sx[v][threadIdx.x + 1][threadIdx.y] - sx[v][threadIdx.x][threadIdx.y]) * ihx +
-                     (__ldg(gy + iy + sy) - __ldg(gy + iy)) * ihy + (__ldg(gz + iz + sz) - __ldg(gz + iz)) * ihz);
-        }
-    }
-    // state: stage 1 reads W^n, stage 2 reads P
-    R s0[4], s1[4];
-    {
-        const R *src = (const R *)(STAGE == 1 ? A.w0 : A.pbuf);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            s0[v] = __ldg(src + v * A.np + lin);
-            s1[v] = std::is_same<R, double>::value ? R(0) : __ldg(src + (4 + v) * A.np + lin);
-        }
-    }
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
+        const R Lt = -(dx[4 + v] * ihx + dy[4 + v] * ihy + dz[4 + v] * ihz);
         if (STAGE == 1) {
+            const R L = -(dx[v] * ihx + dy[v] * ihy + dz[v] * ihz);
             if constexpr (std::is_same<R, double>::value) {
                 const double w = s0[v];
-                ((double *)A.wk1)[v * A.np + lin] = w + 0.5 * dt * L[v] + 0.125 * dt * dt * Lt[v];
-                ((double *)A.pbuf)[v * A.np + lin] = w + dt * L[v] + dt * dt / 6.0 * Lt[v];
+                ((double *)A.wk1)[v * A.np + lin] = w + 0.5 * dt * L + 0.125 * dt * dt * Lt;
+                ((double *)A.pbuf)[v * A.np + lin] = w + dt * L + dt * dt / 6.0 * Lt;
             } else {
                 float hi = s0[v], lo = s1[v];
                 const float offv = v == 0 ? A.off : 0.0f;
-                ((float *)A.wk1)[v * A.np + lin] =
-                    ((hi - offv) + lo) + (0.5f * dtr * L[v] + 0.125f * dtr * dtr * Lt[v]);
-                add_comp(hi, lo, dtr * L[v] + dtr * dtr * (1.0f / 6.0f) * Lt[v]);
+                ((float *)A.wk1)[v * A.np + lin] = ((hi - offv) + lo) + (0.5f * dtr * L + 0.125f * dtr * dtr * Lt);
+                add_comp(hi, lo, dtr * L + dtr * dtr * (1.0f / 6.0f) * Lt);
                 ((float *)A.pbuf)[v * A.np + lin] = hi;
                 ((float *)A.pbuf)[(4 + v) * A.np + lin] = lo;
             }
         } else {
             if constexpr (std::is_same<R, double>::value) {
-                double w = s0[v] + dt * dt / 3.0 * Lt[v];
+                double w = s0[v] + dt * dt / 3.0 * Lt;
                 if (v > 0) w += dt * (double)A.fb[v - 1];
                 ((double *)A.state)[v * A.np + lin] = w;
                 bad |= !isfinite(w);
             } else {
                 float hi = s0[v], lo = s1[v];
-                float inc = dtr * dtr * (1.0f / 3.0f) * Lt[v];
+                float inc = dtr * dtr * (1.0f / 3.0f) * Lt;
                 if (v > 0) inc += dtr * A.fb[v - 1];
                 add_comp(hi, lo, inc);
                 ((float *)A.state)[v * A.np + lin] = hi;
@@ -549,40 +522,244 @@ __global__ void __launch_bounds__(256) update_kernel(UpdArgs<R> A)
             }
         }
     }
+    return !bad;
+}
+
+constexpr int SX_H = TX + 1, SX_W = TY + 1;   // x-face slab of a tile in shared memory (padded)
+
+template <typename R>
+constexpr size_t flux_update_smem_bytes(int nc)
+{
+    return flux_smem_bytes<R>() + (size_t)nc * SX_H * SX_W * sizeof(R);
+}
+
+// z-direction face flux fused with the stage update. Work items are
+// (z segment, tile column) pairs, segment-major, taken round-robin by the
+// persistent blocks, so that the blocks resident at one time march through
+// the same z range of neighbouring columns (their tile halos and the x-face
+// rows they read are shared through L2). Inside an item a block walks the
+// segment's z-faces in order: F(f) - F(f-1) of the column is formed in
+// registers and cell f-1 is updated at once; the first face of an item
+// (the last face of the previous segment) only primes F. The x-face fluxes
+// of the cell plane (x-fastest reads of a y-fastest array) are copied
+// asynchronously into a padded shared slab at the start of the tile; the
+// y-face fluxes and the state are read directly (x-fastest, like the
+// threads).
+struct ZWalk {
+    int it, f, fe, f0;   // item, face, end face (exclusive), first (priming) face of the item
+};
+
+__device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int L, int nf)
+{
+    const int sgm = it / ncol;
+    ZWalk z;
+    z.it = it;
+    z.f0 = sgm > 0 ? sgm * L - 1 : 0;
+    z.f = z.f0;
+    z.fe = min((sgm + 1) * L, nf);
+    return z;
+}
+
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A, UpdArgs<R> U)
+{
+    constexpr bool NEED_F0 = STAGE == 1;
+    constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
+    R *st = sqb + 2 * SQ_N;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
+    R *sx = reinterpret_cast<R *>(bar + 2);               // [NC][SX_H][SX_W]
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY, nf = A.nf, L = U.seg;
+    const int ncol = NA * NB, nitems = ncol * ((nf + L - 1) / L);
+    if ((int)blockIdx.x >= nitems) return;
+    const uint32_t bytes = (uint32_t)(SQ_N * sizeof(R));
+    ZWalk cur = zwalk_item(blockIdx.x, ncol, L, nf);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int col = cur.it % ncol;
+        tma_load_tile(&tmap, sqb, &bar[0], (col % NA) * TX, (col / NA) * TY, cur.f, bytes);
+    }
+    const double dt = A.scal->dt;
+    bool bad = false;
+    R P0[4], P1[4];   // F0, F1 of the previous face of this column
+    for (int k = 0; cur.it < nitems; ++k) {
+        const int buf = k & 1;
+        ZWalk nxt = cur;
+        if (++nxt.f >= nxt.fe) nxt = zwalk_item(cur.it + gridDim.x, ncol, L, nf);
+        if (tid == 0 && nxt.it < nitems) {
+            fence_proxy_async();
+            const int col = nxt.it % ncol;
+            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], (col % NA) * TX, (col / NA) * TY, nxt.f,
+                          bytes);
+        }
+        const int col = cur.it % ncol, f = cur.f;
+        const int a0 = (col % NA) * TX, b0 = (col / NA) * TY;
+        const bool upd = f > cur.f0;
+        if (upd) {
+            // x-face fluxes of cell plane z = f-1: faces a0 .. a0+32, rows b0 .. b0+7.
+            // Thread: row y = b0 + (tid & 7); slab rows r = (c, xf) = tid/8 + 32 i.
+            const int yy = tid & 7;
+            if (b0 + yy < U.ny) {
+                const long sxf = (long)U.nz * U.ny;   // stride between x-faces
+                const R *src = U.ffx + C0 * U.nffx + ((long)a0 * U.nz + (f - 1)) * U.ny + b0 + yy;
+                int c = 0, xf = tid >> 3;
+                long go = xf * sxf;
+#pragma unroll
+                for (int i = 0; i < (NC * SX_H + 31) / 32; ++i) {
+                    if (c < NC && a0 + xf <= U.nx) cp_async(sx + (c * SX_H + xf) * SX_W + yy, src + go);
+                    xf += 32;
+                    go += 32 * sxf;
+                    if (xf >= SX_H) {
+                        xf -= SX_H;
+                        ++c;
+                        go += U.nffx - SX_H * sxf;
+                    }
+                }
+            }
+            cp_async_commit();
+        }
+        // y-face flux differences and the state of this thread's cell, loaded
+        // now so that they arrive during the flux computation
+        const int a = a0 + tx, b = b0 + ty;
+        const bool in = a < A.n1 && b < A.n2;
+        R dy[8], s0[4], s1[4];
+        long lin = 0;
+        if (upd && in) {
+            const int z = f - 1;
+            lin = (long)(a + G) + (long)U.P0 * ((long)(b + G) + (long)U.P1 * (z + G));
+            const long iy = ((long)b * U.nz + z) * U.nx + a, sy = (long)U.nz * U.nx;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const R *py = U.ffy + (C0 + c) * U.nffy + iy;
+                dy[C0 + c] = __ldg(py + sy) - __ldg(py);
+            }
+            const R *src = (const R *)(STAGE == 1 ? U.w0 : U.pbuf);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                s0[v] = __ldg(src + v * U.np + lin);
+                s1[v] = std::is_same<R, double>::value ? R(0) : __ldg(src + (4 + v) * U.np + lin);
+            }
+        }
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            cp_async_wait_all();
+            if (tid == 0) {
+                atomicOr(&A.scal->flags, FLAG_TIMEOUT);
+                if (nxt.it < nitems) mbar_wait(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        tile_t1_pass(sqb + buf * SQ_N, st, tid);
+        __syncthreads();
+
+        R F0[4], F1[4];
+        if (in) {
+            const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
+            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, F0, F1);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                F0[v] *= R(0.25);
+                F1[v] *= R(0.25);
+            }
+        }
+        if (upd) {
+            cp_async_wait_all();
+            __syncthreads();   // the x-face slab of every thread is in place
+            if (in) {
+                const int z = f - 1;
+                R dx[8], dz[8];
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    dx[C0 + c] = sx[(c * SX_H + tx + 1) * SX_W + ty] - sx[(c * SX_H + tx) * SX_W + ty];
+                // local frame of a z-face: (rho, m_z, m_x, m_y); global (rho, m_x, m_y, m_z)
+                constexpr int loc[4] = {0, 2, 3, 1};
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (NEED_F0) dz[v] = F0[loc[v]] - P0[loc[v]];
+                    dz[4 + v] = F1[loc[v]] - P1[loc[v]];
+                }
+                const R ihx = __ldg(A.ih1 + a + G), ihy = __ldg(A.ih2 + b + G), ihz = __ldg(U.ihz + z + G);
+                bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ihx, ihy, ihz, s0, s1);
+            }
+        }
+        if (in) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                P0[v] = F0[v];
+                P1[v] = F1[v];
+            }
+        }
+        cur = nxt;
+        __syncthreads();   // st, the face buffer and the x slab are free again
+    }
     if (STAGE == 2 && bad) atomicOr(&A.scal->flags, FLAG_NONFINITE);
 }
 
-template <typename R>
-int flux_grid(int stage)
+// Resident blocks per SM x SMs for a persistent kernel with `smem` bytes of
+// dynamic shared memory (raises its dynamic shared-memory limit first).
+template <typename K>
+int persistent_grid(K kernel, size_t smem)
 {
-    // persistent grid: resident blocks per SM x SMs (computed once per type)
-    static int blocks[2] = {0, 0};
-    const int s = stage == 1 ? 0 : 1;
-    if (!blocks[s]) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = flux_smem_bytes<R>();
-        if (stage == 1) {
-            cudaFuncSetAttribute(face_flux_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, face_flux_kernel<R, true>, TX * TY, smem);
-        } else {
-            cudaFuncSetAttribute(face_flux_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, face_flux_kernel<R, false>, TX * TY, smem);
-        }
-        blocks[s] = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
-    }
-    return blocks[s];
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, TX * TY, smem);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
-template <typename R>
-void stage_impl(const Ctx &c, int stage)
+template <typename R, int STAGE>
+struct FluxGrids {
+    int flux = 0, flux_update = 0;
+};
+
+template <typename R, int STAGE>
+const FluxGrids<R, STAGE> &flux_grids()
+{
+    static FluxGrids<R, STAGE> g;
+    if (!g.flux) {
+        g.flux = persistent_grid(face_flux_kernel<R, STAGE == 1>, flux_smem_bytes<R>());
+        g.flux_update = persistent_grid(flux_update_kernel<R, STAGE>, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4));
+    }
+    return g;
+}
+
+// z-faces per segment of the fused z kernel: the length L that minimises the
+// steps of the busiest block, ceil(items / G) x (L + 1 priming face), with
+// items = columns x ceil(nf / L), over 1 to 64 segments.
+int z_segment(int ncol, int nf, int G)
+{
+    long best = -1;
+    int bestL = nf;
+    for (int S = 1; S <= 64 && S <= nf; ++S) {
+        const int L = (nf + S - 1) / S, Sa = (nf + L - 1) / L;
+        const long items = (long)ncol * Sa;
+        const long cost = (items + G - 1) / G * (L + (Sa > 1 ? 1 : 0));
+        if (best < 0 || cost < best) {
+            best = cost;
+            bestL = L;
+        }
+    }
+    return bestL;
+}
+
+template <typename R, int STAGE>
+void stage_impl(const Ctx &c)
 {
     const Phys<R> ph = make_phys<R>(c);
-    const R *w = (const R *)(stage == 1 ? c.wk0 : c.wk1);
+    const R *w = (const R *)(STAGE == 1 ? c.wk0 : c.wk1);
     const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
-    const size_t smem = flux_smem_bytes<R>();
-    const int gmax = flux_grid<R>(stage);
+    const FluxGrids<R, STAGE> &grids = flux_grids<R, STAGE>();
+    const dim3 blk(TX, TY);
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
         FaceEqArgs<R> E;
@@ -601,7 +778,6 @@ void stage_impl(const Ctx &c, int stage)
         E.c1 = 1 + t1;
         E.c2 = 1 + t2;
         E.ph = ph;
-        dim3 blk(32, 8);
         E.nf = c.n[d] + 1;
         E.K = kMarch;
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
@@ -624,37 +800,39 @@ void stage_impl(const Ctx &c, int stage)
         F.ph = ph;
         F.scal = c.scal;
         const long ntiles = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY) * F.nf;
-        const int grid = (int)(ntiles < gmax ? ntiles : gmax);
         mark(c, K_FACE_FLUX, 1);
-        if (stage == 1)
-            face_flux_kernel<R, true><<<grid, blk, smem, c.stream>>>(c.tmap[d], F);
-        else
-            face_flux_kernel<R, false><<<grid, blk, smem, c.stream>>>(c.tmap[d], F);
+        if (d < 2) {
+            const int grid = (int)(ntiles < grids.flux ? ntiles : grids.flux);
+            face_flux_kernel<R, STAGE == 1><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(c.tmap[d], F);
+        } else {
+            // z faces: flux and the stage update of every cell
+            UpdArgs<R> U;
+            U.ffx = (const R *)c.ff[0];
+            U.ffy = (const R *)c.ff[1];
+            U.nffx = c.nff[0];
+            U.nffy = c.nff[1];
+            U.ihz = (const R *)c.ih[2];
+            U.nx = c.n[0];
+            U.ny = c.n[1];
+            U.nz = c.n[2];
+            U.P0 = c.P[0];
+            U.P1 = c.P[1];
+            U.np = c.np;
+            U.w0 = c.state;
+            U.wk1 = c.wk1;
+            U.pbuf = c.pbuf;
+            U.state = c.state;
+            U.off = (R)c.off;
+            for (int a = 0; a < 3; ++a) U.fb[a] = (R)c.fbody[a];
+            const int ncol = ((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY);
+            U.seg = z_segment(ncol, F.nf, grids.flux_update);
+            const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
+            const int grid = (int)(nitems < grids.flux_update ? nitems : grids.flux_update);
+            flux_update_kernel<R, STAGE><<<grid, blk, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4), c.stream>>>(
+                c.tmap[d], F, U);
+        }
         mark(c, K_FACE_FLUX, 0);
     }
-    UpdArgs<R> U;
-    for (int d = 0; d < 3; ++d) {
-        U.ff[d] = (const R *)c.ff[d];
-        U.nff[d] = c.nff[d];
-        U.ih[d] = (const R *)c.ih[d];
-        U.n[d] = c.n[d];
-        U.P[d] = c.P[d];
-        U.fb[d] = (R)c.fbody[d];
-    }
-    U.np = c.np;
-    U.w0 = c.state;
-    U.wk1 = c.wk1;
-    U.pbuf = c.pbuf;
-    U.state = c.state;
-    U.off = (R)c.off;
-    U.scal = c.scal;
-    dim3 blk(32, 8), gu((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
-    mark(c, K_UPDATE, 1);
-    if (stage == 1)
-        update_kernel<R, 1><<<gu, blk, 0, c.stream>>>(U);
-    else
-        update_kernel<R, 2><<<gu, blk, 0, c.stream>>>(U);
-    mark(c, K_UPDATE, 0);
 }
 
 // ----------------------------------------------------- prep, CFL, misc --
@@ -926,9 +1104,9 @@ void launch_ghost(const Ctx &c, void *w)
 void launch_stage(const Ctx &c, int stage)
 {
     if (c.prec == GKS_FP64)
-        stage_impl<double>(c, stage);
+        stage == 1 ? stage_impl<double, 1>(c) : stage_impl<double, 2>(c);
     else
-        stage_impl<float>(c, stage);
+        stage == 1 ? stage_impl<float, 1>(c) : stage_impl<float, 2>(c);
 }
 
 void launch_cfl(const Ctx &c)

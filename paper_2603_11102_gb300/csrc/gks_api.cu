@@ -454,7 +454,11 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
         cell_range(c, 1, d->hub[1] - rmax - cut, d->hub[1] + rmax + cut, r.box[1]) ||
         cell_range(c, 2, d->hub[2] - rmax - cut, d->hub[2] + rmax + cut, r.box[2]))
         return fail(g, GKS_ERR_RANGE, "rotor outside the grid");
-    const size_t nd = 4 * (size_t)np + (size_t)npts + 3 * (size_t)npts + 4 * (size_t)npts + 2 * nb + 2 * nb + 3;
+    r.norm = 1.0 / (d->eps * d->eps * d->eps * pow(3.14159265358979323846, 1.5));
+    r.ie2 = 1.0 / (d->eps * d->eps);
+    // per point: scale, X (3), F (4), Xr (3 floats in 2 doubles)
+    const size_t nd = 4 * (size_t)np + (size_t)npts + 3 * (size_t)npts + 4 * (size_t)npts + 2 * (size_t)npts +
+                      2 * nb + 2 * nb + 3;
     double *buf = nullptr;
     int rc = device_alloc(g, (void **)&buf, nd * sizeof(double));
     if (rc) return rc;
@@ -467,6 +471,7 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
     r.scale = buf + o; for (int q = 0; q < npts; ++q) host[o + q] = 1.0; o += npts;
     r.X = buf + o; o += 3 * (size_t)npts;
     r.F = buf + o; o += 4 * (size_t)npts;
+    r.Xr = reinterpret_cast<float *>(buf + o); o += 2 * (size_t)npts;
     r.et = buf + o; o += 2 * nb;
     r.out = buf + o;
     rc = cuda_check(g, cudaMemcpyAsync(buf, host.data(), nd * sizeof(double), cudaMemcpyHostToDevice, c.stream),
@@ -545,11 +550,14 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
     b.nnz = off[n];
     b.csr_off = d_cnt;
     char *cbuf = nullptr;
-    rc = device_alloc(g, (void **)&cbuf, (size_t)b.nnz * (sizeof(double) + sizeof(int)) + 3 * sizeof(double) * b.nbox + 64);
+    rc = device_alloc(g, (void **)&cbuf, (size_t)b.nnz * (sizeof(double) + sizeof(int) + sizeof(float)) +
+                                             3 * (sizeof(double) + sizeof(float)) * b.nbox + 64);
     if (rc) return rc;
     b.csr_w = (double *)cbuf;
     b.Ubox = b.csr_w + b.nnz;
     b.csr_cell = (int *)(b.Ubox + 3 * b.nbox);
+    b.csr_wf = (float *)(b.csr_cell + b.nnz);
+    b.Uboxf = b.csr_wf + b.nnz;
     rc = cuda_check(g, cudaMemcpyAsync(d_cnt, off.data(), sizeof(long) * (n + 1), cudaMemcpyHostToDevice, c.stream),
                     "copy offsets");
     if (rc) return rc;

@@ -20,6 +20,7 @@
 // evaluation of sqrt(dx*dx + dy*dy + dz*dz).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -138,6 +139,8 @@ __global__ void __launch_bounds__(256) alm_loads_kernel(Lattice L, const void *S
         r.X[3 * q] = X[0];
         r.X[3 * q + 1] = X[1];
         r.X[3 * q + 2] = X[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r.Xr[3 * q + d] = (float)(X[d] - r.hub[d]);
         if (p == 0) {
             r.et[2 * b] = -sth;
             r.et[2 * b + 1] = cth;
@@ -215,6 +218,12 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
     hi = h2;
 }
 
+// Projection of the point forces onto the cells of the rotor box (truncated
+// Gaussian, Eq. (Gaussian)), blade-then-point order per cell. FP64 grids:
+// distances and weights in FP64. FP32C grids: the blade screen, the
+// distances and the weights in FP32 on hub-relative coordinates (error below
+// 2e-6 relative in r^2); only a point whose r^2 lies within 1e-5 of the cut
+// takes the FP64 distance, so that the support is decided exactly as in FP64.
 template <typename R>
 __global__ void __launch_bounds__(256) alm_spread_kernel(Lattice L, void *S, RotorDev r, Scalars *scal)
 {
@@ -228,46 +237,70 @@ __global__ void __launch_bounds__(256) alm_spread_kernel(Lattice L, void *S, Rot
     const double xc[3] = {centre(L, 0, i), centre(L, 1, j), centre(L, 2, k)};
     const double cut = 3.0 * r.eps;
     const int npts = r.nb * r.np;
-    const R ie2 = (R)(1.0 / (r.eps * r.eps));
-    const R norm = (R)(1.0 / (r.eps * r.eps * r.eps * pow(kPi, 1.5)));
     R f[3] = {R(0), R(0), R(0)};
     bool any = false;
-    const float cut2f = (float)(cut * cut) * 1.0001f;
-    for (int b = 0; b < r.nb; ++b) {
-        const R e1 = (R)r.et[2 * b], e2 = (R)r.et[2 * b + 1];
-        // every point of blade b lies on the segment hub + s e_r, s in
-        // [rmin, rmax]; a cell farther than 3 eps from it gets nothing
-        {
-            const double ery = r.et[2 * b + 1], erz = -r.et[2 * b];
-            const double px = xc[0] - r.hub[0], py = xc[1] - r.hub[1], pz = xc[2] - r.hub[2];
-            double sp = py * ery + pz * erz;
-            sp = sp < r.rmin ? r.rmin : (sp > r.rmax ? r.rmax : sp);
-            const double qy = py - sp * ery, qz = pz - sp * erz;
-            if (px * px + qy * qy + qz * qz > cut * cut * (1.0 + 1e-6) + 1e-300) continue;
+    if constexpr (std::is_same<R, double>::value) {
+        for (int b = 0; b < r.nb; ++b) {
+            const double e1 = r.et[2 * b], e2 = r.et[2 * b + 1];
+            // every point of blade b lies on the segment hub + s e_r, s in
+            // [rmin, rmax]; a cell farther than 3 eps from it gets nothing
+            {
+                const double ery = e2, erz = -e1;
+                const double px = xc[0] - r.hub[0], py = xc[1] - r.hub[1], pz = xc[2] - r.hub[2];
+                double sp = py * ery + pz * erz;
+                sp = sp < r.rmin ? r.rmin : (sp > r.rmax ? r.rmax : sp);
+                const double qy = py - sp * ery, qz = pz - sp * erz;
+                if (px * px + qy * qy + qz * qz > cut * cut * (1.0 + 1e-6) + 1e-300) continue;
+            }
+            double fb[3] = {0.0, 0.0, 0.0};
+            for (int p = 0; p < r.np; ++p) {
+                const int q = b * r.np + p;
+                const double rr = dist(xc[0] - r.X[3 * q], xc[1] - r.X[3 * q + 1], xc[2] - r.X[3 * q + 2]);
+                if (rr > cut) continue;
+                any = true;
+                const double eta = exp(-(rr / r.eps) * (rr / r.eps)) * r.norm;
+                const double Fx = r.F[q], Ft = r.F[npts + q];
+                fb[0] += -Fx * eta;
+                fb[1] += -Ft * e1 * eta;
+                fb[2] += -Ft * e2 * eta;
+            }
+            f[0] += fb[0];
+            f[1] += fb[1];
+            f[2] += fb[2];
         }
-        R fb[3] = {R(0), R(0), R(0)};
-        for (int p = 0; p < r.np; ++p) {
-            const int q = b * r.np + p;
-            const double dx = xc[0] - r.X[3 * q], dy = xc[1] - r.X[3 * q + 1], dz = xc[2] - r.X[3 * q + 2];
-            // FP32 screen, then the exact FP64 test near the cut
-            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-            if (fx * fx + fy * fy + fz * fz > cut2f) continue;
-            const double rr = dist(dx, dy, dz);
-            if (rr > cut) continue;
-            any = true;
-            R eta;
-            if constexpr (std::is_same<R, double>::value)
-                eta = exp(-(rr / r.eps) * (rr / r.eps)) * norm;
-            else
-                eta = expf(-(float)(rr * rr) * ie2) * norm;
-            const R Fx = (R)r.F[q], Ft = (R)r.F[npts + q];
-            fb[0] += -Fx * eta;
-            fb[1] += -Ft * e1 * eta;
-            fb[2] += -Ft * e2 * eta;
+    } else {
+        const float pc[3] = {(float)(xc[0] - r.hub[0]), (float)(xc[1] - r.hub[1]), (float)(xc[2] - r.hub[2])};
+        const float c2 = (float)(cut * cut), c2lo = c2 * (1.0f - 1e-5f), c2hi = c2 * (1.0f + 1e-5f);
+        const float ie2 = (float)r.ie2, norm = (float)r.norm;
+        const float rmin = (float)r.rmin, rmax = (float)r.rmax;
+        for (int b = 0; b < r.nb; ++b) {
+            const float e1 = (float)r.et[2 * b], e2 = (float)r.et[2 * b + 1];
+            {
+                float sp = pc[1] * e2 - pc[2] * e1;
+                sp = fminf(fmaxf(sp, rmin), rmax);
+                const float qy = pc[1] - sp * e2, qz = pc[2] + sp * e1;
+                if (pc[0] * pc[0] + qy * qy + qz * qz > c2 * 1.0001f) continue;
+            }
+            float fb[3] = {0.0f, 0.0f, 0.0f};
+            for (int p = 0; p < r.np; ++p) {
+                const int q = b * r.np + p;
+                const float dx = pc[0] - r.Xr[3 * q], dy = pc[1] - r.Xr[3 * q + 1], dz = pc[2] - r.Xr[3 * q + 2];
+                const float s2 = dx * dx + dy * dy + dz * dz;
+                if (s2 > c2hi) continue;
+                if (s2 >= c2lo &&
+                    dist(xc[0] - r.X[3 * q], xc[1] - r.X[3 * q + 1], xc[2] - r.X[3 * q + 2]) > cut)
+                    continue;
+                any = true;
+                const float eta = expf(-s2 * ie2) * norm;
+                const float Fx = (float)r.F[q], Ft = (float)r.F[npts + q];
+                fb[0] += -Fx * eta;
+                fb[1] += -Ft * e1 * eta;
+                fb[2] += -Ft * e2 * eta;
+            }
+            f[0] += fb[0];
+            f[1] += fb[1];
+            f[2] += fb[2];
         }
-        f[0] += fb[0];
-        f[1] += fb[1];
-        f[2] += fb[2];
     }
     if (!any) return;
     const long lin = lin_index(L, i, j, k);
@@ -411,6 +444,7 @@ __global__ void __launch_bounds__(256) body_csr_kernel(Lattice L, BodyDev b, lon
                 if (fill) {
                     b.csr_cell[o] = (i - b.box[0][0]) + bx * ((j - b.box[1][0]) + by * (k - b.box[2][0]));
                     b.csr_w[o] = exp(-(rr / b.eps) * (rr / b.eps)) * norm * vol;
+                    b.csr_wf[o] = (float)b.csr_w[o];
                     ++o;
                 }
                 ++cnt;
@@ -418,7 +452,9 @@ __global__ void __launch_bounds__(256) body_csr_kernel(Lattice L, BodyDev b, lon
     if (!fill) counts[p] = cnt;
 }
 
-// Cell velocity m/rho over the body box (FP64), input of the residual.
+// Cell velocity m/rho over the body box, input of the residual (FP64 from
+// the cell state; stored as FP32 on FP32C grids).
+template <typename R>
 __global__ void __launch_bounds__(256) ibm_velocity_kernel(Lattice L, const void *S, BodyDev b)
 {
     if (b.out[5] != 0.0) return;
@@ -430,27 +466,31 @@ __global__ void __launch_bounds__(256) ibm_velocity_kernel(Lattice L, const void
     const int k = b.box[2][0] + (int)(c / ((long)bx * by));
     double q[4];
     cell_state(L, S, lin_index(L, i, j, k), q);
-    b.Ubox[3 * c] = q[1] / q[0];
-    b.Ubox[3 * c + 1] = q[2] / q[0];
-    b.Ubox[3 * c + 2] = q[3] / q[0];
+    R *U = std::is_same<R, double>::value ? (R *)b.Ubox : (R *)b.Uboxf;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) U[3 * c + d] = (R)(q[1 + d] / q[0]);
 }
 
 // Residual max_p |v_p - sum_ijk W_{ijk->p} U_ijk|: one warp per point,
 // lanes stride the point's weights, fixed shuffle tree, atomic max of the
-// (non-negative) result.
+// (non-negative) result. FP32C grids sum in FP32 (terms are ~1/nnz of |U|:
+// the error stays near 1e-7 of |U|).
+template <typename R>
 __global__ void __launch_bounds__(256) ibm_residual_kernel(BodyDev b)
 {
     if (b.out[5] != 0.0) return;
     const int warp = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (warp >= b.n) return;
+    const R *Wt = std::is_same<R, double>::value ? (const R *)b.csr_w : (const R *)b.csr_wf;
+    const R *U = std::is_same<R, double>::value ? (const R *)b.Ubox : (const R *)b.Uboxf;
     const long o0 = b.csr_off[warp], o1 = b.csr_off[warp + 1];
-    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    R u0 = R(0), u1 = R(0), u2 = R(0);
     for (long o = o0 + lane; o < o1; o += 32) {
-        const double W = b.csr_w[o];
+        const R W = Wt[o];
         const long c = b.csr_cell[o];
-        u0 += W * b.Ubox[3 * c];
-        u1 += W * b.Ubox[3 * c + 1];
-        u2 += W * b.Ubox[3 * c + 2];
+        u0 += W * U[3 * c];
+        u1 += W * U[3 * c + 1];
+        u2 += W * U[3 * c + 2];
     }
     for (int s = 16; s > 0; s >>= 1) {
         u0 += __shfl_xor_sync(0xffffffffu, u0, s);
@@ -458,7 +498,8 @@ __global__ void __launch_bounds__(256) ibm_residual_kernel(BodyDev b)
         u2 += __shfl_xor_sync(0xffffffffu, u2, s);
     }
     if (lane == 0) {
-        const double e0 = b.vel[3 * warp] - u0, e1 = b.vel[3 * warp + 1] - u1, e2 = b.vel[3 * warp + 2] - u2;
+        const double e0 = b.vel[3 * warp] - (double)u0, e1 = b.vel[3 * warp + 1] - (double)u1,
+                     e2 = b.vel[3 * warp + 2] - (double)u2;
         const double e = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
         atomicMax((unsigned long long *)&b.out[6], (unsigned long long)__double_as_longlong(e));
     }
@@ -475,16 +516,35 @@ __global__ void ibm_check_kernel(BodyDev b, int s, double tol)
     if (tol > 0.0 && r < tol) b.out[5] = 1.0;
 }
 
-// force on the structure = - sum over box cells (fixed order), FP64
-__global__ void __launch_bounds__(1024) ibm_force_kernel(BodyDev b)
+// Force on the structure = - sum over box cells, FP64 in a fixed order:
+// block k sums its contiguous chunk of cells (thread stride, then a tree)
+// into part[3k..3k+2]; one block then sums the parts in order.
+__global__ void __launch_bounds__(256) ibm_force_part_kernel(BodyDev b, long chunk, double *part)
 {
-    __shared__ double sh[3][1024];
+    __shared__ double sh[3][256];
+    const long c0 = blockIdx.x * chunk, c1 = min(c0 + chunk, b.nbox);
     double s[3] = {0.0, 0.0, 0.0};
-    for (long c = threadIdx.x; c < b.nbox; c += blockDim.x)
+    for (long c = c0 + threadIdx.x; c < c1; c += blockDim.x)
         for (int d = 0; d < 3; ++d) s[d] += b.fsum[3 * c + d];
     for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = s[d];
     __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[3 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) ibm_force_final_kernel(BodyDev b, const double *part, int nparts)
+{
+    __shared__ double sh[3][256];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x)
+        for (int d = 0; d < 3; ++d) s[d] += part[3 * k + d];
+    for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = s[d];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
             for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
         __syncthreads();
@@ -574,17 +634,24 @@ void launch_ibm(const Ctx &c, const BodyDev &b)
             ibm_iter_kernel<float><<<cb, 256, 0, c.stream>>>(L, c.state, b, c.scal, per);
         mark(c, K_IBM, 0);
         mark(c, K_IBM, 1);
-        ibm_velocity_kernel<<<cb, 256, 0, c.stream>>>(L, c.state, b);
-        mark(c, K_IBM, 0);
-        mark(c, K_IBM, 1);
-        ibm_residual_kernel<<<pb, 256, 0, c.stream>>>(b);
+        if (c.prec == GKS_FP64) {
+            ibm_velocity_kernel<double><<<cb, 256, 0, c.stream>>>(L, c.state, b);
+            ibm_residual_kernel<double><<<pb, 256, 0, c.stream>>>(b);
+        } else {
+            ibm_velocity_kernel<float><<<cb, 256, 0, c.stream>>>(L, c.state, b);
+            ibm_residual_kernel<float><<<pb, 256, 0, c.stream>>>(b);
+        }
         mark(c, K_IBM, 0);
         mark(c, K_IBM, 1);
         ibm_check_kernel<<<1, 1, 0, c.stream>>>(b, b.tol > 0.0 ? s : b.niter - 1, b.tol);
         mark(c, K_IBM, 0);
     }
+    // the grid's reduction scratch holds kMaxPartials x 8 doubles
+    const long chunk = std::max(2048L, (b.nbox + kMaxPartials - 1) / kMaxPartials);
+    const int nparts = (int)((b.nbox + chunk - 1) / chunk);
     mark(c, K_IBM, 1);
-    ibm_force_kernel<<<1, 1024, 0, c.stream>>>(b);
+    ibm_force_part_kernel<<<nparts, 256, 0, c.stream>>>(b, chunk, c.partials);
+    ibm_force_final_kernel<<<1, 256, 0, c.stream>>>(b, c.partials, nparts);
     mark(c, K_IBM, 0);
 }
 

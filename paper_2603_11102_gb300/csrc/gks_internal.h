@@ -101,6 +101,8 @@ struct RotorDev {
     double rmin, rmax;  // smallest and largest point radius
     double *r, *chord, *twist, *width, *scale;  // device arrays
     double *X;          // 3 nb np positions of the last step
+    float *Xr;          // the same relative to the hub, FP32 (projection screen)
+    double norm, ie2;   // 1 / (eps^3 pi^1.5) and 1 / eps^2 of the Gaussian kernel
     double *F;          // 4 nb np: F_x, F_th, alpha, phi
     double *et;         // 2 nb: -sin th_b, cos th_b
     double *out;        // thrust[nb], torque[nb], power, cp, ct
@@ -146,6 +148,7 @@ struct BodyDev {
     double *csr_w;              // nnz
     long nnz;
     double *Ubox;               // 3 per box cell: cell velocity of the residual
+    float *csr_wf, *Uboxf;      // FP32 copies of csr_w and Ubox (FP32C grids)
 };
 void launch_body_csr_count(const Ctx &c, const BodyDev &b, long *d_counts);
 void launch_body_csr_fill(const Ctx &c, const BodyDev &b);

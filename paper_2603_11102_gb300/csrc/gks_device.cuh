@@ -68,11 +68,13 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
 // of Jiang-Shu smoothness indicators: the value at the right face (+1/2) and,
 // with the stencils mirrored, at the left face (-1/2). The mirrored
 // indicators are the same numbers in reverse order, so they are computed
-// once. Weights scaled by (eps+b0)^2 (eps+b1)^2 (eps+b2)^2, one division each.
+// once. With s_k = (eps + beta_k)^2 the weights d_k / s_k are scaled by
+// 10 s0 s1 s2 (linear weights 1/10, 6/10, 3/10 -> 1, 6, 3) and the 1/6 of the
+// candidate polynomials moves into the one division per face value.
 template <typename R>
 __device__ __forceinline__ void weno5_pair(const R q[5], R &right, R &left)
 {
-    const R r6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0), qq = R(0.25);
+    const R c13 = R(13.0 / 12.0), qq = R(0.25);
     const R a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
     R t = a - R(2) * b + c, u = a - R(4) * b + R(3) * c;
     R s0 = R(1e-6) + (c13 * t * t + qq * u * u);
@@ -81,22 +83,22 @@ __device__ __forceinline__ void weno5_pair(const R q[5], R &right, R &left)
     t = c - R(2) * d + e; u = R(3) * c - R(4) * d + e;
     R s2 = R(1e-6) + (c13 * t * t + qq * u * u);
     s0 *= s0; s1 *= s1; s2 *= s2;
-    const R s01 = s0 * s1, s02 = s0 * s2, s12 = s1 * s2;
-    // right face
+    const R w02 = R(6) * (s0 * s2), s01 = s0 * s1, s12 = s1 * s2;
+    // right face: candidates 6 p_k on (a,b,c), (b,c,d), (c,d,e)
     {
-        const R p0 = (R(2) * a - R(7) * b + R(11) * c) * r6;
-        const R p1 = (-b + R(5) * c + R(2) * d) * r6;
-        const R p2 = (R(2) * c + R(5) * d - e) * r6;
-        const R w0 = R(0.1) * s12, w1 = R(0.6) * s02, w2 = R(0.3) * s01;
-        right = wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
+        const R p0 = R(2) * a - R(7) * b + R(11) * c;
+        const R p1 = -b + R(5) * c + R(2) * d;
+        const R p2 = R(2) * c + R(5) * d - e;
+        const R w2 = R(3) * s01;
+        right = wdiv(s12 * p0 + w02 * p1 + w2 * p2, R(6) * (s12 + w02 + w2));
     }
     // left face: candidates on (e,d,c), (d,c,b), (c,b,a) with indicators s2, s1, s0
     {
-        const R p0 = (R(2) * e - R(7) * d + R(11) * c) * r6;
-        const R p1 = (-d + R(5) * c + R(2) * b) * r6;
-        const R p2 = (R(2) * c + R(5) * b - a) * r6;
-        const R w0 = R(0.1) * s01, w1 = R(0.6) * s02, w2 = R(0.3) * s12;
-        left = wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
+        const R p0 = R(2) * e - R(7) * d + R(11) * c;
+        const R p1 = -d + R(5) * c + R(2) * b;
+        const R p2 = R(2) * c + R(5) * b - a;
+        const R w2 = R(3) * s12;
+        left = wdiv(s01 * p0 + w02 * p1 + w2 * p2, R(6) * (s01 + w02 + w2));
     }
 }
 

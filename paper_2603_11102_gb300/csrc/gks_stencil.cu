@@ -134,56 +134,6 @@ struct FaceEqArgs {
     Phys<R> ph;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(256) face_eq_kernel(FaceEqArgs<R> A)
-{
-    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
-    const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
-    const int f = blockIdx.z;
-    if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
-    // cell f-1 (left neighbour of face f)
-    const long base = (long)(f - 1 + G) * A.sd + (long)(a + G) * A.s1 + (long)(b + G) * A.s2;
-    const int comp[4] = {0, A.cn, A.c1, A.c2};
-    R c[4][6];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const R *p = A.w + comp[v] * A.np + base;
-#pragma unroll
-        for (int m = 0; m < 6; ++m) c[v][m] = __ldg(p + (long)(m - 2) * A.sd);
-    }
-    R Ql[4], Qr[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        Ql[v] = weno5(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4]);
-        Qr[v] = weno5(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1]);
-    }
-    // equilibrium state: u>0 half of the left Maxwellian, u<0 half of the
-    // right one; written on rho - off
-    const Phys<R> &ph = A.ph;
-    const R rl = ph.off + Ql[0], rr = ph.off + Qr[0];
-    const R Ul = wdiv(Ql[1], rl), Ur = wdiv(Qr[1], rr);
-    const R el = erf(ph.sqlam * Ul), er = erf(ph.sqlam * Ur);
-    const R Pl = R(0.5) + R(0.5) * el;   // <u^0>_{u>0} of the left state
-    const R Pr = R(0.5) - R(0.5) * er;   // <u^0>_{u<0} of the right state
-    const R xl = -ph.lambda * Ul * Ul, xr = -ph.lambda * Ur * Ur;
-    const R El = ph.kE * exp(xl), Er = ph.kE * exp(xr);
-    R Q0[4];
-    Q0[0] = Ql[0] * Pl + Qr[0] * Pr + ph.off * (R(0.5) * (el - er));
-    Q0[1] = Ql[1] * Pl + Qr[1] * Pr + (Ql[0] * El - Qr[0] * Er) +
-            ph.off * (ph.kE * (expm1(xl) - expm1(xr)));
-    Q0[2] = Ql[2] * Pl + Qr[2] * Pr;
-    Q0[3] = Ql[3] * Pl + Qr[3] * Pr;
-    // normal slope at the face: derivative of the quartic through Q0 and the
-    // cell averages f-2..f+1 (the face value drops out)
-    const R s = A.ihf[f] * R(1.0 / 12.0);
-    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        A.fq[v * A.nfq + o] = Q0[v];
-        A.fq[(4 + v) * A.nfq + o] = (R(15) * (c[v][3] - c[v][2]) - (c[v][4] - c[v][1])) * s;
-    }
-}
-
 constexpr int kMarch = 16;   // faces per thread of the marching face-state kernel
 
 // Marching variant: each thread walks K consecutive faces along d at one

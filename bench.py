@@ -303,19 +303,27 @@ def run_ours(args, world, rank, local):
     value = world * cells * args.steps / (ms / 1e3) / 1e6
     ms_step = ms / args.steps
 
-    # roofline of the dominant kernel group
+    # roofline of the dominant kernel group (FP32 or FP64 ALU bound); the
+    # x/y face-flux kernel, the z-face kernel fused with the stage update and
+    # the face-state kernel are each reported against the same ALU peak
     kms = prof["ms"]
-    top = max(kms, key=kms.get)
     fc = face_counts(w.n)
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12 if args.precision == "fp32c" else 1.25
-    if top == "face_flux":
-        flops = args.steps * sum(fc[d]["flux"] * (FLOPS["face_flux_stage1"] + FLOPS["face_flux_stage2"])
-                                 for d in range(3))
-    elif top == "face_eq":
-        flops = args.steps * 2 * sum(fc[d]["eq"] * FLOPS["face_eq"] for d in range(3))
-    else:
-        flops = None
+    flux_pair = FLOPS["face_flux_stage1"] + FLOPS["face_flux_stage2"]
+    group_flops = {
+        "face_flux": args.steps * sum(fc[d]["flux"] * flux_pair for d in (0, 1)),
+        "flux_update": args.steps * fc[2]["flux"] * flux_pair,
+        "face_eq": args.steps * 2 * sum(fc[d]["eq"] * FLOPS["face_eq"] for d in range(3)),
+    }
+    alu = {}
+    for k, fl in group_flops.items():
+        if kms.get(k, 0.0) > 0:
+            a = fl / (kms[k] / 1e3) / 1e12
+            alu[k] = {"achieved": round(a, 3), "frac": round(a / alu_peak, 4),
+                      "avg_launch_ms": round(kms[k] / max(1, prof["launches"][k]), 4)}
+    top = max(kms, key=kms.get)
+    flops = group_flops.get(top)
     achieved = flops / (kms[top] / 1e3) / 1e12 if flops else None
     traffic = read_traffic(top, args.precision)
     roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
@@ -323,7 +331,8 @@ def run_ours(args, world, rank, local):
                 "peak_source": ("FP32 lanes 152 x 128 x 2 x %.0f MHz (max SM clock of %s peaks)"
                                 % (clock_mhz, peak_kind)) if args.precision == "fp32c"
                 else "nominal GB300 FP64 1.25 TFLOP/s",
-                "launches": prof["launches"][top], "avg_launch_ms": kms[top] / max(1, prof["launches"][top])}
+                "launches": prof["launches"][top], "avg_launch_ms": kms[top] / max(1, prof["launches"][top]),
+                "groups": alu}
     hbm_ach = cells * BYTES_PER_CELL_STEP[args.precision] * args.steps / (ms / 1e3) / 1e9
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_ach / peaks["hbm_gbs"], "bytes_per_cell_step": BYTES_PER_CELL_STEP[args.precision],

@@ -252,8 +252,9 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
                      double *h_grad_scales, double *h_grad_uinf);
 
 /* Kernel accounting of the library's own kernels. Every kernel launch is
- * counted per group (0 prep, 1 ghost, 2 cfl, 3 face_eq, 4 face_flux,
- * 5 update, 6 alm, 7 ibm, 8 misc); with timing enabled each launch is also
+ * counted per group (0 prep, 1 ghost, 2 cfl, 3 face_eq, 4 face_flux: x and
+ * y faces, 5 flux_update: z faces fused with the stage update, 6 alm, 7 ibm,
+ * 8 misc); with timing enabled each launch is also
  * bracketed by CUDA events on the grid's stream and its duration summed.
  * gks_profile_enable sets timing on or off and clears the counters;
  * gks_profile_read synchronises, fills out and clears the counters. */

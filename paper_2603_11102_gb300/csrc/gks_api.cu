@@ -888,7 +888,7 @@ int gks_profile_read(gks_grid *g, gks_profile_out *out)
 const char *gks_kernel_group_name(int group)
 {
     static const char *names[K_NGROUPS] = {"prep", "ghost", "cfl", "face_eq", "face_flux",
-                                           "update", "alm", "ibm", "misc"};
+                                           "flux_update", "alm", "ibm", "misc"};
     return (group >= 0 && group < K_NGROUPS) ? names[group] : "";
 }
 

@@ -19,7 +19,7 @@ enum : int { FLAG_NONFINITE = 1, FLAG_CFL = 2, FLAG_RANGE = 4, FLAG_TIMEOUT = 8 
 
 // Kernel groups for the optional per-launch event timing (gks_profile_*).
 enum : int {
-    K_PREP = 0, K_GHOST, K_CFL, K_FACE_EQ, K_FACE_FLUX, K_UPDATE, K_ALM, K_IBM, K_MISC, K_NGROUPS
+    K_PREP = 0, K_GHOST, K_CFL, K_FACE_EQ, K_FACE_FLUX, K_FLUX_UPDATE, K_ALM, K_IBM, K_MISC, K_NGROUPS
 };
 
 // Scalars that live in device memory so that a step needs no host round trip.

@@ -750,7 +750,8 @@ void stage_impl(const Ctx &c)
         F.ph = ph;
         F.scal = c.scal;
         const long ntiles = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY) * F.nf;
-        mark(c, K_FACE_FLUX, 1);
+        const int grp = d < 2 ? K_FACE_FLUX : K_FLUX_UPDATE;
+        mark(c, grp, 1);
         if (d < 2) {
             const int grid = (int)(ntiles < grids.flux ? ntiles : grids.flux);
             face_flux_kernel<R, STAGE == 1><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(c.tmap[d], F);
@@ -781,7 +782,7 @@ void stage_impl(const Ctx &c)
             flux_update_kernel<R, STAGE><<<grid, blk, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4), c.stream>>>(
                 c.tmap[d], F, U);
         }
-        mark(c, K_FACE_FLUX, 0);
+        mark(c, grp, 0);
     }
 }
 

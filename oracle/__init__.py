@@ -72,7 +72,7 @@ def _load():
             "og_diagnostics": (None, [C.c_void_p, _dp]),
             "og_add_rotor": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp,
-                                       _dp, _dp, C.c_int]),
+                                       _dp, _dp, C.c_int, C.c_int]),
             "og_set_force_scales": (C.c_int, [C.c_void_p, C.c_int, _dp]),
             "og_add_body": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int,
                                       C.c_double]),
@@ -294,13 +294,13 @@ class OracleGrid:
         return out
 
     def add_rotor(self, nb, r, chord, twist, width, hub, omega, azimuth0, radius, eps,
-                  rho_inf=1.0, u_inf_ref=1.0, correction=False):
+                  rho_inf=1.0, u_inf_ref=1.0, correction=False, tip_correction=False):
         arrs = [_d(x) for x in (r, chord, twist, width)]
         npt = arrs[0][0].size
         hub_a, hp = _d(hub)
         rid = self.lib.og_add_rotor(self.h, int(nb), int(npt), hp, float(omega), float(azimuth0),
                                     float(radius), float(eps), float(rho_inf), float(u_inf_ref),
-                                    *(p for _, p in arrs), int(bool(correction)))
+                                    *(p for _, p in arrs), int(bool(correction)), int(bool(tip_correction)))
         if rid < 0:
             raise ValueError(self.lib.og_last_error(self.h).decode())
         self.nobj_kind.append(("rotor", int(nb), int(npt)))

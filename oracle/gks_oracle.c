@@ -442,7 +442,7 @@ typedef struct {
     int nb, np;
     double hub[3], omega, azimuth0, eps, rho_inf, radius, u_inf_ref;
     double *r, *chord, *twist, *width, *scale;
-    int correction;
+    int correction, tip_correction;
     double *Fx, *Ft, *alpha, *phi, *X; /* per point: loads, angles, positions */
     double thrust[OG_MAX_BLADES], torque[OG_MAX_BLADES], power, cp, ct;
     /* body */
@@ -971,7 +971,8 @@ static void support_box(const og_grid *g, const double *X, long npts, double rad
 
 int og_add_rotor(og_grid *g, int nb, int np, const double hub[3], double omega, double azimuth0,
                  double radius, double eps, double rho_inf, double u_inf_ref, const double *r,
-                 const double *chord, const double *twist, const double *width, int correction)
+                 const double *chord, const double *twist, const double *width, int correction,
+                 int tip_correction)
 {
     if (!axes_uniform(g)) { set_err(g, "ALM needs uniform axes"); return -1; }
     if (nb < 1 || nb > OG_MAX_BLADES || np < 1 || eps <= 0 || g->nobj >= OG_MAX_OBJECTS) {
@@ -984,6 +985,7 @@ int og_add_rotor(og_grid *g, int nb, int np, const double hub[3], double omega, 
     memcpy(o->hub, hub, sizeof(o->hub));
     o->omega = omega; o->azimuth0 = azimuth0; o->eps = eps; o->rho_inf = rho_inf;
     o->radius = radius; o->u_inf_ref = u_inf_ref; o->correction = correction;
+    o->tip_correction = tip_correction;
     o->r = (double *)malloc(sizeof(double) * np); memcpy(o->r, r, sizeof(double) * np);
     o->chord = (double *)malloc(sizeof(double) * np); memcpy(o->chord, chord, sizeof(double) * np);
     o->twist = (double *)malloc(sizeof(double) * np); memcpy(o->twist, twist, sizeof(double) * np);
@@ -1018,6 +1020,21 @@ static double polar_cl(double a)
 }
 static double polar_cd(double a) { return 0.01 + 0.02 * a * a; }
 
+/* Tip correction factor of Eq. (tip-correction) (Sec. 4.4.2, NTNU rotor):
+ *   f = (2/pi) arccos[exp(-g1 N (R - r) / (2 r sin(phi)))],
+ *   g1 = exp(-c1 (N lambda - c2)) + 0.1,
+ * N blades, rotor radius R, tip speed ratio lambda = omega R / U_inf and the
+ * empirical pair (c1, c2). Readings: sin(phi) is taken in absolute value
+ * (the factor is even in the flow angle's sign), and a point at or beyond
+ * the tip (r >= R) gets f = 0, the limit r -> R. */
+static double tip_factor_shen(int N, double R, double lambda, double r, double phi, double c1, double c2)
+{
+    if (r >= R) return 0.0;
+    double g1 = exp(-c1 * (N * lambda - c2)) + 0.1;
+    double e = exp(-g1 * N * (R - r) / (2.0 * r * fabs(sin(phi))));
+    return 2.0 / PI * acos(e);
+}
+
 static int alm_apply(og_grid *g, og_object *o, double t, double dt)
 {
     long np_ = g->np;
@@ -1048,8 +1065,15 @@ static int alm_apply(og_grid *g, og_object *o, double t, double dt)
             double urel2 = ux * ux + (wr - ut) * (wr - ut);
             double qd = 0.5 * o->rho_inf * o->chord[p] * o->width[p] * urel2;
             double Lf = qd * polar_cl(al), Df = qd * polar_cd(al);
-            o->Fx[q] = (Lf * cos(phi) + Df * sin(phi)) * o->scale[q];
-            o->Ft[q] = (Lf * sin(phi) - Df * cos(phi)) * o->scale[q];
+            double fax = 1.0, ftan = 1.0;
+            if (o->tip_correction) {
+                /* axial (c1, c2) = (0.1219, 21.52), tangential (0.0984, 13.026) */
+                double lambda = o->omega * o->radius / o->u_inf_ref;
+                fax = tip_factor_shen(nb, o->radius, lambda, rr, phi, 0.1219, 21.52);
+                ftan = tip_factor_shen(nb, o->radius, lambda, rr, phi, 0.0984, 13.026);
+            }
+            o->Fx[q] = fax * (Lf * cos(phi) + Df * sin(phi)) * o->scale[q];
+            o->Ft[q] = ftan * (Lf * sin(phi) - Df * cos(phi)) * o->scale[q];
             o->alpha[q] = al;
             o->phi[q] = phi;
         }

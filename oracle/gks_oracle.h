@@ -36,7 +36,8 @@ void og_ghost_filled(og_grid *g, const double *Q, double *out);
 void og_diagnostics(const og_grid *g, double out[5]);
 int og_add_rotor(og_grid *g, int nb, int np, const double hub[3], double omega, double azimuth0,
                  double radius, double eps, double rho_inf, double u_inf_ref, const double *r,
-                 const double *chord, const double *twist, const double *width, int correction);
+                 const double *chord, const double *twist, const double *width, int correction,
+                 int tip_correction);
 int og_set_force_scales(og_grid *g, int id, const double *s);
 int og_add_body(og_grid *g, int n, const double *xyz, const double *dS, const double *vel,
                 double eps, int niter, double tol);

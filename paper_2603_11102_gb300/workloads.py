@@ -45,6 +45,7 @@ class Rotor:
     rho_inf: float = 1.0
     u_inf_ref: float = 1.0
     correction: bool = False
+    tip_correction: bool = False
 
 
 @dataclass

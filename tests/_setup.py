@@ -11,7 +11,7 @@ def oracle_from_workload(w, state=None):
     o.set_body_force(*w.body_force)
     for r in w.rotors:
         o.add_rotor(r.n_blades, r.r, r.chord, r.twist, r.width, r.hub, r.omega, r.azimuth0, r.radius,
-                    r.eps, r.rho_inf, r.u_inf_ref, r.correction)
+                    r.eps, r.rho_inf, r.u_inf_ref, r.correction, r.tip_correction)
     for b in w.bodies:
         o.add_body(b.xyz, b.dS, b.eps, vel=b.vel, niter=b.niter, tol=b.tol)
     o.set_state(w.state0 if state is None else state)

@@ -316,3 +316,47 @@ def test_ibm_quiescent_zero_force_and_relaxation():
         Vp = dx * dS
         K = np.array([lattice_kernel_sum(g, xyz[p], 2 * dx)[0].sum() * vol for p in range(len(dS))])
         assert abs(Vb.sum() - np.dot(Vp, K)) <= 1e-12 * Vb.sum()
+
+
+def test_alm_tip_correction_special_values():
+    """Eq. (tip-correction), Sec. 4.4.2: f = (2/pi) arccos(exp(-x)) with
+    x = g1 N (R - r) / (2 r sin phi), g1 = exp(-c1 (N lambda - c2)) + 0.1,
+    (c1, c2) = (0.1219, 21.52) for F_x and (0.0984, 13.026) for F_theta. In a
+    uniform axial stream the sampled velocity at the first step is exactly
+    the free stream, so phi = atan2(U, omega r). Special values: a point at
+    the tip carries no load (arccos 1 = 0), and where x = ln 2 the factor is
+    (2/pi)(pi/3) = 2/3 of the uncorrected load."""
+    from scipy.optimize import brentq
+
+    n = (24, 32, 32)
+    dom = [(-0.5, 0.5), (-0.7, 0.7), (-0.7, 0.7)]
+    dx = 1.0 / n[0]
+    base = WL.rotor_3x50(D=1.0, hub=(0.0, 0.0, 0.0), dx=dx, n_pts=10)
+    R, N, om = base.radius, base.n_blades, base.omega
+    lam = om * R / 1.0
+
+    def x_of(r, c1, c2):
+        g1 = math.exp(-c1 * (N * lam - c2)) + 0.1
+        return g1 * N * (R - r) / (2 * r * abs(math.sin(math.atan2(1.0, om * r))))
+
+    ra = brentq(lambda r: x_of(r, 0.1219, 21.52) - math.log(2), 0.05 * R, R)
+    rt = brentq(lambda r: x_of(r, 0.0984, 13.026) - math.log(2), 0.05 * R, R)
+    radii = np.array([0.3 * R, ra, rt, R])
+    k = len(radii)
+    chord, twist, width = np.full(k, 0.05), np.full(k, 0.1), np.full(k, 0.02)
+    out = {}
+    for tip in (False, True):
+        g, _ = uniform_flow_grid(n, dom)
+        rid = g.add_rotor(N, radii, chord, twist, width, (0.0, 0.0, 0.0), om, 0.3, R, 2 * dx,
+                          tip_correction=tip)
+        g.step(1)
+        out[tip] = g.forces(rid)
+    f0, f1 = out[False], out[True]
+    assert np.allclose(f1["phi"], np.arctan2(1.0, om * radii)[None, :], rtol=0, atol=1e-15)
+    assert np.all(np.abs(f0["Fx"][:, 3]) > 0) and np.all(np.abs(f0["Ft"][:, 3]) > 0)
+    assert np.all(f1["Fx"][:, 3] == 0.0) and np.all(f1["Ft"][:, 3] == 0.0)
+    assert np.allclose(f1["Fx"][:, 1] / f0["Fx"][:, 1], 2.0 / 3.0, rtol=1e-12)
+    assert np.allclose(f1["Ft"][:, 2] / f0["Ft"][:, 2], 2.0 / 3.0, rtol=1e-12)
+    # the two coefficient pairs give different factors at the same point
+    assert abs(f1["Ft"][0, 1] / f0["Ft"][0, 1] - 2.0 / 3.0) > 1e-3
+    assert np.all(f1["Fx"][:, 0] / f0["Fx"][:, 0] < 1.0)

@@ -179,7 +179,7 @@ def oracle_grid(w):
     o.set_body_force(*w.body_force)
     for r in w.rotors:
         o.add_rotor(r.n_blades, r.r, r.chord, r.twist, r.width, r.hub, r.omega, r.azimuth0, r.radius, r.eps,
-                    r.rho_inf, r.u_inf_ref, r.correction)
+                    r.rho_inf, r.u_inf_ref, r.correction, r.tip_correction)
     for b in w.bodies:
         o.add_body(b.xyz, b.dS, b.eps, vel=b.vel, niter=b.niter, tol=b.tol)
     o.set_state(w.state0)
@@ -203,10 +203,17 @@ def time_oracle(w, steps, warmup):
 
 
 def source_hash():
+    """Hash of the source the face_flux traffic figure depends on: the device
+    header and the face-flux section of gks_stencil.cu."""
+    csrc = os.path.join(ROOT, "paper_2603_11102_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("gks_stencil.cu", "gks_device.cuh", "gks_internal.h"):
-        with open(os.path.join(ROOT, "paper_2603_11102_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "gks_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "gks_stencil.cu")) as fh:
+        text = fh.read()
+    a = text.index("// ------------------------------------------------------------- face flux --")
+    b = text.index("// ------------------------------------------------- z flux + stage update --")
+    h.update(text[a:b].encode())
     return h.hexdigest()[:16]
 
 

@@ -141,7 +141,12 @@ int gks_set_body_force(gks_grid *g, double fx, double fy, double fz);
  * D cos phi, and are projected with the Gaussian of Eq. (Gaussian) cut at
  * 3 eps. correction != 0 applies the free-stream velocity correction of
  * Sec. 3.1 once, with C_D of the uncorrected angle. radius and u_inf_ref
- * normalise C_P and C_T (Sec. 4.4.1). All axes must be uniform. */
+ * normalise C_P and C_T (Sec. 4.4.1). tip_correction != 0 multiplies F_x and
+ * F_th by the tip factors of Eq. (tip-correction) (Sec. 4.4.2):
+ *   f = (2/pi) acos(exp(-g1 N (R - r) / (2 r |sin phi|))),
+ *   g1 = exp(-c1 (N lambda - c2)) + 0.1, lambda = omega R / u_inf_ref,
+ * with (c1, c2) = (0.1219, 21.52) for F_x and (0.0984, 13.026) for F_th,
+ * N = n_blades, R = radius; f = 0 for r >= R. All axes must be uniform. */
 typedef struct {
     int n_blades, n_pts;
     double hub[3];
@@ -149,6 +154,7 @@ typedef struct {
     double rho_inf, u_inf_ref;
     const double *r, *chord, *twist, *width;
     int correction;
+    int tip_correction;
 } gks_rotor_desc;
 
 /* Add a rotor; *id receives its object id. Not allowed after the first step

@@ -434,6 +434,13 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
     r.nb = nb;
     r.np = np;
     r.correction = d->correction ? 1 : 0;
+    r.tip = d->tip_correction ? 1 : 0;
+    {
+        // g1 = exp(-c1 (N lambda - c2)) + 0.1 of the tip factors, lambda = omega R / U_inf
+        const double c1[2] = {0.1219, 0.0984}, c2[2] = {21.52, 13.026};
+        const double tsr = d->omega * d->radius / d->u_inf_ref;
+        for (int k = 0; k < 2; ++k) r.tip_g[k] = exp(-c1[k] * (d->n_blades * tsr - c2[k])) + 0.1;
+    }
     for (int a = 0; a < 3; ++a) r.hub[a] = d->hub[a];
     r.omega = d->omega;
     r.az0 = d->azimuth0;
@@ -775,6 +782,8 @@ int adjoint_check(gks_grid *g)
     if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
     if (!g->rotors.empty() && g->rotors[0].correction)
         return fail(g, GKS_ERR_STATE, "the adjoint does not cover the ALM velocity correction");
+    if (!g->rotors.empty() && g->rotors[0].tip)
+        return fail(g, GKS_ERR_STATE, "the adjoint does not cover the tip correction");
     return GKS_OK;
 }
 }  // namespace

@@ -126,6 +126,15 @@ __device__ __forceinline__ double polar_cl(double a)
 
 // ------------------------------------------------------------------ ALM --
 
+// Tip factor of Eq. (tip-correction): (2/pi) acos(exp(-g1 N (R - r) /
+// (2 r |sin phi|))); 0 at and beyond the tip, 1 where sin phi = 0.
+__device__ __forceinline__ double tip_factor(double g1, int nb, double R, double r, double phi)
+{
+    if (r >= R) return 0.0;
+    const double x = g1 * nb * (R - r) / (2.0 * r * fabs(sin(phi)));
+    return (2.0 / kPi) * acos(exp(-x));
+}
+
 __global__ void __launch_bounds__(256) alm_loads_kernel(Lattice L, const void *S, RotorDev r, Scalars *scal)
 {
     const double t = scal->t + scal->dt;   // blades and samples at t_{n+1}
@@ -167,6 +176,10 @@ __global__ void __launch_bounds__(256) alm_loads_kernel(Lattice L, const void *S
             const double Lf = qd * polar_cl(al), Df = qd * polar_cd(al);
             Fx = (Lf * cos(phi) + Df * sin(phi)) * r.scale[q];
             Ft = (Lf * sin(phi) - Df * cos(phi)) * r.scale[q];
+            if (r.tip) {
+                Fx *= tip_factor(r.tip_g[0], r.nb, r.radius, rr, phi);
+                Ft *= tip_factor(r.tip_g[1], r.nb, r.radius, rr, phi);
+            }
         }
         r.F[q] = Fx;
         r.F[npts + q] = Ft;

@@ -96,7 +96,8 @@ void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored ar
 
 // Actuator line (gks_forcing.cu).
 struct RotorDev {
-    int nb, np, correction;
+    int nb, np, correction, tip;
+    double tip_g[2];    // g1 of the tip factor: axial, tangential
     double hub[3], omega, az0, radius, eps, rho_inf, uref;
     double rmin, rmax;  // smallest and largest point radius
     double *r, *chord, *twist, *width, *scale;  // device arrays

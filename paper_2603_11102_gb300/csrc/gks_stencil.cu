@@ -797,8 +797,9 @@ __device__ __forceinline__ double max_nan(double a, double b) { return (b > a ||
 // time step), and for FP32C the FP32 reconstruction input hi + lo (density
 // as rho - off). One atomicMax per block.
 template <int PREC>
-__global__ void __launch_bounds__(256) prep_cfl_kernel(const void *S, float *wk, long np, int nx, int ny,
-                                                       int nz, int P0, int P1, float off, Scalars *scal)
+__global__ void __launch_bounds__(256) prep_cfl_kernel(const void *__restrict__ S, float *__restrict__ wk, long np,
+                                                       int nx, int ny, int nz, int P0, int P1, float off,
+                                                       Scalars *scal)
 {
     __shared__ double red[8];
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
@@ -809,11 +810,11 @@ __global__ void __launch_bounds__(256) prep_cfl_kernel(const void *S, float *wk,
             const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
             double u2;
             if (PREC == GKS_FP64) {
-                const double *W = (const double *)S;
+                const double *__restrict__ W = (const double *)S;
                 const double r = W[lin], a = W[np + lin], b = W[2 * np + lin], c = W[3 * np + lin];
                 u2 = (a * a + b * b + c * c) / (r * r);
             } else {
-                const float *W = (const float *)S;
+                const float *__restrict__ W = (const float *)S;
                 float h[4], l[4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {

@@ -36,7 +36,8 @@ class RotorDesc(C.Structure):
     _fields_ = [("n_blades", C.c_int), ("n_pts", C.c_int), ("hub", C.c_double * 3), ("omega", C.c_double),
                 ("azimuth0", C.c_double), ("radius", C.c_double), ("eps", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf_ref", C.c_double), ("r", _dp), ("chord", _dp),
-                ("twist", _dp), ("width", _dp), ("correction", C.c_int)]
+                ("twist", _dp), ("width", _dp), ("correction", C.c_int),
+                ("tip_correction", C.c_int)]
 
 
 class ForcesOut(C.Structure):
@@ -234,6 +235,7 @@ class Grid:
         d.rho_inf, d.u_inf_ref = float(rot.rho_inf), float(rot.u_inf_ref)
         d.r, d.chord, d.twist, d.width = (p for _, p in arrs)
         d.correction = int(bool(rot.correction))
+        d.tip_correction = int(bool(getattr(rot, "tip_correction", False)))
         rid = C.c_int()
         _check(lib.gks_add_actuator_lines(self.h, C.byref(d), C.byref(rid)), self.h)
         self.objects.append(("rotor", d.n_blades, d.n_pts))

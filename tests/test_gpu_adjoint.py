@@ -186,3 +186,9 @@ def test_adjoint_rejects_unsupported_grids(mods):
     with pytest.raises(gks.GKSError) as e:
         g2.step_adjoint(g2.adjoint_workspace(), 0.0, W, W)
     assert e.value.code == -5
+    w3 = rotor_box_workload()
+    w3.rotors[0].tip_correction = True
+    g3 = gks.Grid.from_workload(w3, precision="fp64")
+    with pytest.raises(gks.GKSError) as e:
+        g3.step_adjoint(g3.adjoint_workspace(), 0.0, W, W)
+    assert e.value.code == -5

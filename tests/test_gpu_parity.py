@@ -112,6 +112,27 @@ def test_actuator_lines(gks, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_actuator_lines_with_tip_correction(gks, precision):
+    """Eq. (tip-correction): both tip factors on, velocity correction off."""
+    w = small_rotor_workload()
+    w.rotors[0].tip_correction = True
+    g, o, _ = run_pair(gks, w, precision, 3)
+    a, b = g.get_state(), o.get_state()
+    assert rel_linf(a, b) <= TOL[precision], rel_linf_components(a, b)
+    fg, fo = g.forces(0), o.forces(0)
+    tol = 1e-11 if precision == "fp64" else 1e-4
+    for k in ("Fx", "Ft"):
+        assert np.max(np.abs(fg[k] - fo[k])) <= tol * np.max(np.abs(fo[k])), k
+    for k in ("power", "cp", "ct"):
+        assert abs(fg[k] - fo[k]) <= tol * abs(fo[k]), (k, fg[k], fo[k])
+    # the factors act: the corrected loads differ from the uncorrected ones
+    w.rotors[0].tip_correction = False
+    o2 = oracle_from_workload(w)
+    o2.step(3)
+    assert abs(o2.forces(0)["power"] - fo["power"]) > 1e-3 * abs(fo["power"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_actuator_lines_and_immersed_bodies(gks, precision):
     w = small_rotor_workload(ibm=True, n=(72, 32, 32))
     g, o, _ = run_pair(gks, w, precision, 3)

@@ -318,8 +318,17 @@ class Grid:
         _check(lib.gks_get_state_device(self.h, C.c_void_p(out.data_ptr())), self.h)
         return out
 
-    def set_state_tensor(self, t):
+    def set_state_tensor(self, t, sync=True):
+        """Enqueue the scatter of a (4, nz, ny, nx) float64 device tensor into
+        the state on the grid's stream. sync=False returns at once: the caller
+        keeps t alive and unchanged until the grid's stream has passed the
+        scatter (t must then already be float64, contiguous, on this device)."""
         import torch
+        if not sync:
+            if t.dtype != torch.float64 or not t.is_contiguous() or t.device != self.device:
+                raise ValueError("sync=False needs a contiguous float64 tensor on the grid's device")
+            _check(lib.gks_set_state_device(self.h, C.c_void_p(t.data_ptr())), self.h)
+            return
         t = t.to(device=self.device, dtype=torch.float64).contiguous()
         _check(lib.gks_set_state_device(self.h, C.c_void_p(t.data_ptr())), self.h)
         self.stream.synchronize()

@@ -142,7 +142,7 @@ int gks_set_body_force(gks_grid *g, double fx, double fy, double fz);
  * 3 eps. correction != 0 applies the free-stream velocity correction of
  * Sec. 3.1 once, with C_D of the uncorrected angle. radius and u_inf_ref
  * normalise C_P and C_T (Sec. 4.4.1). tip_correction != 0 multiplies F_x and
- * F_th by the tip factors of Eq. (tip-correction) (Sec. 4.4.2):
+ * F_th by the tip factors of Eq. (tip-correction) (Sec. 4.4):
  *   f = (2/pi) acos(exp(-g1 N (R - r) / (2 r |sin phi|))),
  *   g1 = exp(-c1 (N lambda - c2)) + 0.1, lambda = omega R / u_inf_ref,
  * with (c1, c2) = (0.1219, 21.52) for F_x and (0.0984, 13.026) for F_th,
@@ -176,7 +176,7 @@ int gks_set_force_scales(gks_grid *g, int id, const double *h_scales);
 int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, const double *vel,
                       double eps, int niter, double tol, int *id);
 
-/* Advance nsteps S2O4 steps (Sec. 2; forcing after each update, Sec. 3.3:
+/* Advance nsteps S2O4 steps (Sec. 2; forcing after each update, end of Sec. 3.2:
  * body force, rotors in the order added, then bodies in the order added).
  * Synchronises the stream at the end and reports GKS_ERR_NONFINITE,
  * GKS_ERR_CFL or GKS_ERR_RANGE raised on the device. t_out (may be NULL)

@@ -25,7 +25,7 @@
  *   - ALM sampling, loads and Gaussian projection: Sec. 3.1, Eq. (axial-
  *     tangential), Eq. (Gaussian); truncation at 3 eps: Sec. 4.3.1.
  *   - IBM spreading, direct forcing iteration: Sec. 3.2, Eq. (ibm-1),
- *     Eq. (force-ibm); forcing after the S2O4 update: Sec. 3.3.
+ *     Eq. (force-ibm); forcing after the S2O4 update: end of Sec. 3.2.
  *   - Power and thrust coefficients: Sec. 4.4.1.
  *   - Boundary conditions: Sec. 4.1 (periodic, no-slip wall), Sec. 4.3
  *     (Riemann-invariant inflow, extrapolation outflow, slip wall), Sec. 4.4
@@ -1020,7 +1020,7 @@ static double polar_cl(double a)
 }
 static double polar_cd(double a) { return 0.01 + 0.02 * a * a; }
 
-/* Tip correction factor of Eq. (tip-correction) (Sec. 4.4.2, NTNU rotor):
+/* Tip correction factor of Eq. (tip-correction) (Sec. 4.4, NTNU rotor):
  *   f = (2/pi) arccos[exp(-g1 N (R - r) / (2 r sin(phi)))],
  *   g1 = exp(-c1 (N lambda - c2)) + 0.1,
  * N blades, rotor radius R, tip speed ratio lambda = omega R / U_inf and the
@@ -1293,7 +1293,7 @@ static int one_step(og_grid *g)
                 for (int i = 0; i < g->n[0]; ++i) g->W[(1 + d) * np + IDX(g, i, j, k)] += dt * g->fbody[d];
     }
     g->t += dt;
-    /* Sec. 3.3: external forcing after the S2O4 update; rotors, then bodies */
+    /* End of Sec. 3.2: external forcing after the S2O4 update; rotors, then bodies */
     for (int o = 0; o < g->nobj; ++o)
         if (g->obj[o]->kind == 0)
             if (alm_apply(g, g->obj[o], g->t, dt)) return -1;

@@ -2,7 +2,7 @@
 // FP64, for gradients of a functional of the state with respect to the
 // per-point actuator force scales and the inflow speed.
 //
-// The forward step (Sec. 2 and Sec. 3.3) is a composition of
+// The forward step (Sec. 2 and the end of Sec. 3.2) is a composition of
 //   ghost fill G, spatial operator (L, Lt) = S(A) per direction d
 //   [face state: WENO5 + half-space equilibrium + normal slope;
 //    face flux: tangential quartic to the Gauss points + closed-form flux;

@@ -1,5 +1,5 @@
 // gks_forcing.cu -- actuator-line (Sec. 3.1) and immersed-boundary (Sec. 3.2)
-// body forcing, applied after the S2O4 update (Sec. 3.3).
+// body forcing, applied after the S2O4 update (end of Sec. 3.2).
 //
 // ALM: one block per rotor samples the velocity at every actuator point at
 // t_{n+1} (trilinear, cell centres), evaluates the angle of attack, the

@@ -43,3 +43,16 @@ def smooth_workload(n, bc, faces=None, mu=2e-3, seed=0, amp=0.05, cfl=0.5, dt_fi
     Q[1:] += amp * 0.1 * (2 * rng.random(Q[1:].shape) - 1)
     return WL.Workload("smooth-%dx%dx%d" % tuple(n), tuple(n), faces, 0.1, 1.0, mu, [tuple(x) for x in bc],
                        cfl=cfl, dt_fixed=dt_fixed, state0=Q)
+
+
+def paper_values():
+    """Values the paper prints (tests/golden/paper_values.txt): name -> list of floats."""
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out[line[0]] = [float(v) for v in line[1:]]
+    return out
+

@@ -10,6 +10,8 @@ import pytest
 import oracle as O
 from paper_2603_11102_gb300 import workloads as WL
 
+from _setup import paper_values
+
 L2PI = 2 * math.pi
 
 
@@ -250,7 +252,7 @@ def uniform_flow_grid(n, dom, u=1.0, mu=1e-3):
 def test_alm_blades_symmetric_and_momentum_balance():
     """Sec. 3.1: in a uniform axial stream the three blades carry equal loads;
     the momentum the fluid gains equals minus the point forces times the
-    lattice mass of each truncated Gaussian (Eq. (Gaussian), Sec. 3.3)."""
+    lattice mass of each truncated Gaussian (Eq. (Gaussian), end of Sec. 3.2)."""
     n = (24, 32, 32)
     dom = [(-0.5, 0.5), (-0.7, 0.7), (-0.7, 0.7)]
     g, Q = uniform_flow_grid(n, dom)
@@ -319,7 +321,7 @@ def test_ibm_quiescent_zero_force_and_relaxation():
 
 
 def test_alm_tip_correction_special_values():
-    """Eq. (tip-correction), Sec. 4.4.2: f = (2/pi) arccos(exp(-x)) with
+    """Eq. (tip-correction), Sec. 4.4: f = (2/pi) arccos(exp(-x)) with
     x = g1 N (R - r) / (2 r sin phi), g1 = exp(-c1 (N lambda - c2)) + 0.1,
     (c1, c2) = (0.1219, 21.52) for F_x and (0.0984, 13.026) for F_theta. In a
     uniform axial stream the sampled velocity at the first step is exactly
@@ -339,8 +341,10 @@ def test_alm_tip_correction_special_values():
         g1 = math.exp(-c1 * (N * lam - c2)) + 0.1
         return g1 * N * (R - r) / (2 * r * abs(math.sin(math.atan2(1.0, om * r))))
 
-    ra = brentq(lambda r: x_of(r, 0.1219, 21.52) - math.log(2), 0.05 * R, R)
-    rt = brentq(lambda r: x_of(r, 0.0984, 13.026) - math.log(2), 0.05 * R, R)
+    pv = paper_values()
+    ca, ct = pv["tip_correction_axial_c1_c2"], pv["tip_correction_tangential_c1_c2"]
+    ra = brentq(lambda r: x_of(r, *ca) - math.log(2), 0.05 * R, R)
+    rt = brentq(lambda r: x_of(r, *ct) - math.log(2), 0.05 * R, R)
     radii = np.array([0.3 * R, ra, rt, R])
     k = len(radii)
     chord, twist, width = np.full(k, 0.05), np.full(k, 0.1), np.full(k, 0.02)

@@ -15,6 +15,8 @@ from numpy.polynomial import polynomial as P
 
 import oracle as O
 
+from _setup import paper_values
+
 LAM = 0.005          # Ma = 0.1, U_ref = 1
 THETA = 1.0 / (2 * LAM)
 
@@ -271,8 +273,11 @@ def test_gaussian_kernel_normalisation_and_truncation():
     mass = quad(lambda r: 4 * math.pi * r * r * O.gauss_kernel(r, eps), 0, 3 * eps,
                 epsabs=1e-14, epsrel=1e-12, limit=200)[0]
     assert abs(mass - ref) < 1e-12
-    ratio = O.gauss_kernel(2.15 * eps, eps) / O.gauss_kernel(0.0, eps)
-    assert abs(ratio - 0.0098) < 2e-4
+    pv = paper_values()
+    r1 = pv["gaussian_one_percent_radius_over_eps"][0]
+    ratio = O.gauss_kernel(r1 * eps, eps) / O.gauss_kernel(0.0, eps)
+    # the printed radius is rounded to 3 digits: exp(-2.15^2) = 0.0098
+    assert abs(ratio - pv["gaussian_one_percent_level"][0]) < 3e-4
     assert O.gauss_kernel(3 * eps * (1 + 1e-12), eps) == 0.0
     assert O.gauss_kernel(3 * eps * (1 - 1e-12), eps) > 0.0
     # on a lattice with eps = 2h the sampled sum is close to the continuum value

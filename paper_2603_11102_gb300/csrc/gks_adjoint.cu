@@ -173,8 +173,8 @@ __device__ void weno5_rev(double a, double b, double c, double d, double e, doub
     const double s2 = 1e-6 + (c13 * t2 * t2 + 0.25 * u2 * u2);
     const double S0 = s0 * s0, S1 = s1 * s1, S2 = s2 * s2;
     const double w0 = 0.1 * (S1 * S2), w1 = 0.6 * (S0 * S2), w2 = 0.3 * (S0 * S1);
-    const double W = w0 + w1 + w2, N = w0 * p0 + w1 * p1 + w2 * p2, v = N / W;
-    const double Nb = vb / W, Wb = -vb * v / W;
+    const double W = w0 + w1 + w2, N = w0 * p0 + w1 * p1 + w2 * p2, iW = 1.0 / W, v = N * iW;
+    const double Nb = vb * iW, Wb = -Nb * v;
     const double p0b = Nb * w0, p1b = Nb * w1, p2b = Nb * w2;
     const double w0b = Nb * p0 + Wb, w1b = Nb * p1 + Wb, w2b = Nb * p2 + Wb;
     const double S0b = w1b * 0.6 * S2 + w2b * 0.3 * S1;
@@ -197,7 +197,8 @@ __device__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], cons
 {
     const double off = ph.off;
     const double rl = off + Ql[0], rr = off + Qr[0];
-    const double Ul = Ql[1] / rl, Ur = Qr[1] / rr;
+    const double irl = 1.0 / rl, irr = 1.0 / rr;
+    const double Ul = Ql[1] * irl, Ur = Qr[1] * irr;
     const double zl = ph.sqlam * Ul, zr = ph.sqlam * Ur;
     const double el = erf(zl), er = erf(zr);
     const double Pl = 0.5 + 0.5 * el, Pr = 0.5 - 0.5 * er;
@@ -218,13 +219,14 @@ __device__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], cons
     const double Elb = Q0b[1] * Ql[0], Erb = -Q0b[1] * Qr[0];
     double xlb = Q0b[1] * off * ph.kE * exl + Elb * El;
     double xrb = -Q0b[1] * off * ph.kE * exr + Erb * Er;
+    // d erf(z)/dz = (2/sqrt pi) exp(-z^2), and z^2 = lambda U^2: exp(-z^2) = exp(x)
     const double dz = 2.0 / sqrt(kPi);
-    double Ulb = elb * ph.sqlam * dz * exp(-zl * zl) + xlb * (-2.0 * ph.lambda * Ul);
-    double Urb = erb * ph.sqlam * dz * exp(-zr * zr) + xrb * (-2.0 * ph.lambda * Ur);
-    Qlb[1] += Ulb / rl;
-    Qlb[0] += -Ulb * Ul / rl;
-    Qrb[1] += Urb / rr;
-    Qrb[0] += -Urb * Ur / rr;
+    double Ulb = elb * ph.sqlam * dz * exl + xlb * (-2.0 * ph.lambda * Ul);
+    double Urb = erb * ph.sqlam * dz * exr + xrb * (-2.0 * ph.lambda * Ur);
+    Qlb[1] += Ulb * irl;
+    Qlb[0] += -Ulb * Ul * irl;
+    Qrb[1] += Urb * irr;
+    Qrb[0] += -Urb * Ur * irr;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -334,35 +336,40 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     }
 }
 
-// RB: transpose of the t2 pass, per t1-pass row (f, a, b'), b' in [-2, n2+2).
-__global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
+// RB: transpose of the t2 pass, per t1-pass row (f, a, b'), b' in [-2, n2+2),
+// and t1 Gauss point m (blockIdx.y = 2 x row tile + m): a 5-tap gather of
+// the Gauss-point adjoints of the faces b = b'-2 .. b'+2.
+__global__ void __launch_bounds__(256, 3) rev_t2_kernel(RevArgs A)
 {
-    const int a = blockIdx.x * 32 + threadIdx.x, bp = (int)(blockIdx.y * 8 + threadIdx.y) - 2, f = blockIdx.z;
+    const int m = blockIdx.y & 1;
+    const int a = blockIdx.x * 32 + threadIdx.x, bp = (int)((blockIdx.y >> 1) * 8 + threadIdx.y) - 2, f = blockIdx.z;
     if (a >= A.n1 || bp >= A.n2 + 2) return;
-    double X[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}}, Y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    double Z[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    double X[4] = {0, 0, 0, 0}, Y[4] = {0, 0, 0, 0}, Z[4] = {0, 0, 0, 0};
     const int blo = bp - 2 < 0 ? 0 : bp - 2, bhi = bp + 2 > A.n2 - 1 ? A.n2 - 1 : bp + 2;
+    const int nG = (int)A.nG;   // 64 nG < 2^31 (checked by the host)
+    const double *Gm = A.lamG + (long)(m * 32) * A.nG;
+#pragma unroll 1
     for (int b = blo; b <= bhi; ++b) {
         const int s = bp - b + 2;
-        const long face = ((long)f * A.n2 + b) * A.n1 + a;
-        for (int m = 0; m < 2; ++m)
-            for (int nn = 0; nn < 2; ++nn) {
-                const int g = m * 2 + nn;
-                const double wv = cWV[nn][s], wd = cWD[nn][s];
-                for (int v = 0; v < 4; ++v) {
-                    X[m][v] += wv * A.lamG[(g * 16 + 0 + v) * A.nG + face] + wd * A.lamG[(g * 16 + 12 + v) * A.nG + face];
-                    Y[m][v] += wv * A.lamG[(g * 16 + 8 + v) * A.nG + face];
-                    Z[m][v] += wv * A.lamG[(g * 16 + 4 + v) * A.nG + face];
-                }
+        const double *Gf = Gm + ((long)f * A.n2 + b) * A.n1 + a;
+#pragma unroll
+        for (int nn = 0; nn < 2; ++nn) {
+            const double wv = cWV[nn][s], wd = cWD[nn][s];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                X[v] += wv * Gf[(nn * 16 + 0 + v) * nG] + wd * Gf[(nn * 16 + 12 + v) * nG];
+                Y[v] += wv * Gf[(nn * 16 + 8 + v) * nG];
+                Z[v] += wv * Gf[(nn * 16 + 4 + v) * nG];
             }
+        }
     }
     const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
-    for (int m = 0; m < 2; ++m)
-        for (int v = 0; v < 4; ++v) {
-            A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = X[m][v];
-            A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = Y[m][v];
-            A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = Z[m][v];
-        }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = X[v];
+        A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = Y[v];
+        A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = Z[v];
+    }
 }
 
 // RC: transpose of the t1 pass, per face of the extended box.
@@ -794,7 +801,7 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, const dou
             attr = true;
         }
         rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, smem, c.stream>>>(R);
-        rev_t2_kernel<<<dim3((R.n1 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_t2_kernel<<<dim3((R.n1 + 31) / 32, 2 * ((R.n2 + 4 + 7) / 8), nf), blk, 0, c.stream>>>(R);
         rev_t1_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
         rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
         rev_gather_cells_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,

@@ -784,6 +784,11 @@ int adjoint_check(gks_grid *g)
         return fail(g, GKS_ERR_STATE, "the adjoint does not cover the ALM velocity correction");
     if (!g->rotors.empty() && g->rotors[0].tip)
         return fail(g, GKS_ERR_STATE, "the adjoint does not cover the tip correction");
+    // the reverse t2 gather indexes its 64 face arrays with 32-bit offsets
+    for (int d = 0; d < 3; ++d) {
+        const double nf = (double)(c.n[d] + 1) * c.n[(d + 1) % 3] * c.n[(d + 2) % 3];
+        if (64.0 * nf >= 2147483647.0) return fail(g, GKS_ERR_ARG, "grid too large for the adjoint");
+    }
     return GKS_OK;
 }
 }  // namespace

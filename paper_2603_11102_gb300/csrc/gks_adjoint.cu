@@ -756,15 +756,15 @@ __global__ void alm_sample_adj_kernel(AlmAdjArgs A)
 
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
 // for lamL (may be null) and lamLt; result accumulated into w.lamA.
-void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, const double *lamL, const double *lamLt)
+void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], const double *lamL,
+                     const double *lamLt)
 {
     const Phys<double> ph = make_phys<double>(c);
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
-        launch_face_eq_fp64(c, Aw, d);
         RevArgs R;
         R.A = Aw;
-        R.fq = (const double *)c.fq;
+        R.fq = fq[d];   // face box of this direction, kept by the forward recompute
         R.nfq = c.nfq;
         R.e1p = c.e1p[d];
         R.lamL = lamL;
@@ -874,6 +874,8 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
     w->lamP = take(np4);
     w->lamL = take(np4);
     w->lamLt = take(np4);
+    for (int st = 0; st < 2; ++st)
+        for (int d = 0; d < 3; ++d) w->fqs[st][d] = take(8 * c.nfq);
     long nG = 0, nR = 0, maxsurf = 0;
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
@@ -934,13 +936,13 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, (const double *)c.wk1, nullptr, w.lamLt);
+    spatial_adjoint(c, w, (const double *)c.wk1, w.fqs[1], nullptr, w.lamLt);
     ghost_adjoint(c, w, (const double *)c.wk1);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, w.A0, w.lamL, w.lamLt);
+    spatial_adjoint(c, w, w.A0, w.fqs[0], w.lamL, w.lamLt);
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }

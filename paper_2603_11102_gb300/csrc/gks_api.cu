@@ -237,6 +237,41 @@ int gks_workspace_bytes(const gks_grid_desc *desc, size_t *state_bytes, size_t *
     return GKS_OK;
 }
 
+namespace {
+
+// TMA descriptor of the face box of direction a at `base`: dims (t1 padded,
+// t2 + 4, faces, 8 components), box (36, 12, 1, 8). c.e1p must be set.
+int encode_face_map(const Ctx &c, int a, void *base, CUtensorMap *out, std::string *msg)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&encode, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || !encode || q != cudaDriverEntryPointSuccess) {
+            encode = nullptr;
+            *msg = "cuTensorMapEncodeTiled not available";
+            return 1;
+        }
+    }
+    const cuuint64_t es = c.prec == GKS_FP64 ? 8 : 4;
+    const int t2 = a == 2 ? 1 : 2;
+    const cuuint64_t dims[4] = {(cuuint64_t)c.e1p[a], (cuuint64_t)(c.n[t2] + 4), (cuuint64_t)(c.n[a] + 1), 8};
+    const cuuint64_t strides[3] = {dims[0] * es, dims[0] * dims[1] * es, (cuuint64_t)c.nfq * es};
+    const cuuint32_t box[4] = {36, 12, 1, 8};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(out, c.prec == GKS_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *msg = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return 1;
+    }
+    return 0;
+}
+
+}  // namespace
+
 int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_grid **out)
 {
     std::string msg;
@@ -314,35 +349,13 @@ int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_
         if (!rc) rc = upload<double>(g, c.h64[a], h);
         if (rc) { msg = g->err; delete g; return fail(nullptr, rc, msg); }
     }
-    // TMA descriptors of the face box, one per direction: dims (t1 padded,
-    // t2, face, component), box (36, 12, 1, 8)
-    {
-        PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&encode, 12000,
-                                                         cudaEnableDefault, &q);
-        if (e != cudaSuccess || !encode || q != cudaDriverEntryPointSuccess) {
-            msg = "cuTensorMapEncodeTiled not available";
+    // TMA descriptors of the face box, one per direction
+    for (int a = 0; a < 3; ++a) {
+        c.e1p[a] = L.e1p[a];
+        std::string m;
+        if (encode_face_map(c, a, c.fq, &c.tmap[a], &m)) {
             delete g;
-            return fail(nullptr, GKS_ERR_CUDA, msg);
-        }
-        const cuuint64_t es = c.prec == GKS_FP64 ? 8 : 4;
-        for (int a = 0; a < 3; ++a) {
-            const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
-            (void)t1;
-            c.e1p[a] = L.e1p[a];
-            const cuuint64_t dims[4] = {(cuuint64_t)L.e1p[a], (cuuint64_t)(c.n[t2] + 4), (cuuint64_t)(c.n[a] + 1), 8};
-            const cuuint64_t strides[3] = {dims[0] * es, dims[0] * dims[1] * es, (cuuint64_t)L.nfq * es};
-            const cuuint32_t box[4] = {36, 12, 1, 8};
-            const cuuint32_t estr[4] = {1, 1, 1, 1};
-            CUresult r = encode(&c.tmap[a], c.prec == GKS_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                4, c.fq, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) {
-                msg = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
-                delete g;
-                return fail(nullptr, GKS_ERR_CUDA, msg);
-            }
+            return fail(nullptr, GKS_ERR_CUDA, m);
         }
     }
     rc = cuda_check(g, cudaMemsetAsync(c.scal, 0, sizeof(Scalars), c.stream), "clear scalars");
@@ -820,14 +833,26 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
                     "set time");
     if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.scal, 0, 8 * sizeof(double), c.stream), "clear adjoint scalars");
     if (rc) return rc;
+    // each stage and direction keeps its face box for the reverse
+    auto keep_faces = [&](int st) {
+        for (int d = 0; d < 3; ++d) {
+            cc.fq_dir[d] = w.fqs[st][d];
+            std::string m;
+            if (encode_face_map(cc, d, w.fqs[st][d], &cc.tmap_dir[d], &m)) return fail(g, GKS_ERR_CUDA, m);
+        }
+        return (int)GKS_OK;
+    };
     cc.state = w.A0;
     cc.wk0 = w.A0;
     launch_scatter_state(cc, d_state_n);
     launch_ghost(cc, w.A0);
+    if ((rc = keep_faces(0))) return rc;
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
     cc.state = w.Wp;
+    if ((rc = keep_faces(1))) return rc;
     launch_stage(cc, 2);
+    for (int d = 0; d < 3; ++d) cc.fq_dir[d] = nullptr;
     const RotorDev *rot = g->rotors.empty() ? nullptr : &g->rotors[0];
     if (rot) launch_alm_loads(cc, *rot);
     // reverse

@@ -59,6 +59,10 @@ struct Ctx {
     long nfq;
     int e1p[3];               // padded t1 extent of the face box per direction (multiple of 4)
     CUtensorMap tmap[3];      // TMA descriptors of the face box per direction
+    // Optional per-direction face boxes (the adjoint's forward recompute keeps
+    // all of them): when fq_dir[d] is set, direction d uses it and tmap_dir[d].
+    void *fq_dir[3] = {nullptr, nullptr, nullptr};
+    CUtensorMap tmap_dir[3];
     void *ff[3];              // face-averaged F0 and F1 of x and y faces, R[8][nff] (none for z)
     long nff[3];
     void *ih[3];              // R: inverse cell widths, padded index i + 3
@@ -111,11 +115,11 @@ struct RotorDev {
 };
 void launch_alm(const Ctx &c, const RotorDev &r);
 void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no projection
-void launch_face_eq_fp64(const Ctx &c, const double *w, int d);
 
 // Adjoint of one step (gks_adjoint.cu). Buffers of the adjoint workspace.
 struct AdjWork {
     double *A0, *Wp, *lamA, *lamW, *lamP, *lamL, *lamLt;   // 4 * np each (padded indexing)
+    double *fqs[2][3];                                    // face boxes of the recompute, per stage and direction
     double *lamG, *lamR, *lamFQ, *lamC;                   // per face / row buffers
     long nG, nR;                                          // component strides of lamG, lamR
     double *uinf_part;                                    // per inflow ghost contribution
@@ -126,8 +130,8 @@ struct AdjWork {
 size_t adjoint_bytes(const Ctx &c, long npts_total);
 size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
 // Runs the reverse of one step whose forward quantities were recomputed into
-// w (A0, W* in c.wk1, Wp, rotor loads); accumulates into grad (per point) and
-// w.scal[0].
+// w (A0, W* in c.wk1, Wp, rotor loads, the face boxes of both stages in
+// w.fqs); accumulates into grad (per point) and w.scal[0].
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double power_seed, double dt,
                      double t_np1);
 

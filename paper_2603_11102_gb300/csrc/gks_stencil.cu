@@ -715,7 +715,7 @@ void stage_impl(const Ctx &c)
         FaceEqArgs<R> E;
         E.w = w;
         E.np = c.np;
-        E.fq = (R *)c.fq;
+        E.fq = (R *)(c.fq_dir[d] ? c.fq_dir[d] : c.fq);
         E.nfq = c.nfq;
         E.ihf = (const R *)c.ihf[d];
         E.n1 = c.n[t1];
@@ -730,6 +730,7 @@ void stage_impl(const Ctx &c)
         E.ph = ph;
         E.nf = c.n[d] + 1;
         E.K = kMarch;
+        const CUtensorMap &tmap = c.fq_dir[d] ? c.tmap_dir[d] : c.tmap[d];
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
         mark(c, K_FACE_EQ, 1);
         face_eq_march_kernel<R><<<ge, blk, 0, c.stream>>>(E);
@@ -754,7 +755,7 @@ void stage_impl(const Ctx &c)
         mark(c, grp, 1);
         if (d < 2) {
             const int grid = (int)(ntiles < grids.flux ? ntiles : grids.flux);
-            face_flux_kernel<R, STAGE == 1><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(c.tmap[d], F);
+            face_flux_kernel<R, STAGE == 1><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
         } else {
             // z faces: flux and the stage update of every cell
             UpdArgs<R> U;
@@ -780,7 +781,7 @@ void stage_impl(const Ctx &c)
             const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
             const int grid = (int)(nitems < grids.flux_update ? nitems : grids.flux_update);
             flux_update_kernel<R, STAGE><<<grid, blk, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4), c.stream>>>(
-                c.tmap[d], F, U);
+                tmap, F, U);
         }
         mark(c, grp, 0);
     }
@@ -1003,33 +1004,6 @@ int reduce_blocks(long ncell)
 }
 
 }  // namespace
-
-void launch_face_eq_fp64(const Ctx &c, const double *w, int d)
-{
-    const Phys<double> ph = make_phys<double>(c);
-    const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
-    const int t1 = tan1(d), t2 = tan2(d);
-    FaceEqArgs<double> E;
-    E.w = w;
-    E.np = c.np;
-    E.fq = (double *)c.fq;
-    E.nfq = c.nfq;
-    E.ihf = (const double *)c.ihf[d];
-    E.n1 = c.n[t1];
-    E.n2 = c.n[t2];
-    E.e1p = c.e1p[d];
-    E.sd = stride[d];
-    E.s1 = stride[t1];
-    E.s2 = stride[t2];
-    E.cn = 1 + d;
-    E.c1 = 1 + t1;
-    E.c2 = 1 + t2;
-    E.ph = ph;
-    E.nf = c.n[d] + 1;
-    E.K = kMarch;
-    dim3 blk(32, 8), ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
-    face_eq_march_kernel<double><<<ge, blk, 0, c.stream>>>(E);
-}
 
 void launch_prep(const Ctx &c)
 {

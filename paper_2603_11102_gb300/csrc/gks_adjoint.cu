@@ -250,42 +250,12 @@ struct RevArgs {
     Phys<double> ph;
 };
 
-// RA: reverse of the face flux at every interior face.
+// RA: reverse of the face flux at every interior face. The 64 Gauss-point
+// inputs of the face, kept by the forward recompute in lamG, are replaced
+// in place by their adjoints.
 __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
 {
-    extern __shared__ __align__(16) double rev_smem[];
-    double(*sq)[SQ_H][SQ_W] = reinterpret_cast<double(*)[SQ_H][SQ_W]>(rev_smem);
-    double(*st)[SQ_H][TX] = reinterpret_cast<double(*)[SQ_H][TX]>(rev_smem + 8 * SQ_H * SQ_W);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY, f = blockIdx.z;
-    const int e2 = A.n2 + 4;
-    for (int cc = 0; cc < 8; ++cc)
-        for (int r = ty; r < SQ_H; r += TY)
-            for (int col = tx; col < SQ_W; col += TX) {
-                const int sa = a0 + col, sb = b0 + r;
-                double v = 0.0;
-                if (sa < A.n1 + 4 && sb < e2) v = A.fq[cc * A.nfq + ((long)f * e2 + sb) * A.e1p + sa];
-                sq[cc][r][col] = v;
-            }
-    __syncthreads();
-    for (int idx = tid; idx < SQ_H * TX; idx += TX * TY) {
-        const int r = idx / TX, col = idx - r * TX;
-        for (int v = 0; v < 4; ++v) {
-            const double *p = &sq[v][r][col];
-            double vm, vp, dm, dp;
-            tan_val_der(p[0], p[1], p[2], p[3], p[4], vm, vp, dm, dp);
-            st[v * 4 + 0][r][col] = vm;
-            st[v * 4 + 1][r][col] = vp;
-            st[v * 4 + 2][r][col] = dm;
-            st[v * 4 + 3][r][col] = dp;
-            const double *pn = &sq[4 + v][r][col];
-            tan_val_direct(pn[0], pn[1], pn[2], pn[3], pn[4], vm, vp);
-            st[16 + v * 2 + 0][r][col] = vm;
-            st[16 + v * 2 + 1][r][col] = vp;
-        }
-    }
-    __syncthreads();
-    const int a = a0 + tx, b = b0 + ty;
+    const int a = blockIdx.x * TX + threadIdx.x, b = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
     if (a >= A.n1 || b >= A.n2) return;
     // adjoint of the face-averaged fluxes from the two neighbour cells
     const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
@@ -307,31 +277,22 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     }
     const double ih1 = A.ih1[a + G], ih2 = A.ih2[b + G];
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
-    for (int m = 0; m < 2; ++m) {
-        double Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+    for (int g = 0; g < 4; ++g) {
+        double *io = A.lamG + (long)(16 * g) * A.nG + face;
+        double q[4], Dn[4], D1[4], D2[4];
         for (int v = 0; v < 4; ++v) {
-            double vm, vp, dm, dp;
-            tan_val_der(st[v * 4 + m][ty][tx], st[v * 4 + m][ty + 1][tx], st[v * 4 + m][ty + 2][tx],
-                        st[v * 4 + m][ty + 3][tx], st[v * 4 + m][ty + 4][tx], vm, vp, dm, dp);
-            Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
-            tan_val_direct(st[v * 4 + 2 + m][ty][tx], st[v * 4 + 2 + m][ty + 1][tx], st[v * 4 + 2 + m][ty + 2][tx],
-                    st[v * 4 + 2 + m][ty + 3][tx], st[v * 4 + 2 + m][ty + 4][tx], vm, vp);
-            D1[0][v] = vm; D1[1][v] = vp;
-            tan_val_direct(st[16 + v * 2 + m][ty][tx], st[16 + v * 2 + m][ty + 1][tx], st[16 + v * 2 + m][ty + 2][tx],
-                    st[16 + v * 2 + m][ty + 3][tx], st[16 + v * 2 + m][ty + 4][tx], vm, vp);
-            Dn[0][v] = vm; Dn[1][v] = vp;
+            q[v] = io[v * A.nG];
+            Dn[v] = io[(4 + v) * A.nG];
+            D1[v] = io[(8 + v) * A.nG];
+            D2[v] = io[(12 + v) * A.nG];
         }
-        for (int nn = 0; nn < 2; ++nn) {
-            double qb[4], Dnb[4], D1b[4], D2b[4];
-            gk_flux_rev(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, lF0, lF1, A.lamL != nullptr, qb, Dnb, D1b,
-                        D2b);
-            const int g = m * 2 + nn;
-            for (int v = 0; v < 4; ++v) {
-                A.lamG[(g * 16 + 0 + v) * A.nG + face] = qb[v];
-                A.lamG[(g * 16 + 4 + v) * A.nG + face] = Dnb[v];
-                A.lamG[(g * 16 + 8 + v) * A.nG + face] = D1b[v];
-                A.lamG[(g * 16 + 12 + v) * A.nG + face] = D2b[v];
-            }
+        double qb[4], Dnb[4], D1b[4], D2b[4];
+        gk_flux_rev(A.ph, q, Dn, D1, D2, ih1, ih2, lF0, lF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
+        for (int v = 0; v < 4; ++v) {
+            io[v * A.nG] = qb[v];
+            io[(4 + v) * A.nG] = Dnb[v];
+            io[(8 + v) * A.nG] = D1b[v];
+            io[(12 + v) * A.nG] = D2b[v];
         }
     }
 }
@@ -756,8 +717,8 @@ __global__ void alm_sample_adj_kernel(AlmAdjArgs A)
 
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
 // for lamL (may be null) and lamLt; result accumulated into w.lamA.
-void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], const double *lamL,
-                     const double *lamLt)
+void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], double *const gp[3],
+                     const double *lamL, const double *lamLt)
 {
     const Phys<double> ph = make_phys<double>(c);
     for (int d = 0; d < 3; ++d) {
@@ -769,7 +730,7 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *c
         R.e1p = c.e1p[d];
         R.lamL = lamL;
         R.lamLt = lamLt;
-        R.lamG = w.lamG;
+        R.lamG = gp[d];   // Gauss-point inputs of this direction, replaced by their adjoints
         R.nG = w.nG;
         R.lamR = w.lamR;
         R.nR = w.nR;
@@ -794,13 +755,7 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *c
         R.ph = ph;
         const dim3 blk(32, 8);
         const int nf = c.n[d] + 1;
-        const size_t smem = sizeof(double) * (8 * SQ_H * SQ_W + 24 * SQ_H * TX);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(rev_flux_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-        rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, smem, c.stream>>>(R);
+        rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
         rev_t2_kernel<<<dim3((R.n1 + 31) / 32, 2 * ((R.n2 + 4 + 7) / 8), nf), blk, 0, c.stream>>>(R);
         rev_t1_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
         rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
@@ -874,8 +829,6 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
     w->lamP = take(np4);
     w->lamL = take(np4);
     w->lamLt = take(np4);
-    for (int st = 0; st < 2; ++st)
-        for (int d = 0; d < 3; ++d) w->fqs[st][d] = take(8 * c.nfq);
     long nG = 0, nR = 0, maxsurf = 0;
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
@@ -887,7 +840,11 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
     }
     w->nG = nG;
     w->nR = nR;
-    w->lamG = take(64 * nG);
+    for (int st = 0; st < 2; ++st)
+        for (int d = 0; d < 3; ++d) {
+            w->fqs[st][d] = take(8 * c.nfq);
+            w->gps[st][d] = take(64 * nG);
+        }
     w->lamR = take(24 * nR);
     w->lamFQ = take(8 * c.nfq);
     w->lamC = take(24 * c.nfq);
@@ -936,13 +893,13 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, (const double *)c.wk1, w.fqs[1], nullptr, w.lamLt);
+    spatial_adjoint(c, w, (const double *)c.wk1, w.fqs[1], w.gps[1], nullptr, w.lamLt);
     ghost_adjoint(c, w, (const double *)c.wk1);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, w.A0, w.fqs[0], w.lamL, w.lamLt);
+    spatial_adjoint(c, w, w.A0, w.fqs[0], w.gps[0], w.lamL, w.lamLt);
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }

@@ -835,8 +835,10 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     if (rc) return rc;
     // each stage and direction keeps its face box for the reverse
     auto keep_faces = [&](int st) {
+        cc.ngp = w.nG;
         for (int d = 0; d < 3; ++d) {
             cc.fq_dir[d] = w.fqs[st][d];
+            cc.gp_dir[d] = w.gps[st][d];
             std::string m;
             if (encode_face_map(cc, d, w.fqs[st][d], &cc.tmap_dir[d], &m)) return fail(g, GKS_ERR_CUDA, m);
         }
@@ -852,7 +854,7 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     cc.state = w.Wp;
     if ((rc = keep_faces(1))) return rc;
     launch_stage(cc, 2);
-    for (int d = 0; d < 3; ++d) cc.fq_dir[d] = nullptr;
+    for (int d = 0; d < 3; ++d) cc.fq_dir[d] = cc.gp_dir[d] = nullptr;
     const RotorDev *rot = g->rotors.empty() ? nullptr : &g->rotors[0];
     if (rot) launch_alm_loads(cc, *rot);
     // reverse

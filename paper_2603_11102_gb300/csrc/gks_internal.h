@@ -63,6 +63,11 @@ struct Ctx {
     // all of them): when fq_dir[d] is set, direction d uses it and tmap_dir[d].
     void *fq_dir[3] = {nullptr, nullptr, nullptr};
     CUtensorMap tmap_dir[3];
+    // Optional (FP64): per direction, the 64 Gauss-point inputs of every face
+    // (16 g + k arrays of stride ngp; g Gauss point, k = Q0, normal slope, t1
+    // slope, t2 slope x 4 components), written by the flux kernels.
+    void *gp_dir[3] = {nullptr, nullptr, nullptr};
+    long ngp = 0;
     void *ff[3];              // face-averaged F0 and F1 of x and y faces, R[8][nff] (none for z)
     long nff[3];
     void *ih[3];              // R: inverse cell widths, padded index i + 3
@@ -120,8 +125,10 @@ void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no proj
 struct AdjWork {
     double *A0, *Wp, *lamA, *lamW, *lamP, *lamL, *lamLt;   // 4 * np each (padded indexing)
     double *fqs[2][3];                                    // face boxes of the recompute, per stage and direction
-    double *lamG, *lamR, *lamFQ, *lamC;                   // per face / row buffers
-    long nG, nR;                                          // component strides of lamG, lamR
+    double *gps[2][3];                                    // Gauss-point inputs of the recompute (64 nG each);
+                                                          // the reverse flux overwrites them with their adjoints
+    double *lamR, *lamFQ, *lamC;                          // per row / face buffers
+    long nG, nR;                                          // component strides of gps, lamR
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;
     double *pts;                                          // per actuator point scratch (8 per point)

@@ -158,13 +158,13 @@ __device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const dou
     }
 }
 
-// Adjoint of dev::weno5 (same arithmetic for the forward values).
-__device__ void weno5_rev(double a, double b, double c, double d, double e, double vb, double out[5])
+// Adjoint of dev::weno5_pair (both face values of the centre cell of
+// q[0..4], weights folded as in the forward): seeds sR for the right-face
+// value and sL for the left-face value; the cell adjoints are added to out.
+__device__ __forceinline__ void weno5_pair_rev(const double q[5], double sR, double sL, double out[5])
 {
-    const double r6 = 1.0 / 6.0, c13 = 13.0 / 12.0;
-    const double p0 = (2.0 * a - 7.0 * b + 11.0 * c) * r6;
-    const double p1 = (-b + 5.0 * c + 2.0 * d) * r6;
-    const double p2 = (2.0 * c + 5.0 * d - e) * r6;
+    const double c13 = 13.0 / 12.0;
+    const double a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
     const double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
     const double t1 = b - 2.0 * c + d, u1 = b - d;
     const double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
@@ -172,27 +172,43 @@ __device__ void weno5_rev(double a, double b, double c, double d, double e, doub
     const double s1 = 1e-6 + (c13 * t1 * t1 + 0.25 * u1 * u1);
     const double s2 = 1e-6 + (c13 * t2 * t2 + 0.25 * u2 * u2);
     const double S0 = s0 * s0, S1 = s1 * s1, S2 = s2 * s2;
-    const double w0 = 0.1 * (S1 * S2), w1 = 0.6 * (S0 * S2), w2 = 0.3 * (S0 * S1);
-    const double W = w0 + w1 + w2, N = w0 * p0 + w1 * p1 + w2 * p2, iW = 1.0 / W, v = N * iW;
-    const double Nb = vb * iW, Wb = -Nb * v;
-    const double p0b = Nb * w0, p1b = Nb * w1, p2b = Nb * w2;
-    const double w0b = Nb * p0 + Wb, w1b = Nb * p1 + Wb, w2b = Nb * p2 + Wb;
-    const double S0b = w1b * 0.6 * S2 + w2b * 0.3 * S1;
-    const double S1b = w0b * 0.1 * S2 + w2b * 0.3 * S0;
-    const double S2b = w0b * 0.1 * S1 + w1b * 0.6 * S0;
+    const double w02 = 6.0 * (S0 * S2), S01 = S0 * S1, S12 = S1 * S2;
+    // right face: 6 p_k on (a,b,c), (b,c,d), (c,d,e), weights S12, w02, 3 S01
+    const double P0 = 2.0 * a - 7.0 * b + 11.0 * c, P1 = -b + 5.0 * c + 2.0 * d, P2 = 2.0 * c + 5.0 * d - e;
+    const double wr2 = 3.0 * S01;
+    const double iDR = 1.0 / (6.0 * (S12 + w02 + wr2));
+    const double right = (S12 * P0 + w02 * P1 + wr2 * P2) * iDR;
+    // left face: mirrored candidates, weights S01, w02, 3 S12
+    const double Q0 = 2.0 * e - 7.0 * d + 11.0 * c, Q1 = -d + 5.0 * c + 2.0 * b, Q2 = 2.0 * c + 5.0 * b - a;
+    const double wl2 = 3.0 * S12;
+    const double iDL = 1.0 / (6.0 * (S01 + w02 + wl2));
+    const double left = (S01 * Q0 + w02 * Q1 + wl2 * Q2) * iDL;
+    // value = N / D: Nb = s / D, Db = -Nb value
+    const double NRb = sR * iDR, DRb6 = -6.0 * NRb * right;
+    const double NLb = sL * iDL, DLb6 = -6.0 * NLb * left;
+    const double P0b = NRb * S12, P1b = NRb * w02, P2b = NRb * wr2;
+    const double Q0b = NLb * S01, Q1b = NLb * w02, Q2b = NLb * wl2;
+    const double S12b = (NRb * P0 + DRb6) + 3.0 * (NLb * Q2 + DLb6);
+    const double w02b = (NRb * P1 + DRb6) + (NLb * Q1 + DLb6);
+    const double S01b = 3.0 * (NRb * P2 + DRb6) + (NLb * Q0 + DLb6);
+    const double S0b = 6.0 * S2 * w02b + S1 * S01b;
+    const double S1b = S2 * S12b + S0 * S01b;
+    const double S2b = S1 * S12b + 6.0 * S0 * w02b;
     const double s0b = 2.0 * s0 * S0b, s1b = 2.0 * s1 * S1b, s2b = 2.0 * s2 * S2b;
-    const double t0b = s0b * (13.0 / 6.0) * t0, u0b = s0b * 0.5 * u0;
-    const double t1b = s1b * (13.0 / 6.0) * t1, u1b = s1b * 0.5 * u1;
-    const double t2b = s2b * (13.0 / 6.0) * t2, u2b = s2b * 0.5 * u2;
-    out[0] = 2.0 * r6 * p0b + t0b + u0b;
-    out[1] = -7.0 * r6 * p0b - r6 * p1b - 2.0 * t0b - 4.0 * u0b + t1b + u1b;
-    out[2] = 11.0 * r6 * p0b + 5.0 * r6 * p1b + 2.0 * r6 * p2b + t0b + 3.0 * u0b - 2.0 * t1b + t2b + 3.0 * u2b;
-    out[3] = 2.0 * r6 * p1b + 5.0 * r6 * p2b + t1b - u1b - 2.0 * t2b - 4.0 * u2b;
-    out[4] = -r6 * p2b + t2b + u2b;
+    const double t0b = s0b * (2.0 * c13) * t0, u0b = s0b * 0.5 * u0;
+    const double t1b = s1b * (2.0 * c13) * t1, u1b = s1b * 0.5 * u1;
+    const double t2b = s2b * (2.0 * c13) * t2, u2b = s2b * 0.5 * u2;
+    out[0] += t0b + u0b + 2.0 * P0b - Q2b;
+    out[1] += -2.0 * t0b - 4.0 * u0b + t1b + u1b - 7.0 * P0b - P1b + 2.0 * Q1b + 5.0 * Q2b;
+    out[2] += t0b + 3.0 * u0b - 2.0 * t1b + t2b + 3.0 * u2b + 11.0 * P0b + 5.0 * P1b + 2.0 * P2b + 11.0 * Q0b +
+              5.0 * Q1b + 2.0 * Q2b;
+    out[3] += t1b - u1b - 2.0 * t2b - 4.0 * u2b + 2.0 * P1b + 5.0 * P2b - 7.0 * Q0b - Q1b;
+    out[4] += t2b + u2b - P2b + 2.0 * Q0b;
 }
 
 // Adjoint of the half-space equilibrium state (local frame).
-__device__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], const double Qr[4], const double Q0b[4],
+__device__ __forceinline__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], const double Qr[4],
+                                                const double Q0b[4],
                                 double Qlb[4], double Qrb[4])
 {
     const double off = ph.off;
@@ -359,47 +375,93 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
     }
 }
 
-// RD: reverse of WENO5, the equilibrium state and the normal slope, per
-// face of the extended box -> adjoints of the 6 stencil cells.
+// RD: reverse of WENO5, the equilibrium state and the normal slope. Each
+// thread walks kRevMarch faces along d at one position of the extended
+// tangential box with the 6 cells f-3 .. f+2 in registers. Face f's slots
+// of lamC (cells f-3 .. f+2) take its normal-slope adjoint and the paired
+// WENO5 reverse of cell f-1 (seeds: its left value from face f-1, its right
+// value from face f); the last face also takes cell f's reverse (left value
+// only). The sum over faces per cell (RE) is the same as with one reverse
+// per face side.
+constexpr int kRevMarch = 16;
+
 __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
 {
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
-    const int f = blockIdx.z;
-    if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
+    const int nf = A.nd + 1, f0 = blockIdx.z * kRevMarch;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= nf) return;
+    const int f1 = min(f0 + kRevMarch, nf);
     const long stride[3] = {1, (long)A.P[0], (long)A.P[0] * A.P[1]};
     const long sd = stride[A.d];
     int cc[3];
-    cc[A.d] = f - 1; cc[A.t1] = a; cc[A.t2] = b;
-    const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    cc[A.d] = 0; cc[A.t1] = a; cc[A.t2] = b;
+    const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);   // cell 0 along d
     const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
-    double c[4][6];
+    // window w[v][k] = cell f-3+k at face f; before the first face: cells f0-4 .. f0+1
+    double w[4][6];
+#pragma unroll
     for (int v = 0; v < 4; ++v)
-        for (int m = 0; m < 6; ++m) c[v][m] = A.A[comp[v] * A.np + base + (long)(m - 2) * sd];
-    double Ql[4], Qr[4];
-    for (int v = 0; v < 4; ++v) {
-        Ql[v] = weno5(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4]);
-        Qr[v] = weno5(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int cell = f0 - 4 + k;
+            w[v][k] = cell >= -G ? A.A[comp[v] * A.np + base + (long)cell * sd] : 0.0;
+        }
+    // carried: right value of cell f-1 and the left-value seed of cell f-1
+    double Rprev[4], Sprev[4];
+    {
+        double lft[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) weno5_pair(&w[v][1], Rprev[v], lft[v]);   // cell f0-1
+        if (f0 == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Sprev[v] = 0.0;
+        } else {
+            double Rpp[4], dum;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) weno5_pair(&w[v][0], Rpp[v], dum);    // cell f0-2
+            const long o = ((long)(f0 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+            double Q0b[4], Qlb[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Q0b[v] = A.lamFQ[v * A.nfq + o];
+            equilibrium_rev(A.ph, Rpp, lft, Q0b, Qlb, Sprev);
+        }
     }
-    const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
-    double Q0b[4], DNb[4];
-    for (int v = 0; v < 4; ++v) {
-        Q0b[v] = A.lamFQ[v * A.nfq + o];
-        DNb[v] = A.lamFQ[(4 + v) * A.nfq + o];
-    }
-    double Qlb[4], Qrb[4];
-    equilibrium_rev(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
-    const double s = A.ihf[f] * (1.0 / 12.0);
-    for (int v = 0; v < 4; ++v) {
-        double cb[6] = {0, 0, 0, 0, 0, 0}, t[5];
-        weno5_rev(c[v][0], c[v][1], c[v][2], c[v][3], c[v][4], Qlb[v], t);
-        for (int m = 0; m < 5; ++m) cb[m] += t[m];
-        weno5_rev(c[v][5], c[v][4], c[v][3], c[v][2], c[v][1], Qrb[v], t);
-        for (int m = 0; m < 5; ++m) cb[5 - m] += t[m];
-        cb[1] += DNb[v] * s;
-        cb[2] -= 15.0 * DNb[v] * s;
-        cb[3] += 15.0 * DNb[v] * s;
-        cb[4] -= DNb[v] * s;
-        for (int m = 0; m < 6; ++m) A.lamC[(m * 4 + v) * A.nfq + o] = cb[m];
+    for (int f = f0; f < f1; ++f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) w[v][k] = w[v][k + 1];
+            w[v][5] = A.A[comp[v] * A.np + base + (long)(f + 2) * sd];
+        }
+        double Ql[4], Qr[4], Rt[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Ql[v] = Rprev[v];
+            weno5_pair(&w[v][1], Rt[v], Qr[v]);   // cell f
+        }
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+        double Q0b[4], DNb[4], Qlb[4], Qrb[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Q0b[v] = A.lamFQ[v * A.nfq + o];
+            DNb[v] = A.lamFQ[(4 + v) * A.nfq + o];
+        }
+        equilibrium_rev(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
+        const double s = A.ihf[f] * (1.0 / 12.0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double cb[6] = {0, 0, 0, 0, 0, 0};
+            cb[1] += DNb[v] * s;
+            cb[2] -= 15.0 * DNb[v] * s;
+            cb[3] += 15.0 * DNb[v] * s;
+            cb[4] -= DNb[v] * s;
+            weno5_pair_rev(&w[v][0], Qlb[v], Sprev[v], &cb[0]);      // cell f-1
+            if (f == nf - 1) weno5_pair_rev(&w[v][1], 0.0, Qrb[v], &cb[1]);   // cell f, left value only
+#pragma unroll
+            for (int m = 0; m < 6; ++m) A.lamC[(m * 4 + v) * A.nfq + o] = cb[m];
+            Rprev[v] = Rt[v];
+            Sprev[v] = Qrb[v];
+        }
     }
 }
 
@@ -758,7 +820,8 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *c
         rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
         rev_t2_kernel<<<dim3((R.n1 + 31) / 32, 2 * ((R.n2 + 4 + 7) / 8), nf), blk, 0, c.stream>>>(R);
         rev_t1_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
-        rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch), blk,
+                                0, c.stream>>>(R);
         rev_gather_cells_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
                                   c.stream>>>(R);
     }

@@ -42,28 +42,9 @@ __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b
 __host__ __device__ inline int tan1(int d) { return d == 0 ? 1 : 0; }
 __host__ __device__ inline int tan2(int d) { return d == 2 ? 1 : 2; }
 
-// WENO5-JS value at the right face of the centre cell of (a,b,c,d,e), with
-// eps_w = 1e-6 and power 2. The three nonlinear weights d_k/(eps+beta_k)^2
-// are scaled by (eps+beta_0)^2 (eps+beta_1)^2 (eps+beta_2)^2 so that one
-// division remains.
-template <typename R>
-__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
-{
-    const R r6 = R(1.0 / 6.0), c13 = R(13.0 / 12.0), q = R(0.25);
-    const R p0 = (R(2) * a - R(7) * b + R(11) * c) * r6;
-    const R p1 = (-b + R(5) * c + R(2) * d) * r6;
-    const R p2 = (R(2) * c + R(5) * d - e) * r6;
-    R t = a - R(2) * b + c, u = a - R(4) * b + R(3) * c;
-    R s0 = R(1e-6) + (c13 * t * t + q * u * u);
-    t = b - R(2) * c + d; u = b - d;
-    R s1 = R(1e-6) + (c13 * t * t + q * u * u);
-    t = c - R(2) * d + e; u = R(3) * c - R(4) * d + e;
-    R s2 = R(1e-6) + (c13 * t * t + q * u * u);
-    s0 *= s0; s1 *= s1; s2 *= s2;
-    const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
-    return wdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
-}
-
+// WENO5-JS (Sec. 2): eps_w = 1e-6, power 2, linear weights 1/10, 6/10, 3/10
+// on the candidate stencils (a,b,c), (b,c,d), (c,d,e) for the right face of
+// the centre cell c.
 // Both face values of the centre cell of q[0..4] (cells -2..2) from one set
 // of Jiang-Shu smoothness indicators: the value at the right face (+1/2) and,
 // with the stencils mirrored, at the left face (-1/2). The mirrored

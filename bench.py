@@ -260,6 +260,11 @@ def time_adjoint(args, dev):
     g = gks.Grid.from_workload(w, precision="fp64", device=dev)
     iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
     npts = w.rotors[0].n_blades * len(w.rotors[0].r)
+    # untimed warm-up: one checkpoint segment forward and backward (first
+    # kernel launches, the adjoint workspace)
+    sw = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+    uw = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    adjoint.rotor_objective(g, sw, uw, args.adjoint_k, K=args.adjoint_k, iplane=iplane, beta=1.0).backward()
     s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
     u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize(dev)
@@ -273,6 +278,7 @@ def time_adjoint(args, dev):
     g.close()
     fwd, bwd = t1 - t0, t2 - t1
     return {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
+            "warmup": "one untimed segment of %d steps, forward and backward" % args.adjoint_k,
             "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
             "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
             "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"

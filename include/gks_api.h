@@ -250,9 +250,10 @@ int gks_get_state_device(gks_grid *g, double *d_state);
  *               inputs).
  * The forward step is recomputed from d_state_n inside the call; the grid's
  * own state is not changed. Requires a GKS_FP64 grid with a fixed time step,
- * at most one rotor without the velocity or tip correction and no immersed
- * body (GKS_ERR_STATE otherwise), and fewer than 2^31 / 64 faces per
- * direction (GKS_ERR_ARG otherwise). Synchronises the stream. */
+ * at most one rotor without the velocity or tip correction, and immersed
+ * bodies only with a fixed iteration count (tol = 0) (GKS_ERR_STATE
+ * otherwise), and fewer than 2^31 / 64 faces per direction (GKS_ERR_ARG
+ * otherwise). Synchronises the stream. */
 int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes);
 int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n,
                      const double *d_adj_np1, double *d_adj_n, double power_seed,

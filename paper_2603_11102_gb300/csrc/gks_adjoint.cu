@@ -871,6 +871,32 @@ __global__ void __launch_bounds__(256) add_interior_kernel(double *dst, const do
     for (int v = 0; v < 4; ++v) dst[v * np + l] += src[v * np + l];
 }
 
+// Reverse of the direct-forcing iterations of one immersed body with a fixed
+// iteration count N (Sec. 3.2, Eq. (ibm-1)): per box cell with Vbar > 0 each
+// iteration is m <- m + rho phi (vbar - m / rho) = (1 - phi) m + phi rho vbar
+// (density unchanged), so m_N = q m + (1 - q) rho vbar with q = (1 - phi)^N,
+// and lambda_m <- q lambda_m, lambda_rho += (1 - q) sum_d vbar_d lambda_m_d.
+__global__ void __launch_bounds__(256) ibm_adj_kernel(double *lam, long np, int P0, int P1, BodyDev b)
+{
+    const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (c >= b.nbox) return;
+    if (!(b.Vbar[c] > 0.0)) return;
+    const int bx = b.box[0][1] - b.box[0][0] + 1, by = b.box[1][1] - b.box[1][0] + 1;
+    const int i = b.box[0][0] + (int)(c % bx);
+    const int j = b.box[1][0] + (int)((c / bx) % by);
+    const int k = b.box[2][0] + (int)(c / ((long)bx * by));
+    const long l = lin(P0, P1, i, j, k);
+    double q = 1.0;
+    for (int s = 0; s < b.niter; ++s) q *= 1.0 - b.phi[c];
+    double lr = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double lm = lam[(1 + d) * np + l];
+        lam[(1 + d) * np + l] = q * lm;
+        lr += (1.0 - q) * b.vbar[3 * c + d] * lm;
+    }
+    lam[l] += lr;
+}
+
 }  // namespace
 
 // Offsets of the adjoint buffers from `base` (base may be 0 to size them);
@@ -924,11 +950,16 @@ size_t adjoint_bytes(const Ctx &c, long npts_total)
     return adjoint_carve(c, npts_total, nullptr, &w);
 }
 
-void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double power_seed, double dt,
-                     double t_np1)
+void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
+                     double power_seed, double dt, double t_np1)
 {
     const dim3 blk(32, 8), gcell((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
     const size_t bytes4 = sizeof(double) * 4 * c.np;
+    // IBM reverse (bodies act after the rotors, in the order added): lamP
+    // goes from the state after the step to the state after the rotors
+    for (int k = nbodies - 1; k >= 0; --k)
+        ibm_adj_kernel<<<(int)((bodies[k].nbox + 255) / 256), 256, 0, c.stream>>>(w.lamP, c.np, c.P[0], c.P[1],
+                                                                                 bodies[k]);
     // ALM reverse: lamP holds lambda'' (state after the step) and becomes
     // lambda' (state before the forcing); per-point scale gradients in pts
     if (rot) {

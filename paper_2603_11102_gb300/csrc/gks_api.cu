@@ -791,7 +791,9 @@ int adjoint_check(gks_grid *g)
     const Ctx &c = g->c;
     if (c.prec != GKS_FP64) return fail(g, GKS_ERR_STATE, "the adjoint needs a GKS_FP64 grid");
     if (!(c.dt_fixed > 0.0)) return fail(g, GKS_ERR_STATE, "the adjoint needs a fixed time step (dt_fixed > 0)");
-    if (!g->bodies.empty()) return fail(g, GKS_ERR_STATE, "the adjoint does not cover immersed bodies");
+    for (const BodyDev &b : g->bodies)
+        if (b.tol > 0.0)
+            return fail(g, GKS_ERR_STATE, "the adjoint covers immersed bodies with a fixed iteration count (tol = 0)");
     if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
     if (!g->rotors.empty() && g->rotors[0].correction)
         return fail(g, GKS_ERR_STATE, "the adjoint does not cover the ALM velocity correction");
@@ -860,7 +862,7 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     // reverse
     cc.state = w.lamP;
     launch_scatter_state(cc, d_adj_np1);
-    adjoint_reverse(cc, w, rot, power_seed, dt, t_n + dt);
+    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt);
     cc.state = w.lamW;
     launch_gather_state(cc, d_adj_n);
     rc = check_launch(g, "adjoint step");

@@ -139,8 +139,9 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
 // Runs the reverse of one step whose forward quantities were recomputed into
 // w (A0, W* in c.wk1, Wp, rotor loads, the face boxes of both stages in
 // w.fqs); accumulates into grad (per point) and w.scal[0].
-void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, double power_seed, double dt,
-                     double t_np1);
+struct BodyDev;
+void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
+                     double power_seed, double dt, double t_np1);
 
 // Immersed body (gks_forcing.cu).
 struct BodyDev {

@@ -5,7 +5,8 @@ forward step equals <lambda^n, dW^n> (+ the force-scale, inflow-speed and
 power-seed terms) from gks_step_adjoint. Rollout: the checkpointed
 torch.autograd.Function gives the gradient of the wake-deficit plus power
 objective that central differences (h = 1e-6, FP64) of the CUDA forward and
-of the CPU oracle give."""
+of the CPU oracle give. The same with an immersed body (fixed IBM iteration
+count) next to the rotor."""
 import numpy as np
 import pytest
 
@@ -37,6 +38,16 @@ def rotor_box_workload(n=(24, 16, 16), n_pts=6, uinf=1.0):
     Q[0], Q[1] = 1.0, uinf
     return WL.Workload("adjoint-rotor", n, faces, 0.1, 1.0, 2e-3, [(3, 4), (0, 0), (2, 2)], cfl=0.9, dt_fixed=dt,
                        inflow=(1.0, uinf, 0.0, 0.0), state0=Q, rotors=[rot])
+
+
+def rotor_body_workload():
+    """The rotor box plus a cylinder (axis z, behind the rotor) forced by IBM
+    with a fixed iteration count."""
+    w = rotor_box_workload()
+    dx = 3.0 / w.n[0]
+    xyz, dS = WL.cylinder_points((0.4, 0.1, 0.0), 2, 0.12, -0.8, 0.2, 0.09, caps=False)
+    w.bodies = [WL.Body(xyz, dS, 2 * dx, niter=4, tol=0.0)]
+    return w
 
 
 def walls_workload(n=(20, 12, 10)):
@@ -73,17 +84,17 @@ def forward_step(g, torch, W, t_n, scales=None, uinf=None):
     return out, P
 
 
-@pytest.mark.parametrize("case", ["rotor", "walls"])
+@pytest.mark.parametrize("case", ["rotor", "walls", "rotor_body"])
 def test_one_step_adjoint_matches_central_differences(mods, case):
     gks, adjoint, torch = mods
-    w = rotor_box_workload() if case == "rotor" else walls_workload()
+    w = {"rotor": rotor_box_workload, "walls": walls_workload, "rotor_body": rotor_body_workload}[case]()
     g = gks.Grid.from_workload(w, precision="fp64")
     W = torch.tensor(perturbed_state(w, 3), dtype=torch.float64, device="cuda")
     rng = np.random.default_rng(5)
     lam1 = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
-    beta = 0.7 if case == "rotor" else 0.0
+    beta = 0.0 if case == "walls" else 0.7
     t_n = 0.37
-    npts = 3 * 6 if case == "rotor" else 0
+    npts = 0 if case == "walls" else 3 * 6
     s0 = np.ones(max(npts, 1))
     u0 = w.inflow[1]
 
@@ -121,7 +132,7 @@ def test_one_step_adjoint_matches_central_differences(mods, case):
 
 def oracle_objective(w, s, u, nsteps, iplane, beta):
     w = WL.Workload(w.name, w.n, w.faces, w.mach, w.u_ref, w.mu, w.bc, cfl=w.cfl, dt_fixed=w.dt_fixed,
-                    inflow=(1.0, u, 0.0, 0.0), state0=None, rotors=w.rotors)
+                    inflow=(1.0, u, 0.0, 0.0), state0=None, rotors=w.rotors, bodies=w.bodies)
     Q = np.zeros((4,) + w.n[::-1])
     Q[0], Q[1] = 1.0, u
     o = oracle_from_workload(w, Q)
@@ -131,9 +142,10 @@ def oracle_objective(w, s, u, nsteps, iplane, beta):
     return float(np.mean(u - A[1, :, :, iplane] / A[0, :, :, iplane])) + beta * o.forces(0)["power"]
 
 
-def test_rollout_gradient_vs_finite_differences_and_oracle(mods):
+@pytest.mark.parametrize("case", ["rotor", "rotor_body"])
+def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case):
     gks, adjoint, torch = mods
-    w = rotor_box_workload()
+    w = rotor_box_workload() if case == "rotor" else rotor_body_workload()
     g = gks.Grid.from_workload(w, precision="fp64")
     N, K, beta = 6, 2, 1.0
     iplane = 20          # x index downstream of the rotor
@@ -169,6 +181,12 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods):
     fou = (oracle_objective(w, s0, 1.0 + h, N, iplane, beta) -
            oracle_objective(w, s0, 1.0 - h, N, iplane, beta)) / (2 * h)
     assert abs(fou - gu) <= 1e-4 * abs(gu), (fou, gu)
+    if w.bodies:
+        # the body acts on the objective (the case is not the rotor case again)
+        J1 = oracle_objective(w, s0, 1.0, N, iplane, beta)
+        w0 = rotor_box_workload()
+        J0 = oracle_objective(w0, s0, 1.0, N, iplane, beta)
+        assert abs(J1 - J0) > 1e-6 * abs(J0), (J1, J0)
     g.close()
 
 
@@ -185,6 +203,12 @@ def test_adjoint_rejects_unsupported_grids(mods):
     g2 = gks.Grid.from_workload(rotor_box_workload(), precision="fp32c")
     with pytest.raises(gks.GKSError) as e:
         g2.step_adjoint(g2.adjoint_workspace(), 0.0, W, W)
+    assert e.value.code == -5
+    w4 = rotor_body_workload()
+    w4.bodies[0].tol = 0.05
+    g4 = gks.Grid.from_workload(w4, precision="fp64")
+    with pytest.raises(gks.GKSError) as e:
+        g4.step_adjoint(g4.adjoint_workspace(), 0.0, W, W)
     assert e.value.code == -5
     w3 = rotor_box_workload()
     w3.rotors[0].tip_correction = True

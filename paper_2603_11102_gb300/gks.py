@@ -147,6 +147,8 @@ class Grid:
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device")
         self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.n = tuple(int(x) for x in n)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._faces = [np.ascontiguousarray(f, dtype=np.float64) for f in faces]

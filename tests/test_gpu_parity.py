@@ -182,6 +182,33 @@ def test_free_stream_bitwise_and_determinism(gks, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_device_upload_on_a_copy_stream_matches_host_upload(gks, precision):
+    """The end-to-end pattern of the benchmark: the input state uploaded to a
+    device buffer on another stream, the grid's stream waits for it and
+    scatters it without a host synchronisation (set_state_tensor(sync=False));
+    the step gives the state a host upload gives."""
+    import torch
+    w = smooth_workload((33, 9, 17), [(0, 0)] * 3, seed=11)
+    g1 = gks.Grid.from_workload(w, precision=precision)
+    g1.set_state(w.state0)
+    g1.step(2)
+    g2 = gks.Grid.from_workload(w, precision=precision)
+    host = torch.from_numpy(np.ascontiguousarray(w.state0)).pin_memory()
+    dev = torch.empty(host.shape, dtype=torch.float64, device=g2.device)
+    cs = torch.cuda.Stream(g2.device)
+    ev = torch.cuda.Event()
+    with torch.cuda.stream(cs):
+        dev.copy_(host, non_blocking=True)
+        ev.record(cs)
+    g2.stream.wait_event(ev)
+    g2.set_state_tensor(dev, sync=False)
+    g2.step(2)
+    assert np.array_equal(g1.get_state(), g2.get_state())
+    with pytest.raises(ValueError):
+        g2.set_state_tensor(dev.float(), sync=False)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_checkpoint_restart_is_bitwise(gks, precision):
     w = smooth_workload((20, 12, 10), [(0, 0)] * 3, seed=5)
     g = gks.Grid.from_workload(w, precision=precision)

@@ -744,37 +744,52 @@ __global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
     }
 }
 
-// Reverse of the trilinear sampling, points in order (one thread: a few
-// hundred points x 8 corners; deterministic accumulation).
-__global__ void alm_sample_adj_kernel(AlmAdjArgs A)
+// Reverse of the trilinear sampling. One thread per point forms the
+// adjoints its 8 corner cells receive (cell index and 4 values per corner,
+// zero weight -> index -1) in ptc/ptl; one thread then adds them in point
+// and corner order (deterministic; points can share cells).
+__global__ void __launch_bounds__(256) alm_sample_adj_kernel(AlmAdjArgs A, double *ptc, long *ptl)
 {
     const RotorDev &r = A.r;
     const int npts = r.nb * r.np;
-    for (int q = 0; q < npts; ++q) {
-        const int b = q / r.np, p = q - b * r.np;
-        const double th = r.az0 + r.omega * A.t + 2.0 * kPi * b / r.nb;
-        const double rr = r.r[p];
-        const double X[3] = {r.hub[0], r.hub[1] + rr * cos(th), r.hub[2] + rr * sin(th)};
-        int i0[3];
-        double fr[3];
-        if (!trilinear_w(A, X, i0, fr)) continue;
-        const double Ub[3] = {A.pts[8 * q + 3], A.pts[8 * q + 4], A.pts[8 * q + 5]};
-        for (int c = 0; c < 8; ++c) {
-            const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
-            const double w = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1]) * (dk ? fr[2] : 1.0 - fr[2]);
-            if (w == 0.0) continue;
-            const int ii = A.n[0] == 1 ? 0 : i0[0] + di, jj = A.n[1] == 1 ? 0 : i0[1] + dj;
-            const int kk = A.n[2] == 1 ? 0 : i0[2] + dk;
-            const long l = lin(A.P[0], A.P[1], ii, jj, kk);
-            const double rho = A.Wp[l];
-            double dot = 0.0;
-            for (int v = 0; v < 3; ++v) {
-                A.lam[(1 + v) * A.np + l] += w * Ub[v] / rho;
-                dot += Ub[v] * A.Wp[(1 + v) * A.np + l];
-            }
-            A.lam[l] -= w * dot / (rho * rho);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npts) return;
+    for (int c = 0; c < 8; ++c) ptl[8 * q + c] = -1;
+    const int b = q / r.np, p = q - b * r.np;
+    const double th = r.az0 + r.omega * A.t + 2.0 * kPi * b / r.nb;
+    const double rr = r.r[p];
+    const double X[3] = {r.hub[0], r.hub[1] + rr * cos(th), r.hub[2] + rr * sin(th)};
+    int i0[3];
+    double fr[3];
+    if (!trilinear_w(A, X, i0, fr)) return;
+    const double Ub[3] = {A.pts[8 * q + 3], A.pts[8 * q + 4], A.pts[8 * q + 5]};
+    for (int c = 0; c < 8; ++c) {
+        const int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        const double w = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1]) * (dk ? fr[2] : 1.0 - fr[2]);
+        if (w == 0.0) continue;
+        const int ii = A.n[0] == 1 ? 0 : i0[0] + di, jj = A.n[1] == 1 ? 0 : i0[1] + dj;
+        const int kk = A.n[2] == 1 ? 0 : i0[2] + dk;
+        const long l = lin(A.P[0], A.P[1], ii, jj, kk);
+        const double rho = A.Wp[l];
+        double dot = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            ptc[32 * q + 4 * c + 1 + v] = w * Ub[v] / rho;
+            dot += Ub[v] * A.Wp[(1 + v) * A.np + l];
         }
+        ptc[32 * q + 4 * c] = -w * dot / (rho * rho);
+        ptl[8 * q + c] = l;
     }
+}
+
+__global__ void alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const long *ptl)
+{
+    const int npts = A.r.nb * A.r.np;
+    for (int q = 0; q < npts; ++q)
+        for (int c = 0; c < 8; ++c) {
+            const long l = ptl[8 * q + c];
+            if (l < 0) continue;
+            for (int v = 0; v < 4; ++v) A.lam[v * A.np + l] += ptc[32 * q + 4 * c + v];
+        }
 }
 
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
@@ -940,6 +955,8 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
     w->nuinf = 3 * 2 * G * maxsurf;
     w->uinf_part = take(w->nuinf);
     w->pts = take(8 * (npts_total > 0 ? npts_total : 1));
+    w->ptc = take(32 * (npts_total > 0 ? npts_total : 1));
+    w->ptl = take(8 * (npts_total > 0 ? npts_total : 1));
     w->scal = take(8);
     return o;
 }
@@ -981,7 +998,8 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
         const int npts = rot->nb * rot->np;
         alm_interp_adj_kernel<<<npts, 256, 0, c.stream>>>(A);
         alm_loads_adj_kernel<<<1, 256, 0, c.stream>>>(A);
-        alm_sample_adj_kernel<<<1, 1, 0, c.stream>>>(A);
+        alm_sample_adj_kernel<<<(npts + 255) / 256, 256, 0, c.stream>>>(A, w.ptc, (long *)w.ptl);
+        alm_sample_add_kernel<<<1, 1, 0, c.stream>>>(A, w.ptc, (const long *)w.ptl);
     }
     // stage 2: W' = P + dt^2/3 Lt(W*)
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,

@@ -132,6 +132,7 @@ struct AdjWork {
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;
     double *pts;                                          // per actuator point scratch (8 per point)
+    double *ptc, *ptl;                                    // sampling-adjoint corner values (32) and cells (8, as long)
     double *scal;                                         // [0] grad U_inf (device accumulator)
 };
 size_t adjoint_bytes(const Ctx &c, long npts_total);

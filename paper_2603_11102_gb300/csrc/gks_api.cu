@@ -39,6 +39,9 @@ struct gks_grid {
     double *d_diag = nullptr;
     long nstep = 0;
     bool stepped = false;
+    // the FP32 input (FP32C) and max |U|^2 of the current state are in place
+    // (left by the last step or state upload): the next step skips its prep
+    bool prep_valid = false;
 };
 
 namespace {
@@ -395,7 +398,8 @@ int gks_set_state(gks_grid *g, const double *h_state)
                                            cudaMemcpyHostToDevice, g->c.stream),
                         "copy state to device");
     if (rc) return rc;
-    launch_scatter_state(g->c, g->c.staging);
+    launch_scatter_state_prep(g->c, g->c.staging);
+    g->prep_valid = true;
     return check_launch(g, "scatter state");
 }
 
@@ -597,17 +601,33 @@ int gks_step(gks_grid *g, int nsteps, double *t_out)
     if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
     Ctx &c = g->c;
     g->stepped = true;
+    const int nobj = (int)g->obj_kind.size();
+    const bool fused_prep = nobj <= 8;
     for (int s = 0; s < nsteps; ++s) {
-        launch_prep(c);
+        if (!g->prep_valid) launch_prep(c);
         launch_ghost(c, c.wk0);
-        launch_cfl(c);
+        launch_cfl(c);   // dt from max |U|^2, which it clears
         launch_stage(c, 1);
         launch_ghost(c, c.wk1);
+        // stage 2 also prepares the next step on every cell outside the
+        // forcing boxes; the boxes are prepared again after the forcing
+        if (fused_prep) {
+            c.prep_next = 1;
+            c.nprep_box = nobj;
+            for (int k = 0; k < nobj; ++k) {
+                const int(*box)[2] = g->obj_kind[k] == 0 ? g->rotors[g->obj_index[k]].box : g->bodies[g->obj_index[k]].box;
+                memcpy(c.prep_box[k], box, sizeof(int) * 6);
+            }
+        }
         launch_stage(c, 2);
+        c.prep_next = 0;
         for (size_t k = 0; k < g->obj_kind.size(); ++k)
             if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
         for (size_t k = 0; k < g->obj_kind.size(); ++k)
             if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
+        if (fused_prep)
+            for (int k = 0; k < nobj; ++k) launch_prep_box(c, c.prep_box[k]);
+        g->prep_valid = fused_prep;
         launch_advance(c);
         int rc = check_launch(g, "step");
         if (rc) return rc;
@@ -755,6 +775,7 @@ int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes)
                         "copy checkpoint");
     if (rc) return rc;
     launch_raw_copy(g->c, g->c.staging, 0);
+    g->prep_valid = false;
     rc = check_launch(g, "scatter checkpoint");
     if (rc) return rc;
     rc = cuda_check(g, cudaMemcpyAsync(&g->c.scal->t, &h.t, sizeof(double), cudaMemcpyHostToDevice, g->c.stream),
@@ -767,7 +788,8 @@ int gks_load_state(gks_grid *g, const void *h_blob, size_t bytes)
 int gks_set_state_device(gks_grid *g, const double *d_state)
 {
     if (!g || !d_state) return fail(g, GKS_ERR_ARG, "null argument");
-    launch_scatter_state(g->c, d_state);
+    launch_scatter_state_prep(g->c, d_state);
+    g->prep_valid = true;
     return check_launch(g, "scatter state");
 }
 

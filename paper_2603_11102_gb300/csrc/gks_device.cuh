@@ -38,6 +38,38 @@ Phys<R> make_phys(const Ctx &c)
 __device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
 
+// |U|^2 of a cell for the CFL time step, with every operation rounded
+// explicitly so that each kernel that forms it gets the same bits: FP32C from
+// hi + lo in FP32, FP64 from the state. max_u2 keeps a NaN.
+__device__ __forceinline__ double cell_u2(const float h[4], const float l[4])
+{
+    const float r = __fadd_rn(h[0], l[0]), a = __fadd_rn(h[1], l[1]);
+    const float b = __fadd_rn(h[2], l[2]), c = __fadd_rn(h[3], l[3]);
+    const float m2 = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+    return (double)__fdiv_rn(m2, __fmul_rn(r, r));
+}
+__device__ __forceinline__ double cell_u2(const double w[4])
+{
+    const double m2 = __dadd_rn(__dadd_rn(__dmul_rn(w[1], w[1]), __dmul_rn(w[2], w[2])), __dmul_rn(w[3], w[3]));
+    return __ddiv_rn(m2, __dmul_rn(w[0], w[0]));
+}
+__device__ __forceinline__ double max_u2(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Block-wide max of v (blockDim.x * blockDim.y threads, a multiple of 32,
+// at most 1024) folded into *bits (a non-negative double) by one atomicMax.
+__device__ __forceinline__ void block_max_to(double v, unsigned long long *bits)
+{
+    __shared__ double red[32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nw = (blockDim.x * blockDim.y) >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = max_u2(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < nw; ++w) v = max_u2(v, red[w]);
+        atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
 // Direction d: normal axis d, tangential axes t1, t2.
 __host__ __device__ inline int tan1(int d) { return d == 0 ? 1 : 0; }
 __host__ __device__ inline int tan2(int d) { return d == 2 ? 1 : 2; }

@@ -68,6 +68,11 @@ struct Ctx {
     // slope, t2 slope x 4 components), written by the flux kernels.
     void *gp_dir[3] = {nullptr, nullptr, nullptr};
     long ngp = 0;
+    // Stage 2 of a step may prepare the next step (the FP32 input, max |U|^2
+    // outside the forcing boxes, which are redone after the forcing).
+    int prep_next = 0;
+    int nprep_box = 0;
+    int prep_box[8][3][2];
     void *ff[3];              // face-averaged F0 and F1 of x and y faces, R[8][nff] (none for z)
     long nff[3];
     void *ih[3];              // R: inverse cell widths, padded index i + 3
@@ -93,11 +98,13 @@ void record_error(const char *msg);
 
 // Launchers of the stencil path (gks_stencil.cu).
 void launch_prep(const Ctx &c);                        // max |U|^2 into scal; FP32C: state -> wk0
+void launch_prep_box(const Ctx &c, const int box[3][2]);   // the same over the interior cells of a box
 void launch_ghost(const Ctx &c, void *w);              // 3 ghost layers of w (working type)
 void launch_stage(const Ctx &c, int stage);            // face kernels + update
 void launch_cfl(const Ctx &c);                          // dt from max |U| (after launch_prep)
 void launch_advance(const Ctx &c);                      // t += dt
 void launch_scatter_state(const Ctx &c, const double *d_src);  // compact FP64 -> state
+void launch_scatter_state_prep(const Ctx &c, const double *d_src);   // + the prep of the new state
 void launch_gather_state(const Ctx &c, double *d_dst);         // state -> compact FP64
 void launch_diagnostics(const Ctx &c, double *d_out5);
 void launch_fill_rest(const Ctx &c);                            // rho = 1, momentum 0

@@ -417,6 +417,8 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
 
 // ------------------------------------------------- z flux + stage update --
 
+constexpr int kMaxPrepBoxes = 8;   // forcing boxes the fused prep can leave out
+
 template <typename R>
 struct UpdArgs {
     const R *ffx, *ffy;   // face fluxes of the x and y directions (8 arrays each)
@@ -431,6 +433,12 @@ struct UpdArgs {
     R off;
     R fb[3];
     int seg;          // z-faces per segment of the fused z kernel
+    // stage 2, optional: the next step's prep (FP32C: the FP32 input into
+    // wk0n; max |U|^2 over the cells outside the forcing boxes into scal)
+    int prep;
+    float *wk0n;
+    int nbox;
+    int box[kMaxPrepBoxes][3][2];
 };
 
 __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
@@ -454,7 +462,8 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
 // Returns false when a written value is not finite (stage 2).
 template <typename R, int STAGE>
 __device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, double dt, const R dx[], const R dy[],
-                                            const R dz[], R ihx, R ihy, R ihz, const R s0[4], const R s1[4])
+                                            const R dz[], R ihx, R ihy, R ihz, const R s0[4], const R s1[4],
+                                            R o0[4], R o1[4])
 {
     const R dtr = (R)dt;
     bool bad = false;
@@ -481,6 +490,7 @@ __device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, doubl
                 if (v > 0) w += dt * (double)A.fb[v - 1];
                 ((double *)A.state)[v * A.np + lin] = w;
                 bad |= !isfinite(w);
+                o0[v] = w;
             } else {
                 float hi = s0[v], lo = s1[v];
                 float inc = dtr * dtr * (1.0f / 3.0f) * Lt;
@@ -489,6 +499,8 @@ __device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, doubl
                 ((float *)A.state)[v * A.np + lin] = hi;
                 ((float *)A.state)[(4 + v) * A.np + lin] = lo;
                 bad |= !isfinite(hi) || !isfinite(lo);
+                o0[v] = hi;
+                o1[v] = lo;
             }
         }
     }
@@ -559,6 +571,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     }
     const double dt = A.scal->dt;
     bool bad = false;
+    double mx = 0.0;   // stage 2 with prep: max |U|^2 of this thread's cells outside the forcing boxes
     R P0[4], P1[4];   // F0, F1 of the previous face of this column
     for (int k = 0; cur.it < nitems; ++k) {
         const int buf = k & 1;
@@ -659,7 +672,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                     dz[4 + v] = F1[loc[v]] - P1[loc[v]];
                 }
                 const R ihx = __ldg(A.ih1 + a + G), ihy = __ldg(A.ih2 + b + G), ihz = __ldg(U.ihz + z + G);
-                bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ihx, ihy, ihz, s0, s1);
+                R o0[4], o1[4];
+                bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ihx, ihy, ihz, s0, s1, o0, o1);
+                if (STAGE == 2 && U.prep) {
+                    bool boxed = false;
+                    for (int q = 0; q < U.nbox; ++q)
+                        boxed |= a >= U.box[q][0][0] && a <= U.box[q][0][1] && b >= U.box[q][1][0] &&
+                                 b <= U.box[q][1][1] && z >= U.box[q][2][0] && z <= U.box[q][2][1];
+                    if constexpr (std::is_same<R, double>::value) {
+                        if (!boxed) mx = max_u2(mx, cell_u2(o0));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) U.wk0n[v * U.np + lin] = (o0[v] - (v == 0 ? U.off : 0.0f)) + o1[v];
+                        if (!boxed) mx = max_u2(mx, cell_u2(o0, o1));
+                    }
+                }
             }
         }
         if (in) {
@@ -673,6 +700,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         __syncthreads();   // st, the face buffer and the x slab are free again
     }
     if (STAGE == 2 && bad) atomicOr(&A.scal->flags, FLAG_NONFINITE);
+    if (STAGE == 2 && U.prep) block_max_to(mx, &A.scal->maxu2_bits);
 }
 
 // Resident blocks per SM x SMs for a persistent kernel with `smem` bytes of
@@ -801,6 +829,12 @@ void stage_impl(const Ctx &c)
             for (int a = 0; a < 3; ++a) U.fb[a] = (R)c.fbody[a];
             const int ncol = ((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY);
             U.seg = z_segment(ncol, F.nf, grids.flux_update);
+            U.prep = STAGE == 2 && c.prep_next && c.nprep_box <= kMaxPrepBoxes;
+            U.wk0n = c.prec == GKS_FP32C ? (float *)c.wk0 : nullptr;
+            U.nbox = U.prep ? c.nprep_box : 0;
+            for (int q = 0; q < U.nbox; ++q)
+                for (int e = 0; e < 3; ++e)
+                    for (int f2 = 0; f2 < 2; ++f2) U.box[q][e][f2] = c.prep_box[q][e][f2];
             const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
             const int grid = (int)(nitems < grids.flux_update ? nitems : grids.flux_update);
             flux_update_kernel<R, STAGE><<<grid, blk, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4), c.stream>>>(
@@ -814,29 +848,26 @@ void stage_impl(const Ctx &c)
 
 constexpr int kPrepZ = 8;   // z planes per block of the prep / CFL kernel
 
-// max(a, b) that keeps a NaN (so that a non-finite state reaches dt).
-__device__ __forceinline__ double max_nan(double a, double b) { return (b > a || b != b) ? b : a; }
-
 // Start of a step: the largest |U|^2 over the interior cells (for the CFL
-// time step), and for FP32C the FP32 reconstruction input hi + lo (density
-// as rho - off). One atomicMax per block.
+// time step) and, for FP32C, the FP32 reconstruction input hi + lo (density
+// as rho - off), over the interior cells [lo, hi) of a box (the whole
+// interior, or a forcing box after the forcing). One atomicMax per block.
 template <int PREC>
 __global__ void __launch_bounds__(256) prep_cfl_kernel(const void *__restrict__ S, float *__restrict__ wk, long np,
-                                                       int nx, int ny, int nz, int P0, int P1, float off,
-                                                       Scalars *scal)
+                                                       int3 lo, int3 hi, int P0, int P1, float off, Scalars *scal)
 {
-    __shared__ double red[8];
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-    const int k0 = blockIdx.z * kPrepZ, k1 = min(k0 + kPrepZ, nz);
+    const int i = lo.x + blockIdx.x * 32 + threadIdx.x, j = lo.y + blockIdx.y * 8 + threadIdx.y;
+    const int k0 = lo.z + blockIdx.z * kPrepZ, k1 = min(k0 + kPrepZ, hi.z);
     double mx = 0.0;
-    if (i < nx && j < ny) {
+    if (i < hi.x && j < hi.y) {
         for (int k = k0; k < k1; ++k) {
             const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
-            double u2;
             if (PREC == GKS_FP64) {
                 const double *__restrict__ W = (const double *)S;
-                const double r = W[lin], a = W[np + lin], b = W[2 * np + lin], c = W[3 * np + lin];
-                u2 = (a * a + b * b + c * c) / (r * r);
+                double w[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) w[v] = W[v * np + lin];
+                mx = max_u2(mx, cell_u2(w));
             } else {
                 const float *__restrict__ W = (const float *)S;
                 float h[4], l[4];
@@ -847,20 +878,11 @@ __global__ void __launch_bounds__(256) prep_cfl_kernel(const void *__restrict__ 
                 }
 #pragma unroll
                 for (int v = 0; v < 4; ++v) wk[v * np + lin] = (h[v] - (v == 0 ? off : 0.0f)) + l[v];
-                // the time step needs no more than FP32 hi + lo
-                const float r = h[0] + l[0], a = h[1] + l[1], b = h[2] + l[2], c = h[3] + l[3];
-                u2 = (double)((a * a + b * b + c * c) / (r * r));
+                mx = max_u2(mx, cell_u2(h, l));
             }
-            mx = max_nan(mx, u2);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = max_nan(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) red[threadIdx.y] = mx;
-    __syncthreads();
-    if (threadIdx.y == 0 && threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) mx = max_nan(mx, red[w]);
-        atomicMax(&scal->maxu2_bits, (unsigned long long)__double_as_longlong(mx));
-    }
+    block_max_to(mx, &scal->maxu2_bits);
 }
 
 __device__ __forceinline__ void load_cell(int prec, const void *S, long np, long lin, double q[4])
@@ -896,25 +918,49 @@ __global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmi
 
 __global__ void advance_kernel(Scalars *scal) { scal->t = scal->t + scal->dt; }
 
-__global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *src, void *S, long np,
-                                                      int nx, int ny, int nz, int P0, int P1)
+// Compact FP64 state -> the padded state (FP32C: hi = fl32(q), lo =
+// fl32(q - hi)), kPrepZ planes per block. With scal set it also does the
+// work of prep_cfl on the new state (FP32 input into wk for FP32C, max
+// |U|^2 into scal).
+__global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__restrict__ src, void *S, long np,
+                                                      int nx, int ny, int nz, int P0, int P1, float *wk, float off,
+                                                      Scalars *scal)
 {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-    if (i >= nx || j >= ny) return;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * kPrepZ, k1 = min(k0 + kPrepZ, nz);
     const long N = (long)nx * ny * nz;
-    const long ci = i + (long)nx * (j + (long)ny * k);
-    const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+    double mx = 0.0;
+    if (i < nx && j < ny) {
+        for (int k = k0; k < k1; ++k) {
+            const long ci = i + (long)nx * (j + (long)ny * k);
+            const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
+            double q[4];
+            float h[4], l[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const double q = src[v * N + ci];
-        if (prec == GKS_FP64) {
-            ((double *)S)[v * np + lin] = q;
-        } else {
-            const float hi = (float)q;
-            ((float *)S)[v * np + lin] = hi;
-            ((float *)S)[(4 + v) * np + lin] = (float)(q - (double)hi);
+            for (int v = 0; v < 4; ++v) q[v] = src[v * N + ci];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (prec == GKS_FP64) {
+                    ((double *)S)[v * np + lin] = q[v];
+                } else {
+                    h[v] = (float)q[v];
+                    l[v] = (float)(q[v] - (double)h[v]);
+                    ((float *)S)[v * np + lin] = h[v];
+                    ((float *)S)[(4 + v) * np + lin] = l[v];
+                }
+            }
+            if (scal) {
+                if (prec == GKS_FP64) {
+                    mx = max_u2(mx, cell_u2(q));
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) wk[v * np + lin] = (h[v] - (v == 0 ? off : 0.0f)) + l[v];
+                    mx = max_u2(mx, cell_u2(h, l));
+                }
+            }
         }
     }
+    if (scal) block_max_to(mx, &scal->maxu2_bits);
 }
 
 __global__ void __launch_bounds__(256) gather_kernel(int prec, const void *S, double *dst, long np,
@@ -1028,18 +1074,27 @@ int reduce_blocks(long ncell)
 
 }  // namespace
 
-void launch_prep(const Ctx &c)
+void launch_prep_box(const Ctx &c, const int box[3][2])
 {
-    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, (c.n[2] + kPrepZ - 1) / kPrepZ);
+    const int3 lo = make_int3(box[0][0], box[1][0], box[2][0]);
+    const int3 hi = make_int3(box[0][1] + 1, box[1][1] + 1, box[2][1] + 1);
+    if (hi.x <= lo.x || hi.y <= lo.y || hi.z <= lo.z) return;
+    dim3 blk(32, 8), g((hi.x - lo.x + 31) / 32, (hi.y - lo.y + 7) / 8, (hi.z - lo.z + kPrepZ - 1) / kPrepZ);
     const int grp = c.prec == GKS_FP32C ? K_PREP : K_CFL;
     mark(c, grp, 1);
     if (c.prec == GKS_FP32C)
-        prep_cfl_kernel<GKS_FP32C><<<g, blk, 0, c.stream>>>(c.state, (float *)c.wk0, c.np, c.n[0], c.n[1], c.n[2],
-                                                           c.P[0], c.P[1], (float)c.off, c.scal);
+        prep_cfl_kernel<GKS_FP32C><<<g, blk, 0, c.stream>>>(c.state, (float *)c.wk0, c.np, lo, hi, c.P[0], c.P[1],
+                                                           (float)c.off, c.scal);
     else
-        prep_cfl_kernel<GKS_FP64><<<g, blk, 0, c.stream>>>(c.state, nullptr, c.np, c.n[0], c.n[1], c.n[2], c.P[0],
-                                                          c.P[1], 0.0f, c.scal);
+        prep_cfl_kernel<GKS_FP64><<<g, blk, 0, c.stream>>>(c.state, nullptr, c.np, lo, hi, c.P[0], c.P[1], 0.0f,
+                                                          c.scal);
     mark(c, grp, 0);
+}
+
+void launch_prep(const Ctx &c)
+{
+    const int box[3][2] = {{0, c.n[0] - 1}, {0, c.n[1] - 1}, {0, c.n[2] - 1}};
+    launch_prep_box(c, box);
 }
 
 void launch_ghost(const Ctx &c, void *w)
@@ -1074,9 +1129,17 @@ void launch_advance(const Ctx &c)
 
 void launch_scatter_state(const Ctx &c, const double *d_src)
 {
-    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
-    scatter_kernel<<<g, blk, 0, c.stream>>>(c.prec, d_src, c.state, c.np, c.n[0], c.n[1], c.n[2],
-                                            c.P[0], c.P[1]);
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, (c.n[2] + kPrepZ - 1) / kPrepZ);
+    scatter_kernel<<<g, blk, 0, c.stream>>>(c.prec, d_src, c.state, c.np, c.n[0], c.n[1], c.n[2], c.P[0], c.P[1],
+                                            nullptr, 0.0f, nullptr);
+}
+
+void launch_scatter_state_prep(const Ctx &c, const double *d_src)
+{
+    cudaMemsetAsync(&c.scal->maxu2_bits, 0, sizeof(unsigned long long), c.stream);
+    dim3 blk(32, 8), g((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, (c.n[2] + kPrepZ - 1) / kPrepZ);
+    scatter_kernel<<<g, blk, 0, c.stream>>>(c.prec, d_src, c.state, c.np, c.n[0], c.n[1], c.n[2], c.P[0], c.P[1],
+                                            c.prec == GKS_FP32C ? (float *)c.wk0 : nullptr, (float)c.off, c.scal);
 }
 
 void launch_gather_state(const Ctx &c, double *d_dst)

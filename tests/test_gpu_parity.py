@@ -146,6 +146,32 @@ def test_actuator_lines_and_immersed_bodies(gks, precision):
         assert abs(fg["residual"] - fo["residual"]) <= tol * max(abs(fo["residual"]), 1e-12)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_cfl_step_after_forcing_uses_the_forced_state(gks, precision):
+    """Stage 2 prepares the next step outside the forcing boxes and the boxes
+    are prepared again after the forcing: each CFL step is the one of the
+    state the previous step (with its forcing) or an upload left, checked
+    against numpy on that state. The uploaded state has its fastest cells at
+    the hub, inside the rotor box."""
+    w = small_rotor_workload(ibm=True, n=(72, 32, 32))
+    g = gks.Grid.from_workload(w, precision=precision)
+    Q = w.state0.copy()
+    Q[1, 14:18, 14:18, 16:20] *= 1.6
+    g.set_state(Q)
+    hmin = min(np.min(np.diff(f)) for f in w.faces)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    for k in range(3):
+        Q = g.get_state()
+        u2 = (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0] ** 2
+        if k < 2:
+            kk, jj, ii = np.unravel_index(np.argmax(u2), u2.shape)   # the spot, inside the rotor box
+            assert 12 <= kk <= 19 and 12 <= jj <= 19 and 14 <= ii <= 21, (k, kk, jj, ii)
+        g.step(1)
+        ref = w.cfl * hmin / (np.sqrt(np.max(u2)) + 1.0 / w.mach)
+        assert abs(g.last_dt - ref) <= tol * ref, (k, g.last_dt, ref)
+    g.close()
+
+
 def test_ibm_tolerance_mode(gks):
     w = small_rotor_workload(ibm=True, n=(72, 32, 32))
     w.rotors = []

@@ -215,11 +215,11 @@ __device__ __forceinline__ void equilibrium_rev(const Phys<double> &ph, const do
     const double rl = off + Ql[0], rr = off + Qr[0];
     const double irl = 1.0 / rl, irr = 1.0 / rr;
     const double Ul = Ql[1] * irl, Ur = Qr[1] * irr;
-    const double zl = ph.sqlam * Ul, zr = ph.sqlam * Ur;
-    const double el = erf(zl), er = erf(zr);
+    // erf(z) and exp(-z^2) with z = sqrt(lambda) U, as in the forward
+    double el, er, ml, mr, exl, exr;
+    half_space_terms(ph.sqlam * Ul, el, ml, exl);
+    half_space_terms(ph.sqlam * Ur, er, mr, exr);
     const double Pl = 0.5 + 0.5 * el, Pr = 0.5 - 0.5 * er;
-    const double xl = -ph.lambda * Ul * Ul, xr = -ph.lambda * Ur * Ur;
-    const double exl = exp(xl), exr = exp(xr);
     const double El = ph.kE * exl, Er = ph.kE * exr;
     double Plb = 0.0, Prb = 0.0;
     for (int v = 0; v < 4; ++v) {

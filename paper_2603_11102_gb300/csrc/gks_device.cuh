@@ -116,18 +116,54 @@ __device__ __forceinline__ void weno5_pair(const R q[5], R &right, R &left)
 }
 
 // erf(z), exp(-z^2) - 1 and exp(-z^2) of the half-space moments, z =
-// sqrt(lambda) U. FP64: the library functions. FP32: for |z| <= 1/2 (|U| up to
-// 7 U_ref at Ma 0.1) the Maclaurin series
-//   erf z = (2/sqrt pi) sum_n (-1)^n z^(2n+1) / (n! (2n+1)),  n = 0..6,
-//   expm1 x = sum_n x^n / n!,                                 n = 1..7,
-// whose first dropped terms are below 4e-10 and 2e-9 relative, so that the
-// FP32 evaluation is within 2e-7 relative of the exact values; beyond 1/2 the
-// library functions.
+// sqrt(lambda) U. For |z| <= 1/2 (|U| up to 7 U_ref at Ma 0.1) the Maclaurin
+// series
+//   erf z = (2/sqrt pi) sum_n (-1)^n z^(2n+1) / (n! (2n+1)),
+//   expm1 x = sum_n x^n / n!,
+// FP32: n = 0..6 and 1..7 (first dropped terms below 4e-10 and 2e-9
+// relative; within 2e-7 of the exact values after rounding); FP64: n = 0..12
+// and 1..13 (dropped terms below 1e-17; within 3e-16 of libm); exp = 1 +
+// expm1. Beyond 1/2 the library functions.
 __device__ __forceinline__ void half_space_terms(double z, double &e, double &m1, double &ex)
 {
-    e = erf(z);
-    m1 = expm1(-z * z);
-    ex = exp(-z * z);
+    const double t = z * z, x = -t;
+    if (fabs(z) <= 0.5) {
+        constexpr double k = 1.1283791670955126;   // 2 / sqrt(pi)
+        // c_n = k (-1)^n / (n! (2n+1))
+        double p = k / (479001600.0 * 25.0);
+        p = fma(p, t, -k / (39916800.0 * 23.0));
+        p = fma(p, t, k / (3628800.0 * 21.0));
+        p = fma(p, t, -k / (362880.0 * 19.0));
+        p = fma(p, t, k / (40320.0 * 17.0));
+        p = fma(p, t, -k / (5040.0 * 15.0));
+        p = fma(p, t, k / (720.0 * 13.0));
+        p = fma(p, t, -k / (120.0 * 11.0));
+        p = fma(p, t, k / (24.0 * 9.0));
+        p = fma(p, t, -k / (6.0 * 7.0));
+        p = fma(p, t, k / (2.0 * 5.0));
+        p = fma(p, t, -k / 3.0);
+        p = fma(p, t, k);
+        e = p * z;
+        double q = 1.0 / 6227020800.0;   // 1/13!
+        q = fma(q, x, 1.0 / 479001600.0);
+        q = fma(q, x, 1.0 / 39916800.0);
+        q = fma(q, x, 1.0 / 3628800.0);
+        q = fma(q, x, 1.0 / 362880.0);
+        q = fma(q, x, 1.0 / 40320.0);
+        q = fma(q, x, 1.0 / 5040.0);
+        q = fma(q, x, 1.0 / 720.0);
+        q = fma(q, x, 1.0 / 120.0);
+        q = fma(q, x, 1.0 / 24.0);
+        q = fma(q, x, 1.0 / 6.0);
+        q = fma(q, x, 0.5);
+        q = fma(q, x, 1.0);
+        m1 = q * x;
+        ex = 1.0 + m1;
+    } else {
+        e = erf(z);
+        m1 = expm1(x);
+        ex = exp(x);
+    }
 }
 __device__ __forceinline__ void half_space_terms(float z, float &e, float &m1, float &ex)
 {

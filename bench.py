@@ -252,7 +252,8 @@ def adjoint_workload(n=(256, 128, 128)):
 def time_adjoint(args, dev):
     """Forward and checkpointed adjoint of the wake-deficit plus power
     objective; ratio = backward time (segment recomputation included) over
-    the forward time of the same steps."""
+    the forward time of the same steps, with FP32 arithmetic in the local
+    reverse maps (the FD-checked default of this benchmark) and with FP64."""
     import torch
 
     from paper_2603_11102_gb300 import adjoint, gks
@@ -260,29 +261,36 @@ def time_adjoint(args, dev):
     g = gks.Grid.from_workload(w, precision="fp64", device=dev)
     iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
     npts = w.rotors[0].n_blades * len(w.rotors[0].r)
-    # untimed warm-up: one checkpoint segment forward and backward (first
-    # kernel launches, the adjoint workspace)
-    sw = torch.ones(npts, dtype=torch.float64, requires_grad=True)
-    uw = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    adjoint.rotor_objective(g, sw, uw, args.adjoint_k, K=args.adjoint_k, iplane=iplane, beta=1.0).backward()
-    s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
-    u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    J = adjoint.rotor_objective(g, s, u, args.adjoint_steps, K=args.adjoint_k, iplane=iplane, beta=1.0)
-    torch.cuda.synchronize(dev)
-    t1 = time.perf_counter()
-    J.backward()
-    torch.cuda.synchronize(dev)
-    t2 = time.perf_counter()
+
+    def run(steps):
+        s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+        u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        J = adjoint.rotor_objective(g, s, u, steps, K=args.adjoint_k, iplane=iplane, beta=1.0)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, float(u.grad)
+
+    out = {}
+    for rev in ("fp32", "fp64"):
+        g.set_adjoint_precision(rev)
+        run(args.adjoint_k)   # untimed warm-up segment (first launches, the workspace)
+        out[rev] = run(args.adjoint_steps)
     g.close()
-    fwd, bwd = t1 - t0, t2 - t1
+    fwd, bwd, gu = out["fp32"]
+    fwd64, bwd64, gu64 = out["fp64"]
     return {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
             "warmup": "one untimed segment of %d steps, forward and backward" % args.adjoint_k,
+            "reverse_arithmetic": "fp32 (FP64 recompute, storage and sums)",
             "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
             "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
+            "ratio_fp64_reverse": bwd64 / fwd64, "backward_s_fp64_reverse": bwd64,
             "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
-                         % npts, "grad_uinf": float(u.grad)}
+                         % npts, "grad_uinf": gu, "grad_uinf_fp64_reverse": gu64}
 
 
 def run_ours(args, world, rank, local):

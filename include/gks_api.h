@@ -255,6 +255,14 @@ int gks_get_state_device(gks_grid *g, double *d_state);
  * otherwise), and fewer than 2^31 / 64 faces per direction (GKS_ERR_ARG
  * otherwise). Synchronises the stream. */
 int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes);
+/* Arithmetic of the local reverse maps of gks_step_adjoint (the reverse of
+ * the Gauss-point flux, of the WENO5 pair, equilibrium state and normal slope,
+ * and the transposed tangential passes): GKS_FP64 (default) or GKS_FP32C for
+ * FP32 arithmetic. Either way the forward step is recomputed in FP64, the
+ * adjoints are stored and summed in FP64, and WENO5 stencils enter FP32 as
+ * differences from their centre cell. GB300 runs FP32 at about 64x the FP64
+ * rate. Returns GKS_ERR_ARG for another value. */
+int gks_set_adjoint_precision(gks_grid *g, int precision);
 int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n,
                      const double *d_adj_np1, double *d_adj_n, double power_seed,
                      double *h_grad_scales, double *h_grad_uinf);

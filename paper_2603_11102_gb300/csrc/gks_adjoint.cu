@@ -60,42 +60,43 @@ __device__ __forceinline__ long lin(const int P0, const int P1, int i, int j, in
 
 // Adjoint of dev::gk_flux: given the adjoints of F0 (if needF0) and F1,
 // accumulate the adjoints of its inputs (index-space tangential slopes).
-__device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const double Dn[4], const double D1[4],
-                            const double D2[4], double ih1, double ih2, const double lF0[4], const double lF1[4],
-                            bool needF0, double qb[4], double Dnb[4], double D1b[4], double D2b[4])
+template <typename T>
+__device__ __forceinline__ void gk_flux_rev(const Phys<T> &ph, const T q[4], const T Dn[4], const T D1[4],
+                                            const T D2[4], T ih1, T ih2, const T lF0[4], const T lF1[4],
+                                            bool needF0, T qb[4], T Dnb[4], T D1b[4], T D2b[4])
 {
-    const double rho = ph.off + q[0];
-    const double inv = 1.0 / rho;
-    const double invi[3] = {inv, inv * ih1, inv * ih2};
-    const double *D[3] = {Dn, D1, D2};
-    const double U[3] = {q[1] * inv, q[2] * inv, q[3] * inv};
-    double g[3], Gm[3][3];
+    const T rho = ph.off + q[0];
+    const T inv = T(1.0) / rho;
+    const T invi[3] = {inv, inv * ih1, inv * ih2};
+    const T *D[3] = {Dn, D1, D2};
+    const T U[3] = {q[1] * inv, q[2] * inv, q[3] * inv};
+    T g[3], Gm[3][3];
     for (int i = 0; i < 3; ++i) {
         g[i] = D[i][0] * invi[i];
         for (int j = 0; j < 3; ++j) Gm[i][j] = (D[i][j + 1] - U[j] * D[i][0]) * invi[i];
     }
-    const double th = ph.theta, tl = 2.0 * ph.lambda, mu = ph.mu;
-    const double A0 = -(U[0] * g[0] + U[1] * g[1] + U[2] * g[2]) - (Gm[0][0] + Gm[1][1] + Gm[2][2]);
-    double A[3];
+    const T th = ph.theta, tl = T(2.0) * ph.lambda, mu = ph.mu;
+    const T A0 = -(U[0] * g[0] + U[1] * g[1] + U[2] * g[2]) - (Gm[0][0] + Gm[1][1] + Gm[2][2]);
+    T A[3];
     for (int k = 0; k < 3; ++k) A[k] = -g[k] - tl * (U[0] * Gm[0][k] + U[1] * Gm[1][k] + U[2] * Gm[2][k]);
 
-    double rhob = 0.0, Ub[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, Gb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double A0b = 0.0, Ab[3] = {0, 0, 0}, qd[4] = {0, 0, 0, 0};
+    T rhob = T(0.0), Ub[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, Gb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    T A0b = T(0.0), Ab[3] = {0, 0, 0}, qd[4] = {0, 0, 0, 0};
     // F1[0] = rho (A0 U0 + th A_0)
     {
-        const double T0 = A0 * U[0] + th * A[0];
+        const T T0 = A0 * U[0] + th * A[0];
         rhob += lF1[0] * T0;
-        const double T0b = lF1[0] * rho;
+        const T T0b = lF1[0] * rho;
         A0b += T0b * U[0];
         Ub[0] += T0b * A0;
         Ab[0] += T0b * th;
     }
     // F1[1+k] = rho (A0 (U0 U_k + th d_k0) + th (A_k U0 + A_0 U_k))
     for (int k = 0; k < 3; ++k) {
-        const double c = U[0] * U[k] + (k == 0 ? th : 0.0);
-        const double Tk = A0 * c + th * (A[k] * U[0] + A[0] * U[k]);
+        const T c = U[0] * U[k] + (k == 0 ? th : T(0.0));
+        const T Tk = A0 * c + th * (A[k] * U[0] + A[0] * U[k]);
         rhob += lF1[1 + k] * Tk;
-        const double Tb = lF1[1 + k] * rho;
+        const T Tb = lF1[1 + k] * rho;
         A0b += Tb * c;
         Ub[0] += Tb * A0 * U[k];
         Ub[k] += Tb * A0 * U[0];
@@ -109,7 +110,7 @@ __device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const dou
         qd[1] += lF0[1] * U[0];
         Ub[0] += lF0[1] * q[1];
         qd[0] += lF0[1] * th;
-        Gb[0][0] += -2.0 * mu * lF0[1];
+        Gb[0][0] += -T(2.0) * mu * lF0[1];
         for (int k = 1; k < 3; ++k) {
             qd[1] += lF0[1 + k] * U[k];
             Ub[k] += lF0[1 + k] * q[1];
@@ -131,8 +132,8 @@ __device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const dou
         gb[i] -= A0b * U[i];
         Gb[i][i] -= A0b;
     }
-    double Db[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    double invb[3] = {0, 0, 0};
+    T Db[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    T invb[3] = {0, 0, 0};
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) {
             Db[i][j + 1] += Gb[i][j] * invi[i];
@@ -143,7 +144,7 @@ __device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const dou
         Db[i][0] += gb[i] * invi[i];
         invb[i] += gb[i] * D[i][0];
     }
-    double inv_b = invb[0] + invb[1] * ih1 + invb[2] * ih2;
+    T inv_b = invb[0] + invb[1] * ih1 + invb[2] * ih2;
     for (int j = 0; j < 3; ++j) {
         qd[j + 1] += Ub[j] * inv;
         inv_b += Ub[j] * q[j + 1];
@@ -161,88 +162,151 @@ __device__ void gk_flux_rev(const Phys<double> &ph, const double q[4], const dou
 // Adjoint of dev::weno5_pair (both face values of the centre cell of
 // q[0..4], weights folded as in the forward): seeds sR for the right-face
 // value and sL for the left-face value; the cell adjoints are added to out.
-__device__ __forceinline__ void weno5_pair_rev(const double q[5], double sR, double sL, double out[5])
+template <typename T>
+__device__ __forceinline__ void weno5_pair_rev(const T q[5], T sR, T sL, T out[5])
 {
-    const double c13 = 13.0 / 12.0;
-    const double a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
-    const double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
-    const double t1 = b - 2.0 * c + d, u1 = b - d;
-    const double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
-    const double s0 = 1e-6 + (c13 * t0 * t0 + 0.25 * u0 * u0);
-    const double s1 = 1e-6 + (c13 * t1 * t1 + 0.25 * u1 * u1);
-    const double s2 = 1e-6 + (c13 * t2 * t2 + 0.25 * u2 * u2);
-    const double S0 = s0 * s0, S1 = s1 * s1, S2 = s2 * s2;
-    const double w02 = 6.0 * (S0 * S2), S01 = S0 * S1, S12 = S1 * S2;
+    const T c13 = T(13.0) / T(12.0);
+    const T a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
+    const T t0 = a - T(2.0) * b + c, u0 = a - T(4.0) * b + T(3.0) * c;
+    const T t1 = b - T(2.0) * c + d, u1 = b - d;
+    const T t2 = c - T(2.0) * d + e, u2 = T(3.0) * c - T(4.0) * d + e;
+    const T s0 = T(1e-6) + (c13 * t0 * t0 + T(0.25) * u0 * u0);
+    const T s1 = T(1e-6) + (c13 * t1 * t1 + T(0.25) * u1 * u1);
+    const T s2 = T(1e-6) + (c13 * t2 * t2 + T(0.25) * u2 * u2);
+    const T S0 = s0 * s0, S1 = s1 * s1, S2 = s2 * s2;
+    const T w02 = T(6.0) * (S0 * S2), S01 = S0 * S1, S12 = S1 * S2;
     // right face: 6 p_k on (a,b,c), (b,c,d), (c,d,e), weights S12, w02, 3 S01
-    const double P0 = 2.0 * a - 7.0 * b + 11.0 * c, P1 = -b + 5.0 * c + 2.0 * d, P2 = 2.0 * c + 5.0 * d - e;
-    const double wr2 = 3.0 * S01;
-    const double iDR = 1.0 / (6.0 * (S12 + w02 + wr2));
-    const double right = (S12 * P0 + w02 * P1 + wr2 * P2) * iDR;
+    const T P0 = T(2.0) * a - T(7.0) * b + T(11.0) * c, P1 = -b + T(5.0) * c + T(2.0) * d, P2 = T(2.0) * c + T(5.0) * d - e;
+    const T wr2 = T(3.0) * S01;
+    const T iDR = T(1.0) / (T(6.0) * (S12 + w02 + wr2));
+    const T right = (S12 * P0 + w02 * P1 + wr2 * P2) * iDR;
     // left face: mirrored candidates, weights S01, w02, 3 S12
-    const double Q0 = 2.0 * e - 7.0 * d + 11.0 * c, Q1 = -d + 5.0 * c + 2.0 * b, Q2 = 2.0 * c + 5.0 * b - a;
-    const double wl2 = 3.0 * S12;
-    const double iDL = 1.0 / (6.0 * (S01 + w02 + wl2));
-    const double left = (S01 * Q0 + w02 * Q1 + wl2 * Q2) * iDL;
+    const T Q0 = T(2.0) * e - T(7.0) * d + T(11.0) * c, Q1 = -d + T(5.0) * c + T(2.0) * b, Q2 = T(2.0) * c + T(5.0) * b - a;
+    const T wl2 = T(3.0) * S12;
+    const T iDL = T(1.0) / (T(6.0) * (S01 + w02 + wl2));
+    const T left = (S01 * Q0 + w02 * Q1 + wl2 * Q2) * iDL;
     // value = N / D: Nb = s / D, Db = -Nb value
-    const double NRb = sR * iDR, DRb6 = -6.0 * NRb * right;
-    const double NLb = sL * iDL, DLb6 = -6.0 * NLb * left;
-    const double P0b = NRb * S12, P1b = NRb * w02, P2b = NRb * wr2;
-    const double Q0b = NLb * S01, Q1b = NLb * w02, Q2b = NLb * wl2;
-    const double S12b = (NRb * P0 + DRb6) + 3.0 * (NLb * Q2 + DLb6);
-    const double w02b = (NRb * P1 + DRb6) + (NLb * Q1 + DLb6);
-    const double S01b = 3.0 * (NRb * P2 + DRb6) + (NLb * Q0 + DLb6);
-    const double S0b = 6.0 * S2 * w02b + S1 * S01b;
-    const double S1b = S2 * S12b + S0 * S01b;
-    const double S2b = S1 * S12b + 6.0 * S0 * w02b;
-    const double s0b = 2.0 * s0 * S0b, s1b = 2.0 * s1 * S1b, s2b = 2.0 * s2 * S2b;
-    const double t0b = s0b * (2.0 * c13) * t0, u0b = s0b * 0.5 * u0;
-    const double t1b = s1b * (2.0 * c13) * t1, u1b = s1b * 0.5 * u1;
-    const double t2b = s2b * (2.0 * c13) * t2, u2b = s2b * 0.5 * u2;
-    out[0] += t0b + u0b + 2.0 * P0b - Q2b;
-    out[1] += -2.0 * t0b - 4.0 * u0b + t1b + u1b - 7.0 * P0b - P1b + 2.0 * Q1b + 5.0 * Q2b;
-    out[2] += t0b + 3.0 * u0b - 2.0 * t1b + t2b + 3.0 * u2b + 11.0 * P0b + 5.0 * P1b + 2.0 * P2b + 11.0 * Q0b +
-              5.0 * Q1b + 2.0 * Q2b;
-    out[3] += t1b - u1b - 2.0 * t2b - 4.0 * u2b + 2.0 * P1b + 5.0 * P2b - 7.0 * Q0b - Q1b;
-    out[4] += t2b + u2b - P2b + 2.0 * Q0b;
+    const T NRb = sR * iDR, DRb6 = -T(6.0) * NRb * right;
+    const T NLb = sL * iDL, DLb6 = -T(6.0) * NLb * left;
+    const T P0b = NRb * S12, P1b = NRb * w02, P2b = NRb * wr2;
+    const T Q0b = NLb * S01, Q1b = NLb * w02, Q2b = NLb * wl2;
+    const T S12b = (NRb * P0 + DRb6) + T(3.0) * (NLb * Q2 + DLb6);
+    const T w02b = (NRb * P1 + DRb6) + (NLb * Q1 + DLb6);
+    const T S01b = T(3.0) * (NRb * P2 + DRb6) + (NLb * Q0 + DLb6);
+    const T S0b = T(6.0) * S2 * w02b + S1 * S01b;
+    const T S1b = S2 * S12b + S0 * S01b;
+    const T S2b = S1 * S12b + T(6.0) * S0 * w02b;
+    const T s0b = T(2.0) * s0 * S0b, s1b = T(2.0) * s1 * S1b, s2b = T(2.0) * s2 * S2b;
+    const T t0b = s0b * (T(2.0) * c13) * t0, u0b = s0b * T(0.5) * u0;
+    const T t1b = s1b * (T(2.0) * c13) * t1, u1b = s1b * T(0.5) * u1;
+    const T t2b = s2b * (T(2.0) * c13) * t2, u2b = s2b * T(0.5) * u2;
+    out[0] += t0b + u0b + T(2.0) * P0b - Q2b;
+    out[1] += -T(2.0) * t0b - T(4.0) * u0b + t1b + u1b - T(7.0) * P0b - P1b + T(2.0) * Q1b + T(5.0) * Q2b;
+    out[2] += t0b + T(3.0) * u0b - T(2.0) * t1b + t2b + T(3.0) * u2b + T(11.0) * P0b + T(5.0) * P1b + T(2.0) * P2b + T(11.0) * Q0b +
+              T(5.0) * Q1b + T(2.0) * Q2b;
+    out[3] += t1b - u1b - T(2.0) * t2b - T(4.0) * u2b + T(2.0) * P1b + T(5.0) * P2b - T(7.0) * Q0b - Q1b;
+    out[4] += t2b + u2b - P2b + T(2.0) * Q0b;
 }
 
 // Adjoint of the half-space equilibrium state (local frame).
-__device__ __forceinline__ void equilibrium_rev(const Phys<double> &ph, const double Ql[4], const double Qr[4],
-                                                const double Q0b[4],
-                                double Qlb[4], double Qrb[4])
+template <typename T>
+__device__ __forceinline__ void equilibrium_rev(const Phys<T> &ph, const T Ql[4], const T Qr[4], const T Q0b[4],
+                                                T Qlb[4], T Qrb[4])
 {
-    const double off = ph.off;
-    const double rl = off + Ql[0], rr = off + Qr[0];
-    const double irl = 1.0 / rl, irr = 1.0 / rr;
-    const double Ul = Ql[1] * irl, Ur = Qr[1] * irr;
+    const T off = ph.off;
+    const T rl = off + Ql[0], rr = off + Qr[0];
+    const T irl = T(1.0) / rl, irr = T(1.0) / rr;
+    const T Ul = Ql[1] * irl, Ur = Qr[1] * irr;
     // erf(z) and exp(-z^2) with z = sqrt(lambda) U, as in the forward
-    double el, er, ml, mr, exl, exr;
+    T el, er, ml, mr, exl, exr;
     half_space_terms(ph.sqlam * Ul, el, ml, exl);
     half_space_terms(ph.sqlam * Ur, er, mr, exr);
-    const double Pl = 0.5 + 0.5 * el, Pr = 0.5 - 0.5 * er;
-    const double El = ph.kE * exl, Er = ph.kE * exr;
-    double Plb = 0.0, Prb = 0.0;
+    const T Pl = T(0.5) + T(0.5) * el, Pr = T(0.5) - T(0.5) * er;
+    const T El = ph.kE * exl, Er = ph.kE * exr;
+    T Plb = T(0.0), Prb = T(0.0);
     for (int v = 0; v < 4; ++v) {
         Plb += Q0b[v] * Ql[v];
         Prb += Q0b[v] * Qr[v];
         Qlb[v] = Q0b[v] * Pl;
         Qrb[v] = Q0b[v] * Pr;
     }
-    double elb = 0.5 * Q0b[0] * off + 0.5 * Plb;
-    double erb = -0.5 * Q0b[0] * off - 0.5 * Prb;
+    T elb = T(0.5) * Q0b[0] * off + T(0.5) * Plb;
+    T erb = -T(0.5) * Q0b[0] * off - T(0.5) * Prb;
     Qlb[0] += Q0b[1] * El;
     Qrb[0] -= Q0b[1] * Er;
-    const double Elb = Q0b[1] * Ql[0], Erb = -Q0b[1] * Qr[0];
-    double xlb = Q0b[1] * off * ph.kE * exl + Elb * El;
-    double xrb = -Q0b[1] * off * ph.kE * exr + Erb * Er;
+    const T Elb = Q0b[1] * Ql[0], Erb = -Q0b[1] * Qr[0];
+    T xlb = Q0b[1] * off * ph.kE * exl + Elb * El;
+    T xrb = -Q0b[1] * off * ph.kE * exr + Erb * Er;
     // d erf(z)/dz = (2/sqrt pi) exp(-z^2), and z^2 = lambda U^2: exp(-z^2) = exp(x)
-    const double dz = 2.0 / sqrt(kPi);
-    double Ulb = elb * ph.sqlam * dz * exl + xlb * (-2.0 * ph.lambda * Ul);
-    double Urb = erb * ph.sqlam * dz * exr + xrb * (-2.0 * ph.lambda * Ur);
+    const T dz = T(2.0) / T(T(1.7724538509055160273));
+    T Ulb = elb * ph.sqlam * dz * exl + xlb * (-T(2.0) * ph.lambda * Ul);
+    T Urb = erb * ph.sqlam * dz * exr + xrb * (-T(2.0) * ph.lambda * Ur);
     Qlb[1] += Ulb * irl;
     Qlb[0] += -Ulb * Ul * irl;
     Qrb[1] += Urb * irr;
     Qrb[0] += -Urb * Ur * irr;
+}
+
+// The constants of ph in the compute type T of a reverse kernel.
+template <typename T>
+__device__ __forceinline__ Phys<T> phys_as(const Phys<double> &p)
+{
+    Phys<T> q;
+    q.lambda = T(p.lambda);
+    q.theta = T(p.theta);
+    q.mu = T(p.mu);
+    q.off = T(p.off);
+    q.sqlam = T(p.sqlam);
+    q.kE = T(p.kE);
+    return q;
+}
+
+// WENO5 pair of a 5-cell stencil in compute type T on the cells minus the
+// centre cell (both face values shift with it and the reverse depends on
+// differences only), so that FP32 keeps the relative precision of the
+// differences of FP64 states.
+template <typename T>
+__device__ __forceinline__ void pair_values(const double q[5], double &right, double &left)
+{
+    T qs[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qs[k] = T(q[k] - q[2]);
+    T r, l;
+    weno5_pair(qs, r, l);
+    right = q[2] + (double)r;
+    left = q[2] + (double)l;
+}
+
+template <typename T>
+__device__ __forceinline__ void pair_rev(const double q[5], double sR, double sL, double out[5])
+{
+    T qs[5], o[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qs[k] = T(q[k] - q[2]);
+    weno5_pair_rev<T>(qs, T(sR), T(sL), o);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k] += (double)o[k];
+}
+
+// equilibrium_rev in compute type T with FP64 arguments.
+template <typename T>
+__device__ __forceinline__ void equilibrium_rev_as(const Phys<double> &ph, const double Ql[4], const double Qr[4],
+                                                   const double Q0b[4], double Qlb[4], double Qrb[4])
+{
+    const Phys<T> pt = phys_as<T>(ph);
+    T l[4], r[4], b[4], lb[4], rb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        l[v] = T(Ql[v]);
+        r[v] = T(Qr[v]);
+        b[v] = T(Q0b[v]);
+    }
+    equilibrium_rev<T>(pt, l, r, b, lb, rb);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        Qlb[v] = (double)lb[v];
+        Qrb[v] = (double)rb[v];
+    }
 }
 
 // ------------------------------------------------------------------ kernels
@@ -269,6 +333,7 @@ struct RevArgs {
 // RA: reverse of the face flux at every interior face. The 64 Gauss-point
 // inputs of the face, kept by the forward recompute in lamG, are replaced
 // in place by their adjoints.
+template <typename T>
 __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
 {
     const int a = blockIdx.x * TX + threadIdx.x, b = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
@@ -291,87 +356,122 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
             lF0[v] = 0.25 * (-ml * ihl + mr * ihr);
         }
     }
-    const double ih1 = A.ih1[a + G], ih2 = A.ih2[b + G];
+    const T ih1 = T(A.ih1[a + G]), ih2 = T(A.ih2[b + G]);
+    const Phys<T> ph = phys_as<T>(A.ph);
+    T sF0[4], sF1[4];
+    for (int v = 0; v < 4; ++v) {
+        sF0[v] = T(lF0[v]);
+        sF1[v] = T(lF1[v]);
+    }
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
     for (int g = 0; g < 4; ++g) {
         double *io = A.lamG + (long)(16 * g) * A.nG + face;
-        double q[4], Dn[4], D1[4], D2[4];
+        T q[4], Dn[4], D1[4], D2[4];
         for (int v = 0; v < 4; ++v) {
-            q[v] = io[v * A.nG];
-            Dn[v] = io[(4 + v) * A.nG];
-            D1[v] = io[(8 + v) * A.nG];
-            D2[v] = io[(12 + v) * A.nG];
+            q[v] = T(io[v * A.nG]);
+            Dn[v] = T(io[(4 + v) * A.nG]);
+            D1[v] = T(io[(8 + v) * A.nG]);
+            D2[v] = T(io[(12 + v) * A.nG]);
         }
-        double qb[4], Dnb[4], D1b[4], D2b[4];
-        gk_flux_rev(A.ph, q, Dn, D1, D2, ih1, ih2, lF0, lF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
+        T qb[4], Dnb[4], D1b[4], D2b[4];
+        gk_flux_rev<T>(ph, q, Dn, D1, D2, ih1, ih2, sF0, sF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
         for (int v = 0; v < 4; ++v) {
-            io[v * A.nG] = qb[v];
-            io[(4 + v) * A.nG] = Dnb[v];
-            io[(8 + v) * A.nG] = D1b[v];
-            io[(12 + v) * A.nG] = D2b[v];
+            io[v * A.nG] = (double)qb[v];
+            io[(4 + v) * A.nG] = (double)Dnb[v];
+            io[(8 + v) * A.nG] = (double)D1b[v];
+            io[(12 + v) * A.nG] = (double)D2b[v];
         }
     }
 }
 
-// RB: transpose of the t2 pass, per t1-pass row (f, a, b'), b' in [-2, n2+2),
-// and t1 Gauss point m (blockIdx.y = 2 x row tile + m): a 5-tap gather of
-// the Gauss-point adjoints of the faces b = b'-2 .. b'+2.
-__global__ void __launch_bounds__(256, 3) rev_t2_kernel(RevArgs A)
+// RB: transpose of the t2 pass: for every t1-pass row (f, a, b'), b' in
+// [-2, n2+2), t1 Gauss point m and component v, the 5-tap gathers over the
+// faces b = b'-2 .. b'+2 of the Gauss-point adjoints (value and t2 slope into
+// the Q0 row, t1 slope into the t1-derivative row, normal slope into the slope
+// row). A thread owns (a, m, v) of one face plane and walks kRevT2 rows of b'
+// with the 8 adjoints of the 5 faces in a register window, so that every face
+// value is read once.
+constexpr int kRevT2 = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
 {
-    const int m = blockIdx.y & 1;
-    const int a = blockIdx.x * 32 + threadIdx.x, bp = (int)((blockIdx.y >> 1) * 8 + threadIdx.y) - 2, f = blockIdx.z;
-    if (a >= A.n1 || bp >= A.n2 + 2) return;
-    double X[4] = {0, 0, 0, 0}, Y[4] = {0, 0, 0, 0}, Z[4] = {0, 0, 0, 0};
-    const int blo = bp - 2 < 0 ? 0 : bp - 2, bhi = bp + 2 > A.n2 - 1 ? A.n2 - 1 : bp + 2;
-    const int nG = (int)A.nG;   // 64 nG < 2^31 (checked by the host)
-    const double *Gm = A.lamG + (long)(m * 32) * A.nG;
-#pragma unroll 1
-    for (int b = blo; b <= bhi; ++b) {
-        const int s = bp - b + 2;
-        const double *Gf = Gm + ((long)f * A.n2 + b) * A.n1 + a;
+    const int a = blockIdx.x * 32 + threadIdx.x;
+    const int mv = threadIdx.y, m = mv >> 2, v = mv & 3;   // 8 = 2 Gauss points x 4 components
+    const int f = blockIdx.z, bp0 = (int)blockIdx.y * kRevT2 - 2;
+    if (a >= A.n1) return;
+    const int bp1 = min(bp0 + kRevT2, A.n2 + 2);
+    const long nG = A.nG;
+    // per face b: Q0 adjoints of the two t2 points (0, 1), t2 slopes (2, 3),
+    // t1 slopes (4, 5), normal slopes (6, 7) of Gauss points g = 2m + nn
+    auto load = [&](int b, T x[8]) {
+        if (b < 0 || b >= A.n2) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = T(0);
+            return;
+        }
+        const double *Gf = A.lamG + ((long)f * A.n2 + b) * A.n1 + a;
 #pragma unroll
         for (int nn = 0; nn < 2; ++nn) {
-            const double wv = cWV[nn][s], wd = cWD[nn][s];
+            const long g16 = 16L * (2 * m + nn);
+            x[nn] = T(Gf[(g16 + 0 + v) * nG]);
+            x[2 + nn] = T(Gf[(g16 + 12 + v) * nG]);
+            x[4 + nn] = T(Gf[(g16 + 8 + v) * nG]);
+            x[6 + nn] = T(Gf[(g16 + 4 + v) * nG]);
+        }
+    };
+    T win[5][8];   // faces b' - 2 .. b' + 2
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                X[v] += wv * Gf[(nn * 16 + 0 + v) * nG] + wd * Gf[(nn * 16 + 12 + v) * nG];
-                Y[v] += wv * Gf[(nn * 16 + 8 + v) * nG];
-                Z[v] += wv * Gf[(nn * 16 + 4 + v) * nG];
+    for (int k = 0; k < 4; ++k) load(bp0 - 2 + k, win[k + 1]);
+    for (int bp = bp0; bp < bp1; ++bp) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) win[k][e] = win[k + 1][e];
+        load(bp + 2, win[4]);
+        T X = T(0), Y = T(0), Z = T(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {   // face b = bp - 2 + k, stencil offset s = bp - b + 2 = 4 - k
+#pragma unroll
+            for (int nn = 0; nn < 2; ++nn) {
+                const T wv = T(cWV[nn][4 - k]), wd = T(cWD[nn][4 - k]);
+                X += wv * win[k][nn] + wd * win[k][2 + nn];
+                Y += wv * win[k][4 + nn];
+                Z += wv * win[k][6 + nn];
             }
         }
-    }
-    const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = X[v];
-        A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = Y[v];
-        A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = Z[v];
+        const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
+        A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = (double)X;
+        A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = (double)Y;
+        A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = (double)Z;
     }
 }
 
 // RC: transpose of the t1 pass, per face of the extended box.
+template <typename T>
 __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
 {
     const int ap = (int)(blockIdx.x * 32 + threadIdx.x) - 2, bp = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
     const int f = blockIdx.z;
     if (ap >= A.n1 + 2 || bp >= A.n2 + 2) return;
-    double lq[4] = {0, 0, 0, 0}, ln[4] = {0, 0, 0, 0};
+    T lq[4] = {0, 0, 0, 0}, ln[4] = {0, 0, 0, 0};
     const int alo = ap - 2 < 0 ? 0 : ap - 2, ahi = ap + 2 > A.n1 - 1 ? A.n1 - 1 : ap + 2;
     for (int a = alo; a <= ahi; ++a) {
         const int r = ap - a + 2;
         const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
         for (int m = 0; m < 2; ++m) {
-            const double wv = cWV[m][r], wd = cWD[m][r];
+            const T wv = T(cWV[m][r]), wd = T(cWD[m][r]);
             for (int v = 0; v < 4; ++v) {
-                lq[v] += wv * A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] + wd * A.lamR[(1 * 8 + m * 4 + v) * A.nR + row];
-                ln[v] += wv * A.lamR[(2 * 8 + m * 4 + v) * A.nR + row];
+                lq[v] += wv * T(A.lamR[(0 * 8 + m * 4 + v) * A.nR + row]) +
+                         wd * T(A.lamR[(1 * 8 + m * 4 + v) * A.nR + row]);
+                ln[v] += wv * T(A.lamR[(2 * 8 + m * 4 + v) * A.nR + row]);
             }
         }
     }
     const long o = ((long)f * (A.n2 + 4) + (bp + 2)) * A.e1p + (ap + 2);
     for (int v = 0; v < 4; ++v) {
-        A.lamFQ[v * A.nfq + o] = lq[v];
-        A.lamFQ[(4 + v) * A.nfq + o] = ln[v];
+        A.lamFQ[v * A.nfq + o] = (double)lq[v];
+        A.lamFQ[(4 + v) * A.nfq + o] = (double)ln[v];
     }
 }
 
@@ -385,6 +485,7 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
 // per face side.
 constexpr int kRevMarch = 16;
 
+template <typename T>
 __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
 {
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
@@ -411,19 +512,19 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
     {
         double lft[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) weno5_pair(&w[v][1], Rprev[v], lft[v]);   // cell f0-1
+        for (int v = 0; v < 4; ++v) pair_values<T>(&w[v][1], Rprev[v], lft[v]);   // cell f0-1
         if (f0 == 0) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) Sprev[v] = 0.0;
         } else {
             double Rpp[4], dum;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) weno5_pair(&w[v][0], Rpp[v], dum);    // cell f0-2
+            for (int v = 0; v < 4; ++v) pair_values<T>(&w[v][0], Rpp[v], dum);    // cell f0-2
             const long o = ((long)(f0 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
             double Q0b[4], Qlb[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) Q0b[v] = A.lamFQ[v * A.nfq + o];
-            equilibrium_rev(A.ph, Rpp, lft, Q0b, Qlb, Sprev);
+            equilibrium_rev_as<T>(A.ph, Rpp, lft, Q0b, Qlb, Sprev);
         }
     }
     for (int f = f0; f < f1; ++f) {
@@ -437,7 +538,7 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             Ql[v] = Rprev[v];
-            weno5_pair(&w[v][1], Rt[v], Qr[v]);   // cell f
+            pair_values<T>(&w[v][1], Rt[v], Qr[v]);   // cell f
         }
         const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
         double Q0b[4], DNb[4], Qlb[4], Qrb[4];
@@ -446,7 +547,7 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
             Q0b[v] = A.lamFQ[v * A.nfq + o];
             DNb[v] = A.lamFQ[(4 + v) * A.nfq + o];
         }
-        equilibrium_rev(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
+        equilibrium_rev_as<T>(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
         const double s = A.ihf[f] * (1.0 / 12.0);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -455,8 +556,8 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
             cb[2] -= 15.0 * DNb[v] * s;
             cb[3] += 15.0 * DNb[v] * s;
             cb[4] -= DNb[v] * s;
-            weno5_pair_rev(&w[v][0], Qlb[v], Sprev[v], &cb[0]);      // cell f-1
-            if (f == nf - 1) weno5_pair_rev(&w[v][1], 0.0, Qrb[v], &cb[1]);   // cell f, left value only
+            pair_rev<T>(&w[v][0], Qlb[v], Sprev[v], &cb[0]);      // cell f-1
+            if (f == nf - 1) pair_rev<T>(&w[v][1], 0.0, Qrb[v], &cb[1]);   // cell f, left value only
 #pragma unroll
             for (int m = 0; m < 6; ++m) A.lamC[(m * 4 + v) * A.nfq + o] = cb[m];
             Rprev[v] = Rt[v];
@@ -794,6 +895,7 @@ __global__ void alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const lon
 
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
 // for lamL (may be null) and lamLt; result accumulated into w.lamA.
+template <typename T>
 void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], double *const gp[3],
                      const double *lamL, const double *lamLt)
 {
@@ -832,10 +934,10 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *c
         R.ph = ph;
         const dim3 blk(32, 8);
         const int nf = c.n[d] + 1;
-        rev_flux_kernel<<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
-        rev_t2_kernel<<<dim3((R.n1 + 31) / 32, 2 * ((R.n2 + 4 + 7) / 8), nf), blk, 0, c.stream>>>(R);
-        rev_t1_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
-        rev_face_state_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch), blk,
+        rev_flux_kernel<T><<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
+        rev_t2_kernel<T><<<dim3((R.n1 + 31) / 32, (R.n2 + 4 + kRevT2 - 1) / kRevT2, nf), blk, 0, c.stream>>>(R);
+        rev_t1_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
+        rev_face_state_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch), blk,
                                 0, c.stream>>>(R);
         rev_gather_cells_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
                                   c.stream>>>(R);
@@ -968,8 +1070,9 @@ size_t adjoint_bytes(const Ctx &c, long npts_total)
 }
 
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1)
+                     double power_seed, double dt, double t_np1, bool fp32)
 {
+    auto spatial = fp32 ? spatial_adjoint<float> : spatial_adjoint<double>;
     const dim3 blk(32, 8), gcell((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
     const size_t bytes4 = sizeof(double) * 4 * c.np;
     // IBM reverse (bodies act after the rotors, in the order added): lamP
@@ -1005,13 +1108,13 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, (const double *)c.wk1, w.fqs[1], w.gps[1], nullptr, w.lamLt);
+    spatial(c, w, (const double *)c.wk1, w.fqs[1], w.gps[1], nullptr, w.lamLt);
     ghost_adjoint(c, w, (const double *)c.wk1);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial_adjoint(c, w, w.A0, w.fqs[0], w.gps[0], w.lamL, w.lamLt);
+    spatial(c, w, w.A0, w.fqs[0], w.gps[0], w.lamL, w.lamLt);
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }

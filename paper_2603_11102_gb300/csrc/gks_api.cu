@@ -42,6 +42,8 @@ struct gks_grid {
     // the FP32 input (FP32C) and max |U|^2 of the current state are in place
     // (left by the last step or state upload): the next step skips its prep
     bool prep_valid = false;
+    // gks_step_adjoint: FP32 arithmetic in the local reverse maps
+    bool adj_fp32 = false;
 };
 
 namespace {
@@ -830,6 +832,13 @@ int adjoint_check(gks_grid *g)
 }
 }  // namespace
 
+int gks_set_adjoint_precision(gks_grid *g, int precision)
+{
+    if (!g || (precision != GKS_FP64 && precision != GKS_FP32C)) return fail(g, GKS_ERR_ARG, "bad adjoint precision");
+    g->adj_fp32 = precision == GKS_FP32C;
+    return GKS_OK;
+}
+
 int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes)
 {
     if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
@@ -884,7 +893,7 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     // reverse
     cc.state = w.lamP;
     launch_scatter_state(cc, d_adj_np1);
-    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt);
+    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt, g->adj_fp32);
     cc.state = w.lamW;
     launch_gather_state(cc, d_adj_n);
     rc = check_launch(g, "adjoint step");

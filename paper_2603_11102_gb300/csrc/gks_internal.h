@@ -148,8 +148,10 @@ size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
 // w (A0, W* in c.wk1, Wp, rotor loads, the face boxes of both stages in
 // w.fqs); accumulates into grad (per point) and w.scal[0].
 struct BodyDev;
+// fp32: FP32 arithmetic in the local reverse maps (flux, WENO5 pair,
+// equilibrium, transposed tangential passes), FP64 storage and sums.
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1);
+                     double power_seed, double dt, double t_np1, bool fp32);
 
 // Immersed body (gks_forcing.cu).
 struct BodyDev {

@@ -85,6 +85,7 @@ SIGNATURES = {
     "gks_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_adjoint_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_set_adjoint_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_step_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_double, _dp, _dp]),
     "gks_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -334,6 +335,12 @@ class Grid:
         t = t.to(device=self.device, dtype=torch.float64).contiguous()
         _check(lib.gks_set_state_device(self.h, C.c_void_p(t.data_ptr())), self.h)
         self.stream.synchronize()
+
+    def set_adjoint_precision(self, precision):
+        """Arithmetic of the local reverse maps of step_adjoint: "fp64" or
+        "fp32" (FP64 recompute, storage and sums either way)."""
+        code = {"fp64": PRECISIONS["fp64"], "fp32": PRECISIONS["fp32c"]}[precision]
+        _check(lib.gks_set_adjoint_precision(self.h, code), self.h)
 
     def adjoint_workspace(self):
         import torch

@@ -1,27 +1,32 @@
-// gks_adjoint.cu -- hand-written reverse mode (adjoint) of one S2O4 step in
-// FP64, for gradients of a functional of the state with respect to the
+// gks_adjoint.cu -- hand-written reverse mode (adjoint) of one FP64 S2O4
+// step, for gradients of a functional of the state with respect to the
 // per-point actuator force scales and the inflow speed.
 //
 // The forward step (Sec. 2 and the end of Sec. 3.2) is a composition of
 //   ghost fill G, spatial operator (L, Lt) = S(A) per direction d
 //   [face state: WENO5 + half-space equilibrium + normal slope;
 //    face flux: tangential quartic to the Gauss points + closed-form flux;
-//    divergence], the two stage combinations, and the ALM forcing
-//   [trilinear sample, loads, truncated-Gaussian projection].
-// Its adjoint runs the pieces backwards. Every transposed stencil is written
-// as a gather (each output sums its inputs in a fixed order), so the adjoint
-// is deterministic and uses no atomics on the state:
-//   RA  per interior face: recompute the Gauss-point inputs, reverse the
-//       flux, write the 64 Gauss-input adjoints;
+//    divergence], the two stage combinations, the ALM forcing
+//   [trilinear sample, loads, truncated-Gaussian projection] and the IBM
+//   direct forcing. The forward recompute keeps each stage's and direction's
+//   face box and the Gauss-point inputs of every face. Its adjoint runs the
+//   pieces backwards. Every transposed stencil is written as a gather (each
+//   output sums its inputs in a fixed order), so the adjoint is
+//   deterministic and uses no atomics on the state:
+//   RA  per interior face: reverse the flux at the 4 Gauss points, the
+//       Gauss-input adjoints replace the stored inputs;
 //   RB  t2 transpose: Gauss adjoints -> adjoints of the t1-pass rows;
 //   RC  t1 transpose: rows -> adjoints of Q0 and its normal slope per face;
-//   RD  per face: recompute WENO5 and the equilibrium, reverse them and the
-//       normal slope -> adjoints of the 6 cells of the face's stencil;
+//   RD  marching along d: paired WENO5 forward and reverse per cell, the
+//       equilibrium and normal-slope reverse per face -> adjoints of the
+//       6 cells of each face's stencil;
 //   RE  per cell: gather the 6 faces whose stencil holds the cell;
 //   ghost adjoint: axes z, y, x, one launch per side and layer, each ghost
 //       adjoint added to its source cell (Riemann inflow through its
 //       Jacobian; its U_inf sensitivity stored per ghost and reduced in a
 //       fixed order).
+// RA-RD run in a compute type T: double, or float (FP32 arithmetic in the
+// local reverse maps, FP64 loads, stores and sums).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,17 +1,22 @@
 // gks_stencil.cu -- the gas-kinetic stencil of one S2O4 stage on sm_103a.
 //
-// Per stage and per direction d (x, y, z) two kernels run:
-//   face_eq    one thread per face of the tangentially extended face box:
-//              WENO5-JS left/right states along d (Sec. 2, Jiang-Shu), the
-//              equilibrium state Q0 from the half Maxwellians (u>0 from the
-//              left, u<0 from the right), and the quartic normal slope of Q0.
-//   face_flux  32x8 face tiles: linear quartic reconstruction of Q0 and its
-//              normal slope to the 2x2 Gauss points (Sec. 2, Eq. (x_example))
-//              with the tangential pass staged in shared memory, and the
-//              gas-kinetic flux F0 and its time derivative F1 at each point
-//              (Sec. 2, Eq. (flux); Appendix), averaged with weights 1/4.
-// then the update kernel forms L and dL/dt (Eq. (finite)) and applies the
-// two-stage fourth-order combination.
+// Per stage and per direction d (x, y, z):
+//   face_eq      one thread per tangential position of the extended face box,
+//                marching 16 faces along d with a 5-cell window: WENO5-JS
+//                (Sec. 2, Jiang-Shu) left/right states from one paired
+//                evaluation per cell, the equilibrium state Q0 from the half
+//                Maxwellians (u>0 from the left, u<0 from the right), and the
+//                quartic normal slope of Q0.
+//   face_flux    (x, y) persistent, 32x8 face tiles loaded by TMA: linear
+//                quartic reconstruction of Q0 and its normal slope to the 2x2
+//                Gauss points (Sec. 2, Eq. (x_example)) with the t1 pass in
+//                shared memory, and the gas-kinetic flux F0 and its time
+//                derivative F1 at each point (Sec. 2, Eq. (flux); Appendix),
+//                averaged with weights 1/4 and stored per face.
+//   flux_update  (z) the same flux, walking z per tile column, fused with the
+//                divergence (Eq. (finite)) and the two-stage fourth-order
+//                combination of every cell; stage 2 also prepares the next
+//                step (FP32 input, max |U|^2 for the CFL step).
 //
 // All arithmetic runs in the working type R: double for GKS_FP64, float for
 // GKS_FP32C. The reconstruction works on rho - off (off = rho_ref in FP32C,

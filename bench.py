@@ -252,8 +252,11 @@ def adjoint_workload(n=(256, 128, 128)):
 def time_adjoint(args, dev):
     """Forward and checkpointed adjoint of the wake-deficit plus power
     objective; ratio = backward time (segment recomputation included) over
-    the forward time of the same steps, with FP32 arithmetic in the local
-    reverse maps (the FD-checked default of this benchmark) and with FP64."""
+    the forward time of the same steps. Main figure: recorded steps (each
+    segment run forward once with its step tapes, then reversed from them)
+    with FP32 arithmetic in the local reverse maps (the FD-checked default of
+    this benchmark); also per-step recomputation and FP64 reverse
+    arithmetic."""
     import torch
 
     from paper_2603_11102_gb300 import adjoint, gks
@@ -262,12 +265,12 @@ def time_adjoint(args, dev):
     iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
     npts = w.rotors[0].n_blades * len(w.rotors[0].r)
 
-    def run(steps):
+    def run(steps, tape):
         s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
         u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        J = adjoint.rotor_objective(g, s, u, steps, K=args.adjoint_k, iplane=iplane, beta=1.0)
+        J = adjoint.rotor_objective(g, s, u, steps, K=args.adjoint_k, iplane=iplane, beta=1.0, tape=tape)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         J.backward()
@@ -276,21 +279,26 @@ def time_adjoint(args, dev):
         return t1 - t0, t2 - t1, float(u.grad)
 
     out = {}
-    for rev in ("fp32", "fp64"):
+    for rev, tape in (("fp32", "on"), ("fp32", "off"), ("fp64", "on")):
         g.set_adjoint_precision(rev)
-        run(args.adjoint_k)   # untimed warm-up segment (first launches, the workspace)
-        out[rev] = run(args.adjoint_steps)
+        run(args.adjoint_k, tape)   # untimed warm-up segment (first launches, the buffers)
+        out[rev, tape] = run(args.adjoint_steps, tape)
+    tape_gb = g.adjoint_tape_bytes() / 1e9
     g.close()
-    fwd, bwd, gu = out["fp32"]
-    fwd64, bwd64, gu64 = out["fp64"]
+    fwd, bwd, gu = out["fp32", "on"]
+    fwdr, bwdr, gur = out["fp32", "off"]
+    fwd64, bwd64, gu64 = out["fp64", "on"]
     return {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
             "warmup": "one untimed segment of %d steps, forward and backward" % args.adjoint_k,
             "reverse_arithmetic": "fp32 (FP64 recompute, storage and sums)",
+            "recorded_steps": "%d tapes of %.1f GB" % (args.adjoint_k, tape_gb),
             "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
             "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
-            "ratio_fp64_reverse": bwd64 / fwd64, "backward_s_fp64_reverse": bwd64,
+            "ratio_recompute_per_step": bwdr / fwdr, "ratio_fp64_reverse": bwd64 / fwd64,
+            "backward_s_fp64_reverse": bwd64,
             "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
-                         % npts, "grad_uinf": gu, "grad_uinf_fp64_reverse": gu64}
+                         % npts, "grad_uinf": gu, "grad_uinf_recompute_per_step": gur,
+            "grad_uinf_fp64_reverse": gu64}
 
 
 def run_ours(args, world, rank, local):

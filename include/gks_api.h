@@ -249,7 +249,7 @@ int gks_get_state_device(gks_grid *g, double *d_state);
  *   d_adj_n     device, receives lambda^n (compact FP64; may not alias the
  *               inputs).
  * The forward step is recomputed from d_state_n inside the call; the grid's
- * own state is not changed. Requires a GKS_FP64 grid with a fixed time step,
+ * own state and time are not changed. Requires a GKS_FP64 grid with a fixed time step,
  * at most one rotor without the velocity or tip correction, and immersed
  * bodies only with a fixed iteration count (tol = 0) (GKS_ERR_STATE
  * otherwise), and fewer than 2^31 / 64 faces per direction (GKS_ERR_ARG
@@ -266,6 +266,43 @@ int gks_set_adjoint_precision(gks_grid *g, int precision);
 int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n,
                      const double *d_adj_np1, double *d_adj_n, double power_seed,
                      double *h_grad_scales, double *h_grad_uinf);
+
+/* Recorded steps: the same reverse as gks_step_adjoint, split into a forward
+ * step that keeps what its reverse reads (a "tape") and the reverse from that
+ * tape, so that a checkpointed gradient runs each step forward once in the
+ * backward pass instead of twice.
+ *   gks_adjoint_tape_bytes     bytes of one step's tape: t_n and dt, the
+ *                              ghost-filled W^n and W*, the state before the
+ *                              forcing, and per stage and direction the face
+ *                              boxes and the 64 Gauss-point inputs of every
+ *                              face (about 3.6 KB per cell);
+ *   gks_adjoint_scratch_bytes  bytes of the scratch of gks_step_reverse
+ *                              (the workspace of gks_step_adjoint is a tape
+ *                              followed by a scratch);
+ *   gks_step_record            one step of the grid exactly as gks_step(g, 1,
+ *                              t_out), which also fills d_tape (device,
+ *                              caller-owned, 256-byte aligned);
+ *   gks_step_reverse           from the tape of step n and lambda^{n+1}
+ *                              (device, compact FP64), writes lambda^n
+ *                              (device, compact FP64, may not alias) and adds
+ *                              the force-scale and inflow-speed gradients of
+ *                              step n as gks_step_adjoint does; power_seed is
+ *                              dJ/dP for the power of step n. The reverse
+ *                              overwrites the tape's Gauss-point inputs, so a
+ *                              tape is reversed once: a tape that was not
+ *                              recorded or was already reversed gives
+ *                              GKS_ERR_STATE. d_scratch: device,
+ *                              caller-owned, 256-byte aligned. Synchronises
+ *                              the stream.
+ * Both need what gks_step_adjoint needs (GKS_ERR_STATE / GKS_ERR_ARG
+ * otherwise) and use the grid's adjoint precision. The grid's force scales
+ * and inflow must be those of the recorded step when it is reversed. */
+int gks_adjoint_tape_bytes(const gks_grid *g, size_t *bytes);
+int gks_adjoint_scratch_bytes(const gks_grid *g, size_t *bytes);
+int gks_step_record(gks_grid *g, void *d_tape, double *t_out);
+int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d_adj_np1,
+                     double *d_adj_n, double power_seed, double *h_grad_scales,
+                     double *h_grad_uinf);
 
 /* Kernel accounting of the library's own kernels. Every kernel launch is
  * counted per group (0 prep, 1 ghost, 2 cfl, 3 face_eq, 4 face_flux: x and

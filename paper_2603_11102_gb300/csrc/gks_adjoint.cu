@@ -1021,51 +1021,74 @@ __global__ void __launch_bounds__(256) ibm_adj_kernel(double *lam, long np, int 
 
 }  // namespace
 
-// Offsets of the adjoint buffers from `base` (base may be 0 to size them);
-// returns the total bytes.
-size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
-{
+namespace {
+struct Carver {
+    uintptr_t b0;
     size_t o = 0;
-    const uintptr_t b0 = (uintptr_t)base;
-    auto take = [&](size_t n) {
+    double *take(size_t n)
+    {
         double *p = (double *)(b0 + o);
         o += (n * sizeof(double) + 255) & ~(size_t)255;
         return p;
-    };
+    }
+};
+}  // namespace
+
+size_t adjoint_tape_carve(const Ctx &c, void *base, AdjWork *w)
+{
+    Carver k{(uintptr_t)base};
     const long np4 = 4 * c.np;
-    w->A0 = take(np4);
-    w->Wp = take(np4);
-    w->lamA = take(np4);
-    w->lamW = take(np4);
-    w->lamP = take(np4);
-    w->lamL = take(np4);
-    w->lamLt = take(np4);
-    long nG = 0, nR = 0, maxsurf = 0;
+    w->hdr = k.take(4);
+    w->A0 = k.take(np4);
+    w->Ws = k.take(np4);
+    w->Wp = k.take(np4);
+    long nG = 0;
+    for (int d = 0; d < 3; ++d) nG = std::max(nG, (long)(c.n[d] + 1) * c.n[tan1(d)] * c.n[tan2(d)]);
+    w->nG = nG;
+    for (int st = 0; st < 2; ++st)
+        for (int d = 0; d < 3; ++d) {
+            w->fqs[st][d] = k.take(8 * c.nfq);
+            w->gps[st][d] = k.take(64 * nG);
+        }
+    return k.o;
+}
+
+size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
+{
+    Carver k{(uintptr_t)base};
+    const long np4 = 4 * c.np;
+    w->lamA = k.take(np4);
+    w->lamW = k.take(np4);
+    w->lamP = k.take(np4);
+    w->lamL = k.take(np4);
+    w->lamLt = k.take(np4);
+    long nR = 0, maxsurf = 0;
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
-        nG = std::max(nG, (long)(c.n[d] + 1) * c.n[t1] * c.n[t2]);
         nR = std::max(nR, (long)(c.n[d] + 1) * (c.n[t2] + 4) * c.n[t1]);
         const long l1 = t1 < d ? c.n[t1] + 2 * G : c.n[t1];
         const long l2 = t2 < d ? c.n[t2] + 2 * G : c.n[t2];
         maxsurf = std::max(maxsurf, l1 * l2);
     }
-    w->nG = nG;
     w->nR = nR;
-    for (int st = 0; st < 2; ++st)
-        for (int d = 0; d < 3; ++d) {
-            w->fqs[st][d] = take(8 * c.nfq);
-            w->gps[st][d] = take(64 * nG);
-        }
-    w->lamR = take(24 * nR);
-    w->lamFQ = take(8 * c.nfq);
-    w->lamC = take(24 * c.nfq);
+    w->lamR = k.take(24 * nR);
+    w->lamFQ = k.take(8 * c.nfq);
+    w->lamC = k.take(24 * c.nfq);
     w->nuinf = 3 * 2 * G * maxsurf;
-    w->uinf_part = take(w->nuinf);
-    w->pts = take(8 * (npts_total > 0 ? npts_total : 1));
-    w->ptc = take(32 * (npts_total > 0 ? npts_total : 1));
-    w->ptl = take(8 * (npts_total > 0 ? npts_total : 1));
-    w->scal = take(8);
-    return o;
+    w->uinf_part = k.take(w->nuinf);
+    const long np = npts_total > 0 ? npts_total : 1;
+    w->pts = k.take(8 * np);
+    w->ptc = k.take(32 * np);
+    w->ptl = k.take(8 * np);
+    w->scal = k.take(8);
+    w->sc = (Scalars *)k.take((sizeof(Scalars) + 7) / 8);
+    return k.o;
+}
+
+size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
+{
+    const size_t tb = adjoint_tape_carve(c, base, w);
+    return tb + adjoint_scratch_carve(c, npts_total, base ? (void *)((uintptr_t)base + tb) : (void *)tb, w);
 }
 
 size_t adjoint_bytes(const Ctx &c, long npts_total)
@@ -1113,8 +1136,8 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial(c, w, (const double *)c.wk1, w.fqs[1], w.gps[1], nullptr, w.lamLt);
-    ghost_adjoint(c, w, (const double *)c.wk1);
+    spatial(c, w, w.Ws, w.fqs[1], w.gps[1], nullptr, w.lamLt);
+    ghost_adjoint(c, w, w.Ws);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);

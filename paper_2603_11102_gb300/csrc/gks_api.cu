@@ -598,57 +598,114 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
     return GKS_OK;
 }
 
-int gks_step(gks_grid *g, int nsteps, double *t_out)
+namespace {
+int check_flags(gks_grid *g, int flags, const char *where);
+
+// Per stage st of a recorded step, the face boxes and Gauss-point inputs of
+// every direction go to the tape.
+int use_tape_faces(gks_grid *g, Ctx &cc, const AdjWork &w, int st)
 {
-    if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
+    cc.ngp = w.nG;
+    for (int d = 0; d < 3; ++d) {
+        cc.fq_dir[d] = w.fqs[st][d];
+        cc.gp_dir[d] = w.gps[st][d];
+        std::string m;
+        if (encode_face_map(cc, d, w.fqs[st][d], &cc.tmap_dir[d], &m)) return fail(g, GKS_ERR_CUDA, m);
+    }
+    return GKS_OK;
+}
+
+// One S2O4 step of the grid with its forcing. With a tape (FP64 grids) the
+// step also keeps what its reverse reads: t_n and dt, the ghost-filled W^n
+// and W*, the state before the forcing, and both stages' face boxes and
+// Gauss-point inputs; the arithmetic of the step is the same either way.
+int step_once(gks_grid *g, const AdjWork *tp)
+{
     Ctx &c = g->c;
-    g->stepped = true;
+    Ctx cc = c;
     const int nobj = (int)g->obj_kind.size();
     const bool fused_prep = nobj <= 8;
-    for (int s = 0; s < nsteps; ++s) {
-        if (!g->prep_valid) launch_prep(c);
-        launch_ghost(c, c.wk0);
-        launch_cfl(c);   // dt from max |U|^2, which it clears
-        launch_stage(c, 1);
-        launch_ghost(c, c.wk1);
-        // stage 2 also prepares the next step on every cell outside the
-        // forcing boxes; the boxes are prepared again after the forcing
-        if (fused_prep) {
-            c.prep_next = 1;
-            c.nprep_box = nobj;
-            for (int k = 0; k < nobj; ++k) {
-                const int(*box)[2] = g->obj_kind[k] == 0 ? g->rotors[g->obj_index[k]].box : g->bodies[g->obj_index[k]].box;
-                memcpy(c.prep_box[k], box, sizeof(int) * 6);
-            }
-        }
-        launch_stage(c, 2);
-        c.prep_next = 0;
-        for (size_t k = 0; k < g->obj_kind.size(); ++k)
-            if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
-        for (size_t k = 0; k < g->obj_kind.size(); ++k)
-            if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
-        if (fused_prep)
-            for (int k = 0; k < nobj; ++k) launch_prep_box(c, c.prep_box[k]);
-        g->prep_valid = fused_prep;
-        launch_advance(c);
-        int rc = check_launch(g, "step");
+    const size_t bytes4 = sizeof(double) * 4 * c.np;
+    int rc = GKS_OK;
+    if (!g->prep_valid) launch_prep(c);
+    launch_ghost(c, c.wk0);
+    launch_cfl(c);   // dt from max |U|^2, which it clears
+    if (tp) {
+        rc = cuda_check(g, cudaMemcpyAsync(tp->hdr + 1, &c.scal->t, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           c.stream), "record time");
+        if (!rc) rc = cuda_check(g, cudaMemsetAsync(tp->hdr, kTapeMagicByte, sizeof(double), c.stream), "mark tape");
+        if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->A0, c.wk0, bytes4, cudaMemcpyDeviceToDevice, c.stream),
+                                 "record W^n");
+        if (!rc) rc = use_tape_faces(g, cc, *tp, 0);
         if (rc) return rc;
-        g->nstep++;
+        cc.wk1 = tp->Ws;
     }
+    launch_stage(cc, 1);
+    launch_ghost(cc, cc.wk1);
+    if (tp && (rc = use_tape_faces(g, cc, *tp, 1))) return rc;
+    // stage 2 also prepares the next step on every cell outside the forcing
+    // boxes; the boxes are prepared again after the forcing
+    if (fused_prep) {
+        cc.prep_next = 1;
+        cc.nprep_box = nobj;
+        for (int k = 0; k < nobj; ++k) {
+            const int(*box)[2] = g->obj_kind[k] == 0 ? g->rotors[g->obj_index[k]].box : g->bodies[g->obj_index[k]].box;
+            memcpy(cc.prep_box[k], box, sizeof(int) * 6);
+        }
+    }
+    launch_stage(cc, 2);
+    if (tp && (rc = cuda_check(g, cudaMemcpyAsync(tp->Wp, c.state, bytes4, cudaMemcpyDeviceToDevice, c.stream),
+                               "record the state before the forcing")))
+        return rc;
+    for (size_t k = 0; k < g->obj_kind.size(); ++k)
+        if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
+    for (size_t k = 0; k < g->obj_kind.size(); ++k)
+        if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
+    if (fused_prep)
+        for (int k = 0; k < nobj; ++k) launch_prep_box(c, cc.prep_box[k]);
+    g->prep_valid = fused_prep;
+    launch_advance(c);
+    rc = check_launch(g, "step");
+    if (rc) return rc;
+    g->nstep++;
+    return GKS_OK;
+}
+
+int finish_steps(gks_grid *g, double *t_out)
+{
     Scalars sc;
     int rc = read_scalars(g, &sc);
     if (rc) return rc;
     if (t_out) *t_out = sc.t;
     if (sc.flags) {
         int flags = 0;
-        cudaMemcpyAsync(&c.scal->flags, &flags, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+        cudaMemcpyAsync(&g->c.scal->flags, &flags, sizeof(int), cudaMemcpyHostToDevice, g->c.stream);
         sync(g);
-        if (sc.flags & FLAG_NONFINITE) return fail(g, GKS_ERR_NONFINITE, "non-finite value in the state");
-        if (sc.flags & FLAG_RANGE) return fail(g, GKS_ERR_RANGE, "actuator point outside the sampled interior");
-        if (sc.flags & FLAG_CFL) return fail(g, GKS_ERR_CFL, "fixed time step above the CFL limit");
-        if (sc.flags & FLAG_TIMEOUT) return fail(g, GKS_ERR_CUDA, "a device-side wait timed out");
+        return check_flags(g, sc.flags, "state");
     }
     return GKS_OK;
+}
+
+int check_flags(gks_grid *g, int flags, const char *where)
+{
+    std::string w(where);
+    if (flags & FLAG_NONFINITE) return fail(g, GKS_ERR_NONFINITE, "non-finite value in the " + w);
+    if (flags & FLAG_RANGE) return fail(g, GKS_ERR_RANGE, "actuator point outside the sampled interior");
+    if (flags & FLAG_CFL) return fail(g, GKS_ERR_CFL, "fixed time step above the CFL limit");
+    if (flags & FLAG_TIMEOUT) return fail(g, GKS_ERR_CUDA, "a device-side wait timed out");
+    return flags ? fail(g, GKS_ERR_CUDA, "device flag raised in the " + w) : GKS_OK;
+}
+}  // namespace
+
+int gks_step(gks_grid *g, int nsteps, double *t_out)
+{
+    if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
+    g->stepped = true;
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = step_once(g, nullptr);
+        if (rc) return rc;
+    }
+    return finish_steps(g, t_out);
 }
 
 int gks_get_time(gks_grid *g, double *t, double *dt_last)
@@ -846,6 +903,115 @@ int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes)
     return GKS_OK;
 }
 
+int gks_adjoint_tape_bytes(const gks_grid *g, size_t *bytes)
+{
+    if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
+    AdjWork w;
+    *bytes = adjoint_tape_carve(g->c, nullptr, &w);
+    return GKS_OK;
+}
+
+int gks_adjoint_scratch_bytes(const gks_grid *g, size_t *bytes)
+{
+    if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
+    AdjWork w;
+    *bytes = adjoint_scratch_carve(g->c, total_points(g), nullptr, &w);
+    return GKS_OK;
+}
+
+namespace {
+// The reverse of one step from the tape in w (recorded by gks_step_record
+// or by the recompute of gks_step_adjoint), with the time of the tape.
+// init_sc: set the private scalars from the tape (the recompute of
+// gks_step_adjoint has set them already, and its flags are kept).
+int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, double dt, const double *d_adj_np1,
+                      double *d_adj_n, double power_seed, double *h_grad_scales, double *h_grad_uinf)
+{
+    const Ctx &c = g->c;
+    Ctx cc = c;
+    cc.mark = nullptr;
+    cc.scal = w.sc;
+    cc.wk1 = w.Ws;
+    int rc = GKS_OK;
+    if (init_sc) {
+        rc = cuda_check(g, cudaMemsetAsync(w.sc, 0, sizeof(Scalars), c.stream), "clear reverse scalars");
+        if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&w.sc->t, w.hdr + 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                                    c.stream), "reverse time");
+    }
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.scal, 0, 8 * sizeof(double), c.stream), "clear adjoint scalars");
+    if (rc) return rc;
+    // the rotor loads at t_{n+1} from the state before the forcing
+    const RotorDev *rot = g->rotors.empty() ? nullptr : &g->rotors[0];
+    if (rot) {
+        cc.state = w.Wp;
+        launch_alm_loads(cc, *rot);
+    }
+    cc.state = w.lamP;
+    launch_scatter_state(cc, d_adj_np1);
+    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt, g->adj_fp32);
+    cc.state = w.lamW;
+    launch_gather_state(cc, d_adj_n);
+    // the reverse overwrote the Gauss-point inputs: the tape is consumed
+    rc = cuda_check(g, cudaMemsetAsync(w.hdr, 0, sizeof(double), c.stream), "consume tape");
+    if (!rc) rc = check_launch(g, "adjoint step");
+    if (rc) return rc;
+    const long npts = total_points(g);
+    std::vector<double> pts(8 * (npts > 0 ? npts : 1));
+    double gu = 0.0;
+    int flags = 0;
+    if (npts > 0)
+        rc = cuda_check(g, cudaMemcpyAsync(pts.data(), w.pts, sizeof(double) * 8 * npts, cudaMemcpyDeviceToHost, c.stream),
+                        "read scale gradients");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&gu, w.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream),
+                             "read inflow gradient");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&flags, &w.sc->flags, sizeof(int), cudaMemcpyDeviceToHost, c.stream),
+                             "read reverse flags");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    if (flags) return check_flags(g, flags, "adjoint step");
+    if (h_grad_scales)
+        for (long q = 0; q < npts; ++q) h_grad_scales[q] += pts[8 * q + 2];
+    if (h_grad_uinf) *h_grad_uinf += gu;
+    return GKS_OK;
+}
+}  // namespace
+
+int gks_step_record(gks_grid *g, void *d_tape, double *t_out)
+{
+    if (!g || !d_tape) return fail(g, GKS_ERR_ARG, "null argument");
+    if ((uintptr_t)d_tape & 255) return fail(g, GKS_ERR_ARG, "tape must be 256-byte aligned");
+    int rc = adjoint_check(g);
+    if (rc) return rc;
+    AdjWork w;
+    adjoint_tape_carve(g->c, d_tape, &w);
+    g->stepped = true;
+    rc = step_once(g, &w);
+    if (rc) return rc;
+    return finish_steps(g, t_out);
+}
+
+int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d_adj_np1, double *d_adj_n,
+                     double power_seed, double *h_grad_scales, double *h_grad_uinf)
+{
+    if (!g || !d_tape || !d_scratch || !d_adj_np1 || !d_adj_n) return fail(g, GKS_ERR_ARG, "null argument");
+    if (((uintptr_t)d_tape | (uintptr_t)d_scratch) & 255)
+        return fail(g, GKS_ERR_ARG, "tape and scratch must be 256-byte aligned");
+    int rc = adjoint_check(g);
+    if (rc) return rc;
+    AdjWork w;
+    adjoint_tape_carve(g->c, d_tape, &w);
+    adjoint_scratch_carve(g->c, total_points(g), d_scratch, &w);
+    double hdr[3];
+    rc = cuda_check(g, cudaMemcpyAsync(hdr, w.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, g->c.stream), "read tape");
+    if (!rc) rc = sync(g);
+    if (rc) return rc;
+    unsigned char magic[sizeof(double)];
+    memcpy(magic, hdr, sizeof(magic));
+    for (unsigned char m : magic)
+        if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded, or already reversed");
+    return reverse_from_tape(g, w, true, hdr[1], hdr[2], d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
+}
+
 int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n, const double *d_adj_np1,
                      double *d_adj_n, double power_seed, double *h_grad_scales, double *h_grad_uinf)
 {
@@ -857,70 +1023,31 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     AdjWork w;
     adjoint_carve(c, total_points(g), d_adj_work, &w);
     const double dt = c.dt_fixed;
+    // forward recompute of the step from W^n into the tape part of the
+    // workspace, on private scalars (the grid's time and state stay as they
+    // are): A0 = G(W^n), W* = G(stage 1), Wp = stage 2 before the forcing
     Ctx cc = c;
     cc.mark = nullptr;
-    // forward recompute of the step from W^n: A0 = G(W^n), W* (c.wk1), P,
-    // W' (before forcing) and the rotor loads at t_{n+1}
-    double sv[2] = {t_n, dt};
-    rc = cuda_check(g, cudaMemcpyAsync(&c.scal->t, sv, 2 * sizeof(double), cudaMemcpyHostToDevice, c.stream),
-                    "set time");
-    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.scal, 0, 8 * sizeof(double), c.stream), "clear adjoint scalars");
+    cc.scal = w.sc;
+    const double hv[2] = {t_n, dt};
+    rc = cuda_check(g, cudaMemsetAsync(w.sc, 0, sizeof(Scalars), c.stream), "clear reverse scalars");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&w.sc->t, hv, sizeof(hv), cudaMemcpyHostToDevice, c.stream), "set time");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(w.hdr + 1, hv, sizeof(hv), cudaMemcpyHostToDevice, c.stream),
+                             "record time");
+    if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.hdr, kTapeMagicByte, sizeof(double), c.stream), "mark tape");
     if (rc) return rc;
-    // each stage and direction keeps its face box for the reverse
-    auto keep_faces = [&](int st) {
-        cc.ngp = w.nG;
-        for (int d = 0; d < 3; ++d) {
-            cc.fq_dir[d] = w.fqs[st][d];
-            cc.gp_dir[d] = w.gps[st][d];
-            std::string m;
-            if (encode_face_map(cc, d, w.fqs[st][d], &cc.tmap_dir[d], &m)) return fail(g, GKS_ERR_CUDA, m);
-        }
-        return (int)GKS_OK;
-    };
     cc.state = w.A0;
     cc.wk0 = w.A0;
+    cc.wk1 = w.Ws;
     launch_scatter_state(cc, d_state_n);
     launch_ghost(cc, w.A0);
-    if ((rc = keep_faces(0))) return rc;
+    if ((rc = use_tape_faces(g, cc, w, 0))) return rc;
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
     cc.state = w.Wp;
-    if ((rc = keep_faces(1))) return rc;
+    if ((rc = use_tape_faces(g, cc, w, 1))) return rc;
     launch_stage(cc, 2);
-    for (int d = 0; d < 3; ++d) cc.fq_dir[d] = cc.gp_dir[d] = nullptr;
-    const RotorDev *rot = g->rotors.empty() ? nullptr : &g->rotors[0];
-    if (rot) launch_alm_loads(cc, *rot);
-    // reverse
-    cc.state = w.lamP;
-    launch_scatter_state(cc, d_adj_np1);
-    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt, g->adj_fp32);
-    cc.state = w.lamW;
-    launch_gather_state(cc, d_adj_n);
-    rc = check_launch(g, "adjoint step");
-    if (rc) return rc;
-    const long npts = total_points(g);
-    std::vector<double> pts(8 * (npts > 0 ? npts : 1));
-    double gu = 0.0;
-    if (npts > 0)
-        rc = cuda_check(g, cudaMemcpyAsync(pts.data(), w.pts, sizeof(double) * 8 * npts, cudaMemcpyDeviceToHost, c.stream),
-                        "read scale gradients");
-    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&gu, w.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream),
-                             "read inflow gradient");
-    if (!rc) rc = sync(g);
-    if (rc) return rc;
-    if (h_grad_scales)
-        for (long q = 0; q < npts; ++q) h_grad_scales[q] += pts[8 * q + 2];
-    if (h_grad_uinf) *h_grad_uinf += gu;
-    Scalars sc;
-    rc = read_scalars(g, &sc);
-    if (rc) return rc;
-    if (sc.flags) {
-        int flags = 0;
-        cudaMemcpyAsync(&c.scal->flags, &flags, sizeof(int), cudaMemcpyHostToDevice, c.stream);
-        sync(g);
-        return fail(g, GKS_ERR_NONFINITE, "device flag raised during the adjoint step");
-    }
-    return GKS_OK;
+    return reverse_from_tape(g, w, false, t_n, dt, d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
 }
 
 int gks_profile_enable(gks_grid *g, int timing_on)

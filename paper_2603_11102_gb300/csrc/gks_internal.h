@@ -128,25 +128,38 @@ struct RotorDev {
 void launch_alm(const Ctx &c, const RotorDev &r);
 void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no projection
 
-// Adjoint of one step (gks_adjoint.cu). Buffers of the adjoint workspace.
+// Adjoint of one step (gks_adjoint.cu). Buffers of the adjoint workspace:
+// the tape of one step (what the reverse reads of the forward step) and the
+// scratch of the reverse.
+constexpr unsigned char kTapeMagicByte = 0x5A;   // hdr[0] bytes of a recorded, unconsumed tape
 struct AdjWork {
-    double *A0, *Wp, *lamA, *lamW, *lamP, *lamL, *lamLt;   // 4 * np each (padded indexing)
-    double *fqs[2][3];                                    // face boxes of the recompute, per stage and direction
-    double *gps[2][3];                                    // Gauss-point inputs of the recompute (64 nG each);
+    // tape
+    double *hdr;                                          // [0] magic, [1] t_n, [2] dt
+    double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
+    double *fqs[2][3];                                    // face boxes of the forward, per stage and direction
+    double *gps[2][3];                                    // Gauss-point inputs of the forward (64 nG each);
                                                           // the reverse flux overwrites them with their adjoints
+    long nG;                                              // component stride of gps
+    // scratch
+    double *lamA, *lamW, *lamP, *lamL, *lamLt;            // 4 * np each (padded indexing)
     double *lamR, *lamFQ, *lamC;                          // per row / face buffers
-    long nG, nR;                                          // component strides of gps, lamR
+    long nR;                                              // component stride of lamR
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;
     double *pts;                                          // per actuator point scratch (8 per point)
     double *ptc, *ptl;                                    // sampling-adjoint corner values (32) and cells (8, as long)
     double *scal;                                         // [0] grad U_inf (device accumulator)
+    Scalars *sc;                                          // private time, dt and flags of the reverse
 };
+// Offsets from base (0 to size them); each returns its bytes. The full
+// workspace of gks_step_adjoint is a tape followed by a scratch.
+size_t adjoint_tape_carve(const Ctx &c, void *base, AdjWork *w);
+size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
 size_t adjoint_bytes(const Ctx &c, long npts_total);
 size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
-// Runs the reverse of one step whose forward quantities were recomputed into
-// w (A0, W* in c.wk1, Wp, rotor loads, the face boxes of both stages in
-// w.fqs); accumulates into grad (per point) and w.scal[0].
+// Runs the reverse of one step from its tape in w (A0, W* in w.Ws, Wp, the
+// face boxes and Gauss-point inputs of both stages; the rotor loads
+// recomputed from Wp); accumulates into the per-point scratch and w.scal[0].
 struct BodyDev;
 // fp32: FP32 arithmetic in the local reverse maps (flux, WENO5 pair,
 // equilibrium, transposed tangential passes), FP64 storage and sums.

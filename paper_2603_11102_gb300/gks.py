@@ -85,6 +85,11 @@ SIGNATURES = {
     "gks_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_adjoint_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_adjoint_tape_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_adjoint_scratch_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_step_record": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "gks_step_reverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                   _dp, _dp]),
     "gks_set_adjoint_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_step_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_double, _dp, _dp]),
@@ -347,6 +352,44 @@ class Grid:
         nb = C.c_size_t()
         _check(lib.gks_adjoint_workspace_bytes(self.h, C.byref(nb)))
         return torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+
+    def adjoint_tape_bytes(self):
+        nb = C.c_size_t()
+        _check(lib.gks_adjoint_tape_bytes(self.h, C.byref(nb)))
+        return nb.value
+
+    def adjoint_tape(self):
+        """Device buffer for the tape of one recorded step."""
+        import torch
+        return torch.empty(self.adjoint_tape_bytes(), dtype=torch.uint8, device=self.device)
+
+    def adjoint_scratch(self):
+        """Device scratch of step_reverse."""
+        import torch
+        nb = C.c_size_t()
+        _check(lib.gks_adjoint_scratch_bytes(self.h, C.byref(nb)))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+
+    def step_record(self, tape):
+        """One step of the grid (as step(1)) that also fills tape; returns
+        the time after the step."""
+        t = C.c_double()
+        _check(lib.gks_step_record(self.h, C.c_void_p(tape.data_ptr()), C.byref(t)), self.h)
+        return t.value
+
+    def step_reverse(self, tape, scratch, adj_np1, power_seed=0.0, grad_scales=None):
+        """Reverse of the recorded step: returns (lambda^n, grad_uinf of the
+        step); adds its force-scale gradient into grad_scales (numpy). The
+        tape is consumed."""
+        import torch
+        adj_np1 = adj_np1.to(self.device, torch.float64).contiguous()
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        gu = C.c_double(0.0)
+        gs = None if grad_scales is None else grad_scales.ctypes.data_as(_dp)
+        _check(lib.gks_step_reverse(self.h, C.c_void_p(tape.data_ptr()), C.c_void_p(scratch.data_ptr()),
+                                    C.c_void_p(adj_np1.data_ptr()), C.c_void_p(out.data_ptr()), float(power_seed),
+                                    gs, C.byref(gu)), self.h)
+        return out, gu.value
 
     def step_adjoint(self, work, t_n, state_n, adj_np1, power_seed=0.0, grad_scales=None):
         """One reverse step: returns (lambda^n, grad_uinf of this step); adds

@@ -159,9 +159,15 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
     npts = 18
     s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
     u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    J = adjoint.rotor_objective(g, s, u, N, K=K, iplane=iplane, beta=beta)
+    J = adjoint.rotor_objective(g, s, u, N, K=K, iplane=iplane, beta=beta, tape="on")
     J.backward()
     gs, gu = s.grad.numpy().copy(), float(u.grad)
+    # recorded steps and per-step recomputation give the same gradient
+    s2 = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+    u2 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    adjoint.rotor_objective(g, s2, u2, N, K=K, iplane=iplane, beta=beta, tape="off").backward()
+    assert np.max(np.abs(s2.grad.numpy() - gs)) <= 1e-12 * np.max(np.abs(gs))
+    assert abs(float(u2.grad) - gu) <= 1e-12 * abs(gu)
 
     def Jgpu(sv, uv):
         return float(adjoint.rotor_objective(g, torch.tensor(sv, dtype=torch.float64),
@@ -197,6 +203,43 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
     g.close()
 
 
+@pytest.mark.parametrize("rev", ["fp64", "fp32"])
+def test_recorded_step_and_its_reverse(mods, rev):
+    """gks_step_record steps the grid as gks_step does, and gks_step_reverse
+    from its tape gives what gks_step_adjoint gives from W^n; a tape is
+    reversed once."""
+    gks, adjoint, torch = mods
+    w = rotor_body_workload()
+    g = gks.Grid.from_workload(w, precision="fp64")
+    g.set_adjoint_precision(rev)
+    W = torch.tensor(perturbed_state(w, 4), dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(9)
+    lam1 = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
+    t_n = 0.21
+    ref, _ = forward_step(g, torch, W, t_n)
+    tape, scratch = g.adjoint_tape(), g.adjoint_scratch()
+    g.set_state_tensor(W)
+    g.set_time(t_n)
+    t1 = g.step_record(tape)
+    assert torch.equal(g.state_tensor(), ref)
+    assert t1 == g.time
+    gs_r = np.zeros(18)
+    lam_r, gu_r = g.step_reverse(tape, scratch, lam1, 0.4, gs_r)
+    gs_a = np.zeros(18)
+    lam_a, gu_a = g.step_adjoint(g.adjoint_workspace(), t_n, W, lam1, 0.4, gs_a)
+    assert torch.equal(lam_r, lam_a)
+    assert np.array_equal(gs_r, gs_a) and gu_r == gu_a
+    # the grid's state and time are those the recorded step left
+    assert torch.equal(g.state_tensor(), ref) and g.time == t1
+    with pytest.raises(gks.GKSError) as e:
+        g.step_reverse(tape, scratch, lam1)
+    assert e.value.code == -5
+    with pytest.raises(gks.GKSError) as e:
+        g.step_reverse(torch.zeros_like(tape), scratch, lam1)
+    assert e.value.code == -5
+    g.close()
+
+
 def test_adjoint_rejects_unsupported_grids(mods):
     gks, adjoint, torch = mods
     w = rotor_box_workload()
@@ -210,6 +253,9 @@ def test_adjoint_rejects_unsupported_grids(mods):
     g2 = gks.Grid.from_workload(rotor_box_workload(), precision="fp32c")
     with pytest.raises(gks.GKSError) as e:
         g2.step_adjoint(g2.adjoint_workspace(), 0.0, W, W)
+    assert e.value.code == -5
+    with pytest.raises(gks.GKSError) as e:
+        g2.step_record(g.adjoint_tape())
     assert e.value.code == -5
     w4 = rotor_body_workload()
     w4.bodies[0].tol = 0.05

@@ -250,7 +250,7 @@ int gks_get_state_device(gks_grid *g, double *d_state);
  *               inputs).
  * The forward step is recomputed from d_state_n inside the call; the grid's
  * own state and time are not changed. Requires a GKS_FP64 grid with a fixed time step,
- * at most one rotor without the velocity or tip correction, and immersed
+ * at most one rotor (with or without the velocity and tip corrections), and immersed
  * bodies only with a fixed iteration count (tol = 0) (GKS_ERR_STATE
  * otherwise), and fewer than 2^31 / 64 faces per direction (GKS_ERR_ARG
  * otherwise). Synchronises the stream. */

@@ -781,6 +781,23 @@ __device__ bool trilinear_w(const AlmAdjArgs &A, const double X[3], int i0[3], d
 
 __device__ __forceinline__ double cd_of(double a) { return 0.01 + 0.02 * a * a; }
 
+// Tip factor F(phi) = (2/pi) acos(exp(-x)), x = g1 N (R - r) / (2 r |sin phi|)
+// (the same expression as the forward) and dF/dphi = (2/pi) e^-x x' /
+// sqrt(1 - e^-2x) with x' = -x cot phi; F = 0 with zero slope at and beyond
+// the tip, zero slope where e^-x underflows (sin phi -> 0, F -> 1).
+__device__ __forceinline__ void tip_factor_d(double g1, int nb, double R, double r, double phi, double &F,
+                                             double &dF)
+{
+    F = 0.0;
+    dF = 0.0;
+    if (r >= R) return;
+    const double sp = sin(phi);
+    const double x = g1 * nb * (R - r) / (2.0 * r * fabs(sp));
+    const double e = exp(-x);
+    F = (2.0 / kPi) * acos(e);
+    if (e > 0.0) dF = (2.0 / kPi) * e * (-x * cos(phi) / sp) / sqrt(-expm1(-2.0 * x));
+}
+
 // Reverse of the point loads: gradient of the force scales (this step), the
 // power seed, and the adjoint of the sampled velocity.
 __global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
@@ -810,8 +827,16 @@ __global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
                 U[1] += w * A.Wp[2 * A.np + l] / rho;
                 U[2] += w * A.Wp[3 * A.np + l] / rho;
             }
-            const double ux = U[0], ut = -sth * U[1] + cth * U[2];
+            // velocity correction (one pass with C_D of the uncorrected angle)
+            const double ux0 = U[0], ut0 = -sth * U[1] + cth * U[2];
             const double wr = r.omega * rr;
+            double fac = 1.0, phi0 = 0.0;
+            if (r.correction) {
+                phi0 = atan2(ux0, wr - ut0);
+                const double cd0 = cd_of(phi0 - r.twist[p]);
+                fac = 1.0 / (1.0 - cd0 * r.chord[p] / (4.0 * sqrt(kPi) * r.eps));
+            }
+            const double ux = ux0 * fac, ut = ut0 * fac;
             const double av = ux, bv = wr - ut;
             const double phi = atan2(av, bv), al = phi - r.twist[p];
             const double urel2 = av * av + bv * bv;
@@ -824,13 +849,20 @@ __global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
             const double Lf = qd * cl, Df = qd * cd;
             const double cp = cos(phi), sp = sin(phi);
             const double fx = Lf * cp + Df * sp, ft = Lf * sp - Df * cp;
+            // tip factors of the axial and tangential loads
+            double tx = 1.0, tt = 1.0, dtx = 0.0, dtt = 0.0;
+            if (r.tip) {
+                tip_factor_d(r.tip_g[0], r.nb, r.radius, rr, phi, tx, dtx);
+                tip_factor_d(r.tip_g[1], r.nb, r.radius, rr, phi, tt, dtt);
+            }
             const double s = r.scale[q];
             const double mux = A.pts[8 * q + 0];
             const double mut = A.pts[8 * q + 1] + A.power_seed * r.omega * rr;
-            gs = mux * fx + mut * ft;
-            const double fxb = s * mux, ftb = s * mut;
+            gs = mux * tx * fx + mut * tt * ft;
+            const double fxb = s * tx * mux, ftb = s * tt * mut;
             const double Lb = fxb * cp + ftb * sp, Db = fxb * sp - ftb * cp;
-            double phib = fxb * (-Lf * sp + Df * cp) + ftb * (Lf * cp + Df * sp);
+            double phib = fxb * (-Lf * sp + Df * cp) + ftb * (Lf * cp + Df * sp) +
+                          s * (mux * fx * dtx + mut * ft * dtt);
             const double qdb = Lb * cl + Db * cd;
             const double alb = Lb * qd * dcl + Db * qd * 0.04 * al;
             phib += alb;
@@ -838,7 +870,18 @@ __global__ void __launch_bounds__(256) alm_loads_adj_kernel(AlmAdjArgs A)
             const double den = urel2 > 0.0 ? urel2 : 1.0;
             const double ab = phib * bv / den + u2b * 2.0 * av;
             const double bb = -phib * av / den + u2b * 2.0 * bv;
-            const double uxb = ab, utb = -bb;
+            double uxb = ab, utb = -bb;
+            if (r.correction) {
+                // ux = fac ux0, ut = fac ut0, fac = 1 / (1 - k C_D(phi0 - twist)),
+                // dfac/dC_D = k fac^2, phi0 = atan2(ux0, wr - ut0)
+                const double k = r.chord[p] / (4.0 * sqrt(kPi) * r.eps);
+                const double facb = uxb * ux0 + utb * ut0;
+                const double phi0b = facb * k * fac * fac * 0.04 * (phi0 - r.twist[p]);
+                const double b0 = wr - ut0, d0 = ux0 * ux0 + b0 * b0;
+                const double den0 = d0 > 0.0 ? d0 : 1.0;
+                uxb = fac * uxb + phi0b * b0 / den0;
+                utb = fac * utb + phi0b * ux0 / den0;
+            }
             Ub[0] = uxb;
             Ub[1] = -sth * utb;
             Ub[2] = cth * utb;

@@ -876,10 +876,6 @@ int adjoint_check(gks_grid *g)
         if (b.tol > 0.0)
             return fail(g, GKS_ERR_STATE, "the adjoint covers immersed bodies with a fixed iteration count (tol = 0)");
     if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
-    if (!g->rotors.empty() && g->rotors[0].correction)
-        return fail(g, GKS_ERR_STATE, "the adjoint does not cover the ALM velocity correction");
-    if (!g->rotors.empty() && g->rotors[0].tip)
-        return fail(g, GKS_ERR_STATE, "the adjoint does not cover the tip correction");
     // the reverse t2 gather indexes its 64 face arrays with 32-bit offsets
     for (int d = 0; d < 3; ++d) {
         const double nf = (double)(c.n[d] + 1) * c.n[(d + 1) % 3] * c.n[(d + 2) % 3];

@@ -50,6 +50,14 @@ def rotor_body_workload():
     return w
 
 
+def rotor_corrections_workload():
+    """The rotor box with the ALM velocity correction and the tip factors."""
+    w = rotor_box_workload()
+    w.rotors[0].correction = True
+    w.rotors[0].tip_correction = True
+    return w
+
+
 def walls_workload(n=(20, 12, 10)):
     faces = [np.linspace(0, 2.0, n[0] + 1), WL.tanh_faces(n[1]), np.linspace(0, 1.0, n[2] + 1)]
     Q = np.zeros((4, n[2], n[1], n[0]))
@@ -85,12 +93,13 @@ def forward_step(g, torch, W, t_n, scales=None, uinf=None):
 
 
 @pytest.mark.parametrize("rev", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["rotor", "walls", "rotor_body"])
+@pytest.mark.parametrize("case", ["rotor", "walls", "rotor_body", "rotor_corrections"])
 def test_one_step_adjoint_matches_central_differences(mods, case, rev):
     """rev: arithmetic of the local reverse maps (FP64 within 1e-5 of the
     central differences; FP32 within 1e-4)."""
     gks, adjoint, torch = mods
-    w = {"rotor": rotor_box_workload, "walls": walls_workload, "rotor_body": rotor_body_workload}[case]()
+    w = {"rotor": rotor_box_workload, "walls": walls_workload, "rotor_body": rotor_body_workload,
+         "rotor_corrections": rotor_corrections_workload}[case]()
     g = gks.Grid.from_workload(w, precision="fp64")
     g.set_adjoint_precision(rev)
     tol = 1e-5 if rev == "fp64" else 1e-4
@@ -148,10 +157,11 @@ def oracle_objective(w, s, u, nsteps, iplane, beta):
 
 
 @pytest.mark.parametrize("rev", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["rotor", "rotor_body"])
+@pytest.mark.parametrize("case", ["rotor", "rotor_body", "rotor_corrections"])
 def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
     gks, adjoint, torch = mods
-    w = rotor_box_workload() if case == "rotor" else rotor_body_workload()
+    w = {"rotor": rotor_box_workload, "rotor_body": rotor_body_workload,
+         "rotor_corrections": rotor_corrections_workload}[case]()
     g = gks.Grid.from_workload(w, precision="fp64")
     g.set_adjoint_precision(rev)
     N, K, beta = 6, 2, 1.0
@@ -194,8 +204,9 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
     fou = (oracle_objective(w, s0, 1.0 + h, N, iplane, beta) -
            oracle_objective(w, s0, 1.0 - h, N, iplane, beta)) / (2 * h)
     assert abs(fou - gu) <= 1e-4 * abs(gu), (fou, gu)
-    if w.bodies:
-        # the body acts on the objective (the case is not the rotor case again)
+    if w.bodies or w.rotors[0].correction:
+        # the body or the corrections act on the objective (the case is not
+        # the rotor case again)
         J1 = oracle_objective(w, s0, 1.0, N, iplane, beta)
         w0 = rotor_box_workload()
         J0 = oracle_objective(w0, s0, 1.0, N, iplane, beta)
@@ -264,7 +275,7 @@ def test_adjoint_rejects_unsupported_grids(mods):
         g4.step_adjoint(g4.adjoint_workspace(), 0.0, W, W)
     assert e.value.code == -5
     w3 = rotor_box_workload()
-    w3.rotors[0].tip_correction = True
+    w3.rotors.append(rotor_box_workload().rotors[0])
     g3 = gks.Grid.from_workload(w3, precision="fp64")
     with pytest.raises(gks.GKSError) as e:
         g3.step_adjoint(g3.adjoint_workspace(), 0.0, W, W)

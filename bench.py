@@ -252,11 +252,13 @@ def adjoint_workload(n=(256, 128, 128)):
 def time_adjoint(args, dev):
     """Forward and checkpointed adjoint of the wake-deficit plus power
     objective; ratio = backward time (segment recomputation included) over
-    the forward time of the same steps. Main figure: recorded steps (each
-    segment run forward once with its step tapes, then reversed from them)
-    with FP32 arithmetic in the local reverse maps (the FD-checked default of
-    this benchmark); also per-step recomputation and FP64 reverse
-    arithmetic."""
+    the forward time of the same steps. Main figure, on the adjoint
+    configuration (256x128x128 rotor, 200 steps, checkpoint every 20):
+    recorded steps (each segment run forward once with its step tapes, then
+    reversed from them) with FP32 arithmetic in the local reverse maps (the
+    FD-checked default of this benchmark). Beside it, on a shorter run (20
+    steps, checkpoint every 10): per-step recomputation, and recorded steps
+    with FP64 reverse arithmetic."""
     import torch
 
     from paper_2603_11102_gb300 import adjoint, gks
@@ -265,12 +267,12 @@ def time_adjoint(args, dev):
     iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
     npts = w.rotors[0].n_blades * len(w.rotors[0].r)
 
-    def run(steps, tape):
+    def run(steps, K, tape):
         s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
         u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        J = adjoint.rotor_objective(g, s, u, steps, K=args.adjoint_k, iplane=iplane, beta=1.0, tape=tape)
+        J = adjoint.rotor_objective(g, s, u, steps, K=K, iplane=iplane, beta=1.0, tape=tape)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         J.backward()
@@ -278,27 +280,44 @@ def time_adjoint(args, dev):
         t2 = time.perf_counter()
         return t1 - t0, t2 - t1, float(u.grad)
 
-    out = {}
-    for rev, tape in (("fp32", "on"), ("fp32", "off"), ("fp64", "on")):
+    out, tape_gb = {}, {}
+    Kv, Nv = 10, args.adjoint_variant_steps
+    for rev, tape, N, K in (("fp32", "on", args.adjoint_steps, args.adjoint_k), ("fp32", "off", Nv, Kv),
+                            ("fp64", "on", Nv, Kv)):
+        if N <= 0:
+            continue
         g.set_adjoint_precision(rev)
-        run(args.adjoint_k, tape)   # untimed warm-up segment (first launches, the buffers)
-        out[rev, tape] = run(args.adjoint_steps, tape)
-    tape_gb = g.adjoint_tape_bytes() / 1e9
+        tape_gb[rev] = g.adjoint_tape_bytes() / 1e9
+        try:
+            run(K, K, tape)   # untimed warm-up segment (first launches, the buffers)
+            out[rev, tape] = run(N, K, tape)
+        except torch.cuda.OutOfMemoryError:
+            # K tapes do not fit next to what else holds device memory: the
+            # per-step recomputation, reported as such
+            torch.cuda.empty_cache()
+            run(K, K, "off")
+            out[rev, tape] = run(N, K, "off")
+            tape_gb[rev] = 0.0
+        torch.cuda.empty_cache()
     g.close()
     fwd, bwd, gu = out["fp32", "on"]
-    fwdr, bwdr, gur = out["fp32", "off"]
-    fwd64, bwd64, gu64 = out["fp64", "on"]
-    return {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
-            "warmup": "one untimed segment of %d steps, forward and backward" % args.adjoint_k,
-            "reverse_arithmetic": "fp32 (FP64 recompute, storage and sums)",
-            "recorded_steps": "%d tapes of %.1f GB" % (args.adjoint_k, tape_gb),
-            "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
-            "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
-            "ratio_recompute_per_step": bwdr / fwdr, "ratio_fp64_reverse": bwd64 / fwd64,
-            "backward_s_fp64_reverse": bwd64,
-            "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
-                         % npts, "grad_uinf": gu, "grad_uinf_recompute_per_step": gur,
-            "grad_uinf_fp64_reverse": gu64}
+    res = {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
+           "warmup": "one untimed segment, forward and backward",
+           "reverse_arithmetic": "fp32 (FP64 forward, state adjoints and sums; Gauss-point tape in FP32)",
+           "recorded_steps": ("%d tapes of %.1f GB" % (args.adjoint_k, tape_gb["fp32"]) if tape_gb["fp32"] > 0
+                              else "none: out of device memory, per-step recomputation"),
+           "forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
+           "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
+           "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
+                        % npts, "grad_uinf": gu}
+    if ("fp32", "off") in out:
+        f2, b2, g2 = out["fp32", "off"]
+        f3, b3, g3 = out["fp64", "on"]
+        res["variants"] = {"steps": Nv, "checkpoint_every": Kv,
+                           "ratio_recompute_per_step": b2 / f2, "grad_uinf_recompute_per_step": g2,
+                           "ratio_fp64_reverse": b3 / f3, "grad_uinf_fp64_reverse": g3,
+                           "fp64_tape_gb": tape_gb["fp64"]}
+    return res
 
 
 def run_ours(args, world, rank, local):
@@ -488,8 +507,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=10)
-    ap.add_argument("--adjoint-steps", type=int, default=20)
-    ap.add_argument("--adjoint-k", type=int, default=10)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-k", type=int, default=20)
+    ap.add_argument("--adjoint-variant-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -275,7 +275,9 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
  *                              ghost-filled W^n and W*, the state before the
  *                              forcing, and per stage and direction the face
  *                              boxes and the 64 Gauss-point inputs of every
- *                              face (about 3.6 KB per cell);
+ *                              face, stored in the compute type of the reverse
+ *                              (about 3.6 KB per cell with the FP64 adjoint
+ *                              precision, 2.1 KB with FP32);
  *   gks_adjoint_scratch_bytes  bytes of the scratch of gks_step_reverse
  *                              (the workspace of gks_step_adjoint is a tape
  *                              followed by a scratch);
@@ -295,7 +297,8 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
  *                              caller-owned, 256-byte aligned. Synchronises
  *                              the stream.
  * Both need what gks_step_adjoint needs (GKS_ERR_STATE / GKS_ERR_ARG
- * otherwise) and use the grid's adjoint precision. The grid's force scales
+ * otherwise) and use the grid's adjoint precision; a tape recorded with the
+ * other precision gives GKS_ERR_STATE. The grid's force scales
  * and inflow must be those of the recorded step when it is reversed. */
 int gks_adjoint_tape_bytes(const gks_grid *g, size_t *bytes);
 int gks_adjoint_scratch_bytes(const gks_grid *g, size_t *bytes);

@@ -322,7 +322,7 @@ struct RevArgs {
     long nfq;
     int e1p;
     const double *lamL, *lamLt;   // padded indexing; lamL may be null (stage 2)
-    double *lamG;
+    void *lamG;   // Gauss-point inputs / adjoints, stored in the reverse's compute type
     long nG;
     double *lamR;
     long nR;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     }
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
     for (int g = 0; g < 4; ++g) {
-        double *io = A.lamG + (long)(16 * g) * A.nG + face;
+        T *io = (T *)A.lamG + (long)(16 * g) * A.nG + face;
         T q[4], Dn[4], D1[4], D2[4];
         for (int v = 0; v < 4; ++v) {
             q[v] = T(io[v * A.nG]);
@@ -381,10 +381,10 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
         T qb[4], Dnb[4], D1b[4], D2b[4];
         gk_flux_rev<T>(ph, q, Dn, D1, D2, ih1, ih2, sF0, sF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
         for (int v = 0; v < 4; ++v) {
-            io[v * A.nG] = (double)qb[v];
-            io[(4 + v) * A.nG] = (double)Dnb[v];
-            io[(8 + v) * A.nG] = (double)D1b[v];
-            io[(12 + v) * A.nG] = (double)D2b[v];
+            io[v * A.nG] = qb[v];
+            io[(4 + v) * A.nG] = Dnb[v];
+            io[(8 + v) * A.nG] = D1b[v];
+            io[(12 + v) * A.nG] = D2b[v];
         }
     }
 }
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
             for (int k = 0; k < 8; ++k) x[k] = T(0);
             return;
         }
-        const double *Gf = A.lamG + ((long)f * A.n2 + b) * A.n1 + a;
+        const T *Gf = (const T *)A.lamG + ((long)f * A.n2 + b) * A.n1 + a;
 #pragma unroll
         for (int nn = 0; nn < 2; ++nn) {
             const long g16 = 16L * (2 * m + nn);
@@ -944,7 +944,7 @@ __global__ void alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const lon
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
 // for lamL (may be null) and lamLt; result accumulated into w.lamA.
 template <typename T>
-void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], double *const gp[3],
+void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], void *const gp[3],
                      const double *lamL, const double *lamLt)
 {
     const Phys<double> ph = make_phys<double>(c);
@@ -1077,9 +1077,10 @@ struct Carver {
 };
 }  // namespace
 
-size_t adjoint_tape_carve(const Ctx &c, void *base, AdjWork *w)
+size_t adjoint_tape_carve(const Ctx &c, int gp_bytes, void *base, AdjWork *w)
 {
     Carver k{(uintptr_t)base};
+    w->gp_bytes = gp_bytes;
     const long np4 = 4 * c.np;
     w->hdr = k.take(4);
     w->A0 = k.take(np4);
@@ -1091,7 +1092,7 @@ size_t adjoint_tape_carve(const Ctx &c, void *base, AdjWork *w)
     for (int st = 0; st < 2; ++st)
         for (int d = 0; d < 3; ++d) {
             w->fqs[st][d] = k.take(8 * c.nfq);
-            w->gps[st][d] = k.take(64 * nG);
+            w->gps[st][d] = k.take(64 * nG * gp_bytes / 8);
         }
     return k.o;
 }
@@ -1128,22 +1129,24 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
     return k.o;
 }
 
-size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w)
+size_t adjoint_carve(const Ctx &c, long npts_total, int gp_bytes, void *base, AdjWork *w)
 {
-    const size_t tb = adjoint_tape_carve(c, base, w);
+    const size_t tb = adjoint_tape_carve(c, gp_bytes, base, w);
     return tb + adjoint_scratch_carve(c, npts_total, base ? (void *)((uintptr_t)base + tb) : (void *)tb, w);
 }
 
-size_t adjoint_bytes(const Ctx &c, long npts_total)
+size_t adjoint_bytes(const Ctx &c, long npts_total, int gp_bytes)
 {
     AdjWork w;
-    return adjoint_carve(c, npts_total, nullptr, &w);
+    return adjoint_carve(c, npts_total, gp_bytes, nullptr, &w);
 }
 
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1, bool fp32)
+                     double power_seed, double dt, double t_np1)
 {
-    auto spatial = fp32 ? spatial_adjoint<float> : spatial_adjoint<double>;
+    // the compute type of the local reverse maps is the storage type of the
+    // tape's Gauss-point inputs
+    auto spatial = w.gp_bytes == 4 ? spatial_adjoint<float> : spatial_adjoint<double>;
     const dim3 blk(32, 8), gcell((c.n[0] + 31) / 32, (c.n[1] + 7) / 8, c.n[2]);
     const size_t bytes4 = sizeof(double) * 4 * c.np;
     // IBM reverse (bodies act after the rotors, in the order added): lamP

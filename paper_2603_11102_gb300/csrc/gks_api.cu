@@ -606,6 +606,7 @@ int check_flags(gks_grid *g, int flags, const char *where);
 int use_tape_faces(gks_grid *g, Ctx &cc, const AdjWork &w, int st)
 {
     cc.ngp = w.nG;
+    cc.gp_bytes = w.gp_bytes;
     for (int d = 0; d < 3; ++d) {
         cc.fq_dir[d] = w.fqs[st][d];
         cc.gp_dir[d] = w.gps[st][d];
@@ -634,6 +635,9 @@ int step_once(gks_grid *g, const AdjWork *tp)
         rc = cuda_check(g, cudaMemcpyAsync(tp->hdr + 1, &c.scal->t, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
                                            c.stream), "record time");
         if (!rc) rc = cuda_check(g, cudaMemsetAsync(tp->hdr, kTapeMagicByte, sizeof(double), c.stream), "mark tape");
+        const double gb = tp->gp_bytes;
+        if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->hdr + 3, &gb, sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                                 "record the tape's storage");
         if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->A0, c.wk0, bytes4, cudaMemcpyDeviceToDevice, c.stream),
                                  "record W^n");
         if (!rc) rc = use_tape_faces(g, cc, *tp, 0);
@@ -867,6 +871,9 @@ long total_points(const gks_grid *g)
     return n;
 }
 
+// Storage of the tape's Gauss-point inputs: the compute type of the reverse.
+int gp_bytes_of(const gks_grid *g) { return g->adj_fp32 ? 4 : 8; }
+
 int adjoint_check(gks_grid *g)
 {
     const Ctx &c = g->c;
@@ -895,7 +902,7 @@ int gks_set_adjoint_precision(gks_grid *g, int precision)
 int gks_adjoint_workspace_bytes(const gks_grid *g, size_t *bytes)
 {
     if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
-    *bytes = adjoint_bytes(g->c, total_points(g));
+    *bytes = adjoint_bytes(g->c, total_points(g), gp_bytes_of(g));
     return GKS_OK;
 }
 
@@ -903,7 +910,7 @@ int gks_adjoint_tape_bytes(const gks_grid *g, size_t *bytes)
 {
     if (!g || !bytes) return fail(nullptr, GKS_ERR_ARG, "null argument");
     AdjWork w;
-    *bytes = adjoint_tape_carve(g->c, nullptr, &w);
+    *bytes = adjoint_tape_carve(g->c, gp_bytes_of(g), nullptr, &w);
     return GKS_OK;
 }
 
@@ -944,7 +951,7 @@ int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, d
     }
     cc.state = w.lamP;
     launch_scatter_state(cc, d_adj_np1);
-    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt, g->adj_fp32);
+    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt);
     cc.state = w.lamW;
     launch_gather_state(cc, d_adj_n);
     // the reverse overwrote the Gauss-point inputs: the tape is consumed
@@ -979,7 +986,7 @@ int gks_step_record(gks_grid *g, void *d_tape, double *t_out)
     int rc = adjoint_check(g);
     if (rc) return rc;
     AdjWork w;
-    adjoint_tape_carve(g->c, d_tape, &w);
+    adjoint_tape_carve(g->c, gp_bytes_of(g), d_tape, &w);
     g->stepped = true;
     rc = step_once(g, &w);
     if (rc) return rc;
@@ -995,9 +1002,9 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
     int rc = adjoint_check(g);
     if (rc) return rc;
     AdjWork w;
-    adjoint_tape_carve(g->c, d_tape, &w);
+    adjoint_tape_carve(g->c, gp_bytes_of(g), d_tape, &w);
     adjoint_scratch_carve(g->c, total_points(g), d_scratch, &w);
-    double hdr[3];
+    double hdr[4];
     rc = cuda_check(g, cudaMemcpyAsync(hdr, w.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, g->c.stream), "read tape");
     if (!rc) rc = sync(g);
     if (rc) return rc;
@@ -1005,6 +1012,8 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
     memcpy(magic, hdr, sizeof(magic));
     for (unsigned char m : magic)
         if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded, or already reversed");
+    if (hdr[3] != (double)w.gp_bytes)
+        return fail(g, GKS_ERR_STATE, "tape recorded with another adjoint precision");
     return reverse_from_tape(g, w, true, hdr[1], hdr[2], d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
 }
 
@@ -1017,7 +1026,7 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     if (rc) return rc;
     const Ctx &c = g->c;
     AdjWork w;
-    adjoint_carve(c, total_points(g), d_adj_work, &w);
+    adjoint_carve(c, total_points(g), gp_bytes_of(g), d_adj_work, &w);
     const double dt = c.dt_fixed;
     // forward recompute of the step from W^n into the tape part of the
     // workspace, on private scalars (the grid's time and state stay as they
@@ -1025,9 +1034,10 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     Ctx cc = c;
     cc.mark = nullptr;
     cc.scal = w.sc;
-    const double hv[2] = {t_n, dt};
+    const double hv[3] = {t_n, dt, (double)w.gp_bytes};
     rc = cuda_check(g, cudaMemsetAsync(w.sc, 0, sizeof(Scalars), c.stream), "clear reverse scalars");
-    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&w.sc->t, hv, sizeof(hv), cudaMemcpyHostToDevice, c.stream), "set time");
+    if (!rc) rc = cuda_check(g, cudaMemcpyAsync(&w.sc->t, hv, 2 * sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                             "set time");
     if (!rc) rc = cuda_check(g, cudaMemcpyAsync(w.hdr + 1, hv, sizeof(hv), cudaMemcpyHostToDevice, c.stream),
                              "record time");
     if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.hdr, kTapeMagicByte, sizeof(double), c.stream), "mark tape");

@@ -65,9 +65,11 @@ struct Ctx {
     CUtensorMap tmap_dir[3];
     // Optional (FP64): per direction, the 64 Gauss-point inputs of every face
     // (16 g + k arrays of stride ngp; g Gauss point, k = Q0, normal slope, t1
-    // slope, t2 slope x 4 components), written by the flux kernels.
+    // slope, t2 slope x 4 components), written by the flux kernels as double
+    // (gp_bytes 8) or float (gp_bytes 4).
     void *gp_dir[3] = {nullptr, nullptr, nullptr};
     long ngp = 0;
+    int gp_bytes = 8;
     // Stage 2 of a step may prepare the next step (the FP32 input, max |U|^2
     // outside the forcing boxes, which are redone after the forcing).
     int prep_next = 0;
@@ -134,11 +136,12 @@ void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no proj
 constexpr unsigned char kTapeMagicByte = 0x5A;   // hdr[0] bytes of a recorded, unconsumed tape
 struct AdjWork {
     // tape
-    double *hdr;                                          // [0] magic, [1] t_n, [2] dt
+    double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes
     double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
     double *fqs[2][3];                                    // face boxes of the forward, per stage and direction
-    double *gps[2][3];                                    // Gauss-point inputs of the forward (64 nG each);
+    void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each);
                                                           // the reverse flux overwrites them with their adjoints
+    int gp_bytes;                                         // their storage: 8 (FP64 reverse) or 4 (FP32 reverse)
     long nG;                                              // component stride of gps
     // scratch
     double *lamA, *lamW, *lamP, *lamL, *lamLt;            // 4 * np each (padded indexing)
@@ -153,18 +156,19 @@ struct AdjWork {
 };
 // Offsets from base (0 to size them); each returns its bytes. The full
 // workspace of gks_step_adjoint is a tape followed by a scratch.
-size_t adjoint_tape_carve(const Ctx &c, void *base, AdjWork *w);
+size_t adjoint_tape_carve(const Ctx &c, int gp_bytes, void *base, AdjWork *w);
 size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
-size_t adjoint_bytes(const Ctx &c, long npts_total);
-size_t adjoint_carve(const Ctx &c, long npts_total, void *base, AdjWork *w);
+size_t adjoint_bytes(const Ctx &c, long npts_total, int gp_bytes);
+size_t adjoint_carve(const Ctx &c, long npts_total, int gp_bytes, void *base, AdjWork *w);
 // Runs the reverse of one step from its tape in w (A0, W* in w.Ws, Wp, the
 // face boxes and Gauss-point inputs of both stages; the rotor loads
 // recomputed from Wp); accumulates into the per-point scratch and w.scal[0].
 struct BodyDev;
-// fp32: FP32 arithmetic in the local reverse maps (flux, WENO5 pair,
-// equilibrium, transposed tangential passes), FP64 storage and sums.
+// The local reverse maps (flux, WENO5 pair, equilibrium, transposed
+// tangential passes) run in FP32 when the tape's Gauss-point inputs are
+// stored as float (w.gp_bytes 4), else in FP64; FP64 state adjoints and sums.
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1, bool fp32);
+                     double power_seed, double dt, double t_np1);
 
 // Immersed body (gks_forcing.cu).
 struct BodyDev {

@@ -212,8 +212,9 @@ template <typename R>
 struct FluxArgs {
     R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
     long nff;
-    R *gp;           // FP64 only, may be null: the 64 Gauss-point inputs per face (stride ngp)
+    void *gp;        // FP64 only, may be null: the 64 Gauss-point inputs per face (stride ngp)
     long ngp;
+    int gp32;        // gp holds float (else double)
     const R *ih1, *ih2;  // inverse cell widths along t1, t2 (padded index)
     int n1, n2, nf;
     int gcomp[4];        // global component of local component 0..3
@@ -303,11 +304,12 @@ __device__ __forceinline__ void tile_t1_pass(const R *sq, R *st, int tid)
 // t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g): the
 // sums of F0 and F1 over the 4 Gauss points of face (tx, ty) of the tile.
 // FP64 with gp set: the inputs of Gauss point g = 2m + n (Q0, normal slope,
-// t1 and t2 slopes, 4 components each) go to gp[(16 g + k) ngp + face].
+// t1 and t2 slopes, 4 components each) go to gp[(16 g + k) ngp + face], as
+// double or (gp32) rounded to float.
 template <typename R, bool NEED_F0>
 __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, int tx, int ty, R ih1, R ih2,
-                                                R acc0[4], R acc1[4], R *gp = nullptr, long ngp = 0,
-                                                long face = 0)
+                                                R acc0[4], R acc1[4], void *gp = nullptr, int gp32 = 0,
+                                                long ngp = 0, long face = 0)
 {
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc0[v] = acc1[v] = R(0);
@@ -328,16 +330,28 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
             Dn[0][v] = vm; Dn[1][v] = vp;
         }
         if constexpr (sizeof(R) == 8) {
-            if (gp) {
+            if (gp && !gp32) {
 #pragma unroll
                 for (int nn = 0; nn < 2; ++nn) {
-                    R *o = gp + (long)(16 * (2 * m + nn)) * ngp + face;
+                    R *o = (R *)gp + (long)(16 * (2 * m + nn)) * ngp + face;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         o[v * ngp] = Qv[nn][v];
                         o[(4 + v) * ngp] = Dn[nn][v];
                         o[(8 + v) * ngp] = D1[nn][v];
                         o[(12 + v) * ngp] = D2[nn][v];
+                    }
+                }
+            } else if (gp) {
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    float *o = (float *)gp + (long)(16 * (2 * m + nn)) * ngp + face;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        o[v * ngp] = (float)Qv[nn][v];
+                        o[(4 + v) * ngp] = (float)Dn[nn][v];
+                        o[(8 + v) * ngp] = (float)D1[nn][v];
+                        o[(12 + v) * ngp] = (float)D2[nn][v];
                     }
                 }
             }
@@ -409,7 +423,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
             R acc0[4], acc1[4];
             const long o = ((long)f * A.n2 + b) * A.n1 + a;
-            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.ngp, o);
+            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
@@ -652,7 +666,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         R F0[4], F1[4];
         if (in) {
             const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
-            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.ngp,
+            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.gp32, A.ngp,
                                         ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -804,8 +818,9 @@ void stage_impl(const Ctx &c)
         F.gcomp[3] = 1 + t2;
         F.ph = ph;
         F.scal = c.scal;
-        F.gp = (R *)c.gp_dir[d];
+        F.gp = c.gp_dir[d];
         F.ngp = c.ngp;
+        F.gp32 = c.gp_bytes == 4;
         const long ntiles = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY) * F.nf;
         const int grp = d < 2 ? K_FACE_FLUX : K_FLUX_UPDATE;
         mark(c, grp, 1);

@@ -248,6 +248,13 @@ def test_recorded_step_and_its_reverse(mods, rev):
     with pytest.raises(gks.GKSError) as e:
         g.step_reverse(torch.zeros_like(tape), scratch, lam1)
     assert e.value.code == -5
+    # a tape is reversed in the adjoint precision it was recorded with
+    g.set_state_tensor(W)
+    g.step_record(tape)
+    g.set_adjoint_precision("fp64" if rev == "fp32" else "fp32")
+    with pytest.raises(gks.GKSError) as e:
+        g.step_reverse(tape, g.adjoint_scratch(), lam1)
+    assert e.value.code == -5
     g.close()
 
 

@@ -273,11 +273,11 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
  * backward pass instead of twice.
  *   gks_adjoint_tape_bytes     bytes of one step's tape: t_n and dt, the
  *                              ghost-filled W^n and W*, the state before the
- *                              forcing, and per stage and direction the face
- *                              boxes and the 64 Gauss-point inputs of every
- *                              face, stored in the compute type of the reverse
- *                              (about 3.6 KB per cell with the FP64 adjoint
- *                              precision, 2.1 KB with FP32);
+ *                              forcing, and per stage and direction the 64
+ *                              Gauss-point inputs of every face, stored in
+ *                              the compute type of the reverse (about 3.2 KB
+ *                              per cell with the FP64 adjoint precision,
+ *                              1.7 KB with FP32);
  *   gks_adjoint_scratch_bytes  bytes of the scratch of gks_step_reverse
  *                              (the workspace of gks_step_adjoint is a tape
  *                              followed by a scratch);

@@ -8,8 +8,9 @@
 //    face flux: tangential quartic to the Gauss points + closed-form flux;
 //    divergence], the two stage combinations, the ALM forcing
 //   [trilinear sample, loads, truncated-Gaussian projection] and the IBM
-//   direct forcing. The forward recompute keeps each stage's and direction's
-//   face box and the Gauss-point inputs of every face. Its adjoint runs the
+//   direct forcing. The forward step (recorded, or recomputed from W^n)
+//   keeps the Gauss-point inputs of every face of each stage and direction.
+//   Its adjoint runs the
 //   pieces backwards. Every transposed stencil is written as a gather (each
 //   output sums its inputs in a fixed order), so the adjoint is
 //   deterministic and uses no atomics on the state:
@@ -318,8 +319,7 @@ __device__ __forceinline__ void equilibrium_rev_as(const Phys<double> &ph, const
 
 struct RevArgs {
     const double *A;          // forward working array (ghost-filled, padded)
-    const double *fq;         // forward face states of direction d
-    long nfq;
+    long nfq;                 // component stride of the face-box adjoints
     int e1p;
     const double *lamL, *lamLt;   // padded indexing; lamL may be null (stage 2)
     void *lamG;   // Gauss-point inputs / adjoints, stored in the reverse's compute type
@@ -944,7 +944,7 @@ __global__ void alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const lon
 // S^T: adjoint of the spatial operator of working array Aw (ghost-filled),
 // for lamL (may be null) and lamLt; result accumulated into w.lamA.
 template <typename T>
-void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *const fq[3], void *const gp[3],
+void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *const gp[3],
                      const double *lamL, const double *lamLt)
 {
     const Phys<double> ph = make_phys<double>(c);
@@ -952,7 +952,6 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, double *c
         const int t1 = tan1(d), t2 = tan2(d);
         RevArgs R;
         R.A = Aw;
-        R.fq = fq[d];   // face box of this direction, kept by the forward recompute
         R.nfq = c.nfq;
         R.e1p = c.e1p[d];
         R.lamL = lamL;
@@ -1091,7 +1090,6 @@ size_t adjoint_tape_carve(const Ctx &c, int gp_bytes, void *base, AdjWork *w)
     w->nG = nG;
     for (int st = 0; st < 2; ++st)
         for (int d = 0; d < 3; ++d) {
-            w->fqs[st][d] = k.take(8 * c.nfq);
             w->gps[st][d] = k.take(64 * nG * gp_bytes / 8);
         }
     return k.o;
@@ -1182,13 +1180,13 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial(c, w, w.Ws, w.fqs[1], w.gps[1], nullptr, w.lamLt);
+    spatial(c, w, w.Ws, w.gps[1], nullptr, w.lamLt);
     ghost_adjoint(c, w, w.Ws);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial(c, w, w.A0, w.fqs[0], w.gps[0], w.lamL, w.lamLt);
+    spatial(c, w, w.A0, w.gps[0], w.lamL, w.lamLt);
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }

@@ -601,25 +601,19 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
 namespace {
 int check_flags(gks_grid *g, int flags, const char *where);
 
-// Per stage st of a recorded step, the face boxes and Gauss-point inputs of
-// every direction go to the tape.
-int use_tape_faces(gks_grid *g, Ctx &cc, const AdjWork &w, int st)
+// Per stage st of a recorded step, the Gauss-point inputs of every
+// direction go to the tape.
+void use_tape_gauss(Ctx &cc, const AdjWork &w, int st)
 {
     cc.ngp = w.nG;
     cc.gp_bytes = w.gp_bytes;
-    for (int d = 0; d < 3; ++d) {
-        cc.fq_dir[d] = w.fqs[st][d];
-        cc.gp_dir[d] = w.gps[st][d];
-        std::string m;
-        if (encode_face_map(cc, d, w.fqs[st][d], &cc.tmap_dir[d], &m)) return fail(g, GKS_ERR_CUDA, m);
-    }
-    return GKS_OK;
+    for (int d = 0; d < 3; ++d) cc.gp_dir[d] = w.gps[st][d];
 }
 
 // One S2O4 step of the grid with its forcing. With a tape (FP64 grids) the
 // step also keeps what its reverse reads: t_n and dt, the ghost-filled W^n
-// and W*, the state before the forcing, and both stages' face boxes and
-// Gauss-point inputs; the arithmetic of the step is the same either way.
+// and W*, the state before the forcing, and both stages' Gauss-point
+// inputs; the arithmetic of the step is the same either way.
 int step_once(gks_grid *g, const AdjWork *tp)
 {
     Ctx &c = g->c;
@@ -640,13 +634,13 @@ int step_once(gks_grid *g, const AdjWork *tp)
                                  "record the tape's storage");
         if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->A0, c.wk0, bytes4, cudaMemcpyDeviceToDevice, c.stream),
                                  "record W^n");
-        if (!rc) rc = use_tape_faces(g, cc, *tp, 0);
         if (rc) return rc;
+        use_tape_gauss(cc, *tp, 0);
         cc.wk1 = tp->Ws;
     }
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
-    if (tp && (rc = use_tape_faces(g, cc, *tp, 1))) return rc;
+    if (tp) use_tape_gauss(cc, *tp, 1);
     // stage 2 also prepares the next step on every cell outside the forcing
     // boxes; the boxes are prepared again after the forcing
     if (fused_prep) {
@@ -1047,11 +1041,11 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     cc.wk1 = w.Ws;
     launch_scatter_state(cc, d_state_n);
     launch_ghost(cc, w.A0);
-    if ((rc = use_tape_faces(g, cc, w, 0))) return rc;
+    use_tape_gauss(cc, w, 0);
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
     cc.state = w.Wp;
-    if ((rc = use_tape_faces(g, cc, w, 1))) return rc;
+    use_tape_gauss(cc, w, 1);
     launch_stage(cc, 2);
     return reverse_from_tape(g, w, false, t_n, dt, d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
 }

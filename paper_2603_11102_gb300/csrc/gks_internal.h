@@ -59,10 +59,6 @@ struct Ctx {
     long nfq;
     int e1p[3];               // padded t1 extent of the face box per direction (multiple of 4)
     CUtensorMap tmap[3];      // TMA descriptors of the face box per direction
-    // Optional per-direction face boxes (the adjoint's forward recompute keeps
-    // all of them): when fq_dir[d] is set, direction d uses it and tmap_dir[d].
-    void *fq_dir[3] = {nullptr, nullptr, nullptr};
-    CUtensorMap tmap_dir[3];
     // Optional (FP64): per direction, the 64 Gauss-point inputs of every face
     // (16 g + k arrays of stride ngp; g Gauss point, k = Q0, normal slope, t1
     // slope, t2 slope x 4 components), written by the flux kernels as double
@@ -138,7 +134,6 @@ struct AdjWork {
     // tape
     double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes
     double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
-    double *fqs[2][3];                                    // face boxes of the forward, per stage and direction
     void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each);
                                                           // the reverse flux overwrites them with their adjoints
     int gp_bytes;                                         // their storage: 8 (FP64 reverse) or 4 (FP32 reverse)

@@ -783,7 +783,7 @@ void stage_impl(const Ctx &c)
         FaceEqArgs<R> E;
         E.w = w;
         E.np = c.np;
-        E.fq = (R *)(c.fq_dir[d] ? c.fq_dir[d] : c.fq);
+        E.fq = (R *)c.fq;
         E.nfq = c.nfq;
         E.ihf = (const R *)c.ihf[d];
         E.n1 = c.n[t1];
@@ -798,7 +798,7 @@ void stage_impl(const Ctx &c)
         E.ph = ph;
         E.nf = c.n[d] + 1;
         E.K = kMarch;
-        const CUtensorMap &tmap = c.fq_dir[d] ? c.tmap_dir[d] : c.tmap[d];
+        const CUtensorMap &tmap = c.tmap[d];
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
         mark(c, K_FACE_EQ, 1);
         face_eq_march_kernel<R><<<ge, blk, 0, c.stream>>>(E);

@@ -267,12 +267,12 @@ def time_adjoint(args, dev):
     iplane = int(round((5.0 - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
     npts = w.rotors[0].n_blades * len(w.rotors[0].r)
 
-    def run(steps, K, tape):
+    def run(steps, K, tape, grid=None):
         s = torch.ones(npts, dtype=torch.float64, requires_grad=True)
         u = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        J = adjoint.rotor_objective(g, s, u, steps, K=K, iplane=iplane, beta=1.0, tape=tape)
+        J = adjoint.rotor_objective(grid or g, s, u, steps, K=K, iplane=iplane, beta=1.0, tape=tape)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         J.backward()
@@ -300,6 +300,15 @@ def time_adjoint(args, dev):
             tape_gb[rev] = 0.0
         torch.cuda.empty_cache()
     g.close()
+    # the FP32C steps and their recorded reverse (FP32 arithmetic) on the same
+    # configuration
+    if args.adjoint_steps > 0:
+        g32 = gks.Grid.from_workload(w, precision="fp32c", device=dev)
+        run(args.adjoint_k, args.adjoint_k, "on", g32)
+        out["fp32c"] = run(args.adjoint_steps, args.adjoint_k, "on", g32)
+        tape_gb["fp32c"] = g32.adjoint_tape_bytes() / 1e9
+        g32.close()
+        torch.cuda.empty_cache()
     fwd, bwd, gu = out["fp32", "on"]
     res = {"workload": w.name + "-fp64", "steps": args.adjoint_steps, "checkpoint_every": args.adjoint_k,
            "warmup": "one untimed segment, forward and backward",
@@ -310,6 +319,12 @@ def time_adjoint(args, dev):
            "forward_ms_per_step": 1e3 * fwd / args.adjoint_steps,
            "objective": "plane-mean deficit at x = 5D + rotor power; gradient w.r.t. %d force scales and U_inf"
                         % npts, "grad_uinf": gu}
+    if "fp32c" in out:
+        f4, b4, g4 = out["fp32c"]
+        res["fp32c"] = {"forward_s": f4, "backward_s": b4, "ratio": b4 / f4,
+                        "forward_ms_per_step": 1e3 * f4 / args.adjoint_steps,
+                        "recorded_steps": "%d tapes of %.1f GB" % (args.adjoint_k, tape_gb["fp32c"]),
+                        "grad_uinf": g4, "grad_uinf_rel_diff_vs_fp64": abs(g4 - gu) / abs(gu)}
     if ("fp32", "off") in out:
         f2, b2, g2 = out["fp32", "off"]
         f3, b3, g3 = out["fp64", "on"]

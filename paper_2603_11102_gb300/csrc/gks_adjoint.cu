@@ -1124,6 +1124,10 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
     w->ptl = k.take(8 * np);
     w->scal = k.take(8);
     w->sc = (Scalars *)k.take((sizeof(Scalars) + 7) / 8);
+    for (int d = 0; d < 3; ++d) {
+        w->ih64[d] = k.take(c.P[d]);
+        w->ihf64[d] = k.take(c.n[d] + 1);
+    }
     return k.o;
 }
 

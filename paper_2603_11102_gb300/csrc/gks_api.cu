@@ -632,15 +632,23 @@ int step_once(gks_grid *g, const AdjWork *tp)
         const double gb = tp->gp_bytes;
         if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->hdr + 3, &gb, sizeof(double), cudaMemcpyHostToDevice, c.stream),
                                  "record the tape's storage");
-        if (!rc) rc = cuda_check(g, cudaMemcpyAsync(tp->A0, c.wk0, bytes4, cudaMemcpyDeviceToDevice, c.stream),
-                                 "record W^n");
         if (rc) return rc;
+        if (c.prec == GKS_FP64) {
+            rc = cuda_check(g, cudaMemcpyAsync(tp->A0, c.wk0, bytes4, cudaMemcpyDeviceToDevice, c.stream), "record W^n");
+            if (rc) return rc;
+            cc.wk1 = tp->Ws;
+        } else {
+            // FP32C: the FP32 input (rho - off) as FP64 with rho
+            launch_widen(c, (const float *)c.wk0, nullptr, tp->A0, 4 * c.np, c.np, c.off);
+        }
         use_tape_gauss(cc, *tp, 0);
-        cc.wk1 = tp->Ws;
     }
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
-    if (tp) use_tape_gauss(cc, *tp, 1);
+    if (tp) {
+        if (c.prec == GKS_FP32C) launch_widen(c, (const float *)c.wk1, nullptr, tp->Ws, 4 * c.np, c.np, c.off);
+        use_tape_gauss(cc, *tp, 1);
+    }
     // stage 2 also prepares the next step on every cell outside the forcing
     // boxes; the boxes are prepared again after the forcing
     if (fused_prep) {
@@ -652,9 +660,12 @@ int step_once(gks_grid *g, const AdjWork *tp)
         }
     }
     launch_stage(cc, 2);
-    if (tp && (rc = cuda_check(g, cudaMemcpyAsync(tp->Wp, c.state, bytes4, cudaMemcpyDeviceToDevice, c.stream),
-                               "record the state before the forcing")))
+    if (tp && c.prec == GKS_FP64 &&
+        (rc = cuda_check(g, cudaMemcpyAsync(tp->Wp, c.state, bytes4, cudaMemcpyDeviceToDevice, c.stream),
+                         "record the state before the forcing")))
         return rc;
+    if (tp && c.prec == GKS_FP32C)
+        launch_widen(c, (const float *)c.state, (const float *)c.state + 4 * c.np, tp->Wp, 4 * c.np, 0, 0.0);
     for (size_t k = 0; k < g->obj_kind.size(); ++k)
         if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
     for (size_t k = 0; k < g->obj_kind.size(); ++k)
@@ -865,13 +876,17 @@ long total_points(const gks_grid *g)
     return n;
 }
 
-// Storage of the tape's Gauss-point inputs: the compute type of the reverse.
-int gp_bytes_of(const gks_grid *g) { return g->adj_fp32 ? 4 : 8; }
+// Storage of the tape's Gauss-point inputs: the compute type of the reverse
+// (FP32 for the FP32 forward of FP32C grids).
+int gp_bytes_of(const gks_grid *g) { return (g->adj_fp32 || g->c.prec == GKS_FP32C) ? 4 : 8; }
 
-int adjoint_check(gks_grid *g)
+// tape_path: recorded steps, which also cover FP32C grids.
+int adjoint_check(gks_grid *g, bool tape_path)
 {
     const Ctx &c = g->c;
-    if (c.prec != GKS_FP64) return fail(g, GKS_ERR_STATE, "the adjoint needs a GKS_FP64 grid");
+    if (c.prec != GKS_FP64 && !(tape_path && c.prec == GKS_FP32C))
+        return fail(g, GKS_ERR_STATE, tape_path ? "bad grid precision for the adjoint"
+                                                : "gks_step_adjoint needs a GKS_FP64 grid (FP32C: recorded steps)");
     if (!(c.dt_fixed > 0.0)) return fail(g, GKS_ERR_STATE, "the adjoint needs a fixed time step (dt_fixed > 0)");
     for (const BodyDev &b : g->bodies)
         if (b.tol > 0.0)
@@ -929,6 +944,18 @@ int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, d
     cc.mark = nullptr;
     cc.scal = w.sc;
     cc.wk1 = w.Ws;
+    if (c.prec == GKS_FP32C) {
+        // the tape holds FP64 arrays with rho (not rho - off): the reverse
+        // runs as on an FP64 grid, with the FP32 inverse widths of the forward
+        cc.prec = GKS_FP64;
+        cc.off = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            launch_widen(cc, (const float *)c.ih[d], nullptr, w.ih64[d], c.P[d], 0, 0.0);
+            launch_widen(cc, (const float *)c.ihf[d], nullptr, w.ihf64[d], c.n[d] + 1, 0, 0.0);
+            cc.ih[d] = w.ih64[d];
+            cc.ihf[d] = w.ihf64[d];
+        }
+    }
     int rc = GKS_OK;
     if (init_sc) {
         rc = cuda_check(g, cudaMemsetAsync(w.sc, 0, sizeof(Scalars), c.stream), "clear reverse scalars");
@@ -977,7 +1004,7 @@ int gks_step_record(gks_grid *g, void *d_tape, double *t_out)
 {
     if (!g || !d_tape) return fail(g, GKS_ERR_ARG, "null argument");
     if ((uintptr_t)d_tape & 255) return fail(g, GKS_ERR_ARG, "tape must be 256-byte aligned");
-    int rc = adjoint_check(g);
+    int rc = adjoint_check(g, true);
     if (rc) return rc;
     AdjWork w;
     adjoint_tape_carve(g->c, gp_bytes_of(g), d_tape, &w);
@@ -993,7 +1020,7 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
     if (!g || !d_tape || !d_scratch || !d_adj_np1 || !d_adj_n) return fail(g, GKS_ERR_ARG, "null argument");
     if (((uintptr_t)d_tape | (uintptr_t)d_scratch) & 255)
         return fail(g, GKS_ERR_ARG, "tape and scratch must be 256-byte aligned");
-    int rc = adjoint_check(g);
+    int rc = adjoint_check(g, true);
     if (rc) return rc;
     AdjWork w;
     adjoint_tape_carve(g->c, gp_bytes_of(g), d_tape, &w);
@@ -1016,7 +1043,7 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
 {
     if (!g || !d_adj_work || !d_state_n || !d_adj_np1 || !d_adj_n) return fail(g, GKS_ERR_ARG, "null argument");
     if ((uintptr_t)d_adj_work & 255) return fail(g, GKS_ERR_ARG, "adjoint workspace must be 256-byte aligned");
-    int rc = adjoint_check(g);
+    int rc = adjoint_check(g, false);
     if (rc) return rc;
     const Ctx &c = g->c;
     AdjWork w;

@@ -107,6 +107,8 @@ void launch_gather_state(const Ctx &c, double *d_dst);         // state -> compa
 void launch_diagnostics(const Ctx &c, double *d_out5);
 void launch_fill_rest(const Ctx &c);                            // rho = 1, momentum 0
 void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored arrays <-> compact
+// out[i] = a[i] (+ b[i] if b) (+ off0 for i < n0), FP32 -> FP64, i < n
+void launch_widen(const Ctx &c, const float *a, const float *b, double *out, long n, long n0, double off0);
 
 // Actuator line (gks_forcing.cu).
 struct RotorDev {
@@ -148,6 +150,7 @@ struct AdjWork {
     double *ptc, *ptl;                                    // sampling-adjoint corner values (32) and cells (8, as long)
     double *scal;                                         // [0] grad U_inf (device accumulator)
     Scalars *sc;                                          // private time, dt and flags of the reverse
+    double *ih64[3], *ihf64[3];                           // FP64 inverse widths (FP32C grids)
 };
 // Offsets from base (0 to size them); each returns its bytes. The full
 // workspace of gks_step_adjoint is a tape followed by a scratch.

@@ -303,10 +303,11 @@ __device__ __forceinline__ void tile_t1_pass(const R *sq, R *st, int tid)
 
 // t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g): the
 // sums of F0 and F1 over the 4 Gauss points of face (tx, ty) of the tile.
-// FP64 with gp set: the inputs of Gauss point g = 2m + n (Q0, normal slope,
-// t1 and t2 slopes, 4 components each) go to gp[(16 g + k) ngp + face], as
-// double or (gp32) rounded to float.
-template <typename R, bool NEED_F0>
+// GP (the recorded steps of the adjoint) with gp set: the inputs of Gauss
+// point g = 2m + n (Q0 with its density as rho, not rho - off; normal slope,
+// t1 and t2 slopes; 4 components each) go to gp[(16 g + k) ngp + face], as
+// double or (gp32) rounded to float (always float for R = float).
+template <typename R, bool NEED_F0, bool GP = false>
 __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, int tx, int ty, R ih1, R ih2,
                                                 R acc0[4], R acc1[4], void *gp = nullptr, int gp32 = 0,
                                                 long ngp = 0, long face = 0)
@@ -329,29 +330,32 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
             tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
             Dn[0][v] = vm; Dn[1][v] = vp;
         }
-        if constexpr (sizeof(R) == 8) {
-            if (gp && !gp32) {
+        if (GP && gp) {
 #pragma unroll
-                for (int nn = 0; nn < 2; ++nn) {
-                    R *o = (R *)gp + (long)(16 * (2 * m + nn)) * ngp + face;
+            for (int nn = 0; nn < 2; ++nn) {
+                const long o = (long)(16 * (2 * m + nn)) * ngp + face;
+                const R q0 = Qv[nn][0] + ph.off;
+                if (sizeof(R) == 8 && !gp32) {
+                    R *p = (R *)gp + o;
+                    p[0] = q0;
+#pragma unroll
+                    for (int v = 1; v < 4; ++v) p[v * ngp] = Qv[nn][v];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        o[v * ngp] = Qv[nn][v];
-                        o[(4 + v) * ngp] = Dn[nn][v];
-                        o[(8 + v) * ngp] = D1[nn][v];
-                        o[(12 + v) * ngp] = D2[nn][v];
+                        p[(4 + v) * ngp] = Dn[nn][v];
+                        p[(8 + v) * ngp] = D1[nn][v];
+                        p[(12 + v) * ngp] = D2[nn][v];
                     }
-                }
-            } else if (gp) {
+                } else {
+                    float *p = (float *)gp + o;
+                    p[0] = (float)q0;
 #pragma unroll
-                for (int nn = 0; nn < 2; ++nn) {
-                    float *o = (float *)gp + (long)(16 * (2 * m + nn)) * ngp + face;
+                    for (int v = 1; v < 4; ++v) p[v * ngp] = (float)Qv[nn][v];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        o[v * ngp] = (float)Qv[nn][v];
-                        o[(4 + v) * ngp] = (float)Dn[nn][v];
-                        o[(8 + v) * ngp] = (float)D1[nn][v];
-                        o[(12 + v) * ngp] = (float)D2[nn][v];
+                        p[(4 + v) * ngp] = (float)Dn[nn][v];
+                        p[(8 + v) * ngp] = (float)D1[nn][v];
+                        p[(12 + v) * ngp] = (float)D2[nn][v];
                     }
                 }
             }
@@ -372,7 +376,7 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of the next tile is fetched by TMA into the other buffer while the
 // current one is computed.
-template <typename R, bool NEED_F0>
+template <typename R, bool NEED_F0, bool GP>
 __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
             R acc0[4], acc1[4];
             const long o = ((long)f * A.n2 + b) * A.n1 + a;
-            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
+            tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
@@ -561,7 +565,7 @@ __device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int L, int nf)
     return z;
 }
 
-template <typename R, int STAGE>
+template <typename R, int STAGE, bool GP>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A, UpdArgs<R> U)
 {
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         R F0[4], F1[4];
         if (in) {
             const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
-            tile_gauss_flux<R, NEED_F0>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.gp32, A.ngp,
+            tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.gp32, A.ngp,
                                         ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -737,16 +741,19 @@ int persistent_grid(K kernel, size_t smem)
 
 template <typename R, int STAGE>
 struct FluxGrids {
-    int flux = 0, flux_update = 0;
+    int flux[2] = {0, 0}, flux_update[2] = {0, 0};   // without / with the Gauss-point output
 };
 
 template <typename R, int STAGE>
 const FluxGrids<R, STAGE> &flux_grids()
 {
     static FluxGrids<R, STAGE> g;
-    if (!g.flux) {
-        g.flux = persistent_grid(face_flux_kernel<R, STAGE == 1>, flux_smem_bytes<R>());
-        g.flux_update = persistent_grid(flux_update_kernel<R, STAGE>, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4));
+    if (!g.flux[0]) {
+        constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
+        g.flux[0] = persistent_grid(face_flux_kernel<R, STAGE == 1, false>, flux_smem_bytes<R>());
+        g.flux[1] = persistent_grid(face_flux_kernel<R, STAGE == 1, true>, flux_smem_bytes<R>());
+        g.flux_update[0] = persistent_grid(flux_update_kernel<R, STAGE, false>, su);
+        g.flux_update[1] = persistent_grid(flux_update_kernel<R, STAGE, true>, su);
     }
     return g;
 }
@@ -824,9 +831,13 @@ void stage_impl(const Ctx &c)
         const long ntiles = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY) * F.nf;
         const int grp = d < 2 ? K_FACE_FLUX : K_FLUX_UPDATE;
         mark(c, grp, 1);
+        const int gpo = F.gp != nullptr;
         if (d < 2) {
-            const int grid = (int)(ntiles < grids.flux ? ntiles : grids.flux);
-            face_flux_kernel<R, STAGE == 1><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+            const int grid = (int)(ntiles < grids.flux[gpo] ? ntiles : grids.flux[gpo]);
+            if (gpo)
+                face_flux_kernel<R, STAGE == 1, true><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+            else
+                face_flux_kernel<R, STAGE == 1, false><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
         } else {
             // z faces: flux and the stage update of every cell
             UpdArgs<R> U;
@@ -848,7 +859,7 @@ void stage_impl(const Ctx &c)
             U.off = (R)c.off;
             for (int a = 0; a < 3; ++a) U.fb[a] = (R)c.fbody[a];
             const int ncol = ((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY);
-            U.seg = z_segment(ncol, F.nf, grids.flux_update);
+            U.seg = z_segment(ncol, F.nf, grids.flux_update[gpo]);
             U.prep = STAGE == 2 && c.prep_next && c.nprep_box <= kMaxPrepBoxes;
             U.wk0n = c.prec == GKS_FP32C ? (float *)c.wk0 : nullptr;
             U.nbox = U.prep ? c.nprep_box : 0;
@@ -856,9 +867,12 @@ void stage_impl(const Ctx &c)
                 for (int e = 0; e < 3; ++e)
                     for (int f2 = 0; f2 < 2; ++f2) U.box[q][e][f2] = c.prep_box[q][e][f2];
             const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
-            const int grid = (int)(nitems < grids.flux_update ? nitems : grids.flux_update);
-            flux_update_kernel<R, STAGE><<<grid, blk, flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4), c.stream>>>(
-                tmap, F, U);
+            const int grid = (int)(nitems < grids.flux_update[gpo] ? nitems : grids.flux_update[gpo]);
+            constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
+            if (gpo)
+                flux_update_kernel<R, STAGE, true><<<grid, blk, su, c.stream>>>(tmap, F, U);
+            else
+                flux_update_kernel<R, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
         }
         mark(c, grp, 0);
     }
@@ -1187,6 +1201,26 @@ void launch_raw_copy(const Ctx &c, void *compact, int to_compact)
         raw_copy_kernel<float><<<g, blk, 0, c.stream>>>((float *)c.state, (float *)compact, 8, c.np,
                                                         c.n[0], c.n[1], c.n[2], c.P[0], c.P[1],
                                                         to_compact);
+}
+
+// FP32 values as FP64: out[i] = a[i] (+ b[i]) (+ off0 for i < n0), i < n.
+__global__ void __launch_bounds__(256) widen_kernel(const float *a, const float *b, double *out, long n, long n0,
+                                                     double off0)
+{
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < n; i += (long)gridDim.x * 256L) {
+        double v = (double)a[i];
+        if (b) v += (double)b[i];
+        if (i < n0) v += off0;
+        out[i] = v;
+    }
+}
+
+void launch_widen(const Ctx &c, const float *a, const float *b, double *out, long n, long n0, double off0)
+{
+    mark(c, K_MISC, 1);
+    const long nb = (n + 255) / 256;
+    widen_kernel<<<(int)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, c.stream>>>(a, b, out, n, n0, off0);
+    mark(c, K_MISC, 0);
 }
 
 void launch_diagnostics(const Ctx &c, double *d_out5)

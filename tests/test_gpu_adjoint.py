@@ -92,16 +92,25 @@ def forward_step(g, torch, W, t_n, scales=None, uinf=None):
     return out, P
 
 
-@pytest.mark.parametrize("rev", ["fp64", "fp32"])
+@pytest.mark.parametrize("rev", ["fp64", "fp32", "fp32c"])
 @pytest.mark.parametrize("case", ["rotor", "walls", "rotor_body", "rotor_corrections"])
 def test_one_step_adjoint_matches_central_differences(mods, case, rev):
-    """rev: arithmetic of the local reverse maps (FP64 within 1e-5 of the
-    central differences; FP32 within 1e-4)."""
+    """rev: arithmetic of the local reverse maps of the FP64 step (FP64 within
+    1e-5 of the central differences of the FP64 step; FP32 within 1e-4), or
+    fp32c: the recorded FP32C step and its reverse (FP32 arithmetic), against
+    the central differences of the FP64 step: within 1e-4 for the inflow
+    speed and the force scales. In the state direction the inner product
+    <lambda^n, dW> of this random direction nearly cancels (|sum| ~ 1 against
+    terms of total magnitude ~1e4), so the FP32C adjoint, whose elements sit
+    within ~1e-5 of the FP64 step's adjoint (FP32 flux arithmetic: its slopes
+    are small differences of O(1) values), is held to 1e-6 of the summed
+    magnitude of the terms, and element by element to 3e-5 of the FP64
+    step's adjoint."""
     gks, adjoint, torch = mods
     w = {"rotor": rotor_box_workload, "walls": walls_workload, "rotor_body": rotor_body_workload,
          "rotor_corrections": rotor_corrections_workload}[case]()
     g = gks.Grid.from_workload(w, precision="fp64")
-    g.set_adjoint_precision(rev)
+    g.set_adjoint_precision("fp32" if rev == "fp32c" else rev)
     tol = 1e-5 if rev == "fp64" else 1e-4
     W = torch.tensor(perturbed_state(w, 3), dtype=torch.float64, device="cuda")
     rng = np.random.default_rng(5)
@@ -116,12 +125,24 @@ def test_one_step_adjoint_matches_central_differences(mods, case, rev):
         out, P = forward_step(g, torch, Wx, t_n, s if npts else None, u)
         return float((lam1 * out).sum().item()) + beta * P
 
-    work = g.adjoint_workspace()
-    if npts:
-        g.set_force_scales(0, s0)
-    g.set_inflow(1.0, u0, 0.0, 0.0)
     gs = np.zeros(max(npts, 1))
-    lam0, gu = g.step_adjoint(work, t_n, W, lam1, beta, gs if npts else None)
+    if rev == "fp32c":
+        ga = gks.Grid.from_workload(w, precision="fp32c")
+        if npts:
+            ga.set_force_scales(0, s0)
+        ga.set_inflow(1.0, u0, 0.0, 0.0)
+        ga.set_state_tensor(W)
+        ga.set_time(t_n)
+        tape = ga.adjoint_tape()
+        ga.step_record(tape)
+        lam0, gu = ga.step_reverse(tape, ga.adjoint_scratch(), lam1, beta, gs if npts else None)
+        ga.close()
+    else:
+        work = g.adjoint_workspace()
+        if npts:
+            g.set_force_scales(0, s0)
+        g.set_inflow(1.0, u0, 0.0, 0.0)
+        lam0, gu = g.step_adjoint(work, t_n, W, lam1, beta, gs if npts else None)
 
     # state direction. The WENO weights of this noisy state sit in the
     # beta ~ eps_w regime, where they bend on a 1e-3 scale: the central
@@ -131,7 +152,13 @@ def test_one_step_adjoint_matches_central_differences(mods, case, rev):
     h = 1e-7
     fd = (J(W + h * dW, s0, u0) - J(W - h * dW, s0, u0)) / (2 * h)
     ad = float((lam0 * dW).sum().item())
-    assert abs(fd - ad) <= tol * max(abs(ad), 1e-12), (fd, ad)
+    if rev == "fp32c":
+        mag = float((lam0 * dW).abs().sum().item())
+        assert abs(fd - ad) <= 1e-6 * mag, (fd, ad, mag)
+        ref, _ = g.step_adjoint(g.adjoint_workspace(), t_n, W, lam1, beta, None)
+        assert float((lam0 - ref).abs().max()) <= 3e-5 * float(ref.abs().max())
+    else:
+        assert abs(fd - ad) <= tol * max(abs(ad), 1e-12), (fd, ad)
     # inflow speed
     fdu = (J(W, s0, u0 + h) - J(W, s0, u0 - h)) / (2 * h)
     assert abs(fdu - gu) <= tol * max(abs(fdu), 1e-3), (fdu, gu)
@@ -156,14 +183,18 @@ def oracle_objective(w, s, u, nsteps, iplane, beta):
     return float(np.mean(u - A[1, :, :, iplane] / A[0, :, :, iplane])) + beta * o.forces(0)["power"]
 
 
-@pytest.mark.parametrize("rev", ["fp64", "fp32"])
+@pytest.mark.parametrize("rev", ["fp64", "fp32", "fp32c"])
 @pytest.mark.parametrize("case", ["rotor", "rotor_body", "rotor_corrections"])
 def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
+    """rev as in the one-step test; fp32c: the gradient of the FP32C
+    rollout (recorded steps), checked against central differences of the
+    FP64 rollout and of the oracle."""
     gks, adjoint, torch = mods
     w = {"rotor": rotor_box_workload, "rotor_body": rotor_body_workload,
          "rotor_corrections": rotor_corrections_workload}[case]()
-    g = gks.Grid.from_workload(w, precision="fp64")
-    g.set_adjoint_precision(rev)
+    g = gks.Grid.from_workload(w, precision="fp32c" if rev == "fp32c" else "fp64")
+    g.set_adjoint_precision("fp32" if rev == "fp32c" else rev)
+    gfd = gks.Grid.from_workload(w, precision="fp64") if rev == "fp32c" else g
     N, K, beta = 6, 2, 1.0
     iplane = 20          # x index downstream of the rotor
     npts = 18
@@ -172,15 +203,16 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
     J = adjoint.rotor_objective(g, s, u, N, K=K, iplane=iplane, beta=beta, tape="on")
     J.backward()
     gs, gu = s.grad.numpy().copy(), float(u.grad)
-    # recorded steps and per-step recomputation give the same gradient
-    s2 = torch.ones(npts, dtype=torch.float64, requires_grad=True)
-    u2 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    adjoint.rotor_objective(g, s2, u2, N, K=K, iplane=iplane, beta=beta, tape="off").backward()
-    assert np.max(np.abs(s2.grad.numpy() - gs)) <= 1e-12 * np.max(np.abs(gs))
-    assert abs(float(u2.grad) - gu) <= 1e-12 * abs(gu)
+    if rev != "fp32c":
+        # recorded steps and per-step recomputation give the same gradient
+        s2 = torch.ones(npts, dtype=torch.float64, requires_grad=True)
+        u2 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        adjoint.rotor_objective(g, s2, u2, N, K=K, iplane=iplane, beta=beta, tape="off").backward()
+        assert np.max(np.abs(s2.grad.numpy() - gs)) <= 1e-12 * np.max(np.abs(gs))
+        assert abs(float(u2.grad) - gu) <= 1e-12 * abs(gu)
 
     def Jgpu(sv, uv):
-        return float(adjoint.rotor_objective(g, torch.tensor(sv, dtype=torch.float64),
+        return float(adjoint.rotor_objective(gfd, torch.tensor(sv, dtype=torch.float64),
                                              torch.tensor(uv, dtype=torch.float64), N, K=K, iplane=iplane,
                                              beta=beta))
 
@@ -272,8 +304,11 @@ def test_adjoint_rejects_unsupported_grids(mods):
     with pytest.raises(gks.GKSError) as e:
         g2.step_adjoint(g2.adjoint_workspace(), 0.0, W, W)
     assert e.value.code == -5
+    w2 = rotor_box_workload()
+    w2.dt_fixed = 0.0
+    g5 = gks.Grid.from_workload(w2, precision="fp32c")
     with pytest.raises(gks.GKSError) as e:
-        g2.step_record(g.adjoint_tape())
+        g5.step_record(g5.adjoint_tape())
     assert e.value.code == -5
     w4 = rotor_body_workload()
     w4.bodies[0].tol = 0.05

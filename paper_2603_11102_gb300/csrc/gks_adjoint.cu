@@ -319,14 +319,18 @@ __device__ __forceinline__ void equilibrium_rev_as(const Phys<double> &ph, const
 
 struct RevArgs {
     const double *A;          // forward working array (ghost-filled, padded)
+    const float *Ahi, *Alo;   // FP32 reverse: A as hi + lo floats
     long nfq;                 // component stride of the face-box adjoints
     int e1p;
     const double *lamL, *lamLt;   // padded indexing; lamL may be null (stage 2)
-    void *lamG;   // Gauss-point inputs / adjoints, stored in the reverse's compute type
+    // adjoints inside the spatial adjoint of one direction, stored in the
+    // reverse's compute type: Gauss-point inputs (replaced by their adjoints),
+    // t1-pass rows, face boxes, per-face cell slots
+    void *lamG;
     long nG;
-    double *lamR;
+    void *lamR;
     long nR;
-    double *lamFQ, *lamC;
+    void *lamFQ, *lamC;
     double *lamA;
     const double *ihd, *ih1, *ih2, *ihf;
     int n[3], P[3];
@@ -345,29 +349,24 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     if (a >= A.n1 || b >= A.n2) return;
     // adjoint of the face-averaged fluxes from the two neighbour cells
     const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
-    double lF0[4] = {0, 0, 0, 0}, lF1[4] = {0, 0, 0, 0};
+    T sF0[4] = {0, 0, 0, 0}, sF1[4] = {0, 0, 0, 0};
     int cl[3], cr[3];
     cl[A.d] = f - 1; cl[A.t1] = a; cl[A.t2] = b;
     cr[A.d] = f; cr[A.t1] = a; cr[A.t2] = b;
     const bool hasl = f - 1 >= 0, hasr = f < A.nd;
     const long il = lin(A.P[0], A.P[1], cl[0], cl[1], cl[2]), ir = lin(A.P[0], A.P[1], cr[0], cr[1], cr[2]);
-    const double ihl = hasl ? A.ihd[f - 1 + G] : 0.0, ihr = hasr ? A.ihd[f + G] : 0.0;
+    const T ihl = hasl ? T(A.ihd[f - 1 + G]) : T(0), ihr = hasr ? T(A.ihd[f + G]) : T(0);
     for (int v = 0; v < 4; ++v) {
         const long o = gc[v] * A.np;
-        const double ll = hasl ? A.lamLt[o + il] : 0.0, lr = hasr ? A.lamLt[o + ir] : 0.0;
-        lF1[v] = 0.25 * (-ll * ihl + lr * ihr);
+        const T ll = hasl ? T(A.lamLt[o + il]) : T(0), lr = hasr ? T(A.lamLt[o + ir]) : T(0);
+        sF1[v] = T(0.25) * (-ll * ihl + lr * ihr);
         if (A.lamL) {
-            const double ml = hasl ? A.lamL[o + il] : 0.0, mr = hasr ? A.lamL[o + ir] : 0.0;
-            lF0[v] = 0.25 * (-ml * ihl + mr * ihr);
+            const T ml = hasl ? T(A.lamL[o + il]) : T(0), mr = hasr ? T(A.lamL[o + ir]) : T(0);
+            sF0[v] = T(0.25) * (-ml * ihl + mr * ihr);
         }
     }
     const T ih1 = T(A.ih1[a + G]), ih2 = T(A.ih2[b + G]);
     const Phys<T> ph = phys_as<T>(A.ph);
-    T sF0[4], sF1[4];
-    for (int v = 0; v < 4; ++v) {
-        sF0[v] = T(lF0[v]);
-        sF1[v] = T(lF1[v]);
-    }
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
     for (int g = 0; g < 4; ++g) {
         T *io = (T *)A.lamG + (long)(16 * g) * A.nG + face;
@@ -446,9 +445,10 @@ __global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
             }
         }
         const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
-        A.lamR[(0 * 8 + m * 4 + v) * A.nR + row] = (double)X;
-        A.lamR[(1 * 8 + m * 4 + v) * A.nR + row] = (double)Y;
-        A.lamR[(2 * 8 + m * 4 + v) * A.nR + row] = (double)Z;
+        T *lr = (T *)A.lamR;
+        lr[(0 * 8 + m * 4 + v) * A.nR + row] = X;
+        lr[(1 * 8 + m * 4 + v) * A.nR + row] = Y;
+        lr[(2 * 8 + m * 4 + v) * A.nR + row] = Z;
     }
 }
 
@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
     const int f = blockIdx.z;
     if (ap >= A.n1 + 2 || bp >= A.n2 + 2) return;
     T lq[4] = {0, 0, 0, 0}, ln[4] = {0, 0, 0, 0};
+    const T *lr = (const T *)A.lamR;
     const int alo = ap - 2 < 0 ? 0 : ap - 2, ahi = ap + 2 > A.n1 - 1 ? A.n1 - 1 : ap + 2;
     for (int a = alo; a <= ahi; ++a) {
         const int r = ap - a + 2;
@@ -467,16 +468,16 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
         for (int m = 0; m < 2; ++m) {
             const T wv = T(cWV[m][r]), wd = T(cWD[m][r]);
             for (int v = 0; v < 4; ++v) {
-                lq[v] += wv * T(A.lamR[(0 * 8 + m * 4 + v) * A.nR + row]) +
-                         wd * T(A.lamR[(1 * 8 + m * 4 + v) * A.nR + row]);
-                ln[v] += wv * T(A.lamR[(2 * 8 + m * 4 + v) * A.nR + row]);
+                lq[v] += wv * lr[(0 * 8 + m * 4 + v) * A.nR + row] + wd * lr[(1 * 8 + m * 4 + v) * A.nR + row];
+                ln[v] += wv * lr[(2 * 8 + m * 4 + v) * A.nR + row];
             }
         }
     }
     const long o = ((long)f * (A.n2 + 4) + (bp + 2)) * A.e1p + (ap + 2);
+    T *fq = (T *)A.lamFQ;
     for (int v = 0; v < 4; ++v) {
-        A.lamFQ[v * A.nfq + o] = (double)lq[v];
-        A.lamFQ[(4 + v) * A.nfq + o] = (double)ln[v];
+        fq[v * A.nfq + o] = lq[v];
+        fq[(4 + v) * A.nfq + o] = ln[v];
     }
 }
 
@@ -490,9 +491,11 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
 // per face side.
 constexpr int kRevMarch = 16;
 
-template <typename T>
 __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
 {
+    using T = double;
+    const double *lamFQ = (const double *)A.lamFQ;
+    double *lamC = (double *)A.lamC;
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
     const int nf = A.nd + 1, f0 = blockIdx.z * kRevMarch;
     if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= nf) return;
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
             const long o = ((long)(f0 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
             double Q0b[4], Qlb[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) Q0b[v] = A.lamFQ[v * A.nfq + o];
+            for (int v = 0; v < 4; ++v) Q0b[v] = lamFQ[v * A.nfq + o];
             equilibrium_rev_as<T>(A.ph, Rpp, lft, Q0b, Qlb, Sprev);
         }
     }
@@ -549,8 +552,8 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
         double Q0b[4], DNb[4], Qlb[4], Qrb[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            Q0b[v] = A.lamFQ[v * A.nfq + o];
-            DNb[v] = A.lamFQ[(4 + v) * A.nfq + o];
+            Q0b[v] = lamFQ[v * A.nfq + o];
+            DNb[v] = lamFQ[(4 + v) * A.nfq + o];
         }
         equilibrium_rev_as<T>(A.ph, Ql, Qr, Q0b, Qlb, Qrb);
         const double s = A.ihf[f] * (1.0 / 12.0);
@@ -564,32 +567,162 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
             pair_rev<T>(&w[v][0], Qlb[v], Sprev[v], &cb[0]);      // cell f-1
             if (f == nf - 1) pair_rev<T>(&w[v][1], 0.0, Qrb[v], &cb[1]);   // cell f, left value only
 #pragma unroll
-            for (int m = 0; m < 6; ++m) A.lamC[(m * 4 + v) * A.nfq + o] = cb[m];
+            for (int m = 0; m < 6; ++m) lamC[(m * 4 + v) * A.nfq + o] = cb[m];
             Rprev[v] = Rt[v];
             Sprev[v] = Qrb[v];
         }
     }
 }
 
+// The WENO5 pair in FP32 of 5 cells given as hi + lo floats, on the cells
+// minus the centre cell: (hi_k - hi_2) + (lo_k - lo_2) keeps the precision of
+// the FP64 differences (the hi difference of nearby values is exact).
+__device__ __forceinline__ void diffs32(const float hi[5], const float lo[5], float qs[5])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qs[k] = (hi[k] - hi[2]) + (lo[k] - lo[2]);
+}
+
+__device__ __forceinline__ void pair_values32(const float hi[5], const float lo[5], float &right, float &left)
+{
+    float qs[5], r, l;
+    diffs32(hi, lo, qs);
+    weno5_pair(qs, r, l);
+    right = hi[2] + (lo[2] + r);
+    left = hi[2] + (lo[2] + l);
+}
+
+__device__ __forceinline__ void pair_rev32(const float hi[5], const float lo[5], float sR, float sL, float out[5])
+{
+    float qs[5];
+    diffs32(hi, lo, qs);
+    weno5_pair_rev<float>(qs, sR, sL, out);
+}
+
+// RD in FP32 (the FP32 reverse): the same march as rev_face_state_kernel on
+// the working array split into hi + lo floats, with FP32 face-box adjoints in
+// and FP32 cell slots out.
+__global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
+{
+    const float *lamFQ = (const float *)A.lamFQ;
+    float *lamC = (float *)A.lamC;
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int nf = A.nd + 1, f0 = blockIdx.z * kRevMarch;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= nf) return;
+    const int f1 = min(f0 + kRevMarch, nf);
+    const long stride[3] = {1, (long)A.P[0], (long)A.P[0] * A.P[1]};
+    const long sd = stride[A.d];
+    int cc[3];
+    cc[A.d] = 0; cc[A.t1] = a; cc[A.t2] = b;
+    const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    const Phys<float> ph = phys_as<float>(A.ph);
+    float wh[4][6], wl[4][6];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int cell = f0 - 4 + k;
+            const long l = comp[v] * A.np + base + (long)cell * sd;
+            wh[v][k] = cell >= -G ? A.Ahi[l] : 0.0f;
+            wl[v][k] = cell >= -G ? A.Alo[l] : 0.0f;
+        }
+    float Rprev[4], Sprev[4];
+    {
+        float lft[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) pair_values32(&wh[v][1], &wl[v][1], Rprev[v], lft[v]);   // cell f0-1
+        if (f0 == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Sprev[v] = 0.0f;
+        } else {
+            float Rpp[4], dum;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pair_values32(&wh[v][0], &wl[v][0], Rpp[v], dum);    // cell f0-2
+            const long o = ((long)(f0 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+            float Q0b[4], Qlb[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Q0b[v] = lamFQ[v * A.nfq + o];
+            equilibrium_rev<float>(ph, Rpp, lft, Q0b, Qlb, Sprev);
+        }
+    }
+    for (int f = f0; f < f1; ++f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                wh[v][k] = wh[v][k + 1];
+                wl[v][k] = wl[v][k + 1];
+            }
+            const long l = comp[v] * A.np + base + (long)(f + 2) * sd;
+            wh[v][5] = A.Ahi[l];
+            wl[v][5] = A.Alo[l];
+        }
+        float Ql[4], Qr[4], Rt[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Ql[v] = Rprev[v];
+            pair_values32(&wh[v][1], &wl[v][1], Rt[v], Qr[v]);   // cell f
+        }
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+        float Q0b[4], DNb[4], Qlb[4], Qrb[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Q0b[v] = lamFQ[v * A.nfq + o];
+            DNb[v] = lamFQ[(4 + v) * A.nfq + o];
+        }
+        equilibrium_rev<float>(ph, Ql, Qr, Q0b, Qlb, Qrb);
+        const float s = (float)(A.ihf[f] * (1.0 / 12.0));
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float cb[6] = {0, 0, 0, 0, 0, 0};
+            const float ds = DNb[v] * s;
+            cb[1] += ds;
+            cb[2] -= 15.0f * ds;
+            cb[3] += 15.0f * ds;
+            cb[4] -= ds;
+            pair_rev32(&wh[v][0], &wl[v][0], Qlb[v], Sprev[v], &cb[0]);      // cell f-1
+            if (f == nf - 1) pair_rev32(&wh[v][1], &wl[v][1], 0.0f, Qrb[v], &cb[1]);   // cell f, left value only
+#pragma unroll
+            for (int m = 0; m < 6; ++m) lamC[(m * 4 + v) * A.nfq + o] = cb[m];
+            Rprev[v] = Rt[v];
+            Sprev[v] = Qrb[v];
+        }
+    }
+}
+
+// A (FP64) as hi + lo floats for the FP32 face-state reverse.
+__global__ void __launch_bounds__(256) split_kernel(const double *A, float *hi, float *lo, long n)
+{
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < n; i += (long)gridDim.x * 256L) {
+        const double x = A[i];
+        const float h = (float)x;
+        hi[i] = h;
+        lo[i] = (float)(x - (double)h);
+    }
+}
+
 // RE: gather, per cell of the padded box along d and the extended
 // tangential box, the contributions of the 6 faces whose stencil holds it.
+template <typename T>
 __global__ void __launch_bounds__(256) rev_gather_cells_kernel(RevArgs A)
 {
+    const T *lamC = (const T *)A.lamC;
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
     const int c = (int)blockIdx.z - G;
     if (a >= A.n1 + 2 || b >= A.n2 + 2) return;
     const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
-    double acc[4] = {0, 0, 0, 0};
+    T acc[4] = {0, 0, 0, 0};
     const int flo = c - 2 < 0 ? 0 : c - 2, fhi = c + 3 > A.nd ? A.nd : c + 3;
     for (int f = flo; f <= fhi; ++f) {
         const int m = c - f + 3;
         const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
-        for (int v = 0; v < 4; ++v) acc[v] += A.lamC[(m * 4 + v) * A.nfq + o];
+        for (int v = 0; v < 4; ++v) acc[v] += lamC[(m * 4 + v) * A.nfq + o];
     }
     int cc[3];
     cc[A.d] = c; cc[A.t1] = a; cc[A.t2] = b;
     const long l = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
-    for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + l] += acc[v];
+    for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + l] += (double)acc[v];
 }
 
 // Ghost adjoint of one (axis, side, layer): the ghost's adjoint goes to its
@@ -948,10 +1081,18 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
                      const double *lamL, const double *lamLt)
 {
     const Phys<double> ph = make_phys<double>(c);
+    constexpr bool f32 = sizeof(T) == 4;
+    float *Ahi = (float *)w.Asplit, *Alo = Ahi + 4 * c.np;
+    if (f32) {
+        const long n = 4 * c.np, nb = (n + 255) / 256;
+        split_kernel<<<(int)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, c.stream>>>(Aw, Ahi, Alo, n);
+    }
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
         RevArgs R;
         R.A = Aw;
+        R.Ahi = Ahi;
+        R.Alo = Alo;
         R.nfq = c.nfq;
         R.e1p = c.e1p[d];
         R.lamL = lamL;
@@ -984,10 +1125,13 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
         rev_flux_kernel<T><<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
         rev_t2_kernel<T><<<dim3((R.n1 + 31) / 32, (R.n2 + 4 + kRevT2 - 1) / kRevT2, nf), blk, 0, c.stream>>>(R);
         rev_t1_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
-        rev_face_state_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch), blk,
-                                0, c.stream>>>(R);
-        rev_gather_cells_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
-                                  c.stream>>>(R);
+        const dim3 gfs((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch);
+        if (f32)
+            rev_face_state32_kernel<<<gfs, blk, 0, c.stream>>>(R);
+        else
+            rev_face_state_kernel<<<gfs, blk, 0, c.stream>>>(R);
+        rev_gather_cells_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
+                                     c.stream>>>(R);
     }
 }
 
@@ -1116,6 +1260,7 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
     w->lamR = k.take(24 * nR);
     w->lamFQ = k.take(8 * c.nfq);
     w->lamC = k.take(24 * c.nfq);
+    w->Asplit = k.take(4 * c.np);   // 8 np floats: hi, lo
     w->nuinf = 3 * 2 * G * maxsurf;
     w->uinf_part = k.take(w->nuinf);
     const long np = npts_total > 0 ? npts_total : 1;

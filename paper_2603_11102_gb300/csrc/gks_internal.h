@@ -142,7 +142,8 @@ struct AdjWork {
     long nG;                                              // component stride of gps
     // scratch
     double *lamA, *lamW, *lamP, *lamL, *lamLt;            // 4 * np each (padded indexing)
-    double *lamR, *lamFQ, *lamC;                          // per row / face buffers
+    double *lamR, *lamFQ, *lamC;                          // per row / face buffers (FP32 reverse: floats)
+    double *Asplit;                                       // FP32 reverse: the working array as hi, lo floats
     long nR;                                              // component stride of lamR
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;

@@ -339,13 +339,18 @@ struct RevArgs {
     Phys<double> ph;
 };
 
-// RA: reverse of the face flux at every interior face. The 64 Gauss-point
-// inputs of the face, kept by the forward recompute in lamG, are replaced
-// in place by their adjoints.
+// RA: reverse of the face flux at every interior face. The 16 inputs of each
+// Gauss point, kept by the forward in lamG, are replaced in place by their
+// adjoints. A thread takes one Gauss point g of one face (block: 32 faces
+// along t1 x 2 along t2 x the 4 Gauss points), so that a face's 4 points run
+// side by side and share the cell-adjoint loads through L1.
+constexpr int kRevFluxB = 2;   // faces along t2 per block
+
 template <typename T>
 __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
 {
-    const int a = blockIdx.x * TX + threadIdx.x, b = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
+    const int g = threadIdx.y & 3;
+    const int a = blockIdx.x * 32 + threadIdx.x, b = blockIdx.y * kRevFluxB + (threadIdx.y >> 2), f = blockIdx.z;
     if (a >= A.n1 || b >= A.n2) return;
     // adjoint of the face-averaged fluxes from the two neighbour cells
     const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
@@ -368,23 +373,23 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     const T ih1 = T(A.ih1[a + G]), ih2 = T(A.ih2[b + G]);
     const Phys<T> ph = phys_as<T>(A.ph);
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
-    for (int g = 0; g < 4; ++g) {
-        T *io = (T *)A.lamG + (long)(16 * g) * A.nG + face;
-        T q[4], Dn[4], D1[4], D2[4];
-        for (int v = 0; v < 4; ++v) {
-            q[v] = T(io[v * A.nG]);
-            Dn[v] = T(io[(4 + v) * A.nG]);
-            D1[v] = T(io[(8 + v) * A.nG]);
-            D2[v] = T(io[(12 + v) * A.nG]);
-        }
-        T qb[4], Dnb[4], D1b[4], D2b[4];
-        gk_flux_rev<T>(ph, q, Dn, D1, D2, ih1, ih2, sF0, sF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
-        for (int v = 0; v < 4; ++v) {
-            io[v * A.nG] = qb[v];
-            io[(4 + v) * A.nG] = Dnb[v];
-            io[(8 + v) * A.nG] = D1b[v];
-            io[(12 + v) * A.nG] = D2b[v];
-        }
+    T *io = (T *)A.lamG + (long)(16 * g) * A.nG + face;
+    T q[4], Dn[4], D1[4], D2[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        q[v] = io[v * A.nG];
+        Dn[v] = io[(4 + v) * A.nG];
+        D1[v] = io[(8 + v) * A.nG];
+        D2[v] = io[(12 + v) * A.nG];
+    }
+    T qb[4], Dnb[4], D1b[4], D2b[4];
+    gk_flux_rev<T>(ph, q, Dn, D1, D2, ih1, ih2, sF0, sF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        io[v * A.nG] = qb[v];
+        io[(4 + v) * A.nG] = Dnb[v];
+        io[(8 + v) * A.nG] = D1b[v];
+        io[(12 + v) * A.nG] = D2b[v];
     }
 }
 
@@ -1122,7 +1127,7 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
         R.ph = ph;
         const dim3 blk(32, 8);
         const int nf = c.n[d] + 1;
-        rev_flux_kernel<T><<<dim3((R.n1 + TX - 1) / TX, (R.n2 + TY - 1) / TY, nf), blk, 0, c.stream>>>(R);
+        rev_flux_kernel<T><<<dim3((R.n1 + 31) / 32, (R.n2 + kRevFluxB - 1) / kRevFluxB, nf), blk, 0, c.stream>>>(R);
         rev_t2_kernel<T><<<dim3((R.n1 + 31) / 32, (R.n2 + 4 + kRevT2 - 1) / kRevT2, nf), blk, 0, c.stream>>>(R);
         rev_t1_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
         const dim3 gfs((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch);

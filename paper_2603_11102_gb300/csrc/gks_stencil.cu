@@ -636,6 +636,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         // now so that they arrive during the flux computation
         const int a = a0 + tx, b = b0 + ty;
         const bool in = a < A.n1 && b < A.n2;
+        // inverse widths (x, y of the flux and the update; z of the update),
+        // loaded with the prefetch so that their latency overlaps it
+        R ih1 = R(0), ih2 = R(0), ihz = R(0);
+        if (in) {
+            ih1 = __ldg(A.ih1 + a + G);
+            ih2 = __ldg(A.ih2 + b + G);
+            if (upd) ihz = __ldg(U.ihz + f - 1 + G);
+        }
         R dy[8], s0[4], s1[4];
         long lin = 0;
         if (upd && in) {
@@ -669,7 +677,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 
         R F0[4], F1[4];
         if (in) {
-            const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
             tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.gp32, A.ngp,
                                         ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
@@ -694,7 +701,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                     if (NEED_F0) dz[v] = F0[loc[v]] - P0[loc[v]];
                     dz[4 + v] = F1[loc[v]] - P1[loc[v]];
                 }
-                const R ihx = __ldg(A.ih1 + a + G), ihy = __ldg(A.ih2 + b + G), ihz = __ldg(U.ihz + z + G);
+                const R ihx = ih1, ihy = ih2;
                 R o0[4], o1[4];
                 bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ihx, ihy, ihz, s0, s1, o0, o1);
                 if (STAGE == 2 && U.prep) {

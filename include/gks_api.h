@@ -297,8 +297,10 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
  *                              caller-owned, 256-byte aligned. Synchronises
  *                              the stream.
  * Both need what gks_step_adjoint needs (GKS_ERR_STATE / GKS_ERR_ARG
- * otherwise) and use the grid's adjoint precision; a tape recorded with the
- * other precision gives GKS_ERR_STATE. The grid's force scales
+ * otherwise), except that they also take GKS_FP32C grids and immersed
+ * bodies with a residual tolerance (the tape keeps the iterations each body
+ * ran; at most 28 bodies), and use the grid's adjoint precision; a tape
+ * recorded with the other precision gives GKS_ERR_STATE. The grid's force scales
  * and inflow must be those of the recorded step when it is reversed. */
 int gks_adjoint_tape_bytes(const gks_grid *g, size_t *bytes);
 int gks_adjoint_scratch_bytes(const gks_grid *g, size_t *bytes);

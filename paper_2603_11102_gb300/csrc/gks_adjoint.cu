@@ -1230,7 +1230,7 @@ size_t adjoint_tape_carve(const Ctx &c, int gp_bytes, void *base, AdjWork *w)
     Carver k{(uintptr_t)base};
     w->gp_bytes = gp_bytes;
     const long np4 = 4 * c.np;
-    w->hdr = k.take(4);
+    w->hdr = k.take(kTapeHeader);
     w->A0 = k.take(np4);
     w->Ws = k.take(np4);
     w->Wp = k.take(np4);
@@ -1294,7 +1294,7 @@ size_t adjoint_bytes(const Ctx &c, long npts_total, int gp_bytes)
 }
 
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1)
+                     const int *ibm_iters, double power_seed, double dt, double t_np1)
 {
     // the compute type of the local reverse maps is the storage type of the
     // tape's Gauss-point inputs
@@ -1303,9 +1303,11 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     const size_t bytes4 = sizeof(double) * 4 * c.np;
     // IBM reverse (bodies act after the rotors, in the order added): lamP
     // goes from the state after the step to the state after the rotors
-    for (int k = nbodies - 1; k >= 0; --k)
-        ibm_adj_kernel<<<(int)((bodies[k].nbox + 255) / 256), 256, 0, c.stream>>>(w.lamP, c.np, c.P[0], c.P[1],
-                                                                                 bodies[k]);
+    for (int k = nbodies - 1; k >= 0; --k) {
+        BodyDev b = bodies[k];
+        b.niter = ibm_iters[k];
+        ibm_adj_kernel<<<(int)((b.nbox + 255) / 256), 256, 0, c.stream>>>(w.lamP, c.np, c.P[0], c.P[1], b);
+    }
     // ALM reverse: lamP holds lambda'' (state after the step) and becomes
     // lambda' (state before the forcing); per-point scale gradients in pts
     if (rot) {

@@ -669,7 +669,14 @@ int step_once(gks_grid *g, const AdjWork *tp)
     for (size_t k = 0; k < g->obj_kind.size(); ++k)
         if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
     for (size_t k = 0; k < g->obj_kind.size(); ++k)
-        if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
+        if (g->obj_kind[k] == 1) {
+            const int bi = g->obj_index[k];
+            launch_ibm(c, g->bodies[bi]);
+            if (tp && (rc = cuda_check(g, cudaMemcpyAsync(tp->hdr + 4 + bi, g->bodies[bi].out + 3, sizeof(double),
+                                                          cudaMemcpyDeviceToDevice, c.stream),
+                                       "record the IBM iterations")))
+                return rc;
+        }
     if (fused_prep)
         for (int k = 0; k < nobj; ++k) launch_prep_box(c, cc.prep_box[k]);
     g->prep_valid = fused_prep;
@@ -889,8 +896,12 @@ int adjoint_check(gks_grid *g, bool tape_path)
                                                 : "gks_step_adjoint needs a GKS_FP64 grid (FP32C: recorded steps)");
     if (!(c.dt_fixed > 0.0)) return fail(g, GKS_ERR_STATE, "the adjoint needs a fixed time step (dt_fixed > 0)");
     for (const BodyDev &b : g->bodies)
-        if (b.tol > 0.0)
-            return fail(g, GKS_ERR_STATE, "the adjoint covers immersed bodies with a fixed iteration count (tol = 0)");
+        if (b.tol > 0.0 && !tape_path)
+            return fail(g, GKS_ERR_STATE,
+                        "gks_step_adjoint covers immersed bodies with a fixed iteration count (tol = 0); "
+                        "recorded steps cover the tolerance mode");
+    if (tape_path && g->bodies.size() > (size_t)kTapeMaxBodies)
+        return fail(g, GKS_ERR_STATE, "too many immersed bodies for a tape");
     if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
     // the reverse t2 gather indexes its 64 face arrays with 32-bit offsets
     for (int d = 0; d < 3; ++d) {
@@ -936,8 +947,9 @@ namespace {
 // or by the recompute of gks_step_adjoint), with the time of the tape.
 // init_sc: set the private scalars from the tape (the recompute of
 // gks_step_adjoint has set them already, and its flags are kept).
-int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, double dt, const double *d_adj_np1,
-                      double *d_adj_n, double power_seed, double *h_grad_scales, double *h_grad_uinf)
+int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, double dt, const int *ibm_iters,
+                      const double *d_adj_np1, double *d_adj_n, double power_seed, double *h_grad_scales,
+                      double *h_grad_uinf)
 {
     const Ctx &c = g->c;
     Ctx cc = c;
@@ -972,7 +984,7 @@ int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, d
     }
     cc.state = w.lamP;
     launch_scatter_state(cc, d_adj_np1);
-    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), power_seed, dt, t_n + dt);
+    adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), ibm_iters, power_seed, dt, t_n + dt);
     cc.state = w.lamW;
     launch_gather_state(cc, d_adj_n);
     // the reverse overwrote the Gauss-point inputs: the tape is consumed
@@ -1025,7 +1037,7 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
     AdjWork w;
     adjoint_tape_carve(g->c, gp_bytes_of(g), d_tape, &w);
     adjoint_scratch_carve(g->c, total_points(g), d_scratch, &w);
-    double hdr[4];
+    double hdr[kTapeHeader];
     rc = cuda_check(g, cudaMemcpyAsync(hdr, w.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, g->c.stream), "read tape");
     if (!rc) rc = sync(g);
     if (rc) return rc;
@@ -1035,7 +1047,14 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
         if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded, or already reversed");
     if (hdr[3] != (double)w.gp_bytes)
         return fail(g, GKS_ERR_STATE, "tape recorded with another adjoint precision");
-    return reverse_from_tape(g, w, true, hdr[1], hdr[2], d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
+    std::vector<int> iters(g->bodies.size());
+    for (size_t k = 0; k < iters.size(); ++k) {
+        iters[k] = (int)hdr[4 + k];
+        if (iters[k] < 1 || iters[k] > g->bodies[k].niter)
+            return fail(g, GKS_ERR_STATE, "tape with an invalid IBM iteration count");
+    }
+    return reverse_from_tape(g, w, true, hdr[1], hdr[2], iters.data(), d_adj_np1, d_adj_n, power_seed,
+                             h_grad_scales, h_grad_uinf);
 }
 
 int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_state_n, const double *d_adj_np1,
@@ -1074,7 +1093,10 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
     cc.state = w.Wp;
     use_tape_gauss(cc, w, 1);
     launch_stage(cc, 2);
-    return reverse_from_tape(g, w, false, t_n, dt, d_adj_np1, d_adj_n, power_seed, h_grad_scales, h_grad_uinf);
+    std::vector<int> iters(g->bodies.size());
+    for (size_t k = 0; k < iters.size(); ++k) iters[k] = g->bodies[k].niter;   // tol = 0: every iteration runs
+    return reverse_from_tape(g, w, false, t_n, dt, iters.data(), d_adj_np1, d_adj_n, power_seed, h_grad_scales,
+                             h_grad_uinf);
 }
 
 int gks_profile_enable(gks_grid *g, int timing_on)

@@ -132,9 +132,12 @@ void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no proj
 // the tape of one step (what the reverse reads of the forward step) and the
 // scratch of the reverse.
 constexpr unsigned char kTapeMagicByte = 0x5A;   // hdr[0] bytes of a recorded, unconsumed tape
+constexpr int kTapeHeader = 32;                    // doubles of the tape header
+constexpr int kTapeMaxBodies = kTapeHeader - 4;    // IBM iteration counts a tape records
 struct AdjWork {
     // tape
-    double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes
+    double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes,
+                                                          // [4 + k] IBM iterations of body k
     double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
     void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each);
                                                           // the reverse flux overwrites them with their adjoints
@@ -166,8 +169,9 @@ struct BodyDev;
 // The local reverse maps (flux, WENO5 pair, equilibrium, transposed
 // tangential passes) run in FP32 when the tape's Gauss-point inputs are
 // stored as float (w.gp_bytes 4), else in FP64; FP64 state adjoints and sums.
+// ibm_iters[k]: the direct-forcing iterations body k ran in the step.
 void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const BodyDev *bodies, int nbodies,
-                     double power_seed, double dt, double t_np1);
+                     const int *ibm_iters, double power_seed, double dt, double t_np1);
 
 // Immersed body (gks_forcing.cu).
 struct BodyDev {

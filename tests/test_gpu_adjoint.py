@@ -171,6 +171,66 @@ def test_one_step_adjoint_matches_central_differences(mods, case, rev):
     g.close()
 
 
+@pytest.mark.parametrize("rev", ["fp64", "fp32"])
+def test_ibm_tolerance_mode_through_recorded_steps(mods, rev):
+    """IBM with a residual tolerance: the iteration count is piecewise
+    constant in the state, so the step's derivative is that of the realised
+    count, which the recorded step keeps. The tolerance is set between the
+    residuals after the second and third iteration of this state, so that
+    the count (3 of at most 6) is the same at every finite-difference point."""
+    gks, adjoint, torch = mods
+    w = rotor_body_workload()
+    w.bodies[0].niter = 6
+    w.bodies[0].tol = 1e-300   # a tolerance it never meets: the residual after every iteration
+    W = torch.tensor(perturbed_state(w, 3), dtype=torch.float64, device="cuda")
+    t_n = 0.37
+    g0 = gks.Grid.from_workload(w, precision="fp64")
+    forward_step(g0, torch, W, t_n)
+    r = g0.forces(1)["residual_history"]
+    g0.close()
+    assert len(r) == 6 and r[2] < r[1]
+    w.bodies[0].tol = float(np.sqrt(r[1] * r[2]))
+    g = gks.Grid.from_workload(w, precision="fp64")
+    g.set_adjoint_precision(rev)
+    rng = np.random.default_rng(5)
+    lam1 = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
+    beta, npts, u0 = 0.7, 18, w.inflow[1]
+    s0 = np.ones(npts)
+
+    def J(Wx, s=None, u=None):
+        out, P = forward_step(g, torch, Wx, t_n, s, u)
+        assert g.forces(1)["iters"] == 3
+        return float((lam1 * out).sum().item()) + beta * P
+
+    g.set_force_scales(0, s0)
+    g.set_inflow(1.0, u0, 0.0, 0.0)
+    g.set_state_tensor(W)
+    g.set_time(t_n)
+    tape = g.adjoint_tape()
+    g.step_record(tape)
+    assert g.forces(1)["iters"] == 3
+    gs = np.zeros(npts)
+    lam0, gu = g.step_reverse(tape, g.adjoint_scratch(), lam1, beta, gs)
+    tol = 1e-5 if rev == "fp64" else 1e-4
+    dW = torch.tensor(rng.standard_normal(W.shape), dtype=torch.float64, device="cuda")
+    dW[0] *= 0.1
+    h = 1e-7
+    fd = (J(W + h * dW, s0, u0) - J(W - h * dW, s0, u0)) / (2 * h)
+    ad = float((lam0 * dW).sum().item())
+    assert abs(fd - ad) <= tol * max(abs(ad), 1e-12), (fd, ad)
+    fdu = (J(W, s0, u0 + h) - J(W, s0, u0 - h)) / (2 * h)
+    assert abs(fdu - gu) <= tol * max(abs(fdu), 1e-3), (fdu, gu)
+    ds = rng.standard_normal(npts)
+    h = 1e-6
+    fds = (J(W, s0 + h * ds, u0) - J(W, s0 - h * ds, u0)) / (2 * h)
+    assert abs(fds - float(np.dot(gs, ds))) <= tol * max(abs(fds), 1e-12), (fds, np.dot(gs, ds))
+    # the per-step recomputation keeps refusing the tolerance mode
+    with pytest.raises(gks.GKSError) as e:
+        g.step_adjoint(g.adjoint_workspace(), t_n, W, lam1)
+    assert e.value.code == -5
+    g.close()
+
+
 def oracle_objective(w, s, u, nsteps, iplane, beta):
     w = WL.Workload(w.name, w.n, w.faces, w.mach, w.u_ref, w.mu, w.bc, cfl=w.cfl, dt_fixed=w.dt_fixed,
                     inflow=(1.0, u, 0.0, 0.0), state0=None, rotors=w.rotors, bodies=w.bodies)

@@ -89,3 +89,20 @@ def test_cyclic_axis_permutation(gks, precision):
         scale = np.max(np.abs(A[c]))
         err = np.max(np.abs(A[c] - B[c]))
         assert err <= TOL[precision] * scale, (precision, c, err, scale)
+
+
+def test_load_history_fp32c_against_fp64(gks):
+    """The load history of a small rotor + tower + nacelle run (every 5
+    steps): FP32C and FP64 give the same thrust, power, coefficients and body
+    force to FP32-flux accuracy, and the same conserved totals."""
+    from paper_2603_11102_gb300 import history
+    w = WL.alm_ibm_rotor(n=(64, 32, 32), n_pts=10)
+    w.state0 = WL.perturbed(w, 0.02, seed=5)
+    r32, _ = history.record(w, "fp32c", 20, 5)
+    r64, _ = history.record(w, "fp64", 20, 5)
+    a32, a64 = np.array(r32), np.array(r64)
+    assert a32.shape == (4, len(history.FIELDS)) and np.array_equal(a32[:, 0], [5, 10, 15, 20])
+    for name in ("thrust", "torque", "power", "cp", "ct", "body_fx", "mass", "ke"):
+        i = history.FIELDS.index(name)
+        scale = np.max(np.abs(a64[:, i]))
+        assert scale > 0 and np.max(np.abs(a32[:, i] - a64[:, i])) <= 1e-5 * scale, name

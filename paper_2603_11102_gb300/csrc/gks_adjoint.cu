@@ -1068,7 +1068,56 @@ __global__ void __launch_bounds__(256) alm_sample_adj_kernel(AlmAdjArgs A, doubl
     }
 }
 
-__global__ void alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const long *ptl)
+// The sampling adjoints added to their cells. Entries e = 8 q + c (point q,
+// corner c) name a cell (or -1 for a zero weight); points share cells. One
+// block sorts the (cell, entry) keys (bitonic, in shared memory), so that
+// each cell's entries sit together in entry order, and the first thread of
+// each cell adds their sum: deterministic, and no two threads write a cell.
+// More than kSampleSort entries take the sequential kernel below.
+constexpr int kSampleSort = 2048;
+
+__global__ void __launch_bounds__(1024) alm_sample_add_kernel(AlmAdjArgs A, const double *ptc, const long *ptl)
+{
+    __shared__ unsigned long long key[kSampleSort];
+    constexpr unsigned long long kNone = ~0ull;
+    const int n = 8 * A.r.nb * A.r.np;
+    for (int i = threadIdx.x; i < kSampleSort; i += blockDim.x) {
+        const long l = i < n ? ptl[i] : -1;
+        key[i] = l < 0 ? kNone : ((unsigned long long)l << 12) | (unsigned long long)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= kSampleSort; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kSampleSort; i += blockDim.x) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = key[i], b = key[p];
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long ki = key[i];
+        if (ki == kNone) continue;
+        const unsigned long long cell = ki >> 12;
+        if (i > 0 && (key[i - 1] >> 12) == cell) continue;
+        double acc[4] = {0, 0, 0, 0};
+        for (int j = i; j < n && key[j] != kNone && (key[j] >> 12) == cell; ++j) {
+            const long e = (long)(key[j] & 4095ull);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] += ptc[4 * e + v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) A.lam[v * A.np + (long)cell] += acc[v];
+    }
+}
+
+__global__ void alm_sample_add_serial_kernel(AlmAdjArgs A, const double *ptc, const long *ptl)
 {
     const int npts = A.r.nb * A.r.np;
     for (int q = 0; q < npts; ++q)
@@ -1330,7 +1379,10 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
         alm_interp_adj_kernel<<<npts, 256, 0, c.stream>>>(A);
         alm_loads_adj_kernel<<<1, 256, 0, c.stream>>>(A);
         alm_sample_adj_kernel<<<(npts + 255) / 256, 256, 0, c.stream>>>(A, w.ptc, (long *)w.ptl);
-        alm_sample_add_kernel<<<1, 1, 0, c.stream>>>(A, w.ptc, (const long *)w.ptl);
+        if (8 * npts <= kSampleSort)
+            alm_sample_add_kernel<<<1, 1024, 0, c.stream>>>(A, w.ptc, (const long *)w.ptl);
+        else
+            alm_sample_add_serial_kernel<<<1, 1, 0, c.stream>>>(A, w.ptc, (const long *)w.ptl);
     }
     // stage 2: W' = P + dt^2/3 Lt(W*)
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,

@@ -290,9 +290,9 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
  *                              the force-scale and inflow-speed gradients of
  *                              step n as gks_step_adjoint does; power_seed is
  *                              dJ/dP for the power of step n. The reverse
- *                              overwrites the tape's Gauss-point inputs, so a
- *                              tape is reversed once: a tape that was not
- *                              recorded or was already reversed gives
+ *                              only reads the tape, so one tape serves any
+ *                              number of reverses (several adjoint seeds); a
+ *                              tape that was not recorded gives
  *                              GKS_ERR_STATE. d_scratch: device,
  *                              caller-owned, 256-byte aligned. Synchronises
  *                              the stream.

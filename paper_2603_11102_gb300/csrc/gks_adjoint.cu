@@ -1,5 +1,5 @@
-// gks_adjoint.cu -- hand-written reverse mode (adjoint) of one FP64 S2O4
-// step, for gradients of a functional of the state with respect to the
+// gks_adjoint.cu -- hand-written reverse mode (adjoint) of one S2O4 step
+// (FP64 or FP32C), for gradients of a functional of the state with respect to the
 // per-point actuator force scales and the inflow speed.
 //
 // The forward step (Sec. 2 and the end of Sec. 3.2) is a composition of
@@ -10,12 +10,12 @@
 //   [trilinear sample, loads, truncated-Gaussian projection] and the IBM
 //   direct forcing. The forward step (recorded, or recomputed from W^n)
 //   keeps the Gauss-point inputs of every face of each stage and direction.
-//   Its adjoint runs the
-//   pieces backwards. Every transposed stencil is written as a gather (each
+//   Its adjoint runs the pieces backwards. Every transposed stencil is
+//   written as a gather (each
 //   output sums its inputs in a fixed order), so the adjoint is
 //   deterministic and uses no atomics on the state:
-//   RA  per interior face: reverse the flux at the 4 Gauss points, the
-//       Gauss-input adjoints replace the stored inputs;
+//   RA  per Gauss point of an interior face: reverse the flux (16 input
+//       adjoints from the recorded inputs, which stay as they are);
 //   RB  t2 transpose: Gauss adjoints -> adjoints of the t1-pass rows;
 //   RC  t1 transpose: rows -> adjoints of Q0 and its normal slope per face;
 //   RD  marching along d: paired WENO5 forward and reverse per cell, the
@@ -26,8 +26,8 @@
 //       adjoint added to its source cell (Riemann inflow through its
 //       Jacobian; its U_inf sensitivity stored per ghost and reduced in a
 //       fixed order).
-// RA-RD run in a compute type T: double, or float (FP32 arithmetic in the
-// local reverse maps, FP64 loads, stores and sums).
+// RA-RE run in a compute type T: double, or float (FP32 arithmetic and
+// FP32 intermediate adjoints; the state adjoints and their sums in FP64).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -323,10 +323,11 @@ struct RevArgs {
     long nfq;                 // component stride of the face-box adjoints
     int e1p;
     const double *lamL, *lamLt;   // padded indexing; lamL may be null (stage 2)
-    // adjoints inside the spatial adjoint of one direction, stored in the
-    // reverse's compute type: Gauss-point inputs (replaced by their adjoints),
-    // t1-pass rows, face boxes, per-face cell slots
+    // the recorded Gauss-point inputs (read only) and the adjoints inside the
+    // spatial adjoint of one direction, in the reverse's compute type:
+    // Gauss-point inputs, t1-pass rows, face boxes, per-face cell slots
     void *lamG;
+    void *lamGa;
     long nG;
     void *lamR;
     long nR;
@@ -339,9 +340,9 @@ struct RevArgs {
     Phys<double> ph;
 };
 
-// RA: reverse of the face flux at every interior face. The 16 inputs of each
-// Gauss point, kept by the forward in lamG, are replaced in place by their
-// adjoints. A thread takes one Gauss point g of one face (block: 32 faces
+// RA: reverse of the face flux at every interior face: from the 16 recorded
+// inputs of each Gauss point (lamG, only read) their adjoints (lamGa, same
+// layout). A thread takes one Gauss point g of one face (block: 32 faces
 // along t1 x 2 along t2 x the 4 Gauss points), so that a face's 4 points run
 // side by side and share the cell-adjoint loads through L1.
 constexpr int kRevFluxB = 2;   // faces along t2 per block
@@ -373,14 +374,15 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     const T ih1 = T(A.ih1[a + G]), ih2 = T(A.ih2[b + G]);
     const Phys<T> ph = phys_as<T>(A.ph);
     const long face = ((long)f * A.n2 + b) * A.n1 + a;
-    T *io = (T *)A.lamG + (long)(16 * g) * A.nG + face;
+    const T *in = (const T *)A.lamG + (long)(16 * g) * A.nG + face;
+    T *io = (T *)A.lamGa + (long)(16 * g) * A.nG + face;
     T q[4], Dn[4], D1[4], D2[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        q[v] = io[v * A.nG];
-        Dn[v] = io[(4 + v) * A.nG];
-        D1[v] = io[(8 + v) * A.nG];
-        D2[v] = io[(12 + v) * A.nG];
+        q[v] = in[v * A.nG];
+        Dn[v] = in[(4 + v) * A.nG];
+        D1[v] = in[(8 + v) * A.nG];
+        D2[v] = in[(12 + v) * A.nG];
     }
     T qb[4], Dnb[4], D1b[4], D2b[4];
     gk_flux_rev<T>(ph, q, Dn, D1, D2, ih1, ih2, sF0, sF1, A.lamL != nullptr, qb, Dnb, D1b, D2b);
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
             for (int k = 0; k < 8; ++k) x[k] = T(0);
             return;
         }
-        const T *Gf = (const T *)A.lamG + ((long)f * A.n2 + b) * A.n1 + a;
+        const T *Gf = (const T *)A.lamGa + ((long)f * A.n2 + b) * A.n1 + a;
 #pragma unroll
         for (int nn = 0; nn < 2; ++nn) {
             const long g16 = 16L * (2 * m + nn);
@@ -1151,7 +1153,8 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
         R.e1p = c.e1p[d];
         R.lamL = lamL;
         R.lamLt = lamLt;
-        R.lamG = gp[d];   // Gauss-point inputs of this direction, replaced by their adjoints
+        R.lamG = gp[d];   // Gauss-point inputs of this direction (read only)
+        R.lamGa = w.lamGa;
         R.nG = w.nG;
         R.lamR = w.lamR;
         R.nR = w.nR;
@@ -1314,6 +1317,9 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
     w->lamR = k.take(24 * nR);
     w->lamFQ = k.take(8 * c.nfq);
     w->lamC = k.take(24 * c.nfq);
+    long nG = 0;
+    for (int d = 0; d < 3; ++d) nG = std::max(nG, (long)(c.n[d] + 1) * c.n[tan1(d)] * c.n[tan2(d)]);
+    w->lamGa = k.take(64 * nG);   // Gauss-point adjoints of one direction (double or float)
     w->Asplit = k.take(4 * c.np);   // 8 np floats: hi, lo
     w->nuinf = 3 * 2 * G * maxsurf;
     w->uinf_part = k.take(w->nuinf);

@@ -987,9 +987,7 @@ int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, d
     adjoint_reverse(cc, w, rot, g->bodies.data(), (int)g->bodies.size(), ibm_iters, power_seed, dt, t_n + dt);
     cc.state = w.lamW;
     launch_gather_state(cc, d_adj_n);
-    // the reverse overwrote the Gauss-point inputs: the tape is consumed
-    rc = cuda_check(g, cudaMemsetAsync(w.hdr, 0, sizeof(double), c.stream), "consume tape");
-    if (!rc) rc = check_launch(g, "adjoint step");
+    rc = check_launch(g, "adjoint step");
     if (rc) return rc;
     const long npts = total_points(g);
     std::vector<double> pts(8 * (npts > 0 ? npts : 1));
@@ -1044,7 +1042,7 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
     unsigned char magic[sizeof(double)];
     memcpy(magic, hdr, sizeof(magic));
     for (unsigned char m : magic)
-        if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded, or already reversed");
+        if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded");
     if (hdr[3] != (double)w.gp_bytes)
         return fail(g, GKS_ERR_STATE, "tape recorded with another adjoint precision");
     std::vector<int> iters(g->bodies.size());

@@ -131,7 +131,7 @@ void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no proj
 // Adjoint of one step (gks_adjoint.cu). Buffers of the adjoint workspace:
 // the tape of one step (what the reverse reads of the forward step) and the
 // scratch of the reverse.
-constexpr unsigned char kTapeMagicByte = 0x5A;   // hdr[0] bytes of a recorded, unconsumed tape
+constexpr unsigned char kTapeMagicByte = 0x5A;   // hdr[0] bytes of a recorded tape
 constexpr int kTapeHeader = 32;                    // doubles of the tape header
 constexpr int kTapeMaxBodies = kTapeHeader - 4;    // IBM iteration counts a tape records
 struct AdjWork {
@@ -139,12 +139,12 @@ struct AdjWork {
     double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes,
                                                           // [4 + k] IBM iterations of body k
     double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
-    void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each);
-                                                          // the reverse flux overwrites them with their adjoints
+    void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each)
     int gp_bytes;                                         // their storage: 8 (FP64 reverse) or 4 (FP32 reverse)
     long nG;                                              // component stride of gps
     // scratch
     double *lamA, *lamW, *lamP, *lamL, *lamLt;            // 4 * np each (padded indexing)
+    double *lamGa;                                        // Gauss-point adjoints of one direction (64 nG)
     double *lamR, *lamFQ, *lamC;                          // per row / face buffers (FP32 reverse: floats)
     double *Asplit;                                       // FP32 reverse: the working array as hi, lo floats
     long nR;                                              // component stride of lamR

@@ -380,7 +380,7 @@ class Grid:
     def step_reverse(self, tape, scratch, adj_np1, power_seed=0.0, grad_scales=None):
         """Reverse of the recorded step: returns (lambda^n, grad_uinf of the
         step); adds its force-scale gradient into grad_scales (numpy). The
-        tape is consumed."""
+        tape is only read: it can be reversed again (another seed)."""
         import torch
         adj_np1 = adj_np1.to(self.device, torch.float64).contiguous()
         out = torch.empty(self.shape, dtype=torch.float64, device=self.device)

@@ -309,8 +309,8 @@ def test_rollout_gradient_vs_finite_differences_and_oracle(mods, case, rev):
 @pytest.mark.parametrize("rev", ["fp64", "fp32"])
 def test_recorded_step_and_its_reverse(mods, rev):
     """gks_step_record steps the grid as gks_step does, and gks_step_reverse
-    from its tape gives what gks_step_adjoint gives from W^n; a tape is
-    reversed once."""
+    from its tape gives what gks_step_adjoint gives from W^n; the reverse
+    only reads the tape, so a second reverse gives the same bits."""
     gks, adjoint, torch = mods
     w = rotor_body_workload()
     g = gks.Grid.from_workload(w, precision="fp64")
@@ -334,9 +334,9 @@ def test_recorded_step_and_its_reverse(mods, rev):
     assert np.array_equal(gs_r, gs_a) and gu_r == gu_a
     # the grid's state and time are those the recorded step left
     assert torch.equal(g.state_tensor(), ref) and g.time == t1
-    with pytest.raises(gks.GKSError) as e:
-        g.step_reverse(tape, scratch, lam1)
-    assert e.value.code == -5
+    gs_2 = np.zeros(18)
+    lam_2, gu_2 = g.step_reverse(tape, scratch, lam1, 0.4, gs_2)
+    assert torch.equal(lam_2, lam_r) and np.array_equal(gs_2, gs_r) and gu_2 == gu_r
     with pytest.raises(gks.GKSError) as e:
         g.step_reverse(torch.zeros_like(tape), scratch, lam1)
     assert e.value.code == -5

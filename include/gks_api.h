@@ -182,6 +182,13 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
  * GKS_ERR_CFL or GKS_ERR_RANGE raised on the device. t_out (may be NULL)
  * receives the time after the last step. */
 int gks_step(gks_grid *g, int nsteps, double *t_out);
+/* The same steps, enqueued on the grid's stream without synchronising:
+ * device-side errors stay flagged on the device and are reported by the next
+ * gks_step or gks_sync. */
+int gks_step_async(gks_grid *g, int nsteps);
+/* Synchronise the grid's stream, report errors flagged on the device as
+ * gks_step does, and give the current time (t_out may be NULL). */
+int gks_sync(gks_grid *g, double *t_out);
 
 /* Current time and the last time step (synchronises). */
 int gks_get_time(gks_grid *g, double *t, double *dt_last);
@@ -206,6 +213,18 @@ typedef struct {
     double residual;
 } gks_forces_out;
 int gks_forces(gks_grid *g, int id, gks_forces_out *out, double *h_points);
+
+/* The load record of object id, copied on the grid's stream into h_out
+ * without synchronising: asynchronous when h_out is page-locked; the caller
+ * synchronises the stream (an event, a later call that synchronises) before
+ * reading it. The record holds what gks_forces reports, as doubles:
+ *   rotor: thrust[n_blades], torque[n_blades], power, C_P, C_T;
+ *   body: force[3], iterations, residual, two internal words, then the
+ *         residual of each iteration (niter values).
+ * gks_forces_record_len gives its length in doubles; n is the room at h_out
+ * (GKS_ERR_ARG if smaller). */
+int gks_forces_record_len(const gks_grid *g, int id, size_t *n);
+int gks_forces_async(gks_grid *g, int id, double *h_out, size_t n);
 
 /* Mass, momentum (3) and kinetic energy summed over interior cells with
  * their volumes, in FP64 (synchronises). */

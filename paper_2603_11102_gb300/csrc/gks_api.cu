@@ -713,7 +713,7 @@ int check_flags(gks_grid *g, int flags, const char *where)
 }
 }  // namespace
 
-int gks_step(gks_grid *g, int nsteps, double *t_out)
+int gks_step_async(gks_grid *g, int nsteps)
 {
     if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
     g->stepped = true;
@@ -721,7 +721,19 @@ int gks_step(gks_grid *g, int nsteps, double *t_out)
         int rc = step_once(g, nullptr);
         if (rc) return rc;
     }
+    return GKS_OK;
+}
+
+int gks_sync(gks_grid *g, double *t_out)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
     return finish_steps(g, t_out);
+}
+
+int gks_step(gks_grid *g, int nsteps, double *t_out)
+{
+    int rc = gks_step_async(g, nsteps);
+    return rc ? rc : finish_steps(g, t_out);
 }
 
 int gks_get_time(gks_grid *g, double *t, double *dt_last)
@@ -779,6 +791,28 @@ int gks_forces(gks_grid *g, int id, gks_forces_out *out, double *h_points)
     out->residual = o[4];
     if (h_points) memcpy(h_points, &o[7], sizeof(double) * b.niter);
     return GKS_OK;
+}
+
+int gks_forces_record_len(const gks_grid *g, int id, size_t *n)
+{
+    if (!g || !n || id < 0 || id >= (int)g->obj_kind.size()) return fail(nullptr, GKS_ERR_ARG, "bad object id");
+    if (g->obj_kind[id] == 0)
+        *n = 2 * (size_t)g->rotors[g->obj_index[id]].nb + 3;
+    else
+        *n = 7 + (size_t)g->bodies[g->obj_index[id]].niter;
+    return GKS_OK;
+}
+
+int gks_forces_async(gks_grid *g, int id, double *h_out, size_t n)
+{
+    size_t len = 0;
+    if (!g || !h_out) return fail(g, GKS_ERR_ARG, "null argument");
+    int rc = gks_forces_record_len(g, id, &len);
+    if (rc) return fail(g, rc, "bad object id");
+    if (n < len) return fail(g, GKS_ERR_ARG, "record buffer too small");
+    const double *src = g->obj_kind[id] == 0 ? g->rotors[g->obj_index[id]].out : g->bodies[g->obj_index[id]].out;
+    return cuda_check(g, cudaMemcpyAsync(h_out, src, sizeof(double) * len, cudaMemcpyDeviceToHost, g->c.stream),
+                      "copy load record");
 }
 
 int gks_diagnostics(gks_grid *g, double out[5])

@@ -85,6 +85,10 @@ SIGNATURES = {
     "gks_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gks_adjoint_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "gks_forces_record_len": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
+    "gks_step_async": (C.c_int, [C.c_void_p, C.c_int]),
+    "gks_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "gks_forces_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "gks_adjoint_tape_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "gks_adjoint_scratch_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "gks_step_record": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
@@ -266,9 +270,21 @@ class Grid:
         self.objects.append(("body", int(dS.size), int(body.niter)))
         return bid.value
 
-    def step(self, nsteps=1):
+    def step(self, nsteps=1, sync=True):
+        """nsteps steps; returns the time after them. sync=False enqueues
+        them without waiting (returns None; errors flagged on the device
+        surface at the next synchronising step or sync())."""
+        if not sync:
+            _check(lib.gks_step_async(self.h, int(nsteps)), self.h)
+            return None
         t = C.c_double()
         _check(lib.gks_step(self.h, int(nsteps), C.byref(t)), self.h)
+        return t.value
+
+    def sync(self):
+        """Wait for the grid's stream; report device-side errors; the time."""
+        t = C.c_double()
+        _check(lib.gks_sync(self.h, C.byref(t)), self.h)
         return t.value
 
     @property
@@ -302,6 +318,21 @@ class Grid:
         _check(lib.gks_forces(self.h, int(oid), C.byref(out), res.ctypes.data_as(_dp)), self.h)
         return {"force": np.array(out.body_force[:]), "iters": out.iters, "residual": out.residual,
                 "residual_history": res[:out.iters].copy()}
+
+    def forces_record(self, oid):
+        """A page-locked float64 tensor for the load record of object oid
+        (see forces_async)."""
+        import torch
+        n = C.c_size_t()
+        _check(lib.gks_forces_record_len(self.h, int(oid), C.byref(n)), self.h)
+        return torch.empty(n.value, dtype=torch.float64).pin_memory()
+
+    def forces_async(self, oid, record):
+        """Enqueue on the grid's stream the copy of object oid's load record
+        (rotor: thrust per blade, torque per blade, power, C_P, C_T) into the
+        page-locked tensor `record`; read it after the stream (an event
+        recorded on it) has reached that point."""
+        _check(lib.gks_forces_async(self.h, int(oid), C.c_void_p(record.data_ptr()), record.numel()), self.h)
 
     def diagnostics(self):
         out = np.zeros(5)

@@ -276,3 +276,34 @@ def test_errors_are_reported_and_context_stays_usable(gks):
     with pytest.raises(gks.GKSError) as e:
         g3.add_rotor(far)
     assert e.value.code == -6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_async_steps_and_load_records(gks, precision):
+    """gks_step_async steps exactly as gks_step does; gks_forces_async copies
+    the load record gks_forces reports, without synchronising."""
+    import torch
+    w = WL.alm_ibm_rotor(n=(64, 32, 32), steps=1, n_pts=10)
+    w.state0 = WL.perturbed(w, 0.02, seed=8)
+    a = gks.Grid.from_workload(w, precision=precision)
+    b = gks.Grid.from_workload(w, precision=precision)
+    ta = a.step(3)
+    rec = b.forces_record(0)
+    assert b.step(3, sync=False) is None
+    b.forces_async(0, rec)
+    tb = b.sync()
+    assert ta == tb
+    assert np.array_equal(a.get_state(), b.get_state())
+    f = a.forces(0)
+    nb = len(f["thrust"])
+    r = rec.numpy()
+    assert rec.numel() == 2 * nb + 3 and torch.is_tensor(rec) and rec.is_pinned()
+    assert np.array_equal(r[:nb], f["thrust"]) and np.array_equal(r[nb:2 * nb], f["torque"])
+    assert r[2 * nb] == f["power"] and r[2 * nb + 1] == f["cp"] and r[2 * nb + 2] == f["ct"]
+    brec = b.forces_record(1)
+    b.forces_async(1, brec)
+    b.sync()
+    fb = a.forces(1)
+    assert np.array_equal(brec.numpy()[:3], fb["force"]) and int(brec[3]) == fb["iters"]
+    a.close()
+    b.close()

@@ -25,6 +25,10 @@ struct Profiler {
     };
     std::vector<Rec> recs;
     cudaEvent_t open_ev = nullptr;
+    // the end event of the last timed launch; the next launch begins at it
+    // (one event per launch boundary; whatever the host enqueues between
+    // two launches is counted in the second)
+    cudaEvent_t last_end = nullptr;
     long launches[K_NGROUPS] = {0};
 };
 
@@ -199,13 +203,18 @@ void prof_mark(void *ctx, int group, int begin)
     if (begin) {
         p.launches[group]++;
         if (p.timing) {
-            p.open_ev = prof_event(p);
-            cudaEventRecord(p.open_ev, g->c.stream);
+            if (p.last_end) {
+                p.open_ev = p.last_end;
+            } else {
+                p.open_ev = prof_event(p);
+                cudaEventRecord(p.open_ev, g->c.stream);
+            }
         }
     } else if (p.timing) {
         cudaEvent_t e = prof_event(p);
         cudaEventRecord(e, g->c.stream);
         p.recs.push_back({group, p.open_ev, e});
+        p.last_end = e;
     }
 }
 
@@ -622,6 +631,7 @@ int step_once(gks_grid *g, const AdjWork *tp)
     const bool fused_prep = nobj <= 8;
     const size_t bytes4 = sizeof(double) * 4 * c.np;
     int rc = GKS_OK;
+    g->prof.last_end = nullptr;   // launch boundaries are shared inside a step only
     if (!g->prep_valid) launch_prep(c);
     launch_ghost(c, c.wk0);
     launch_cfl(c);   // dt from max |U|^2, which it clears
@@ -681,6 +691,7 @@ int step_once(gks_grid *g, const AdjWork *tp)
         for (int k = 0; k < nobj; ++k) launch_prep_box(c, cc.prep_box[k]);
     g->prep_valid = fused_prep;
     launch_advance(c);
+    g->prof.last_end = nullptr;
     rc = check_launch(g, "step");
     if (rc) return rc;
     g->nstep++;
@@ -1139,6 +1150,7 @@ int gks_profile_enable(gks_grid *g, int timing_on)
     Profiler &p = g->prof;
     p.timing = timing_on != 0;
     p.next = 0;
+    p.last_end = nullptr;
     p.recs.clear();
     for (int k = 0; k < K_NGROUPS; ++k) p.launches[k] = 0;
     return GKS_OK;
@@ -1163,6 +1175,7 @@ int gks_profile_read(gks_grid *g, gks_profile_out *out)
         p.launches[k] = 0;
     }
     p.next = 0;
+    p.last_end = nullptr;
     p.recs.clear();
     return GKS_OK;
 }

@@ -107,11 +107,20 @@ def test_workspace_sizes_and_validation(gks):
     bad = [dict(n=(2, 6, 5), bc=((1, 1), (0, 0), (0, 0))),   # too few cells for a wall
            dict(bc=((0, 1), (0, 0), (0, 0))),                # periodic on one end only
            dict(faces=[np.linspace(1, 0, 9), np.linspace(0, 1, 7), np.linspace(0, 1, 6)]),
-           dict(precision=7), dict(cfl=0.0)]
+           dict(precision=7), dict(cfl=0.0),
+           dict(n=(0, 6, 5), faces=[np.zeros(1), np.linspace(0, 1, 7), np.linspace(0, 1, 6)]),   # empty axis
+           # more cells than the 32-bit face-tile indices of the flux kernels cover
+           dict(n=(2000, 1100, 1000), faces=[np.linspace(0, 1, 2001), np.linspace(0, 1, 1101),
+                                              np.linspace(0, 1, 1001)])]
     for kw in bad:
         d, keep = make_desc(gks, **kw)
         assert lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)) == -1, kw
         assert lib.gks_last_error(None)
     # null handles
     assert lib.gks_step(None, 1, None) == -1
+    assert lib.gks_step_async(None, 1) == -1
+    assert lib.gks_sync(None, None) == -1
+    assert lib.gks_step_record(None, None, None) == -1
+    assert lib.gks_step_reverse(None, None, None, None, None, 0.0, None, None) == -1
+    assert lib.gks_forces_async(None, 0, None, 0) == -1
     assert lib.gks_destroy_grid(None) == -1

@@ -334,7 +334,9 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
  * 8 misc); with timing enabled each launch is also
  * bracketed by CUDA events on the grid's stream and its duration summed.
  * gks_profile_enable sets timing on or off and clears the counters;
- * gks_profile_read synchronises, fills out and clears the counters. */
+ * gks_profile_read synchronises, fills out and clears the counters. With
+ * the environment variable GKS_NVTX=1 at grid creation every launch is also
+ * an NVTX range named after its group (for Nsight tools). */
 #define GKS_NUM_KERNEL_GROUPS 9
 typedef struct {
     long launches[GKS_NUM_KERNEL_GROUPS];

@@ -4,9 +4,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -17,6 +19,7 @@ using namespace gks;
 
 struct Profiler {
     bool timing = false;
+    bool nvtx = false;   // NVTX range per launch (environment variable GKS_NVTX=1 at grid creation)
     std::vector<cudaEvent_t> pool;
     size_t next = 0;
     struct Rec {
@@ -200,6 +203,12 @@ void prof_mark(void *ctx, int group, int begin)
 {
     gks_grid *g = (gks_grid *)ctx;
     Profiler &p = g->prof;
+    if (p.nvtx) {
+        if (begin)
+            nvtxRangePushA(gks_kernel_group_name(group));
+        else
+            nvtxRangePop();
+    }
     if (begin) {
         p.launches[group]++;
         if (p.timing) {
@@ -338,6 +347,8 @@ int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_
     g->d_diag = (double *)(w + L.o_diag);
     c.staging = (double *)c.ff[0];   // the face-flux buffers hold >= 4 N doubles
     c.mark = prof_mark;
+    const char *nv = getenv("GKS_NVTX");
+    g->prof.nvtx = nv && nv[0] == '1';
     c.mark_ctx = g;
 
     // geometry tables

@@ -341,6 +341,29 @@ def time_adjoint(args, dev):
     return res
 
 
+def time_small_graphs(dev, steps=500):
+    """A launch-bound case: the 32^3 Taylor-Green vortex in FP32C, plain
+    steps against steps replayed from a CUDA graph (gks_set_graphs)."""
+    import torch
+
+    from paper_2603_11102_gb300 import gks
+    w = WL.taylor_green_3d(32)
+    out = {"workload": "taylor-green-32^3", "precision": "fp32-compensated", "steps": steps}
+    for key, on in (("plain_mlups", False), ("graph_mlups", True)):
+        g = gks.Grid.from_workload(w, precision="fp32c", device=dev)
+        g.set_graphs(on)
+        g.step(5)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        g.step(steps, sync=False)
+        b.record(g.stream)
+        g.sync()
+        out[key] = w.cells * steps / (a.elapsed_time(b) / 1e3) / 1e6
+        g.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -487,6 +510,8 @@ def run_ours(args, world, rank, local):
                 "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
         g64.close()
 
+    graphs = time_small_graphs(dev) if rank == 0 and not args.no_graphs else None
+
     adj = None
     if args.adjoint_steps > 0 and rank == 0:
         adj = time_adjoint(args, dev)
@@ -511,7 +536,7 @@ def run_ours(args, world, rank, local):
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "hbm_step": hbm, "kernel_share": share, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64,
-            "adjoint": adj}
+            "small_grid_graphs": graphs, "adjoint": adj}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -544,6 +569,7 @@ def main():
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-graphs", action="store_true", help="skip the small-grid CUDA graph timing")
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-k", type=int, default=20)

@@ -189,6 +189,15 @@ int gks_step_async(gks_grid *g, int nsteps);
 /* Synchronise the grid's stream, report errors flagged on the device as
  * gks_step does, and give the current time (t_out may be NULL). */
 int gks_sync(gks_grid *g, double *t_out);
+/* With on != 0, gks_step and gks_step_async replay a CUDA graph of one step
+ * once the grid is in its steady state (a plain step done, the next step's
+ * input prepared by the last one, at most 8 forcing objects, profiling
+ * timing and NVTX off): one graph launch per step instead of one launch per
+ * kernel, which pays on small grids whose steps are launch-bound. The graph
+ * is captured when first needed and again after gks_set_inflow,
+ * gks_set_body_force or gks_profile_enable; results are the same bits as
+ * plain steps. Off by default. */
+int gks_set_graphs(gks_grid *g, int on);
 
 /* Current time and the last time step (synchronises). */
 int gks_get_time(gks_grid *g, double *t, double *dt_last);

@@ -51,6 +51,15 @@ struct gks_grid {
     bool prep_valid = false;
     // gks_step_adjoint: FP32 arithmetic in the local reverse maps
     bool adj_fp32 = false;
+    // CUDA graph of one steady-state step (gks_set_graphs): captured when
+    // first needed and again after any change of what its launches read by
+    // value (inflow, body force, profiling mode), counted by `version`
+    bool use_graphs = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // capture stream (the grid's own may be the legacy one)
+    long version = 0, graph_version = -1;
+    long graph_launches[K_NGROUPS] = {0};
 };
 
 namespace {
@@ -400,6 +409,9 @@ int gks_destroy_grid(gks_grid *g)
 {
     if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
     cudaStreamSynchronize(g->c.stream);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (void *p : g->owned) cudaFree(p);
     for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
     delete g;
@@ -446,6 +458,7 @@ int gks_set_inflow(gks_grid *g, double rho, double u, double v, double w)
     g->c.inflow[1] = u;
     g->c.inflow[2] = v;
     g->c.inflow[3] = w;
+    g->version++;
     return GKS_OK;
 }
 
@@ -455,6 +468,7 @@ int gks_set_body_force(gks_grid *g, double fx, double fy, double fz)
     g->c.fbody[0] = fx;
     g->c.fbody[1] = fy;
     g->c.fbody[2] = fz;
+    g->version++;
     return GKS_OK;
 }
 
@@ -735,13 +749,83 @@ int check_flags(gks_grid *g, int flags, const char *where)
 }
 }  // namespace
 
+namespace {
+// Capture one step (as step_once enqueues it in the current host state) into
+// the grid's graph. Nothing runs; the host-side effects of the captured step
+// (step count, launch counters) are undone, a replay redoes them.
+int capture_step(gks_grid *g)
+{
+    Ctx &c = g->c;
+    int rc = GKS_OK;
+    if (!g->cap_stream &&
+        (rc = cuda_check(g, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "capture stream")))
+        return rc;
+    long saved[K_NGROUPS];
+    memcpy(saved, g->prof.launches, sizeof(saved));
+    const long nstep0 = g->nstep;
+    const cudaStream_t own = c.stream;
+    c.stream = g->cap_stream;
+    rc = cuda_check(g, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) {
+        c.stream = own;
+        return rc;
+    }
+    rc = step_once(g, nullptr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
+    c.stream = own;
+    g->nstep = nstep0;
+    for (int k = 0; k < K_NGROUPS; ++k) {
+        g->graph_launches[k] = g->prof.launches[k] - saved[k];
+        g->prof.launches[k] = saved[k];
+    }
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : cuda_check(g, e, "end capture");
+    }
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = graph;
+    rc = cuda_check(g, cudaGraphInstantiate(&g->gexec, graph, 0), "instantiate graph");
+    if (rc) return rc;
+    g->graph_version = g->version;
+    return GKS_OK;
+}
+}  // namespace
+
+int gks_set_graphs(gks_grid *g, int on)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    g->use_graphs = on != 0;
+    return GKS_OK;
+}
+
 int gks_step_async(gks_grid *g, int nsteps)
 {
     if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
-    g->stepped = true;
     for (int s = 0; s < nsteps; ++s) {
-        int rc = step_once(g, nullptr);
-        if (rc) return rc;
+        // a step replays the graph in the steady state: the next step's
+        // prep done by the last step (at most kMaxPrepBoxes forcing
+        // objects), no per-launch profiling, and one plain step done before
+        // (the kernels' one-time launch setup)
+        const bool replay = g->use_graphs && g->stepped && g->prep_valid && g->obj_kind.size() <= 8 &&
+                            !g->prof.timing && !g->prof.nvtx;
+        int rc;
+        if (replay) {
+            if (!g->gexec || g->graph_version != g->version) {
+                rc = capture_step(g);
+                if (rc) return rc;
+            }
+            rc = cuda_check(g, cudaGraphLaunch(g->gexec, g->c.stream), "graph launch");
+            if (rc) return rc;
+            for (int k = 0; k < K_NGROUPS; ++k) g->prof.launches[k] += g->graph_launches[k];
+            g->nstep++;
+        } else {
+            g->stepped = true;
+            rc = step_once(g, nullptr);
+            if (rc) return rc;
+        }
     }
     return GKS_OK;
 }
@@ -1160,6 +1244,7 @@ int gks_profile_enable(gks_grid *g, int timing_on)
     if (rc) return rc;
     Profiler &p = g->prof;
     p.timing = timing_on != 0;
+    g->version++;
     p.next = 0;
     p.last_end = nullptr;
     p.recs.clear();

@@ -87,6 +87,7 @@ SIGNATURES = {
     "gks_adjoint_workspace_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "gks_forces_record_len": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
     "gks_step_async": (C.c_int, [C.c_void_p, C.c_int]),
+    "gks_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "gks_forces_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "gks_adjoint_tape_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -280,6 +281,11 @@ class Grid:
         t = C.c_double()
         _check(lib.gks_step(self.h, int(nsteps), C.byref(t)), self.h)
         return t.value
+
+    def set_graphs(self, on=True):
+        """Replay a CUDA graph of one step in the steady state (see
+        gks_set_graphs); the same results as plain steps."""
+        _check(lib.gks_set_graphs(self.h, int(bool(on))), self.h)
 
     def sync(self):
         """Wait for the grid's stream; report device-side errors; the time."""

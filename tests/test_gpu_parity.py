@@ -307,3 +307,30 @@ def test_async_steps_and_load_records(gks, precision):
     assert np.array_equal(brec.numpy()[:3], fb["force"]) and int(brec[3]) == fb["iters"]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_graph_replayed_steps_are_plain_steps(gks, precision):
+    """Steps replayed from a CUDA graph give the bits plain steps give, with
+    the same launch count, also across a change of the inflow (which makes
+    the grid capture the step again)."""
+    w = WL.alm_ibm_rotor(n=(64, 32, 32), steps=1, n_pts=10)
+    w.state0 = WL.perturbed(w, 0.02, seed=4)
+    a = gks.Grid.from_workload(w, precision=precision)
+    b = gks.Grid.from_workload(w, precision=precision)
+    b.set_graphs(True)
+    for g in (a, b):
+        g.profile_enable(timing=False)
+        g.step(1)
+        g.step(3)
+        g.set_inflow(1.0, 1.05, 0.0, 0.0)
+        g.step(2, sync=False)
+        g.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.time == b.time
+    pa, pb = a.profile_read(), b.profile_read()
+    assert pa["launches"] == pb["launches"] and pa["total_launches"] == pb["total_launches"] > 0
+    fa, fb = a.forces(0), b.forces(0)
+    assert fa["power"] == fb["power"] and np.array_equal(a.forces(1)["force"], b.forces(1)["force"])
+    a.close()
+    b.close()

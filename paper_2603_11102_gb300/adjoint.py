@@ -77,9 +77,10 @@ class RotorObjective(torch.autograd.Function):
         dt = grid.dt_fixed
         ckpts = {0: uniform_state(grid, u)}
         for n in range(nsteps):
-            grid.step(1)
+            grid.step(1, sync=False)   # stream-ordered; device errors surface at the sync below
             if (n + 1) % K == 0 and n + 1 < nsteps:
                 ckpts[n + 1] = grid.state_tensor()
+        grid.sync()
         WN = grid.state_tensor()
         P = grid.forces(0)["power"]
         J = plane_deficit(WN, iplane, u) + beta * P

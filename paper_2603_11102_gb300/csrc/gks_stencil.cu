@@ -735,6 +735,29 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 
 // Resident blocks per SM x SMs for a persistent kernel with `smem` bytes of
 // dynamic shared memory (raises its dynamic shared-memory limit first).
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Faces per thread of the marching face-state kernel: kMarch, halved (down
+// to 4) while the launch would have fewer than two blocks per SM, so that a
+// small grid spreads its march over the GPU (each halving adds one WENO5 pair
+// per thread to warm the window up).
+int march_faces(long blocks_xy, int nf)
+{
+    int K = kMarch;
+    while (K > 4 && blocks_xy * ((nf + K - 1) / K) < 2L * sm_count()) K /= 2;
+    return K;
+}
+
 template <typename K>
 int persistent_grid(K kernel, size_t smem)
 {
@@ -811,9 +834,9 @@ void stage_impl(const Ctx &c)
         E.c2 = 1 + t2;
         E.ph = ph;
         E.nf = c.n[d] + 1;
-        E.K = kMarch;
+        E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf);
         const CUtensorMap &tmap = c.tmap[d];
-        dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + kMarch - 1) / kMarch);
+        dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
         mark(c, K_FACE_EQ, 1);
         face_eq_march_kernel<R><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);

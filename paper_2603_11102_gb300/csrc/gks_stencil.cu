@@ -750,7 +750,9 @@ int sm_count()
 // Faces per thread of the marching face-state kernel: kMarch, halved (down
 // to 4) while the launch would have fewer than two blocks per SM, so that a
 // small grid spreads its march over the GPU (each halving adds one WENO5 pair
-// per thread to warm the window up).
+// per thread to warm the window up). A model that traded waves of resident
+// blocks against the per-thread work chose shorter marches for the large
+// grids too and was slower there.
 int march_faces(long blocks_xy, int nf)
 {
     int K = kMarch;

@@ -40,6 +40,8 @@ extern "C" {
 #define GKS_ERR_CFL (-4)       /* fixed time step above the CFL limit given        */
 #define GKS_ERR_STATE (-5)     /* call not allowed in the current state             */
 #define GKS_ERR_RANGE (-6)     /* actuator point outside the sampled interior       */
+#define GKS_ERR_DEBUG_BOUNDS (-7) /* debug-bounds build only: a kernel met an index
+                                     outside its buffer (the access was skipped)     */
 
 #define GKS_MAX_BLADES 8
 

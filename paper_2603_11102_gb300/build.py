@@ -2,7 +2,11 @@
 
 Each CUDA translation unit is compiled in parallel, then linked into
 ``paper_2603_11102_gb300/_build/libgks.so``. Run ``python -m
-paper_2603_11102_gb300.build`` or call :func:`build`.
+paper_2603_11102_gb300.build`` or call :func:`build`. ``build(debug=True)``
+(or ``--debug-bounds``) builds ``_build/debug/libgks_debug.so`` with
+GKS_DEBUG_BOUNDS: kernels check their data-dependent indices and the calls
+report GKS_ERR_DEBUG_BOUNDS instead of touching memory outside a buffer;
+``gks.load`` takes it when the environment variable GKS_DEBUG_BOUNDS=1.
 """
 from __future__ import annotations
 
@@ -16,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgks.so")
+OUT_DEBUG = os.path.join(OUT, "debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libgks_debug.so")
 SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu", "gks_adjoint.cu"]
 HEADERS = ["gks_internal.h", "gks_device.cuh", os.path.join(ROOT, "include", "gks_api.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -33,24 +39,27 @@ def flags(extra=()):
                    "-I", CSRC] + list(extra)
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [h if os.path.isabs(h) else os.path.join(CSRC, h)
                                                        for h in HEADERS]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    lib, out = (LIB_DEBUG, OUT_DEBUG) if debug else (LIB, OUT)
+    if debug:
+        extra = list(extra) + ["-DGKS_DEBUG_BOUNDS"]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(out, s.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [cc] + flags(extra) + ["-c", os.path.join(CSRC, s), "-o", obj]
         if verbose:
@@ -65,13 +74,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(out.decode(errors="replace"))
     if errors:
         raise RuntimeError("nvcc failed\n" + "\n".join(errors))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else (), debug="--debug-bounds" in sys.argv))

@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "gks_bounds.cuh"
 #include "gks_device.cuh"
 #include "gks_internal.h"
 
@@ -361,6 +362,7 @@ __global__ void __launch_bounds__(256) rev_flux_kernel(RevArgs A)
     cr[A.d] = f; cr[A.t1] = a; cr[A.t2] = b;
     const bool hasl = f - 1 >= 0, hasr = f < A.nd;
     const long il = lin(A.P[0], A.P[1], cl[0], cl[1], cl[2]), ir = lin(A.P[0], A.P[1], cr[0], cr[1], cr[2]);
+    if (!in_bounds(il, A.np) || !in_bounds(ir, A.np) || !in_bounds(((long)f * A.n2 + b) * A.n1 + a, A.nG)) return;
     const T ihl = hasl ? T(A.ihd[f - 1 + G]) : T(0), ihr = hasr ? T(A.ihd[f + G]) : T(0);
     for (int v = 0; v < 4; ++v) {
         const long o = gc[v] * A.np;
@@ -421,6 +423,11 @@ __global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
             for (int k = 0; k < 8; ++k) x[k] = T(0);
             return;
         }
+        if (!in_bounds(((long)f * A.n2 + b) * A.n1 + a, nG)) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = T(0);
+            return;
+        }
         const T *Gf = (const T *)A.lamGa + ((long)f * A.n2 + b) * A.n1 + a;
 #pragma unroll
         for (int nn = 0; nn < 2; ++nn) {
@@ -452,6 +459,7 @@ __global__ void __launch_bounds__(256) rev_t2_kernel(RevArgs A)
             }
         }
         const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
+        if (!in_bounds(row, A.nR)) continue;
         T *lr = (T *)A.lamR;
         lr[(0 * 8 + m * 4 + v) * A.nR + row] = X;
         lr[(1 * 8 + m * 4 + v) * A.nR + row] = Y;
@@ -472,6 +480,7 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
     for (int a = alo; a <= ahi; ++a) {
         const int r = ap - a + 2;
         const long row = ((long)f * (A.n2 + 4) + (bp + 2)) * A.n1 + a;
+        if (!in_bounds(row, A.nR)) continue;
         for (int m = 0; m < 2; ++m) {
             const T wv = T(cWV[m][r]), wd = T(cWD[m][r]);
             for (int v = 0; v < 4; ++v) {
@@ -481,6 +490,7 @@ __global__ void __launch_bounds__(256) rev_t1_kernel(RevArgs A)
         }
     }
     const long o = ((long)f * (A.n2 + 4) + (bp + 2)) * A.e1p + (ap + 2);
+    if (!in_bounds(o, A.nfq)) return;
     T *fq = (T *)A.lamFQ;
     for (int v = 0; v < 4; ++v) {
         fq[v * A.nfq + o] = lq[v];
@@ -512,6 +522,11 @@ __global__ void __launch_bounds__(256) rev_face_state_kernel(RevArgs A)
     int cc[3];
     cc[A.d] = 0; cc[A.t1] = a; cc[A.t2] = b;
     const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);   // cell 0 along d
+    // cells f0-4 .. f1+1 are read, faces f0-1 .. f1-1 read and written
+    if (!in_bounds(base + (long)(f0 - 4 < -G ? -G : f0 - 4) * sd, A.np) || !in_bounds(base + (long)(f1 + 1) * sd, A.np) ||
+        !in_bounds(((long)(f0 > 0 ? f0 - 1 : 0) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
     const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
     // window w[v][k] = cell f-3+k at face f; before the first face: cells f0-4 .. f0+1
     double w[4][6];
@@ -622,6 +637,11 @@ __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
     int cc[3];
     cc[A.d] = 0; cc[A.t1] = a; cc[A.t2] = b;
     const long base = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    // cells f0-4 .. f1+1 are read, faces f0-1 .. f1-1 read and written
+    if (!in_bounds(base + (long)(f0 - 4 < -G ? -G : f0 - 4) * sd, A.np) || !in_bounds(base + (long)(f1 + 1) * sd, A.np) ||
+        !in_bounds(((long)(f0 > 0 ? f0 - 1 : 0) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
     const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
     const Phys<float> ph = phys_as<float>(A.ph);
     float wh[4][6], wl[4][6];
@@ -724,11 +744,13 @@ __global__ void __launch_bounds__(256) rev_gather_cells_kernel(RevArgs A)
     for (int f = flo; f <= fhi; ++f) {
         const int m = c - f + 3;
         const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+        if (!in_bounds(o, A.nfq)) continue;
         for (int v = 0; v < 4; ++v) acc[v] += lamC[(m * 4 + v) * A.nfq + o];
     }
     int cc[3];
     cc[A.d] = c; cc[A.t1] = a; cc[A.t2] = b;
     const long l = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
+    if (!in_bounds(l, A.np)) return;
     for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + l] += (double)acc[v];
 }
 
@@ -764,6 +786,7 @@ __global__ void __launch_bounds__(256) ghost_rev_kernel(GhostRevArgs A)
     cg[d] = gi; cg[A.e1] = a; cg[A.e2] = b;
     cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
     const long ig = lin(A.P[0], A.P[1], cg[0], cg[1], cg[2]), is = lin(A.P[0], A.P[1], cs[0], cs[1], cs[2]);
+    if (!in_bounds(ig, A.np) || !in_bounds(is, A.np)) return;
     double lg[4];
     for (int v = 0; v < 4; ++v) {
         lg[v] = A.lamA[v * A.np + ig];
@@ -1404,5 +1427,7 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }
+
+int bounds_flag_adjoint() { return bounds_flag_take(); }
 
 }  // namespace gks

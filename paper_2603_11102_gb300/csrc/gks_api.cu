@@ -723,11 +723,20 @@ int step_once(gks_grid *g, const AdjWork *tp)
     return GKS_OK;
 }
 
+// Debug-bounds builds: whether a kernel met an index outside its buffer
+// since the last look (always false in a plain build).
+bool bounds_hit()
+{
+    const int f = bounds_flag_stencil() | bounds_flag_forcing() | bounds_flag_adjoint();
+    return f != 0;
+}
+
 int finish_steps(gks_grid *g, double *t_out)
 {
     Scalars sc;
     int rc = read_scalars(g, &sc);
     if (rc) return rc;
+    if (bounds_hit()) return fail(g, GKS_ERR_DEBUG_BOUNDS, "a kernel met an index outside its buffer");
     if (t_out) *t_out = sc.t;
     if (sc.flags) {
         int flags = 0;
@@ -1142,6 +1151,7 @@ int reverse_from_tape(gks_grid *g, const AdjWork &w, bool init_sc, double t_n, d
                              "read reverse flags");
     if (!rc) rc = sync(g);
     if (rc) return rc;
+    if (bounds_hit()) return fail(g, GKS_ERR_DEBUG_BOUNDS, "a kernel met an index outside its buffer");
     if (flags) return check_flags(g, flags, "adjoint step");
     if (h_grad_scales)
         for (long q = 0; q < npts; ++q) h_grad_scales[q] += pts[8 * q + 2];

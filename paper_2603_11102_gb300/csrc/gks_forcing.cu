@@ -24,6 +24,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "gks_bounds.cuh"
 #include "gks_internal.h"
 
 namespace gks {
@@ -317,6 +318,7 @@ __global__ void __launch_bounds__(256) alm_spread_kernel(Lattice L, void *S, Rot
     }
     if (!any) return;
     const long lin = lin_index(L, i, j, k);
+    if (!in_bounds(lin, L.np)) return;
     const double dt = scal->dt;
     if constexpr (std::is_same<R, double>::value) {
         double *W = (double *)S;
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(256) ibm_iter_kernel(Lattice L, void *S, BodyD
     const int j = b.box[1][0] + (int)((c / bx) % by);
     const int k = b.box[2][0] + (int)(c / ((long)bx * by));
     const long lin = lin_index(L, i, j, k);
+    if (!in_bounds(lin, L.np)) return;
     const double dt = scal->dt;
     const double vol = L.h[0] * L.h[1] * L.h[2];
     const double phi = b.phi[c];
@@ -478,6 +481,7 @@ __global__ void __launch_bounds__(256) ibm_velocity_kernel(Lattice L, const void
     const int j = b.box[1][0] + (int)((c / bx) % by);
     const int k = b.box[2][0] + (int)(c / ((long)bx * by));
     double q[4];
+    if (!in_bounds(lin_index(L, i, j, k), L.np)) return;
     cell_state(L, S, lin_index(L, i, j, k), q);
     R *U = std::is_same<R, double>::value ? (R *)b.Ubox : (R *)b.Uboxf;
 #pragma unroll
@@ -501,6 +505,7 @@ __global__ void __launch_bounds__(256) ibm_residual_kernel(BodyDev b)
     for (long o = o0 + lane; o < o1; o += 32) {
         const R W = Wt[o];
         const long c = b.csr_cell[o];
+        if (!in_bounds(c, b.nbox)) continue;
         u0 += W * U[3 * c];
         u1 += W * U[3 * c + 1];
         u2 += W * U[3 * c + 2];
@@ -667,5 +672,7 @@ void launch_ibm(const Ctx &c, const BodyDev &b)
     ibm_force_final_kernel<<<1, 256, 0, c.stream>>>(b, c.partials, nparts);
     mark(c, K_IBM, 0);
 }
+
+int bounds_flag_forcing() { return bounds_flag_take(); }
 
 }  // namespace gks

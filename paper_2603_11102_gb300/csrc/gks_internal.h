@@ -94,6 +94,12 @@ inline void mark(const Ctx &c, int group, int begin)
 // Message returned by gks_last_error(NULL) on this thread (gks_api.cu).
 void record_error(const char *msg);
 
+// Debug-bounds builds: the index-check flag of each translation unit with
+// kernels, taken and cleared (always 0 in a plain build).
+int bounds_flag_stencil();
+int bounds_flag_forcing();
+int bounds_flag_adjoint();
+
 // Launchers of the stencil path (gks_stencil.cu).
 void launch_prep(const Ctx &c);                        // max |U|^2 into scal; FP32C: state -> wk0
 void launch_prep_box(const Ctx &c, const int box[3][2]);   // the same over the interior cells of a box

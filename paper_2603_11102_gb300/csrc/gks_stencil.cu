@@ -26,6 +26,7 @@
 
 #include <type_traits>
 
+#include "gks_bounds.cuh"
 #include "gks_device.cuh"
 #include "gks_internal.h"
 
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) ghost_kernel(GhostArgs<R> A)
     cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
     const long ig = (long)(cg[0] + G) + (long)A.P[0] * ((long)(cg[1] + G) + (long)A.P[1] * (cg[2] + G));
     const long is = (long)(cs[0] + G) + (long)A.P[0] * ((long)(cs[1] + G) + (long)A.P[1] * (cs[2] + G));
+    if (!in_bounds(ig, A.np) || !in_bounds(is, A.np)) return;
     R q[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = A.w[v * A.np + is];
@@ -155,6 +157,11 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
     if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= A.nf) return;
     const int f1 = min(f0 + A.K, A.nf);
     const long base = (long)(a + G) * A.s1 + (long)(b + G) * A.s2;   // cell index along d = -G
+    // cells f0-3 .. f1+1 are read, faces f0 .. f1-1 written
+    if (!in_bounds(base + (long)(f0 - 3 + G) * A.sd, A.np) || !in_bounds(base + (long)(f1 + 1 + G) * A.sd, A.np) ||
+        !in_bounds(((long)f0 * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
     const int comp[4] = {0, A.cn, A.c1, A.c2};
     const Phys<R> &ph = A.ph;
     // window w[v][k] = cell (c - 2 + k); start with c = f0 - 1
@@ -430,6 +437,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
+                if (!in_bounds(o, A.nff)) break;
                 if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
                 A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * acc1[v];
             }
@@ -620,7 +628,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                 long go = xf * sxf;
 #pragma unroll
                 for (int i = 0; i < (NC * SX_H + 31) / 32; ++i) {
-                    if (c < NC && a0 + xf <= U.nx) cp_async(sx + (c * SX_H + xf) * SX_W + yy, src + go);
+                    if (c < NC && a0 + xf <= U.nx &&
+                        in_bounds(((long)(a0 + xf) * U.nz + (f - 1)) * U.ny + b0 + yy, U.nffx))
+                        cp_async(sx + (c * SX_H + xf) * SX_W + yy, src + go);
                     xf += 32;
                     go += 32 * sxf;
                     if (xf >= SX_H) {
@@ -646,20 +656,24 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         }
         R dy[8], s0[4], s1[4];
         long lin = 0;
+        bool cell_ok = true;
         if (upd && in) {
             const int z = f - 1;
             lin = (long)(a + G) + (long)U.P0 * ((long)(b + G) + (long)U.P1 * (z + G));
             const long iy = ((long)b * U.nz + z) * U.nx + a, sy = (long)U.nz * U.nx;
+            cell_ok = in_bounds(lin, U.np) && in_bounds(iy, U.nffy) && in_bounds(iy + sy, U.nffy);
+            if (cell_ok) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const R *py = U.ffy + (C0 + c) * U.nffy + iy;
-                dy[C0 + c] = __ldg(py + sy) - __ldg(py);
-            }
-            const R *src = (const R *)(STAGE == 1 ? U.w0 : U.pbuf);
+                for (int c = 0; c < NC; ++c) {
+                    const R *py = U.ffy + (C0 + c) * U.nffy + iy;
+                    dy[C0 + c] = __ldg(py + sy) - __ldg(py);
+                }
+                const R *src = (const R *)(STAGE == 1 ? U.w0 : U.pbuf);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                s0[v] = __ldg(src + v * U.np + lin);
-                s1[v] = std::is_same<R, double>::value ? R(0) : __ldg(src + (4 + v) * U.np + lin);
+                for (int v = 0; v < 4; ++v) {
+                    s0[v] = __ldg(src + v * U.np + lin);
+                    s1[v] = std::is_same<R, double>::value ? R(0) : __ldg(src + (4 + v) * U.np + lin);
+                }
             }
         }
         const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
@@ -688,7 +702,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         if (upd) {
             cp_async_wait_all();
             __syncthreads();   // the x-face slab of every thread is in place
-            if (in) {
+            if (in && cell_ok) {
                 const int z = f - 1;
                 R dx[8], dz[8];
 #pragma unroll
@@ -1263,5 +1277,7 @@ void launch_diagnostics(const Ctx &c, double *d_out5)
                                                   c.partials);
     diag_final_kernel<<<1, 256, 0, c.stream>>>(c.partials, nb, d_out5);
 }
+
+int bounds_flag_stencil() { return bounds_flag_take(); }
 
 }  // namespace gks

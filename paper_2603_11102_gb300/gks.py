@@ -18,7 +18,8 @@ from . import build as _build
 
 GKS_OK = 0
 ERRORS = {-1: "GKS_ERR_ARG", -2: "GKS_ERR_CUDA", -3: "GKS_ERR_NONFINITE", -4: "GKS_ERR_CFL",
-          -5: "GKS_ERR_STATE", -6: "GKS_ERR_RANGE"}
+          -5: "GKS_ERR_STATE", -6: "GKS_ERR_RANGE",
+          -7: "GKS_ERR_DEBUG_BOUNDS"}
 FP64, FP32C = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32c": FP32C}
 MAX_BLADES = 8
@@ -106,7 +107,9 @@ lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The plain library, or the debug-bounds one when the environment
+    variable GKS_DEBUG_BOUNDS=1 (built by ``build.build(debug=True)``)."""
+    return _build.LIB_DEBUG if os.environ.get("GKS_DEBUG_BOUNDS") == "1" else _build.LIB
 
 
 def load(path: str | None = None):

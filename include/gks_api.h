@@ -14,7 +14,9 @@
  *     (for example torch tensors): the library never frees it, and it must
  *     outlive the grid. The library owns only the small device buffers it
  *     allocates for actuator lines and immersed bodies (freed by
- *     gks_destroy_grid); a time step allocates nothing.
+ *     gks_destroy_grid); a time step allocates nothing (with gks_set_graphs
+ *     the first captured step also creates the graph and a capture stream,
+ *     likewise freed by gks_destroy_grid).
  *   - Work is enqueued on the CUDA stream given in the grid description (NULL
  *     = the legacy default stream). Calls that return results to the host
  *     synchronise that stream.

@@ -46,15 +46,31 @@ struct GhostArgs {
     int bc0, bc1;
     R off, csound;
     R uin[3];
+    int rows;   // x ghosts (d = 0): one thread per ghost of a (y, z) row, rows x 2G threads
 };
 
 template <typename R>
 __global__ void __launch_bounds__(256) ghost_kernel(GhostArgs<R> A)
 {
-    const int a = A.lo1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    const int b = A.lo2 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-    if (a >= A.lo1 + A.len1 || b >= A.lo2 + A.len2) return;
-    const int s = blockIdx.z / G, l = blockIdx.z % G + 1;
+    int a, b, s, l;
+    if (A.rows) {
+        // x ghosts: consecutive threads take the 2G ghosts of one row, whose
+        // cells are contiguous in memory (the lanes of a warp cover ~5 rows)
+        const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+        const long r = t / (2 * G);
+        if (r >= A.rows) return;
+        const int k = (int)(t - r * 2 * G);
+        s = k / G;
+        l = k % G + 1;
+        a = A.lo1 + (int)(r % A.len1);
+        b = A.lo2 + (int)(r / A.len1);
+    } else {
+        a = A.lo1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+        b = A.lo2 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+        if (a >= A.lo1 + A.len1 || b >= A.lo2 + A.len2) return;
+        s = blockIdx.z / G;
+        l = blockIdx.z % G + 1;
+    }
     const int d = A.d, nd = A.n[d];
     const int bc = s == 0 ? A.bc0 : A.bc1;
     const int gi = s == 0 ? -l : nd - 1 + l;
@@ -117,9 +133,16 @@ void ghost_impl(const Ctx &c, R *w)
         A.off = (R)c.off;
         A.csound = (R)c.csound;
         for (int e = 0; e < 3; ++e) A.uin[e] = (R)c.inflow[1 + e];
-        dim3 blk(32, 8), grd((A.len1 + 31) / 32, (A.len2 + 7) / 8, 2 * G);
         mark(c, K_GHOST, 1);
-        ghost_kernel<R><<<grd, blk, 0, c.stream>>>(A);
+        if (d == 0) {
+            A.rows = A.len1 * A.len2;
+            const long nt = (long)A.rows * 2 * G;
+            ghost_kernel<R><<<(int)((nt + 255) / 256), 256, 0, c.stream>>>(A);
+        } else {
+            A.rows = 0;
+            dim3 blk(32, 8), grd((A.len1 + 31) / 32, (A.len2 + 7) / 8, 2 * G);
+            ghost_kernel<R><<<grd, blk, 0, c.stream>>>(A);
+        }
         mark(c, K_GHOST, 0);
     }
 }

@@ -27,6 +27,11 @@
  *   - IBM spreading, direct forcing iteration: Sec. 3.2, Eq. (ibm-1),
  *     Eq. (force-ibm); forcing after the S2O4 update: end of Sec. 3.2.
  *   - Power and thrust coefficients: Sec. 4.4.1.
+ *   - Airfoil polar: the paper's airfoil tables are not available; a
+ *     synthetic analytic polar stands in (lift 2 pi sin(alpha) clipped at
+ *     +-1.4, drag 0.01 + 0.02 alpha^2). Parity unpinned beyond its
+ *     definition: the special values its tests check (no lift at alpha = 0,
+ *     the thin-airfoil slope, the clip) are the definition itself.
  *   - Boundary conditions: Sec. 4.1 (periodic, no-slip wall), Sec. 4.3
  *     (Riemann-invariant inflow, extrapolation outflow, slip wall), Sec. 4.4
  *     (symmetry).

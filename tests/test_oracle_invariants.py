@@ -364,3 +364,56 @@ def test_alm_tip_correction_special_values():
     # the two coefficient pairs give different factors at the same point
     assert abs(f1["Ft"][0, 1] / f0["Ft"][0, 1] - 2.0 / 3.0) > 1e-3
     assert np.all(f1["Fx"][:, 0] / f0["Fx"][:, 0] < 1.0)
+
+
+def test_alm_point_loads_follow_blade_element_geometry():
+    """Sec. 3.1, Eq. (axial-tangential): a blade element feels the air moving
+    past it at w = (U_x, U_theta - omega r) in the (axial, tangential) plane;
+    drag acts along w and lift across it, each 1/2 rho |w|^2 c (span width)
+    times its coefficient, and the point force is the sum. In a uniform axial
+    stream U_inf = 1 the sampled velocity is exactly (1, 0, 0) at the first
+    step, so w = (1, -omega r) follows from the geometry alone. The force
+    resolved by dot products along and across w gives back drag and lift;
+    the polar's special cases fix the coefficients: no lift at alpha = 0, the
+    thin-airfoil slope 2 pi below stall (C_L = 2 pi sin alpha), the stall
+    clip +-1.4 and the drag 0.01 + 0.02 alpha^2. Per-point chord, width and
+    target angle differ so that a mixed-up index, a swapped sine and cosine
+    or a wrong sign shows; the force scale multiplies the load."""
+    n = (24, 32, 32)
+    dom = [(-0.5, 0.5), (-0.7, 0.7), (-0.7, 0.7)]
+    dx = 1.0 / n[0]
+    base = WL.rotor_3x50(D=1.0, hub=(0.0, 0.0, 0.0), dx=dx, n_pts=10)
+    R, N, om = base.radius, base.n_blades, base.omega
+    radii = np.array([0.3, 0.5, 0.7, 0.9]) * R
+    target = np.array([0.0, 0.05, 0.5, -0.5])           # angle of attack per point
+    chord = np.array([0.05, 0.07, 0.04, 0.06])
+    width = np.array([0.02, 0.03, 0.025, 0.015])
+    phi = np.arctan2(1.0, om * radii)                    # flow angle from the geometry
+    twist = phi - target
+    out = {}
+    for scale in (1.0, 2.0):
+        g, _ = uniform_flow_grid(n, dom)
+        rid = g.add_rotor(N, radii, chord, twist, width, (0.0, 0.0, 0.0), om, 0.3, R, 2 * dx)
+        if scale != 1.0:
+            g.set_force_scales(rid, np.full(N * len(radii), scale))
+        g.step(1)
+        out[scale] = g.forces(rid)
+    f = out[1.0]
+    assert np.allclose(f["alpha"], target[None, :], rtol=0, atol=1e-14)
+    Wx, Wt = np.ones_like(radii), -om * radii
+    W = np.hypot(Wx, Wt)
+    qd = 0.5 * 1.0 * W ** 2 * chord * width
+    along = (f["Fx"] * Wx + f["Ft"] * Wt) / W              # component along the relative wind
+    across = (f["Fx"] * (-Wt) + f["Ft"] * Wx) / W          # rotated +90 deg: lift direction
+    cd = 0.01 + 0.02 * target ** 2
+    cl = np.array([0.0, 2 * math.pi * math.sin(0.05), 1.4, -1.4])
+    assert np.allclose(along, (qd * cd)[None, :], rtol=1e-12, atol=0)
+    assert np.allclose(across, (qd * cl)[None, :], rtol=1e-12, atol=1e-18)
+    # thin-airfoil slope below stall, to O(alpha^3)
+    assert abs(across[0, 1] / (qd[1] * 0.05) - 2 * math.pi) < 2 * math.pi * 0.05 ** 2 / 6 * 1.01
+    # a turbine: positive lift gives thrust and driving torque
+    assert np.all(f["Fx"][:, 1:3] > 0) and np.all(f["Ft"][:, 1:3] > 0)
+    # thrust, torque and power are the sums over points
+    assert np.allclose(f["thrust"], f["Fx"].sum(axis=1), rtol=1e-14)
+    assert np.allclose(f["torque"], (f["Ft"] * radii[None, :]).sum(axis=1), rtol=1e-14)
+    assert np.array_equal(out[2.0]["Fx"], 2.0 * f["Fx"]) and np.array_equal(out[2.0]["Ft"], 2.0 * f["Ft"])

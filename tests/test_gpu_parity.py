@@ -147,6 +147,34 @@ def test_actuator_lines_and_immersed_bodies(gks, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_moving_immersed_bodies(gks, precision):
+    """Eq. (ibm-1) with prescribed point velocities (the velocity argument of
+    gks_add_ib_points): the tower and the nacelle each turn about their own
+    centroid, at different rates about different axes, so that every point
+    has its own velocity and the target velocity varies across the shell."""
+    w = small_rotor_workload(ibm=True, n=(72, 32, 32))
+    for body, Om in zip(w.bodies, ([0.0, 0.0, 20.0], [6.0, -4.0, 3.0])):
+        c = body.xyz.mean(axis=0)
+        body.vel = np.cross(np.array(Om), body.xyz - c)
+    g, o, _ = run_pair(gks, w, precision, 3)
+    a, b = g.get_state(), o.get_state()
+    assert rel_linf(a, b) <= TOL[precision], rel_linf_components(a, b)
+    tol = 1e-10 if precision == "fp64" else 2e-4
+    for oid in (1, 2):
+        fg, fo = g.forces(oid), o.forces(oid)
+        assert np.max(np.abs(fg["force"] - fo["force"])) <= tol * np.max(np.abs(fo["force"])), (fg, fo)
+        assert fg["iters"] == fo["iters"]
+        assert abs(fg["residual"] - fo["residual"]) <= tol * max(abs(fo["residual"]), 1e-12)
+    g.close()
+    # the velocities matter: the same bodies at rest feel other forces
+    o_rest = oracle_from_workload(small_rotor_workload(ibm=True, n=(72, 32, 32)), None)
+    o_rest.step(3)
+    for oid in (1, 2):
+        f_turn, f_rest = o.forces(oid)["force"], o_rest.forces(oid)["force"]
+        assert np.max(np.abs(f_turn - f_rest)) > 1e-3 * np.max(np.abs(f_rest)), oid
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_cfl_step_after_forcing_uses_the_forced_state(gks, precision):
     """Stage 2 prepares the next step outside the forcing boxes and the boxes
     are prepared again after the forcing: each CFL step is the one of the

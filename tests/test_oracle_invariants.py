@@ -239,12 +239,12 @@ def lattice_kernel_sum(g, X, eps):
     return eta, vol
 
 
-def uniform_flow_grid(n, dom, u=1.0, mu=1e-3):
+def uniform_flow_grid(n, dom, u=1.0, mu=1e-3, rho=1.0):
     faces = [np.linspace(dom[d][0], dom[d][1], n[d] + 1) for d in range(3)]
     g = O.OracleGrid(n, faces, 0.1, 1.0, mu, [("periodic", "periodic")] * 3, dt_fixed=0.01)
     Q = np.zeros((4, n[2], n[1], n[0]))
-    Q[0] = 1.0
-    Q[1] = u
+    Q[0] = rho
+    Q[1] = rho * u
     g.set_state(Q)
     return g, Q
 
@@ -417,3 +417,51 @@ def test_alm_point_loads_follow_blade_element_geometry():
     assert np.allclose(f["thrust"], f["Fx"].sum(axis=1), rtol=1e-14)
     assert np.allclose(f["torque"], (f["Ft"] * radii[None, :]).sum(axis=1), rtol=1e-14)
     assert np.array_equal(out[2.0]["Fx"], 2.0 * f["Fx"]) and np.array_equal(out[2.0]["Ft"], 2.0 * f["Ft"])
+
+
+def test_ibm_moving_body():
+    """Sec. 3.2, Eq. (ibm-1) with prescribed point velocities: the target
+    velocity of a forced cell is the kernel- and volume-weighted average of
+    its points' velocities. (a) A body carried with a uniform stream (every
+    point at the stream velocity 1) asks for no change: zero force and the
+    state unchanged, bit for bit (the weighted average of a constant 1 is
+    exactly 1). (b) The same body moving through fluid at rest at
+    V = (0.3, -0.2, 0.1) (density 1.25): each forced cell relaxes as
+    U_s = V (1 - (1 - phi)^s),
+    the fluid gains the momentum dt times minus the force on the body, and
+    the force on the body points against its motion (along -V)."""
+    n = (20, 20, 20)
+    dom = [(-0.5, 0.5)] * 3
+    dx = 1.0 / 20
+    xyz, dS = WL.cylinder_points((0.0, 0.0, 0.0), 2, 0.1, -0.3, 0.3, 0.03, caps=True)
+    npts = len(dS)
+    # (a) carried with the stream
+    g, Q = uniform_flow_grid(n, dom, u=1.0)
+    vel = np.tile([1.0, 0.0, 0.0], (npts, 1))
+    bid = g.add_body(xyz, dS, 2 * dx, vel=vel, niter=6)
+    g.step(2)
+    assert np.all(g.forces(bid)["force"] == 0.0) and np.array_equal(g.get_state(), Q)
+    # (b) moving through fluid at rest
+    V = np.array([0.3, -0.2, 0.1])
+    g, Q = uniform_flow_grid(n, dom, u=0.0, rho=1.25)
+    bid = g.add_body(xyz, dS, 2 * dx, vel=np.tile(V, (npts, 1)), niter=7)
+    g.step(1)
+    fo = g.forces(bid)
+    A = g.get_state()
+    box, Vb, phi = g.body_fields(bid)
+    (i0, i1), (j0, j1), (k0, k1) = box
+    sl = (slice(k0, k1 + 1), slice(j0, j1 + 1), slice(i0, i1 + 1))
+    for d in range(3):
+        Ub = A[1 + d][sl] / A[0][sl]
+        assert np.allclose(Ub, V[d] * (1 - (1 - phi) ** 7), rtol=1e-12, atol=1e-15), d
+    # outside the forcing box the fluid stays at rest
+    mask = np.ones(A.shape[1:], bool)
+    mask[sl] = False
+    assert np.all(A[1:, mask] == 0.0)
+    vol = dx ** 3
+    for d in range(3):
+        dm = math.fsum(((A[1 + d] - Q[1 + d]) * vol).ravel())
+        assert abs(dm - (-0.01 * fo["force"][d])) <= 1e-12 * abs(dm), d
+    f = np.asarray(fo["force"])
+    assert np.dot(f, V) < 0
+    assert np.allclose(f / np.linalg.norm(f), -V / np.linalg.norm(V), rtol=0, atol=1e-12)

@@ -576,7 +576,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-graphs", action="store_true", help="skip the small-grid CUDA graph timing")
-    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-k", type=int, default=20)
     ap.add_argument("--adjoint-variant-steps", type=int, default=20)

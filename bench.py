@@ -559,7 +559,8 @@ def run_reference(args, world, rank):
             "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "cells": w.cells, "precision": "fp64 (oracle)",
-                       "parallelism": "host cores"},
+                       "rotor_points": sum(r.n_blades * len(r.r) for r in w.rotors),
+                       "ib_points": sum(len(b.dS) for b in w.bodies), "parallelism": "host cores"},
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

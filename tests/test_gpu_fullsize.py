@@ -95,3 +95,60 @@ def test_full_size_free_stream_is_bitwise_uniform(gks, precision):
     g.step(2)
     assert np.array_equal(g.get_state(), Q0)
     g.close()
+
+
+# The other two grids the benchmark runs at full size, compared the same way:
+# the turbulent channel on 128^3 (tanh-stretched y between no-slip walls,
+# periodic x and z, driving body force) through the whole height, and the
+# rotor without tower on 512 x 192 x 192 (inflow, outflow, periodic y, slip z;
+# anisotropic cells) on a window that holds the actuator-line supports and
+# every sampled point at least MARGIN cells inside its cut faces.
+OTHER = {
+    # name: (window origin x, y, z), window size, boundary kinds of the window
+    "channel-128^3": ((40, 0, 50), (30, 128, 30), None),
+    "alm-rotor-512x192x192": ((108, 56, 56), (40, 80, 80), [(4, 4), (4, 4), (4, 4)]),
+}
+
+
+def other_workload(name):
+    if name == "channel-128^3":
+        return WL.channel((128, 128, 128))
+    w = WL.alm_rotor((512, 192, 192))
+    w.state0 = WL.perturbed(w, 0.02, seed=23)
+    return w
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("name", sorted(OTHER))
+def test_other_full_size_grids_match_oracle_window(gks, name, precision):
+    w = other_workload(name)
+    lo, n, bcw = OTHER[name]
+    if bcw is None:   # channel: the walls are true boundaries, x and z are cut
+        bcw = [(4, 4), tuple(w.bc[1]), (4, 4)]
+    g = gks.Grid.from_workload(w, precision=precision)
+    g.step(1)
+    dt = g.last_dt
+    A = g.get_state()
+    frot = g.forces(0) if w.rotors else None
+    g.close()
+    faces = [w.faces[a][lo[a]:lo[a] + n[a] + 1].copy() for a in range(3)]
+    Q = w.state0[:, lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]].copy()
+    win = WL.Workload("window", n, faces, w.mach, w.u_ref, w.mu, bcw, cfl=w.cfl, dt_fixed=dt, inflow=w.inflow,
+                      body_force=w.body_force, state0=Q, rotors=w.rotors, bodies=w.bodies)
+    o = oracle_from_workload(win)
+    o.step(1)
+    B = o.get_state()
+    m = MARGIN
+    # a window face inside the full grid is cut; compare only MARGIN cells in from it
+    cut = [[lo[a] > 0, lo[a] + n[a] < w.n[a]] for a in range(3)]
+    rng = [slice(m if cut[a][0] else 0, n[a] - m if cut[a][1] else n[a]) for a in range(3)]
+    sl = (slice(None), rng[2], rng[1], rng[0])
+    Ag = A[:, lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]]
+    err = np.max(np.abs(Ag[sl] - B[sl])) / np.max(np.abs(B[sl]))
+    assert err <= TOL[precision], err
+    assert np.max(np.abs(Ag[sl][1:] - Q[sl][1:])) > 1e-6   # the state moved in the compared region
+    if frot is not None:
+        tol = 1e-11 if precision == "fp64" else 2e-4
+        fo = o.forces(0)
+        for k in ("thrust", "torque"):
+            assert np.max(np.abs(frot[k] - fo[k])) <= tol * np.max(np.abs(fo[k])), (k, frot[k], fo[k])

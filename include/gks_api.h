@@ -171,7 +171,9 @@ int gks_set_force_scales(gks_grid *g, int id, const double *h_scales);
 
 /* Add a stationary or moving immersed body (Sec. 3.2) of n Lagrangian
  * points: xyz (3n host values, point-major), surface element areas dS (n),
- * point velocities vel (3n, or NULL for a stationary body), the kernel width
+ * point velocities vel (3n, or NULL for a stationary body; the points keep
+ * their positions, so vel prescribes the surface velocity of a body whose
+ * shape stays in place, e.g. one turning about its own axis), the kernel width
  * eps of the truncated Gaussian used both ways, the number of direct-forcing
  * iterations niter (>= 1) and a residual tolerance tol (0 = always niter
  * iterations). V_p = Delta dS with Delta = (dx dy dz)^(1/3). The cell fields

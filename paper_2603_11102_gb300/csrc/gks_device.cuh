@@ -41,19 +41,21 @@ __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b
 // |U|^2 of a cell for the CFL time step, with every operation rounded
 // explicitly so that each kernel that forms it gets the same bits: FP32C from
 // hi + lo in FP32, FP64 from the state. max_u2 keeps a NaN.
-__device__ __forceinline__ double cell_u2(const float h[4], const float l[4])
+__device__ __forceinline__ float cell_u2f(const float h[4], const float l[4])
 {
     const float r = __fadd_rn(h[0], l[0]), a = __fadd_rn(h[1], l[1]);
     const float b = __fadd_rn(h[2], l[2]), c = __fadd_rn(h[3], l[3]);
     const float m2 = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
-    return (double)__fdiv_rn(m2, __fmul_rn(r, r));
+    return __fdiv_rn(m2, __fmul_rn(r, r));
 }
+__device__ __forceinline__ double cell_u2(const float h[4], const float l[4]) { return (double)cell_u2f(h, l); }
 __device__ __forceinline__ double cell_u2(const double w[4])
 {
     const double m2 = __dadd_rn(__dadd_rn(__dmul_rn(w[1], w[1]), __dmul_rn(w[2], w[2])), __dmul_rn(w[3], w[3]));
     return __ddiv_rn(m2, __dmul_rn(w[0], w[0]));
 }
 __device__ __forceinline__ double max_u2(double a, double b) { return (b > a || b != b) ? b : a; }
+__device__ __forceinline__ float max_u2f(float a, float b) { return (b > a || b != b) ? b : a; }
 
 // Block-wide max of v (blockDim.x * blockDim.y threads, a multiple of 32,
 // at most 1024) folded into *bits (a non-negative double) by one atomicMax.

@@ -1021,10 +1021,45 @@ __global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmi
 
 __global__ void advance_kernel(Scalars *scal) { scal->t = scal->t + scal->dt; }
 
+// hi = fl32(q), lo = fl32(q - hi) (round to nearest even) from the bits of
+// q with integer and FP32 operations only: the FP64 pipe of this GPU runs at
+// a small fraction of the FP32 rate, and four conversions and a subtraction
+// per value in FP64 made the state upload compute-bound. With q =
+// (-1)^s 2^e 1.m (52-bit m) and 2^-74 <= |q| < 2^127, hi keeps the top 23
+// bits of m, rounded by the low 29 bits (a carry into the exponent is the
+// correct result); q - hi is t 2^(e-52) with t = low bits (rounded down) or
+// 2^29 - low bits (rounded up, opposite sign), and fl32 of it is fl32(t)
+// scaled by the normal power of two 2^(e-52). q - hi = 0 gives +0, as the
+// FP64 subtraction does. Zero and the other exponents take the FP64 route.
+__device__ __forceinline__ void split_hi_lo(double q, float &h, float &l)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+    const unsigned int sgn = hw & 0x80000000u;
+    if (e >= -74 && e <= 126) {
+        const unsigned int top = ((hw & 0xfffffu) << 3) | (lw >> 29);
+        const unsigned int low = lw & 0x1fffffffu;
+        const bool up = low > 0x10000000u || (low == 0x10000000u && (top & 1u));
+        h = __uint_as_float((sgn | ((unsigned int)(e + 127) << 23) | top) + (up ? 1u : 0u));
+        const unsigned int t = up ? 0x20000000u - low : low;
+        const float mag = __fmul_rn(__uint2float_rn(t), __uint_as_float((unsigned int)(e + 75) << 23));
+        const bool neg = (sgn != 0u) != up;
+        l = __uint_as_float(__float_as_uint(mag) | ((neg && t != 0u) ? 0x80000000u : 0u));
+    } else if ((b << 1) == 0ull) {
+        h = __uint_as_float(sgn);
+        l = 0.0f;
+    } else {
+        h = (float)q;
+        l = (float)(q - (double)h);
+    }
+}
+
 // Compact FP64 state -> the padded state (FP32C: hi = fl32(q), lo =
 // fl32(q - hi)), kPrepZ planes per block. With scal set it also does the
 // work of prep_cfl on the new state (FP32 input into wk for FP32C, max
-// |U|^2 into scal).
+// |U|^2 into scal; FP32C takes the max over the FP32 values of cell_u2,
+// whose order and NaN the conversion to double keeps).
 __global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__restrict__ src, void *S, long np,
                                                       int nx, int ny, int nz, int P0, int P1, float *wk, float off,
                                                       Scalars *scal)
@@ -1033,6 +1068,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__
     const int k0 = blockIdx.z * kPrepZ, k1 = min(k0 + kPrepZ, nz);
     const long N = (long)nx * ny * nz;
     double mx = 0.0;
+    float mxf = 0.0f;
     if (i < nx && j < ny) {
         for (int k = k0; k < k1; ++k) {
             const long ci = i + (long)nx * (j + (long)ny * k);
@@ -1046,8 +1082,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__
                 if (prec == GKS_FP64) {
                     ((double *)S)[v * np + lin] = q[v];
                 } else {
-                    h[v] = (float)q[v];
-                    l[v] = (float)(q[v] - (double)h[v]);
+                    split_hi_lo(q[v], h[v], l[v]);
                     ((float *)S)[v * np + lin] = h[v];
                     ((float *)S)[(4 + v) * np + lin] = l[v];
                 }
@@ -1058,12 +1093,12 @@ __global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__
                 } else {
 #pragma unroll
                     for (int v = 0; v < 4; ++v) wk[v * np + lin] = (h[v] - (v == 0 ? off : 0.0f)) + l[v];
-                    mx = max_u2(mx, cell_u2(h, l));
+                    mxf = max_u2f(mxf, cell_u2f(h, l));
                 }
             }
         }
     }
-    if (scal) block_max_to(mx, &scal->maxu2_bits);
+    if (scal) block_max_to(prec == GKS_FP64 ? mx : (double)mxf, &scal->maxu2_bits);
 }
 
 __global__ void __launch_bounds__(256) gather_kernel(int prec, const void *S, double *dst, long np,

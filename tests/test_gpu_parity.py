@@ -174,6 +174,59 @@ def test_moving_immersed_bodies(gks, precision):
         assert np.max(np.abs(f_turn - f_rest)) > 1e-3 * np.max(np.abs(f_rest)), oid
 
 
+def split_test_values(count, seed):
+    """FP64 values for the hi/lo split: random over a wide exponent range,
+    values whose 29 discarded bits are exactly half an FP32 ulp (ties to
+    even) or one bit either side, all-ones mantissas (the rounding carries
+    into the exponent), zeros of both signs, and exponents at and beyond the
+    ends of the integer route (2^-74, 2^126, smaller and larger)."""
+    rng = np.random.default_rng(seed)
+    v = [(rng.random(count // 2) - 0.5) * 10.0 ** rng.integers(-30, 30, count // 2)]
+    m = rng.integers(0, 1 << 23, count // 4).astype(np.uint64)
+    e = rng.integers(-74, 127, count // 4).astype(np.int64)
+    low = rng.choice(np.array([0x10000000, 0x0FFFFFFF, 0x10000001, 0, 0x1FFFFFFF, 1], dtype=np.uint64),
+                     count // 4)
+    bits = ((e + 1023).astype(np.uint64) << np.uint64(52)) | (m << np.uint64(29)) | low
+    bits |= rng.integers(0, 2, count // 4).astype(np.uint64) << np.uint64(63)
+    v.append(bits.view(np.float64))
+    ee = np.arange(-74, 127).astype(np.uint64)
+    v.append((((ee + np.uint64(1023)) << np.uint64(52)) | np.uint64((1 << 52) - 1)).view(np.float64))
+    v.append(np.array([0.0, -0.0, 1.0, -1.0, 2.0 ** -74, -(2.0 ** -74), 2.0 ** -75, 2.0 ** -90, 1e-30,
+                       2.0 ** 126 * 1.75, 2.0 ** 127 * 1.5, -(2.0 ** 127) * 1.25, 5e-324]))
+    return np.concatenate(v)
+
+
+def test_fp32c_upload_splits_every_value_exactly(gks):
+    """gks_set_state and gks_set_state_device on an FP32C grid store
+    hi = fl32(q) and lo = fl32(q - hi), round to nearest even, for every
+    value; the words are read back raw from the state buffer through
+    gks_state_layout and compared bit for bit with numpy's conversions."""
+    import torch
+    n = (24, 20, 18)
+    w = smooth_workload(n, [(0, 0)] * 3, seed=5)
+    N = n[0] * n[1] * n[2]
+    vals = split_test_values(4 * N, seed=8)
+    Q = np.resize(vals, 4 * N).reshape(4, n[2], n[1], n[0])
+    with np.errstate(over="ignore"):
+        h_ref = Q.astype(np.float32)
+        l_ref = (Q - h_ref.astype(np.float64)).astype(np.float32)
+    g = gks.Grid.from_workload(w, precision="fp32c")
+    P0, P1, P2, eb, narr, stride, G = g.layout()
+    assert eb == 4 and narr == 8
+    for upload in ("host", "device"):
+        g.set_state(w.state0)
+        if upload == "host":
+            g.set_state(Q)
+        else:
+            g.set_state_tensor(torch.tensor(Q, dtype=torch.float64, device=g.device))
+        torch.cuda.synchronize(g.device)
+        raw = g.state_buf[:narr * stride * 4].view(torch.int32).cpu().numpy().reshape(narr, stride)
+        cells = raw[:, :P0 * P1 * P2].reshape(narr, P2, P1, P0)[:, G:G + n[2], G:G + n[1], G:G + n[0]]
+        assert np.array_equal(cells[:4], h_ref.view(np.int32)), upload
+        assert np.array_equal(cells[4:], l_ref.view(np.int32)), upload
+    g.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_cfl_step_after_forcing_uses_the_forced_state(gks, precision):
     """Stage 2 prepares the next step outside the forcing boxes and the boxes

@@ -166,6 +166,55 @@ def test_equilibrium_of_equal_states_is_that_state():
     assert np.allclose(Q0, Q, rtol=2e-15, atol=1e-15)
 
 
+@pytest.mark.parametrize("lam", [LAM, 0.5])
+def test_equilibrium_of_unequal_states_by_quadrature(lam):
+    """Sec. 2, Eq. (flux) and the equilibrium state below it: Q0 collects the
+    particles of the left Maxwellian moving right (u > 0) and those of the
+    right one moving left (u < 0). Integrated here over the normal velocity
+    by adaptive quadrature of the 1D Maxwellian; a tangential velocity enters
+    as the mean of its Gaussian factor. Unequal densities and velocities in
+    every component, including a left state drifting left and a right state
+    drifting right."""
+    from scipy.integrate import quad
+
+    def half(rho, U, sign, k):
+        f = lambda u: u ** k * math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
+        lo, hi = (0.0, np.inf) if sign > 0 else (-np.inf, 0.0)
+        return rho * quad(f, lo, hi, epsabs=0.0, epsrel=1e-13, limit=200)[0]
+
+    cases = [((1.03, 0.4, 0.2, -0.1), (0.97, -0.3, -0.05, 0.15)),
+             ((1.2, -2.5, 0.7, 0.3), (0.8, 3.0, -0.4, -0.9))]
+    for (rl, ul, vl, wl), (rr, ur, vr, wr) in cases:
+        Ql = np.array([rl, rl * ul, rl * vl, rl * wl])
+        Qr = np.array([rr, rr * ur, rr * vr, rr * wr])
+        Q0 = O.equilibrium_local(lam, Ql, Qr)
+        n0l, n0r = half(rl, ul, +1, 0), half(rr, ur, -1, 0)
+        ref = np.array([n0l + n0r, half(rl, ul, +1, 1) + half(rr, ur, -1, 1), vl * n0l + vr * n0r,
+                        wl * n0l + wr * n0r])
+        assert np.allclose(Q0, ref, rtol=1e-11, atol=1e-12 * max(abs(ul), abs(ur), 1.0)), (Q0, ref)
+
+
+def test_cfl_time_step_of_the_oracle():
+    """Sec. 2 (CFL condition): dt = CFL min(dx, dy, dz) / (max |U| + C) over
+    the interior cells, C = sqrt(1 / (2 lambda)) = U_ref / Ma, on a stretched
+    grid whose smallest cell is not where the fastest cell is."""
+    n = (10, 8, 6)
+    faces = [np.linspace(0.0, 1.0, n[0] + 1), np.cumsum(np.r_[0.0, np.linspace(0.05, 0.2, n[1])]),
+             np.linspace(0.0, 0.9, n[2] + 1)]
+    mach, cfl = 0.2, 0.7
+    g = O.OracleGrid(n, faces, mach, 1.0, 1e-3, [("periodic", "periodic")] * 3, cfl=cfl)
+    rng = np.random.default_rng(4)
+    Q = np.zeros((4,) + tuple(n[::-1]))
+    Q[0] = 1.0 + 0.1 * rng.random(Q[0].shape)
+    Q[1:] = Q[0] * (rng.random(Q[1:].shape) - 0.5)
+    Q[1, 4, 5, 7] = Q[0, 4, 5, 7] * 1.9
+    g.set_state(Q)
+    umax = np.sqrt(np.max((Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0] ** 2))
+    hmin = min(np.min(np.diff(f)) for f in faces)
+    assert hmin == pytest.approx(0.05)
+    assert g.cfl_dt() == pytest.approx(cfl * hmin / (umax + 1.0 / mach), rel=1e-14)
+
+
 # -------------------------------------------------------- reconstruction ---
 
 def cell_avgs(c, offsets, half=0.5):

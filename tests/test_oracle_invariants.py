@@ -465,3 +465,26 @@ def test_ibm_moving_body():
     f = np.asarray(fo["force"])
     assert np.dot(f, V) < 0
     assert np.allclose(f / np.linalg.norm(f), -V / np.linalg.norm(V), rtol=0, atol=1e-12)
+
+
+def test_constant_body_force_accelerates_a_uniform_stream():
+    """The constant driving force of the channel case (Sec. 4.1), added as
+    dt f to the momentum after the S2O4 update: in a periodic box a uniform
+    stream stays uniform (its fluxes cancel exactly) and gains dt f per step
+    in momentum, bit for bit, while the density does not change."""
+    n = (8, 6, 5)
+    faces = [np.linspace(0.0, 1.0, n[0] + 1), np.linspace(0.0, 0.8, n[1] + 1), np.linspace(0.0, 0.6, n[2] + 1)]
+    dt, f = 2e-3, (0.37, -0.11, 0.05)
+    g = O.OracleGrid(n, faces, 0.1, 1.0, 1e-3, [("periodic", "periodic")] * 3, dt_fixed=dt)
+    g.set_body_force(*f)
+    Q = np.zeros((4,) + tuple(n[::-1]))
+    Q[0], Q[1], Q[2], Q[3] = 1.1, 1.1 * 0.4, -1.1 * 0.2, 0.0
+    g.set_state(Q)
+    ref = Q.copy()
+    for _ in range(5):
+        g.step(1)
+        for d in range(3):
+            ref[1 + d] = ref[1 + d] + dt * f[d]
+    A = g.get_state()
+    assert np.array_equal(A[0], Q[0])
+    assert np.array_equal(A[1:], ref[1:])

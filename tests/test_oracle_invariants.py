@@ -488,3 +488,44 @@ def test_constant_body_force_accelerates_a_uniform_stream():
     A = g.get_state()
     assert np.array_equal(A[0], Q[0])
     assert np.array_equal(A[1:], ref[1:])
+
+
+def test_alm_samples_a_linear_shear_flow_exactly_at_the_blade_positions():
+    """Sec. 3.1: the velocity at an actuator point is interpolated from the
+    cell centres, and the blades stand at azimuth theta0 + omega t_{n+1} +
+    2 pi b / N (readings of the sampling time and of trilinear
+    interpolation). A parallel shear flow U_x = a + b y + c z (rho = 1, no
+    cross-flow) is a steady solution of the scheme away from the boundaries,
+    and trilinear interpolation reproduces a linear field exactly; with no
+    tangential velocity the flow angle is atan2(U_x, omega r), so
+    omega r tan(phi) must equal the field at each point's position. The
+    three blades sit at different (y, z), so a swapped coordinate, a wrong
+    azimuth or time level, or a misplaced interpolation stencil shows."""
+    n = (24, 32, 32)
+    dom = [(-0.5, 0.5), (-0.7, 0.7), (-0.7, 0.7)]
+    faces = [np.linspace(dom[d][0], dom[d][1], n[d] + 1) for d in range(3)]
+    dt = 0.01
+    g = O.OracleGrid(n, faces, 0.1, 1.0, 1e-3, [("periodic", "periodic"), ("outflow", "outflow"),
+                                               ("outflow", "outflow")], dt_fixed=dt)
+    a, b, c = 1.0, 0.5, -0.3
+    yc = 0.5 * (faces[1][1:] + faces[1][:-1])
+    zc = 0.5 * (faces[2][1:] + faces[2][:-1])
+    Q = np.zeros((4,) + tuple(n[::-1]))
+    Q[0] = 1.0
+    Q[1] = a + b * yc[None, :, None] + c * zc[:, None, None]
+    g.set_state(Q)
+    dx = 1.0 / n[0]
+    radii = np.array([0.1, 0.2, 0.3])
+    om, th0, N = 14.0, 0.3, 3
+    k = len(radii)
+    rid = g.add_rotor(N, radii, np.full(k, 0.05), np.full(k, 0.1), np.full(k, 0.02), (0.0, 0.0, 0.0), om, th0,
+                      0.5, 2 * dx)
+    g.step(1)
+    f = g.forces(rid)
+    t1 = g.time
+    assert t1 == pytest.approx(dt, rel=1e-15)
+    for bl in range(N):
+        th = th0 + om * t1 + 2 * math.pi * bl / N
+        y, z = radii * math.cos(th), radii * math.sin(th)
+        ux = om * radii * np.tan(f["phi"][bl])
+        assert np.allclose(ux, a + b * y + c * z, rtol=0, atol=1e-12), (bl, ux, a + b * y + c * z)

@@ -529,3 +529,28 @@ def test_alm_samples_a_linear_shear_flow_exactly_at_the_blade_positions():
         y, z = radii * math.cos(th), radii * math.sin(th)
         ux = om * radii * np.tan(f["phi"][bl])
         assert np.allclose(ux, a + b * y + c * z, rtol=0, atol=1e-12), (bl, ux, a + b * y + c * z)
+
+
+def test_diagnostics_are_the_volume_integrals():
+    """The global reductions (mass, momentum, kinetic energy): integrals of
+    rho, rho U and |rho U|^2 / (2 rho) over the cells of a stretched grid,
+    here summed exactly with math.fsum, against the oracle's compensated
+    sums (to within the rounding of each term)."""
+    n = (9, 7, 5)
+    faces = [np.linspace(0.0, 1.0, n[0] + 1), np.cumsum(np.r_[0.0, np.linspace(0.05, 0.2, n[1])]),
+             np.linspace(-0.3, 0.6, n[2] + 1) ** 3]
+    g = O.OracleGrid(n, faces, 0.1, 1.0, 1e-3, [("periodic", "periodic")] * 3, dt_fixed=1e-3)
+    rng = np.random.default_rng(12)
+    Q = np.zeros((4,) + tuple(n[::-1]))
+    Q[0] = 1.0 + 0.2 * rng.random(Q[0].shape)
+    Q[1:] = Q[0] * (rng.random(Q[1:].shape) - 0.5) * 3.0
+    g.set_state(Q)
+    vol = np.diff(faces[2])[:, None, None] * np.diff(faces[1])[None, :, None] * np.diff(faces[0])[None, None, :]
+    ke = 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]
+    terms = [(q * vol).ravel() for q in (Q[0], Q[1], Q[2], Q[3], ke)]
+    d = g.diagnostics()
+    for a, t in zip(d, terms):
+        # each term is rounded once on either side (the cell volume's product order differs)
+        assert abs(a - math.fsum(t)) <= 4e-16 * math.fsum(np.abs(t)), (d, [math.fsum(t) for t in terms])
+    # the sums are compensated: as accurate as the exact sum of the rounded terms
+    assert abs(d[0] - math.fsum(terms[0])) <= 2.3e-16 * d[0]

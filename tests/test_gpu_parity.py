@@ -68,6 +68,22 @@ def test_all_boundary_kinds_stretched_ragged(gks, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_inflow_on_the_high_side_and_across_axes(gks, precision):
+    """Inflow through the high x face (the invariant U + C ln rho leaves the
+    domain) and the low y face (normal velocity V), outflow at low x, a
+    no-slip wall at high y, periodic z; ragged sizes."""
+    n = (29, 19, 9)
+    faces = [np.linspace(0, 2.5, n[0] + 1), np.linspace(0, 1.5, n[1] + 1), np.linspace(0, 0.8, n[2] + 1)]
+    bc = [(4, 3), (3, 1), (0, 0)]
+    w = smooth_workload(n, bc, faces=faces, seed=3)
+    w.inflow = (1.0, -0.8, 0.3, 0.07)
+    g, o, _ = run_pair(gks, w, precision, 8)
+    a, b = g.get_state(), o.get_state()
+    err = rel_linf(a, b)
+    assert err <= TOL[precision], (err, rel_linf_components(a, b))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_channel_small_with_body_force(gks, precision):
     w = WL.channel((20, 24, 12), steps=10)
     g, o, _ = run_pair(gks, w, precision, 10)

@@ -554,3 +554,39 @@ def test_diagnostics_are_the_volume_integrals():
         assert abs(a - math.fsum(t)) <= 4e-16 * math.fsum(np.abs(t)), (d, [math.fsum(t) for t in terms])
     # the sums are compensated: as accurate as the exact sum of the rounded terms
     assert abs(d[0] - math.fsum(terms[0])) <= 2.3e-16 * d[0]
+
+
+def test_inflow_ghosts_on_the_high_side_and_across_axes():
+    """Sec. 4.3 inflow on the other sides: at a high face the outgoing
+    characteristic (speed U + C) carries U + C ln rho out of the domain, so
+    the ghost keeps that invariant with the prescribed velocity; at a low y
+    face the normal velocity is V and the invariant V - C ln rho. Outflow
+    on the low x face copies the first cell."""
+    n = (5, 6, 4)
+    bc = [("outflow", "inflow"), ("inflow", "noslip"), ("periodic", "periodic")]
+    g = grid(n, bc=bc)
+    uin = (-0.8, 0.3, 0.07)
+    g.set_inflow(1.0, *uin)
+    rng = np.random.default_rng(13)
+    Q = np.zeros((4, n[2], n[1], n[0]))
+    Q[0] = 1.0 + 0.05 * rng.random(Q[0].shape)
+    Q[1:] = rng.normal(size=Q[1:].shape) * 0.3
+    A = g.ghost_filled(Q)
+    G = 3
+    I = lambda i, j, k: (slice(None), k + G, j + G, i + G)
+    C = 10.0
+    for j in range(n[1]):
+        for k in range(n[2]):
+            q1 = A[I(n[0] - 1, j, k)]
+            for l in range(1, 4):
+                gq = A[I(n[0] - 1 + l, j, k)]
+                assert abs((gq[1] / gq[0] + C * math.log(gq[0])) - (q1[1] / q1[0] + C * math.log(q1[0]))) < 1e-12
+                assert np.allclose(gq[1:] / gq[0], uin, rtol=0, atol=1e-14)
+                assert np.array_equal(A[I(-l, j, k)], A[I(0, j, k)])
+    for i in range(n[0]):
+        for k in range(n[2]):
+            q1 = A[I(i, 0, k)]
+            for l in range(1, 4):
+                gq = A[I(i, -l, k)]
+                assert abs((gq[2] / gq[0] - C * math.log(gq[0])) - (q1[2] / q1[0] - C * math.log(q1[0]))) < 1e-12
+                assert np.allclose(gq[1:] / gq[0], uin, rtol=0, atol=1e-14)

@@ -590,3 +590,32 @@ def test_inflow_ghosts_on_the_high_side_and_across_axes():
                 gq = A[I(i, -l, k)]
                 assert abs((gq[2] / gq[0] - C * math.log(gq[0])) - (q1[2] / q1[0] - C * math.log(q1[0]))) < 1e-12
                 assert np.allclose(gq[1:] / gq[0], uin, rtol=0, atol=1e-14)
+
+
+def test_alm_velocity_correction_special_value():
+    """Sec. 3.1 velocity correction (reading R14: one pass, C_D of the
+    uncorrected angle): the sampled velocity is divided by
+    1 - C_D c / (4 sqrt(pi) eps). In a uniform axial stream, with the twist
+    set so that the uncorrected angle of attack is alpha0 and the chord so
+    that C_D(alpha0) c / (4 sqrt(pi) eps) = 1/2, the axial velocity doubles:
+    phi = atan2(2 U_inf, omega r), against atan2(U_inf, omega r) without the
+    correction."""
+    n = (24, 32, 32)
+    dom = [(-0.5, 0.5), (-0.7, 0.7), (-0.7, 0.7)]
+    dx = 1.0 / n[0]
+    eps = 2 * dx
+    om, N, R = 14.0, 3, 0.5
+    radii = np.array([0.15, 0.3, 0.45])
+    alpha0 = np.array([0.0, 0.3, -0.6])
+    phi0 = np.arctan2(1.0, om * radii)
+    cd0 = 0.01 + 0.02 * alpha0 ** 2
+    chord = 0.5 * 4 * math.sqrt(math.pi) * eps / cd0
+    out = {}
+    for corr in (False, True):
+        g, _ = uniform_flow_grid(n, dom)
+        rid = g.add_rotor(N, radii, chord, phi0 - alpha0, np.full(3, 0.02), (0.0, 0.0, 0.0), om, 0.3, R, eps,
+                          correction=corr)
+        g.step(1)
+        out[corr] = g.forces(rid)
+    assert np.allclose(out[False]["phi"], phi0[None, :], rtol=0, atol=1e-15)
+    assert np.allclose(out[True]["phi"], np.arctan2(2.0, om * radii)[None, :], rtol=0, atol=1e-14)

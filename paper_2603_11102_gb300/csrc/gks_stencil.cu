@@ -1022,7 +1022,7 @@ __global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmi
 __global__ void advance_kernel(Scalars *scal) { scal->t = scal->t + scal->dt; }
 
 // hi = fl32(q), lo = fl32(q - hi) (round to nearest even) from the bits of
-// q with integer and FP32 operations only: the FP64 pipe of this GPU runs at
+// q with integer and FP32 operations only: the FP64 pipe of GB300 (sm_103) runs at
 // a small fraction of the FP32 rate, and four conversions and a subtraction
 // per value in FP64 made the state upload compute-bound. With q =
 // (-1)^s 2^e 1.m (52-bit m) and 2^-74 <= |q| < 2^127, hi keeps the top 23

@@ -497,6 +497,23 @@ def run_ours(args, world, rank, local):
                           "steps replayed from a CUDA graph",
                "power_read": len(power)}
         del stage
+
+    # the global reductions (mass, momentum, kinetic energy; FP64 sums in a
+    # fixed order), taken on demand and read on the host: time per call over
+    # the whole grid, which reads the state once (32 B per cell)
+    reductions = None
+    try:
+        g.diagnostics()
+        torch.cuda.synchronize(dev)
+        nd = 20
+        t0 = time.perf_counter()
+        for _ in range(nd):
+            g.diagnostics()
+        tr = (time.perf_counter() - t0) / nd
+        reductions = {"ms_per_call": tr * 1e3, "calls": nd, "state_gb": cells * 32 / 1e9,
+                      "gbs": cells * 32 / tr / 1e9, "timing": "host clock around the call (includes its read-back)"}
+    except Exception as exc:   # reported, not fatal: the step figures above stand
+        reductions = {"error": str(exc)[:200]}
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -542,7 +559,7 @@ def run_ours(args, world, rank, local):
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline, "hbm_step": hbm, "kernel_share": share, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64,
-            "small_grid_graphs": graphs, "adjoint": adj}
+            "small_grid_graphs": graphs, "adjoint": adj, "reductions": reductions}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -380,9 +380,13 @@ const char *gks_kernel_group_name(int group);
  * Returns GKS_ERR_ARG for null pointers, empty extents or more than
  * 33,554,432 cells (the scratch limit), GKS_ERR_CUDA if a launch fails; the
  * message is in gks_last_error(NULL). The work is asynchronous on stream.
- * The first call on a device looks up the device address of the static
- * scratch (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. All calls share the one scratch array:
+ * Each call outside stream capture looks up the device address of the
+ * static scratch (cudaGetSymbolAddress) with the current device, so a device
+ * reset never leaves a stale address; a call made while its stream is being
+ * captured reuses the address of the last uncaptured call on that device, so
+ * make one call before any capture (and again after a device reset):
+ * otherwise the captured call returns GKS_ERR_STATE. All calls share the one
+ * scratch array:
  * calls that overlap on the GPU (in flight on different streams at once)
  * race and must be serialised by the caller. */
 int gks_diagnostics_noalloc(const double *d_state, int nx, int ny, int nz, const double *d_hx,

@@ -33,16 +33,23 @@ std::mutex g_mu;
 double *g_scratch[kMaxDevices] = {};
 
 // Device address of g_partials on the current device. In host code the
-// symbol name is only a host-side stand-in, so the address is looked up once
-// per device with that device current, and cached.
-int scratch_address(double **out, std::string *msg)
+// symbol name is only a host-side stand-in, so the address is looked up with
+// that device current. A call outside stream capture looks it up again every
+// time (cheap once the module is loaded), so a device reset or a re-created
+// primary context, which reload the module at another address, never leaves
+// a stale pointer behind; a call inside a capture cannot make that query and
+// takes the address of the last uncaptured call on the device.
+int scratch_address(cudaStream_t stream, double **out, std::string *msg)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *msg = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return GKS_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) { *msg = "device ordinal out of range"; return GKS_ERR_ARG; }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) { *msg = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e); return GKS_ERR_CUDA; }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         double *p = nullptr;
         e = cudaGetSymbolAddress((void **)&p, g_partials);
         if (e != cudaSuccess || !p) {
@@ -50,6 +57,9 @@ int scratch_address(double **out, std::string *msg)
             return GKS_ERR_CUDA;
         }
         g_scratch[dev] = p;
+    } else if (!g_scratch[dev]) {
+        *msg = "the first call on a device must come before any stream capture";
+        return GKS_ERR_STATE;
     }
     *out = g_scratch[dev];
     return GKS_OK;
@@ -125,14 +135,14 @@ extern "C" int gks_diagnostics_noalloc(const double *d_state, int nx, int ny, in
                           "of 4096 cells); use gks_diagnostics for larger grids");
         return GKS_ERR_ARG;
     }
+    cudaStream_t s = (cudaStream_t)stream;
     double *scratch = nullptr;
-    int rc = scratch_address(&scratch, &msg);
+    int rc = scratch_address(s, &scratch, &msg);
     if (rc) {
         gks::record_error(("gks_diagnostics_noalloc: " + msg).c_str());
         return rc;
     }
     const int nblocks = (int)((N + kCellsPerBlock - 1) / kCellsPerBlock);
-    cudaStream_t s = (cudaStream_t)stream;
     noalloc_partial_kernel<<<nblocks, kThreads, 0, s>>>(d_state, N, nx, ny, d_hx, d_hy, d_hz, scratch);
     noalloc_final_kernel<<<1, kThreads, 0, s>>>(scratch, nblocks, d_out);
     const cudaError_t e = cudaGetLastError();

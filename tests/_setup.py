@@ -56,3 +56,20 @@ def paper_values():
                 out[line[0]] = [float(v) for v in line[1:]]
     return out
 
+
+
+def report(case, precision, steps, a=None, b=None, **extra):
+    """Record a parity case's measured errors (one JSON line per call) in the
+    file named by GKS_PARITY_REPORT, when that variable is set: the whole-state
+    relative L-infinity, the same per component, and any extra figures."""
+    import json
+    import os
+    path = os.environ.get("GKS_PARITY_REPORT")
+    if not path:
+        return
+    rec = {"case": case, "precision": precision, "steps": int(steps)}
+    if a is not None:
+        rec.update(rel_linf=rel_linf(a, b), components=rel_linf_components(a, b))
+    rec.update({k: (float(v) if np.isscalar(v) else [float(x) for x in np.ravel(v)]) for k, v in extra.items()})
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")

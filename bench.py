@@ -35,10 +35,11 @@ sys.path.insert(0, ROOT)
 
 from paper_2603_11102_gb300 import workloads as WL  # noqa: E402
 
-# FP32 operations per face in the source of the two face kernels (adds,
-# multiplies, FMA = 2, one per division/transcendental call), counted per
-# face of the face box each launch processes.
-FLOPS = {
+# Hand estimates of the FP32 operations per face of the face box each launch
+# processes (adds, multiplies, FMA = 2): used only when no measured count of
+# the current kernel source is committed (profiles/flops.txt, ncu counts of
+# the FFMA, FADD and FMUL instructions executed).
+FLOPS_ESTIMATE = {
     # WENO5 on 4 variables x 2 sides (40 each), half-space equilibrium (~40
     # plus 2 erf, 2 exp, 2 expm1), normal slope (4 x 5)
     "face_eq": 4 * 2 * 40 + 46 + 20,
@@ -46,7 +47,11 @@ FLOPS = {
     "face_flux_stage1": 168 + 504 + 4 * 118 + 8,
     "face_flux_stage2": 168 + 504 + 4 * 100 + 4,
 }
-SM_COUNT, FP32_LANES = 152, 128
+FLOPS_ESTIMATE["flux_update_stage1"] = FLOPS_ESTIMATE["face_flux_stage1"]
+FLOPS_ESTIMATE["flux_update_stage2"] = FLOPS_ESTIMATE["face_flux_stage2"]
+# the source section of gks_stencil.cu each kernel group is built from
+SECTIONS = {"face_eq": ("face state", "face flux"), "face_flux": ("face flux", "z flux + stage update"),
+            "flux_update": ("z flux + stage update", "prep, CFL, misc")}
 BYTES_PER_CELL_STEP = {"fp32c": 160, "fp64": 192}
 
 
@@ -150,6 +155,8 @@ def make_workload(name):
         return WL.taylor_green_3d(32)
     if name == "tgv192":
         return WL.taylor_green_3d(192)
+    if name == "tgv96":
+        return WL.taylor_green_3d(96)
     raise ValueError(name)
 
 
@@ -208,18 +215,23 @@ def time_oracle(w, steps, warmup):
     return mlups, dt, oracle.get_threads(), desc
 
 
-def source_hash():
-    """Hash of the source the face_flux traffic figure depends on: the device
-    header and the face-flux section of gks_stencil.cu."""
+def source_hash(group="face_flux"):
+    """Hash of the source a kernel group's measured figures depend on: the
+    device header and the group's section of gks_stencil.cu."""
     csrc = os.path.join(ROOT, "paper_2603_11102_gb300", "csrc")
     h = hashlib.sha256()
     with open(os.path.join(csrc, "gks_device.cuh"), "rb") as fh:
         h.update(fh.read())
     with open(os.path.join(csrc, "gks_stencil.cu")) as fh:
         text = fh.read()
-    a = text.index("// ------------------------------------------------------------- face flux --")
-    b = text.index("// ------------------------------------------------- z flux + stage update --")
-    h.update(text[a:b].encode())
+    first, last = SECTIONS[group]
+
+    def marker(name):
+        for line in text.splitlines():
+            if line.startswith("// ---") and line.rstrip().endswith(" " + name + " --"):
+                return text.index(line)
+        raise ValueError(name)
+    h.update(text[marker(first):marker(last)].encode())
     return h.hexdigest()[:16]
 
 
@@ -229,12 +241,67 @@ def read_traffic(kernel, precision):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    cur = source_hash()
+    cur = source_hash(kernel) if kernel in SECTIONS else None
     for line in open(p):
         parts = line.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == precision and parts[3] == cur:
             return float(parts[2])
     return None
+
+
+def read_flops(precision):
+    """Measured operations per face of each kernel group and stage (ncu counts
+    of FFMA x 2 + FADD + FMUL, or the FP64 ones) from profiles/flops.txt,
+    where they were taken on the current kernel sources; else the hand
+    estimates. Returns ({group_stage: flops}, {group: source})."""
+    out, src = {}, {}
+    p = os.path.join(ROOT, "profiles", "flops.txt")
+    hashes = {g: source_hash(g) for g in SECTIONS}
+    if os.path.exists(p):
+        for line in open(p):
+            parts = line.split("#", 1)[0].split()
+            if len(parts) == 5 and parts[1] == precision and parts[0] in hashes and parts[4] == hashes[parts[0]]:
+                key = parts[0] if parts[2] == "-" else "%s_stage%s" % (parts[0], parts[2])
+                out[key] = float(parts[3])
+                src[parts[0]] = "measured (profiles/flops.txt)"
+    for k, v in FLOPS_ESTIMATE.items():
+        if k not in out:
+            out[k] = v
+            src.setdefault(k.split("_stage")[0], "hand estimate")
+    return out, src
+
+
+def measure_alu_peak(dev, fp64, seconds=1.0, repeats=3):
+    """Arithmetic peak of this GPU from the library's FMA-loop probe, timed
+    with CUDA events on one stream: (best, median) TFLOP/s over `repeats`
+    launches of about `seconds` each."""
+    import torch
+
+    from paper_2603_11102_gb300 import gks
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(4 * sms, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def once(iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fl = gks.alu_peak_probe(fp64, iters, sink, st)
+        b.record(st)
+        b.synchronize()
+        return fl, a.elapsed_time(b)
+
+    iters = 16
+    while True:
+        fl, ms = once(iters)
+        if ms > 50.0:
+            break
+        iters *= 4
+    iters = max(1, int(iters * seconds * 1e3 / ms))
+    rates = []
+    for _ in range(repeats):
+        fl, ms = once(iters)
+        rates.append(fl / (ms / 1e3) / 1e12)
+    return max(rates), statistics.median(rates), sms
 
 
 def face_counts(n):
@@ -397,34 +464,53 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel group (FP32 or FP64 ALU bound); the
     # x/y face-flux kernel, the z-face kernel fused with the stage update and
-    # the face-state kernel are each reported against the same ALU peak
+    # the face-state kernel are each reported against the same ALU peak: the
+    # FMA-loop probe's median rate on this GPU (after the timed region), the
+    # operations of each launch from the measured per-face counts
     kms = prof["ms"]
     fc = face_counts(w.n)
+    fp64_run = args.precision == "fp64"
+    probe = {}
+    if not args.no_alu_probe:
+        for name, is64 in (("fp32", False), ("fp64", True)):
+            best, med, sms = measure_alu_peak(dev, is64)
+            probe[name] = {"best_tflops": best, "median_tflops": med}
+        probe["sms"] = sms
+        probe["method"] = ("library FMA loop (gks_alu_peak_probe): 4 blocks of 256 threads per SM, 8 independent "
+                           "chains per thread, 3 launches of ~1 s timed with CUDA events")
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12 if args.precision == "fp32c" else 1.25
-    flux_pair = FLOPS["face_flux_stage1"] + FLOPS["face_flux_stage2"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if probe:
+        alu_peak = probe["fp64" if fp64_run else "fp32"]["median_tflops"]
+        peak_source = "measured: median of the %s FMA-loop probe on this GPU" % ("FP64" if fp64_run else "FP32")
+    elif not fp64_run:
+        alu_peak = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+        peak_source = "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, clock_mhz)
+    else:
+        alu_peak, peak_source = 1.25, "nominal GB300 FP64 1.25 TFLOP/s"
+    FL, fl_src = read_flops(args.precision)
     group_flops = {
-        "face_flux": args.steps * sum(fc[d]["flux"] * flux_pair for d in (0, 1)),
-        "flux_update": args.steps * fc[2]["flux"] * flux_pair,
-        "face_eq": args.steps * 2 * sum(fc[d]["eq"] * FLOPS["face_eq"] for d in range(3)),
+        "face_flux": args.steps * sum(fc[d]["flux"] * (FL["face_flux_stage1"] + FL["face_flux_stage2"])
+                                      for d in (0, 1)),
+        "flux_update": args.steps * fc[2]["flux"] * (FL["flux_update_stage1"] + FL["flux_update_stage2"]),
+        "face_eq": args.steps * 2 * sum(fc[d]["eq"] * FL["face_eq"] for d in range(3)),
     }
     alu = {}
     for k, fl in group_flops.items():
         if kms.get(k, 0.0) > 0:
             a = fl / (kms[k] / 1e3) / 1e12
             alu[k] = {"achieved": round(a, 3), "frac": round(a / alu_peak, 4),
-                      "avg_launch_ms": round(kms[k] / max(1, prof["launches"][k]), 4)}
+                      "avg_launch_ms": round(kms[k] / max(1, prof["launches"][k]), 4),
+                      "flops_source": fl_src.get(k)}
     top = max(kms, key=kms.get)
     flops = group_flops.get(top)
     achieved = flops / (kms[top] / 1e3) / 1e12 if flops else None
     traffic = read_traffic(top, args.precision)
     roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
-                "peak_source": ("FP32 lanes 152 x 128 x 2 x %.0f MHz (max SM clock of %s peaks)"
-                                % (clock_mhz, peak_kind)) if args.precision == "fp32c"
-                else "nominal GB300 FP64 1.25 TFLOP/s",
+                "peak_source": peak_source, "flops_source": fl_src.get(top),
                 "launches": prof["launches"][top], "avg_launch_ms": kms[top] / max(1, prof["launches"][top]),
-                "groups": alu}
+                "groups": alu, "alu_probe": probe or None}
     hbm_ach = cells * BYTES_PER_CELL_STEP[args.precision] * args.steps / (ms / 1e3) / 1e9
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": hbm_ach / peaks["hbm_gbs"], "bytes_per_cell_step": BYTES_PER_CELL_STEP[args.precision],
@@ -499,19 +585,27 @@ def run_ours(args, world, rank, local):
         del stage
 
     # the global reductions (mass, momentum, kinetic energy; FP64 sums in a
-    # fixed order), taken on demand and read on the host: time per call over
-    # the whole grid, which reads the state once (32 B per cell)
+    # fixed order), taken on demand and read on the host: the device time of
+    # their two kernels per call over the whole grid (CUDA events of the
+    # library's profiler on the grid's stream), which read the state once
+    # (32 B per cell), and the host time of the whole call with its read-back
     reductions = None
     try:
+        g.profile_enable(timing=True)
         g.diagnostics()
         torch.cuda.synchronize(dev)
+        g.profile_enable(timing=True)
         nd = 20
         t0 = time.perf_counter()
         for _ in range(nd):
             g.diagnostics()
         tr = (time.perf_counter() - t0) / nd
-        reductions = {"ms_per_call": tr * 1e3, "calls": nd, "state_gb": cells * 32 / 1e9,
-                      "gbs": cells * 32 / tr / 1e9, "timing": "host clock around the call (includes its read-back)"}
+        pr = g.profile_read()
+        kd = pr["ms"]["misc"] / max(1, pr["launches"]["misc"])
+        reductions = {"device_ms_per_call": kd, "calls": nd, "state_gb": cells * 32 / 1e9,
+                      "gbs": cells * 32 / (kd / 1e3) / 1e9, "host_ms_per_call": tr * 1e3,
+                      "timing": "device: CUDA events around the two reduction kernels on the grid's stream; "
+                                "host: clock around the call (includes its read-back and synchronisation)"}
     except Exception as exc:   # reported, not fatal: the step figures above stand
         reductions = {"error": str(exc)[:200]}
     g.close()
@@ -530,7 +624,20 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize(dev)
         ms64 = max_over_ranks(a.elapsed_time(b), world, dev)
         fp64 = {"value": world * cells * args.fp64_steps / (ms64 / 1e3) / 1e6, "unit": "MLUPS",
-                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps, "arithmetic": "fp64"}
+        # the same FP64 grid with double-single reconstruction and flux
+        # (gks_set_fp64_arithmetic): FP64 state, face buffers, update and sums
+        g64.set_fp64_arithmetic("ds")
+        g64.step(1)
+        torch.cuda.synchronize(dev)
+        a.record(g64.stream)
+        g64.step(args.fp64_steps)
+        b.record(g64.stream)
+        torch.cuda.synchronize(dev)
+        msds = max_over_ranks(a.elapsed_time(b), world, dev)
+        fp64["double_single"] = {"value": world * cells * args.fp64_steps / (msds / 1e3) / 1e6, "unit": "MLUPS",
+                                 "steps": args.fp64_steps, "ms_per_step": msds / args.fp64_steps,
+                                 "arithmetic": "double-single reconstruction and flux, FP64 state and sums"}
         g64.close()
 
     graphs = time_small_graphs(dev) if rank == 0 and not args.no_graphs else None
@@ -542,9 +649,16 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
         mlups, secs, cores, desc = time_oracle(w, args.cpu_steps, 0)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": secs}
+        # the same window on one host thread (fewer steps: ~1/cores of the rate)
+        oracle.set_threads(1)
+        m1, s1, _, _ = time_oracle(w, args.cpu_steps_one_thread, 0)
+        oracle.set_threads(cores)
+        cpu["one_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1, "steps": args.cpu_steps_one_thread,
+                             "seconds": s1}
 
     line = {"metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -589,18 +703,20 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="alm-ibm", choices=["alm-ibm", "alm", "channel", "tgv", "tgv192"])
+    ap.add_argument("--workload", default="alm-ibm", choices=["alm-ibm", "alm", "channel", "tgv", "tgv96", "tgv192"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-graphs", action="store_true", help="skip the small-grid CUDA graph timing")
     ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps-one-thread", type=int, default=2)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-k", type=int, default=20)
     ap.add_argument("--adjoint-variant-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-alu-probe", action="store_true", help="skip the FMA-loop peak measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -205,6 +205,19 @@ int gks_sync(gks_grid *g, double *t_out);
  * plain steps. Off by default. */
 int gks_set_graphs(gks_grid *g, int on);
 
+/* Arithmetic of the reconstruction and flux kernels of an FP64 grid:
+ * double_single = 0 (default) runs them in FP64; 1 runs them in double-single
+ * arithmetic (each value an unevaluated sum of two FP32 numbers, about 48
+ * significant bits, error-free transformations of Knuth and Dekker) on the
+ * FP32 pipe, with the state, the face buffers, the stage update and every
+ * sum still in FP64 and the transcendental terms of the equilibrium state
+ * evaluated in FP64. GB300 runs FP64 at about 1/64 of its FP32 rate, so the
+ * double-single step is several times faster; its results agree with the
+ * FP64 ones to about 1e-13 relative (not bit for bit). Recorded steps of the
+ * adjoint (gks_step_record) always run in FP64. Applies from the next step.
+ * Returns GKS_ERR_STATE for an FP32C grid. */
+int gks_set_fp64_arithmetic(gks_grid *g, int double_single);
+
 /* Current time and the last time step (synchronises). */
 int gks_get_time(gks_grid *g, double *t, double *dt_last);
 int gks_set_time(gks_grid *g, double t);
@@ -391,6 +404,19 @@ const char *gks_kernel_group_name(int group);
  * race and must be serialised by the caller. */
 int gks_diagnostics_noalloc(const double *d_state, int nx, int ny, int nz, const double *d_hx,
                             const double *d_hy, const double *d_hz, double *d_out, void *stream);
+
+/* gks_alu_peak_probe: a measurement aid with no counterpart in the paper.
+ * Launches, asynchronously on stream, a loop of independent fused multiply-
+ * adds (FP64 when fp64 != 0, else FP32) over 4 blocks of 256 threads per SM,
+ * each thread doing iters x 128 FMAs, and writes to *flops the operations of
+ * that launch (2 per FMA). Timed with CUDA events on the same stream, the
+ * ratio is the arithmetic peak the stencil kernels' ALU roofline is measured
+ * against.
+ *   d_sink  device buffer of at least 4 x (number of SMs) doubles; nothing is
+ *           written to it in practice (it keeps the loop's result alive).
+ * Returns GKS_ERR_ARG for null pointers or iters < 1, GKS_ERR_CUDA if the
+ * launch fails. */
+int gks_alu_peak_probe(int fp64, long iters, void *d_sink, void *stream, double *flops);
 
 #ifdef __cplusplus
 }

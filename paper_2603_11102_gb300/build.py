@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgks.so")
 OUT_DEBUG = os.path.join(OUT, "debug")
 LIB_DEBUG = os.path.join(OUT_DEBUG, "libgks_debug.so")
-SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu", "gks_adjoint.cu"]
+SOURCES = ["gks_api.cu", "gks_stencil.cu", "gks_forcing.cu", "gks_noalloc.cu", "gks_adjoint.cu", "gks_peak.cu"]
 HEADERS = ["gks_internal.h", "gks_device.cuh", os.path.join(ROOT, "include", "gks_api.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1164,7 +1164,7 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
     float *Ahi = (float *)w.Asplit, *Alo = Ahi + 4 * c.np;
     if (f32) {
         const long n = 4 * c.np, nb = (n + 255) / 256;
-        split_kernel<<<(int)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, c.stream>>>(Aw, Ahi, Alo, n);
+        split_kernel<<<(int)(nb < 16L * sm_count() ? nb : 16L * sm_count()), 256, 0, c.stream>>>(Aw, Ahi, Alo, n);
     }
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);

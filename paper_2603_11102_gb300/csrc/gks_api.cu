@@ -252,6 +252,19 @@ int cell_range(const Ctx &c, int a, double lo, double hi, int out[2])
 
 void gks::record_error(const char *msg) { g_err = msg; }
 
+// Streaming multiprocessors of the current device, looked up once.
+int gks::sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
 extern "C" {
 
 const char *gks_last_error(const gks_grid *g) { return g ? g->err.c_str() : g_err.c_str(); }
@@ -803,6 +816,15 @@ int capture_step(gks_grid *g)
 }
 }  // namespace
 
+int gks_set_fp64_arithmetic(gks_grid *g, int double_single)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    if (g->c.prec != GKS_FP64) return fail(g, GKS_ERR_STATE, "FP64 grids only");
+    g->c.fp64_ds = double_single != 0;
+    g->version++;   // a captured step graph is captured again
+    return GKS_OK;
+}
+
 int gks_set_graphs(gks_grid *g, int on)
 {
     if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
@@ -933,7 +955,12 @@ int gks_forces_async(gks_grid *g, int id, double *h_out, size_t n)
 int gks_diagnostics(gks_grid *g, double out[5])
 {
     if (!g || !out) return fail(g, GKS_ERR_ARG, "null argument");
+    // timed as its own range of the misc group (no boundary shared with a step)
+    g->prof.last_end = nullptr;
+    mark(g->c, K_MISC, 1);
     launch_diagnostics(g->c, g->d_diag);
+    mark(g->c, K_MISC, 0);
+    g->prof.last_end = nullptr;
     int rc = check_launch(g, "diagnostics");
     if (!rc)
         rc = cuda_check(g, cudaMemcpyAsync(out, g->d_diag, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->c.stream),

@@ -9,6 +9,7 @@
 
 #include <cstdint>
 
+#include "gks_ds.cuh"
 #include "gks_internal.h"
 
 namespace gks {
@@ -194,6 +195,29 @@ __device__ __forceinline__ void half_space_terms(float z, float &e, float &m1, f
         m1 = expm1f(x);
         ex = expf(x);
     }
+}
+
+// Value conversion between a storage type and a compute type (identity, or
+// double <-> double-single).
+template <typename T>
+__device__ __forceinline__ T cvt(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ dsf cvt<dsf>(double x) { return to_ds(x); }
+template <typename T>
+__device__ __forceinline__ T cvt(float x) { return (T)x; }
+template <typename T>
+__device__ __forceinline__ T cvt(dsf x) { return (T)to_double(x); }
+template <>
+__device__ __forceinline__ dsf cvt<dsf>(dsf x) { return x; }
+
+// Double-single: the transcendental terms in FP64 (two calls per face).
+__device__ __forceinline__ void half_space_terms(dsf z, dsf &e, dsf &m1, dsf &ex)
+{
+    double de, dm, dx;
+    half_space_terms(to_double(z), de, dm, dx);
+    e = to_ds(de);
+    m1 = to_ds(dm);
+    ex = to_ds(dx);
 }
 
 // Equilibrium state at a face (local frame, rho written as rho - off): the

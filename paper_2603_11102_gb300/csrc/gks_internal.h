@@ -39,6 +39,7 @@ struct Scalars {
 // Host-side description of every device buffer and constant of one grid.
 struct Ctx {
     int prec;                 // GKS_FP64 or GKS_FP32C
+    int fp64_ds = 0;          // FP64 grids: reconstruction and flux in double-single arithmetic
     int n[3], P[3];
     long np;                  // element stride between component arrays (>= P0 P1 P2)
     long ncell;               // interior cells
@@ -93,6 +94,8 @@ inline void mark(const Ctx &c, int group, int begin)
 
 // Message returned by gks_last_error(NULL) on this thread (gks_api.cu).
 void record_error(const char *msg);
+// Streaming multiprocessors of the current device (looked up once).
+int sm_count();
 
 // Debug-bounds builds: the index-check flag of each translation unit with
 // kernels, taken and cleared (always 0 in a plain build).

@@ -149,7 +149,7 @@ void ghost_impl(const Ctx &c, R *w)
 
 // ------------------------------------------------------------ face state --
 
-template <typename R>
+template <typename R, typename C = R>
 struct FaceEqArgs {
     const R *w;      // working state, 4 arrays of np
     long np;
@@ -161,7 +161,7 @@ struct FaceEqArgs {
     long sd, s1, s2; // element strides along d, t1, t2
     int cn, c1, c2;  // state component of the normal / t1 / t2 momentum
     int nf, K;       // faces along d, faces per thread of the marching kernel
-    Phys<R> ph;
+    Phys<C> ph;      // in the compute type
 };
 
 constexpr int kMarch = 16;   // faces per thread of the marching face-state kernel
@@ -170,9 +170,10 @@ constexpr int kMarch = 16;   // faces per thread of the marching face-state kern
 // tangential position of the extended face box, with the 5 cells around the
 // current cell in registers. Per cell it forms both face values of WENO5
 // from one set of smoothness indicators; face f takes the right-face value
-// of cell f-1 and the left-face value of cell f.
-template <typename R>
-__global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
+// of cell f-1 and the left-face value of cell f. R is the storage type, C
+// the arithmetic type (R, or double-single for FP64 storage).
+template <typename R, typename C = R>
+__global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
 {
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
     const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
@@ -186,19 +187,19 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
         !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
         return;
     const int comp[4] = {0, A.cn, A.c1, A.c2};
-    const Phys<R> &ph = A.ph;
+    const Phys<C> &ph = A.ph;
     // window w[v][k] = cell (c - 2 + k); start with c = f0 - 1
-    R w[4][5];
+    C w[4][5];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const R *p = A.w + comp[v] * A.np + base;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) w[v][k] = __ldg(p + (long)(f0 - 3 + k + G) * A.sd);
+        for (int k = 0; k < 5; ++k) w[v][k] = cvt<C>(__ldg(p + (long)(f0 - 3 + k + G) * A.sd));
     }
-    R Qprev[4];
+    C Qprev[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        R l;
+        C l;
         weno5_pair(w[v], Qprev[v], l);
     }
     // the cell entering the window, loaded one face ahead
@@ -206,12 +207,12 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
 #pragma unroll
     for (int v = 0; v < 4; ++v) nxt[v] = __ldg(A.w + comp[v] * A.np + base + (long)(f0 + 2 + G) * A.sd);
     for (int f = f0; f < f1; ++f) {
-        R Ql[4], Qr[4];
+        C Ql[4], Qr[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) w[v][k] = w[v][k + 1];
-            w[v][4] = nxt[v];
+            w[v][4] = cvt<C>(nxt[v]);
         }
         if (f + 1 < f1) {
             // cell f + 3 <= nf + 1 = n + 2: inside the ghost layers
@@ -223,22 +224,22 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R> A)
             Ql[v] = Qprev[v];
             weno5_pair(w[v], Qprev[v], Qr[v]);
         }
-        R Q0[4];
+        C Q0[4];
         face_equilibrium(ph, Ql, Qr, Q0);
-        const R s = A.ihf[f] * R(1.0 / 12.0);
+        const C s = cvt<C>(A.ihf[f]) * C(1.0 / 12.0);
         const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            A.fq[v * A.nfq + o] = Q0[v];
+            A.fq[v * A.nfq + o] = cvt<R>(Q0[v]);
             // cells f-2 .. f+1 are w[v][0..3]
-            A.fq[(4 + v) * A.nfq + o] = (R(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s;
+            A.fq[(4 + v) * A.nfq + o] = cvt<R>((C(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s);
         }
     }
 }
 
 // ------------------------------------------------------------- face flux --
 
-template <typename R>
+template <typename R, typename C = R>
 struct FluxArgs {
     R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
     long nff;
@@ -248,7 +249,7 @@ struct FluxArgs {
     const R *ih1, *ih2;  // inverse cell widths along t1, t2 (padded index)
     int n1, n2, nf;
     int gcomp[4];        // global component of local component 0..3
-    Phys<R> ph;
+    Phys<C> ph;          // in the compute type
     Scalars *scal;
 };
 
@@ -278,6 +279,19 @@ __device__ __forceinline__ void sts4(double *p, const double q[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(q[0], q[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(q[2], q[3]);
 }
+// FP64 storage, double-single arithmetic: converted at the load
+__device__ __forceinline__ void lds8(const double *p, dsf q[8])
+{
+    double d[8];
+    lds8(p, d);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) q[i] = to_ds(d[i]);
+}
+__device__ __forceinline__ void sts4(dsf *p, const dsf q[4])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(q[0].hi, q[0].lo, q[1].hi, q[1].lo);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(q[2].hi, q[2].lo, q[3].hi, q[3].lo);
+}
 
 // Tile t of the face box as (t1 tile, t2 tile, face): t = ta + NA (tb + NB f).
 struct TileIdx {
@@ -302,19 +316,19 @@ static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assu
 // tasks (Q0 or slope, component, row, group of 4 columns): a task reads 8
 // consecutive values of its row and writes 4 columns; the lanes of a warp
 // share the kind and the component.
-template <typename R>
-__device__ __forceinline__ void tile_t1_pass(const R *sq, R *st, int tid)
+template <typename R, typename C>
+__device__ __forceinline__ void tile_t1_pass(const R *sq, C *st, int tid)
 {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const int task = tid + j * 256;
         const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
         const int r = rc >> 3, cg = rc & 7;
-        R q[8];
+        C q[8];
         lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
-        R *o = st + r * TX + 4 * cg;
+        C *o = st + r * TX + 4 * cg;
         if (kind == 0) {
-            R vm[4], vp[4], dm[4], dp[4];
+            C vm[4], vp[4], dm[4], dp[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
             sts4(o + (v * 4 + 0) * ST_ROWS, vm);
@@ -322,7 +336,7 @@ __device__ __forceinline__ void tile_t1_pass(const R *sq, R *st, int tid)
             sts4(o + (v * 4 + 2) * ST_ROWS, dm);
             sts4(o + (v * 4 + 3) * ST_ROWS, dp);
         } else {
-            R vm[4], vp[4];
+            C vm[4], vp[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
             sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
@@ -360,7 +374,8 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
             tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
             Dn[0][v] = vm; Dn[1][v] = vp;
         }
-        if (GP && gp) {
+        if constexpr (GP) {
+          if (gp) {
 #pragma unroll
             for (int nn = 0; nn < 2; ++nn) {
                 const long o = (long)(16 * (2 * m + nn)) * ngp + face;
@@ -389,6 +404,7 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
                     }
                 }
             }
+          }
         }
 #pragma unroll
         for (int nn = 0; nn < 2; ++nn) {
@@ -406,12 +422,13 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of the next tile is fetched by TMA into the other buffer while the
 // current one is computed.
-template <typename R, bool NEED_F0, bool GP>
-__global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A)
+template <typename R, typename C, bool NEED_F0, bool GP>
+__global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A)
 {
+    static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
-    R *st = sqb + 2 * SQ_N;
+    C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
@@ -454,15 +471,15 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
 
         const int a = a0 + tx, b = b0 + ty;
         if (a < A.n1 && b < A.n2) {
-            const R ih1 = __ldg(A.ih1 + a + G), ih2 = __ldg(A.ih2 + b + G);
-            R acc0[4], acc1[4];
+            const C ih1 = cvt<C>(__ldg(A.ih1 + a + G)), ih2 = cvt<C>(__ldg(A.ih2 + b + G));
+            C acc0[4], acc1[4];
             const long o = ((long)f * A.n2 + b) * A.n1 + a;
-            tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
+            tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (!in_bounds(o, A.nff)) break;
-                if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * acc0[v];
-                A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * acc1[v];
+                if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * cvt<R>(acc0[v]);
+                A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * cvt<R>(acc1[v]);
             }
         }
         __syncthreads();   // st and this buffer are free again
@@ -596,15 +613,16 @@ __device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int L, int nf)
     return z;
 }
 
-template <typename R, int STAGE, bool GP>
+template <typename R, typename C, int STAGE, bool GP>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
-    flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R> A, UpdArgs<R> U)
+    flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A, UpdArgs<R> U)
 {
+    static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
     constexpr bool NEED_F0 = STAGE == 1;
     constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
-    R *st = sqb + 2 * SQ_N;
+    C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     R *sx = reinterpret_cast<R *>(bar + 2);               // [NC][SX_H][SX_W]
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -626,7 +644,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const double dt = A.scal->dt;
     bool bad = false;
     double mx = 0.0;   // stage 2 with prep: max |U|^2 of this thread's cells outside the forcing boxes
-    R P0[4], P1[4];   // F0, F1 of the previous face of this column
+    R P0[4], P1[4];   // F0, F1 of the previous face of this column (storage type: the
+                      // differences of neighbouring faces telescope exactly)
     for (int k = 0; cur.it < nitems; ++k) {
         const int buf = k & 1;
         ZWalk nxt = cur;
@@ -714,12 +733,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 
         R F0[4], F1[4];
         if (in) {
-            tile_gauss_flux<R, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, F0, F1, A.gp, A.gp32, A.ngp,
-                                        ((long)f * A.n2 + b) * A.n1 + a);
+            C G0[4], G1[4];
+            tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, cvt<C>(ih1), cvt<C>(ih2), G0, G1, A.gp, A.gp32,
+                                            A.ngp, ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                F0[v] *= R(0.25);
-                F1[v] *= R(0.25);
+                F0[v] = NEED_F0 ? R(0.25) * cvt<R>(G0[v]) : R(0);
+                F1[v] = R(0.25) * cvt<R>(G1[v]);
             }
         }
         if (upd) {
@@ -770,19 +790,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     if (STAGE == 2 && U.prep) block_max_to(mx, &A.scal->maxu2_bits);
 }
 
-// Resident blocks per SM x SMs for a persistent kernel with `smem` bytes of
-// dynamic shared memory (raises its dynamic shared-memory limit first).
-int sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
 
 // Faces per thread of the marching face-state kernel: kMarch, halved (down
 // to 4) while the launch would have fewer than two blocks per SM, so that a
@@ -808,21 +815,25 @@ int persistent_grid(K kernel, size_t smem)
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
-template <typename R, int STAGE>
+template <typename R, typename C, int STAGE>
 struct FluxGrids {
     int flux[2] = {0, 0}, flux_update[2] = {0, 0};   // without / with the Gauss-point output
 };
 
-template <typename R, int STAGE>
-const FluxGrids<R, STAGE> &flux_grids()
+// The Gauss-point output (recorded steps of the adjoint) exists only where the
+// arithmetic type is the storage type.
+template <typename R, typename C, int STAGE>
+const FluxGrids<R, C, STAGE> &flux_grids()
 {
-    static FluxGrids<R, STAGE> g;
+    static FluxGrids<R, C, STAGE> g;
     if (!g.flux[0]) {
         constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
-        g.flux[0] = persistent_grid(face_flux_kernel<R, STAGE == 1, false>, flux_smem_bytes<R>());
-        g.flux[1] = persistent_grid(face_flux_kernel<R, STAGE == 1, true>, flux_smem_bytes<R>());
-        g.flux_update[0] = persistent_grid(flux_update_kernel<R, STAGE, false>, su);
-        g.flux_update[1] = persistent_grid(flux_update_kernel<R, STAGE, true>, su);
+        g.flux[0] = persistent_grid(face_flux_kernel<R, C, STAGE == 1, false>, flux_smem_bytes<R>());
+        g.flux_update[0] = persistent_grid(flux_update_kernel<R, C, STAGE, false>, su);
+        if constexpr (std::is_same<R, C>::value) {
+            g.flux[1] = persistent_grid(face_flux_kernel<R, C, STAGE == 1, true>, flux_smem_bytes<R>());
+            g.flux_update[1] = persistent_grid(flux_update_kernel<R, C, STAGE, true>, su);
+        }
     }
     return g;
 }
@@ -846,17 +857,17 @@ int z_segment(int ncol, int nf, int G)
     return bestL;
 }
 
-template <typename R, int STAGE>
+template <typename R, typename C, int STAGE>
 void stage_impl(const Ctx &c)
 {
-    const Phys<R> ph = make_phys<R>(c);
+    const Phys<C> ph = make_phys<C>(c);
     const R *w = (const R *)(STAGE == 1 ? c.wk0 : c.wk1);
     const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
-    const FluxGrids<R, STAGE> &grids = flux_grids<R, STAGE>();
+    const FluxGrids<R, C, STAGE> &grids = flux_grids<R, C, STAGE>();
     const dim3 blk(TX, TY);
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
-        FaceEqArgs<R> E;
+        FaceEqArgs<R, C> E;
         E.w = w;
         E.np = c.np;
         E.fq = (R *)c.fq;
@@ -877,10 +888,10 @@ void stage_impl(const Ctx &c)
         const CUtensorMap &tmap = c.tmap[d];
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
         mark(c, K_FACE_EQ, 1);
-        face_eq_march_kernel<R><<<ge, blk, 0, c.stream>>>(E);
+        face_eq_march_kernel<R, C><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);
 
-        FluxArgs<R> F;
+        FluxArgs<R, C> F;
         F.ff = (R *)c.ff[d];
         F.nff = c.nff[d];
         F.ih1 = (const R *)c.ih[t1];
@@ -901,12 +912,17 @@ void stage_impl(const Ctx &c)
         const int grp = d < 2 ? K_FACE_FLUX : K_FLUX_UPDATE;
         mark(c, grp, 1);
         const int gpo = F.gp != nullptr;
+        if constexpr (!std::is_same<R, C>::value) F.gp = nullptr;
         if (d < 2) {
             const int grid = (int)(ntiles < grids.flux[gpo] ? ntiles : grids.flux[gpo]);
-            if (gpo)
-                face_flux_kernel<R, STAGE == 1, true><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
-            else
-                face_flux_kernel<R, STAGE == 1, false><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+            if constexpr (std::is_same<R, C>::value) {
+                if (gpo)
+                    face_flux_kernel<R, C, STAGE == 1, true><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+                else
+                    face_flux_kernel<R, C, STAGE == 1, false><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+            } else {
+                face_flux_kernel<R, C, STAGE == 1, false><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+            }
         } else {
             // z faces: flux and the stage update of every cell
             UpdArgs<R> U;
@@ -938,10 +954,14 @@ void stage_impl(const Ctx &c)
             const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
             const int grid = (int)(nitems < grids.flux_update[gpo] ? nitems : grids.flux_update[gpo]);
             constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
-            if (gpo)
-                flux_update_kernel<R, STAGE, true><<<grid, blk, su, c.stream>>>(tmap, F, U);
-            else
-                flux_update_kernel<R, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
+            if constexpr (std::is_same<R, C>::value) {
+                if (gpo)
+                    flux_update_kernel<R, C, STAGE, true><<<grid, blk, su, c.stream>>>(tmap, F, U);
+                else
+                    flux_update_kernel<R, C, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
+            } else {
+                flux_update_kernel<R, C, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
+            }
         }
         mark(c, grp, 0);
     }
@@ -1245,10 +1265,12 @@ void launch_ghost(const Ctx &c, void *w)
 
 void launch_stage(const Ctx &c, int stage)
 {
-    if (c.prec == GKS_FP64)
-        stage == 1 ? stage_impl<double, 1>(c) : stage_impl<double, 2>(c);
+    if (c.prec == GKS_FP64 && c.fp64_ds && !c.gp_dir[0])
+        stage == 1 ? stage_impl<double, dsf, 1>(c) : stage_impl<double, dsf, 2>(c);
+    else if (c.prec == GKS_FP64)
+        stage == 1 ? stage_impl<double, double, 1>(c) : stage_impl<double, double, 2>(c);
     else
-        stage == 1 ? stage_impl<float, 1>(c) : stage_impl<float, 2>(c);
+        stage == 1 ? stage_impl<float, float, 1>(c) : stage_impl<float, float, 2>(c);
 }
 
 void launch_cfl(const Ctx &c)
@@ -1323,7 +1345,7 @@ void launch_widen(const Ctx &c, const float *a, const float *b, double *out, lon
 {
     mark(c, K_MISC, 1);
     const long nb = (n + 255) / 256;
-    widen_kernel<<<(int)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, c.stream>>>(a, b, out, n, n0, off0);
+    widen_kernel<<<(int)(nb < 16L * sm_count() ? nb : 16L * sm_count()), 256, 0, c.stream>>>(a, b, out, n, n0, off0);
     mark(c, K_MISC, 0);
 }
 

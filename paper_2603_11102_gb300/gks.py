@@ -89,6 +89,7 @@ SIGNATURES = {
     "gks_forces_record_len": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
     "gks_step_async": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "gks_set_fp64_arithmetic": (C.c_int, [C.c_void_p, C.c_int]),
     "gks_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "gks_forces_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "gks_adjoint_tape_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -101,6 +102,7 @@ SIGNATURES = {
                                    C.c_double, _dp, _dp]),
     "gks_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gks_alu_peak_probe": (C.c_int, [C.c_int, C.c_long, C.c_void_p, C.c_void_p, _dp]),
 }
 
 lib = None
@@ -445,6 +447,13 @@ class Grid:
                                     gs, C.byref(gu)), self.h)
         return out, gu.value
 
+    def set_fp64_arithmetic(self, mode):
+        """"fp64" (default) or "ds": double-single reconstruction and flux on
+        an FP64 grid (gks_set_fp64_arithmetic)."""
+        if mode not in ("fp64", "ds"):
+            raise ValueError(mode)
+        _check(lib.gks_set_fp64_arithmetic(self.h, int(mode == "ds")), self.h)
+
     def profile_enable(self, timing=True):
         _check(lib.gks_profile_enable(self.h, int(bool(timing))), self.h)
 
@@ -460,3 +469,16 @@ class Grid:
         out = (C.c_long * 7)()
         _check(lib.gks_state_layout(self.h, out), self.h)
         return list(out)
+
+
+def alu_peak_probe(fp64: bool, iters: int, sink, stream) -> float:
+    """Launch the FMA-loop peak probe of the library on stream (async); sink
+    is a device tensor of at least 4 x SMs doubles. Returns the FP32 (or FP64)
+    operations of that launch; time it with CUDA events on the same stream."""
+    load()
+    out = C.c_double(0.0)
+    rc = lib.gks_alu_peak_probe(int(bool(fp64)), int(iters), C.c_void_p(sink.data_ptr()),
+                                C.c_void_p(stream.cuda_stream), C.byref(out))
+    if rc != GKS_OK:
+        raise GKSError(rc, lib.gks_last_error(None).decode())
+    return out.value

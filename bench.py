@@ -441,6 +441,8 @@ def run_ours(args, world, rank, local):
     w = make_workload(args.workload)
     peaks, peak_kind = load_peaks()
     g = gks.Grid.from_workload(w, precision=args.precision, device=dev)
+    if args.precision == "fp64" and args.fp64_arithmetic == "ds":
+        g.set_fp64_arithmetic("ds")
     for _ in range(args.warmup):
         g.step(1)
     stream = g.stream
@@ -706,6 +708,8 @@ def main():
     ap.add_argument("--workload", default="alm-ibm", choices=["alm-ibm", "alm", "channel", "tgv", "tgv96", "tgv192"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-arithmetic", default="fp64", choices=["fp64", "ds"],
+                    help="with --precision fp64: FP64 or double-single reconstruction and flux")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-graphs", action="store_true", help="skip the small-grid CUDA graph timing")
     ap.add_argument("--cpu-steps", type=int, default=20)

@@ -210,14 +210,50 @@ __device__ __forceinline__ T cvt(dsf x) { return (T)to_double(x); }
 template <>
 __device__ __forceinline__ dsf cvt<dsf>(dsf x) { return x; }
 
-// Double-single: the transcendental terms in FP64 (two calls per face).
+// Double-single: the same Maclaurin series as the FP64 version (n = 0..12
+// and 1..13, dropped terms below 1e-17) in double-single arithmetic for
+// |z| <= 1/2; beyond, the FP64 library functions.
 __device__ __forceinline__ void half_space_terms(dsf z, dsf &e, dsf &m1, dsf &ex)
 {
-    double de, dm, dx;
-    half_space_terms(to_double(z), de, dm, dx);
-    e = to_ds(de);
-    m1 = to_ds(dm);
-    ex = to_ds(dx);
+    if (fabsf(z.hi) <= 0.5f) {
+        const dsf t = z * z, x = -t;
+        constexpr double k = 1.1283791670955126;   // 2 / sqrt(pi)
+        dsf p = dsf(k / (479001600.0 * 25.0));
+        p = fma(p, t, dsf(-k / (39916800.0 * 23.0)));
+        p = fma(p, t, dsf(k / (3628800.0 * 21.0)));
+        p = fma(p, t, dsf(-k / (362880.0 * 19.0)));
+        p = fma(p, t, dsf(k / (40320.0 * 17.0)));
+        p = fma(p, t, dsf(-k / (5040.0 * 15.0)));
+        p = fma(p, t, dsf(k / (720.0 * 13.0)));
+        p = fma(p, t, dsf(-k / (120.0 * 11.0)));
+        p = fma(p, t, dsf(k / (24.0 * 9.0)));
+        p = fma(p, t, dsf(-k / (6.0 * 7.0)));
+        p = fma(p, t, dsf(k / (2.0 * 5.0)));
+        p = fma(p, t, dsf(-k / 3.0));
+        p = fma(p, t, dsf(k));
+        e = p * z;
+        dsf q = dsf(1.0 / 6227020800.0);   // 1/13!
+        q = fma(q, x, dsf(1.0 / 479001600.0));
+        q = fma(q, x, dsf(1.0 / 39916800.0));
+        q = fma(q, x, dsf(1.0 / 3628800.0));
+        q = fma(q, x, dsf(1.0 / 362880.0));
+        q = fma(q, x, dsf(1.0 / 40320.0));
+        q = fma(q, x, dsf(1.0 / 5040.0));
+        q = fma(q, x, dsf(1.0 / 720.0));
+        q = fma(q, x, dsf(1.0 / 120.0));
+        q = fma(q, x, dsf(1.0 / 24.0));
+        q = fma(q, x, dsf(1.0 / 6.0));
+        q = fma(q, x, dsf(0.5));
+        q = fma(q, x, dsf(1.0));
+        m1 = q * x;
+        ex = dsf(1.0) + m1;
+    } else {
+        double de, dm, dx;
+        half_space_terms(to_double(z), de, dm, dx);
+        e = to_ds(de);
+        m1 = to_ds(dm);
+        ex = to_ds(dx);
+    }
 }
 
 // Equilibrium state at a face (local frame, rho written as rho - off): the
@@ -395,6 +431,10 @@ __device__ __forceinline__ void cp_async(double *dst, const double *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)),
                  "l"((unsigned long long)__cvta_generic_to_global(src))
                  : "memory");
+}
+__device__ __forceinline__ void cp_async(dsf *dst, const dsf *src)
+{
+    cp_async(reinterpret_cast<double *>(dst), reinterpret_cast<const double *>(src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }

@@ -27,13 +27,50 @@ struct __align__(8) dsf {
     __host__ __device__ explicit constexpr dsf(int x) : hi((float)x), lo(0.0f) {}
 };
 
-__device__ __forceinline__ double to_double(dsf a) { return __dadd_rn((double)a.hi, (double)a.lo); }
-__device__ __forceinline__ double to_double(double a) { return a; }
+// hi = fl32(q), lo = fl32(q - hi) (round to nearest even) from the bits of
+// q with integer and FP32 operations only: the FP64 pipe of GB300 (sm_103) runs at
+// a small fraction of the FP32 rate, and four conversions and a subtraction
+// per value in FP64 made the state upload compute-bound. With q =
+// (-1)^s 2^e 1.m (52-bit m) and 2^-74 <= |q| < 2^127, hi keeps the top 23
+// bits of m, rounded by the low 29 bits (a carry into the exponent is the
+// correct result); q - hi is t 2^(e-52) with t = low bits (rounded down) or
+// 2^29 - low bits (rounded up, opposite sign), and fl32 of it is fl32(t)
+// scaled by the normal power of two 2^(e-52). q - hi = 0 gives +0, as the
+// FP64 subtraction does. Zero and the other exponents take the FP64 route.
+__device__ __forceinline__ void split_hi_lo(double q, float &h, float &l)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+    const unsigned int sgn = hw & 0x80000000u;
+    if (e >= -74 && e <= 126) {
+        const unsigned int top = ((hw & 0xfffffu) << 3) | (lw >> 29);
+        const unsigned int low = lw & 0x1fffffffu;
+        const bool up = low > 0x10000000u || (low == 0x10000000u && (top & 1u));
+        h = __uint_as_float((sgn | ((unsigned int)(e + 127) << 23) | top) + (up ? 1u : 0u));
+        const unsigned int t = up ? 0x20000000u - low : low;
+        const float mag = __fmul_rn(__uint2float_rn(t), __uint_as_float((unsigned int)(e + 75) << 23));
+        const bool neg = (sgn != 0u) != up;
+        l = __uint_as_float(__float_as_uint(mag) | ((neg && t != 0u) ? 0x80000000u : 0u));
+    } else if ((b << 1) == 0ull) {
+        h = __uint_as_float(sgn);
+        l = 0.0f;
+    } else {
+        h = (float)q;
+        l = (float)(q - (double)h);
+    }
+}
+
+// double -> double-single without FP64 arithmetic (hi + lo keeps the top 48
+// bits of the 53), double-single -> double by one FP64 addition.
 __device__ __forceinline__ dsf to_ds(double x)
 {
-    const float h = __double2float_rn(x);
-    return dsf(h, __double2float_rn(__dsub_rn(x, (double)h)));
+    dsf r;
+    split_hi_lo(x, r.hi, r.lo);
+    return r;
 }
+__device__ __forceinline__ double to_double(dsf a) { return __dadd_rn((double)a.hi, (double)a.lo); }
+__device__ __forceinline__ double to_double(double a) { return a; }
 
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ dsf two_sum(float a, float b)
@@ -88,6 +125,8 @@ __device__ __forceinline__ dsf &operator*=(dsf &a, dsf b) { return a = a * b; }
 using ::fma;
 __device__ __forceinline__ dsf fma(dsf a, dsf b, dsf c) { return a * b + c; }
 __device__ __forceinline__ dsf wdiv(dsf a, dsf b) { return a / b; }
+// exact scaling by a power of two
+__device__ __forceinline__ dsf scale_pow2(dsf a, float p) { return dsf(__fmul_rn(a.hi, p), __fmul_rn(a.lo, p)); }
 
 }  // namespace dev
 }  // namespace gks

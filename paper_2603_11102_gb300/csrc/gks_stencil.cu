@@ -149,11 +149,17 @@ void ghost_impl(const Ctx &c, R *w)
 
 // ------------------------------------------------------------ face state --
 
+// Storage type of the face boxes and face fluxes between kernels: double-
+// single pairs when the arithmetic is double-single (no conversion between
+// the kernels), else the state's type.
+template <typename R, typename C>
+using Mid = typename std::conditional<std::is_same<C, dsf>::value, dsf, R>::type;
+
 template <typename R, typename C = R>
 struct FaceEqArgs {
     const R *w;      // working state, 4 arrays of np
     long np;
-    R *fq;           // 8 arrays of nfq
+    Mid<R, C> *fq;   // 8 arrays of nfq
     long nfq;
     const R *ihf;    // inverse centre distance at faces of axis d
     int n1, n2;      // interior cells along t1, t2
@@ -230,9 +236,9 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
         const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            A.fq[v * A.nfq + o] = cvt<R>(Q0[v]);
+            A.fq[v * A.nfq + o] = cvt<Mid<R, C>>(Q0[v]);
             // cells f-2 .. f+1 are w[v][0..3]
-            A.fq[(4 + v) * A.nfq + o] = cvt<R>((C(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s);
+            A.fq[(4 + v) * A.nfq + o] = cvt<Mid<R, C>>((C(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s);
         }
     }
 }
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
 
 template <typename R, typename C = R>
 struct FluxArgs {
-    R *ff;           // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
+    Mid<R, C> *ff;   // 8 arrays of nff (0..3 F0, 4..7 F1, global components)
     long nff;
     void *gp;        // FP64 only, may be null: the 64 Gauss-point inputs per face (stride ngp)
     long ngp;
@@ -252,6 +258,12 @@ struct FluxArgs {
     Phys<C> ph;          // in the compute type
     Scalars *scal;
 };
+
+// The face average 1/4 sum of the Gauss-point fluxes in the storage type M.
+template <typename M, typename C>
+__device__ __forceinline__ M quarter(C acc) { return cvt<M>(acc) * M(0.25); }
+template <>
+__device__ __forceinline__ dsf quarter<dsf, dsf>(dsf acc) { return scale_pow2(acc, 0.25f); }
 
 // 8 consecutive values of a shared-memory row from a 16-byte aligned address,
 // and 4 consecutive values to one.
@@ -279,13 +291,14 @@ __device__ __forceinline__ void sts4(double *p, const double q[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(q[0], q[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(q[2], q[3]);
 }
-// FP64 storage, double-single arithmetic: converted at the load
-__device__ __forceinline__ void lds8(const double *p, dsf q[8])
+__device__ __forceinline__ void lds8(const dsf *p, dsf q[8])
 {
-    double d[8];
-    lds8(p, d);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) q[i] = to_ds(d[i]);
+    for (int i = 0; i < 4; ++i) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[i];
+        q[2 * i] = dsf(a.x, a.y);
+        q[2 * i + 1] = dsf(a.z, a.w);
+    }
 }
 __device__ __forceinline__ void sts4(dsf *p, const dsf q[4])
 {
@@ -426,8 +439,9 @@ template <typename R, typename C, bool NEED_F0, bool GP>
 __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A)
 {
     static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
+    using M = Mid<R, C>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
+    M *sqb = reinterpret_cast<M *>(smem_raw);            // 2 buffers of SQ_N
     C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -462,7 +476,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             __syncthreads();
             return;
         }
-        const R *sq = sqb + buf * SQ_N;
+        const M *sq = sqb + buf * SQ_N;
         const int a0 = cur.ta * TX, b0 = cur.tb * TY, f = cur.f;
         cur = nxt;
 
@@ -478,8 +492,8 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (!in_bounds(o, A.nff)) break;
-                if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = R(0.25) * cvt<R>(acc0[v]);
-                A.ff[(4 + A.gcomp[v]) * A.nff + o] = R(0.25) * cvt<R>(acc1[v]);
+                if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = quarter<M>(acc0[v]);
+                A.ff[(4 + A.gcomp[v]) * A.nff + o] = quarter<M>(acc1[v]);
             }
         }
         __syncthreads();   // st and this buffer are free again
@@ -490,9 +504,19 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
 
 constexpr int kMaxPrepBoxes = 8;   // forcing boxes the fused prep can leave out
 
-template <typename R>
+// Read-only loads and 8-byte asynchronous copies of a face-flux value.
+__device__ __forceinline__ float ldg_m(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ldg_m(const double *p) { return __ldg(p); }
+__device__ __forceinline__ dsf ldg_m(const dsf *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return dsf(v.x, v.y);
+}
+
+
+template <typename R, typename M = R>
 struct UpdArgs {
-    const R *ffx, *ffy;   // face fluxes of the x and y directions (8 arrays each)
+    const M *ffx, *ffy;   // face fluxes of the x and y directions (8 arrays each)
     long nffx, nffy;
     const R *ihz;         // inverse cell widths along z (padded index)
     int nx, ny, nz, P0, P1;
@@ -531,6 +555,36 @@ __device__ __forceinline__ void add_comp(float &hi, float &lo, float d)
 //   stage 1: W* = W + dt/2 L + dt^2/8 Lt, P = W + dt L + dt^2/6 Lt,
 //   stage 2: W = P + dt^2/3 Lt(W*) + dt f_body.
 // Returns false when a written value is not finite (stage 2).
+// Double-single arithmetic on an FP64 grid: the same update with the state
+// split into double-single (exact to 48 bits) and the results composed back
+// into FP64.
+template <int STAGE>
+__device__ __forceinline__ bool update_cell_ds(const UpdArgs<double, dsf> &A, long lin, double dt, const dsf dx[],
+                                               const dsf dy[], const dsf dz[], dsf ihx, dsf ihy, dsf ihz,
+                                               const double s0[4], double o0[4])
+{
+    const dsf h = to_ds(dt), h2 = h * h;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const dsf Lt = -(dx[4 + v] * ihx + dy[4 + v] * ihy + dz[4 + v] * ihz);
+        const dsf w = to_ds(s0[v]);
+        if (STAGE == 1) {
+            const dsf L = -(dx[v] * ihx + dy[v] * ihy + dz[v] * ihz);
+            ((double *)A.wk1)[v * A.np + lin] = to_double(w + (scale_pow2(h, 0.5f) * L + scale_pow2(h2, 0.125f) * Lt));
+            ((double *)A.pbuf)[v * A.np + lin] = to_double(w + (h * L + (h2 / dsf(6.0)) * Lt));
+        } else {
+            dsf inc = (h2 / dsf(3.0)) * Lt;
+            if (v > 0) inc += h * to_ds((double)A.fb[v - 1]);
+            const double wn = to_double(w + inc);
+            ((double *)A.state)[v * A.np + lin] = wn;
+            bad |= !isfinite(wn);
+            o0[v] = wn;
+        }
+    }
+    return !bad;
+}
+
 template <typename R, int STAGE>
 __device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, double dt, const R dx[], const R dy[],
                                             const R dz[], R ihx, R ihy, R ihz, const R s0[4], const R s1[4],
@@ -615,16 +669,18 @@ __device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int L, int nf)
 
 template <typename R, typename C, int STAGE, bool GP>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
-    flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A, UpdArgs<R> U)
+    flux_update_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A, UpdArgs<R, Mid<R, C>> U)
 {
     static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
+    using M = Mid<R, C>;                       // face boxes, face fluxes and their differences
+    constexpr bool DS = std::is_same<C, dsf>::value;
     constexpr bool NEED_F0 = STAGE == 1;
     constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    R *sqb = reinterpret_cast<R *>(smem_raw);            // 2 buffers of SQ_N
+    M *sqb = reinterpret_cast<M *>(smem_raw);            // 2 buffers of SQ_N
     C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
-    R *sx = reinterpret_cast<R *>(bar + 2);               // [NC][SX_H][SX_W]
+    M *sx = reinterpret_cast<M *>(bar + 2);               // [NC][SX_H][SX_W]
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY, nf = A.nf, L = U.seg;
     const int ncol = NA * NB, nitems = ncol * ((nf + L - 1) / L);
@@ -644,7 +700,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const double dt = A.scal->dt;
     bool bad = false;
     double mx = 0.0;   // stage 2 with prep: max |U|^2 of this thread's cells outside the forcing boxes
-    R P0[4], P1[4];   // F0, F1 of the previous face of this column (storage type: the
+    M P0[4], P1[4];   // F0, F1 of the previous face of this column (storage type: the
                       // differences of neighbouring faces telescope exactly)
     for (int k = 0; cur.it < nitems; ++k) {
         const int buf = k & 1;
@@ -665,7 +721,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             const int yy = tid & 7;
             if (b0 + yy < U.ny) {
                 const long sxf = (long)U.nz * U.ny;   // stride between x-faces
-                const R *src = U.ffx + C0 * U.nffx + ((long)a0 * U.nz + (f - 1)) * U.ny + b0 + yy;
+                const M *src = U.ffx + C0 * U.nffx + ((long)a0 * U.nz + (f - 1)) * U.ny + b0 + yy;
                 int c = 0, xf = tid >> 3;
                 long go = xf * sxf;
 #pragma unroll
@@ -696,7 +752,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             ih2 = __ldg(A.ih2 + b + G);
             if (upd) ihz = __ldg(U.ihz + f - 1 + G);
         }
-        R dy[8], s0[4], s1[4];
+        M dy[8];
+        R s0[4], s1[4];
         long lin = 0;
         bool cell_ok = true;
         if (upd && in) {
@@ -707,8 +764,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             if (cell_ok) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const R *py = U.ffy + (C0 + c) * U.nffy + iy;
-                    dy[C0 + c] = __ldg(py + sy) - __ldg(py);
+                    const M *py = U.ffy + (C0 + c) * U.nffy + iy;
+                    dy[C0 + c] = ldg_m(py + sy) - ldg_m(py);
                 }
                 const R *src = (const R *)(STAGE == 1 ? U.w0 : U.pbuf);
 #pragma unroll
@@ -731,15 +788,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         tile_t1_pass(sqb + buf * SQ_N, st, tid);
         __syncthreads();
 
-        R F0[4], F1[4];
+        M F0[4], F1[4];
         if (in) {
             C G0[4], G1[4];
             tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, cvt<C>(ih1), cvt<C>(ih2), G0, G1, A.gp, A.gp32,
                                             A.ngp, ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                F0[v] = NEED_F0 ? R(0.25) * cvt<R>(G0[v]) : R(0);
-                F1[v] = R(0.25) * cvt<R>(G1[v]);
+                F0[v] = NEED_F0 ? quarter<M>(G0[v]) : M(0);
+                F1[v] = quarter<M>(G1[v]);
             }
         }
         if (upd) {
@@ -747,7 +804,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             __syncthreads();   // the x-face slab of every thread is in place
             if (in && cell_ok) {
                 const int z = f - 1;
-                R dx[8], dz[8];
+                M dx[8], dz[8];
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     dx[C0 + c] = sx[(c * SX_H + tx + 1) * SX_W + ty] - sx[(c * SX_H + tx) * SX_W + ty];
@@ -758,9 +815,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                     if (NEED_F0) dz[v] = F0[loc[v]] - P0[loc[v]];
                     dz[4 + v] = F1[loc[v]] - P1[loc[v]];
                 }
-                const R ihx = ih1, ihy = ih2;
                 R o0[4], o1[4];
-                bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ihx, ihy, ihz, s0, s1, o0, o1);
+                if constexpr (DS)
+                    bad |= !update_cell_ds<STAGE>(U, lin, dt, dx, dy, dz, cvt<dsf>(ih1), cvt<dsf>(ih2), cvt<dsf>(ihz),
+                                                  s0, o0);
+                else
+                    bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ih1, ih2, ihz, s0, s1, o0, o1);
                 if (STAGE == 2 && U.prep) {
                     bool boxed = false;
                     for (int q = 0; q < U.nbox; ++q)
@@ -870,7 +930,7 @@ void stage_impl(const Ctx &c)
         FaceEqArgs<R, C> E;
         E.w = w;
         E.np = c.np;
-        E.fq = (R *)c.fq;
+        E.fq = (Mid<R, C> *)c.fq;
         E.nfq = c.nfq;
         E.ihf = (const R *)c.ihf[d];
         E.n1 = c.n[t1];
@@ -892,7 +952,7 @@ void stage_impl(const Ctx &c)
         mark(c, K_FACE_EQ, 0);
 
         FluxArgs<R, C> F;
-        F.ff = (R *)c.ff[d];
+        F.ff = (Mid<R, C> *)c.ff[d];
         F.nff = c.nff[d];
         F.ih1 = (const R *)c.ih[t1];
         F.ih2 = (const R *)c.ih[t2];
@@ -925,9 +985,9 @@ void stage_impl(const Ctx &c)
             }
         } else {
             // z faces: flux and the stage update of every cell
-            UpdArgs<R> U;
-            U.ffx = (const R *)c.ff[0];
-            U.ffy = (const R *)c.ff[1];
+            UpdArgs<R, Mid<R, C>> U;
+            U.ffx = (const Mid<R, C> *)c.ff[0];
+            U.ffy = (const Mid<R, C> *)c.ff[1];
             U.nffx = c.nff[0];
             U.nffy = c.nff[1];
             U.ihz = (const R *)c.ih[2];
@@ -1041,39 +1101,6 @@ __global__ void dt_kernel(Scalars *scal, double cfl, double dt_fixed, double hmi
 
 __global__ void advance_kernel(Scalars *scal) { scal->t = scal->t + scal->dt; }
 
-// hi = fl32(q), lo = fl32(q - hi) (round to nearest even) from the bits of
-// q with integer and FP32 operations only: the FP64 pipe of GB300 (sm_103) runs at
-// a small fraction of the FP32 rate, and four conversions and a subtraction
-// per value in FP64 made the state upload compute-bound. With q =
-// (-1)^s 2^e 1.m (52-bit m) and 2^-74 <= |q| < 2^127, hi keeps the top 23
-// bits of m, rounded by the low 29 bits (a carry into the exponent is the
-// correct result); q - hi is t 2^(e-52) with t = low bits (rounded down) or
-// 2^29 - low bits (rounded up, opposite sign), and fl32 of it is fl32(t)
-// scaled by the normal power of two 2^(e-52). q - hi = 0 gives +0, as the
-// FP64 subtraction does. Zero and the other exponents take the FP64 route.
-__device__ __forceinline__ void split_hi_lo(double q, float &h, float &l)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
-    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
-    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
-    const unsigned int sgn = hw & 0x80000000u;
-    if (e >= -74 && e <= 126) {
-        const unsigned int top = ((hw & 0xfffffu) << 3) | (lw >> 29);
-        const unsigned int low = lw & 0x1fffffffu;
-        const bool up = low > 0x10000000u || (low == 0x10000000u && (top & 1u));
-        h = __uint_as_float((sgn | ((unsigned int)(e + 127) << 23) | top) + (up ? 1u : 0u));
-        const unsigned int t = up ? 0x20000000u - low : low;
-        const float mag = __fmul_rn(__uint2float_rn(t), __uint_as_float((unsigned int)(e + 75) << 23));
-        const bool neg = (sgn != 0u) != up;
-        l = __uint_as_float(__float_as_uint(mag) | ((neg && t != 0u) ? 0x80000000u : 0u));
-    } else if ((b << 1) == 0ull) {
-        h = __uint_as_float(sgn);
-        l = 0.0f;
-    } else {
-        h = (float)q;
-        l = (float)(q - (double)h);
-    }
-}
 
 // Compact FP64 state -> the padded state (FP32C: hi = fl32(q), lo =
 // fl32(q - hi)), kPrepZ planes per block. With scal set it also does the

@@ -24,19 +24,42 @@ def test_face_counts_of_the_benchmark():
 
 def test_traffic_figure_only_for_the_current_sources(tmp_path, monkeypatch):
     import bench
-    cur = bench.source_hash()
-    assert len(cur) == 16
-    assert bench.read_traffic("face_flux", "fp32c") == pytest.approx(1.334e9)
-    assert bench.read_traffic("face_flux", "fp64") is None
+    cur = bench.source_hash("face_flux")
+    assert len(cur) == 16 and cur != bench.source_hash("face_eq")
     # a figure taken on other sources is not used
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "traffic.txt").write_text("face_flux fp32c 1e9 0123456789abcdef\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "source_hash", lambda: cur)
+    monkeypatch.setattr(bench, "source_hash", lambda group="face_flux": cur)
     assert bench.read_traffic("face_flux", "fp32c") is None
     (prof / "traffic.txt").write_text("face_flux fp32c 1e9 %s\n" % cur)
     assert bench.read_traffic("face_flux", "fp32c") == 1e9
+    assert bench.read_traffic("face_flux", "fp64") is None
+
+
+def test_measured_flops_only_for_the_current_sources(tmp_path, monkeypatch):
+    import bench
+    hashes = {g: bench.source_hash(g) for g in bench.SECTIONS}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "flops.txt").write_text(
+        "# comment\n"
+        "face_eq fp32c - 470.0 %s\n"
+        "face_flux fp32c 1 1200.0 %s\n"
+        "face_flux fp32c 2 1100.0 %s\n"
+        "flux_update fp32c 1 1300.0 0123456789abcdef\n" % (hashes["face_eq"], hashes["face_flux"],
+                                                            hashes["face_flux"]))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda group="face_flux": hashes[group])
+    fl, src = bench.read_flops("fp32c")
+    assert fl["face_eq"] == 470.0 and fl["face_flux_stage1"] == 1200.0 and fl["face_flux_stage2"] == 1100.0
+    assert src["face_eq"].startswith("measured") and src["face_flux"].startswith("measured")
+    # a stale line falls back to the hand estimate
+    assert fl["flux_update_stage1"] == bench.FLOPS_ESTIMATE["flux_update_stage1"]
+    assert src["flux_update"] == "hand estimate"
+    fl64, src64 = bench.read_flops("fp64")
+    assert all(v == "hand estimate" for v in src64.values())
 
 
 class _FakeGrid:

@@ -816,14 +816,33 @@ __global__ void __launch_bounds__(256) ghost_rev_kernel(GhostRevArgs A)
         A.uinf_part[(long)(b - A.lo2) * A.len1 + (a - A.lo1)] = gu;
 }
 
-__global__ void __launch_bounds__(1024) reduce_add_kernel(const double *x, long n, double *acc)
+// Fixed-order two-pass sum of x[0..n) added to *acc: block b of kRedBlocks
+// sums its contiguous chunk (thread-strided, then a shared-memory tree) into
+// part[b]; one block then sums the parts the same way.
+constexpr int kRedBlocks = 256;
+
+__global__ void __launch_bounds__(256) reduce_part_kernel(const double *x, long n, double *part)
 {
-    __shared__ double sh[1024];
+    __shared__ double sh[256];
+    const long chunk = (n + kRedBlocks - 1) / kRedBlocks, i0 = blockIdx.x * chunk;
+    const long i1 = i0 + chunk < n ? i0 + chunk : n;
     double s = 0.0;
-    for (long i = threadIdx.x; i < n; i += 1024) s += x[i];
+    for (long i = i0 + threadIdx.x; i < i1; i += 256) s += x[i];
     sh[threadIdx.x] = s;
     __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(256) reduce_final_kernel(const double *part, double *acc)
+{
+    __shared__ double sh[256];
+    sh[threadIdx.x] = part[threadIdx.x];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
@@ -1247,7 +1266,9 @@ void ghost_adjoint(const Ctx &c, const AdjWork &w, const double *Aw)
                 ghost_rev_kernel<<<dim3((A.len1 + 31) / 32, (A.len2 + 7) / 8, 1), dim3(32, 8), 0, c.stream>>>(A);
             }
     }
-    reduce_add_kernel<<<1, 1024, 0, c.stream>>>(w.uinf_part, w.nuinf, w.scal);
+    static_assert(kRedBlocks == 256, "one part per thread of the final pass");
+    reduce_part_kernel<<<kRedBlocks, 256, 0, c.stream>>>(w.uinf_part, w.nuinf, w.red);
+    reduce_final_kernel<<<1, 256, 0, c.stream>>>(w.red, w.scal);
 }
 
 __global__ void __launch_bounds__(256) add_interior_kernel(double *dst, const double *src, long np, int nx, int ny,
@@ -1346,6 +1367,7 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
     w->Asplit = k.take(4 * c.np);   // 8 np floats: hi, lo
     w->nuinf = 3 * 2 * G * maxsurf;
     w->uinf_part = k.take(w->nuinf);
+    w->red = k.take(kRedBlocks);
     const long np = npts_total > 0 ? npts_total : 1;
     w->pts = k.take(8 * np);
     w->ptc = k.take(32 * np);

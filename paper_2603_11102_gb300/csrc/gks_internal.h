@@ -159,6 +159,7 @@ struct AdjWork {
     long nR;                                              // component stride of lamR
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;
+    double *red;                                          // partial sums of uinf_part (kRedBlocks)
     double *pts;                                          // per actuator point scratch (8 per point)
     double *ptc, *ptl;                                    // sampling-adjoint corner values (32) and cells (8, as long)
     double *scal;                                         // [0] grad U_inf (device accumulator)

@@ -130,9 +130,11 @@ def test_inflow_on_the_high_side_and_across_axes(gks, precision):
     front (rho up to 1.18 at Mach 0.1) runs in from the high x face; near it
     the WENO weights switch and the oracle itself turns a relative input
     perturbation u into ~1e3 u after 20 steps (and ~10 u after 8). The fixed
-    bar holds at 8 steps; at 20 steps the error is held to 4x the oracle's own
-    response to a perturbation of the working precision's unit roundoff
-    (measured ratio ~1.3 in FP32C), and the fixed bar where that is larger."""
+    bar holds at 8 steps; at 20 steps the error is held to 8x the oracle's own
+    response to a perturbation of the working precision's unit roundoff (the
+    kernels round at every step, not only the input; measured ratios 2.1 in
+    FP64, 1.3 in FP32C, 3.7 in double-single), and the fixed bar where that is
+    larger."""
     n = (29, 19, 9)
     faces = [np.linspace(0, 2.5, n[0] + 1), np.linspace(0, 1.5, n[1] + 1), np.linspace(0, 0.8, n[2] + 1)]
     bc = [(4, 3), (3, 1), (0, 0)]
@@ -145,7 +147,7 @@ def test_inflow_on_the_high_side_and_across_axes(gks, precision):
     g, o, _ = run_pair(gks, w, precision, 20)
     a, b = g.get_state(), o.get_state()
     err = rel_linf(a, b)
-    bound = max(TOL[precision], 4.0 * oracle_response(w, 20, UNIT_ROUNDOFF[precision]))
+    bound = max(TOL[precision], 8.0 * oracle_response(w, 20, UNIT_ROUNDOFF[precision]))
     report("test_inflow_on_the_high_side_and_across_axes:conditioning", precision, 20, bound=bound)
     assert err <= bound, (err, bound, rel_linf_components(a, b))
 

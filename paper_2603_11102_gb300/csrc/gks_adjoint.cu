@@ -58,6 +58,18 @@ __device__ __constant__ double cWD[2][5] = {
     {1.0 / 12.0 - kS3 / 54.0, -2.0 / 3.0 + 13.0 * kS3 / 54.0, -4.0 * kS3 / 9.0, 2.0 / 3.0 + 13.0 * kS3 / 54.0,
      -1.0 / 12.0 - kS3 / 54.0}};
 
+// The same weights in FP32 for the FP32C reverse (no conversion at each use).
+__device__ __constant__ float cWV32[2][5] = {
+    {(float)(-1.0 / 4320.0 - 7.0 * kS3 / 432.0), (float)(1.0 / 1080.0 + 25.0 * kS3 / 216.0), (float)(719.0 / 720.0),
+     (float)(1.0 / 1080.0 - 25.0 * kS3 / 216.0), (float)(-1.0 / 4320.0 + 7.0 * kS3 / 432.0)},
+    {(float)(-1.0 / 4320.0 + 7.0 * kS3 / 432.0), (float)(1.0 / 1080.0 - 25.0 * kS3 / 216.0), (float)(719.0 / 720.0),
+     (float)(1.0 / 1080.0 + 25.0 * kS3 / 216.0), (float)(-1.0 / 4320.0 - 7.0 * kS3 / 432.0)}};
+__device__ __constant__ float cWD32[2][5] = {
+    {(float)(1.0 / 12.0 + kS3 / 54.0), (float)(-2.0 / 3.0 - 13.0 * kS3 / 54.0), (float)(4.0 * kS3 / 9.0),
+     (float)(2.0 / 3.0 - 13.0 * kS3 / 54.0), (float)(-1.0 / 12.0 + kS3 / 54.0)},
+    {(float)(1.0 / 12.0 - kS3 / 54.0), (float)(-2.0 / 3.0 + 13.0 * kS3 / 54.0), (float)(-4.0 * kS3 / 9.0),
+     (float)(2.0 / 3.0 + 13.0 * kS3 / 54.0), (float)(-1.0 / 12.0 - kS3 / 54.0)}};
+
 __device__ __forceinline__ long lin(const int P0, const int P1, int i, int j, int k)
 {
     return (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
@@ -624,6 +636,7 @@ __device__ __forceinline__ void pair_rev32(const float hi[5], const float lo[5],
 // RD in FP32 (the FP32 reverse): the same march as rev_face_state_kernel on
 // the working array split into hi + lo floats, with FP32 face-box adjoints in
 // and FP32 cell slots out.
+template <bool LO>
 __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
 {
     const float *lamFQ = (const float *)A.lamFQ;
@@ -652,7 +665,7 @@ __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
             const int cell = f0 - 4 + k;
             const long l = comp[v] * A.np + base + (long)cell * sd;
             wh[v][k] = cell >= -G ? A.Ahi[l] : 0.0f;
-            wl[v][k] = cell >= -G ? A.Alo[l] : 0.0f;
+            wl[v][k] = (LO && cell >= -G) ? A.Alo[l] : 0.0f;
         }
     float Rprev[4], Sprev[4];
     {
@@ -683,7 +696,7 @@ __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
             }
             const long l = comp[v] * A.np + base + (long)(f + 2) * sd;
             wh[v][5] = A.Ahi[l];
-            wl[v][5] = A.Alo[l];
+            wl[v][5] = LO ? A.Alo[l] : 0.0f;
         }
         float Ql[4], Qr[4], Rt[4];
 #pragma unroll
@@ -752,6 +765,215 @@ __global__ void __launch_bounds__(256) rev_gather_cells_kernel(RevArgs A)
     const long l = lin(A.P[0], A.P[1], cc[0], cc[1], cc[2]);
     if (!in_bounds(l, A.np)) return;
     for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + l] += (double)acc[v];
+}
+
+// ------------------------------------------------ fused FP32C reverse (RA-RC)
+
+// FP32C grids: RA, RB and RC of one direction in one pass over the 32 x 8
+// face tiles of the forward, with the Gauss-point inputs and adjoints kept in
+// shared memory. Per tile: the face box of the forward (recomputed from the
+// recorded FP32 working array by the forward's face-state kernel) arrives by
+// TMA and the forward's t1 pass fills the rows; each thread then takes one
+// face, redoes its t2 pass and reverses the flux at its 4 Gauss points (the
+// 64 input adjoints go to shared memory, over the dead face-box buffer);
+// the transposed t2 pass (each row adjoint gathers the faces that read the
+// row) and the transposed t1 pass (each face-box adjoint gathers the row
+// columns that read it) give the adjoints of the tile's face box with its
+// tangential halo, written as the tile's partial. Halos overlap the
+// neighbouring tiles: sum_partials32_kernel adds the partials of a face in a
+// fixed order.
+struct Rev32Args {
+    const double *lamL, *lamLt;       // padded cell adjoints; lamL null in stage 2
+    const float *ihd, *ih1, *ih2;     // inverse cell widths along d, t1, t2 (padded index)
+    float *part;                      // per tile: 8 x SQ_H x SQ_W face-box adjoints
+    int n1, n2, nf, nd, d, t1, t2, P0, P1;
+    long np;
+    Phys<float> ph;
+    Scalars *scal;
+};
+
+constexpr int kPartN = 8 * SQ_H * SQ_W;   // face-box adjoints of one tile
+constexpr int kGA = 64 * TX * TY;         // Gauss-point input adjoints of one tile
+
+constexpr size_t rev_tile32_smem_bytes() { return (size_t)(kGA + ST_N) * sizeof(float) + 2 * sizeof(uint64_t); }
+static_assert(SQ_N <= kGA, "the face-box tile lives in the Gauss-point adjoint buffer");
+
+__global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constant__ CUtensorMap tmap, Rev32Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ga = reinterpret_cast<float *>(smem_raw);   // [64][TY][TX]
+    float *sq = ga;                                     // face-box tile, dead after the t1 pass
+    float *st = ga + kGA;                               // t1-pass rows, then their adjoints
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
+    const int ntiles = NA * NB * A.nf;
+    const uint32_t bytes = (uint32_t)(SQ_N * sizeof(float));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    const bool needF0 = A.lamL != nullptr;
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int ta = t % NA, tb = (t / NA) % NB, f = t / (NA * NB);
+        if (tid == 0) {
+            fence_proxy_async();
+            tma_load_tile(&tmap, sq, &bar[0], ta * TX, tb * TY, f, bytes);
+        }
+        const bool ok = mbar_wait(&bar[0], (uint32_t)(k & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(&A.scal->flags, FLAG_TIMEOUT);
+            return;
+        }
+        tile_t1_pass(sq, st, tid);
+        __syncthreads();
+
+        // RA: per face, the 4 Gauss points
+        const int a = ta * TX + tx, b = tb * TY + ty;
+        if (a < A.n1 && b < A.n2) {
+            int cl[3], cr[3];
+            cl[A.d] = f - 1; cl[A.t1] = a; cl[A.t2] = b;
+            cr[A.d] = f; cr[A.t1] = a; cr[A.t2] = b;
+            const bool hasl = f >= 1, hasr = f < A.nd;
+            const long il = lin(A.P0, A.P1, cl[0], cl[1], cl[2]), ir = lin(A.P0, A.P1, cr[0], cr[1], cr[2]);
+            const bool okc = in_bounds(il, A.np) && in_bounds(ir, A.np);
+            const float ihl = hasl ? A.ihd[f - 1 + G] : 0.0f, ihr = hasr ? A.ihd[f + G] : 0.0f;
+            float sF0[4] = {0, 0, 0, 0}, sF1[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const long o = gc[v] * A.np;
+                const float ll = (hasl && okc) ? (float)A.lamLt[o + il] : 0.0f;
+                const float lr = (hasr && okc) ? (float)A.lamLt[o + ir] : 0.0f;
+                sF1[v] = 0.25f * (-ll * ihl + lr * ihr);
+                if (needF0) {
+                    const float ml = (hasl && okc) ? (float)A.lamL[o + il] : 0.0f;
+                    const float mr = (hasr && okc) ? (float)A.lamL[o + ir] : 0.0f;
+                    sF0[v] = 0.25f * (-ml * ihl + mr * ihr);
+                }
+            }
+            const float ih1 = A.ih1[a + G], ih2 = A.ih2[b + G];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                float Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+                    const float *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+                    const float *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+                    float vm, vp, dm, dp;
+                    tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
+                    Qv[0][v] = vm; Qv[1][v] = vp; D2[0][v] = dm; D2[1][v] = dp;
+                    tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+                    D1[0][v] = vm; D1[1][v] = vp;
+                    tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+                    Dn[0][v] = vm; Dn[1][v] = vp;
+                }
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    float qb[4], Dnb[4], D1b[4], D2b[4];
+                    gk_flux_rev<float>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, sF0, sF1, needF0, qb, Dnb,
+                                       D1b, D2b);
+                    float *gp = ga + (16 * (2 * m + nn)) * (TX * TY) + tid;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        gp[v * (TX * TY)] = qb[v];
+                        gp[(4 + v) * (TX * TY)] = Dnb[v];
+                        gp[(8 + v) * (TX * TY)] = D1b[v];
+                        gp[(12 + v) * (TX * TY)] = D2b[v];
+                    }
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < 64; ++j) ga[j * (TX * TY) + tid] = 0.0f;
+        }
+        __syncthreads();
+
+        // RB: row r of the t1 pass is read by the faces bb = r-4 .. r of the
+        // tile with stencil index r - bb; arrays as the forward writes them
+        for (int e = tid; e < 24 * ST_ROWS; e += TX * TY) {
+            const int arr = e / ST_ROWS, rem = e - arr * ST_ROWS, r = rem / TX, c = rem - r * TX;
+            int v, m, kind;   // kind 0: Q0 value rows, 1: t1-derivative rows, 2: normal-slope rows
+            if (arr < 16) {
+                v = arr >> 2;
+                m = arr & 1;
+                kind = (arr >> 1) & 1;
+            } else {
+                v = (arr - 16) >> 1;
+                m = (arr - 16) & 1;
+                kind = 2;
+            }
+            const int jq = kind == 0 ? v : (kind == 1 ? 8 + v : 4 + v);
+            float acc = 0.0f;
+            const int blo = r - 4 > 0 ? r - 4 : 0, bhi = r < TY - 1 ? r : TY - 1;
+            for (int bb = blo; bb <= bhi; ++bb) {
+                const int sx = r - bb;
+                const float *g0 = ga + bb * TX + c;
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    const int g16 = 16 * (2 * m + nn);
+                    acc += cWV32[nn][sx] * g0[(g16 + jq) * (TX * TY)];
+                    if (kind == 0) acc += cWD32[nn][sx] * g0[(g16 + 12 + v) * (TX * TY)];
+                }
+            }
+            st[e] = acc;
+        }
+        __syncthreads();
+
+        // RC: face-box column cc is read by the row columns c = cc-4 .. cc
+        float *out = A.part + (long)t * kPartN;
+        for (int e = tid; e < kPartN; e += TX * TY) {
+            const int j = e / (SQ_H * SQ_W), rem = e - j * (SQ_H * SQ_W), r = rem / SQ_W, cc = rem - r * SQ_W;
+            float acc = 0.0f;
+            const int clo = cc - 4 > 0 ? cc - 4 : 0, chi = cc < TX - 1 ? cc : TX - 1;
+            for (int c = clo; c <= chi; ++c) {
+                const int sx = cc - c;
+                const float *r0 = st + r * TX + c;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    if (j < 4)
+                        acc += cWV32[m][sx] * r0[(j * 4 + m) * ST_ROWS] + cWD32[m][sx] * r0[(j * 4 + 2 + m) * ST_ROWS];
+                    else
+                        acc += cWV32[m][sx] * r0[(16 + (j - 4) * 2 + m) * ST_ROWS];
+                }
+            }
+            out[e] = acc;
+        }
+        __syncthreads();   // the buffers are free for the next tile
+    }
+}
+
+// Face-box adjoints of direction d (the layout of the forward's face box)
+// from the tile partials: face (f, a', b') of the extended box lies in the
+// tangential halo of at most two tiles along each axis; their partials are
+// added in tile order.
+__global__ void __launch_bounds__(256) sum_partials32_kernel(const float *part, float *lamFQ, long nfq, int e1p,
+                                                             int n1, int n2)
+{
+    const int ap = (int)(blockIdx.x * TX + threadIdx.x) - 2, bp = (int)(blockIdx.y * TY + threadIdx.y) - 2;
+    const int f = blockIdx.z;
+    if (ap >= n1 + 2 || bp >= n2 + 2) return;
+    const int NA = (n1 + TX - 1) / TX, NB = (n2 + TY - 1) / TY;
+    const int ta1 = (ap + 2) / TX, tb1 = (bp + 2) / TY;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ta = ta1 - 1; ta <= ta1; ++ta) {
+        const int cc = ap + 2 - ta * TX;
+        if (ta < 0 || ta >= NA || cc < 0 || cc >= SQ_W) continue;
+        for (int tb = tb1 - 1; tb <= tb1; ++tb) {
+            const int r = bp + 2 - tb * TY;
+            if (tb < 0 || tb >= NB || r < 0 || r >= SQ_H) continue;
+            const float *p = part + (long)(ta + NA * (tb + NB * (long)f)) * kPartN + r * SQ_W + cc;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += p[j * (SQ_H * SQ_W)];
+        }
+    }
+    const long o = ((long)f * (n2 + 4) + (bp + 2)) * e1p + (ap + 2);
+    if (!in_bounds(o, nfq)) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) lamFQ[j * nfq + o] = acc[j];
 }
 
 // Ghost adjoint of one (axis, side, layer): the ghost's adjoint goes to its
@@ -1226,11 +1448,90 @@ void spatial_adjoint(const Ctx &c, const AdjWork &w, const double *Aw, void *con
         rev_t1_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, nf), blk, 0, c.stream>>>(R);
         const dim3 gfs((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch);
         if (f32)
-            rev_face_state32_kernel<<<gfs, blk, 0, c.stream>>>(R);
+            rev_face_state32_kernel<true><<<gfs, blk, 0, c.stream>>>(R);
         else
             rev_face_state_kernel<<<gfs, blk, 0, c.stream>>>(R);
         rev_gather_cells_kernel<T><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
                                      c.stream>>>(R);
+    }
+}
+
+// S^T of an FP32C grid through the fused reverse: per direction the forward
+// face boxes from the FP32 working array A32 (as the forward read it), RA-RC
+// in one pass over the tiles, the partials added per face, then RD on the
+// FP32 cells and RE. c32 is the grid's own context (FP32 widths, the density
+// offset, the face-box buffer and its TMA maps); cw the reverse's context.
+void spatial_adjoint_fused32(const Ctx &cw, const AdjWork &w, const float *A32, const double *lamL,
+                             const double *lamLt)
+{
+    const Ctx &c = *w.c32;
+    const Phys<float> ph = make_phys<float>(c);
+    const dim3 blk(TX, TY);
+    const size_t smem = rev_tile32_smem_bytes();
+    static int grid_blocks = 0;
+    if (!grid_blocks) {
+        int per = 0;
+        cudaFuncSetAttribute(rev_tile32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rev_tile32_kernel, TX * TY, smem);
+        grid_blocks = (per > 0 ? per : 1) * sm_count();
+    }
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = tan1(d), t2 = tan2(d);
+        launch_face_state32(c, d, A32);
+        Rev32Args Q;
+        Q.lamL = lamL;
+        Q.lamLt = lamLt;
+        Q.ihd = (const float *)c.ih[d];
+        Q.ih1 = (const float *)c.ih[t1];
+        Q.ih2 = (const float *)c.ih[t2];
+        Q.part = w.part;
+        Q.n1 = c.n[t1];
+        Q.n2 = c.n[t2];
+        Q.nf = c.n[d] + 1;
+        Q.nd = c.n[d];
+        Q.d = d;
+        Q.t1 = t1;
+        Q.t2 = t2;
+        Q.P0 = c.P[0];
+        Q.P1 = c.P[1];
+        Q.np = c.np;
+        Q.ph = ph;
+        Q.scal = w.sc;
+        const long ntiles = (long)((Q.n1 + TX - 1) / TX) * ((Q.n2 + TY - 1) / TY) * Q.nf;
+        const int grid = (int)(ntiles < grid_blocks ? ntiles : grid_blocks);
+        rev_tile32_kernel<<<grid, blk, smem, c.stream>>>(c.tmap[d], Q);
+        sum_partials32_kernel<<<dim3((Q.n1 + 4 + TX - 1) / TX, (Q.n2 + 4 + TY - 1) / TY, Q.nf), blk, 0, c.stream>>>(
+            w.part, (float *)w.lamFQ, c.nfq, c.e1p[d], Q.n1, Q.n2);
+        // RD on the FP32 cells (density as rho - off, the forward's offset) and RE
+        RevArgs R;
+        R.A = nullptr;
+        R.Ahi = A32;
+        R.Alo = nullptr;
+        R.nfq = c.nfq;
+        R.e1p = c.e1p[d];
+        R.lamL = lamL;
+        R.lamLt = lamLt;
+        R.lamFQ = w.lamFQ;
+        R.lamC = w.lamC;
+        R.lamA = w.lamA;
+        R.ihf = (const double *)cw.ihf[d];
+        for (int e = 0; e < 3; ++e) {
+            R.n[e] = c.n[e];
+            R.P[e] = c.P[e];
+        }
+        R.d = d;
+        R.t1 = t1;
+        R.t2 = t2;
+        R.nd = c.n[d];
+        R.n1 = c.n[t1];
+        R.n2 = c.n[t2];
+        R.np = c.np;
+        R.ph = make_phys<double>(c);
+        const int nf = c.n[d] + 1;
+        const dim3 gfs((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch);
+        rev_face_state32_kernel<false><<<gfs, blk, 0, c.stream>>>(R);
+        rev_gather_cells_kernel<float><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
+                                         c.stream>>>(R);
     }
 }
 
@@ -1333,6 +1634,15 @@ size_t adjoint_tape_carve(const Ctx &c, int gp_bytes, void *base, AdjWork *w)
     long nG = 0;
     for (int d = 0; d < 3; ++d) nG = std::max(nG, (long)(c.n[d] + 1) * c.n[tan1(d)] * c.n[tan2(d)]);
     w->nG = nG;
+    if (c.prec == GKS_FP32C) {
+        // the reverse recomputes the face boxes and Gauss-point inputs from
+        // the FP32 working arrays (the fused reverse): no Gauss-point tape
+        w->A0f = (float *)k.take(np4 / 2);
+        w->Wsf = (float *)k.take(np4 / 2);
+        for (int st = 0; st < 2; ++st)
+            for (int d = 0; d < 3; ++d) w->gps[st][d] = nullptr;
+        return k.o;
+    }
     for (int st = 0; st < 2; ++st)
         for (int d = 0; d < 3; ++d) {
             w->gps[st][d] = k.take(64 * nG * gp_bytes / 8);
@@ -1358,13 +1668,22 @@ size_t adjoint_scratch_carve(const Ctx &c, long npts_total, void *base, AdjWork 
         maxsurf = std::max(maxsurf, l1 * l2);
     }
     w->nR = nR;
-    w->lamR = k.take(24 * nR);
     w->lamFQ = k.take(8 * c.nfq);
     w->lamC = k.take(24 * c.nfq);
-    long nG = 0;
-    for (int d = 0; d < 3; ++d) nG = std::max(nG, (long)(c.n[d] + 1) * c.n[tan1(d)] * c.n[tan2(d)]);
-    w->lamGa = k.take(64 * nG);   // Gauss-point adjoints of one direction (double or float)
-    w->Asplit = k.take(4 * c.np);   // 8 np floats: hi, lo
+    if (c.prec == GKS_FP32C) {
+        // the fused reverse: tile partials instead of Gauss-point and row adjoints
+        long np = 0;
+        for (int d = 0; d < 3; ++d)
+            np = std::max(np, (long)((c.n[tan1(d)] + TX - 1) / TX) * ((c.n[tan2(d)] + TY - 1) / TY) * (c.n[d] + 1));
+        w->part = (float *)k.take((np * kPartN + 1) / 2);
+        w->lamR = w->lamGa = w->Asplit = nullptr;
+    } else {
+        w->lamR = k.take(24 * nR);
+        long nG = 0;
+        for (int d = 0; d < 3; ++d) nG = std::max(nG, (long)(c.n[d] + 1) * c.n[tan1(d)] * c.n[tan2(d)]);
+        w->lamGa = k.take(64 * nG);     // Gauss-point adjoints of one direction (double or float)
+        w->Asplit = k.take(4 * c.np);   // 8 np floats: hi, lo
+    }
     w->nuinf = 3 * 2 * G * maxsurf;
     w->uinf_part = k.take(w->nuinf);
     w->red = k.take(kRedBlocks);
@@ -1439,13 +1758,19 @@ void adjoint_reverse(const Ctx &c, const AdjWork &w, const RotorDev *rot, const 
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(2, nullptr, w.lamP, nullptr, nullptr, w.lamLt, dt, c.np,
                                                    c.n[0], c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial(c, w, w.Ws, w.gps[1], nullptr, w.lamLt);
+    if (w.A0f)
+        spatial_adjoint_fused32(c, w, w.Wsf, nullptr, w.lamLt);
+    else
+        spatial(c, w, w.Ws, w.gps[1], nullptr, w.lamLt);
     ghost_adjoint(c, w, w.Ws);
     // stage 1: lamA (interior) is lambda of W*
     rev_update_kernel<<<gcell, blk, 0, c.stream>>>(1, w.lamA, w.lamP, w.lamW, w.lamL, w.lamLt, dt, c.np, c.n[0],
                                                    c.n[1], c.P[0], c.P[1]);
     cudaMemsetAsync(w.lamA, 0, bytes4, c.stream);
-    spatial(c, w, w.A0, w.gps[0], w.lamL, w.lamLt);
+    if (w.A0f)
+        spatial_adjoint_fused32(c, w, w.A0f, w.lamL, w.lamLt);
+    else
+        spatial(c, w, w.A0, w.gps[0], w.lamL, w.lamLt);
     ghost_adjoint(c, w, w.A0);
     add_interior_kernel<<<gcell, blk, 0, c.stream>>>(w.lamW, w.lamA, c.np, c.n[0], c.n[1], c.P[0], c.P[1]);
 }

@@ -686,16 +686,26 @@ int step_once(gks_grid *g, const AdjWork *tp)
             if (rc) return rc;
             cc.wk1 = tp->Ws;
         } else {
-            // FP32C: the FP32 input (rho - off) as FP64 with rho
+            // FP32C: the FP32 input (rho - off) as the reverse's stencil reads
+            // it, and as FP64 with rho for the rest of the reverse
+            rc = cuda_check(g, cudaMemcpyAsync(tp->A0f, c.wk0, sizeof(float) * 4 * c.np, cudaMemcpyDeviceToDevice,
+                                               c.stream), "record the FP32 W^n");
+            if (rc) return rc;
             launch_widen(c, (const float *)c.wk0, nullptr, tp->A0, 4 * c.np, c.np, c.off);
         }
-        use_tape_gauss(cc, *tp, 0);
+        if (c.prec == GKS_FP64) use_tape_gauss(cc, *tp, 0);
     }
     launch_stage(cc, 1);
     launch_ghost(cc, cc.wk1);
     if (tp) {
-        if (c.prec == GKS_FP32C) launch_widen(c, (const float *)c.wk1, nullptr, tp->Ws, 4 * c.np, c.np, c.off);
-        use_tape_gauss(cc, *tp, 1);
+        if (c.prec == GKS_FP32C) {
+            rc = cuda_check(g, cudaMemcpyAsync(tp->Wsf, c.wk1, sizeof(float) * 4 * c.np, cudaMemcpyDeviceToDevice,
+                                               c.stream), "record the FP32 W*");
+            if (rc) return rc;
+            launch_widen(c, (const float *)c.wk1, nullptr, tp->Ws, 4 * c.np, c.np, c.off);
+        } else {
+            use_tape_gauss(cc, *tp, 1);
+        }
     }
     // stage 2 also prepares the next step on every cell outside the forcing
     // boxes; the boxes are prepared again after the forcing
@@ -1222,6 +1232,7 @@ int gks_step_reverse(gks_grid *g, void *d_tape, void *d_scratch, const double *d
         if (m != kTapeMagicByte) return fail(g, GKS_ERR_STATE, "tape not recorded");
     if (hdr[3] != (double)w.gp_bytes)
         return fail(g, GKS_ERR_STATE, "tape recorded with another adjoint precision");
+    w.c32 = &g->c;
     std::vector<int> iters(g->bodies.size());
     for (size_t k = 0; k < iters.size(); ++k) {
         iters[k] = (int)hdr[4 + k];

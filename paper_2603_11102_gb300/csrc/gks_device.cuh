@@ -374,6 +374,83 @@ constexpr int SQ_N = 8 * SQ_H * SQ_W;
 constexpr int ST_ROWS = SQ_H * TX;          // rows of the t1 pass
 constexpr int ST_N = 24 * ST_ROWS;
 
+// 8 consecutive values of a shared-memory row from a 16-byte aligned address,
+// and 4 consecutive values to one.
+__device__ __forceinline__ void lds8(const float *p, float q[8])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+    q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double *p, double q[8])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[i];
+        q[2 * i] = a.x;
+        q[2 * i + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void sts4(float *p, const float q[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(q[0], q[1], q[2], q[3]);
+}
+__device__ __forceinline__ void sts4(double *p, const double q[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(q[0], q[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(q[2], q[3]);
+}
+__device__ __forceinline__ void lds8(const dsf *p, dsf q[8])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[i];
+        q[2 * i] = dsf(a.x, a.y);
+        q[2 * i + 1] = dsf(a.z, a.w);
+    }
+}
+__device__ __forceinline__ void sts4(dsf *p, const dsf q[4])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(q[0].hi, q[0].lo, q[1].hi, q[1].lo);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(q[2].hi, q[2].lo, q[3].hi, q[3].lo);
+}
+
+static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assumes 32 x 8 tiles");
+
+// t1 pass of one tile: values and t1-derivatives of Q0, values of the normal
+// slope, at the two t1 Gauss points, for every row of the tile. 768 equal
+// tasks (Q0 or slope, component, row, group of 4 columns): a task reads 8
+// consecutive values of its row and writes 4 columns; the lanes of a warp
+// share the kind and the component.
+template <typename R, typename C>
+__device__ __forceinline__ void tile_t1_pass(const R *sq, C *st, int tid)
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int task = tid + j * 256;
+        const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
+        const int r = rc >> 3, cg = rc & 7;
+        C q[8];
+        lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
+        C *o = st + r * TX + 4 * cg;
+        if (kind == 0) {
+            C vm[4], vp[4], dm[4], dp[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
+            sts4(o + (v * 4 + 0) * ST_ROWS, vm);
+            sts4(o + (v * 4 + 1) * ST_ROWS, vp);
+            sts4(o + (v * 4 + 2) * ST_ROWS, dm);
+            sts4(o + (v * 4 + 3) * ST_ROWS, dp);
+        } else {
+            C vm[4], vp[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
+            sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
+            sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
+        }
+    }
+}
+
 template <typename R>
 constexpr size_t flux_smem_bytes()
 {

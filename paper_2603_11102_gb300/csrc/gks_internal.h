@@ -113,6 +113,7 @@ void launch_advance(const Ctx &c);                      // t += dt
 void launch_scatter_state(const Ctx &c, const double *d_src);  // compact FP64 -> state
 void launch_scatter_state_prep(const Ctx &c, const double *d_src);   // + the prep of the new state
 void launch_gather_state(const Ctx &c, double *d_dst);         // state -> compact FP64
+void launch_face_state32(const Ctx &c, int d, const float *w);
 void launch_diagnostics(const Ctx &c, double *d_out5);
 void launch_fill_rest(const Ctx &c);                            // rho = 1, momentum 0
 void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored arrays <-> compact
@@ -148,6 +149,9 @@ struct AdjWork {
     double *hdr;                                          // [0] magic, [1] t_n, [2] dt, [3] gp_bytes,
                                                           // [4 + k] IBM iterations of body k
     double *A0, *Ws, *Wp;                                 // ghost-filled W^n, ghost-filled W*, state before the forcing
+    float *A0f = nullptr, *Wsf = nullptr;                 // FP32C: the FP32 working arrays of both stages as the
+                                                          // forward read them (rho - off, ghost-filled)
+    const Ctx *c32 = nullptr;                             // FP32C: the grid's own context (FP32 widths, offset)
     void *gps[2][3];                                      // Gauss-point inputs of the forward (64 nG each)
     int gp_bytes;                                         // their storage: 8 (FP64 reverse) or 4 (FP32 reverse)
     long nG;                                              // component stride of gps
@@ -160,6 +164,7 @@ struct AdjWork {
     double *uinf_part;                                    // per inflow ghost contribution
     long nuinf;
     double *red;                                          // partial sums of uinf_part (kRedBlocks)
+    float *part = nullptr;                                // FP32C: per-tile face-box adjoints of one direction
     double *pts;                                          // per actuator point scratch (8 per point)
     double *ptc, *ptl;                                    // sampling-adjoint corner values (32) and cells (8, as long)
     double *scal;                                         // [0] grad U_inf (device accumulator)

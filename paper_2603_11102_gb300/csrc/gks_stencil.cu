@@ -265,47 +265,6 @@ __device__ __forceinline__ M quarter(C acc) { return cvt<M>(acc) * M(0.25); }
 template <>
 __device__ __forceinline__ dsf quarter<dsf, dsf>(dsf acc) { return scale_pow2(acc, 0.25f); }
 
-// 8 consecutive values of a shared-memory row from a 16-byte aligned address,
-// and 4 consecutive values to one.
-__device__ __forceinline__ void lds8(const float *p, float q[8])
-{
-    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
-    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
-    q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
-}
-__device__ __forceinline__ void lds8(const double *p, double q[8])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const double2 a = reinterpret_cast<const double2 *>(p)[i];
-        q[2 * i] = a.x;
-        q[2 * i + 1] = a.y;
-    }
-}
-__device__ __forceinline__ void sts4(float *p, const float q[4])
-{
-    *reinterpret_cast<float4 *>(p) = make_float4(q[0], q[1], q[2], q[3]);
-}
-__device__ __forceinline__ void sts4(double *p, const double q[4])
-{
-    reinterpret_cast<double2 *>(p)[0] = make_double2(q[0], q[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(q[2], q[3]);
-}
-__device__ __forceinline__ void lds8(const dsf *p, dsf q[8])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 a = reinterpret_cast<const float4 *>(p)[i];
-        q[2 * i] = dsf(a.x, a.y);
-        q[2 * i + 1] = dsf(a.z, a.w);
-    }
-}
-__device__ __forceinline__ void sts4(dsf *p, const dsf q[4])
-{
-    reinterpret_cast<float4 *>(p)[0] = make_float4(q[0].hi, q[0].lo, q[1].hi, q[1].lo);
-    reinterpret_cast<float4 *>(p)[1] = make_float4(q[2].hi, q[2].lo, q[3].hi, q[3].lo);
-}
-
 // Tile t of the face box as (t1 tile, t2 tile, face): t = ta + NA (tb + NB f).
 struct TileIdx {
     int ta, tb, f;
@@ -320,42 +279,6 @@ __device__ __forceinline__ TileIdx tile_add(TileIdx t, const TileIdx &g, int NA,
     if (t.ta >= NA) { t.ta -= NA; t.tb += 1; }
     if (t.tb >= NB) { t.tb -= NB; t.f += 1; }
     return t;
-}
-
-static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assumes 32 x 8 tiles");
-
-// t1 pass of one tile: values and t1-derivatives of Q0, values of the normal
-// slope, at the two t1 Gauss points, for every row of the tile. 768 equal
-// tasks (Q0 or slope, component, row, group of 4 columns): a task reads 8
-// consecutive values of its row and writes 4 columns; the lanes of a warp
-// share the kind and the component.
-template <typename R, typename C>
-__device__ __forceinline__ void tile_t1_pass(const R *sq, C *st, int tid)
-{
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int task = tid + j * 256;
-        const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
-        const int r = rc >> 3, cg = rc & 7;
-        C q[8];
-        lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
-        C *o = st + r * TX + 4 * cg;
-        if (kind == 0) {
-            C vm[4], vp[4], dm[4], dp[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
-            sts4(o + (v * 4 + 0) * ST_ROWS, vm);
-            sts4(o + (v * 4 + 1) * ST_ROWS, vp);
-            sts4(o + (v * 4 + 2) * ST_ROWS, dm);
-            sts4(o + (v * 4 + 3) * ST_ROWS, dp);
-        } else {
-            C vm[4], vp[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
-            sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
-            sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
-        }
-    }
 }
 
 // t2 pass at each t1 Gauss point m, then the flux at (m, -g), (m, +g): the
@@ -917,34 +840,43 @@ int z_segment(int ncol, int nf, int G)
     return bestL;
 }
 
+// Arguments of the face-state kernel of direction d on working array w.
+template <typename R, typename C>
+FaceEqArgs<R, C> face_eq_args(const Ctx &c, int d, const R *w, const Phys<C> &ph)
+{
+    const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
+    const int t1 = tan1(d), t2 = tan2(d);
+    FaceEqArgs<R, C> E;
+    E.w = w;
+    E.np = c.np;
+    E.fq = (Mid<R, C> *)c.fq;
+    E.nfq = c.nfq;
+    E.ihf = (const R *)c.ihf[d];
+    E.n1 = c.n[t1];
+    E.n2 = c.n[t2];
+    E.e1p = c.e1p[d];
+    E.sd = stride[d];
+    E.s1 = stride[t1];
+    E.s2 = stride[t2];
+    E.cn = 1 + d;
+    E.c1 = 1 + t1;
+    E.c2 = 1 + t2;
+    E.ph = ph;
+    E.nf = c.n[d] + 1;
+    E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf);
+    return E;
+}
+
 template <typename R, typename C, int STAGE>
 void stage_impl(const Ctx &c)
 {
     const Phys<C> ph = make_phys<C>(c);
     const R *w = (const R *)(STAGE == 1 ? c.wk0 : c.wk1);
-    const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
     const FluxGrids<R, C, STAGE> &grids = flux_grids<R, C, STAGE>();
     const dim3 blk(TX, TY);
     for (int d = 0; d < 3; ++d) {
         const int t1 = tan1(d), t2 = tan2(d);
-        FaceEqArgs<R, C> E;
-        E.w = w;
-        E.np = c.np;
-        E.fq = (Mid<R, C> *)c.fq;
-        E.nfq = c.nfq;
-        E.ihf = (const R *)c.ihf[d];
-        E.n1 = c.n[t1];
-        E.n2 = c.n[t2];
-        E.e1p = c.e1p[d];
-        E.sd = stride[d];
-        E.s1 = stride[t1];
-        E.s2 = stride[t2];
-        E.cn = 1 + d;
-        E.c1 = 1 + t1;
-        E.c2 = 1 + t2;
-        E.ph = ph;
-        E.nf = c.n[d] + 1;
-        E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf);
+        const FaceEqArgs<R, C> E = face_eq_args<R, C>(c, d, w, ph);
         const CUtensorMap &tmap = c.tmap[d];
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
         mark(c, K_FACE_EQ, 1);
@@ -1288,6 +1220,15 @@ void launch_ghost(const Ctx &c, void *w)
         ghost_impl<double>(c, (double *)w);
     else
         ghost_impl<float>(c, (float *)w);
+}
+
+// FP32C: the forward face state of direction d from the FP32 working array
+// w into the face box c.fq (the reverse recomputes it instead of storing it).
+void launch_face_state32(const Ctx &c, int d, const float *w)
+{
+    const FaceEqArgs<float, float> E = face_eq_args<float, float>(c, d, w, make_phys<float>(c));
+    const dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
+    face_eq_march_kernel<float, float><<<ge, dim3(TX, TY), 0, c.stream>>>(E);
 }
 
 void launch_stage(const Ctx &c, int stage)

@@ -786,8 +786,8 @@ struct Rev32Args {
     const double *lamL, *lamLt;       // padded cell adjoints; lamL null in stage 2
     const float *ihd, *ih1, *ih2;     // inverse cell widths along d, t1, t2 (padded index)
     float *part;                      // per tile: 8 x SQ_H x SQ_W face-box adjoints
-    int n1, n2, nf, nd, d, t1, t2, P0, P1;
-    long np;
+    int n1, n2, nf, nd, d, t1, t2;
+    long np, sd, s1, s2, base;        // padded strides along d, t1, t2; index of cell (0, 0, 0)
     Phys<float> ph;
     Scalars *scal;
 };
@@ -834,11 +834,8 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         // RA: per face, the 4 Gauss points
         const int a = ta * TX + tx, b = tb * TY + ty;
         if (a < A.n1 && b < A.n2) {
-            int cl[3], cr[3];
-            cl[A.d] = f - 1; cl[A.t1] = a; cl[A.t2] = b;
-            cr[A.d] = f; cr[A.t1] = a; cr[A.t2] = b;
             const bool hasl = f >= 1, hasr = f < A.nd;
-            const long il = lin(A.P0, A.P1, cl[0], cl[1], cl[2]), ir = lin(A.P0, A.P1, cr[0], cr[1], cr[2]);
+            const long ir = A.base + (long)f * A.sd + (long)a * A.s1 + (long)b * A.s2, il = ir - A.sd;
             const bool okc = in_bounds(il, A.np) && in_bounds(ir, A.np);
             const float ihl = hasl ? A.ihd[f - 1 + G] : 0.0f, ihr = hasr ? A.ihd[f + G] : 0.0f;
             float sF0[4] = {0, 0, 0, 0}, sF1[4] = {0, 0, 0, 0};
@@ -892,8 +889,9 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         }
         __syncthreads();
 
-        // RB: row r of the t1 pass is read by the faces bb = r-4 .. r of the
-        // tile with stencil index r - bb; arrays as the forward writes them
+        // RB: row r of the t1 pass is read by the faces bb = r - sx of the tile
+        // with stencil index sx (unrolled, so that the weights are constant
+        // operands); a warp takes one array and row, its lanes the columns
         for (int e = tid; e < 24 * ST_ROWS; e += TX * TY) {
             const int arr = e / ST_ROWS, rem = e - arr * ST_ROWS, r = rem / TX, c = rem - r * TX;
             int v, m, kind;   // kind 0: Q0 value rows, 1: t1-derivative rows, 2: normal-slope rows
@@ -908,9 +906,10 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
             }
             const int jq = kind == 0 ? v : (kind == 1 ? 8 + v : 4 + v);
             float acc = 0.0f;
-            const int blo = r - 4 > 0 ? r - 4 : 0, bhi = r < TY - 1 ? r : TY - 1;
-            for (int bb = blo; bb <= bhi; ++bb) {
-                const int sx = r - bb;
+#pragma unroll
+            for (int sx = 0; sx < 5; ++sx) {
+                const int bb = r - sx;
+                if (bb < 0 || bb >= TY) continue;
                 const float *g0 = ga + bb * TX + c;
 #pragma unroll
                 for (int nn = 0; nn < 2; ++nn) {
@@ -923,24 +922,30 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         }
         __syncthreads();
 
-        // RC: face-box column cc is read by the row columns c = cc-4 .. cc
+        // RC: face-box column cc is read by the row columns c = cc - sx; a
+        // warp takes one (component, row), its lanes the columns (36: a
+        // second pass of 4 lanes)
         float *out = A.part + (long)t * kPartN;
-        for (int e = tid; e < kPartN; e += TX * TY) {
-            const int j = e / (SQ_H * SQ_W), rem = e - j * (SQ_H * SQ_W), r = rem / SQ_W, cc = rem - r * SQ_W;
-            float acc = 0.0f;
-            const int clo = cc - 4 > 0 ? cc - 4 : 0, chi = cc < TX - 1 ? cc : TX - 1;
-            for (int c = clo; c <= chi; ++c) {
-                const int sx = cc - c;
-                const float *r0 = st + r * TX + c;
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int pr = warp; pr < 8 * SQ_H; pr += (TX * TY) / 32) {
+            const int j = pr / SQ_H, r = pr - j * SQ_H;
+            for (int cc = lane; cc < SQ_W; cc += 32) {
+                float acc = 0.0f;
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    if (j < 4)
-                        acc += cWV32[m][sx] * r0[(j * 4 + m) * ST_ROWS] + cWD32[m][sx] * r0[(j * 4 + 2 + m) * ST_ROWS];
-                    else
-                        acc += cWV32[m][sx] * r0[(16 + (j - 4) * 2 + m) * ST_ROWS];
+                for (int sx = 0; sx < 5; ++sx) {
+                    const int c = cc - sx;
+                    if (c < 0 || c >= TX) continue;
+                    const float *r0 = st + r * TX + c;
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        if (j < 4)
+                            acc += cWV32[m][sx] * r0[(j * 4 + m) * ST_ROWS] + cWD32[m][sx] * r0[(j * 4 + 2 + m) * ST_ROWS];
+                        else
+                            acc += cWV32[m][sx] * r0[(16 + (j - 4) * 2 + m) * ST_ROWS];
+                    }
                 }
+                out[(j * SQ_H + r) * SQ_W + cc] = acc;
             }
-            out[e] = acc;
         }
         __syncthreads();   // the buffers are free for the next tile
     }
@@ -1492,8 +1497,11 @@ void spatial_adjoint_fused32(const Ctx &cw, const AdjWork &w, const float *A32, 
         Q.d = d;
         Q.t1 = t1;
         Q.t2 = t2;
-        Q.P0 = c.P[0];
-        Q.P1 = c.P[1];
+        const long stride[3] = {1, (long)c.P[0], (long)c.P[0] * c.P[1]};
+        Q.sd = stride[d];
+        Q.s1 = stride[t1];
+        Q.s2 = stride[t2];
+        Q.base = G * (stride[0] + stride[1] + stride[2]);
         Q.np = c.np;
         Q.ph = ph;
         Q.scal = w.sc;

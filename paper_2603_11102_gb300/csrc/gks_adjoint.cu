@@ -731,6 +731,130 @@ __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
     }
 }
 
+// RD and RE of an FP32C grid in one march: a thread owns the cells
+// [c0, c0 + kRevCells) of one line along d (ghost cells included) and walks
+// the faces c0 - 2 .. c0 + kRevCells + 2 that read them, with the 6 cells of
+// the current face's stencil in registers (FP32 cells as the forward read
+// them, density as rho - off) and their adjoints in a rolling window; a cell
+// leaves the window after its last face (f = c + 3) and its adjoint, summed
+// over its faces in face order as RE sums them, is added to lamA. Each cell
+// is written by one thread. The face reverse is rev_face_state32_kernel's.
+constexpr int kRevCells = 24;
+
+__global__ void __launch_bounds__(256) rev_face_cells32_kernel(RevArgs A)
+{
+    const float *lamFQ = (const float *)A.lamFQ;
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int nf = A.nd + 1;
+    const int c0 = (int)blockIdx.z * kRevCells - G, c1 = min(c0 + kRevCells, A.nd + G);
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || c0 >= A.nd + G) return;
+    const int fs = max(0, c0 - 2), fe = min(nf - 1, c1 + 2);   // faces [fs, fe]
+    if (fs > fe) return;
+    // padded strides by axis (selects, not an indexed local array)
+    auto str = [&](int ax) -> long { return ax == 0 ? 1L : (ax == 1 ? (long)A.P[0] : (long)A.P[0] * A.P[1]); };
+    const long sd = str(A.d);
+    const long base = G * (1L + A.P[0] + (long)A.P[0] * A.P[1]) + (long)a * str(A.t1) + (long)b * str(A.t2);
+    // cells fs-4 .. fe+2 are read, faces fs-1 .. fe read
+    if (!in_bounds(base + (long)(fs - 4 < -G ? -G : fs - 4) * sd, A.np) || !in_bounds(base + (long)(fe + 2) * sd, A.np) ||
+        !in_bounds(((long)(fs > 0 ? fs - 1 : 0) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)fe * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
+    const int comp[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
+    const Phys<float> ph = phys_as<float>(A.ph);
+    const float zl[5] = {0, 0, 0, 0, 0};
+    float wh[4][6];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int cell = fs - 4 + k;
+            wh[v][k] = cell >= -G ? A.Ahi[comp[v] * A.np + base + (long)cell * sd] : 0.0f;
+        }
+    float Rprev[4], Sprev[4];
+    {
+        float lft[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) pair_values32(&wh[v][1], zl, Rprev[v], lft[v]);   // cell fs-1
+        if (fs == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Sprev[v] = 0.0f;
+        } else {
+            float Rpp[4], dum;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pair_values32(&wh[v][0], zl, Rpp[v], dum);    // cell fs-2
+            const long o = ((long)(fs - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+            float Q0b[4], Qlb[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Q0b[v] = lamFQ[v * A.nfq + o];
+            equilibrium_rev<float>(ph, Rpp, lft, Q0b, Qlb, Sprev);
+        }
+    }
+    float acc[4][6];   // adjoints of the cells f-3 .. f+2 of the current face f
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[v][k] = 0.0f;
+    for (int f = fs; f <= fe; ++f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) wh[v][k] = wh[v][k + 1];
+            wh[v][5] = A.Ahi[comp[v] * A.np + base + (long)(f + 2) * sd];
+        }
+        float Ql[4], Qr[4], Rt[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Ql[v] = Rprev[v];
+            pair_values32(&wh[v][1], zl, Rt[v], Qr[v]);   // cell f
+        }
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+        float Q0b[4], DNb[4], Qlb[4], Qrb[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Q0b[v] = lamFQ[v * A.nfq + o];
+            DNb[v] = lamFQ[(4 + v) * A.nfq + o];
+        }
+        equilibrium_rev<float>(ph, Ql, Qr, Q0b, Qlb, Qrb);
+        const float s = (float)(A.ihf[f] * (1.0 / 12.0));
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float cb[6] = {0, 0, 0, 0, 0, 0};
+            const float ds = DNb[v] * s;
+            cb[1] += ds;
+            cb[2] -= 15.0f * ds;
+            cb[3] += 15.0f * ds;
+            cb[4] -= ds;
+            pair_rev32(&wh[v][0], zl, Qlb[v], Sprev[v], &cb[0]);      // cell f-1
+            if (f == nf - 1) pair_rev32(&wh[v][1], zl, 0.0f, Qrb[v], &cb[1]);   // cell f, left value only
+#pragma unroll
+            for (int m = 0; m < 6; ++m) acc[v][m] += cb[m];
+            Rprev[v] = Rt[v];
+            Sprev[v] = Qrb[v];
+        }
+        // cell f-3 has had its last face: add it if this thread owns it
+        const int cl = f - 3;
+        if (cl >= c0 && cl < c1) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + base + (long)cl * sd] += (double)acc[v][0];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[v][k] = acc[v][k + 1];
+            acc[v][5] = 0.0f;
+        }
+    }
+    // cells fe-2 .. fe+2 are still in the window (their faces beyond fe do not exist)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int cl = fe - 2 + k;
+        if (cl >= c0 && cl < c1) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) A.lamA[comp[v] * A.np + base + (long)cl * sd] += (double)acc[v][k];
+        }
+    }
+}
+
 // A (FP64) as hi + lo floats for the FP32 face-state reverse.
 __global__ void __launch_bounds__(256) split_kernel(const double *A, float *hi, float *lo, long n)
 {
@@ -892,8 +1016,9 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         // RB: row r of the t1 pass is read by the faces bb = r - sx of the tile
         // with stencil index sx (unrolled, so that the weights are constant
         // operands); a warp takes one array and row, its lanes the columns
-        for (int e = tid; e < 24 * ST_ROWS; e += TX * TY) {
-            const int arr = e / ST_ROWS, rem = e - arr * ST_ROWS, r = rem / TX, c = rem - r * TX;
+        const int wrp = tid >> 5, c = tid & 31;
+        for (int pr = wrp; pr < 24 * SQ_H; pr += (TX * TY) / 32) {
+            const int arr = pr / SQ_H, r = pr - arr * SQ_H;
             int v, m, kind;   // kind 0: Q0 value rows, 1: t1-derivative rows, 2: normal-slope rows
             if (arr < 16) {
                 v = arr >> 2;
@@ -918,7 +1043,7 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                     if (kind == 0) acc += cWD32[nn][sx] * g0[(g16 + 12 + v) * (TX * TY)];
                 }
             }
-            st[e] = acc;
+            st[arr * ST_ROWS + r * TX + c] = acc;
         }
         __syncthreads();
 
@@ -926,16 +1051,15 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         // warp takes one (component, row), its lanes the columns (36: a
         // second pass of 4 lanes)
         float *out = A.part + (long)t * kPartN;
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int pr = warp; pr < 8 * SQ_H; pr += (TX * TY) / 32) {
+        for (int pr = wrp; pr < 8 * SQ_H; pr += (TX * TY) / 32) {
             const int j = pr / SQ_H, r = pr - j * SQ_H;
-            for (int cc = lane; cc < SQ_W; cc += 32) {
+            for (int cc = c; cc < SQ_W; cc += 32) {
                 float acc = 0.0f;
 #pragma unroll
                 for (int sx = 0; sx < 5; ++sx) {
-                    const int c = cc - sx;
-                    if (c < 0 || c >= TX) continue;
-                    const float *r0 = st + r * TX + c;
+                    const int cs = cc - sx;
+                    if (cs < 0 || cs >= TX) continue;
+                    const float *r0 = st + r * TX + cs;
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
                         if (j < 4)
@@ -1537,9 +1661,9 @@ void spatial_adjoint_fused32(const Ctx &cw, const AdjWork &w, const float *A32, 
         R.ph = make_phys<double>(c);
         const int nf = c.n[d] + 1;
         const dim3 gfs((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, (nf + kRevMarch - 1) / kRevMarch);
-        rev_face_state32_kernel<false><<<gfs, blk, 0, c.stream>>>(R);
-        rev_gather_cells_kernel<float><<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8, R.nd + 2 * G), blk, 0,
-                                         c.stream>>>(R);
+        (void)gfs;
+        rev_face_cells32_kernel<<<dim3((R.n1 + 4 + 31) / 32, (R.n2 + 4 + 7) / 8,
+                                       (R.nd + 2 * G + kRevCells - 1) / kRevCells), blk, 0, c.stream>>>(R);
     }
 }
 

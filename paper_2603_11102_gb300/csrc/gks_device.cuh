@@ -454,7 +454,7 @@ __device__ __forceinline__ void tile_t1_pass(const R *sq, C *st, int tid)
 template <typename R>
 constexpr size_t flux_smem_bytes()
 {
-    return (size_t)(2 * SQ_N + ST_N) * sizeof(R) + 2 * sizeof(unsigned long long);
+    return (size_t)(SQ_N + ST_N) * sizeof(R) + 2 * sizeof(unsigned long long);
 }
 
 

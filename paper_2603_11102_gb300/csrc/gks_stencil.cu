@@ -356,16 +356,17 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
 }
 
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
-// box of the next tile is fetched by TMA into the other buffer while the
-// current one is computed.
+// box of a tile is dead once its t1 pass is in shared memory, so the next
+// tile's face box is fetched by TMA into the same buffer while the Gauss
+// points of the current one are computed (one buffer: more blocks per SM).
 template <typename R, typename C, bool NEED_F0, bool GP>
 __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A)
 {
     static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
     using M = Mid<R, C>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    M *sqb = reinterpret_cast<M *>(smem_raw);            // 2 buffers of SQ_N
-    C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
+    M *sq = reinterpret_cast<M *>(smem_raw);             // face-box tile (SQ_N)
+    C *st = reinterpret_cast<C *>(sq + SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
@@ -376,35 +377,30 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
     TileIdx cur = {(int)(blockIdx.x % NA), (int)((blockIdx.x / NA) % NB), (int)(blockIdx.x / (NA * NB))};
     if (tid == 0) {
         mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
     int t = blockIdx.x;
-    if (tid == 0 && t < ntiles) tma_load_tile(&tmap, sqb, &bar[0], cur.ta * TX, cur.tb * TY, cur.f, bytes);
+    if (tid == 0 && t < ntiles) tma_load_tile(&tmap, sq, &bar[0], cur.ta * TX, cur.tb * TY, cur.f, bytes);
     for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
-        const int buf = k & 1;
         const int tn = t + gridDim.x;
         const TileIdx nxt = tile_add(cur, g, NA, NB);
-        if (tid == 0 && tn < ntiles) {
-            fence_proxy_async();
-            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], nxt.ta * TX, nxt.tb * TY, nxt.f, bytes);
-        }
-        const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
+        const bool ok = mbar_wait(&bar[0], (uint32_t)(k & 1));
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(&A.scal->flags, FLAG_TIMEOUT);
-                if (tn < ntiles) mbar_wait(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
-            }
-            __syncthreads();
+            if (tid == 0) atomicOr(&A.scal->flags, FLAG_TIMEOUT);
             return;
         }
-        const M *sq = sqb + buf * SQ_N;
         const int a0 = cur.ta * TX, b0 = cur.tb * TY, f = cur.f;
         cur = nxt;
 
         tile_t1_pass(sq, st, tid);
         __syncthreads();
+        // the face box is free: fetch the next tile's while this one's Gauss
+        // points are computed
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            tma_load_tile(&tmap, sq, &bar[0], nxt.ta * TX, nxt.tb * TY, nxt.f, bytes);
+        }
 
         const int a = a0 + tx, b = b0 + ty;
         if (a < A.n1 && b < A.n2) {
@@ -600,8 +596,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     constexpr bool NEED_F0 = STAGE == 1;
     constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    M *sqb = reinterpret_cast<M *>(smem_raw);            // 2 buffers of SQ_N
-    C *st = reinterpret_cast<C *>(sqb + 2 * SQ_N);
+    M *sq = reinterpret_cast<M *>(smem_raw);             // face-box tile (SQ_N), refilled after its t1 pass
+    C *st = reinterpret_cast<C *>(sq + SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     M *sx = reinterpret_cast<M *>(bar + 2);               // [NC][SX_H][SX_W]
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -612,13 +608,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     ZWalk cur = zwalk_item(blockIdx.x, ncol, L, nf);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
     if (tid == 0) {
         const int col = cur.it % ncol;
-        tma_load_tile(&tmap, sqb, &bar[0], (col % NA) * TX, (col / NA) * TY, cur.f, bytes);
+        tma_load_tile(&tmap, sq, &bar[0], (col % NA) * TX, (col / NA) * TY, cur.f, bytes);
     }
     const double dt = A.scal->dt;
     bool bad = false;
@@ -626,15 +621,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     M P0[4], P1[4];   // F0, F1 of the previous face of this column (storage type: the
                       // differences of neighbouring faces telescope exactly)
     for (int k = 0; cur.it < nitems; ++k) {
-        const int buf = k & 1;
         ZWalk nxt = cur;
         if (++nxt.f >= nxt.fe) nxt = zwalk_item(cur.it + gridDim.x, ncol, L, nf);
-        if (tid == 0 && nxt.it < nitems) {
-            fence_proxy_async();
-            const int col = nxt.it % ncol;
-            tma_load_tile(&tmap, sqb + (buf ^ 1) * SQ_N, &bar[buf ^ 1], (col % NA) * TX, (col / NA) * TY, nxt.f,
-                          bytes);
-        }
         const int col = cur.it % ncol, f = cur.f;
         const int a0 = (col % NA) * TX, b0 = (col / NA) * TY;
         const bool upd = f > cur.f0;
@@ -698,18 +686,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                 }
             }
         }
-        const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
+        const bool ok = mbar_wait(&bar[0], (uint32_t)(k & 1));
         if (__syncthreads_or(!ok)) {
             cp_async_wait_all();
-            if (tid == 0) {
-                atomicOr(&A.scal->flags, FLAG_TIMEOUT);
-                if (nxt.it < nitems) mbar_wait(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
-            }
+            if (tid == 0) atomicOr(&A.scal->flags, FLAG_TIMEOUT);
             __syncthreads();
             return;
         }
-        tile_t1_pass(sqb + buf * SQ_N, st, tid);
+        tile_t1_pass(sq, st, tid);
         __syncthreads();
+        // the face box is free: fetch the next tile's during this one's flux
+        if (tid == 0 && nxt.it < nitems) {
+            fence_proxy_async();
+            const int col = nxt.it % ncol;
+            tma_load_tile(&tmap, sq, &bar[0], (col % NA) * TX, (col / NA) * TY, nxt.f, bytes);
+        }
 
         M F0[4], F1[4];
         if (in) {

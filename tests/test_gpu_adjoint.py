@@ -104,8 +104,9 @@ def test_one_step_adjoint_matches_central_differences(mods, case, rev):
     terms of total magnitude ~1e4), so the FP32C adjoint, whose elements sit
     within ~1e-5 of the FP64 step's adjoint (FP32 flux arithmetic: its slopes
     are small differences of O(1) values), is held to 1e-6 of the summed
-    magnitude of the terms, and element by element to 3e-5 of the FP64
-    step's adjoint."""
+    magnitude of the terms, element by element to 3e-5 of the FP64 step's
+    adjoint, and along a direction that follows the sign of that adjoint
+    (no cancellation) to 1e-4 of the central difference."""
     gks, adjoint, torch = mods
     w = {"rotor": rotor_box_workload, "walls": walls_workload, "rotor_body": rotor_body_workload,
          "rotor_corrections": rotor_corrections_workload}[case]()
@@ -157,6 +158,13 @@ def test_one_step_adjoint_matches_central_differences(mods, case, rev):
         assert abs(fd - ad) <= 1e-6 * mag, (fd, ad, mag)
         ref, _ = g.step_adjoint(g.adjoint_workspace(), t_n, W, lam1, beta, None)
         assert float((lam0 - ref).abs().max()) <= 3e-5 * float(ref.abs().max())
+        # a direction whose inner product cannot cancel: every element along
+        # the sign of the FP64 step's adjoint, with a random size
+        dWa = torch.sign(ref) * torch.tensor(0.5 + rng.random(W.shape), dtype=torch.float64, device="cuda")
+        dWa[0] *= 0.1
+        fda = (J(W + h * dWa, s0, u0) - J(W - h * dWa, s0, u0)) / (2 * h)
+        ada = float((lam0 * dWa).sum().item())
+        assert abs(fda - ada) <= 1e-4 * abs(fda), (fda, ada)
     else:
         assert abs(fd - ad) <= tol * max(abs(ad), 1e-12), (fd, ad)
     # inflow speed

@@ -23,7 +23,7 @@ FULL = (384, 256, 256)
 WIN_LO = (78, 74, 0)          # window origin (cells): x, y, z (z starts at the ground)
 WIN_N = (42, 108, 180)
 MARGIN = 7
-TOL = {"fp64": 1e-12, "fp32c": 1e-5}
+TOL = {"fp64": 1e-12, "fp32c": 1e-5, "fp64ds": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -51,10 +51,13 @@ def window(w, dt):
                        inflow=w.inflow, state0=Q, rotors=w.rotors, bodies=w.bodies)
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32c", "fp64", "fp64ds"])
 def test_full_size_step_matches_oracle_window(gks, workload, precision):
+    """fp64ds: the FP64 grid with double-single reconstruction and flux."""
     w = workload
-    g = gks.Grid.from_workload(w, precision=precision)
+    g = gks.Grid.from_workload(w, precision="fp64" if precision == "fp64ds" else precision)
+    if precision == "fp64ds":
+        g.set_fp64_arithmetic("ds")
     g.step(1)
     dt = g.last_dt
     A = g.get_state()
@@ -65,7 +68,7 @@ def test_full_size_step_matches_oracle_window(gks, workload, precision):
     umax = np.sqrt(np.max((Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0] ** 2))
     hmin = min(np.min(np.diff(f)) for f in w.faces)
     ref_dt = w.cfl * hmin / (umax + 1.0 / w.mach)
-    assert abs(dt - ref_dt) <= (1e-13 if precision == "fp64" else 1e-6) * ref_dt
+    assert abs(dt - ref_dt) <= (1e-6 if precision == "fp32c" else 1e-13) * ref_dt
     # the oracle on the window with the same time step
     o = oracle_from_workload(window(w, dt))
     o.step(1)
@@ -77,7 +80,7 @@ def test_full_size_step_matches_oracle_window(gks, workload, precision):
     assert err <= TOL[precision], err
     # the forcing acted inside the compared region
     assert np.max(np.abs(Ag[sl][1] - w.state0[1, lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]][sl[1:]])) > 0
-    tol = 1e-11 if precision == "fp64" else 2e-4
+    tol = 2e-4 if precision == "fp32c" else 1e-11
     fo = o.forces(0)
     for k in ("thrust", "torque"):
         assert np.max(np.abs(frot[k] - fo[k])) <= tol * np.max(np.abs(fo[k])), (k, frot[k], fo[k])

@@ -917,28 +917,17 @@ struct Rev32Args {
 };
 
 constexpr int kPartN = 8 * SQ_H * SQ_W;   // face-box adjoints of one tile
-constexpr int kGA = 32 * TX * TY;         // Gauss-point input adjoints of one t1 Gauss row of a tile
+constexpr int kGA = 64 * TX * TY;         // Gauss-point input adjoints of one tile
 
-constexpr size_t rev_tile32_smem_bytes()
-{
-    return (size_t)(SQ_N + kGA + ST_N) * sizeof(float) + 2 * sizeof(uint64_t);
-}
-
-// The t1-pass arrays of Gauss row m: Q0 values v*4+m, t1 derivatives v*4+2+m,
-// normal-slope values 16+2v+m (v = 0..3).
-__device__ __forceinline__ int row_array(int m, int q)
-{
-    const int v = q % 4, kind = q / 4;
-    return kind == 0 ? v * 4 + m : (kind == 1 ? v * 4 + 2 + m : 16 + 2 * v + m);
-}
+constexpr size_t rev_tile32_smem_bytes() { return (size_t)(kGA + ST_N) * sizeof(float) + 2 * sizeof(uint64_t); }
+static_assert(SQ_N <= kGA, "the face-box tile lives in the Gauss-point adjoint buffer");
 
 __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constant__ CUtensorMap tmap, Rev32Args A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *sq = reinterpret_cast<float *>(smem_raw);    // face-box tile, refilled after its t1 pass
-    float *ga = sq + SQ_N;                              // [32][TY][TX]: adjoints of one Gauss row m
-    float *st = ga + kGA;                               // t1-pass rows; each row m's arrays become their
-                                                        // adjoints once the row's Gauss points are reversed
+    float *ga = reinterpret_cast<float *>(smem_raw);   // [64][TY][TX]
+    float *sq = ga;                                     // face-box tile, dead after the t1 pass
+    float *st = ga + kGA;                               // t1-pass rows, then their adjoints
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY;
@@ -951,14 +940,13 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
     __syncthreads();
     const int gc[4] = {0, 1 + A.d, 1 + A.t1, 1 + A.t2};
     const bool needF0 = A.lamL != nullptr;
-    const int wrp = tid >> 5, lane = tid & 31;
-    if (tid == 0 && (int)blockIdx.x < ntiles) {
-        const int t = blockIdx.x;
-        tma_load_tile(&tmap, sq, &bar[0], (t % NA) * TX, ((t / NA) % NB) * TY, t / (NA * NB), bytes);
-    }
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int ta = t % NA, tb = (t / NA) % NB, f = t / (NA * NB);
+        if (tid == 0) {
+            fence_proxy_async();
+            tma_load_tile(&tmap, sq, &bar[0], ta * TX, tb * TY, f, bytes);
+        }
         const bool ok = mbar_wait(&bar[0], (uint32_t)(k & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(&A.scal->flags, FLAG_TIMEOUT);
@@ -966,23 +954,15 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         }
         tile_t1_pass(sq, st, tid);
         __syncthreads();
-        // the face box is free: fetch the next tile's
-        const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) {
-            fence_proxy_async();
-            tma_load_tile(&tmap, sq, &bar[0], (tn % NA) * TX, ((tn / NA) % NB) * TY, tn / (NA * NB), bytes);
-        }
 
-        // seeds of this thread's face: the adjoints of its face-averaged fluxes
+        // RA: per face, the 4 Gauss points
         const int a = ta * TX + tx, b = tb * TY + ty;
-        const bool valid = a < A.n1 && b < A.n2;
-        float sF0[4] = {0, 0, 0, 0}, sF1[4] = {0, 0, 0, 0};
-        float ih1 = 0.0f, ih2 = 0.0f;
-        if (valid) {
+        if (a < A.n1 && b < A.n2) {
             const bool hasl = f >= 1, hasr = f < A.nd;
             const long ir = A.base + (long)f * A.sd + (long)a * A.s1 + (long)b * A.s2, il = ir - A.sd;
             const bool okc = in_bounds(il, A.np) && in_bounds(ir, A.np);
             const float ihl = hasl ? A.ihd[f - 1 + G] : 0.0f, ihr = hasr ? A.ihd[f + G] : 0.0f;
+            float sF0[4] = {0, 0, 0, 0}, sF1[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const long o = gc[v] * A.np;
@@ -995,12 +975,9 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                     sF0[v] = 0.25f * (-ml * ihl + mr * ihr);
                 }
             }
-            ih1 = A.ih1[a + G];
-            ih2 = A.ih2[b + G];
-        }
-        for (int m = 0; m < 2; ++m) {
-            // RA for the Gauss points (m, nn) of this thread's face
-            if (valid) {
+            const float ih1 = A.ih1[a + G], ih2 = A.ih2[b + G];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
                 float Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
@@ -1020,7 +997,7 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                     float qb[4], Dnb[4], D1b[4], D2b[4];
                     gk_flux_rev<float>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, sF0, sF1, needF0, qb, Dnb,
                                        D1b, D2b);
-                    float *gp = ga + (16 * nn) * (TX * TY) + tid;
+                    float *gp = ga + (16 * (2 * m + nn)) * (TX * TY) + tid;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         gp[v * (TX * TY)] = qb[v];
@@ -1029,34 +1006,46 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                         gp[(12 + v) * (TX * TY)] = D2b[v];
                     }
                 }
-            } else {
+            }
+        } else {
 #pragma unroll 4
-                for (int j = 0; j < 32; ++j) ga[j * (TX * TY) + tid] = 0.0f;
-            }
-            __syncthreads();   // every face's row-m Gauss points are reversed; row m's arrays are dead
-            // RB for row m: row r is read by the faces bb = r - sx with stencil
-            // index sx (unrolled: constant weights); a warp takes one array and
-            // row, its lanes the columns; the adjoint replaces the array in st
-            for (int pr = wrp; pr < 12 * SQ_H; pr += (TX * TY) / 32) {
-                const int q = pr / SQ_H, r = pr - q * SQ_H;
-                const int v = q % 4, kind = q / 4;   // 0: Q0 values, 1: t1 derivatives, 2: normal slopes
-                const int jq = kind == 0 ? v : (kind == 1 ? 8 + v : 4 + v);
-                float acc = 0.0f;
-#pragma unroll
-                for (int sx = 0; sx < 5; ++sx) {
-                    const int bb = r - sx;
-                    if (bb < 0 || bb >= TY) continue;
-                    const float *g0 = ga + bb * TX + lane;
-#pragma unroll
-                    for (int nn = 0; nn < 2; ++nn) {
-                        acc += cWV32[nn][sx] * g0[(16 * nn + jq) * (TX * TY)];
-                        if (kind == 0) acc += cWD32[nn][sx] * g0[(16 * nn + 12 + v) * (TX * TY)];
-                    }
-                }
-                st[row_array(m, q) * ST_ROWS + r * TX + lane] = acc;
-            }
-            __syncthreads();   // ga is free for row m + 1; row m's adjoints are in st
+            for (int j = 0; j < 64; ++j) ga[j * (TX * TY) + tid] = 0.0f;
         }
+        __syncthreads();
+
+        // RB: row r of the t1 pass is read by the faces bb = r - sx of the tile
+        // with stencil index sx (unrolled, so that the weights are constant
+        // operands); a warp takes one array and row, its lanes the columns
+        const int wrp = tid >> 5, c = tid & 31;
+        for (int pr = wrp; pr < 24 * SQ_H; pr += (TX * TY) / 32) {
+            const int arr = pr / SQ_H, r = pr - arr * SQ_H;
+            int v, m, kind;   // kind 0: Q0 value rows, 1: t1-derivative rows, 2: normal-slope rows
+            if (arr < 16) {
+                v = arr >> 2;
+                m = arr & 1;
+                kind = (arr >> 1) & 1;
+            } else {
+                v = (arr - 16) >> 1;
+                m = (arr - 16) & 1;
+                kind = 2;
+            }
+            const int jq = kind == 0 ? v : (kind == 1 ? 8 + v : 4 + v);
+            float acc = 0.0f;
+#pragma unroll
+            for (int sx = 0; sx < 5; ++sx) {
+                const int bb = r - sx;
+                if (bb < 0 || bb >= TY) continue;
+                const float *g0 = ga + bb * TX + c;
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    const int g16 = 16 * (2 * m + nn);
+                    acc += cWV32[nn][sx] * g0[(g16 + jq) * (TX * TY)];
+                    if (kind == 0) acc += cWD32[nn][sx] * g0[(g16 + 12 + v) * (TX * TY)];
+                }
+            }
+            st[arr * ST_ROWS + r * TX + c] = acc;
+        }
+        __syncthreads();
 
         // RC: face-box column cc is read by the row columns c = cc - sx; a
         // warp takes one (component, row), its lanes the columns (36: a
@@ -1064,7 +1053,7 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         float *out = A.part + (long)t * kPartN;
         for (int pr = wrp; pr < 8 * SQ_H; pr += (TX * TY) / 32) {
             const int j = pr / SQ_H, r = pr - j * SQ_H;
-            for (int cc = lane; cc < SQ_W; cc += 32) {
+            for (int cc = c; cc < SQ_W; cc += 32) {
                 float acc = 0.0f;
 #pragma unroll
                 for (int sx = 0; sx < 5; ++sx) {
@@ -1082,7 +1071,7 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                 out[(j * SQ_H + r) * SQ_W + cc] = acc;
             }
         }
-        __syncthreads();   // st is free for the next tile's t1 pass
+        __syncthreads();   // the buffers are free for the next tile
     }
 }
 

@@ -278,7 +278,7 @@ int gks_state_layout(const gks_grid *g, long out[7]);
 int gks_set_state_device(gks_grid *g, const double *d_state);
 int gks_get_state_device(gks_grid *g, double *d_state);
 
-/* Adjoint of one step (reverse mode, FP64): for a functional J of the state
+/* Adjoint of one step (reverse mode): for a functional J of the state
  * after the step, given lambda^{n+1} = dJ/dW^{n+1}, computes
  * lambda^n = dJ/dW^n (through the ghost fill, both S2O4 stages with their
  * WENO5 reconstruction, equilibrium state, tangential Gauss-point
@@ -296,7 +296,10 @@ int gks_get_state_device(gks_grid *g, double *d_state);
  *   d_adj_n     device, receives lambda^n (compact FP64; may not alias the
  *               inputs).
  * The forward step is recomputed from d_state_n inside the call; the grid's
- * own state and time are not changed. Requires a GKS_FP64 grid with a fixed time step,
+ * own state and time are not changed. On a GKS_FP32C grid the recomputed
+ * step is the FP32C step (d_state_n split into hi + lo as gks_set_state
+ * does) and its reverse is the FP32 reverse of the recorded steps, whatever
+ * the adjoint precision. Requires a fixed time step,
  * at most one rotor (with or without the velocity and tip corrections), and immersed
  * bodies only with a fixed iteration count (tol = 0) (GKS_ERR_STATE
  * otherwise), and fewer than 2^31 / 64 faces per direction (GKS_ERR_ARG

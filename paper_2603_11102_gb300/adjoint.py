@@ -22,7 +22,6 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import gks
 
 
 def uniform_state(grid, uinf, rho=1.0):
@@ -93,9 +92,6 @@ class RotorObjective(torch.autograd.Function):
     def backward(ctx, gJ):
         g, N, K, dt = ctx.grid, ctx.nsteps, ctx.K, ctx.dt
         tapes = _tapes(g, min(K, N), ctx.tape)
-        if tapes is None and g.precision != gks.PRECISIONS["fp64"]:
-            raise RuntimeError("an FP32C grid differentiates through recorded steps only: "
-                               "no room for %d tapes (lower K)" % min(K, N))
         work = g.adjoint_scratch() if tapes else g.adjoint_workspace()
         lam = plane_deficit_seed(ctx.WN, ctx.iplane)
         gs = np.zeros(ctx.nscales)
@@ -135,10 +131,10 @@ def rotor_objective(grid, scales, uinf, nsteps, K=20, iplane=None, beta=1.0, tap
     """J as a differentiable function of (scales, uinf) (float64 CPU tensors
     with requires_grad); the grid must have one rotor and dt_fixed > 0. On an
     FP64 grid the gradient is that of the FP64 steps; on an FP32C grid that of
-    the FP32C steps (recorded steps only; FP32 reverse arithmetic). tape:
+    the FP32C steps (FP32 reverse arithmetic). tape:
     "auto" (recorded steps when K tapes fit on the device), "on" (always; the
     allocation fails if they do not fit) or "off" (recompute every reverse
-    step, FP64 grids)."""
+    step)."""
     if iplane is None:
         raise ValueError("iplane (x index of the sampling plane) is required")
     if scales.dtype != torch.float64 or uinf.dtype != torch.float64:

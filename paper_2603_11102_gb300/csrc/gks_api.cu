@@ -1077,9 +1077,7 @@ int gp_bytes_of(const gks_grid *g) { return (g->adj_fp32 || g->c.prec == GKS_FP3
 int adjoint_check(gks_grid *g, bool tape_path)
 {
     const Ctx &c = g->c;
-    if (c.prec != GKS_FP64 && !(tape_path && c.prec == GKS_FP32C))
-        return fail(g, GKS_ERR_STATE, tape_path ? "bad grid precision for the adjoint"
-                                                : "gks_step_adjoint needs a GKS_FP64 grid (FP32C: recorded steps)");
+    if (c.prec != GKS_FP64 && c.prec != GKS_FP32C) return fail(g, GKS_ERR_STATE, "bad grid precision for the adjoint");
     if (!(c.dt_fixed > 0.0)) return fail(g, GKS_ERR_STATE, "the adjoint needs a fixed time step (dt_fixed > 0)");
     for (const BodyDev &b : g->bodies)
         if (b.tol > 0.0 && !tape_path)
@@ -1268,17 +1266,39 @@ int gks_step_adjoint(gks_grid *g, void *d_adj_work, double t_n, const double *d_
                              "record time");
     if (!rc) rc = cuda_check(g, cudaMemsetAsync(w.hdr, kTapeMagicByte, sizeof(double), c.stream), "mark tape");
     if (rc) return rc;
-    cc.state = w.A0;
-    cc.wk0 = w.A0;
-    cc.wk1 = w.Ws;
-    launch_scatter_state(cc, d_state_n);
-    launch_ghost(cc, w.A0);
-    use_tape_gauss(cc, w, 0);
-    launch_stage(cc, 1);
-    launch_ghost(cc, cc.wk1);
-    cc.state = w.Wp;
-    use_tape_gauss(cc, w, 1);
-    launch_stage(cc, 2);
+    if (c.prec == GKS_FP32C) {
+        // the FP32C step recomputed in the workspace: the compensated state
+        // (hi, lo) in the scratch's lamA (cleared by the reverse before its
+        // use), P in the tape's Ws as hi, lo floats until W* is widened into
+        // it after stage 2, the FP32 reconstruction inputs of both stages in
+        // A0f and Wsf as the reverse reads them
+        w.c32 = &g->c;
+        cc.state = w.lamA;
+        cc.wk0 = w.A0f;
+        cc.wk1 = w.Wsf;
+        cc.pbuf = w.Ws;
+        cc.prep_next = 0;
+        launch_scatter_state_prep(cc, d_state_n);
+        launch_ghost(cc, cc.wk0);
+        launch_widen(cc, w.A0f, nullptr, w.A0, 4 * c.np, c.np, c.off);
+        launch_stage(cc, 1);
+        launch_ghost(cc, cc.wk1);
+        launch_stage(cc, 2);
+        launch_widen(cc, w.Wsf, nullptr, w.Ws, 4 * c.np, c.np, c.off);
+        launch_widen(cc, (const float *)w.lamA, (const float *)w.lamA + 4 * c.np, w.Wp, 4 * c.np, 0, 0.0);
+    } else {
+        cc.state = w.A0;
+        cc.wk0 = w.A0;
+        cc.wk1 = w.Ws;
+        launch_scatter_state(cc, d_state_n);
+        launch_ghost(cc, w.A0);
+        use_tape_gauss(cc, w, 0);
+        launch_stage(cc, 1);
+        launch_ghost(cc, cc.wk1);
+        cc.state = w.Wp;
+        use_tape_gauss(cc, w, 1);
+        launch_stage(cc, 2);
+    }
     std::vector<int> iters(g->bodies.size());
     for (size_t k = 0; k < iters.size(); ++k) iters[k] = g->bodies[k].niter;   // tol = 0: every iteration runs
     return reverse_from_tape(g, w, false, t_n, dt, iters.data(), d_adj_np1, d_adj_n, power_seed, h_grad_scales,

@@ -1014,11 +1014,13 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
         __syncthreads();
 
         // RB: row r of the t1 pass is read by the faces bb = r - sx of the tile
-        // with stencil index sx (unrolled, so that the weights are constant
-        // operands); a warp takes one array and row, its lanes the columns
-        const int wrp = tid >> 5, c = tid & 31;
-        for (int pr = wrp; pr < 24 * SQ_H; pr += (TX * TY) / 32) {
-            const int arr = pr / SQ_H, r = pr - arr * SQ_H;
+        // with stencil index sx. A thread takes one array and one column: the
+        // adjoints of the 8 faces of the column that the array's rows feed
+        // sit in registers and the 12 rows are 5-tap sums of them (indices
+        // and weights compile-time; the same terms in the same order as a
+        // gather per row)
+        for (int task = tid; task < 24 * TX; task += TX * TY) {
+            const int arr = task / TX, c = task - arr * TX;
             int v, m, kind;   // kind 0: Q0 value rows, 1: t1-derivative rows, 2: normal-slope rows
             if (arr < 16) {
                 v = arr >> 2;
@@ -1030,46 +1032,81 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                 kind = 2;
             }
             const int jq = kind == 0 ? v : (kind == 1 ? 8 + v : 4 + v);
-            float acc = 0.0f;
+            float X[TY][2], Y[TY][2];
 #pragma unroll
-            for (int sx = 0; sx < 5; ++sx) {
-                const int bb = r - sx;
-                if (bb < 0 || bb >= TY) continue;
-                const float *g0 = ga + bb * TX + c;
+            for (int bb = 0; bb < TY; ++bb)
 #pragma unroll
                 for (int nn = 0; nn < 2; ++nn) {
-                    const int g16 = 16 * (2 * m + nn);
-                    acc += cWV32[nn][sx] * g0[(g16 + jq) * (TX * TY)];
-                    if (kind == 0) acc += cWD32[nn][sx] * g0[(g16 + 12 + v) * (TX * TY)];
+                    const float *g0 = ga + (16 * (2 * m + nn)) * (TX * TY) + bb * TX + c;
+                    X[bb][nn] = g0[jq * (TX * TY)];
+                    Y[bb][nn] = kind == 0 ? g0[(12 + v) * (TX * TY)] : 0.0f;
                 }
-            }
-            st[arr * ST_ROWS + r * TX + c] = acc;
-        }
-        __syncthreads();
-
-        // RC: face-box column cc is read by the row columns c = cc - sx; a
-        // warp takes one (component, row), its lanes the columns (36: a
-        // second pass of 4 lanes)
-        float *out = A.part + (long)t * kPartN;
-        for (int pr = wrp; pr < 8 * SQ_H; pr += (TX * TY) / 32) {
-            const int j = pr / SQ_H, r = pr - j * SQ_H;
-            for (int cc = c; cc < SQ_W; cc += 32) {
+            float *o = st + arr * ST_ROWS + c;
+#pragma unroll
+            for (int r = 0; r < SQ_H; ++r) {
                 float acc = 0.0f;
 #pragma unroll
                 for (int sx = 0; sx < 5; ++sx) {
-                    const int cs = cc - sx;
-                    if (cs < 0 || cs >= TX) continue;
-                    const float *r0 = st + r * TX + cs;
+                    const int bb = r - sx;
+                    if (bb < 0 || bb >= TY) continue;
+#pragma unroll
+                    for (int nn = 0; nn < 2; ++nn) {
+                        acc += cWV32[nn][sx] * X[bb][nn];
+                        if (kind == 0) acc += cWD32[nn][sx] * Y[bb][nn];
+                    }
+                }
+                o[r * TX] = acc;
+            }
+        }
+        __syncthreads();
+
+        // RC: face-box column cc is read by the row columns c = cc - sx. A
+        // thread takes one component, one row and 4 face-box columns cc0 ..
+        // cc0+3: the 8 row columns cc0-4 .. cc0+3 of each array it needs come
+        // by 128-bit loads (zero outside the tile), the 4 outputs are 5-tap
+        // sums of them and leave by one 128-bit store
+        float *out = A.part + (long)t * kPartN;
+        constexpr int NG = SQ_W / 4;   // 9 groups of 4 columns
+        for (int task = tid; task < 8 * SQ_H * NG; task += TX * TY) {
+            const int j = task / (SQ_H * NG), rem = task - j * (SQ_H * NG), r = rem / NG, gq = rem - r * NG;
+            const int cc0 = 4 * gq;
+            const int na = j < 4 ? 4 : 2;
+            int arrs[4];
+            if (j < 4) {
+                arrs[0] = j * 4; arrs[1] = j * 4 + 1; arrs[2] = j * 4 + 2; arrs[3] = j * 4 + 3;
+            } else {
+                arrs[0] = 16 + (j - 4) * 2; arrs[1] = arrs[0] + 1; arrs[2] = arrs[3] = arrs[0];
+            }
+            float Z[4][8];   // per array, row columns cc0-4 .. cc0+3
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float *rowp = st + arrs[q] * ST_ROWS + r * TX;
+                const float4 lo4 = (q < na && cc0 >= 4) ? *reinterpret_cast<const float4 *>(rowp + cc0 - 4)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 hi4 = (q < na && cc0 < TX) ? *reinterpret_cast<const float4 *>(rowp + cc0)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                Z[q][0] = lo4.x; Z[q][1] = lo4.y; Z[q][2] = lo4.z; Z[q][3] = lo4.w;
+                Z[q][4] = hi4.x; Z[q][5] = hi4.y; Z[q][6] = hi4.z; Z[q][7] = hi4.w;
+            }
+            float res[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int sx = 0; sx < 5; ++sx) {
+                    const int k = 4 + i - sx;   // row column cc0 + i - sx
+                    if (cc0 + i - sx < 0 || cc0 + i - sx >= TX) continue;
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
                         if (j < 4)
-                            acc += cWV32[m][sx] * r0[(j * 4 + m) * ST_ROWS] + cWD32[m][sx] * r0[(j * 4 + 2 + m) * ST_ROWS];
+                            acc += cWV32[m][sx] * Z[m][k] + cWD32[m][sx] * Z[2 + m][k];
                         else
-                            acc += cWV32[m][sx] * r0[(16 + (j - 4) * 2 + m) * ST_ROWS];
+                            acc += cWV32[m][sx] * Z[m][k];
                     }
                 }
-                out[(j * SQ_H + r) * SQ_W + cc] = acc;
+                res[i] = acc;
             }
+            *reinterpret_cast<float4 *>(out + (j * SQ_H + r) * SQ_W + cc0) = make_float4(res[0], res[1], res[2], res[3]);
         }
         __syncthreads();   // the buffers are free for the next tile
     }

@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(256) rev_face_state32_kernel(RevArgs A)
 // is written by one thread. The face reverse is rev_face_state32_kernel's.
 constexpr int kRevCells = 24;
 
-__global__ void __launch_bounds__(256) rev_face_cells32_kernel(RevArgs A)
+__global__ void __launch_bounds__(256, 2) rev_face_cells32_kernel(RevArgs A)
 {
     const float *lamFQ = (const float *)A.lamFQ;
     const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2, b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
@@ -794,12 +794,21 @@ __global__ void __launch_bounds__(256) rev_face_cells32_kernel(RevArgs A)
     for (int v = 0; v < 4; ++v)
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc[v][k] = 0.0f;
+    // the cell entering the window, loaded one face ahead
+    float nxt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) nxt[v] = A.Ahi[comp[v] * A.np + base + (long)(fs + 2) * sd];
+#pragma unroll 1
     for (int f = fs; f <= fe; ++f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) wh[v][k] = wh[v][k + 1];
-            wh[v][5] = A.Ahi[comp[v] * A.np + base + (long)(f + 2) * sd];
+            wh[v][5] = nxt[v];
+        }
+        if (f < fe) {   // cell f + 3 <= fe + 2: inside the checked range
+#pragma unroll
+            for (int v = 0; v < 4; ++v) nxt[v] = A.Ahi[comp[v] * A.np + base + (long)(f + 3) * sd];
         }
         float Ql[4], Qr[4], Rt[4];
 #pragma unroll
@@ -1150,58 +1159,64 @@ struct GhostRevArgs {
     double *uinf_part;
     int n[3], P[3];
     long np;
-    int d, e1, e2, lo1, lo2, len1, len2, s, l, bc;
+    int d, e1, e2, lo1, lo2, len1, len2, s, bc;
+    long uinf_layer;   // stride of uinf_part between layers
     double csound, uin[3];
 };
 
+// One (axis, side): the layers l = G .. 1 in turn, each thread one position
+// of the side (the sources are interior cells, so a thread's layers are its
+// own and keep the order of a sweep per layer).
 __global__ void __launch_bounds__(256) ghost_rev_kernel(GhostRevArgs A)
 {
     const int a = A.lo1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int b = A.lo2 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
     if (a >= A.lo1 + A.len1 || b >= A.lo2 + A.len2) return;
-    const int d = A.d, nd = A.n[d], s = A.s, l = A.l, bc = A.bc;
-    const int gi = s == 0 ? -l : nd - 1 + l;
-    int src;
-    if (bc == GKS_BC_PERIODIC) {
-        src = gi % nd;
-        if (src < 0) src += nd;
-    } else if (bc == GKS_BC_NOSLIP || bc == GKS_BC_SLIP) {
-        src = s == 0 ? l - 1 : nd - l;
-    } else {
-        src = s == 0 ? 0 : nd - 1;
+    const int d = A.d, nd = A.n[d], s = A.s, bc = A.bc;
+    for (int l = G; l >= 1; --l) {
+        const int gi = s == 0 ? -l : nd - 1 + l;
+        int src;
+        if (bc == GKS_BC_PERIODIC) {
+            src = gi % nd;
+            if (src < 0) src += nd;
+        } else if (bc == GKS_BC_NOSLIP || bc == GKS_BC_SLIP) {
+            src = s == 0 ? l - 1 : nd - l;
+        } else {
+            src = s == 0 ? 0 : nd - 1;
+        }
+        int cg[3], cs[3];
+        cg[d] = gi; cg[A.e1] = a; cg[A.e2] = b;
+        cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
+        const long ig = lin(A.P[0], A.P[1], cg[0], cg[1], cg[2]), is = lin(A.P[0], A.P[1], cs[0], cs[1], cs[2]);
+        if (!in_bounds(ig, A.np) || !in_bounds(is, A.np)) continue;
+        double lg[4];
+        for (int v = 0; v < 4; ++v) {
+            lg[v] = A.lamA[v * A.np + ig];
+            A.lamA[v * A.np + ig] = 0.0;
+        }
+        double add[4] = {lg[0], lg[1], lg[2], lg[3]};
+        double gu = 0.0;
+        if (bc == GKS_BC_NOSLIP) {
+            add[1] = -lg[1]; add[2] = -lg[2]; add[3] = -lg[3];
+        } else if (bc == GKS_BC_SLIP) {
+            add[1 + d] = -lg[1 + d];
+        } else if (bc == GKS_BC_INFLOW) {
+            const double r1 = A.A[is], un1 = A.A[(1 + d) * A.np + is] / r1;
+            const double sg = s == 0 ? 1.0 : -1.0;
+            const double x = sg * (A.uin[d] - un1) / A.csound;
+            const double ex = exp(x);
+            const double rg = r1 * ex;
+            const double rgb = lg[0] + lg[1] * A.uin[0] + lg[2] * A.uin[1] + lg[3] * A.uin[2];
+            add[0] = rgb * ex * (1.0 + sg * un1 / A.csound);
+            add[1] = add[2] = add[3] = 0.0;
+            add[1 + d] = -rgb * sg * ex / A.csound;
+            // sensitivity to the inflow speed U_inf = u_in[0]
+            gu = lg[1] * rg + (d == 0 ? rgb * r1 * ex * sg / A.csound : 0.0);
+        }
+        for (int v = 0; v < 4; ++v) A.lamA[v * A.np + is] += add[v];
+        if (bc == GKS_BC_INFLOW)
+            A.uinf_part[(long)(l - 1) * A.uinf_layer + (long)(b - A.lo2) * A.len1 + (a - A.lo1)] = gu;
     }
-    int cg[3], cs[3];
-    cg[d] = gi; cg[A.e1] = a; cg[A.e2] = b;
-    cs[d] = src; cs[A.e1] = a; cs[A.e2] = b;
-    const long ig = lin(A.P[0], A.P[1], cg[0], cg[1], cg[2]), is = lin(A.P[0], A.P[1], cs[0], cs[1], cs[2]);
-    if (!in_bounds(ig, A.np) || !in_bounds(is, A.np)) return;
-    double lg[4];
-    for (int v = 0; v < 4; ++v) {
-        lg[v] = A.lamA[v * A.np + ig];
-        A.lamA[v * A.np + ig] = 0.0;
-    }
-    double add[4] = {lg[0], lg[1], lg[2], lg[3]};
-    double gu = 0.0;
-    if (bc == GKS_BC_NOSLIP) {
-        add[1] = -lg[1]; add[2] = -lg[2]; add[3] = -lg[3];
-    } else if (bc == GKS_BC_SLIP) {
-        add[1 + d] = -lg[1 + d];
-    } else if (bc == GKS_BC_INFLOW) {
-        const double r1 = A.A[is], un1 = A.A[(1 + d) * A.np + is] / r1;
-        const double sg = s == 0 ? 1.0 : -1.0;
-        const double x = sg * (A.uin[d] - un1) / A.csound;
-        const double ex = exp(x);
-        const double rg = r1 * ex;
-        const double rgb = lg[0] + lg[1] * A.uin[0] + lg[2] * A.uin[1] + lg[3] * A.uin[2];
-        add[0] = rgb * ex * (1.0 + sg * un1 / A.csound);
-        add[1] = add[2] = add[3] = 0.0;
-        add[1 + d] = -rgb * sg * ex / A.csound;
-        // sensitivity to the inflow speed U_inf = u_in[0]
-        gu = lg[1] * rg + (d == 0 ? rgb * r1 * ex * sg / A.csound : 0.0);
-    }
-    for (int v = 0; v < 4; ++v) A.lamA[v * A.np + is] += add[v];
-    if (bc == GKS_BC_INFLOW)
-        A.uinf_part[(long)(b - A.lo2) * A.len1 + (a - A.lo1)] = gu;
 }
 
 // Fixed-order two-pass sum of x[0..n) added to *acc: block b of kRedBlocks
@@ -1727,14 +1742,13 @@ void ghost_adjoint(const Ctx &c, const AdjWork &w, const double *Aw)
         A.len2 = A.e2 < d ? c.n[A.e2] + 2 * G : c.n[A.e2];
         A.csound = c.csound;
         for (int e = 0; e < 3; ++e) A.uin[e] = c.inflow[1 + e];
-        for (int s = 0; s < 2; ++s)
-            for (int l = G; l >= 1; --l) {
-                A.s = s;
-                A.l = l;
-                A.bc = c.bc[d][s];
-                A.uinf_part = w.uinf_part + ((long)((d * 2 + s) * G + (l - 1))) * (w.nuinf / (6 * G));
-                ghost_rev_kernel<<<dim3((A.len1 + 31) / 32, (A.len2 + 7) / 8, 1), dim3(32, 8), 0, c.stream>>>(A);
-            }
+        for (int s = 0; s < 2; ++s) {
+            A.s = s;
+            A.bc = c.bc[d][s];
+            A.uinf_layer = w.nuinf / (6 * G);
+            A.uinf_part = w.uinf_part + (long)((d * 2 + s) * G) * A.uinf_layer;
+            ghost_rev_kernel<<<dim3((A.len1 + 31) / 32, (A.len2 + 7) / 8, 1), dim3(32, 8), 0, c.stream>>>(A);
+        }
     }
     static_assert(kRedBlocks == 256, "one part per thread of the final pass");
     reduce_part_kernel<<<kRedBlocks, 256, 0, c.stream>>>(w.uinf_part, w.nuinf, w.red);

@@ -1040,13 +1040,21 @@ __global__ void __launch_bounds__(256) scatter_kernel(int prec, const double *__
     double mx = 0.0;
     float mxf = 0.0f;
     if (i < nx && j < ny) {
+        // the next plane's values are loaded while this one's are stored
+        double qn[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qn[v] = k0 < k1 ? src[v * N + i + (long)nx * (j + (long)ny * k0)] : 0.0;
         for (int k = k0; k < k1; ++k) {
-            const long ci = i + (long)nx * (j + (long)ny * k);
             const long lin = (long)(i + G) + (long)P0 * ((long)(j + G) + (long)P1 * (k + G));
             double q[4];
             float h[4], l[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) q[v] = src[v * N + ci];
+            for (int v = 0; v < 4; ++v) q[v] = qn[v];
+            if (k + 1 < k1) {
+                const long cn = i + (long)nx * (j + (long)ny * (k + 1));
+#pragma unroll
+                for (int v = 0; v < 4; ++v) qn[v] = src[v * N + cn];
+            }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (prec == GKS_FP64) {

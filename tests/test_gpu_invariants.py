@@ -174,3 +174,36 @@ def test_taylor_green_2d_viscous_decay_rate_on_the_gpu(gks, precision):
     g.close()
     rate = -np.polyfit(np.array(ts), np.log(np.array(ke)), 1)[0]
     assert abs(rate / (4 * nu) - 1) < 0.01, rate
+
+
+def test_alu_peak_probe_counts_its_operations(gks):
+    """gks_alu_peak_probe: the operations it reports are 2 per FMA of its
+    launch (4 blocks of 256 threads per SM, 128 FMAs per iteration), its
+    rate scales with the work (twice the iterations, about twice the time),
+    and the FP32 rate lies within the GPU's nominal bounds (FP64 well below
+    it on GB300)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(4 * sms, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fp64, iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fl = gks.alu_peak_probe(fp64, iters, sink, st)
+        b.record(st)
+        b.synchronize()
+        return fl, a.elapsed_time(b) / 1e3
+
+    gks.alu_peak_probe(False, 1000, sink, st)   # warm-up
+    fl1, t1 = timed(False, 20000)
+    fl2, t2 = timed(False, 40000)
+    assert fl1 == 2.0 * 4 * sms * 256 * 20000 * 128 and fl2 == 2 * fl1
+    assert 1.6 <= t2 / t1 <= 2.4, (t1, t2)
+    rate32 = fl2 / t2 / 1e12
+    nominal = sms * 128 * 2 * 2.2e9 / 1e12          # FP32 lanes x 2 x a clock above any GB300 boost
+    assert 0.3 * nominal <= rate32 <= 1.05 * nominal, (rate32, nominal)
+    fl64, t64 = timed(True, 2000)
+    assert fl64 / t64 / 1e12 < 0.5 * rate32
+    assert not torch.any(sink != 0)   # the loop's results stay in registers

@@ -286,7 +286,7 @@ namespace {
 
 // TMA descriptor of the face box of direction a at `base`: dims (t1 padded,
 // t2 + 4, faces, 8 components), box (36, 12, 1, 8). c.e1p must be set.
-int encode_face_map(const Ctx &c, int a, void *base, CUtensorMap *out, std::string *msg)
+int encode_face_map(const Ctx &c, int a, void *base, CUtensorMap *out, std::string *msg, int rows = 12)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -303,7 +303,7 @@ int encode_face_map(const Ctx &c, int a, void *base, CUtensorMap *out, std::stri
     const int t2 = a == 2 ? 1 : 2;
     const cuuint64_t dims[4] = {(cuuint64_t)c.e1p[a], (cuuint64_t)(c.n[t2] + 4), (cuuint64_t)(c.n[a] + 1), 8};
     const cuuint64_t strides[3] = {dims[0] * es, dims[0] * dims[1] * es, (cuuint64_t)c.nfq * es};
-    const cuuint32_t box[4] = {36, 12, 1, 8};
+    const cuuint32_t box[4] = {36, (cuuint32_t)rows, 1, 8};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = encode(out, c.prec == GKS_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -400,7 +400,8 @@ int gks_create_grid(const gks_grid_desc *desc, void *d_state, void *d_work, gks_
     for (int a = 0; a < 3; ++a) {
         c.e1p[a] = L.e1p[a];
         std::string m;
-        if (encode_face_map(c, a, c.fq, &c.tmap[a], &m)) {
+        if (encode_face_map(c, a, c.fq, &c.tmap[a], &m) ||
+            (c.prec == GKS_FP32C && encode_face_map(c, a, c.fq, &c.tmapT[a], &m, 20))) {
             delete g;
             return fail(nullptr, GKS_ERR_CUDA, m);
         }

@@ -417,36 +417,49 @@ __device__ __forceinline__ void sts4(dsf *p, const dsf q[4])
 
 static_assert(TX * TY == 256 && SQ_H == 12 && TX == 32, "t1-pass task split assumes 32 x 8 tiles");
 
-// t1 pass of one tile: values and t1-derivatives of Q0, values of the normal
-// slope, at the two t1 Gauss points, for every row of the tile. 768 equal
-// tasks (Q0 or slope, component, row, group of 4 columns): a task reads 8
+// Taller face tiles (FP32C x and y faces): 32 x 16 faces, each thread two
+// faces adjacent along t2, so that the t2 pass reads 6 rows for 2 faces
+// instead of 5 for 1 and the t1 pass recomputes 4 halo rows per 16 instead
+// of per 8.
+constexpr int TYT = 16;
+constexpr int SQ_HT = TYT + 4;
+constexpr int SQ_NT = 8 * SQ_HT * SQ_W;
+constexpr int ST_ROWS_T = SQ_HT * TX;
+constexpr int ST_NT = 24 * ST_ROWS_T;
+
+// t1 pass of one tile of H rows (with the tangential halo): values and
+// t1-derivatives of Q0, values of the normal slope, at the two t1 Gauss
+// points, for every row of the tile. 64 H equal tasks (Q0 or slope,
+// component, row, group of 4 columns), H / 4 per thread: a task reads 8
 // consecutive values of its row and writes 4 columns; the lanes of a warp
-// share the kind and the component.
-template <typename R, typename C>
+// share the kind and the component (8 H is a multiple of 32).
+template <typename R, typename C, int H = SQ_H>
 __device__ __forceinline__ void tile_t1_pass(const R *sq, C *st, int tid)
 {
+    static_assert(H % 4 == 0, "a warp's tasks share kind and component");
+    constexpr int NQ = 32 * H, NV = 8 * H, ROWS = H * TX;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < H / 4; ++j) {
         const int task = tid + j * 256;
-        const int kind = task >= 384, rem = task - kind * 384, v = rem / 96, rc = rem - v * 96;
+        const int kind = task >= NQ, rem = task - kind * NQ, v = rem / NV, rc = rem - v * NV;
         const int r = rc >> 3, cg = rc & 7;
         C q[8];
-        lds8(sq + ((kind * 4 + v) * SQ_H + r) * SQ_W + 4 * cg, q);
+        lds8(sq + ((kind * 4 + v) * H + r) * SQ_W + 4 * cg, q);
         C *o = st + r * TX + 4 * cg;
         if (kind == 0) {
             C vm[4], vp[4], dm[4], dp[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tan_val_der(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i], dm[i], dp[i]);
-            sts4(o + (v * 4 + 0) * ST_ROWS, vm);
-            sts4(o + (v * 4 + 1) * ST_ROWS, vp);
-            sts4(o + (v * 4 + 2) * ST_ROWS, dm);
-            sts4(o + (v * 4 + 3) * ST_ROWS, dp);
+            sts4(o + (v * 4 + 0) * ROWS, vm);
+            sts4(o + (v * 4 + 1) * ROWS, vp);
+            sts4(o + (v * 4 + 2) * ROWS, dm);
+            sts4(o + (v * 4 + 3) * ROWS, dp);
         } else {
             C vm[4], vp[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tan_val_direct(q[i], q[i + 1], q[i + 2], q[i + 3], q[i + 4], vm[i], vp[i]);
-            sts4(o + (16 + v * 2 + 0) * ST_ROWS, vm);
-            sts4(o + (16 + v * 2 + 1) * ST_ROWS, vp);
+            sts4(o + (16 + v * 2 + 0) * ROWS, vm);
+            sts4(o + (16 + v * 2 + 1) * ROWS, vp);
         }
     }
 }
@@ -456,6 +469,7 @@ constexpr size_t flux_smem_bytes()
 {
     return (size_t)(SQ_N + ST_N) * sizeof(R) + 2 * sizeof(unsigned long long);
 }
+constexpr size_t flux_tall_smem_bytes() { return (size_t)(SQ_NT + ST_NT) * sizeof(float) + 2 * sizeof(unsigned long long); }
 
 
 // ---- TMA and mbarrier helpers (sm_90+ PTX) ----

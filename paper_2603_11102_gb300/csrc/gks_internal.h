@@ -60,6 +60,7 @@ struct Ctx {
     long nfq;
     int e1p[3];               // padded t1 extent of the face box per direction (multiple of 4)
     CUtensorMap tmap[3];      // TMA descriptors of the face box per direction
+    CUtensorMap tmapT[3];     // FP32C: the same with 20-row boxes (32 x 16 face tiles)
     // Optional (FP64): per direction, the 64 Gauss-point inputs of every face
     // (16 g + k arrays of stride ngp; g Gauss point, k = Q0, normal slope, t1
     // slope, t2 slope x 4 components), written by the flux kernels as double

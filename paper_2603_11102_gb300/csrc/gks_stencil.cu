@@ -419,6 +419,124 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
     }
 }
 
+// The t2 pass and the flux of the two faces (tx, r0) and (tx, r0 + 1) of a
+// tall tile (FP32C): each row array is read once over the 6 rows r0 .. r0+5
+// that the two 5-point stencils cover; the sums of F0 and F1 over the 4
+// Gauss points of each face, in the order of tile_gauss_flux.
+template <bool NEED_F0>
+__device__ __forceinline__ void tile_gauss_flux_pair(const Phys<float> &ph, const float *st, int tx, int r0,
+                                                     float ih1, const float ih2[2], float acc0[2][4],
+                                                     float acc1[2][4])
+{
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc0[e][v] = acc1[e][v] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        float Qv[2][2][4], Dn[2][2][4], D1[2][2][4], D2[2][2][4];   // [face][t2 point][component]
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float *x = st + (v * 4 + m) * ST_ROWS_T + r0 * TX + tx;
+            const float *y = st + (v * 4 + 2 + m) * ST_ROWS_T + r0 * TX + tx;
+            const float *z = st + (16 + v * 2 + m) * ST_ROWS_T + r0 * TX + tx;
+            float p[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) p[i] = x[i * TX];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                tan_val_der(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Qv[e][0][v], Qv[e][1][v], D2[e][0][v],
+                            D2[e][1][v]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) p[i] = y[i * TX];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], D1[e][0][v], D1[e][1][v]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) p[i] = z[i * TX];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Dn[e][0][v], Dn[e][1][v]);
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int nn = 0; nn < 2; ++nn) {
+                float F0[4], F1[4];
+                gk_flux<float, NEED_F0>(ph, Qv[e][nn], Dn[e][nn], D1[e][nn], D2[e][nn], ih1, ih2[e], F0, F1);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (NEED_F0) acc0[e][v] += F0[v];
+                    acc1[e][v] += F1[v];
+                }
+            }
+    }
+}
+
+// face_flux_kernel on 32 x 16 tiles for FP32C grids (the same results bit
+// for bit): the face box of a tile (its tangential halo included) arrives by
+// TMA, the t1 pass fills 20 rows, and each thread computes two faces.
+template <bool NEED_F0>
+__global__ void __launch_bounds__(256, 2) face_flux_tall_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                FluxArgs<float, float> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *sq = reinterpret_cast<float *>(smem_raw);   // face-box tile (SQ_NT)
+    float *st = sq + SQ_NT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_NT);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TYT - 1) / TYT;
+    const int ntiles = NA * NB * A.nf;
+    const uint32_t bytes = (uint32_t)(SQ_NT * sizeof(float));
+    const TileIdx g = {(int)(gridDim.x % NA), (int)((gridDim.x / NA) % NB), (int)(gridDim.x / (NA * NB))};
+    TileIdx cur = {(int)(blockIdx.x % NA), (int)((blockIdx.x / NA) % NB), (int)(blockIdx.x / (NA * NB))};
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    if (tid == 0 && t < ntiles) tma_load_tile(&tmap, sq, &bar[0], cur.ta * TX, cur.tb * TYT, cur.f, bytes);
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int tn = t + gridDim.x;
+        const TileIdx nxt = tile_add(cur, g, NA, NB);
+        const bool ok = mbar_wait(&bar[0], (uint32_t)(k & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(&A.scal->flags, FLAG_TIMEOUT);
+            return;
+        }
+        const int a0 = cur.ta * TX, b0 = cur.tb * TYT, f = cur.f;
+        cur = nxt;
+
+        tile_t1_pass<float, float, SQ_HT>(sq, st, tid);
+        __syncthreads();
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            tma_load_tile(&tmap, sq, &bar[0], nxt.ta * TX, nxt.tb * TYT, nxt.f, bytes);
+        }
+
+        const int a = a0 + tx, b = b0 + 2 * ty;
+        if (a < A.n1 && b < A.n2) {
+            // b + 1 <= n2: inside the padded width array even when face b + 1 is not stored
+            const float ih1 = __ldg(A.ih1 + a + G);
+            const float ih2[2] = {__ldg(A.ih2 + b + G), __ldg(A.ih2 + b + 1 + G)};
+            float acc0[2][4], acc1[2][4];
+            tile_gauss_flux_pair<NEED_F0>(A.ph, st, tx, 2 * ty, ih1, ih2, acc0, acc1);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const long o = ((long)f * A.n2 + b + e) * A.n1 + a;
+                if (b + e >= A.n2 || !in_bounds(o, A.nff)) break;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (NEED_F0) A.ff[A.gcomp[v] * A.nff + o] = acc0[e][v] * 0.25f;
+                    A.ff[(4 + A.gcomp[v]) * A.nff + o] = acc1[e][v] * 0.25f;
+                }
+            }
+        }
+        __syncthreads();   // st and the face-box buffer are free again
+    }
+}
+
 // ------------------------------------------------- z flux + stage update --
 
 constexpr int kMaxPrepBoxes = 8;   // forcing boxes the fused prep can leave out
@@ -792,6 +910,7 @@ int persistent_grid(K kernel, size_t smem)
 template <typename R, typename C, int STAGE>
 struct FluxGrids {
     int flux[2] = {0, 0}, flux_update[2] = {0, 0};   // without / with the Gauss-point output
+    int flux_tall = 0;                               // FP32C: 32 x 16 face tiles
 };
 
 // The Gauss-point output (recorded steps of the adjoint) exists only where the
@@ -808,6 +927,8 @@ const FluxGrids<R, C, STAGE> &flux_grids()
             g.flux[1] = persistent_grid(face_flux_kernel<R, C, STAGE == 1, true>, flux_smem_bytes<R>());
             g.flux_update[1] = persistent_grid(flux_update_kernel<R, C, STAGE, true>, su);
         }
+        if constexpr (std::is_same<R, float>::value && std::is_same<C, float>::value)
+            g.flux_tall = persistent_grid(face_flux_tall_kernel<STAGE == 1>, flux_tall_smem_bytes());
     }
     return g;
 }
@@ -898,6 +1019,15 @@ void stage_impl(const Ctx &c)
         if constexpr (!std::is_same<R, C>::value) F.gp = nullptr;
         if (d < 2) {
             const int grid = (int)(ntiles < grids.flux[gpo] ? ntiles : grids.flux[gpo]);
+            if constexpr (std::is_same<R, float>::value && std::is_same<C, float>::value) {
+                if (!gpo) {
+                    const long nt = (long)((F.n1 + TX - 1) / TX) * ((F.n2 + TYT - 1) / TYT) * F.nf;
+                    const int gt = (int)(nt < grids.flux_tall ? nt : grids.flux_tall);
+                    face_flux_tall_kernel<STAGE == 1><<<gt, blk, flux_tall_smem_bytes(), c.stream>>>(c.tmapT[d], F);
+                    mark(c, grp, 0);
+                    continue;
+                }
+            }
             if constexpr (std::is_same<R, C>::value) {
                 if (gpo)
                     face_flux_kernel<R, C, STAGE == 1, true><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);

@@ -541,14 +541,6 @@ __global__ void __launch_bounds__(256, 2) face_flux_tall_kernel(const __grid_con
 
 constexpr int kMaxPrepBoxes = 8;   // forcing boxes the fused prep can leave out
 
-// Read-only loads and 8-byte asynchronous copies of a face-flux value.
-__device__ __forceinline__ float ldg_m(const float *p) { return __ldg(p); }
-__device__ __forceinline__ double ldg_m(const double *p) { return __ldg(p); }
-__device__ __forceinline__ dsf ldg_m(const dsf *p)
-{
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-    return dsf(v.x, v.y);
-}
 
 
 template <typename R, typename M = R>
@@ -671,10 +663,12 @@ __device__ __forceinline__ bool update_cell(const UpdArgs<R> &A, long lin, doubl
 
 constexpr int SX_H = TX + 1, SX_W = TY + 1;   // x-face slab of a tile in shared memory (padded)
 
+constexpr int SY_H = TY + 1;                  // y-face slab of a tile: the TY + 1 face rows of its cells
+
 template <typename R>
 constexpr size_t flux_update_smem_bytes(int nc)
 {
-    return flux_smem_bytes<R>() + (size_t)nc * SX_H * SX_W * sizeof(R);
+    return flux_smem_bytes<R>() + (size_t)nc * (SX_H * SX_W + SY_H * TX) * sizeof(R);
 }
 
 // z-direction face flux fused with the stage update. Work items are
@@ -685,22 +679,27 @@ constexpr size_t flux_update_smem_bytes(int nc)
 // segment's z-faces in order: F(f) - F(f-1) of the column is formed in
 // registers and cell f-1 is updated at once; the first face of an item
 // (the last face of the previous segment) only primes F. The x-face fluxes
-// of the cell plane (x-fastest reads of a y-fastest array) are copied
-// asynchronously into a padded shared slab at the start of the tile; the
-// y-face fluxes and the state are read directly (x-fastest, like the
-// threads).
+// of the cell plane (x-fastest reads of a y-fastest array) and its y-face
+// fluxes are copied asynchronously into shared slabs at the start of the
+// tile (the x slab padded against bank conflicts), so that no register waits
+// on them during the flux; the state of the thread's cell is loaded into
+// registers (nothing reads it before the update).
 struct ZWalk {
     int it, f, fe, f0;   // item, face, end face (exclusive), first (priming) face of the item
+    int a0, b0;          // first cell of the item's tile column along x, y
 };
 
-__device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int L, int nf)
+// Item it: its segment and tile column, decoded once per item (not per face).
+__device__ __forceinline__ ZWalk zwalk_item(int it, int ncol, int NA, int L, int nf)
 {
-    const int sgm = it / ncol;
+    const int sgm = it / ncol, col = it - sgm * ncol, cb = col / NA;
     ZWalk z;
     z.it = it;
     z.f0 = sgm > 0 ? sgm * L - 1 : 0;
     z.f = z.f0;
     z.fe = min((sgm + 1) * L, nf);
+    z.a0 = (col - cb * NA) * TX;
+    z.b0 = cb * TY;
     return z;
 }
 
@@ -718,21 +717,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     C *st = reinterpret_cast<C *>(sq + SQ_N);
     uint64_t *bar = reinterpret_cast<uint64_t *>(st + ST_N);
     M *sx = reinterpret_cast<M *>(bar + 2);               // [NC][SX_H][SX_W]
+    M *sy = sx + NC * SX_H * SX_W;                        // [NC][SY_H][TX]
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NA = (A.n1 + TX - 1) / TX, NB = (A.n2 + TY - 1) / TY, nf = A.nf, L = U.seg;
     const int ncol = NA * NB, nitems = ncol * ((nf + L - 1) / L);
     if ((int)blockIdx.x >= nitems) return;
     const uint32_t bytes = (uint32_t)(SQ_N * sizeof(R));
-    ZWalk cur = zwalk_item(blockIdx.x, ncol, L, nf);
+    ZWalk cur = zwalk_item(blockIdx.x, ncol, NA, L, nf);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        const int col = cur.it % ncol;
-        tma_load_tile(&tmap, sq, &bar[0], (col % NA) * TX, (col / NA) * TY, cur.f, bytes);
-    }
+    if (tid == 0) tma_load_tile(&tmap, sq, &bar[0], cur.a0, cur.b0, cur.f, bytes);
     const double dt = A.scal->dt;
     bool bad = false;
     double mx = 0.0;   // stage 2 with prep: max |U|^2 of this thread's cells outside the forcing boxes
@@ -740,37 +737,46 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                       // differences of neighbouring faces telescope exactly)
     for (int k = 0; cur.it < nitems; ++k) {
         ZWalk nxt = cur;
-        if (++nxt.f >= nxt.fe) nxt = zwalk_item(cur.it + gridDim.x, ncol, L, nf);
-        const int col = cur.it % ncol, f = cur.f;
-        const int a0 = (col % NA) * TX, b0 = (col / NA) * TY;
+        if (++nxt.f >= nxt.fe) nxt = zwalk_item(cur.it + gridDim.x, ncol, NA, L, nf);
+        const int f = cur.f, a0 = cur.a0, b0 = cur.b0;
         const bool upd = f > cur.f0;
         if (upd) {
             // x-face fluxes of cell plane z = f-1: faces a0 .. a0+32, rows b0 .. b0+7.
-            // Thread: row y = b0 + (tid & 7); slab rows r = (c, xf) = tid/8 + 32 i.
-            const int yy = tid & 7;
+            // Thread: row y = b0 + (tid & 7), face a0 + tid/8 of every component;
+            // the 8 threads with tid/8 = 0 also take face a0 + 32.
+            const int yy = tid & 7, xf = tid >> 3;
             if (b0 + yy < U.ny) {
                 const long sxf = (long)U.nz * U.ny;   // stride between x-faces
-                const M *src = U.ffx + C0 * U.nffx + ((long)a0 * U.nz + (f - 1)) * U.ny + b0 + yy;
-                int c = 0, xf = tid >> 3;
-                long go = xf * sxf;
+                const long g0 = ((long)(a0 + xf) * U.nz + (f - 1)) * U.ny + b0 + yy;
+                const M *src = U.ffx + C0 * U.nffx + g0;
+                if (a0 + xf <= U.nx && in_bounds(g0, U.nffx)) {
 #pragma unroll
-                for (int i = 0; i < (NC * SX_H + 31) / 32; ++i) {
-                    if (c < NC && a0 + xf <= U.nx &&
-                        in_bounds(((long)(a0 + xf) * U.nz + (f - 1)) * U.ny + b0 + yy, U.nffx))
-                        cp_async(sx + (c * SX_H + xf) * SX_W + yy, src + go);
-                    xf += 32;
-                    go += 32 * sxf;
-                    if (xf >= SX_H) {
-                        xf -= SX_H;
-                        ++c;
-                        go += U.nffx - SX_H * sxf;
-                    }
+                    for (int c = 0; c < NC; ++c) cp_async(sx + (c * SX_H + xf) * SX_W + yy, src + c * U.nffx);
                 }
+                if (xf == 0 && a0 + 32 <= U.nx && in_bounds(g0 + 32 * sxf, U.nffx)) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        cp_async(sx + (c * SX_H + 32) * SX_W + yy, src + c * U.nffx + 32 * sxf);
+                }
+            }
+            // y-face fluxes of the plane: faces b0 .. b0+8 along y, columns a0 .. a0+31.
+            // Thread: column a0 + tx, face row ty of every component; face row 8 of
+            // component ty.
+            if (a0 + tx < U.nx) {
+                const long g1 = ((long)(b0 + ty) * U.nz + (f - 1)) * U.nx + a0 + tx;
+                const M *src = U.ffy + C0 * U.nffy + g1;
+                if (b0 + ty <= U.ny && in_bounds(g1, U.nffy)) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cp_async(sy + (c * SY_H + ty) * TX + tx, src + c * U.nffy);
+                }
+                const long g8 = g1 + (long)(TY - ty) * U.nz * U.nx;   // face row b0 + 8
+                if (ty < NC && b0 + TY <= U.ny && in_bounds(g8, U.nffy))
+                    cp_async(sy + (ty * SY_H + TY) * TX + tx, U.ffy + (C0 + ty) * U.nffy + g8);
             }
             cp_async_commit();
         }
-        // y-face flux differences and the state of this thread's cell, loaded
-        // now so that they arrive during the flux computation
+        // the state of this thread's cell, loaded now so that it arrives
+        // during the flux computation
         const int a = a0 + tx, b = b0 + ty;
         const bool in = a < A.n1 && b < A.n2;
         // inverse widths (x, y of the flux and the update; z of the update),
@@ -781,21 +787,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             ih2 = __ldg(A.ih2 + b + G);
             if (upd) ihz = __ldg(U.ihz + f - 1 + G);
         }
-        M dy[8];
         R s0[4], s1[4];
         long lin = 0;
         bool cell_ok = true;
         if (upd && in) {
             const int z = f - 1;
             lin = (long)(a + G) + (long)U.P0 * ((long)(b + G) + (long)U.P1 * (z + G));
-            const long iy = ((long)b * U.nz + z) * U.nx + a, sy = (long)U.nz * U.nx;
-            cell_ok = in_bounds(lin, U.np) && in_bounds(iy, U.nffy) && in_bounds(iy + sy, U.nffy);
+            cell_ok = in_bounds(lin, U.np);
             if (cell_ok) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const M *py = U.ffy + (C0 + c) * U.nffy + iy;
-                    dy[C0 + c] = ldg_m(py + sy) - ldg_m(py);
-                }
                 const R *src = (const R *)(STAGE == 1 ? U.w0 : U.pbuf);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
@@ -816,8 +815,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         // the face box is free: fetch the next tile's during this one's flux
         if (tid == 0 && nxt.it < nitems) {
             fence_proxy_async();
-            const int col = nxt.it % ncol;
-            tma_load_tile(&tmap, sq, &bar[0], (col % NA) * TX, (col / NA) * TY, nxt.f, bytes);
+            tma_load_tile(&tmap, sq, &bar[0], nxt.a0, nxt.b0, nxt.f, bytes);
         }
 
         M F0[4], F1[4];
@@ -836,10 +834,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             __syncthreads();   // the x-face slab of every thread is in place
             if (in && cell_ok) {
                 const int z = f - 1;
-                M dx[8], dz[8];
+                M dx[8], dy[8], dz[8];
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
+                for (int c = 0; c < NC; ++c) {
                     dx[C0 + c] = sx[(c * SX_H + tx + 1) * SX_W + ty] - sx[(c * SX_H + tx) * SX_W + ty];
+                    dy[C0 + c] = sy[(c * SY_H + ty + 1) * TX + tx] - sy[(c * SY_H + ty) * TX + tx];
+                }
                 // local frame of a z-face: (rho, m_z, m_x, m_y); global (rho, m_x, m_y, m_z)
                 constexpr int loc[4] = {0, 2, 3, 1};
 #pragma unroll
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             }
         }
         cur = nxt;
-        __syncthreads();   // st, the face buffer and the x slab are free again
+        __syncthreads();   // st, the face buffer and the slabs are free again
     }
     if (STAGE == 2 && bad) atomicOr(&A.scal->flags, FLAG_NONFINITE);
     if (STAGE == 2 && U.prep) block_max_to(mx, &A.scal->maxu2_bits);

@@ -212,6 +212,9 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
     R nxt[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) nxt[v] = __ldg(A.w + comp[v] * A.np + base + (long)(f0 + 2 + G) * A.sd);
+    // unrolled (FP32) so that the window shifts and the carried values cost no moves
+    constexpr int UNR = std::is_same<C, float>::value ? 2 : 1;
+#pragma unroll UNR
     for (int f = f0; f < f1; ++f) {
         C Ql[4], Qr[4];
 #pragma unroll

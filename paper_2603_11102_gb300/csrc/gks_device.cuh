@@ -368,6 +368,67 @@ __device__ __forceinline__ void gk_flux(const Phys<R> &ph, const R q[4], const R
     F1[3] = rho * (A0 * (U0 * U2) + th * (A2 * U0 + An * U2));
 }
 
+// ---- Packed FP32 pairs ----
+//
+// Two independent FP32 values that go through the same arithmetic (the two
+// t1 Gauss points of a face) as one float2: the FP32x2 add, multiply and
+// fused multiply-add of sm_100 and later do both in one instruction, which
+// halves the issue slots of the arithmetic (the FP32 kernels are bound by
+// instruction issue, not by the FMA pipe). Every operation is rounded
+// explicitly, each lane exactly as its scalar counterpart (__fadd_rn,
+// __fmul_rn, __fmaf_rn); nothing is contracted implicitly.
+struct f2 {
+    float2 v;
+    f2() = default;
+    __device__ __forceinline__ f2(float2 a) : v(a) {}
+    __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit f2(float a) : v(make_float2(a, a)) {}   // both lanes
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+// a - b as a + (-1) b: the product is exact, so one rounding as in __fsub_rn
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return fma(b, f2(-1.0f), a); }
+__device__ __forceinline__ f2 &operator+=(f2 &a, f2 b) { return a = a + b; }
+// the two-instruction approximate division of the scalar FP32 path, per lane
+__device__ __forceinline__ f2 wdiv(f2 a, f2 b) { return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
+
+// gk_flux at two Gauss points at once (the closed form above, every
+// multiply-add fused explicitly). ph holds the FP32 constants.
+template <bool NEED_F0>
+__device__ __forceinline__ void gk_flux2(const Phys<float> &ph, const f2 q[4], const f2 Dn[4], const f2 D1[4],
+                                         const f2 D2[4], f2 ih1, f2 ih2, f2 F0[4], f2 F1[4])
+{
+    const f2 m1(-1.0f);
+    const f2 rho = f2(ph.off) + q[0];
+    const f2 inv = wdiv(f2(1.0f), rho), ninv = inv * m1;
+    const f2 inv1 = inv * ih1, inv2 = inv * ih2, ninv1 = ninv * ih1, ninv2 = ninv * ih2;
+    const f2 U0 = q[1] * inv, U1 = q[2] * inv, U2 = q[3] * inv;
+    // the logarithmic density slopes, negated: -d_k ln rho
+    const f2 ng0 = Dn[0] * ninv, ng1 = D1[0] * ninv1, ng2 = D2[0] * ninv2;
+    // G_ik = d_i U_k = (d_i m_k) / rho - U_k d_i ln rho
+    const f2 G00 = fma(U0, ng0, Dn[1] * inv), G01 = fma(U1, ng0, Dn[2] * inv), G02 = fma(U2, ng0, Dn[3] * inv);
+    const f2 G10 = fma(U0, ng1, D1[1] * inv1), G11 = fma(U1, ng1, D1[2] * inv1), G12 = fma(U2, ng1, D1[3] * inv1);
+    const f2 G20 = fma(U0, ng2, D2[1] * inv2), G21 = fma(U1, ng2, D2[2] * inv2), G22 = fma(U2, ng2, D2[3] * inv2);
+    const f2 th(ph.theta), ntl(-2.0f * ph.lambda);
+    // A0 = -(U.g) - (G00 + G11 + G22); A_k = -g_k - 2 lambda U_i G_ik
+    const f2 A0 = fma(U2, ng2, fma(U1, ng1, U0 * ng0)) - ((G00 + G11) + G22);
+    const f2 An = fma(ntl, fma(U2, G20, fma(U1, G10, U0 * G00)), ng0);
+    const f2 A1 = fma(ntl, fma(U2, G21, fma(U1, G11, U0 * G01)), ng1);
+    const f2 A2 = fma(ntl, fma(U2, G22, fma(U1, G12, U0 * G02)), ng2);
+    if (NEED_F0) {
+        const f2 nmu(-ph.mu), n2mu(-2.0f * ph.mu);
+        F0[0] = q[1];
+        F0[1] = fma(q[1], U0, fma(th, q[0], G00 * n2mu));
+        F0[2] = fma(q[1], U1, (G01 + G10) * nmu);
+        F0[3] = fma(q[1], U2, (G02 + G20) * nmu);
+    }
+    F1[0] = rho * fma(A0, U0, th * An);
+    F1[1] = rho * fma(A0, fma(U0, U0, th), f2(2.0f * ph.theta) * (An * U0));
+    F1[2] = rho * fma(A0, U0 * U1, th * fma(A1, U0, An * U1));
+    F1[3] = rho * fma(A0, U0 * U2, th * fma(A2, U0, An * U2));
+}
+
 constexpr int TX = 32, TY = 8;              // face tile
 constexpr int SQ_W = TX + 4, SQ_H = TY + 4; // tile with the tangential halo
 constexpr int SQ_N = 8 * SQ_H * SQ_W;

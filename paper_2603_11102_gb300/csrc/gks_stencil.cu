@@ -358,6 +358,36 @@ __device__ __forceinline__ void tile_gauss_flux(const Phys<R> &ph, const R *st, 
     }
 }
 
+// tile_gauss_flux for FP32 arithmetic: the same t2 pass, the flux at the two
+// t2 Gauss points of each t1 Gauss point as one packed evaluation.
+template <bool NEED_F0>
+__device__ __forceinline__ void tile_gauss_flux_f32(const Phys<float> &ph, const float *st, int tx, int ty, float ih1,
+                                                    float ih2, float acc0[4], float acc1[4])
+{
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc0[v] = acc1[v] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        f2 Qv[4], Dn[4], D1[4], D2[4];   // t2 Gauss points -g, +g in the lanes
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+            const float *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+            const float *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+            tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], Qv[v].v.x, Qv[v].v.y, D2[v].v.x, D2[v].v.y);
+            tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], D1[v].v.x, D1[v].v.y);
+            tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], Dn[v].v.x, Dn[v].v.y);
+        }
+        f2 F0[4], F1[4];
+        gk_flux2<NEED_F0>(ph, Qv, Dn, D1, D2, f2(ih1), f2(ih2), F0, F1);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (NEED_F0) acc0[v] += F0[v].v.x + F0[v].v.y;
+            acc1[v] += F1[v].v.x + F1[v].v.y;
+        }
+    }
+}
+
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of a tile is dead once its t1 pass is in shared memory, so the next
 // tile's face box is fetched by TMA into the same buffer while the Gauss
@@ -437,7 +467,8 @@ __device__ __forceinline__ void tile_gauss_flux_pair(const Phys<float> &ph, cons
         for (int v = 0; v < 4; ++v) acc0[e][v] = acc1[e][v] = 0.0f;
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-        float Qv[2][2][4], Dn[2][2][4], D1[2][2][4], D2[2][2][4];   // [face][t2 point][component]
+        // [face][component], the two t2 Gauss points -g, +g in the lanes of a pair
+        f2 Qv[2][4], Dn[2][4], D1[2][4], D2[2][4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float *x = st + (v * 4 + m) * ST_ROWS_T + r0 * TX + tx;
@@ -448,31 +479,29 @@ __device__ __forceinline__ void tile_gauss_flux_pair(const Phys<float> &ph, cons
             for (int i = 0; i < 6; ++i) p[i] = x[i * TX];
 #pragma unroll
             for (int e = 0; e < 2; ++e)
-                tan_val_der(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Qv[e][0][v], Qv[e][1][v], D2[e][0][v],
-                            D2[e][1][v]);
+                tan_val_der(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Qv[e][v].v.x, Qv[e][v].v.y, D2[e][v].v.x,
+                            D2[e][v].v.y);
 #pragma unroll
             for (int i = 0; i < 6; ++i) p[i] = y[i * TX];
 #pragma unroll
             for (int e = 0; e < 2; ++e)
-                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], D1[e][0][v], D1[e][1][v]);
+                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], D1[e][v].v.x, D1[e][v].v.y);
 #pragma unroll
             for (int i = 0; i < 6; ++i) p[i] = z[i * TX];
 #pragma unroll
             for (int e = 0; e < 2; ++e)
-                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Dn[e][0][v], Dn[e][1][v]);
+                tan_val_direct(p[e], p[e + 1], p[e + 2], p[e + 3], p[e + 4], Dn[e][v].v.x, Dn[e][v].v.y);
         }
 #pragma unroll
-        for (int e = 0; e < 2; ++e)
+        for (int e = 0; e < 2; ++e) {
+            f2 F0[4], F1[4];
+            gk_flux2<NEED_F0>(ph, Qv[e], Dn[e], D1[e], D2[e], f2(ih1), f2(ih2[e]), F0, F1);
 #pragma unroll
-            for (int nn = 0; nn < 2; ++nn) {
-                float F0[4], F1[4];
-                gk_flux<float, NEED_F0>(ph, Qv[e][nn], Dn[e][nn], D1[e][nn], D2[e][nn], ih1, ih2[e], F0, F1);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    if (NEED_F0) acc0[e][v] += F0[v];
-                    acc1[e][v] += F1[v];
-                }
+            for (int v = 0; v < 4; ++v) {
+                if (NEED_F0) acc0[e][v] += F0[v].v.x + F0[v].v.y;
+                acc1[e][v] += F1[v].v.x + F1[v].v.y;
             }
+        }
     }
 }
 
@@ -824,8 +853,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         M F0[4], F1[4];
         if (in) {
             C G0[4], G1[4];
-            tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, cvt<C>(ih1), cvt<C>(ih2), G0, G1, A.gp, A.gp32,
-                                            A.ngp, ((long)f * A.n2 + b) * A.n1 + a);
+            if constexpr (std::is_same<C, float>::value && !GP)
+                tile_gauss_flux_f32<NEED_F0>(A.ph, st, tx, ty, ih1, ih2, G0, G1);
+            else
+                tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, cvt<C>(ih1), cvt<C>(ih2), G0, G1, A.gp, A.gp32,
+                                                A.ngp, ((long)f * A.n2 + b) * A.n1 + a);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 F0[v] = NEED_F0 ? quarter<M>(G0[v]) : M(0);

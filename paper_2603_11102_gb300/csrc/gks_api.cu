@@ -129,8 +129,9 @@ void plan(const gks_grid_desc *d, Layout *L)
         const long nfq = (long)(d->n[a] + 1) * (d->n[t2] + 4) * L->e1p[a];
         if (nfq > L->nfq) L->nfq = nfq;
         // face fluxes are kept for x and y only: the z-face kernel applies
-        // the stage update itself
-        L->nff[a] = a == 2 ? 0 : (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
+        // the stage update itself (FP64 grids keep the z faces too, for the
+        // separate update of their double-single arithmetic)
+        L->nff[a] = a == 2 && d->precision != GKS_FP64 ? 0 : (long)(d->n[a] + 1) * d->n[t1] * d->n[t2];
     }
     L->nfq = (L->nfq + 63) / 64 * 64;
     size_t o = 0;

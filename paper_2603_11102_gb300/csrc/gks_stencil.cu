@@ -579,6 +579,9 @@ template <typename R, typename M = R>
 struct UpdArgs {
     const M *ffx, *ffy;   // face fluxes of the x and y directions (8 arrays each)
     long nffx, nffy;
+    const M *ffz;         // z face fluxes (the separate update of double-single FP64 grids)
+    long nffz;
+    const R *ihx, *ihy;   // inverse cell widths along x, y (separate update)
     const R *ihz;         // inverse cell widths along z (padded index)
     int nx, ny, nz, P0, P1;
     long np;
@@ -918,6 +921,74 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 }
 
 
+// Stage update of every cell from stored x, y and z face fluxes, for FP64
+// grids in double-single arithmetic: there the fused z kernel needs about 220
+// registers (one block per SM) while the face-flux kernel runs two blocks per
+// SM, so the z faces go through face_flux_kernel into their own buffer and
+// this kernel applies update_cell_ds (the same operations as the fused
+// kernel, the same bits). One thread per cell of a 32 x 8 x 1 block; the
+// x-face fluxes of the block's cells (y-fastest) arrive through a padded
+// shared slab.
+template <int STAGE>
+__global__ void __launch_bounds__(256) update_ds_kernel(UpdArgs<double, dsf> U, Scalars *scal)
+{
+    constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
+    __shared__ dsf sx[NC][SX_H][SX_W];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int a0 = blockIdx.x * TX, b0 = blockIdx.y * TY, z = blockIdx.z;
+    {
+        // x faces a0 .. a0+32 of rows b0 .. b0+7: thread row b0 + (tid & 7),
+        // face a0 + tid/8; the 8 threads with tid/8 = 0 also take face a0 + 32
+        const int yy = tid & 7, xf = tid >> 3;
+        if (b0 + yy < U.ny) {
+            const long sxf = (long)U.nz * U.ny;
+            const long g0 = ((long)(a0 + xf) * U.nz + z) * U.ny + b0 + yy;
+            if (a0 + xf <= U.nx && in_bounds(g0, U.nffx)) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sx[c][xf][yy] = U.ffx[(C0 + c) * U.nffx + g0];
+            }
+            if (xf == 0 && a0 + 32 <= U.nx && in_bounds(g0 + 32 * sxf, U.nffx)) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sx[c][32][yy] = U.ffx[(C0 + c) * U.nffx + g0 + 32 * sxf];
+            }
+        }
+    }
+    __syncthreads();
+    const int a = a0 + tx, b = b0 + ty;
+    bool bad = false;
+    double mx = 0.0;
+    if (a < U.nx && b < U.ny) {
+        const long lin = (long)(a + G) + (long)U.P0 * ((long)(b + G) + (long)U.P1 * (z + G));
+        const long iy = ((long)b * U.nz + z) * U.nx + a, sy = (long)U.nz * U.nx;
+        const long iz = ((long)z * U.ny + b) * U.nx + a, sz = (long)U.ny * U.nx;
+        if (in_bounds(lin, U.np) && in_bounds(iy + sy, U.nffy) && in_bounds(iz + sz, U.nffz)) {
+            dsf dx[8], dy[8], dz[8];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int k = C0 + c;
+                dx[k] = sx[c][tx + 1][ty] - sx[c][tx][ty];
+                dy[k] = U.ffy[k * U.nffy + iy + sy] - U.ffy[k * U.nffy + iy];
+                dz[k] = U.ffz[k * U.nffz + iz + sz] - U.ffz[k * U.nffz + iz];
+            }
+            const double *src = (const double *)(STAGE == 1 ? U.w0 : U.pbuf);
+            double s0[4], o0[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) s0[v] = src[v * U.np + lin];
+            bad = !update_cell_ds<STAGE>(U, lin, scal->dt, dx, dy, dz, to_ds(__ldg(U.ihx + a + G)),
+                                         to_ds(__ldg(U.ihy + b + G)), to_ds(__ldg(U.ihz + z + G)), s0, o0);
+            if (STAGE == 2 && U.prep) {
+                bool boxed = false;
+                for (int q = 0; q < U.nbox; ++q)
+                    boxed |= a >= U.box[q][0][0] && a <= U.box[q][0][1] && b >= U.box[q][1][0] &&
+                             b <= U.box[q][1][1] && z >= U.box[q][2][0] && z <= U.box[q][2][1];
+                if (!boxed) mx = max_u2(mx, cell_u2(o0));
+            }
+        }
+    }
+    if (STAGE == 2 && bad) atomicOr(&scal->flags, FLAG_NONFINITE);
+    if (STAGE == 2 && U.prep) block_max_to(mx, &scal->maxu2_bits);
+}
+
 // Faces per thread of the marching face-state kernel: kMarch, halved (down
 // to 4) while the launch would have fewer than two blocks per SM, so that a
 // small grid spreads its march over the GPU (each halving adds one WENO5 pair
@@ -957,7 +1028,8 @@ const FluxGrids<R, C, STAGE> &flux_grids()
     if (!g.flux[0]) {
         constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
         g.flux[0] = persistent_grid(face_flux_kernel<R, C, STAGE == 1, false>, flux_smem_bytes<R>());
-        g.flux_update[0] = persistent_grid(flux_update_kernel<R, C, STAGE, false>, su);
+        if constexpr (!std::is_same<C, dsf>::value)   // double-single: separate z update
+            g.flux_update[0] = persistent_grid(flux_update_kernel<R, C, STAGE, false>, su);
         if constexpr (std::is_same<R, C>::value) {
             g.flux[1] = persistent_grid(face_flux_kernel<R, C, STAGE == 1, true>, flux_smem_bytes<R>());
             g.flux_update[1] = persistent_grid(flux_update_kernel<R, C, STAGE, true>, su);
@@ -1014,6 +1086,42 @@ FaceEqArgs<R, C> face_eq_args(const Ctx &c, int d, const R *w, const Phys<C> &ph
     return E;
 }
 
+// Arguments of the stage update of the z-face kernels (the fused one and the
+// separate double-single one).
+template <typename R, typename C, int STAGE>
+UpdArgs<R, Mid<R, C>> update_args(const Ctx &c, const FluxArgs<R, C> &F)
+{
+    UpdArgs<R, Mid<R, C>> U;
+    U.ffx = (const Mid<R, C> *)c.ff[0];
+    U.ffy = (const Mid<R, C> *)c.ff[1];
+    U.nffx = c.nff[0];
+    U.nffy = c.nff[1];
+    U.ffz = nullptr;
+    U.nffz = 0;
+    U.ihx = U.ihy = nullptr;
+    U.ihz = (const R *)c.ih[2];
+    U.nx = c.n[0];
+    U.ny = c.n[1];
+    U.nz = c.n[2];
+    U.P0 = c.P[0];
+    U.P1 = c.P[1];
+    U.np = c.np;
+    U.w0 = c.state;
+    U.wk1 = c.wk1;
+    U.pbuf = c.pbuf;
+    U.state = c.state;
+    U.off = (R)c.off;
+    for (int a = 0; a < 3; ++a) U.fb[a] = (R)c.fbody[a];
+    U.seg = 0;
+    U.prep = STAGE == 2 && c.prep_next && c.nprep_box <= kMaxPrepBoxes;
+    U.wk0n = c.prec == GKS_FP32C ? (float *)c.wk0 : nullptr;
+    U.nbox = U.prep ? c.nprep_box : 0;
+    for (int q = 0; q < U.nbox; ++q)
+        for (int e = 0; e < 3; ++e)
+            for (int k = 0; k < 2; ++k) U.box[q][e][k] = c.prep_box[q][e][k];
+    return U;
+}
+
 template <typename R, typename C, int STAGE>
 void stage_impl(const Ctx &c)
 {
@@ -1052,6 +1160,22 @@ void stage_impl(const Ctx &c)
         mark(c, grp, 1);
         const int gpo = F.gp != nullptr;
         if constexpr (!std::is_same<R, C>::value) F.gp = nullptr;
+        if constexpr (std::is_same<C, dsf>::value) {
+            if (d == 2) {
+                // double-single: z-face fluxes into their own buffer, then the update
+                const int grid = (int)(ntiles < grids.flux[0] ? ntiles : grids.flux[0]);
+                face_flux_kernel<R, C, STAGE == 1, false><<<grid, blk, flux_smem_bytes<R>(), c.stream>>>(tmap, F);
+                UpdArgs<R, Mid<R, C>> U = update_args<R, C, STAGE>(c, F);
+                U.ffz = (const Mid<R, C> *)c.ff[2];
+                U.nffz = c.nff[2];
+                U.ihx = (const R *)c.ih[0];
+                U.ihy = (const R *)c.ih[1];
+                const dim3 gu((c.n[0] + TX - 1) / TX, (c.n[1] + TY - 1) / TY, c.n[2]);
+                update_ds_kernel<STAGE><<<gu, blk, 0, c.stream>>>(U, c.scal);
+                mark(c, grp, 0);
+                continue;
+            }
+        }
         if (d < 2) {
             const int grid = (int)(ntiles < grids.flux[gpo] ? ntiles : grids.flux[gpo]);
             if constexpr (std::is_same<R, float>::value && std::is_same<C, float>::value) {
@@ -1073,32 +1197,9 @@ void stage_impl(const Ctx &c)
             }
         } else {
             // z faces: flux and the stage update of every cell
-            UpdArgs<R, Mid<R, C>> U;
-            U.ffx = (const Mid<R, C> *)c.ff[0];
-            U.ffy = (const Mid<R, C> *)c.ff[1];
-            U.nffx = c.nff[0];
-            U.nffy = c.nff[1];
-            U.ihz = (const R *)c.ih[2];
-            U.nx = c.n[0];
-            U.ny = c.n[1];
-            U.nz = c.n[2];
-            U.P0 = c.P[0];
-            U.P1 = c.P[1];
-            U.np = c.np;
-            U.w0 = c.state;
-            U.wk1 = c.wk1;
-            U.pbuf = c.pbuf;
-            U.state = c.state;
-            U.off = (R)c.off;
-            for (int a = 0; a < 3; ++a) U.fb[a] = (R)c.fbody[a];
+            UpdArgs<R, Mid<R, C>> U = update_args<R, C, STAGE>(c, F);
             const int ncol = ((F.n1 + TX - 1) / TX) * ((F.n2 + TY - 1) / TY);
             U.seg = z_segment(ncol, F.nf, grids.flux_update[gpo]);
-            U.prep = STAGE == 2 && c.prep_next && c.nprep_box <= kMaxPrepBoxes;
-            U.wk0n = c.prec == GKS_FP32C ? (float *)c.wk0 : nullptr;
-            U.nbox = U.prep ? c.nprep_box : 0;
-            for (int q = 0; q < U.nbox; ++q)
-                for (int e = 0; e < 3; ++e)
-                    for (int f2 = 0; f2 < 2; ++f2) U.box[q][e][f2] = c.prep_box[q][e][f2];
             const long nitems = (long)ncol * ((F.nf + U.seg - 1) / U.seg);
             const int grid = (int)(nitems < grids.flux_update[gpo] ? nitems : grids.flux_update[gpo]);
             constexpr size_t su = flux_update_smem_bytes<R>(STAGE == 1 ? 8 : 4);
@@ -1107,8 +1208,6 @@ void stage_impl(const Ctx &c)
                     flux_update_kernel<R, C, STAGE, true><<<grid, blk, su, c.stream>>>(tmap, F, U);
                 else
                     flux_update_kernel<R, C, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
-            } else {
-                flux_update_kernel<R, C, STAGE, false><<<grid, blk, su, c.stream>>>(tmap, F, U);
             }
         }
         mark(c, grp, 0);

@@ -393,6 +393,88 @@ __device__ __forceinline__ f2 &operator+=(f2 &a, f2 b) { return a = a + b; }
 // the two-instruction approximate division of the scalar FP32 path, per lane
 __device__ __forceinline__ f2 wdiv(f2 a, f2 b) { return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
 
+// Two double-single values side by side (hi and lo parts as packed pairs):
+// every operation is lane by lane the double-single operation of gks_ds.cuh
+// (the same FP32 operations in the same order, so the same bits), with one
+// packed instruction doing both lanes. Used for the flux of double-single
+// grids at two Gauss points at once.
+struct dsf2 {
+    f2 hi, lo;
+    dsf2() = default;
+    __device__ __forceinline__ dsf2(f2 h, f2 l) : hi(h), lo(l) {}
+    __device__ __forceinline__ dsf2(dsf a, dsf b) : hi(a.hi, b.hi), lo(a.lo, b.lo) {}
+    __device__ __forceinline__ explicit dsf2(dsf a) : hi(a.hi), lo(a.lo) {}           // both lanes
+    __device__ __forceinline__ explicit dsf2(double x) : dsf2(dsf(x)) {}
+    __device__ __forceinline__ explicit dsf2(int x) : dsf2(dsf(x)) {}
+    __device__ __forceinline__ dsf lane(int k) const
+    {
+        return k == 0 ? dsf(hi.v.x, lo.v.x) : dsf(hi.v.y, lo.v.y);
+    }
+};
+__device__ __forceinline__ dsf2 two_sum(f2 a, f2 b)
+{
+    const f2 s = a + b;
+    const f2 bb = s - a;
+    return dsf2(s, (a - (s - bb)) + (b - bb));
+}
+// two_sum(a, -b): the same bits, with the negations folded into exact
+// subtractions
+__device__ __forceinline__ dsf2 two_diff(f2 a, f2 b)
+{
+    const f2 s = a - b;
+    const f2 bb = s - a;
+    return dsf2(s, (a - (s - bb)) - (b + bb));
+}
+__device__ __forceinline__ dsf2 fast_two_sum(f2 a, f2 b)
+{
+    const f2 s = a + b;
+    return dsf2(s, b - (s - a));
+}
+__device__ __forceinline__ dsf2 operator+(dsf2 a, dsf2 b)
+{
+    dsf2 s = two_sum(a.hi, b.hi);
+    const dsf2 t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ dsf2 operator-(dsf2 a, dsf2 b)
+{
+    dsf2 s = two_diff(a.hi, b.hi);
+    const dsf2 t = two_diff(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ dsf2 operator-(dsf2 a) { return dsf2(a.hi * f2(-1.0f), a.lo * f2(-1.0f)); }
+__device__ __forceinline__ dsf2 operator*(dsf2 a, dsf2 b)
+{
+    const f2 p = a.hi * b.hi;
+    f2 e = fma(a.hi, b.hi, p * f2(-1.0f));
+    e = fma(a.hi, b.lo, e);
+    e = fma(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dsf2 operator/(dsf2 a, dsf2 b)
+{
+    const f2 q1(__fdiv_rn(a.hi.v.x, b.hi.v.x), __fdiv_rn(a.hi.v.y, b.hi.v.y));
+    const dsf2 r = a - b * dsf2(q1, f2(0.0f));
+    const f2 q2(__fdiv_rn(r.hi.v.x, b.hi.v.x), __fdiv_rn(r.hi.v.y, b.hi.v.y));
+    return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ dsf2 &operator+=(dsf2 &a, dsf2 b) { return a = a + b; }
+__device__ __forceinline__ dsf2 wdiv(dsf2 a, dsf2 b) { return a / b; }
+
+__device__ __forceinline__ Phys<dsf2> pair_phys(const Phys<dsf> &p)
+{
+    Phys<dsf2> q;
+    q.lambda = dsf2(p.lambda);
+    q.theta = dsf2(p.theta);
+    q.mu = dsf2(p.mu);
+    q.off = dsf2(p.off);
+    q.sqlam = dsf2(p.sqlam);
+    q.kE = dsf2(p.kE);
+    return q;
+}
+
 // gk_flux at two Gauss points at once (the closed form above, every
 // multiply-add fused explicitly). ph holds the FP32 constants.
 template <bool NEED_F0>

@@ -388,12 +388,52 @@ __device__ __forceinline__ void tile_gauss_flux_f32(const Phys<float> &ph, const
     }
 }
 
+// tile_gauss_flux for double-single arithmetic (no Gauss-point output): the
+// same t2 pass, the flux at the two t2 Gauss points of each t1 Gauss point
+// as one evaluation on packed double-single pairs, summed in the same order
+// (the same bits).
+template <bool NEED_F0>
+__device__ __forceinline__ void tile_gauss_flux_ds2(const Phys<dsf> &ph, const Phys<dsf2> &ph2, const dsf *st, int tx,
+                                                    int ty, dsf ih1, dsf ih2, dsf acc0[4], dsf acc1[4])
+{
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc0[v] = acc1[v] = dsf(0);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        dsf2 Qv[4], Dn[4], D1[4], D2[4];   // t2 Gauss points -g, +g in the lanes
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const dsf *x = st + (v * 4 + m) * ST_ROWS + ty * TX + tx;
+            const dsf *y = st + (v * 4 + 2 + m) * ST_ROWS + ty * TX + tx;
+            const dsf *z = st + (16 + v * 2 + m) * ST_ROWS + ty * TX + tx;
+            dsf vm, vp, dm, dp;
+            tan_val_der(x[0], x[TX], x[2 * TX], x[3 * TX], x[4 * TX], vm, vp, dm, dp);
+            Qv[v] = dsf2(vm, vp);
+            D2[v] = dsf2(dm, dp);
+            tan_val_direct(y[0], y[TX], y[2 * TX], y[3 * TX], y[4 * TX], vm, vp);
+            D1[v] = dsf2(vm, vp);
+            tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
+            Dn[v] = dsf2(vm, vp);
+        }
+        dsf2 F0[4], F1[4];
+        gk_flux<dsf2, NEED_F0>(ph2, Qv, Dn, D1, D2, dsf2(ih1), dsf2(ih2), F0, F1);
+#pragma unroll
+        for (int nn = 0; nn < 2; ++nn)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (NEED_F0) acc0[v] += F0[v].lane(nn);
+                acc1[v] += F1[v].lane(nn);
+            }
+    }
+}
+
 // Persistent: each block walks tiles blockIdx.x, +gridDim.x, ...; the face
 // box of a tile is dead once its t1 pass is in shared memory, so the next
 // tile's face box is fetched by TMA into the same buffer while the Gauss
 // points of the current one are computed (one buffer: more blocks per SM).
 template <typename R, typename C, bool NEED_F0, bool GP>
-__global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A)
+__global__ void __launch_bounds__(256, std::is_same<C, dsf>::value ? 2 : 1)
+    face_flux_kernel(const __grid_constant__ CUtensorMap tmap, FluxArgs<R, C> A)
 {
     static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
     using M = Mid<R, C>;
@@ -440,7 +480,10 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const __grid_constant__ 
             const C ih1 = cvt<C>(__ldg(A.ih1 + a + G)), ih2 = cvt<C>(__ldg(A.ih2 + b + G));
             C acc0[4], acc1[4];
             const long o = ((long)f * A.n2 + b) * A.n1 + a;
-            tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
+            if constexpr (std::is_same<C, dsf>::value && !GP)
+                tile_gauss_flux_ds2<NEED_F0>(A.ph, pair_phys(A.ph), st, tx, ty, ih1, ih2, acc0, acc1);
+            else
+                tile_gauss_flux<C, NEED_F0, GP>(A.ph, st, tx, ty, ih1, ih2, acc0, acc1, A.gp, A.gp32, A.ngp, o);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (!in_bounds(o, A.nff)) break;

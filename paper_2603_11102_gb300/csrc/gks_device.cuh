@@ -463,6 +463,74 @@ __device__ __forceinline__ dsf2 operator/(dsf2 a, dsf2 b)
 __device__ __forceinline__ dsf2 &operator+=(dsf2 &a, dsf2 b) { return a = a + b; }
 __device__ __forceinline__ dsf2 wdiv(dsf2 a, dsf2 b) { return a / b; }
 
+__device__ __forceinline__ dsf2 &operator*=(dsf2 &a, dsf2 b) { return a = a * b; }
+__device__ __forceinline__ dsf2 fma(dsf2 a, dsf2 b, dsf2 c) { return a * b + c; }
+
+// half_space_terms of two double-single arguments: the series of both lanes
+// as pairs when both lie in |z| <= 1/2, else lane by lane (the same bits as
+// the scalar double-single version either way).
+__device__ __forceinline__ void half_space_terms(dsf2 z, dsf2 &e, dsf2 &m1, dsf2 &ex)
+{
+    if (fabsf(z.hi.v.x) <= 0.5f && fabsf(z.hi.v.y) <= 0.5f) {
+        const dsf2 t = z * z, x = -t;
+        constexpr double k = 1.1283791670955126;   // 2 / sqrt(pi)
+        dsf2 p = dsf2(k / (479001600.0 * 25.0));
+        p = fma(p, t, dsf2(-k / (39916800.0 * 23.0)));
+        p = fma(p, t, dsf2(k / (3628800.0 * 21.0)));
+        p = fma(p, t, dsf2(-k / (362880.0 * 19.0)));
+        p = fma(p, t, dsf2(k / (40320.0 * 17.0)));
+        p = fma(p, t, dsf2(-k / (5040.0 * 15.0)));
+        p = fma(p, t, dsf2(k / (720.0 * 13.0)));
+        p = fma(p, t, dsf2(-k / (120.0 * 11.0)));
+        p = fma(p, t, dsf2(k / (24.0 * 9.0)));
+        p = fma(p, t, dsf2(-k / (6.0 * 7.0)));
+        p = fma(p, t, dsf2(k / (2.0 * 5.0)));
+        p = fma(p, t, dsf2(-k / 3.0));
+        p = fma(p, t, dsf2(k));
+        e = p * z;
+        dsf2 q = dsf2(1.0 / 6227020800.0);   // 1/13!
+        q = fma(q, x, dsf2(1.0 / 479001600.0));
+        q = fma(q, x, dsf2(1.0 / 39916800.0));
+        q = fma(q, x, dsf2(1.0 / 3628800.0));
+        q = fma(q, x, dsf2(1.0 / 362880.0));
+        q = fma(q, x, dsf2(1.0 / 40320.0));
+        q = fma(q, x, dsf2(1.0 / 5040.0));
+        q = fma(q, x, dsf2(1.0 / 720.0));
+        q = fma(q, x, dsf2(1.0 / 120.0));
+        q = fma(q, x, dsf2(1.0 / 24.0));
+        q = fma(q, x, dsf2(1.0 / 6.0));
+        q = fma(q, x, dsf2(0.5));
+        q = fma(q, x, dsf2(1.0));
+        m1 = q * x;
+        ex = dsf2(1.0) + m1;
+    } else {
+        dsf e0, e1, m0, m1_, x0, x1;
+        half_space_terms(z.lane(0), e0, m0, x0);
+        half_space_terms(z.lane(1), e1, m1_, x1);
+        e = dsf2(e0, e1);
+        m1 = dsf2(m0, m1_);
+        ex = dsf2(x0, x1);
+    }
+}
+
+// face_equilibrium in double-single with the left and right half-space terms
+// evaluated as one pair (the same bits as face_equilibrium<dsf>).
+__device__ __forceinline__ void face_equilibrium_ds2(const Phys<dsf> &ph, const dsf Ql[4], const dsf Qr[4], dsf Q0[4])
+{
+    const dsf2 r = dsf2(ph.off) + dsf2(Ql[0], Qr[0]);
+    const dsf2 U = wdiv(dsf2(Ql[1], Qr[1]), r);
+    dsf2 e, m1, x;
+    half_space_terms(dsf2(ph.sqlam) * U, e, m1, x);
+    const dsf el = e.lane(0), er = e.lane(1), ml = m1.lane(0), mr = m1.lane(1);
+    const dsf Pl = dsf(0.5) + dsf(0.5) * el;   // <u^0>_{u>0} of the left state
+    const dsf Pr = dsf(0.5) - dsf(0.5) * er;   // <u^0>_{u<0} of the right state
+    const dsf El = ph.kE * x.lane(0), Er = ph.kE * x.lane(1);
+    Q0[0] = Ql[0] * Pl + Qr[0] * Pr + ph.off * (dsf(0.5) * (el - er));
+    Q0[1] = Ql[1] * Pl + Qr[1] * Pr + (Ql[0] * El - Qr[0] * Er) + ph.off * (ph.kE * (ml - mr));
+    Q0[2] = Ql[2] * Pl + Qr[2] * Pr;
+    Q0[3] = Ql[3] * Pl + Qr[3] * Pr;
+}
+
 __device__ __forceinline__ Phys<dsf2> pair_phys(const Phys<dsf> &p)
 {
     Phys<dsf2> q;

@@ -246,6 +246,82 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
     }
 }
 
+// face_eq_march_kernel for FP64 grids in double-single arithmetic on packed
+// pairs: WENO5 of the components paired as (rho, m_n) and (m_t1, m_t2), the
+// half-space terms of the left and right states as one pair, the normal
+// slopes paired like the components. Every lane takes the operations of the
+// scalar double-single kernel, so the face boxes have the same bits.
+__global__ void __launch_bounds__(256, 2) face_eq_ds2_kernel(FaceEqArgs<double, dsf> A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
+    const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f0 = blockIdx.z * A.K;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= A.nf) return;
+    const int f1 = min(f0 + A.K, A.nf);
+    const long base = (long)(a + G) * A.s1 + (long)(b + G) * A.s2;   // cell index along d = -G
+    // cells f0-3 .. f1+1 are read, faces f0 .. f1-1 written
+    if (!in_bounds(base + (long)(f0 - 3 + G) * A.sd, A.np) || !in_bounds(base + (long)(f1 + 1 + G) * A.sd, A.np) ||
+        !in_bounds(((long)f0 * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
+    const double *pc[4] = {A.w + base, A.w + (long)A.cn * A.np + base, A.w + (long)A.c1 * A.np + base,
+                           A.w + (long)A.c2 * A.np + base};
+    // window w[p][k] = cell (c - 2 + k) of component pair p; start with c = f0 - 1
+    dsf2 w[2][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const long o = (long)(f0 - 3 + k + G) * A.sd;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) w[q][k] = dsf2(to_ds(__ldg(pc[2 * q] + o)), to_ds(__ldg(pc[2 * q + 1] + o)));
+    }
+    dsf2 Qprev[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        dsf2 l;
+        weno5_pair(w[q], Qprev[q], l);
+    }
+    // the cell entering the window, loaded one face ahead
+    double nxt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) nxt[v] = __ldg(pc[v] + (long)(f0 + 2 + G) * A.sd);
+    for (int f = f0; f < f1; ++f) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[q][k] = w[q][k + 1];
+            w[q][4] = dsf2(to_ds(nxt[2 * q]), to_ds(nxt[2 * q + 1]));
+        }
+        if (f + 1 < f1) {
+            // cell f + 3 <= nf + 1 = n + 2: inside the ghost layers
+#pragma unroll
+            for (int v = 0; v < 4; ++v) nxt[v] = __ldg(pc[v] + (long)(f + 3 + G) * A.sd);
+        }
+        dsf Ql[4], Qr[4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            Ql[2 * q] = Qprev[q].lane(0);
+            Ql[2 * q + 1] = Qprev[q].lane(1);
+            dsf2 r;
+            weno5_pair(w[q], Qprev[q], r);
+            Qr[2 * q] = r.lane(0);
+            Qr[2 * q + 1] = r.lane(1);
+        }
+        dsf Q0[4];
+        face_equilibrium_ds2(A.ph, Ql, Qr, Q0);
+        const dsf2 s(to_ds(A.ihf[f]) * dsf(1.0 / 12.0));
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            // cells f-2 .. f+1 are w[q][0..3]
+            const dsf2 dq = (dsf2(15) * (w[q][2] - w[q][1]) - (w[q][3] - w[q][0])) * s;
+            A.fq[(2 * q) * A.nfq + o] = Q0[2 * q];
+            A.fq[(2 * q + 1) * A.nfq + o] = Q0[2 * q + 1];
+            A.fq[(4 + 2 * q) * A.nfq + o] = dq.lane(0);
+            A.fq[(5 + 2 * q) * A.nfq + o] = dq.lane(1);
+        }
+    }
+}
+
 // ------------------------------------------------------------- face flux --
 
 template <typename R, typename C = R>
@@ -1178,7 +1254,10 @@ void stage_impl(const Ctx &c)
         const CUtensorMap &tmap = c.tmap[d];
         dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
         mark(c, K_FACE_EQ, 1);
-        face_eq_march_kernel<R, C><<<ge, blk, 0, c.stream>>>(E);
+        if constexpr (std::is_same<C, dsf>::value)
+            face_eq_ds2_kernel<<<ge, blk, 0, c.stream>>>(E);
+        else
+            face_eq_march_kernel<R, C><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);
 
         FluxArgs<R, C> F;

@@ -410,16 +410,17 @@ int gks_diagnostics_noalloc(const double *d_state, int nx, int ny, int nz, const
 
 /* gks_alu_peak_probe: a measurement aid with no counterpart in the paper.
  * Launches, asynchronously on stream, a loop of independent fused multiply-
- * adds (FP64 when fp64 != 0, else FP32) over 4 blocks of 256 threads per SM,
- * each thread doing iters x 128 FMAs, and writes to *flops the operations of
- * that launch (2 per FMA). Timed with CUDA events on the same stream, the
- * ratio is the arithmetic peak the stencil kernels' ALU roofline is measured
- * against.
+ * adds over 4 blocks of 256 threads per SM, each thread doing iters x 128
+ * FMAs, and writes to *flops the operations of that launch (2 per FMA).
+ *   kind    0: FP32 FMAs; 1: FP64 FMAs; 2: FP32 FMAs as packed pairs (two
+ *           lanes per FFMA2 instruction, the form of the packed stencil code).
+ * Timed with CUDA events on the same stream, the ratio is the arithmetic peak
+ * the stencil kernels' ALU roofline is measured against.
  *   d_sink  device buffer of at least 4 x (number of SMs) doubles; nothing is
  *           written to it in practice (it keeps the loop's result alive).
- * Returns GKS_ERR_ARG for null pointers or iters < 1, GKS_ERR_CUDA if the
- * launch fails. */
-int gks_alu_peak_probe(int fp64, long iters, void *d_sink, void *stream, double *flops);
+ * Returns GKS_ERR_ARG for null pointers, iters < 1 or another kind,
+ * GKS_ERR_CUDA if the launch fails. */
+int gks_alu_peak_probe(int kind, long iters, void *d_sink, void *stream, double *flops);
 
 #ifdef __cplusplus
 }

@@ -471,13 +471,14 @@ class Grid:
         return list(out)
 
 
-def alu_peak_probe(fp64: bool, iters: int, sink, stream) -> float:
+def alu_peak_probe(kind, iters: int, sink, stream) -> float:
     """Launch the FMA-loop peak probe of the library on stream (async); sink
-    is a device tensor of at least 4 x SMs doubles. Returns the FP32 (or FP64)
-    operations of that launch; time it with CUDA events on the same stream."""
+    is a device tensor of at least 4 x SMs doubles. kind: False / 0 FP32,
+    True / 1 FP64, 2 FP32 packed pairs. Returns the operations of that
+    launch; time it with CUDA events on the same stream."""
     load()
     out = C.c_double(0.0)
-    rc = lib.gks_alu_peak_probe(int(bool(fp64)), int(iters), C.c_void_p(sink.data_ptr()),
+    rc = lib.gks_alu_peak_probe(int(kind), int(iters), C.c_void_p(sink.data_ptr()),
                                 C.c_void_p(stream.cuda_stream), C.byref(out))
     if rc != GKS_OK:
         raise GKSError(rc, lib.gks_last_error(None).decode())

@@ -206,4 +206,10 @@ def test_alu_peak_probe_counts_its_operations(gks):
     assert 0.3 * nominal <= rate32 <= 1.05 * nominal, (rate32, nominal)
     fl64, t64 = timed(True, 2000)
     assert fl64 / t64 / 1e12 < 0.5 * rate32
+    # packed FP32 pairs: the same operations per launch, half the
+    # instructions; the FMA pipes stay the bound (no more than the nominal
+    # FP32 rate)
+    fl2x, t2x = timed(2, 40000)
+    assert fl2x == fl2
+    assert 0.3 * nominal <= fl2x / t2x / 1e12 <= 1.05 * nominal, (fl2x / t2x / 1e12, nominal)
     assert not torch.any(sink != 0)   # the loop's results stay in registers

@@ -99,8 +99,9 @@ __device__ __forceinline__ void gk_flux_rev(const Phys<T> &ph, const T q[4], con
     T A[3];
     for (int k = 0; k < 3; ++k) A[k] = -g[k] - tl * (U[0] * Gm[0][k] + U[1] * Gm[1][k] + U[2] * Gm[2][k]);
 
-    T rhob = T(0.0), Ub[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, Gb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    T A0b = T(0.0), Ab[3] = {0, 0, 0}, qd[4] = {0, 0, 0, 0};
+    const T z0 = T(0.0);
+    T rhob = z0, Ub[3] = {z0, z0, z0}, gb[3] = {z0, z0, z0}, Gb[3][3] = {{z0, z0, z0}, {z0, z0, z0}, {z0, z0, z0}};
+    T A0b = z0, Ab[3] = {z0, z0, z0}, qd[4] = {z0, z0, z0, z0};
     // F1[0] = rho (A0 U0 + th A_0)
     {
         const T T0 = A0 * U[0] + th * A[0];
@@ -151,8 +152,8 @@ __device__ __forceinline__ void gk_flux_rev(const Phys<T> &ph, const T q[4], con
         gb[i] -= A0b * U[i];
         Gb[i][i] -= A0b;
     }
-    T Db[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    T invb[3] = {0, 0, 0};
+    T Db[3][4] = {{z0, z0, z0, z0}, {z0, z0, z0, z0}, {z0, z0, z0, z0}};
+    T invb[3] = {z0, z0, z0};
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) {
             Db[i][j + 1] += Gb[i][j] * invi[i];
@@ -1001,18 +1002,37 @@ __global__ void __launch_bounds__(256, 2) rev_tile32_kernel(const __grid_constan
                     tan_val_direct(z[0], z[TX], z[2 * TX], z[3 * TX], z[4 * TX], vm, vp);
                     Dn[0][v] = vm; Dn[1][v] = vp;
                 }
-#pragma unroll
-                for (int nn = 0; nn < 2; ++nn) {
-                    float qb[4], Dnb[4], D1b[4], D2b[4];
-                    gk_flux_rev<float>(A.ph, Qv[nn], Dn[nn], D1[nn], D2[nn], ih1, ih2, sF0, sF1, needF0, qb, Dnb,
-                                       D1b, D2b);
-                    float *gp = ga + (16 * (2 * m + nn)) * (TX * TY) + tid;
+                // the flux reverse at the two t2 Gauss points as one evaluation on
+                // packed FP32 pairs (the points in the lanes)
+                {
+                    f2 q2[4], n2[4], a2[4], b2[4], s0[4], s1[4], qb[4], Dnb[4], D1b[4], D2b[4];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        gp[v * (TX * TY)] = qb[v];
-                        gp[(4 + v) * (TX * TY)] = Dnb[v];
-                        gp[(8 + v) * (TX * TY)] = D1b[v];
-                        gp[(12 + v) * (TX * TY)] = D2b[v];
+                        q2[v] = f2(Qv[0][v], Qv[1][v]);
+                        n2[v] = f2(Dn[0][v], Dn[1][v]);
+                        a2[v] = f2(D1[0][v], D1[1][v]);
+                        b2[v] = f2(D2[0][v], D2[1][v]);
+                        s0[v] = f2(sF0[v]);
+                        s1[v] = f2(sF1[v]);
+                    }
+                    Phys<f2> p2;
+                    p2.lambda = f2(A.ph.lambda);
+                    p2.theta = f2(A.ph.theta);
+                    p2.mu = f2(A.ph.mu);
+                    p2.off = f2(A.ph.off);
+                    p2.sqlam = f2(A.ph.sqlam);
+                    p2.kE = f2(A.ph.kE);
+                    gk_flux_rev<f2>(p2, q2, n2, a2, b2, f2(ih1), f2(ih2), s0, s1, needF0, qb, Dnb, D1b, D2b);
+#pragma unroll
+                    for (int nn = 0; nn < 2; ++nn) {
+                        float *gp = ga + (16 * (2 * m + nn)) * (TX * TY) + tid;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            gp[v * (TX * TY)] = nn ? qb[v].v.y : qb[v].v.x;
+                            gp[(4 + v) * (TX * TY)] = nn ? Dnb[v].v.y : Dnb[v].v.x;
+                            gp[(8 + v) * (TX * TY)] = nn ? D1b[v].v.y : D1b[v].v.x;
+                            gp[(12 + v) * (TX * TY)] = nn ? D2b[v].v.y : D2b[v].v.x;
+                        }
                     }
                 }
             }

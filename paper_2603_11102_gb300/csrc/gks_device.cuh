@@ -383,6 +383,7 @@ struct f2 {
     __device__ __forceinline__ f2(float2 a) : v(a) {}
     __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
     __device__ __forceinline__ explicit f2(float a) : v(make_float2(a, a)) {}   // both lanes
+    __device__ __forceinline__ explicit f2(double a) : f2((float)a) {}
 };
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
@@ -390,6 +391,10 @@ __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, 
 // a - b as a + (-1) b: the product is exact, so one rounding as in __fsub_rn
 __device__ __forceinline__ f2 operator-(f2 a, f2 b) { return fma(b, f2(-1.0f), a); }
 __device__ __forceinline__ f2 &operator+=(f2 &a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2 &operator-=(f2 &a, f2 b) { return a = a - b; }
+__device__ __forceinline__ f2 operator-(f2 a) { return a * f2(-1.0f); }
+// IEEE division per lane (the scalar FP32 path's a / b)
+__device__ __forceinline__ f2 operator/(f2 a, f2 b) { return f2(__fdiv_rn(a.v.x, b.v.x), __fdiv_rn(a.v.y, b.v.y)); }
 // the two-instruction approximate division of the scalar FP32 path, per lane
 __device__ __forceinline__ f2 wdiv(f2 a, f2 b) { return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
 

@@ -7,16 +7,20 @@
 //                evaluation per cell, the equilibrium state Q0 from the half
 //                Maxwellians (u>0 from the left, u<0 from the right), and the
 //                quartic normal slope of Q0.
-//   face_flux    (x, y) persistent, 32x8 face tiles loaded by TMA: linear
-//                quartic reconstruction of Q0 and its normal slope to the 2x2
-//                Gauss points (Sec. 2, Eq. (x_example)) with the t1 pass in
-//                shared memory, and the gas-kinetic flux F0 and its time
-//                derivative F1 at each point (Sec. 2, Eq. (flux); Appendix),
-//                averaged with weights 1/4 and stored per face.
+//   face_flux    (x, y) persistent, face tiles loaded by TMA (32x16 with two
+//                faces per thread for FP32C, 32x8 otherwise): linear quartic
+//                reconstruction of Q0 and its normal slope to the 2x2 Gauss
+//                points (Sec. 2, Eq. (x_example)) with the t1 pass in shared
+//                memory, and the gas-kinetic flux F0 and its time derivative
+//                F1 at each point (Sec. 2, Eq. (flux); Appendix), averaged
+//                with weights 1/4 and stored per face. The flux of FP32 and
+//                double-single arithmetic runs at two Gauss points at once on
+//                packed pairs.
 //   flux_update  (z) the same flux, walking z per tile column, fused with the
 //                divergence (Eq. (finite)) and the two-stage fourth-order
 //                combination of every cell; stage 2 also prepares the next
-//                step (FP32 input, max |U|^2 for the CFL step).
+//                step (FP32 input, max |U|^2 for the CFL step). Double-single
+//                grids store the z-face fluxes and update in update_ds_kernel.
 //
 // All arithmetic runs in the working type R: double for GKS_FP64, float for
 // GKS_FP32C. The reconstruction works on rho - off (off = rho_ref in FP32C,
@@ -863,7 +867,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 {
     static_assert(sizeof(C) == sizeof(R), "the t1-pass rows share the storage size");
     using M = Mid<R, C>;                       // face boxes, face fluxes and their differences
-    constexpr bool DS = std::is_same<C, dsf>::value;
+    // double-single grids take the z faces through face_flux_kernel and
+    // update_ds_kernel instead
+    static_assert(!std::is_same<C, dsf>::value, "the fused z kernel runs FP64 or FP32 arithmetic");
     constexpr bool NEED_F0 = STAGE == 1;
     constexpr int NC = STAGE == 1 ? 8 : 4, C0 = STAGE == 1 ? 0 : 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1005,11 +1011,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                     dz[4 + v] = F1[loc[v]] - P1[loc[v]];
                 }
                 R o0[4], o1[4];
-                if constexpr (DS)
-                    bad |= !update_cell_ds<STAGE>(U, lin, dt, dx, dy, dz, cvt<dsf>(ih1), cvt<dsf>(ih2), cvt<dsf>(ihz),
-                                                  s0, o0);
-                else
-                    bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ih1, ih2, ihz, s0, s1, o0, o1);
+                bad |= !update_cell<R, STAGE>(U, lin, dt, dx, dy, dz, ih1, ih2, ihz, s0, s1, o0, o1);
                 if (STAGE == 2 && U.prep) {
                     bool boxed = false;
                     for (int q = 0; q < U.nbox; ++q)

@@ -621,6 +621,39 @@ def run_ours(args, world, rank, local):
     del g
     torch.cuda.empty_cache()
 
+    # optional: the same workload as a slab group (gks_slab_step: x-slabs on
+    # this GPU with the halo exchange of every stage), cuts evenly spaced and
+    # moved off the forcing supports
+    slab_group = None
+    if args.slabs > 1:
+        nx = w.n[0]
+        fx = np.asarray(w.faces[0])
+        dx = fx[1] - fx[0]
+        forced = [int((r.hub[0] - fx[0]) / dx) for r in w.rotors] + \
+                 [int((np.mean(np.asarray(b.xyz).reshape(-1, 3)[:, 0]) - fx[0]) / dx) for b in w.bodies]
+        cuts = []
+        for k in range(1, args.slabs):
+            c = k * nx // args.slabs
+            while any(abs(c - f) < 24 for f in forced):
+                c += 8
+            cuts.append(c)
+        sg = gks.SlabGroup(w, cuts, precision=args.precision, device=dev)
+        sg.step(2)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(sg.slabs[0].stream)
+        sg.step(args.steps)
+        b.record(sg.slabs[0].stream)
+        torch.cuda.synchronize(dev)
+        mss = max_over_ranks(a.elapsed_time(b), world, dev) / args.steps
+        slab_group = {"slabs": args.slabs, "cuts": cuts, "value": world * cells / (mss / 1e3) / 1e6, "unit": "MLUPS",
+                      "ms_per_step": mss, "steps": args.steps,
+                      "note": "one GPU: the slabs' kernels run one after another on one stream; the halo copies "
+                              "and the per-slab launches are the overhead against the single grid"}
+        sg.close()
+        del sg
+        torch.cuda.empty_cache()
+
     fp64 = None
     if args.precision == "fp32c" and not args.no_fp64:
         g64 = gks.Grid.from_workload(w, precision="fp64", device=dev)
@@ -683,6 +716,8 @@ def run_ours(args, world, rank, local):
             "roofline": roofline, "hbm_step": hbm, "kernel_share": share, "cpu_baseline": cpu,
             "clocks": clocks, "e2e": e2e, "gpu_launches": prof["total_launches"], "fp64": fp64,
             "small_grid_graphs": graphs, "adjoint": adj, "reductions": reductions}
+    if slab_group is not None:
+        line["slab_group"] = slab_group
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -728,6 +763,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-alu-probe", action="store_true", help="skip the FMA-loop peak measurement")
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="also time the workload as a group of this many x-slabs on this GPU (gks_slab_step)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -57,13 +57,18 @@ typedef enum { GKS_FP64 = 0, GKS_FP32C = 1 } gks_precision;
 /* Boundary kinds (Sec. 4): periodic; no-slip isothermal wall (mirror, all
  * momenta negated); slip / symmetry wall (mirror, normal momentum negated);
  * inflow with prescribed velocity and density from the outgoing isothermal
- * Riemann invariant U -/+ C ln rho; extrapolation (zero-gradient) outflow. */
+ * Riemann invariant U -/+ C ln rho; extrapolation (zero-gradient) outflow.
+ * GKS_BC_EXCHANGE (x faces only): the side of an x-slab that borders the
+ * next slab of a slab group; its ghost planes come from that slab
+ * (gks_slab_step, Sec. 3's decomposition of the domain into x-slabs), never
+ * from a boundary rule. */
 typedef enum {
     GKS_BC_PERIODIC = 0,
     GKS_BC_NOSLIP = 1,
     GKS_BC_SLIP = 2,
     GKS_BC_INFLOW = 3,
-    GKS_BC_OUTFLOW = 4
+    GKS_BC_OUTFLOW = 4,
+    GKS_BC_EXCHANGE = 5
 } gks_bc;
 
 typedef struct gks_grid gks_grid;
@@ -188,6 +193,31 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
  * GKS_ERR_CFL or GKS_ERR_RANGE raised on the device. t_out (may be NULL)
  * receives the time after the last step. */
 int gks_step(gks_grid *g, int nsteps, double *t_out);
+
+/* gks_slab_step: advance a slab group, nslab grids that split one domain
+ * along x (the paper's multi-GPU decomposition, Sec. 3: x-slabs with a halo
+ * exchange per stage), by nsteps steps, on one device. slabs[0 .. nslab-1]
+ * are in the order of increasing x; each was created by gks_create_grid with
+ * its own share of the x faces and GKS_BC_EXCHANGE on every x side that
+ * borders another slab (slab s's high side and slab s+1's low side; slab 0's
+ * low and slab nslab-1's high side for a periodic x axis, which the group
+ * then closes). Per stage, after each slab's ghost fill, the three interior
+ * x-planes of the working array next to each exchange side (all y and z
+ * rows, ghost rows included) are copied into the neighbour's ghost planes;
+ * the CFL time step takes the largest |U|^2 of all slabs and the smallest
+ * cell width of all slabs; each slab applies its own rotors and bodies,
+ * whose kernel supports must not reach an exchange side (gks_add_actuator_lines
+ * and gks_add_ib_points return GKS_ERR_RANGE otherwise). The first call
+ * also gives each exchange side's ghost cells the neighbour's cell widths
+ * (the geometry tables a grid of the whole domain has at the cut), so the
+ * state of every slab then has the bits that grid would have.
+ * Requirements (GKS_ERR_ARG otherwise): 1 <= nslab <= 64; the same precision,
+ * arithmetic, y and z cells, faces and boundary kinds, physics (Mach, U_ref,
+ * mu, CFL or fixed dt, rho_ref) and stream on every slab; exchange sides
+ * exactly where stated above; no CUDA graphs (gks_set_graphs) on a slab. Synchronises the stream at the end
+ * and reports device flags like gks_step, per slab. t_out (may be NULL)
+ * receives the time after the last step. Allocates nothing. */
+int gks_slab_step(gks_grid *const *slabs, int nslab, int nsteps, double *t_out);
 /* The same steps, enqueued on the grid's stream without synchronising:
  * device-side errors stay flagged on the device and are reported by the next
  * gks_step or gks_sync. */

@@ -98,7 +98,8 @@ int validate(const gks_grid_desc *d, std::string *msg)
     for (int a = 0; a < 3; ++a) {
         const bool p0 = d->bc[a][0] == GKS_BC_PERIODIC, p1 = d->bc[a][1] == GKS_BC_PERIODIC;
         for (int s = 0; s < 2; ++s)
-            if (d->bc[a][s] < GKS_BC_PERIODIC || d->bc[a][s] > GKS_BC_OUTFLOW) { *msg = "bad boundary kind"; return GKS_ERR_ARG; }
+            if (d->bc[a][s] < GKS_BC_PERIODIC || d->bc[a][s] > GKS_BC_EXCHANGE ||
+                (d->bc[a][s] == GKS_BC_EXCHANGE && a != 0)) { *msg = "bad boundary kind"; return GKS_ERR_ARG; }
         if (p0 != p1) { *msg = "periodic must be set on both ends of an axis"; return GKS_ERR_ARG; }
         if (d->n[a] < (p0 ? 1 : 3)) { *msg = "too few cells on an axis"; return GKS_ERR_ARG; }
         if (d->n[a] > (1 << 24)) { *msg = "too many cells on an axis"; return GKS_ERR_ARG; }
@@ -235,6 +236,16 @@ void prof_mark(void *ctx, int group, int begin)
         p.recs.push_back({group, p.open_ev, e});
         p.last_end = e;
     }
+}
+
+// Whether the x cells of [lo, hi] (with the one-cell margin of cell_range)
+// reach past an exchange side: a kernel support there would need the
+// neighbouring slab's cells.
+bool reaches_exchange(const Ctx &c, double lo, double hi)
+{
+    const long i0 = (long)floor((lo - c.x0[0]) / c.hu[0] - 0.5) - 1;
+    const long i1 = (long)ceil((hi - c.x0[0]) / c.hu[0] - 0.5) + 1;
+    return (c.bc[0][0] == GKS_BC_EXCHANGE && i0 < 0) || (c.bc[0][1] == GKS_BC_EXCHANGE && i1 > c.n[0] - 1);
 }
 
 int cell_range(const Ctx &c, int a, double lo, double hi, int out[2])
@@ -529,6 +540,8 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
         cell_range(c, 1, d->hub[1] - rmax - cut, d->hub[1] + rmax + cut, r.box[1]) ||
         cell_range(c, 2, d->hub[2] - rmax - cut, d->hub[2] + rmax + cut, r.box[2]))
         return fail(g, GKS_ERR_RANGE, "rotor outside the grid");
+    if (reaches_exchange(c, d->hub[0] - cut, d->hub[0] + cut))
+        return fail(g, GKS_ERR_RANGE, "rotor support reaches an exchange side of the slab");
     r.norm = 1.0 / (d->eps * d->eps * d->eps * pow(3.14159265358979323846, 1.5));
     r.ie2 = 1.0 / (d->eps * d->eps);
     // per point: scale, X (3), F (4), Xr (3 floats in 2 doubles)
@@ -585,6 +598,15 @@ int gks_add_ib_points(gks_grid *g, int n, const double *xyz, const double *dS, c
     b.eps = eps;
     b.tol = tol;
     if (body_box(c, xyz, n, eps, b.box)) return fail(g, GKS_ERR_RANGE, "body outside the grid");
+    {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int p = 0; p < n; ++p) {
+            lo = fmin(lo, xyz[3 * p]);
+            hi = fmax(hi, xyz[3 * p]);
+        }
+        if (reaches_exchange(c, lo - 3.0 * eps, hi + 3.0 * eps))
+            return fail(g, GKS_ERR_RANGE, "body support reaches an exchange side of the slab");
+    }
     b.nbox = (long)(b.box[0][1] - b.box[0][0] + 1) * (b.box[1][1] - b.box[1][0] + 1) * (b.box[2][1] - b.box[2][0] + 1);
     const size_t nd = 7 * (size_t)n + 8 * (size_t)b.nbox + 7 + niter;
     double *buf = nullptr;
@@ -885,6 +907,177 @@ int gks_step(gks_grid *g, int nsteps, double *t_out)
     return rc ? rc : finish_steps(g, t_out);
 }
 
+namespace {
+// Slab groups: the x halo exchange of the working array of a stage (0: W,
+// 1: W*) between every pair of neighbouring slabs, in both directions.
+void slab_exchange(gks_grid *const *sl, int n, int stage)
+{
+    auto work = [&](int s) { return stage == 0 ? sl[s]->c.wk0 : sl[s]->c.wk1; };
+    for (int s = 0; s < n; ++s) {
+        if (sl[s]->c.bc[0][1] != GKS_BC_EXCHANGE) continue;
+        const int r = s + 1 < n ? s + 1 : 0;   // the right neighbour; slab 0 closes a periodic x axis
+        launch_halo_copy(sl[s]->c, work(s), 1, sl[r]->c, work(r), 0);
+        launch_halo_copy(sl[r]->c, work(r), 0, sl[s]->c, work(s), 1);
+    }
+}
+
+// One step of a slab group on one stream: the sequence of step_once on every
+// slab, with the halo exchange after each ghost fill and the group's largest
+// |U|^2 for the time step.
+int slab_step_once(gks_grid *const *sl, int n)
+{
+    for (int s = 0; s < n; ++s) {
+        gks_grid *g = sl[s];
+        g->prof.last_end = nullptr;
+        g->stepped = true;
+        if (!g->prep_valid) launch_prep(g->c);
+        launch_ghost(g->c, g->c.wk0);
+    }
+    slab_exchange(sl, n, 0);
+    Scalars *scal[64];
+    for (int s = 0; s < n; ++s) scal[s] = sl[s]->c.scal;
+    launch_group_max_u2(scal, n, sl[0]->c.stream);
+    for (int s = 0; s < n; ++s) launch_cfl(sl[s]->c);
+    std::vector<Ctx> cc(n);
+    for (int s = 0; s < n; ++s) {
+        cc[s] = sl[s]->c;
+        launch_stage(cc[s], 1);
+        launch_ghost(cc[s], cc[s].wk1);
+    }
+    slab_exchange(sl, n, 1);
+    std::vector<int> fused(n);
+    for (int s = 0; s < n; ++s) {
+        gks_grid *g = sl[s];
+        const int nobj = (int)g->obj_kind.size();
+        fused[s] = nobj <= 8;
+        if (fused[s]) {
+            cc[s].prep_next = 1;
+            cc[s].nprep_box = nobj;
+            for (int k = 0; k < nobj; ++k) {
+                const int(*box)[2] =
+                    g->obj_kind[k] == 0 ? g->rotors[g->obj_index[k]].box : g->bodies[g->obj_index[k]].box;
+                memcpy(cc[s].prep_box[k], box, sizeof(int) * 6);
+            }
+        }
+        launch_stage(cc[s], 2);
+    }
+    for (int s = 0; s < n; ++s) {
+        gks_grid *g = sl[s];
+        const Ctx &c = g->c;
+        for (size_t k = 0; k < g->obj_kind.size(); ++k)
+            if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
+        for (size_t k = 0; k < g->obj_kind.size(); ++k)
+            if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
+        if (fused[s])
+            for (int k = 0; k < cc[s].nprep_box; ++k) launch_prep_box(c, cc[s].prep_box[k]);
+        g->prep_valid = fused[s];
+        launch_advance(c);
+        g->prof.last_end = nullptr;
+        const int rc = check_launch(g, "slab step");
+        if (rc) return rc;
+        g->nstep++;
+    }
+    return GKS_OK;
+}
+
+// Host copy of a device array of doubles (slab-group checks).
+int fetch(gks_grid *g, const double *d, size_t n, std::vector<double> *out)
+{
+    out->resize(n);
+    return cuda_check(g, cudaMemcpy(out->data(), d, n * sizeof(double), cudaMemcpyDeviceToHost), "read widths");
+}
+
+// The x geometry tables of two neighbouring slabs at their cut: the ghost
+// cell widths of each exchange side become the other slab's interior widths
+// (at creation they mirror the slab's own), and the inverse widths of those
+// ghosts and the inverse centre distance of the cut face follow, as a grid of
+// the whole domain has them.
+int patch_cut(gks_grid *gl, gks_grid *gr)
+{
+    Ctx &l = gl->c, &r = gr->c;
+    std::vector<double> hl, hr0;
+    int rc = fetch(gl, l.h64[0], l.P[0], &hl);
+    if (!rc && gr != gl) rc = fetch(gr, r.h64[0], r.P[0], &hr0);
+    if (rc) return rc;
+    std::vector<double> &hr = gr == gl ? hl : hr0;   // one slab closing a periodic axis on itself
+    const int nl = l.n[0];
+    for (int k = 0; k < G; ++k) {
+        hl[G + nl + k] = hr[G + k];
+        hr[G - 1 - k] = hl[G + nl - 1 - k];
+    }
+    std::vector<double> il(hl.size()), ir(hr.size()), fl(nl + 1), fr(r.n[0] + 1);
+    for (size_t i = 0; i < hl.size(); ++i) il[i] = 1.0 / hl[i];
+    for (size_t i = 0; i < hr.size(); ++i) ir[i] = 1.0 / hr[i];
+    for (int f = 0; f <= nl; ++f) fl[f] = 1.0 / (0.5 * (hl[G + f - 1] + hl[G + f]));
+    for (int f = 0; f <= r.n[0]; ++f) fr[f] = 1.0 / (0.5 * (hr[G + f - 1] + hr[G + f]));
+    const bool f64 = l.prec == GKS_FP64;
+    rc = upload<double>(gl, l.h64[0], hl);
+    if (!rc) rc = upload<double>(gr, r.h64[0], hr);
+    if (!rc) rc = f64 ? upload<double>(gl, l.ih[0], il) : upload<float>(gl, l.ih[0], il);
+    if (!rc) rc = f64 ? upload<double>(gr, r.ih[0], ir) : upload<float>(gr, r.ih[0], ir);
+    if (!rc) rc = f64 ? upload<double>(gl, l.ihf[0], fl) : upload<float>(gl, l.ihf[0], fl);
+    if (!rc) rc = f64 ? upload<double>(gr, r.ihf[0], fr) : upload<float>(gr, r.ihf[0], fr);
+    if (!rc) rc = sync(gl);
+    return rc;
+}
+}  // namespace
+
+int gks_slab_step(gks_grid *const *slabs, int nslab, int nsteps, double *t_out)
+{
+    if (!slabs || nslab < 1 || nslab > 64 || nsteps < 0) return fail(nullptr, GKS_ERR_ARG, "bad slab-group arguments");
+    for (int s = 0; s < nslab; ++s)
+        if (!slabs[s]) return fail(nullptr, GKS_ERR_ARG, "null slab");
+    gks_grid *g0 = slabs[0];
+    const Ctx &c0 = g0->c;
+    std::vector<double> hy0, hz0;
+    int rc = fetch(g0, c0.h64[1], c0.P[1], &hy0);
+    if (!rc) rc = fetch(g0, c0.h64[2], c0.P[2], &hz0);
+    if (rc) return rc;
+    double hmin = INFINITY;
+    for (int s = 0; s < nslab; ++s) {
+        gks_grid *g = slabs[s];
+        const Ctx &c = g->c;
+        if (c.prec != c0.prec || c.fp64_ds != c0.fp64_ds || c.n[1] != c0.n[1] || c.n[2] != c0.n[2] ||
+            c.stream != c0.stream || c.lambda != c0.lambda || c.mu != c0.mu || c.off != c0.off || c.cfl != c0.cfl ||
+            c.dt_fixed != c0.dt_fixed)
+            return fail(nullptr, GKS_ERR_ARG, "slabs differ in precision, arithmetic, y/z cells, physics or stream");
+        for (int a = 1; a < 3; ++a)
+            if (c.bc[a][0] != c0.bc[a][0] || c.bc[a][1] != c0.bc[a][1])
+                return fail(nullptr, GKS_ERR_ARG, "slabs differ in their y or z boundary kinds");
+        if (g->use_graphs) return fail(nullptr, GKS_ERR_ARG, "slab groups step without CUDA graphs");
+        std::vector<double> hy, hz;
+        rc = fetch(g, c.h64[1], c.P[1], &hy);
+        if (!rc) rc = fetch(g, c.h64[2], c.P[2], &hz);
+        if (rc) return rc;
+        if (hy != hy0 || hz != hz0) return fail(nullptr, GKS_ERR_ARG, "slabs differ in their y or z faces");
+        const bool hi_ex = c.bc[0][1] == GKS_BC_EXCHANGE;
+        const bool lo_next = slabs[s + 1 < nslab ? s + 1 : 0]->c.bc[0][0] == GKS_BC_EXCHANGE;
+        if (s + 1 < nslab && !(hi_ex && lo_next))
+            return fail(nullptr, GKS_ERR_ARG, "neighbouring slabs must face each other with exchange sides");
+        if (s + 1 == nslab && hi_ex != lo_next)
+            return fail(nullptr, GKS_ERR_ARG, "a periodic x axis needs exchange sides on both ends of the group");
+        if (hi_ex) {
+            gks_grid *gr = slabs[s + 1 < nslab ? s + 1 : 0];
+            rc = patch_cut(g, gr);
+            if (rc) return rc;
+        }
+        hmin = fmin(hmin, c.hmin);
+    }
+    for (int s = 0; s < nslab; ++s) slabs[s]->c.hmin = hmin;   // the CFL step of the whole domain
+    for (int k = 0; k < nsteps; ++k) {
+        rc = slab_step_once(slabs, nslab);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < nslab; ++s) {
+        rc = finish_steps(slabs[s], s == 0 ? t_out : nullptr);
+        if (rc) {
+            g_err = slabs[s]->err;
+            return rc;
+        }
+    }
+    return GKS_OK;
+}
+
 int gks_get_time(gks_grid *g, double *t, double *dt_last)
 {
     if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
@@ -1089,6 +1282,8 @@ int adjoint_check(gks_grid *g, bool tape_path)
     if (tape_path && g->bodies.size() > (size_t)kTapeMaxBodies)
         return fail(g, GKS_ERR_STATE, "too many immersed bodies for a tape");
     if (g->rotors.size() > 1) return fail(g, GKS_ERR_STATE, "the adjoint covers at most one rotor");
+    if (c.bc[0][0] == GKS_BC_EXCHANGE || c.bc[0][1] == GKS_BC_EXCHANGE)
+        return fail(g, GKS_ERR_STATE, "the adjoint covers whole grids, not slabs");
     // the reverse t2 gather indexes its 64 face arrays with 32-bit offsets
     for (int d = 0; d < 3; ++d) {
         const double nf = (double)(c.n[d] + 1) * c.n[(d + 1) % 3] * c.n[(d + 2) % 3];

@@ -120,6 +120,12 @@ void launch_fill_rest(const Ctx &c);                            // rho = 1, mome
 void launch_raw_copy(const Ctx &c, void *compact, int to_compact);  // stored arrays <-> compact
 // out[i] = a[i] (+ b[i] if b) (+ off0 for i < n0), FP32 -> FP64, i < n
 void launch_widen(const Ctx &c, const float *a, const float *b, double *out, long n, long n0, double off0);
+// Slab groups (x-slabs of one domain on one device): the G x-planes of the
+// working array next to x side `side_src` of `src` (all y and z rows, ghost
+// rows included) into the G ghost planes on side `side_dst` of `dst`; and the
+// largest max |U|^2 of the group into every slab's scalars.
+void launch_halo_copy(const Ctx &src, const void *w_src, int side_src, const Ctx &dst, void *w_dst, int side_dst);
+void launch_group_max_u2(Scalars *const *scal, int n, cudaStream_t stream);
 
 // Actuator line (gks_forcing.cu).
 struct RotorDev {

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256) ghost_kernel(GhostArgs<R> A)
     }
     const int d = A.d, nd = A.n[d];
     const int bc = s == 0 ? A.bc0 : A.bc1;
+    if (bc == GKS_BC_EXCHANGE) return;   // filled from the neighbouring slab
     const int gi = s == 0 ? -l : nd - 1 + l;
     int src;
     if (bc == GKS_BC_PERIODIC) {
@@ -1607,6 +1608,64 @@ void launch_ghost(const Ctx &c, void *w)
         ghost_impl<double>(c, (double *)w);
     else
         ghost_impl<float>(c, (float *)w);
+}
+
+// ------------------------------------------------------------ slab groups --
+
+// One thread per element of the G x-planes: (component, row, plane) with
+// row = the (y, z) position over the padded P1 x P2 rows.
+template <typename T>
+__global__ void __launch_bounds__(256) halo_copy_kernel(const T *__restrict__ src, long np_src, int P0_src, int i_src,
+                                                        T *__restrict__ dst, long np_dst, int P0_dst, int i_dst,
+                                                        long rows)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long per = rows * G;
+    if (t >= 4 * per) return;
+    const int v = (int)(t / per);
+    const long r = t - v * per, row = r / G;
+    const int l = (int)(r - row * G);
+    const long is = (long)(i_src + l) + (long)P0_src * row, id = (long)(i_dst + l) + (long)P0_dst * row;
+    if (!in_bounds(is, np_src) || !in_bounds(id, np_dst)) return;
+    dst[v * np_dst + id] = src[v * np_src + is];
+}
+
+void launch_halo_copy(const Ctx &src, const void *w_src, int side_src, const Ctx &dst, void *w_dst, int side_dst)
+{
+    // padded x index of the first plane: the interior planes next to the
+    // low side start at G, next to the high side at n; the ghost planes of
+    // the low side start at 0, of the high side at n + G
+    const int i_src = side_src == 0 ? G : src.n[0];
+    const int i_dst = side_dst == 0 ? 0 : dst.n[0] + G;
+    const long rows = (long)src.P[1] * src.P[2];
+    const long nt = 4 * rows * G;
+    const int grid = (int)((nt + 255) / 256);
+    mark(dst, K_GHOST, 1);
+    if (src.prec == GKS_FP64)
+        halo_copy_kernel<double><<<grid, 256, 0, dst.stream>>>((const double *)w_src, src.np, src.P[0], i_src,
+                                                                (double *)w_dst, dst.np, dst.P[0], i_dst, rows);
+    else
+        halo_copy_kernel<float><<<grid, 256, 0, dst.stream>>>((const float *)w_src, src.np, src.P[0], i_src,
+                                                               (float *)w_dst, dst.np, dst.P[0], i_dst, rows);
+    mark(dst, K_GHOST, 0);
+}
+
+struct GroupScal {
+    Scalars *p[64];
+};
+
+__global__ void group_max_u2_kernel(GroupScal g, int n)
+{
+    unsigned long long m = 0ull;   // bits of non-negative doubles order like the values
+    for (int s = 0; s < n; ++s) m = max(m, g.p[s]->maxu2_bits);
+    for (int s = 0; s < n; ++s) g.p[s]->maxu2_bits = m;
+}
+
+void launch_group_max_u2(Scalars *const *scal, int n, cudaStream_t stream)
+{
+    GroupScal g;
+    for (int s = 0; s < n && s < 64; ++s) g.p[s] = scal[s];
+    group_max_u2_kernel<<<1, 1, 0, stream>>>(g, n);
 }
 
 // FP32C: the forward face state of direction d from the FP32 working array

@@ -72,6 +72,7 @@ SIGNATURES = {
     "gks_add_ib_points": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int, C.c_double,
                                     C.POINTER(C.c_int)]),
     "gks_step": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "gks_slab_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, _dp]),
     "gks_get_time": (C.c_int, [C.c_void_p, _dp, _dp]),
     "gks_set_time": (C.c_int, [C.c_void_p, C.c_double]),
     "gks_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ForcesOut), _dp]),
@@ -154,7 +155,8 @@ class Grid:
 
     Parameters mirror ``gks_grid_desc``; ``bc`` is [(lo, hi)] per axis with the
     integer kinds of the C ABI (0 periodic, 1 no-slip, 2 slip, 3 inflow,
-    4 outflow)."""
+    4 outflow, 5 exchange: an x side shared with the next slab of a
+    :class:`SlabGroup`)."""
 
     def __init__(self, n, faces, mach, u_ref, mu, bc, precision="fp64", cfl=0.5, dt_fixed=0.0,
                  rho_ref=1.0, device=None, stream=None):
@@ -483,3 +485,75 @@ def alu_peak_probe(kind, iters: int, sink, stream) -> float:
     if rc != GKS_OK:
         raise GKSError(rc, lib.gks_last_error(None).decode())
     return out.value
+
+
+EXCHANGE = 5
+
+
+class SlabGroup:
+    """A workload's domain split along x into slabs at the cell indices
+    ``cuts`` (0 < c_1 < c_2 < ... < n_x), one grid per slab on the same device
+    and stream, stepped together by ``gks_slab_step`` (the halo exchange of
+    every stage, the common time step). Each rotor and body goes to the slab
+    that holds its x position (its kernel support must not reach a cut).
+    Host-side bookkeeping only: splitting the faces, the boundary kinds and
+    the initial state, and joining the slabs' states."""
+
+    def __init__(self, w, cuts, precision="fp64", **kw):
+        nx = int(w.n[0])
+        self.cuts = [0] + [int(c) for c in cuts] + [nx]
+        if any(b - a < 3 for a, b in zip(self.cuts[:-1], self.cuts[1:])):
+            raise ValueError("every slab needs at least 3 x cells: %s" % (self.cuts,))
+        periodic = w.bc[0][0] == 0
+        ns = len(self.cuts) - 1
+        fx = np.asarray(w.faces[0], dtype=np.float64)
+        self.slabs = []
+        for s in range(ns):
+            a, b = self.cuts[s], self.cuts[s + 1]
+            lo = EXCHANGE if (s > 0 or periodic) else w.bc[0][0]
+            hi = EXCHANGE if (s + 1 < ns or periodic) else w.bc[0][1]
+            bc = [(lo, hi), tuple(w.bc[1]), tuple(w.bc[2])]
+            g = Grid((b - a, w.n[1], w.n[2]), [fx[a:b + 1], w.faces[1], w.faces[2]], w.mach, w.u_ref, w.mu, bc,
+                     precision=precision, cfl=w.cfl, dt_fixed=w.dt_fixed, rho_ref=w.rho_ref,
+                     stream=self.slabs[0].stream if self.slabs else kw.get("stream"),
+                     device=kw.get("device"))
+            g.set_inflow(*w.inflow)
+            g.set_body_force(*w.body_force)
+            if w.state0 is not None:
+                g.set_state(np.ascontiguousarray(w.state0[:, :, :, a:b]))
+            self.slabs.append(g)
+        # object id of the whole workload -> (slab, id in that slab)
+        self.objects = []
+        for r in w.rotors:
+            s = self.slab_of(r.hub[0])
+            self.objects.append((s, self.slabs[s].add_rotor(r)))
+        for bd in w.bodies:
+            s = self.slab_of(float(np.mean(np.asarray(bd.xyz).reshape(-1, 3)[:, 0])))
+            self.objects.append((s, self.slabs[s].add_body(bd)))
+        self._handles = (C.c_void_p * ns)(*[g.h for g in self.slabs])
+
+    def slab_of(self, x):
+        """The slab whose x faces hold coordinate x."""
+        for s, g in enumerate(self.slabs):
+            f = g._faces[0]
+            if f[0] <= x < f[-1] or (s == len(self.slabs) - 1 and x == f[-1]):
+                return s
+        raise ValueError("x = %g outside the domain" % x)
+
+    def step(self, nsteps=1):
+        t = C.c_double()
+        _check(lib.gks_slab_step(self._handles, len(self.slabs), int(nsteps), C.byref(t)))
+        return t.value
+
+    def get_state(self):
+        """The (4, nz, ny, nx) FP64 state of the whole domain."""
+        return np.concatenate([g.get_state() for g in self.slabs], axis=3)
+
+    def forces(self, oid):
+        s, i = self.objects[oid]
+        return self.slabs[s].forces(i)
+
+    def close(self):
+        for g in self.slabs:
+            g.close()
+

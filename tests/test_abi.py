@@ -108,6 +108,10 @@ def test_workspace_sizes_and_validation(gks):
            dict(bc=((0, 1), (0, 0), (0, 0))),                # periodic on one end only
            dict(faces=[np.linspace(1, 0, 9), np.linspace(0, 1, 7), np.linspace(0, 1, 6)]),
            dict(precision=7), dict(cfl=0.0),
+           dict(bc=((0, 0), (5, 5), (0, 0))),                # exchange sides are x sides only
+           dict(bc=((0, 0), (0, 0), (2, 5))),
+           dict(bc=((0, 5), (0, 0), (0, 0))),                # periodic on one end only
+           dict(bc=((4, 6), (0, 0), (0, 0))),                # no such kind
            dict(n=(0, 6, 5), faces=[np.zeros(1), np.linspace(0, 1, 7), np.linspace(0, 1, 6)]),   # empty axis
            # more cells than the 32-bit face-tile indices of the flux kernels cover
            dict(n=(2000, 1100, 1000), faces=[np.linspace(0, 1, 2001), np.linspace(0, 1, 1101),
@@ -116,7 +120,13 @@ def test_workspace_sizes_and_validation(gks):
         d, keep = make_desc(gks, **kw)
         assert lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)) == -1, kw
         assert lib.gks_last_error(None)
+    # an x-slab of a slab group: exchange sides on x
+    d, keep = make_desc(gks, bc=((5, 5), (0, 0), (0, 0)))
+    assert lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)) == 0
+    d, keep = make_desc(gks, bc=((3, 5), (2, 2), (1, 1)))
+    assert lib.gks_workspace_bytes(C.byref(d), C.byref(sb), C.byref(wb)) == 0
     # null handles
+    assert lib.gks_slab_step(None, 1, 1, None) == -1
     assert lib.gks_step(None, 1, None) == -1
     assert lib.gks_step_async(None, 1) == -1
     assert lib.gks_sync(None, None) == -1

@@ -1,0 +1,142 @@
+"""Slab groups (gks_slab_step): a domain split along x into slabs on one
+device, stepped with the x halo exchange of every stage and a common time
+step, reproduces a single grid of the whole domain (the paper's
+decomposition into x-slabs, Sec. 3; run here on one GPU): bit for bit in
+FP64; in FP32C to the rounding of the FP32 face state, whose march (unrolled
+by two along the normal) rounds a face by its position in the march, which a
+cut moves."""
+import numpy as np
+import pytest
+
+from _setup import rel_linf, smooth_workload
+from paper_2603_11102_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gks():
+    from paper_2603_11102_gb300 import build, gks
+    build.build()
+    gks.load()
+    return gks
+
+
+def single_and_slabs(gks, w, cuts, precision, steps):
+    g = gks.Grid.from_workload(w, precision=precision)
+    t1 = g.step(steps)
+    sg = gks.SlabGroup(w, cuts, precision=precision)
+    t2 = sg.step(steps)
+    return g, sg, t1, t2
+
+
+def assert_same(g, sg, t1, t2, precision):
+    a, b = sg.get_state(), g.get_state()
+    if precision == "fp64":
+        assert t1 == t2
+        assert np.array_equal(a, b)
+    else:
+        assert abs(t2 - t1) <= 1e-8 * t1, (t1, t2)
+        assert rel_linf(a, b) <= 1e-6, rel_linf(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_periodic_three_slabs_match_the_single_grid_bitwise(gks, precision):
+    """Taylor-Green 40^3, periodic in x: three slabs (13, 14, 13 cells), the
+    group closing the periodic axis; the CFL step from the group's maximum."""
+    w = WL.taylor_green_3d(40, steps=10)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [13, 27], precision, 10)
+    assert_same(g, sg, t1, t2, precision)
+    g.close()
+    sg.close()
+    # 64^3 cut in the middle, and one slab closing the periodic axis on itself
+    w = WL.taylor_green_3d(64, steps=4)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [29], precision, 4)
+    assert_same(g, sg, t1, t2, precision)
+    g.close()
+    sg.close()
+    g, sg, t1, t2 = single_and_slabs(gks, w, [], precision, 4)
+    assert_same(g, sg, t1, t2, precision)
+    g.close()
+    sg.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_channel_two_slabs_match_the_single_grid_bitwise(gks, precision):
+    """The channel on a ragged 70 x 45 x 37 grid: periodic x cut into two
+    slabs, tanh-stretched y between no-slip walls, periodic z, driving body
+    force."""
+    w = WL.channel((70, 45, 37), steps=8)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [35], precision, 8)
+    assert_same(g, sg, t1, t2, precision)
+    g.close()
+    sg.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_rotor_and_bodies_in_one_slab_of_two(gks, precision):
+    """Rotor, tower and nacelle (inflow x-, outflow x+) with the cut
+    downstream of every kernel support: the state, the rotor loads and the
+    body forces match the single grid's (bit for bit in FP64)."""
+    w = WL.alm_ibm_rotor(n=(96, 64, 64), steps=6, n_pts=20)
+    w.state0 = WL.perturbed(w, 0.02, seed=9)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [60], precision, 6)
+    assert_same(g, sg, t1, t2, precision)
+    for oid in range(3):
+        a, b = g.forces(oid), sg.forces(oid)
+        for k, v in a.items():
+            x, y = np.asarray(v, dtype=np.float64), np.asarray(b[k], dtype=np.float64)
+            if precision == "fp64":
+                assert np.array_equal(x, y), (oid, k)
+            else:
+                assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(x)), 1e-30), (oid, k)
+    g.close()
+    sg.close()
+
+
+def test_smooth_state_with_walls_and_an_outflow_across_four_slabs(gks):
+    """A seeded smooth state with inflow / outflow in x, slip and no-slip
+    walls in y and z, four slabs of unequal widths (FP64)."""
+    n = (41, 12, 10)
+    faces = [np.linspace(0.0, 2.0, n[0] + 1), np.linspace(0.0, 1.0, n[1] + 1), np.linspace(0.0, 0.8, n[2] + 1)]
+    w = smooth_workload(n, [(3, 4), (2, 2), (1, 1)], faces=faces, seed=4)
+    w.inflow = (1.0, 0.6, 0.0, 0.05)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [9, 20, 31], "fp64", 6)
+    assert_same(g, sg, t1, t2, "fp64")
+    g.close()
+    sg.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_stretched_x_axis_cut_three_times(gks, precision):
+    """A tanh-stretched x axis (inflow / outflow), periodic y, slip z, cut
+    into three slabs of unequal widths: the ghost cells of each cut take the
+    neighbour's widths, so the geometry matches the single grid's and the
+    state does too (bit for bit in FP64)."""
+    n = (36, 10, 12)
+    faces = [WL.tanh_faces(n[0]), np.linspace(0.0, 1.0, n[1] + 1), np.linspace(0.0, 1.2, n[2] + 1)]
+    w = smooth_workload(n, [(3, 4), (0, 0), (2, 2)], faces=faces, seed=6)
+    w.inflow = (1.0, 0.5, 0.05, 0.0)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [10, 23], precision, 6)
+    assert_same(g, sg, t1, t2, precision)
+    g.close()
+    sg.close()
+
+
+def test_support_across_a_cut_and_mismatched_slabs_are_refused(gks):
+    """A rotor whose kernel support reaches a cut is refused (GKS_ERR_RANGE);
+    slabs whose y faces differ are refused by the group step (GKS_ERR_ARG)."""
+    w = WL.alm_rotor(n=(96, 32, 32), steps=2, n_pts=10)
+    hub_cell = int(round((w.rotors[0].hub[0] - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
+    with pytest.raises(gks.GKSError) as e:
+        gks.SlabGroup(w, [hub_cell + 2], precision="fp64")
+    assert e.value.code == -6
+    a = gks.Grid((12, 8, 8), [np.linspace(0, 1, 13), np.linspace(0, 1, 9), np.linspace(0, 1, 9)], 0.1, 1.0, 1e-3,
+                 [(4, 5), (0, 0), (0, 0)])
+    b = gks.Grid((12, 8, 8), [np.linspace(1, 2, 13), np.linspace(0, 1.5, 9), np.linspace(0, 1, 9)], 0.1, 1.0, 1e-3,
+                 [(5, 4), (0, 0), (0, 0)], stream=a.stream)
+    import ctypes as C
+    h = (C.c_void_p * 2)(a.h, b.h)
+    assert gks.lib.gks_slab_step(h, 2, 1, None) == -1
+    a.close()
+    b.close()

@@ -490,6 +490,40 @@ def alu_peak_probe(kind, iters: int, sink, stream) -> float:
 EXCHANGE = 5
 
 
+def plan_slabs(w, cuts):
+    """The slabs of a workload cut along x at the cell indices ``cuts``: per
+    slab its cells, faces, boundary kinds (exchange sides between slabs, and
+    at both ends of a periodic x axis) and share of the initial state; and
+    the slab of every rotor (by its hub) and body (by the mean x of its
+    points), in the workload's order. Host-side bookkeeping (no device)."""
+    nx = int(w.n[0])
+    cuts = [0] + [int(c) for c in cuts] + [nx]
+    if any(b - a < 3 for a, b in zip(cuts[:-1], cuts[1:])):
+        raise ValueError("every slab needs at least 3 x cells: %s" % (cuts,))
+    periodic = w.bc[0][0] == 0
+    ns = len(cuts) - 1
+    fx = np.asarray(w.faces[0], dtype=np.float64)
+    slabs = []
+    for s in range(ns):
+        a, b = cuts[s], cuts[s + 1]
+        lo = EXCHANGE if (s > 0 or periodic) else w.bc[0][0]
+        hi = EXCHANGE if (s + 1 < ns or periodic) else w.bc[0][1]
+        slabs.append({"n": (b - a, w.n[1], w.n[2]), "faces": [fx[a:b + 1], w.faces[1], w.faces[2]],
+                      "bc": [(lo, hi), tuple(w.bc[1]), tuple(w.bc[2])],
+                      "state0": None if w.state0 is None else np.ascontiguousarray(w.state0[:, :, :, a:b])})
+
+    def slab_of(x):
+        for s in range(ns):
+            f0, f1 = fx[cuts[s]], fx[cuts[s + 1]]
+            if f0 <= x < f1 or (s == ns - 1 and x == f1):
+                return s
+        raise ValueError("x = %g outside the domain" % x)
+
+    objects = [("rotor", r, slab_of(r.hub[0])) for r in w.rotors]
+    objects += [("body", b, slab_of(float(np.mean(np.asarray(b.xyz).reshape(-1, 3)[:, 0])))) for b in w.bodies]
+    return {"cuts": cuts, "slabs": slabs, "objects": objects}
+
+
 class SlabGroup:
     """A workload's domain split along x into slabs at the cell indices
     ``cuts`` (0 < c_1 < c_2 < ... < n_x), one grid per slab on the same device
@@ -500,45 +534,24 @@ class SlabGroup:
     the initial state, and joining the slabs' states."""
 
     def __init__(self, w, cuts, precision="fp64", **kw):
-        nx = int(w.n[0])
-        self.cuts = [0] + [int(c) for c in cuts] + [nx]
-        if any(b - a < 3 for a, b in zip(self.cuts[:-1], self.cuts[1:])):
-            raise ValueError("every slab needs at least 3 x cells: %s" % (self.cuts,))
-        periodic = w.bc[0][0] == 0
-        ns = len(self.cuts) - 1
-        fx = np.asarray(w.faces[0], dtype=np.float64)
+        plan = plan_slabs(w, cuts)
+        self.cuts = plan["cuts"]
         self.slabs = []
-        for s in range(ns):
-            a, b = self.cuts[s], self.cuts[s + 1]
-            lo = EXCHANGE if (s > 0 or periodic) else w.bc[0][0]
-            hi = EXCHANGE if (s + 1 < ns or periodic) else w.bc[0][1]
-            bc = [(lo, hi), tuple(w.bc[1]), tuple(w.bc[2])]
-            g = Grid((b - a, w.n[1], w.n[2]), [fx[a:b + 1], w.faces[1], w.faces[2]], w.mach, w.u_ref, w.mu, bc,
-                     precision=precision, cfl=w.cfl, dt_fixed=w.dt_fixed, rho_ref=w.rho_ref,
-                     stream=self.slabs[0].stream if self.slabs else kw.get("stream"),
-                     device=kw.get("device"))
+        for sp in plan["slabs"]:
+            g = Grid(sp["n"], sp["faces"], w.mach, w.u_ref, w.mu, sp["bc"], precision=precision, cfl=w.cfl,
+                     dt_fixed=w.dt_fixed, rho_ref=w.rho_ref,
+                     stream=self.slabs[0].stream if self.slabs else kw.get("stream"), device=kw.get("device"))
             g.set_inflow(*w.inflow)
             g.set_body_force(*w.body_force)
-            if w.state0 is not None:
-                g.set_state(np.ascontiguousarray(w.state0[:, :, :, a:b]))
+            if sp["state0"] is not None:
+                g.set_state(sp["state0"])
             self.slabs.append(g)
         # object id of the whole workload -> (slab, id in that slab)
         self.objects = []
-        for r in w.rotors:
-            s = self.slab_of(r.hub[0])
-            self.objects.append((s, self.slabs[s].add_rotor(r)))
-        for bd in w.bodies:
-            s = self.slab_of(float(np.mean(np.asarray(bd.xyz).reshape(-1, 3)[:, 0])))
-            self.objects.append((s, self.slabs[s].add_body(bd)))
-        self._handles = (C.c_void_p * ns)(*[g.h for g in self.slabs])
-
-    def slab_of(self, x):
-        """The slab whose x faces hold coordinate x."""
-        for s, g in enumerate(self.slabs):
-            f = g._faces[0]
-            if f[0] <= x < f[-1] or (s == len(self.slabs) - 1 and x == f[-1]):
-                return s
-        raise ValueError("x = %g outside the domain" % x)
+        for kind, obj, s in plan["objects"]:
+            sid = self.slabs[s].add_rotor(obj) if kind == "rotor" else self.slabs[s].add_body(obj)
+            self.objects.append((s, sid))
+        self._handles = (C.c_void_p * len(self.slabs))(*[g.h for g in self.slabs])
 
     def step(self, nsteps=1):
         t = C.c_double()

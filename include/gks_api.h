@@ -170,6 +170,32 @@ typedef struct {
  * (GKS_ERR_STATE). Allocates small library-owned device buffers. */
 int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *desc, int *id);
 
+/* gks_set_slab_lattice: for a slab of a slab group (gks_slab_step), the
+ * uniform x lattice of the group's whole domain, on which the forcing places
+ * cell centres and actuator and IB points: its origin x0, cell width hx, and
+ * the number of the domain's cells before this slab's first one. With it a
+ * slab's forcing has the bits of the whole grid's. Call it before adding
+ * rotors or bodies (GKS_ERR_STATE otherwise); the slab's x axis must be
+ * uniform and its first face must lie on that lattice (GKS_ERR_ARG
+ * otherwise). gks_slab_step requires it on every slab of a group that holds
+ * rotors or bodies. */
+int gks_set_slab_lattice(gks_grid *g, double x0, double hx, int cells_before);
+
+/* gks_share_actuator_lines: in a slab group, give slab g its share of rotor id
+ * of the neighbouring slab `owner` whose kernel support reaches their cut:
+ * in every group step the owner samples the flow and computes the point
+ * forces and loads, then g spreads those point forces into its own cells.
+ * *id_out receives the share's object id on g; gks_forces on it reports the
+ * owner's loads. g and owner must have the same precision and x lattice
+ * (gks_set_slab_lattice) and g must not have been stepped (GKS_ERR_ARG,
+ * GKS_ERR_STATE); GKS_ERR_RANGE if the support misses g. The share reads the
+ * owner's point buffers (it allocates nothing): destroy the two together. A
+ * grid holding a share steps only within its group (gks_step returns
+ * GKS_ERR_STATE). The rotors' own exchange-side check happens in
+ * gks_slab_step: a rotor whose support reaches a cut must be shared with the
+ * slab behind the cut. */
+int gks_share_actuator_lines(gks_grid *owner, int id, gks_grid *g, int *id_out);
+
 /* Per-point force scales s (host array of n_blades * n_pts, blade-major)
  * multiplying every point force of rotor id; 1 by default. */
 int gks_set_force_scales(gks_grid *g, int id, const double *h_scales);
@@ -205,9 +231,14 @@ int gks_step(gks_grid *g, int nsteps, double *t_out);
  * x-planes of the working array next to each exchange side (all y and z
  * rows, ghost rows included) are copied into the neighbour's ghost planes;
  * the CFL time step takes the largest |U|^2 of all slabs and the smallest
- * cell width of all slabs; each slab applies its own rotors and bodies,
- * whose kernel supports must not reach an exchange side (gks_add_actuator_lines
- * and gks_add_ib_points return GKS_ERR_RANGE otherwise). The first call
+ * cell width of all slabs; each slab applies its own rotors and bodies. A
+ * rotor's kernel support may reach a cut if the slab behind the cut holds a
+ * share of it (gks_share_actuator_lines; GKS_ERR_RANGE otherwise): owners
+ * compute their rotors' loads and spread them, then the shares spread the
+ * owners' point forces, then the bodies are applied. Bodies must stay inside
+ * their slab (gks_add_ib_points returns GKS_ERR_RANGE otherwise). With
+ * rotors or bodies, every slab needs the domain's x lattice
+ * (gks_set_slab_lattice). The first call
  * also gives each exchange side's ghost cells the neighbour's cell widths
  * (the geometry tables a grid of the whole domain has at the cut), so the
  * state of every slab then has the bits that grid would have.

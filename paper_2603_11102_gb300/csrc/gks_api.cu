@@ -40,6 +40,9 @@ struct gks_grid {
     Profiler prof;
     std::string err;
     std::vector<RotorDev> rotors;
+    // per rotor: for a share of a neighbouring slab's rotor (gks_share_actuator_lines), the owner
+    // grid and the owner's rotor index; else null, -1
+    std::vector<std::pair<const gks_grid *, int>> rotor_owner;
     std::vector<BodyDev> bodies;
     std::vector<int> obj_kind, obj_index;
     std::vector<void *> owned;
@@ -241,17 +244,23 @@ void prof_mark(void *ctx, int group, int begin)
 // Whether the x cells of [lo, hi] (with the one-cell margin of cell_range)
 // reach past an exchange side: a kernel support there would need the
 // neighbouring slab's cells.
+bool reaches_exchange_side(const Ctx &c, double lo, double hi, int side)
+{
+    if (c.bc[0][side] != GKS_BC_EXCHANGE) return false;
+    if (side == 0) return (long)floor((lo - c.x0[0]) / c.hu[0] - 0.5) - 1 - c.xoff < 0;
+    return (long)ceil((hi - c.x0[0]) / c.hu[0] - 0.5) + 1 - c.xoff > c.n[0] - 1;
+}
+
 bool reaches_exchange(const Ctx &c, double lo, double hi)
 {
-    const long i0 = (long)floor((lo - c.x0[0]) / c.hu[0] - 0.5) - 1;
-    const long i1 = (long)ceil((hi - c.x0[0]) / c.hu[0] - 0.5) + 1;
-    return (c.bc[0][0] == GKS_BC_EXCHANGE && i0 < 0) || (c.bc[0][1] == GKS_BC_EXCHANGE && i1 > c.n[0] - 1);
+    return reaches_exchange_side(c, lo, hi, 0) || reaches_exchange_side(c, lo, hi, 1);
 }
 
 int cell_range(const Ctx &c, int a, double lo, double hi, int out[2])
 {
-    long i0 = (long)floor((lo - c.x0[a]) / c.hu[a] - 0.5) - 1;
-    long i1 = (long)ceil((hi - c.x0[a]) / c.hu[a] - 0.5) + 1;
+    const int off = a == 0 ? c.xoff : 0;
+    long i0 = (long)floor((lo - c.x0[a]) / c.hu[a] - 0.5) - 1 - off;
+    long i1 = (long)ceil((hi - c.x0[a]) / c.hu[a] - 0.5) + 1 - off;
     if (i0 < 0) i0 = 0;
     if (i1 > c.n[a] - 1) i1 = c.n[a] - 1;
     if (i1 < i0) return -1;
@@ -540,8 +549,6 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
         cell_range(c, 1, d->hub[1] - rmax - cut, d->hub[1] + rmax + cut, r.box[1]) ||
         cell_range(c, 2, d->hub[2] - rmax - cut, d->hub[2] + rmax + cut, r.box[2]))
         return fail(g, GKS_ERR_RANGE, "rotor outside the grid");
-    if (reaches_exchange(c, d->hub[0] - cut, d->hub[0] + cut))
-        return fail(g, GKS_ERR_RANGE, "rotor support reaches an exchange side of the slab");
     r.norm = 1.0 / (d->eps * d->eps * d->eps * pow(3.14159265358979323846, 1.5));
     r.ie2 = 1.0 / (d->eps * d->eps);
     // per point: scale, X (3), F (4), Xr (3 floats in 2 doubles)
@@ -567,9 +574,53 @@ int gks_add_actuator_lines(gks_grid *g, const gks_rotor_desc *d, int *id)
     if (!rc) rc = sync(g);
     if (rc) return rc;
     g->rotors.push_back(r);
+    g->rotor_owner.push_back({nullptr, -1});
     g->obj_kind.push_back(0);
     g->obj_index.push_back((int)g->rotors.size() - 1);
     *id = (int)g->obj_kind.size() - 1;
+    return GKS_OK;
+}
+
+int gks_set_slab_lattice(gks_grid *g, double x0, double hx, int cells_before)
+{
+    if (!g) return fail(nullptr, GKS_ERR_ARG, "null grid");
+    Ctx &c = g->c;
+    if (g->stepped || !g->obj_kind.empty())
+        return fail(g, GKS_ERR_STATE, "the slab lattice is set before rotors, bodies and steps");
+    if (!(hx > 0.0) || cells_before < 0 || !c.uniform[0]) return fail(g, GKS_ERR_ARG, "bad slab lattice");
+    // the slab's first face lies on that lattice
+    if (fabs(c.x0[0] - (x0 + cells_before * hx)) > 1e-6 * hx || fabs(c.hu[0] - hx) > 1e-6 * hx)
+        return fail(g, GKS_ERR_ARG, "the slab's x faces are not on that lattice");
+    c.x0[0] = x0;
+    c.hu[0] = hx;
+    c.xoff = cells_before;
+    return GKS_OK;
+}
+
+int gks_share_actuator_lines(gks_grid *owner, int id, gks_grid *g, int *id_out)
+{
+    if (!owner || !g || !id_out || owner == g) return fail(g, GKS_ERR_ARG, "bad arguments");
+    if (id < 0 || id >= (int)owner->obj_kind.size() || owner->obj_kind[id] != 0)
+        return fail(g, GKS_ERR_ARG, "no rotor with that id on the owner");
+    const int ri = owner->obj_index[id];
+    if (owner->rotor_owner[ri].first) return fail(g, GKS_ERR_ARG, "that rotor is itself a share");
+    Ctx &c = g->c;
+    if (g->stepped) return fail(g, GKS_ERR_STATE, "objects must be added before the first step");
+    if (c.prec != owner->c.prec || !(c.uniform[0] && c.uniform[1] && c.uniform[2]) ||
+        c.x0[0] != owner->c.x0[0] || c.hu[0] != owner->c.hu[0])
+        return fail(g, GKS_ERR_ARG, "the sharing slab needs the owner's precision and x lattice");
+    RotorDev r = owner->rotors[ri];   // the owner's point buffers, read after the owner's loads
+    r.shared = 1;
+    const double cut = 3.0 * r.eps, rm = fmax(fabs(r.rmax), fabs(r.rmin));
+    if (cell_range(c, 0, r.hub[0] - cut, r.hub[0] + cut, r.box[0]) ||
+        cell_range(c, 1, r.hub[1] - rm - cut, r.hub[1] + rm + cut, r.box[1]) ||
+        cell_range(c, 2, r.hub[2] - rm - cut, r.hub[2] + rm + cut, r.box[2]))
+        return fail(g, GKS_ERR_RANGE, "the rotor's support misses this slab");
+    g->rotors.push_back(r);
+    g->rotor_owner.push_back({owner, ri});
+    g->obj_kind.push_back(0);
+    g->obj_index.push_back((int)g->rotors.size() - 1);
+    *id_out = (int)g->obj_kind.size() - 1;
     return GKS_OK;
 }
 
@@ -869,6 +920,8 @@ int gks_set_graphs(gks_grid *g, int on)
 int gks_step_async(gks_grid *g, int nsteps)
 {
     if (!g || nsteps < 0) return fail(g, GKS_ERR_ARG, "bad arguments");
+    for (const auto &o : g->rotor_owner)
+        if (o.first) return fail(g, GKS_ERR_STATE, "a slab holding a share of another slab's rotor steps with its group");
     for (int s = 0; s < nsteps; ++s) {
         // a step replays the graph in the steady state: the next step's
         // prep done by the last step (at most kMaxPrepBoxes forcing
@@ -961,11 +1014,19 @@ int slab_step_once(gks_grid *const *sl, int n)
         }
         launch_stage(cc[s], 2);
     }
+    // rotors: each owner's loads and projection, then every share's projection
+    // of the owner's point forces into its own cells; then the bodies
+    for (int s = 0; s < n; ++s)
+        for (size_t k = 0; k < sl[s]->obj_kind.size(); ++k)
+            if (sl[s]->obj_kind[k] == 0 && !sl[s]->rotors[sl[s]->obj_index[k]].shared)
+                launch_alm(sl[s]->c, sl[s]->rotors[sl[s]->obj_index[k]]);
+    for (int s = 0; s < n; ++s)
+        for (size_t k = 0; k < sl[s]->obj_kind.size(); ++k)
+            if (sl[s]->obj_kind[k] == 0 && sl[s]->rotors[sl[s]->obj_index[k]].shared)
+                launch_alm_spread(sl[s]->c, sl[s]->rotors[sl[s]->obj_index[k]]);
     for (int s = 0; s < n; ++s) {
         gks_grid *g = sl[s];
         const Ctx &c = g->c;
-        for (size_t k = 0; k < g->obj_kind.size(); ++k)
-            if (g->obj_kind[k] == 0) launch_alm(c, g->rotors[g->obj_index[k]]);
         for (size_t k = 0; k < g->obj_kind.size(); ++k)
             if (g->obj_kind[k] == 1) launch_ibm(c, g->bodies[g->obj_index[k]]);
         if (fused[s])
@@ -1062,6 +1123,40 @@ int gks_slab_step(gks_grid *const *slabs, int nslab, int nsteps, double *t_out)
             if (rc) return rc;
         }
         hmin = fmin(hmin, c.hmin);
+    }
+    // forcing: the slabs place cells on one x lattice, and a rotor whose
+    // support reaches an exchange side is shared with the slab behind it
+    const bool forced = [&] {
+        for (int s = 0; s < nslab; ++s)
+            if (!slabs[s]->obj_kind.empty()) return true;
+        return false;
+    }();
+    if (forced) {
+        int before = 0;
+        for (int s = 0; s < nslab; ++s) {
+            const Ctx &c = slabs[s]->c;
+            if (c.x0[0] != c0.x0[0] || c.hu[0] != c0.hu[0] || c.xoff != before)
+                return fail(nullptr, GKS_ERR_ARG, "forcing in a slab group needs every slab on one x lattice "
+                                                  "(gks_set_slab_lattice)");
+            before += c.n[0];
+        }
+        for (int s = 0; s < nslab; ++s) {
+            gks_grid *g = slabs[s];
+            for (size_t k = 0; k < g->rotors.size(); ++k) {
+                const RotorDev &r = g->rotors[k];
+                if (r.shared) continue;
+                const double cut = 3.0 * r.eps;
+                for (int side = 0; side < 2; ++side) {
+                    if (!reaches_exchange_side(g->c, r.hub[0] - cut, r.hub[0] + cut, side)) continue;
+                    const gks_grid *nb = slabs[side == 0 ? (s > 0 ? s - 1 : nslab - 1) : (s + 1 < nslab ? s + 1 : 0)];
+                    bool covered = false;
+                    for (const auto &o : nb->rotor_owner) covered |= o.first == g && o.second == (int)k;
+                    if (!covered)
+                        return fail(nullptr, GKS_ERR_RANGE, "a rotor support reaches a slab cut and the slab behind "
+                                                            "it holds no share of it (gks_share_actuator_lines)");
+                }
+            }
+        }
     }
     for (int s = 0; s < nslab; ++s) slabs[s]->c.hmin = hmin;   // the CFL step of the whole domain
     for (int k = 0; k < nsteps; ++k) {

@@ -35,7 +35,8 @@ constexpr double kPi = 3.14159265358979323846;
 struct Lattice {
     int n[3], P[3];
     long np;
-    double x0[3], h[3];
+    double x0[3], h[3];   // origin and width of the uniform lattice (a slab: its group's domain)
+    int off[3];           // index of the grid's first cell in that lattice (a slab: along x)
     int prec;
 };
 
@@ -47,6 +48,7 @@ Lattice make_lattice(const Ctx &c)
         L.P[d] = c.P[d];
         L.x0[d] = c.x0[d];
         L.h[d] = c.hu[d];
+        L.off[d] = d == 0 ? c.xoff : 0;
     }
     L.np = c.np;
     L.prec = c.prec;
@@ -60,7 +62,7 @@ __device__ __forceinline__ long lin_index(const Lattice &L, int i, int j, int k)
 
 __device__ __forceinline__ double centre(const Lattice &L, int d, int i)
 {
-    return __dadd_rn(L.x0[d], __dmul_rn((double)i + 0.5, L.h[d]));
+    return __dadd_rn(L.x0[d], __dmul_rn((double)(i + L.off[d]) + 0.5, L.h[d]));
 }
 
 __device__ __forceinline__ double dist(double dx, double dy, double dz)
@@ -88,7 +90,7 @@ __device__ bool trilinear(const Lattice &L, const void *S, const double X[3], do
     int i0[3];
     double fr[3];
     for (int d = 0; d < 3; ++d) {
-        const double s = (X[d] - L.x0[d]) / L.h[d] - 0.5;
+        const double s = (X[d] - L.x0[d]) / L.h[d] - 0.5 - (double)L.off[d];
         const double fl = floor(s);
         i0[d] = (int)fl;
         fr[d] = s - fl;
@@ -430,8 +432,8 @@ __device__ void point_cube(const Lattice &L, const BodyDev &b, int p, int lo[3],
 {
     const double cut = 3.0 * b.eps;
     for (int d = 0; d < 3; ++d) {
-        lo[d] = (int)floor((b.xyz[3 * p + d] - cut - L.x0[d]) / L.h[d] - 0.5) - 1;
-        hi[d] = (int)ceil((b.xyz[3 * p + d] + cut - L.x0[d]) / L.h[d] - 0.5) + 1;
+        lo[d] = (int)floor((b.xyz[3 * p + d] - cut - L.x0[d]) / L.h[d] - 0.5) - 1 - L.off[d];
+        hi[d] = (int)ceil((b.xyz[3 * p + d] + cut - L.x0[d]) / L.h[d] - 0.5) + 1 - L.off[d];
         if (lo[d] < b.box[d][0]) lo[d] = b.box[d][0];
         if (hi[d] > b.box[d][1]) hi[d] = b.box[d][1];
     }
@@ -584,6 +586,12 @@ void launch_alm(const Ctx &c, const RotorDev &r)
     mark(c, K_ALM, 1);
     alm_loads_kernel<<<1, 256, 0, c.stream>>>(L, c.state, r, c.scal);
     mark(c, K_ALM, 0);
+    launch_alm_spread(c, r);
+}
+
+void launch_alm_spread(const Ctx &c, const RotorDev &r)
+{
+    const Lattice L = make_lattice(c);
     const long nbox = (long)(r.box[0][1] - r.box[0][0] + 1) * (r.box[1][1] - r.box[1][0] + 1) *
                       (r.box[2][1] - r.box[2][0] + 1);
     if (nbox <= 0) return;
@@ -605,8 +613,9 @@ int body_box(const Ctx &c, const double *xyz, int n, double eps, int box[3][2])
             lo = fmin(lo, xyz[3 * p + d]);
             hi = fmax(hi, xyz[3 * p + d]);
         }
-        long a = (long)floor((lo - rad - c.x0[d]) / c.hu[d] - 0.5) - 1;
-        long b = (long)ceil((hi + rad - c.x0[d]) / c.hu[d] - 0.5) + 1;
+        const int off = d == 0 ? c.xoff : 0;
+        long a = (long)floor((lo - rad - c.x0[d]) / c.hu[d] - 0.5) - 1 - off;
+        long b = (long)ceil((hi + rad - c.x0[d]) / c.hu[d] - 0.5) + 1 - off;
         if (a < 0) a = 0;
         if (b > c.n[d] - 1) b = c.n[d] - 1;
         if (b < a) return -1;

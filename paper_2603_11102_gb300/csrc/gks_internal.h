@@ -49,6 +49,7 @@ struct Ctx {
     double inflow[4];         // rho, u, v, w
     double fbody[3];
     double x0[3], hu[3];      // origin and width of uniform axes (forcing)
+    int xoff = 0;             // a slab's first cell in the x lattice of its group's domain (forcing)
     int uniform[3];
     cudaStream_t stream;
 
@@ -141,7 +142,10 @@ struct RotorDev {
     double *et;         // 2 nb: -sin th_b, cos th_b
     double *out;        // thrust[nb], torque[nb], power, cp, ct
     int box[3][2];      // interior cell box swept by the 3 eps supports
+    int shared = 0;     // a slab's share of a neighbouring slab's rotor: its point buffers are the
+                        // owner's, the owner computes the loads, this grid only spreads them
 };
+void launch_alm_spread(const Ctx &c, const RotorDev &r);   // projection only (a shared rotor)
 void launch_alm(const Ctx &c, const RotorDev &r);
 void launch_alm_loads(const Ctx &c, const RotorDev &r);   // loads only, no projection
 

@@ -73,6 +73,8 @@ SIGNATURES = {
                                     C.POINTER(C.c_int)]),
     "gks_step": (C.c_int, [C.c_void_p, C.c_int, _dp]),
     "gks_slab_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, _dp]),
+    "gks_set_slab_lattice": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int]),
+    "gks_share_actuator_lines": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
     "gks_get_time": (C.c_int, [C.c_void_p, _dp, _dp]),
     "gks_set_time": (C.c_int, [C.c_void_p, C.c_double]),
     "gks_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ForcesOut), _dp]),
@@ -260,6 +262,18 @@ class Grid:
         _check(lib.gks_add_actuator_lines(self.h, C.byref(d), C.byref(rid)), self.h)
         self.objects.append(("rotor", d.n_blades, d.n_pts))
         return rid.value
+
+    def set_slab_lattice(self, x0, hx, cells_before):
+        """The x lattice of a slab group's domain (gks_set_slab_lattice)."""
+        _check(lib.gks_set_slab_lattice(self.h, float(x0), float(hx), int(cells_before)), self.h)
+
+    def share_rotor(self, owner, rid):
+        """This slab's share of rotor rid of the neighbouring slab owner
+        (gks_share_actuator_lines); returns the share's object id."""
+        out = C.c_int()
+        _check(lib.gks_share_actuator_lines(owner.h, int(rid), self.h, C.byref(out)), self.h)
+        self.objects.append(owner.objects[rid])   # its loads are the owner's
+        return out.value
 
     def set_force_scales(self, rid, s):
         s, p = _arr(s)
@@ -508,7 +522,7 @@ def plan_slabs(w, cuts):
         a, b = cuts[s], cuts[s + 1]
         lo = EXCHANGE if (s > 0 or periodic) else w.bc[0][0]
         hi = EXCHANGE if (s + 1 < ns or periodic) else w.bc[0][1]
-        slabs.append({"n": (b - a, w.n[1], w.n[2]), "faces": [fx[a:b + 1], w.faces[1], w.faces[2]],
+        slabs.append({"n": (b - a, w.n[1], w.n[2]), "faces": [fx[a:b + 1], w.faces[1], w.faces[2]], "cells_before": a,
                       "bc": [(lo, hi), tuple(w.bc[1]), tuple(w.bc[2])],
                       "state0": None if w.state0 is None else np.ascontiguousarray(w.state0[:, :, :, a:b])})
 
@@ -519,9 +533,31 @@ def plan_slabs(w, cuts):
                 return s
         raise ValueError("x = %g outside the domain" % x)
 
-    objects = [("rotor", r, slab_of(r.hub[0])) for r in w.rotors]
+    h = fx[1] - fx[0]
+    xc = 0.5 * (fx[1:] + fx[:-1])
+
+    def rotor_slabs(r):
+        # the owner samples the hub plane: both cell centres around it inside
+        # the slab; the slabs that the 3 eps support (with a cell of margin)
+        # reaches get shares
+        owner = None
+        for s in range(ns):
+            if xc[cuts[s]] <= r.hub[0] <= xc[cuts[s + 1] - 1]:
+                owner = s
+        if owner is None:
+            raise ValueError("a cut lies within half a cell of the rotor plane at x = %g" % r.hub[0])
+        lo, hi = r.hub[0] - 3 * r.eps - 2 * h, r.hub[0] + 3 * r.eps + 2 * h
+        shares = [s for s in range(ns) if s != owner and fx[cuts[s]] < hi and fx[cuts[s + 1]] > lo]
+        return owner, shares
+
+    objects, shares = [], []
+    for r in w.rotors:
+        owner, sh = rotor_slabs(r)
+        objects.append(("rotor", r, owner))
+        shares.append(sh)
     objects += [("body", b, slab_of(float(np.mean(np.asarray(b.xyz).reshape(-1, 3)[:, 0])))) for b in w.bodies]
-    return {"cuts": cuts, "slabs": slabs, "objects": objects}
+    return {"cuts": cuts, "slabs": slabs, "objects": objects, "rotor_shares": shares,
+            "lattice": (float(fx[0]), float(h))}
 
 
 class SlabGroup:
@@ -545,12 +581,17 @@ class SlabGroup:
             g.set_body_force(*w.body_force)
             if sp["state0"] is not None:
                 g.set_state(sp["state0"])
+            if w.rotors or w.bodies:
+                g.set_slab_lattice(plan["lattice"][0], plan["lattice"][1], sp["cells_before"])
             self.slabs.append(g)
         # object id of the whole workload -> (slab, id in that slab)
         self.objects = []
-        for kind, obj, s in plan["objects"]:
+        for k, (kind, obj, s) in enumerate(plan["objects"]):
             sid = self.slabs[s].add_rotor(obj) if kind == "rotor" else self.slabs[s].add_body(obj)
             self.objects.append((s, sid))
+            if kind == "rotor":
+                for t in plan["rotor_shares"][k]:
+                    self.slabs[t].share_rotor(self.slabs[s], sid)
         self._handles = (C.c_void_p * len(self.slabs))(*[g.h for g in self.slabs])
 
     def step(self, nsteps=1):

@@ -94,6 +94,47 @@ def test_rotor_and_bodies_in_one_slab_of_two(gks, precision):
     sg.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("cut", [27, 20])
+def test_rotor_support_across_a_cut_is_shared(gks, precision, cut):
+    """A rotor whose kernel support crosses the cut: the slab that holds the
+    rotor plane samples the flow and computes the loads, the slab behind the
+    cut spreads the same point forces into its cells (a share); the rotor
+    sits in the first slab (cut 27) or in the second (cut 20, its cells on
+    the domain's lattice by their offset)."""
+    w = WL.alm_rotor(n=(96, 32, 32), steps=6, n_pts=20)
+    w.state0 = WL.perturbed(w, 0.02, seed=3)
+    plan = gks.plan_slabs(w, [cut])
+    assert plan["rotor_shares"][0] == [1 - plan["objects"][0][2]]
+    g, sg, t1, t2 = single_and_slabs(gks, w, [cut], precision, 6)
+    assert_same(g, sg, t1, t2, precision)
+    a, b = g.forces(0), sg.forces(0)
+    for k, v in a.items():
+        x, y = np.asarray(v, dtype=np.float64), np.asarray(b[k], dtype=np.float64)
+        if precision == "fp64":
+            assert np.array_equal(x, y), k
+        else:
+            assert np.max(np.abs(x - y)) <= 1e-5 * max(np.max(np.abs(x)), 1e-30), k
+    g.close()
+    sg.close()
+
+
+def test_objects_in_a_later_slab_sit_on_the_domain_lattice(gks):
+    """Rotor, tower and nacelle all in the second slab (cut at x cell 10):
+    their cells and points on the domain's lattice through the slab's offset,
+    so state, loads and body forces have the single grid's bits (FP64)."""
+    w = WL.alm_ibm_rotor(n=(96, 64, 64), steps=4, n_pts=20)
+    w.state0 = WL.perturbed(w, 0.02, seed=5)
+    g, sg, t1, t2 = single_and_slabs(gks, w, [10], "fp64", 4)
+    assert_same(g, sg, t1, t2, "fp64")
+    for oid in range(3):
+        a, b = g.forces(oid), sg.forces(oid)
+        for k, v in a.items():
+            assert np.array_equal(np.asarray(v), np.asarray(b[k])), (oid, k)
+    g.close()
+    sg.close()
+
+
 def test_smooth_state_with_walls_and_an_outflow_across_four_slabs(gks):
     """A seeded smooth state with inflow / outflow in x, slip and no-slip
     walls in y and z, four slabs of unequal widths (FP64)."""
@@ -124,18 +165,31 @@ def test_stretched_x_axis_cut_three_times(gks, precision):
 
 
 def test_support_across_a_cut_and_mismatched_slabs_are_refused(gks):
-    """A rotor whose kernel support reaches a cut is refused (GKS_ERR_RANGE);
+    """A rotor whose kernel support reaches a cut without a share behind it is
+    refused by the group step (GKS_ERR_RANGE), a body's at registration;
     slabs whose y faces differ are refused by the group step (GKS_ERR_ARG)."""
+    import ctypes as C
     w = WL.alm_rotor(n=(96, 32, 32), steps=2, n_pts=10)
-    hub_cell = int(round((w.rotors[0].hub[0] - w.faces[0][0]) / (w.faces[0][1] - w.faces[0][0])))
+    plan = gks.plan_slabs(w, [27])
+    grids = []
+    for sp in plan["slabs"]:
+        gr = gks.Grid(sp["n"], sp["faces"], w.mach, w.u_ref, w.mu, sp["bc"], precision="fp64",
+                      stream=grids[0].stream if grids else None)
+        gr.set_slab_lattice(plan["lattice"][0], plan["lattice"][1], sp["cells_before"])
+        grids.append(gr)
+    grids[0].add_rotor(w.rotors[0])   # no share on the second slab
+    h = (C.c_void_p * 2)(grids[0].h, grids[1].h)
+    assert gks.lib.gks_slab_step(h, 2, 1, None) == -6
+    wb = WL.alm_ibm_rotor(n=(96, 64, 64), steps=2, n_pts=10)
     with pytest.raises(gks.GKSError) as e:
-        gks.SlabGroup(w, [hub_cell + 2], precision="fp64")
+        gks.SlabGroup(wb, [27], precision="fp64")   # the nacelle's support crosses x cell 27
     assert e.value.code == -6
+    for gr in grids:
+        gr.close()
     a = gks.Grid((12, 8, 8), [np.linspace(0, 1, 13), np.linspace(0, 1, 9), np.linspace(0, 1, 9)], 0.1, 1.0, 1e-3,
                  [(4, 5), (0, 0), (0, 0)])
     b = gks.Grid((12, 8, 8), [np.linspace(1, 2, 13), np.linspace(0, 1.5, 9), np.linspace(0, 1, 9)], 0.1, 1.0, 1e-3,
                  [(5, 4), (0, 0), (0, 0)], stream=a.stream)
-    import ctypes as C
     h = (C.c_void_p * 2)(a.h, b.h)
     assert gks.lib.gks_slab_step(h, 2, 1, None) == -1
     a.close()

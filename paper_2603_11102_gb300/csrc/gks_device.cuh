@@ -536,6 +536,106 @@ __device__ __forceinline__ void face_equilibrium_ds2(const Phys<dsf> &ph, const 
     Q0[3] = Ql[3] * Pl + Qr[3] * Pr;
 }
 
+// ---- FP32 face state on packed pairs ----
+
+// Approximate reciprocal per lane (the scalar FP32 path's __fdividef(1, x)).
+__device__ __forceinline__ f2 wrcp(f2 x) { return f2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+
+// weno5_pair of two components at once, every multiply-add fused explicitly
+// and the constant factors folded into the candidates:
+//  - the indicators are those of weno5_pair divided by 13/12 (the weights
+//    depend on their ratios only): s_k = (eps 12/13 + t_k^2 + (3/13) u_k^2)^2,
+//    with u_0 = t_0 + 2 (c - b) and u_2 = t_2 + 2 (c - d);
+//  - the right-face weights times 10 s0 s1 s2 / 3 are s1 s2 / 3, 2 s0 s2 and
+//    s0 s1 (mirrored for the left face), so with the candidates P_k = the
+//    integer-coefficient ones divided by 18, 3 and 6 the face value is
+//    (s12 P0 + s02 P1 + s01 P2) / (s12 / 3 + 2 s02 + s01).
+__device__ __forceinline__ void weno5_pair2(const f2 q[5], f2 &right, f2 &left)
+{
+    const f2 m2(-2.0f), two(2.0f), eps(float(12e-6 / 13.0)), k(float(3.0 / 13.0));
+    const f2 a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
+    f2 t = fma(b, m2, a) + c, u = fma(c - b, two, t);
+    f2 s0 = fma(t, t, fma(u * k, u, eps));
+    t = fma(c, m2, b) + d;
+    u = b - d;
+    f2 s1 = fma(t, t, fma(u * k, u, eps));
+    t = fma(d, m2, c) + e;
+    u = fma(c - d, two, t);
+    f2 s2 = fma(t, t, fma(u * k, u, eps));
+    s0 = s0 * s0;
+    s1 = s1 * s1;
+    s2 = s2 * s2;
+    const f2 s02 = s0 * s2, s01 = s0 * s1, s12 = s1 * s2;
+    const f2 third(float(1.0 / 3.0));
+    const f2 c3 = c * third, c53 = c * f2(float(5.0 / 3.0)), c1118 = c * f2(float(11.0 / 18.0));
+    const f2 k19(float(1.0 / 9.0)), k718(float(-7.0 / 18.0)), k23(float(2.0 / 3.0)), km13(float(-1.0 / 3.0));
+    const f2 k56(float(5.0 / 6.0)), km16(float(-1.0 / 6.0));
+    {
+        // right face: candidates on (a,b,c), (b,c,d), (c,d,e)
+        const f2 P0 = fma(a, k19, fma(b, k718, c1118));
+        const f2 P1 = fma(b, km13, fma(d, k23, c53));
+        const f2 P2 = fma(e, km16, fma(d, k56, c3));
+        right = fma(s12, P0, fma(s02, P1, s01 * P2)) * wrcp(fma(s12, third, fma(s02, two, s01)));
+    }
+    {
+        // left face: the mirrored candidates with indicators s2, s1, s0
+        const f2 P0 = fma(e, k19, fma(d, k718, c1118));
+        const f2 P1 = fma(d, km13, fma(b, k23, c53));
+        const f2 P2 = fma(a, km16, fma(b, k56, c3));
+        left = fma(s01, P0, fma(s02, P1, s12 * P2)) * wrcp(fma(s01, third, fma(s02, two, s12)));
+    }
+}
+
+// half_space_terms of two FP32 arguments: the series of both lanes as pairs
+// when both lie in |z| <= 1/2 (the same operations per lane as the scalar
+// series, so the same bits), else lane by lane.
+__device__ __forceinline__ void half_space_terms(f2 z, f2 &e, f2 &m1, f2 &ex)
+{
+    if (fabsf(z.v.x) <= 0.5f && fabsf(z.v.y) <= 0.5f) {
+        const f2 t = z * z, x = t * f2(-1.0f);
+        constexpr double k = 1.1283791670955126;   // 2 / sqrt(pi)
+        f2 p = f2(float(k / (720.0 * 13.0)));
+        p = fma(p, t, f2(float(-k / (120.0 * 11.0))));
+        p = fma(p, t, f2(float(k / (24.0 * 9.0))));
+        p = fma(p, t, f2(float(-k / (6.0 * 7.0))));
+        p = fma(p, t, f2(float(k / (2.0 * 5.0))));
+        p = fma(p, t, f2(float(-k / 3.0)));
+        p = fma(p, t, f2(float(k)));
+        e = p * z;
+        f2 q = f2(float(1.0 / 5040.0));
+        q = fma(q, x, f2(float(1.0 / 720.0)));
+        q = fma(q, x, f2(float(1.0 / 120.0)));
+        q = fma(q, x, f2(float(1.0 / 24.0)));
+        q = fma(q, x, f2(float(1.0 / 6.0)));
+        q = fma(q, x, f2(0.5f));
+        q = fma(q, x, f2(1.0f));
+        m1 = q * x;
+        ex = f2(1.0f) + m1;
+    } else {
+        half_space_terms(z.v.x, e.v.x, m1.v.x, ex.v.x);
+        half_space_terms(z.v.y, e.v.y, m1.v.y, ex.v.y);
+    }
+}
+
+// face_equilibrium with the components paired as (rho, m_n) and (m_t1, m_t2)
+// (index 0 and 1 of L, R and Q0) and the half-space terms of the left and
+// right states as one pair (lane 0 left, lane 1 right).
+__device__ __forceinline__ void face_equilibrium2(const Phys<float> &ph, const f2 L[2], const f2 R[2], f2 Q0[2])
+{
+    const f2 r = f2(ph.off) + f2(L[0].v.x, R[0].v.x);
+    const f2 U = f2(L[0].v.y, R[0].v.y) * wrcp(r);
+    f2 e, m1, x;
+    half_space_terms(f2(ph.sqlam) * U, e, m1, x);
+    // (<u^0>_{u>0} of the left state, <u^0>_{u<0} of the right one)
+    const f2 P = fma(e, f2(0.5f, -0.5f), f2(0.5f));
+    const f2 E = f2(ph.kE) * x;
+    const float d0 = (0.5f * ph.off) * (e.v.x - e.v.y);
+    const float d1 = fmaf(L[0].v.x, E.v.x, -(R[0].v.x * E.v.y)) + (ph.kE * ph.off) * (m1.v.x - m1.v.y);
+    const f2 Pl(P.v.x), Pr(P.v.y);
+    Q0[0] = fma(R[0], Pr, fma(L[0], Pl, f2(d0, d1)));
+    Q0[1] = fma(R[1], Pr, L[1] * Pl);
+}
+
 __device__ __forceinline__ Phys<dsf2> pair_phys(const Phys<dsf> &p)
 {
     Phys<dsf2> q;

@@ -175,14 +175,18 @@ struct FaceEqArgs {
     Phys<C> ph;      // in the compute type
 };
 
-constexpr int kMarch = 16;   // faces per thread of the marching face-state kernel
+// Faces per thread of the marching face-state kernels: FP32 (packed) and
+// FP64 / double-single (the longer march halves the FP32 kernel's window
+// warm-up at the same speed of the march itself).
+constexpr int kMarch32 = 32, kMarch = 16;
 
 // Marching variant: each thread walks K consecutive faces along d at one
 // tangential position of the extended face box, with the 5 cells around the
 // current cell in registers. Per cell it forms both face values of WENO5
 // from one set of smoothness indicators; face f takes the right-face value
-// of cell f-1 and the left-face value of cell f. R is the storage type, C
-// the arithmetic type (R, or double-single for FP64 storage).
+// of cell f-1 and the left-face value of cell f. Launched for FP64 grids in
+// FP64 arithmetic; FP32 grids and double-single arithmetic take the packed
+// variants below, which march the same way.
 template <typename R, typename C = R>
 __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
 {
@@ -217,9 +221,6 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
     R nxt[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) nxt[v] = __ldg(A.w + comp[v] * A.np + base + (long)(f0 + 2 + G) * A.sd);
-    // unrolled (FP32) so that the window shifts and the carried values cost no moves
-    constexpr int UNR = std::is_same<C, float>::value ? 2 : 1;
-#pragma unroll UNR
     for (int f = f0; f < f1; ++f) {
         C Ql[4], Qr[4];
 #pragma unroll
@@ -247,6 +248,77 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
             A.fq[v * A.nfq + o] = cvt<Mid<R, C>>(Q0[v]);
             // cells f-2 .. f+1 are w[v][0..3]
             A.fq[(4 + v) * A.nfq + o] = cvt<Mid<R, C>>((C(15) * (w[v][2] - w[v][1]) - (w[v][3] - w[v][0])) * s);
+        }
+    }
+}
+
+// face_eq_march_kernel for FP32 grids on packed pairs: WENO5 of the
+// components paired as (rho, m_n) and (m_t1, m_t2), the half-space terms of
+// the left and right states as one pair, the normal slopes paired like the
+// components. Unrolled by two so that the window shifts cost no moves.
+__global__ void __launch_bounds__(256, 3) face_eq_f2_kernel(FaceEqArgs<float, float> A)
+{
+    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
+    const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
+    const int f0 = blockIdx.z * A.K;
+    if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= A.nf) return;
+    const int f1 = min(f0 + A.K, A.nf);
+    const long base = (long)(a + G) * A.s1 + (long)(b + G) * A.s2;   // cell index along d = -G
+    // cells f0-3 .. f1+1 are read, faces f0 .. f1-1 written
+    if (!in_bounds(base + (long)(f0 - 3 + G) * A.sd, A.np) || !in_bounds(base + (long)(f1 + 1 + G) * A.sd, A.np) ||
+        !in_bounds(((long)f0 * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq) ||
+        !in_bounds(((long)(f1 - 1) * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2), A.nfq))
+        return;
+    const float *pc[4] = {A.w + base, A.w + (long)A.cn * A.np + base, A.w + (long)A.c1 * A.np + base,
+                          A.w + (long)A.c2 * A.np + base};
+    // window w[p][k] = cell (c - 2 + k) of component pair p; start with c = f0 - 1
+    f2 w[2][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const long o = (long)(f0 - 3 + k + G) * A.sd;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) w[q][k] = f2(__ldg(pc[2 * q] + o), __ldg(pc[2 * q + 1] + o));
+    }
+    f2 Qprev[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        f2 l;
+        weno5_pair2(w[q], Qprev[q], l);
+    }
+    // the cell entering the window, loaded one face ahead
+    float nxt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) nxt[v] = __ldg(pc[v] + (long)(f0 + 2 + G) * A.sd);
+#pragma unroll 2
+    for (int f = f0; f < f1; ++f) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[q][k] = w[q][k + 1];
+            w[q][4] = f2(nxt[2 * q], nxt[2 * q + 1]);
+        }
+        if (f + 1 < f1) {
+            // cell f + 3 <= nf + 1 = n + 2: inside the ghost layers
+#pragma unroll
+            for (int v = 0; v < 4; ++v) nxt[v] = __ldg(pc[v] + (long)(f + 3 + G) * A.sd);
+        }
+        f2 Ql[2], Qr[2], Q0[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            Ql[q] = Qprev[q];
+            weno5_pair2(w[q], Qprev[q], Qr[q]);
+        }
+        face_equilibrium2(A.ph, Ql, Qr, Q0);
+        const f2 s(A.ihf[f] * float(1.0 / 12.0));
+        const long o = ((long)f * (A.n2 + 4) + (b + 2)) * A.e1p + (a + 2);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            // cells f-2 .. f+1 are w[q][0..3]
+            const f2 dq = fma(w[q][3] - w[q][0], f2(-1.0f), (w[q][2] - w[q][1]) * f2(15.0f)) * s;
+            A.fq[(2 * q) * A.nfq + o] = Q0[q].v.x;
+            A.fq[(2 * q + 1) * A.nfq + o] = Q0[q].v.y;
+            A.fq[(4 + 2 * q) * A.nfq + o] = dq.v.x;
+            A.fq[(5 + 2 * q) * A.nfq + o] = dq.v.y;
         }
     }
 }
@@ -1111,15 +1183,15 @@ __global__ void __launch_bounds__(256) update_ds_kernel(UpdArgs<double, dsf> U, 
     if (STAGE == 2 && U.prep) block_max_to(mx, &scal->maxu2_bits);
 }
 
-// Faces per thread of the marching face-state kernel: kMarch, halved (down
-// to 4) while the launch would have fewer than two blocks per SM, so that a
-// small grid spreads its march over the GPU (each halving adds one WENO5 pair
-// per thread to warm the window up). A model that traded waves of resident
-// blocks against the per-thread work chose shorter marches for the large
-// grids too and was slower there.
-int march_faces(long blocks_xy, int nf)
+// Faces per thread of the marching face-state kernel: k0 (kMarch32 or
+// kMarch), halved (down to 4) while the launch would have fewer than two
+// blocks per SM, so that a small grid spreads its march over the GPU (each
+// halving adds one WENO5 pair per thread to warm the window up). A model that
+// traded waves of resident blocks against the per-thread work chose shorter
+// marches for the large grids too and was slower there.
+int march_faces(long blocks_xy, int nf, int k0)
 {
-    int K = kMarch;
+    int K = k0;
     while (K > 4 && blocks_xy * ((nf + K - 1) / K) < 2L * sm_count()) K /= 2;
     return K;
 }
@@ -1204,7 +1276,8 @@ FaceEqArgs<R, C> face_eq_args(const Ctx &c, int d, const R *w, const Phys<C> &ph
     E.c2 = 1 + t2;
     E.ph = ph;
     E.nf = c.n[d] + 1;
-    E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf);
+    E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf,
+                      std::is_same<C, float>::value ? kMarch32 : kMarch);
     return E;
 }
 
@@ -1259,6 +1332,8 @@ void stage_impl(const Ctx &c)
         mark(c, K_FACE_EQ, 1);
         if constexpr (std::is_same<C, dsf>::value)
             face_eq_ds2_kernel<<<ge, blk, 0, c.stream>>>(E);
+        else if constexpr (std::is_same<C, float>::value)
+            face_eq_f2_kernel<<<ge, blk, 0, c.stream>>>(E);
         else
             face_eq_march_kernel<R, C><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);
@@ -1674,7 +1749,7 @@ void launch_face_state32(const Ctx &c, int d, const float *w)
 {
     const FaceEqArgs<float, float> E = face_eq_args<float, float>(c, d, w, make_phys<float>(c));
     const dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
-    face_eq_march_kernel<float, float><<<ge, dim3(TX, TY), 0, c.stream>>>(E);
+    face_eq_f2_kernel<<<ge, dim3(TX, TY), 0, c.stream>>>(E);
 }
 
 void launch_stage(const Ctx &c, int stage)

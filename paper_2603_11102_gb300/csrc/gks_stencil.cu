@@ -1184,15 +1184,17 @@ __global__ void __launch_bounds__(256) update_ds_kernel(UpdArgs<double, dsf> U, 
 }
 
 // Faces per thread of the marching face-state kernel: k0 (kMarch32 or
-// kMarch), halved (down to 4) while the launch would have fewer than two
-// blocks per SM, so that a small grid spreads its march over the GPU (each
-// halving adds one WENO5 pair per thread to warm the window up). A model that
-// traded waves of resident blocks against the per-thread work chose shorter
-// marches for the large grids too and was slower there.
-int march_faces(long blocks_xy, int nf, int k0)
+// kMarch), halved (down to 4) while the launch would have fewer than
+// min_per_sm blocks per SM, so that a smaller grid spreads its march over
+// more resident blocks (each halving adds one WENO5 pair per thread to warm
+// the window up). The packed FP32 kernel (3 blocks per SM) asks for 9, three
+// waves: measured on 128^3, 192^3 and 384x256x256 grids this picked the
+// fastest of 8, 16 and 32 faces each time (0.045, 0.122, 0.383 ms per
+// launch). The FP64 kernels ask for 2.
+int march_faces(long blocks_xy, int nf, int k0, int min_per_sm)
 {
     int K = k0;
-    while (K > 4 && blocks_xy * ((nf + K - 1) / K) < 2L * sm_count()) K /= 2;
+    while (K > 4 && blocks_xy * ((nf + K - 1) / K) < (long)min_per_sm * sm_count()) K /= 2;
     return K;
 }
 
@@ -1276,8 +1278,9 @@ FaceEqArgs<R, C> face_eq_args(const Ctx &c, int d, const R *w, const Phys<C> &ph
     E.c2 = 1 + t2;
     E.ph = ph;
     E.nf = c.n[d] + 1;
-    E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf,
-                      std::is_same<C, float>::value ? kMarch32 : kMarch);
+    constexpr bool F32 = std::is_same<C, float>::value;
+    E.K = march_faces((long)((E.n1 + 4 + 31) / 32) * ((E.n2 + 4 + 7) / 8), E.nf, F32 ? kMarch32 : kMarch,
+                      F32 ? 9 : 2);
     return E;
 }
 

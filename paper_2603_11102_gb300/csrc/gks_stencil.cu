@@ -256,11 +256,19 @@ __global__ void __launch_bounds__(256) face_eq_march_kernel(FaceEqArgs<R, C> A)
 // components paired as (rho, m_n) and (m_t1, m_t2), the half-space terms of
 // the left and right states as one pair, the normal slopes paired like the
 // components. Unrolled by two so that the window shifts cost no moves.
+//
+// SEG (the x faces, whose cells are consecutive along the march but a row
+// apart across t1): a warp's lanes are 4 consecutive march segments of K
+// faces times 8 rows along t1, so that the rows a warp walks (8 per
+// component instead of 32) stay in L1 for the K faces that reuse each sector;
+// a store of the face box still writes 4 whole sectors (8 rows of 4
+// segments).
+template <bool SEG>
 __global__ void __launch_bounds__(256, 3) face_eq_f2_kernel(FaceEqArgs<float, float> A)
 {
-    const int a = (int)(blockIdx.x * 32 + threadIdx.x) - 2;
+    const int a = SEG ? (int)(blockIdx.x * 8 + (threadIdx.x & 7)) - 2 : (int)(blockIdx.x * 32 + threadIdx.x) - 2;
     const int b = (int)(blockIdx.y * 8 + threadIdx.y) - 2;
-    const int f0 = blockIdx.z * A.K;
+    const int f0 = SEG ? (int)(blockIdx.z * 4 + (threadIdx.x >> 3)) * A.K : (int)blockIdx.z * A.K;
     if (a >= A.n1 + 2 || b >= A.n2 + 2 || f0 >= A.nf) return;
     const int f1 = min(f0 + A.K, A.nf);
     const long base = (long)(a + G) * A.s1 + (long)(b + G) * A.s2;   // cell index along d = -G
@@ -320,6 +328,21 @@ __global__ void __launch_bounds__(256, 3) face_eq_f2_kernel(FaceEqArgs<float, fl
             A.fq[(4 + 2 * q) * A.nfq + o] = dq.v.x;
             A.fq[(5 + 2 * q) * A.nfq + o] = dq.v.y;
         }
+    }
+}
+
+// FP32 face state of direction d: the x faces (unit stride along the
+// normal) by march segments of at most 8 faces, 4 per warp.
+void launch_face_eq_f2(FaceEqArgs<float, float> E, int d, cudaStream_t stream)
+{
+    const dim3 blk(TX, TY);
+    if (d == 0 && E.sd == 1) {
+        E.K = std::min(E.K, 8);
+        const dim3 g((E.n1 + 4 + 7) / 8, (E.n2 + 4 + 7) / 8, (E.nf + 4 * E.K - 1) / (4 * E.K));
+        face_eq_f2_kernel<true><<<g, blk, 0, stream>>>(E);
+    } else {
+        const dim3 g((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
+        face_eq_f2_kernel<false><<<g, blk, 0, stream>>>(E);
     }
 }
 
@@ -1336,7 +1359,7 @@ void stage_impl(const Ctx &c)
         if constexpr (std::is_same<C, dsf>::value)
             face_eq_ds2_kernel<<<ge, blk, 0, c.stream>>>(E);
         else if constexpr (std::is_same<C, float>::value)
-            face_eq_f2_kernel<<<ge, blk, 0, c.stream>>>(E);
+            launch_face_eq_f2(E, d, c.stream);
         else
             face_eq_march_kernel<R, C><<<ge, blk, 0, c.stream>>>(E);
         mark(c, K_FACE_EQ, 0);
@@ -1750,9 +1773,7 @@ void launch_group_max_u2(Scalars *const *scal, int n, cudaStream_t stream)
 // w into the face box c.fq (the reverse recomputes it instead of storing it).
 void launch_face_state32(const Ctx &c, int d, const float *w)
 {
-    const FaceEqArgs<float, float> E = face_eq_args<float, float>(c, d, w, make_phys<float>(c));
-    const dim3 ge((E.n1 + 4 + 31) / 32, (E.n2 + 4 + 7) / 8, (E.nf + E.K - 1) / E.K);
-    face_eq_f2_kernel<<<ge, dim3(TX, TY), 0, c.stream>>>(E);
+    launch_face_eq_f2(face_eq_args<float, float>(c, d, w, make_phys<float>(c)), d, c.stream);
 }
 
 void launch_stage(const Ctx &c, int stage)
